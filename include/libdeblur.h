@@ -1,0 +1,148 @@
+/*
+ * libdeblur -- Wiener + robust regularised Richardson-Lucy (WR3L) deblurring
+ * on one NVIDIA B300 (sm_103a).  C ABI.
+ *
+ * Method: Welk, Raudaschl, Schwarzbauer, Erler, Laeuter, "Fast and Robust
+ * Linear Motion Deblurring".  The observed grey image f is modelled as
+ * f = g*h + n for a known space-invariant point-spread function h (Sec. 2,
+ * Eq. 1).  The pipeline is a Wiener filter (Sec. 2.1, Eq. 2), a positivity
+ * floor (Sec. 3.2) and a fixed number of RRRL iterations (Sec. 2.3,
+ * Eq. 9-12).
+ *
+ * General conventions for every entry point:
+ *   - Images are float32, row-major, H rows x W columns, with a row pitch of
+ *     `ld` elements (ld >= W).  Pixel (i, j) is at ptr[i*ld + j].
+ *   - All image, tap, workspace and status pointers are DEVICE pointers owned
+ *     by the caller.  The library allocates nothing; scratch space is the
+ *     caller's workspace `ws` of `ws_bytes` bytes (see db_workspace_bytes),
+ *     which must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously; no entry point synchronises the device.
+ *   - Argument errors are returned synchronously as a db_status and nothing is
+ *     enqueued.  Errors found on the device (invalid taps, non-finite values,
+ *     a bounded wait that ran out) are OR-ed as DB_FLAG_* bits into the int32
+ *     word `*dev_status` (may be NULL to skip checking), which the caller
+ *     zeroes before and reads after synchronising; db_status_from_flags maps
+ *     it to a db_status.
+ *   - A PSF tap (a, b) sits at offset (dy, dx) = (a - kh/2, b - kw/2) (integer
+ *     division) from the origin.  Convolution is
+ *       (u*h)(i,j)  = sum_ab h[a][b] u(i-dy, j-dx),
+ *     correlation with the adjoint h*(x) = h(-x) (Sec. 2) is
+ *       (v*h*)(i,j) = sum_ab h[a][b] v(i+dy, j+dx).
+ *     Spatial-mode sums continue the image constantly across the boundary
+ *     (clamped indices), Fourier-mode sums periodically (Sec. 4.2).
+ */
+#ifndef LIBDEBLUR_H
+#define LIBDEBLUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DB_OK = 0,
+  DB_ERR_ARG = 1,          /* NULL pointer, bad enum, non-positive size      */
+  DB_ERR_SHAPE = 2,        /* H, W or ld out of the supported range          */
+  DB_ERR_PSF = 3,          /* PSF extent invalid or larger than the image    */
+  DB_ERR_WORKSPACE = 4,    /* ws NULL, misaligned or smaller than required   */
+  DB_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement    */
+  DB_ERR_CUDA = 6,         /* a kernel launch or async copy failed           */
+  DB_ERR_TIMEOUT = 7,      /* device flag: a bounded wait gave up            */
+  DB_ERR_NONFINITE = 8,    /* device flag: NaN/Inf produced or consumed      */
+  DB_ERR_TAPS = 9          /* device flag: negative/non-finite taps, sum<=0,
+                              or a "box" PSF whose taps are not uniform      */
+} db_status;
+
+/* Device status bits (OR-ed into *dev_status). */
+#define DB_FLAG_TAPS      0x1
+#define DB_FLAG_NONFINITE 0x2
+#define DB_FLAG_TIMEOUT   0x4
+#define DB_FLAG_BOX       0x8
+
+typedef enum {
+  DB_PSF_GENERAL = 0,  /* any non-negative kh x kw taps                      */
+  DB_PSF_BOX = 1       /* uniform motion along a coordinate axis: kh == 1 or
+                          kw == 1 and all taps equal (Sec. 4.3, "Uniform
+                          linear motion"); enables the running-sum blur     */
+} db_psf_kind;
+
+typedef enum {
+  DB_CONV_CLAMP = 0,    /* spatial sums, constant continuation (Sec. 4.2)   */
+  DB_CONV_PERIODIC = 1  /* Fourier-domain sums, periodic continuation        */
+} db_conv_mode;
+
+typedef struct {
+  int kh, kw;          /* PSF extent, 1..255 each, kh <= H and kw <= W       */
+  int kind;            /* db_psf_kind                                        */
+  const float* taps;   /* DEVICE, kh*kw floats row-major; used as given (the
+                          caller normalises), must be >= 0 with a positive sum */
+} db_psf;
+
+typedef struct {
+  float K;          /* Wiener noise weight, > 0 (Eq. 2)                      */
+  float alpha;      /* regulariser weight, >= 0 (Eq. 9)                      */
+  float eps_phi;    /* robust data penaliser: phi'(z) = eps/sqrt(z+eps^2)    */
+  float eps_psi;    /* TV diffusivity: psi'(z) = 1/sqrt(z+eps^2)             */
+  float pos_floor;  /* delta > 0: f and the Wiener output are floored at it  */
+  int phi_robust;   /* 1: robust phi' above, 0: phi' == 1 (plain RL data term) */
+  int psi_tv;       /* 1: TV psi' above, 0: psi' == 1 (linear diffusion)     */
+  int conv;         /* db_conv_mode used by the RRRL blur/correlation        */
+} db_params;
+
+/* Bytes of workspace the calls below need for one image of H x W with this
+ * PSF and parameters (the maximum over db_wiener, db_rrl_iterate and
+ * db_deblur).  Returns 0 for invalid arguments. */
+size_t db_workspace_bytes(int H, int W, const db_psf* psf, const db_params* p);
+
+/* Wiener initialisation (Sec. 2.1, Eq. 2, and Sec. 3.2):
+ *   f0 = max(f, delta);  u0 = max( Re IDFT( DFT(f0) conj(h^) / (|h^|^2 + K) ), delta )
+ * with the DFT at the native image size and h^ the DFT of the PSF wrapped
+ * with its origin at (0,0).  A PSF on one row (kh == 1) or one column
+ * (kw == 1) is filtered with 1D transforms along that axis, which is the same
+ * operator (Sec. 4.3, "Non-uniform linear motion").  f and u0 may not alias.
+ * Supported sizes: H, W in 1..4096 (power-of-two extents use radix-2^k
+ * transforms, other extents Bluestein's chirp-z form of the same DFT). */
+db_status db_wiener(const float* f, float* u0, int H, int W, int ld,
+                    const db_psf* psf, const db_params* p,
+                    void* ws, size_t ws_bytes, int* dev_status, void* stream);
+
+/* `iters` RRRL iterations in place on u (Sec. 2.3, Eq. 9-12):
+ *   b = u*h;  W = phi'(r_f(b)) with r_f(s) = s - f - f ln(s/f)  (Eq. 7, 10)
+ *   A = (W f/b)*h*;  B = W*h*;  D = div(psi'(|grad u|^2) grad u)  (Eq. 11)
+ *   u <- u (A + alpha [D]+) / (B - alpha [D]-),   [z]+- = (z +- |z|)/2 (Eq. 12)
+ * with f0 = max(f, delta) in place of f.  D uses central differences and zero
+ * flux across the image boundary (Sec. 4.1).  u must be > 0 on entry (the
+ * Wiener output of db_wiener is).  If `ckpt` is not NULL, u before iteration
+ * k is also written to ckpt + (k/ckpt_every)*H*W (packed, pitch W) for every
+ * k that is a multiple of ckpt_every (k = 0 included); ckpt holds
+ * (iters-1)/ckpt_every + 1 images. */
+db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld,
+                         const db_psf* psf, const db_params* p, int iters,
+                         float* ckpt, int ckpt_every,
+                         void* ws, size_t ws_bytes, int* dev_status, void* stream);
+
+/* db_wiener followed by db_rrl_iterate: the whole WR3L pipeline (Sec. 3.2). */
+db_status db_deblur(const float* f, float* u, int H, int W, int ld,
+                    const db_psf* psf, const db_params* p, int iters,
+                    void* ws, size_t ws_bytes, int* dev_status, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* db_status_string(db_status s);
+
+/* Map an OR of DB_FLAG_* bits to the most specific db_status (DB_OK if 0). */
+db_status db_status_from_flags(int flags);
+
+/* Library version string, e.g. "libdeblur 0.1 sm_103a". */
+const char* db_version(void);
+
+/* Number of CUDA kernels this library has enqueued in this process so far
+ * (host-side counter; a CUDA-graph replay of captured calls adds nothing). */
+long long db_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBDEBLUR_H */

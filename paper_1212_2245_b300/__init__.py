@@ -1,0 +1,161 @@
+"""libdeblur Python binding: argument marshalling over the C ABI.
+
+Every step of the Wiener + RRRL pipeline runs in the CUDA library
+(`libdeblur.so`, built in-tree for sm_103a); this module only checks tensor
+layouts, passes device pointers, sizes and the current CUDA stream, and turns
+status codes into exceptions.  PyTorch supplies device memory and streams.
+There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from .params import Params
+
+__all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
+           "deblur", "version"]
+
+
+class DeblurError(RuntimeError):
+    pass
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        msg = _lib.load().db_status_string(code).decode()
+        raise DeblurError(f"{what}: {msg} (status {code})")
+
+
+def _db_params(p: Params) -> _lib.DbParams:
+    conv = {"clamp": _lib.DB_CONV_CLAMP, "periodic": _lib.DB_CONV_PERIODIC}[p.conv]
+    return _lib.DbParams(float(p.K), float(p.alpha), float(p.eps_phi), float(p.eps_psi),
+                         float(p.pos_floor), int(p.phi_robust), int(p.psi_tv), conv)
+
+
+def _kind(kind: str) -> int:
+    return _lib.DB_PSF_BOX if kind.startswith("box") else _lib.DB_PSF_GENERAL
+
+
+def _db_psf(taps: torch.Tensor, kind: str) -> _lib.DbPsf:
+    if not (taps.is_cuda and taps.dtype == torch.float32 and taps.dim() == 2 and taps.is_contiguous()):
+        raise ValueError("taps must be a contiguous 2D float32 CUDA tensor")
+    return _lib.DbPsf(taps.shape[0], taps.shape[1], _kind(kind), taps.data_ptr())
+
+
+def _image(x: torch.Tensor, name: str):
+    if not (x.is_cuda and x.dtype == torch.float32 and x.dim() == 2 and x.stride(1) == 1):
+        raise ValueError(f"{name} must be a 2D float32 CUDA tensor with unit column stride")
+    return x.shape[0], x.shape[1], x.stride(0)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def workspace_bytes(H: int, W: int, kh: int, kw: int, params: Params) -> int:
+    lib = _lib.load()
+    psf = _lib.DbPsf(kh, kw, 0, None)
+    p = _db_params(params)
+    n = lib.db_workspace_bytes(H, W, ctypes.byref(psf), ctypes.byref(p))
+    if n == 0:
+        raise DeblurError("invalid size or parameters for workspace query")
+    return int(n)
+
+
+class Workspace:
+    """Caller-owned device scratch (256-byte aligned) and status word."""
+
+    def __init__(self, nbytes: int, device=None):
+        device = device or torch.device("cuda", torch.cuda.current_device())
+        self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = self.buf.data_ptr() + off
+        self.nbytes = nbytes
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    @classmethod
+    def for_image(cls, H, W, kh, kw, params):
+        return cls(workspace_bytes(H, W, kh, kw, params))
+
+    def reset_status(self):
+        self.status.zero_()
+
+    def raise_on_flags(self, what: str):
+        flags = int(self.status.item())
+        if flags:
+            code = _lib.load().db_status_from_flags(flags)
+            _check(code, f"{what} (device flags 0x{flags:x})")
+
+
+def _ws(ws, H, W, taps, params):
+    return ws if ws is not None else Workspace.for_image(H, W, taps.shape[0], taps.shape[1], params)
+
+
+def wiener(f: torch.Tensor, taps: torch.Tensor, params: Params, *, kind: str = "general",
+           out: torch.Tensor | None = None, ws: Workspace | None = None, check: bool = True):
+    """Wiener initialisation u0 = max(Wiener(max(f, delta)), delta) (Eq. 2)."""
+    H, W, ld = _image(f, "f")
+    u0 = out if out is not None else torch.empty_like(f)
+    if _image(u0, "out")[2] != ld or u0.shape != f.shape:
+        raise ValueError("out must match f's shape and row stride")
+    ws = _ws(ws, H, W, taps, params)
+    if check:
+        ws.reset_status()
+    lib = _lib.load()
+    psf, p = _db_psf(taps, kind), _db_params(params)
+    _check(lib.db_wiener(f.data_ptr(), u0.data_ptr(), H, W, ld, ctypes.byref(psf), ctypes.byref(p),
+                         ws.ptr, ws.nbytes, ws.status.data_ptr(), _stream()), "db_wiener")
+    if check:
+        ws.raise_on_flags("db_wiener")
+    return u0
+
+
+def rrl_iterate(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *,
+                kind: str = "general", ckpt: torch.Tensor | None = None, ckpt_every: int = 0,
+                ws: Workspace | None = None, check: bool = True):
+    """`iters` RRRL iterations in place on u (Eq. 9-12)."""
+    H, W, ld = _image(f, "f")
+    if _image(u, "u")[2] != ld or u.shape != f.shape:
+        raise ValueError("u must match f's shape and row stride")
+    ws = _ws(ws, H, W, taps, params)
+    if check:
+        ws.reset_status()
+    ck = 0
+    if ckpt is not None:
+        nck = (iters - 1) // ckpt_every + 1 if iters > 0 else 0
+        if not (ckpt.is_cuda and ckpt.dtype == torch.float32 and ckpt.is_contiguous()
+                and ckpt.numel() >= nck * H * W):
+            raise ValueError("ckpt must be a contiguous float32 CUDA tensor of (iters-1)//every+1 images")
+        ck = ckpt.data_ptr()
+    lib = _lib.load()
+    psf, p = _db_psf(taps, kind), _db_params(params)
+    _check(lib.db_rrl_iterate(f.data_ptr(), u.data_ptr(), H, W, ld, ctypes.byref(psf), ctypes.byref(p),
+                              int(iters), ck, int(ckpt_every), ws.ptr, ws.nbytes, ws.status.data_ptr(),
+                              _stream()), "db_rrl_iterate")
+    if check:
+        ws.raise_on_flags("db_rrl_iterate")
+    return u
+
+
+def deblur(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, kind: str = "general",
+           out: torch.Tensor | None = None, ws: Workspace | None = None, check: bool = True):
+    """Whole WR3L pipeline: Wiener, floor, `iters` RRRL iterations (Sec. 3.2)."""
+    H, W, ld = _image(f, "f")
+    u = out if out is not None else torch.empty_like(f)
+    ws = _ws(ws, H, W, taps, params)
+    if check:
+        ws.reset_status()
+    lib = _lib.load()
+    psf, p = _db_psf(taps, kind), _db_params(params)
+    _check(lib.db_deblur(f.data_ptr(), u.data_ptr(), H, W, ld, ctypes.byref(psf), ctypes.byref(p),
+                         int(iters), ws.ptr, ws.nbytes, ws.status.data_ptr(), _stream()), "db_deblur")
+    if check:
+        ws.raise_on_flags("db_deblur")
+    return u
+
+
+def version() -> str:
+    return _lib.load().db_version().decode()

@@ -1,0 +1,194 @@
+// C ABI of libdeblur: argument validation, workspace layout and dispatch.
+// The operations themselves are documented in include/libdeblur.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+#include <atomic>
+
+namespace db {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
+  (void)conv;
+  WsLayout L = {};
+  size_t off = 0;
+  L.taps = off;  off += align256((size_t)kh * kw * sizeof(Tap));
+  L.ntaps = off; off += 256;
+  L.utmp = off;  off += align256((size_t)H * W * sizeof(float));
+  size_t spec_elems, work_elems;
+  if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
+  else if (kw == 1) { spec_elems = (size_t)H; work_elems = 0; }
+  else { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
+  L.spec = off;  off += align256(spec_elems * sizeof(float2));
+  L.work = off;  off += align256(work_elems * sizeof(float2));
+  L.total = off;
+  return L;
+}
+
+static db_status check_image(const void* a, const void* b, int H, int W, int ld) {
+  if (!a || !b) return DB_ERR_ARG;
+  if (H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ld < W) return DB_ERR_SHAPE;
+  return DB_OK;
+}
+
+static db_status check_psf(const db_psf* psf, int H, int W) {
+  if (!psf || !psf->taps) return DB_ERR_ARG;
+  if (psf->kh < 1 || psf->kw < 1 || psf->kh > kMaxTapSide || psf->kw > kMaxTapSide) return DB_ERR_PSF;
+  if (psf->kh > H || psf->kw > W) return DB_ERR_PSF;
+  if (psf->kind != DB_PSF_GENERAL && psf->kind != DB_PSF_BOX) return DB_ERR_ARG;
+  if (psf->kind == DB_PSF_BOX && psf->kh != 1 && psf->kw != 1) return DB_ERR_PSF;
+  return DB_OK;
+}
+
+static db_status check_params(const db_params* p) {
+  if (!p) return DB_ERR_ARG;
+  if (!(p->K > 0.f) || !(p->alpha >= 0.f) || !(p->eps_phi > 0.f) || !(p->eps_psi > 0.f) ||
+      !(p->pos_floor > 0.f))
+    return DB_ERR_ARG;
+  if (p->conv != DB_CONV_CLAMP && p->conv != DB_CONV_PERIODIC) return DB_ERR_ARG;
+  if ((p->phi_robust != 0 && p->phi_robust != 1) || (p->psi_tv != 0 && p->psi_tv != 1)) return DB_ERR_ARG;
+  return DB_OK;
+}
+
+static db_status check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (!ws || ((uintptr_t)ws & 255u) != 0) return DB_ERR_WORKSPACE;
+  if (ws_bytes < need) return DB_ERR_WORKSPACE;
+  return DB_OK;
+}
+
+static bool wiener_supported(int H, int W, int kh, int kw) {
+  if (kh == 1) return is_pow2(W);
+  if (kw == 1) return is_pow2(H);
+  return is_pow2(H) && is_pow2(W);
+}
+
+static RrlParams to_rrl(const db_params* p) {
+  RrlParams r;
+  r.alpha = p->alpha; r.eps_phi = p->eps_phi; r.eps_psi = p->eps_psi; r.floor = p->pos_floor;
+  r.phi_robust = p->phi_robust; r.psi_tv = p->psi_tv;
+  return r;
+}
+
+}  // namespace db
+
+using namespace db;
+
+extern "C" {
+
+size_t db_workspace_bytes(int H, int W, const db_psf* psf, const db_params* p) {
+  if (H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || !psf) return 0;
+  if (psf->kh < 1 || psf->kw < 1 || psf->kh > kMaxTapSide || psf->kw > kMaxTapSide) return 0;
+  if (psf->kh > H || psf->kw > W || check_params(p) != DB_OK) return 0;
+  return ws_layout(H, W, psf->kh, psf->kw, p->conv).total;
+}
+
+db_status db_wiener(const float* f, float* u0, int H, int W, int ld, const db_psf* psf,
+                    const db_params* p, void* ws, size_t ws_bytes, int* dev_status, void* stream) {
+  db_status st;
+  if ((st = check_image(f, u0, H, W, ld)) != DB_OK) return st;
+  if ((st = check_psf(psf, H, W)) != DB_OK) return st;
+  if ((st = check_params(p)) != DB_OK) return st;
+  if (f == u0) return DB_ERR_ARG;
+  const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != DB_OK) return st;
+  if (!wiener_supported(H, W, psf->kh, psf->kw)) return DB_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  if (launch_compact_taps(psf->taps, psf->kh, psf->kw, psf->kind, (Tap*)(base + L.taps),
+                          (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  if (run_wiener(f, u0, H, W, ld, psf->taps, psf->kh, psf->kw, p->K, p->pos_floor, ws, L,
+                 dev_status, s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  return DB_OK;
+}
+
+db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const db_psf* psf,
+                         const db_params* p, int iters, float* ckpt, int ckpt_every, void* ws,
+                         size_t ws_bytes, int* dev_status, void* stream) {
+  db_status st;
+  if ((st = check_image(f, u, H, W, ld)) != DB_OK) return st;
+  if ((st = check_psf(psf, H, W)) != DB_OK) return st;
+  if ((st = check_params(p)) != DB_OK) return st;
+  if (iters < 0) return DB_ERR_ARG;
+  if (ckpt && ckpt_every < 1) return DB_ERR_ARG;
+  if (f == u) return DB_ERR_ARG;
+  const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != DB_OK) return st;
+  if (p->conv != DB_CONV_CLAMP) return DB_ERR_UNSUPPORTED;
+  if (iters == 0) return DB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  Tap* taps = (Tap*)(base + L.taps);
+  int* ntaps = (int*)(base + L.ntaps);
+  float* tmp = (float*)(base + L.utmp);
+  if (launch_compact_taps(psf->taps, psf->kh, psf->kw, psf->kind, taps, ntaps, dev_status, s) !=
+      cudaSuccess)
+    return DB_ERR_CUDA;
+  const RrlParams rp = to_rrl(p);
+  const float* src = u;
+  int ld_src = ld;
+  for (int k = 0; k < iters; ++k) {
+    if (ckpt && k % ckpt_every == 0) {
+      float* dst = ckpt + (size_t)(k / ckpt_every) * H * W;
+      if (cudaMemcpy2DAsync(dst, (size_t)W * sizeof(float), src, (size_t)ld_src * sizeof(float),
+                            (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return DB_ERR_CUDA;
+    }
+    float* dst = (k % 2 == 0) ? tmp : u;
+    const int ld_dst = (k % 2 == 0) ? W : ld;
+    if (launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, taps, ntaps, psf->kh, psf->kw,
+                           rp, dev_status, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    src = dst;
+    ld_src = ld_dst;
+  }
+  if (src != u) {
+    if (cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), src, (size_t)W * sizeof(float),
+                          (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+  }
+  return DB_OK;
+}
+
+db_status db_deblur(const float* f, float* u, int H, int W, int ld, const db_psf* psf,
+                    const db_params* p, int iters, void* ws, size_t ws_bytes, int* dev_status,
+                    void* stream) {
+  db_status st = db_wiener(f, u, H, W, ld, psf, p, ws, ws_bytes, dev_status, stream);
+  if (st != DB_OK) return st;
+  return db_rrl_iterate(f, u, H, W, ld, psf, p, iters, nullptr, 0, ws, ws_bytes, dev_status, stream);
+}
+
+const char* db_status_string(db_status s) {
+  switch (s) {
+    case DB_OK: return "ok";
+    case DB_ERR_ARG: return "invalid argument";
+    case DB_ERR_SHAPE: return "image shape out of range";
+    case DB_ERR_PSF: return "invalid PSF extent";
+    case DB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case DB_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DB_ERR_CUDA: return "CUDA launch or copy failed";
+    case DB_ERR_TIMEOUT: return "bounded device wait gave up";
+    case DB_ERR_NONFINITE: return "non-finite value produced";
+    case DB_ERR_TAPS: return "invalid PSF taps";
+  }
+  return "unknown status";
+}
+
+db_status db_status_from_flags(int flags) {
+  if (flags == 0) return DB_OK;
+  if (flags & DB_FLAG_TIMEOUT) return DB_ERR_TIMEOUT;
+  if (flags & (DB_FLAG_TAPS | DB_FLAG_BOX)) return DB_ERR_TAPS;
+  if (flags & DB_FLAG_NONFINITE) return DB_ERR_NONFINITE;
+  return DB_ERR_ARG;
+}
+
+const char* db_version(void) { return "libdeblur 0.1 sm_103a"; }
+
+long long db_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Shared-memory FP32 FFT building blocks (power-of-two lengths).
+//
+// The Wiener filter (Sec. 2.1, Eq. 2) and the Fourier-mode blur/correlation
+// (Sec. 4.1, "Fourier transform"; Sec. 4.3) only ever use a transform to
+// multiply by a spectrum and transform back.  The forward transform is
+// therefore a decimation-in-frequency (DIF) sweep that leaves its output in
+// bit-reversed order, and the inverse a decimation-in-time (DIT) sweep that
+// takes bit-reversed input and returns natural order: no reordering pass is
+// ever needed, provided the spectrum multiplied in between went through the
+// same forward sweep (it does: PSF spectra are computed with these routines).
+//
+// Pairs of radix-2 stages are fused into one radix-2^2 butterfly held in
+// registers, halving the shared-memory sweeps.  Twiddles come from a table
+// tw[k] = exp(-2 pi i k / NT) built once per CTA with sincospif (exact
+// arguments for power-of-two NT).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace db {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -i
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+// multiply by +i
+__device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a.x); }
+
+// tw[k] = exp(-2 pi i k / NT), k in [0, NT)
+__device__ inline void fft_build_twiddles(float2* tw, int NT) {
+  for (int k = threadIdx.x; k < NT; k += blockDim.x) {
+    float s, c;
+    sincospif(-2.0f * (float)k / (float)NT, &s, &c);
+    tw[k] = make_float2(c, s);
+  }
+}
+
+// Forward DIF transform of `nseq` sequences of length N = 2^logN held in
+// shared memory: element k of sequence q is x[q*ss + k*es].  Output is in
+// bit-reversed order.  `seq_fast` chooses the thread->work mapping: true when
+// sequences are interleaved element-wise (columns), false when each sequence
+// is contiguous (rows).  tw is a table for length NT = N << tw_shift.
+// Ends with __syncthreads().
+__device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, const float2* tw,
+                               int tw_shift, bool seq_fast) {
+  const int N = 1 << logN;
+  const int nb = N >> 2;  // radix-4 butterflies per sequence
+  int logLen = logN;
+  while (logLen >= 2) {
+    const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
+    const int tstep = 1 << (logN - logLen + tw_shift);  // NT / len
+    const int items = nseq * nb;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      int q, b;
+      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+      const int blk = b >> logm, j = b & (m - 1);
+      float2* p = x + q * ss + (blk * len + j) * es;
+      const int sm = m * es;
+      float2 x0 = p[0], x1 = p[sm], x2 = p[2 * sm], x3 = p[3 * sm];
+      const float2 w1 = tw[j * tstep], w2 = tw[2 * j * tstep];
+      float2 y0 = cadd(x0, x2), y2 = cmul(csub(x0, x2), w1);
+      float2 y1 = cadd(x1, x3), y3 = cmul_mi(cmul(csub(x1, x3), w1));
+      p[0] = cadd(y0, y1);
+      p[sm] = cmul(csub(y0, y1), w2);
+      p[2 * sm] = cadd(y2, y3);
+      p[3 * sm] = cmul(csub(y2, y3), w2);
+    }
+    __syncthreads();
+    logLen -= 2;
+  }
+  if (logLen == 1) {  // last radix-2 stage, blocks of length 2, twiddle 1
+    const int items = nseq * (N >> 1);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      int q, b;
+      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / (N >> 1); b = it - q * (N >> 1); }
+      float2* p = x + q * ss + (2 * b) * es;
+      float2 a = p[0], c = p[es];
+      p[0] = cadd(a, c);
+      p[es] = csub(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse DIT transform (unnormalised: returns N times the inverse DFT),
+// taking bit-reversed input to natural order.  Exactly mirrors fft_dif.
+// Ends with __syncthreads().
+__device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss, const float2* tw,
+                                   int tw_shift, bool seq_fast) {
+  const int N = 1 << logN;
+  const int nb = N >> 2;
+  int logLen = (logN & 1) ? 1 : 0;
+  if (logLen == 1) {
+    const int items = nseq * (N >> 1);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      int q, b;
+      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / (N >> 1); b = it - q * (N >> 1); }
+      float2* p = x + q * ss + (2 * b) * es;
+      float2 a = p[0], c = p[es];
+      p[0] = cadd(a, c);
+      p[es] = csub(a, c);
+    }
+    __syncthreads();
+  }
+  for (logLen += 2; logLen <= logN; logLen += 2) {
+    const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
+    const int tstep = 1 << (logN - logLen + tw_shift);
+    const int items = nseq * nb;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      int q, b;
+      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+      const int blk = b >> logm, j = b & (m - 1);
+      float2* p = x + q * ss + (blk * len + j) * es;
+      const int sm = m * es;
+      float2 z0 = p[0], z1 = p[sm], z2 = p[2 * sm], z3 = p[3 * sm];
+      const float2 w1 = tw[j * tstep], w2 = tw[2 * j * tstep];
+      float2 t1 = cmulc(z1, w2), t3 = cmulc(z3, w2);
+      float2 y0 = cadd(z0, t1), y1 = csub(z0, t1);
+      float2 y2 = cadd(z2, t3), y3 = csub(z2, t3);
+      float2 u2 = cmulc(y2, w1), u3 = cmul_pi(cmulc(y3, w1));
+      p[0] = cadd(y0, u2);
+      p[2 * sm] = csub(y0, u2);
+      p[sm] = cadd(y1, u3);
+      p[3 * sm] = csub(y1, u3);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace db

@@ -23,6 +23,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.signal
 
+from .params import Params
+
 SEED_BASE = 12122245
 
 
@@ -166,18 +168,6 @@ def degrade(g: np.ndarray, h: np.ndarray, sigma: float, rng: np.random.Generator
 # --------------------------------------------------------------------------
 # workloads
 # --------------------------------------------------------------------------
-@dataclass
-class Params:
-    K: float = 0.006          # Wiener noise weight (Eq. 2)
-    alpha: float = 0.003      # regularisation weight (Eq. 9)
-    eps_phi: float = 1.0      # robust data-term penaliser scale
-    eps_psi: float = 10.0     # TV regulariser scale (grey levels; stability reading)
-    pos_floor: float = 0.1    # positivity floor for f and the Wiener output
-    phi_robust: int = 1       # 1: regularised-L1 phi', 0: phi' == 1
-    psi_tv: int = 1           # 1: TV psi', 0: psi' == 1
-    conv: str = "clamp"       # "clamp" (spatial) or "periodic" (Fourier)
-
-
 @dataclass
 class Case:
     name: str

@@ -1,0 +1,142 @@
+"""GPU parity: the CUDA path against the FP64 oracle on the same seeded
+inputs.  Bar: max-abs <= 1e-3 and RMS <= 1e-4 grey levels (0-255 scale)
+after the stated iteration count."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1212_2245_b300 import synth
+from paper_1212_2245_b300.params import Params
+
+pytestmark = pytest.mark.gpu
+
+MAX_ABS, RMS = 1e-3, 1e-4
+
+
+def err(gpu, ref):
+    d = (gpu.double().cpu() - torch.as_tensor(ref, dtype=torch.float64)).abs()
+    return float(d.max()), float(d.pow(2).mean().sqrt())
+
+
+def assert_close(gpu, ref, what, max_abs=MAX_ABS, rms=RMS):
+    m, r = err(gpu, ref)
+    assert m <= max_abs and r <= rms, f"{what}: max-abs {m:.3e} rms {r:.3e}"
+    return m, r
+
+
+def cuda(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32).cuda()
+
+
+def oracle_pipeline(case):
+    return oracle.ops.wr3l(case.f, case.h, case.params, case.iters)
+
+
+@pytest.mark.parametrize("maker", [synth.case_box256, synth.case_line1024])
+def test_full_pipeline_configs(lib, maker):
+    case = maker()
+    f, h = cuda(case.f), cuda(case.h)
+    u0_ref, u_ref = oracle_pipeline(case)
+    u0 = lib.wiener(f, h, case.params, kind=case.psf_kind)
+    assert_close(u0, u0_ref, f"{case.name} Wiener")
+    u = lib.rrl_iterate(f, u0.clone(), h, case.params, case.iters, kind=case.psf_kind)
+    assert_close(u, u_ref, f"{case.name} WR3L")
+    ud = lib.deblur(f, h, case.params, case.iters, kind=case.psf_kind)
+    assert torch.equal(ud, u)
+
+
+def _iterate_case(H, W, h, iters, params, kind="general", seed=0, ld=None):
+    rng = np.random.default_rng(seed)
+    g = synth.scene(H, W, rng).astype(np.float32)
+    f = synth.degrade(g, h, 2.0, rng, salt_pepper=0.01)
+    u0 = np.maximum(synth.blur_replicate(f, np.ones((1, 1))), 0.1).astype(np.float32)  # any positive start
+    return f, u0
+
+
+@pytest.mark.parametrize("H,W", [(77, 131), (1, 1), (3, 200), (200, 3), (65, 64), (33, 97)])
+@pytest.mark.parametrize("psf", ["line", "box", "gauss", "col", "identity"])
+def test_iterations_ragged_shapes(lib, H, W, psf):
+    rng = np.random.default_rng(H * 1000 + W)
+    h = {"line": synth.line_psf(9, 30.0, 10.0), "box": synth.box_psf(7), "col": synth.raised_cosine_1d(5, "col"),
+         "gauss": synth.gaussian_mixture_psf(7, rng), "identity": np.ones((1, 1), np.float32)}[psf]
+    if h.shape[0] > H or h.shape[1] > W:
+        pytest.skip("PSF larger than image")
+    kind = "box" if psf == "box" else "general"
+    p = Params()
+    iters = 5
+    f, u0 = _iterate_case(H, W, h, iters, p)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, iters)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, iters, kind=kind)
+    assert_close(u, ref, f"{psf} {H}x{W}")
+
+
+def test_pitched_rows_and_odd_iteration_count(lib):
+    H, W, ld = 70, 90, 128
+    h = synth.line_psf(11, 30.0, 12.0)
+    p = Params(alpha=0.01)
+    f, u0 = _iterate_case(H, W, h, 3, p)
+    fp = torch.zeros(H, ld, device="cuda"); fp[:, :W] = cuda(f)
+    up = torch.full((H, ld), -7.0, device="cuda"); up[:, :W] = cuda(u0)
+    lib.rrl_iterate(fp[:, :W], up[:, :W], cuda(h), p, 3)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 3)
+    assert_close(up[:, :W], ref, "pitched")
+    assert torch.all(up[:, W:] == -7.0), "wrote outside the image"
+
+
+@pytest.mark.parametrize("variant", [dict(phi_robust=0), dict(psi_tv=0, alpha=1e-4), dict(alpha=0.0),
+                                     dict(eps_phi=0.5, eps_psi=3.0, alpha=0.002)])
+def test_parameter_variants(lib, variant):
+    H, W = 96, 128
+    h = synth.line_psf(13, 45.0, 14.0)
+    p = Params(**variant)
+    f, u0 = _iterate_case(H, W, h, 6, p, seed=3)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 6)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6)
+    assert_close(u, ref, str(variant))
+
+
+@pytest.mark.parametrize("H,W,shape", [(128, 256, (1, 15)), (256, 128, (9, 1)), (64, 512, (5, 7)),
+                                       (512, 64, (17, 27)), (1, 256, (1, 31)), (256, 1, (7, 1)),
+                                       (2, 2, (1, 1)), (4096, 16, (3, 5))])
+def test_wiener_shapes(lib, H, W, shape):
+    rng = np.random.default_rng(H + W)
+    h = rng.uniform(0.1, 1.0, size=shape)
+    h = (h / h.sum()).astype(np.float32)
+    g = synth.scene(H, W, rng).astype(np.float32)
+    f = synth.degrade(g, h, 2.0, rng)
+    p = Params(K=0.01)
+    ref = oracle.positivity_floor(oracle.ops._wiener_any(oracle.condition_input(f, p.pos_floor),
+                                                         torch.tensor(h, dtype=torch.float64), p.K), p.pos_floor)
+    u0 = lib.wiener(cuda(f), cuda(h), p)
+    assert_close(u0, ref, f"wiener {H}x{W} psf {shape}")
+
+
+def test_checkpoints_hold_intermediate_iterates(lib):
+    H, W = 64, 96
+    h = synth.raised_cosine_1d(9)
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, 7, p)
+    ck = torch.empty(3, H, W, device="cuda")
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7, ckpt=ck, ckpt_every=3)
+    u3 = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 3)
+    u6 = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6)
+    assert torch.equal(ck[0], cuda(u0)) and torch.equal(ck[1], u3) and torch.equal(ck[2], u6)
+    assert torch.equal(lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7), u)
+
+
+def test_device_flags_for_bad_taps(lib):
+    f = cuda(np.full((32, 32), 100.0))
+    p = Params()
+    with pytest.raises(lib.DeblurError, match="taps"):
+        lib.rrl_iterate(f, f.clone(), cuda(np.array([[0.5, -0.1, 0.6]])), p, 1)
+    with pytest.raises(lib.DeblurError, match="taps"):
+        lib.rrl_iterate(f, f.clone(), cuda(np.array([[0.3, 0.4, 0.3]])), p, 1, kind="box")
+    with pytest.raises(lib.DeblurError):
+        lib.wiener(f, cuda(np.zeros((1, 3))), p)
+
+
+def test_unsupported_is_reported(lib):
+    f = cuda(np.full((32, 48), 100.0))
+    with pytest.raises(lib.DeblurError, match="unsupported"):
+        lib.wiener(f, cuda(np.ones((3, 3)) / 9), Params())
