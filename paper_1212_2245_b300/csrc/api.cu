@@ -16,7 +16,7 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   (void)conv;
   WsLayout L = {};
   size_t off = 0;
-  L.taps = off;  off += align256((size_t)kh * kw * sizeof(Tap));
+  L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
   L.ntaps = off; off += 256;
   L.utmp = off;  off += align256((size_t)H * W * sizeof(float));
   size_t spec_elems, work_elems;
@@ -98,7 +98,7 @@ db_status db_wiener(const float* f, float* u0, int H, int W, int ld, const db_ps
   if (!wiener_supported(H, W, psf->kh, psf->kw)) return DB_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   char* base = (char*)ws;
-  if (launch_compact_taps(psf->taps, psf->kh, psf->kw, psf->kind, (Tap*)(base + L.taps),
+  if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, (TapGroup*)(base + L.taps),
                           (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
     return DB_ERR_CUDA;
   if (run_wiener(f, u0, H, W, ld, psf->taps, psf->kh, psf->kw, p->K, p->pos_floor, ws, L,
@@ -123,10 +123,11 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
   if (iters == 0) return DB_OK;
   cudaStream_t s = (cudaStream_t)stream;
   char* base = (char*)ws;
-  Tap* taps = (Tap*)(base + L.taps);
-  int* ntaps = (int*)(base + L.ntaps);
+  TapGroup* groups = (TapGroup*)(base + L.taps);
+  int* ngroups = (int*)(base + L.ntaps);
   float* tmp = (float*)(base + L.utmp);
-  if (launch_compact_taps(psf->taps, psf->kh, psf->kw, psf->kind, taps, ntaps, dev_status, s) !=
+  if (rrl_spatial_smem(psf->kh, psf->kw) > 227 * 1024) return DB_ERR_UNSUPPORTED;
+  if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, groups, ngroups, dev_status, s) !=
       cudaSuccess)
     return DB_ERR_CUDA;
   const RrlParams rp = to_rrl(p);
@@ -141,7 +142,7 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
     }
     float* dst = (k % 2 == 0) ? tmp : u;
     const int ld_dst = (k % 2 == 0) ? W : ld;
-    if (launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, taps, ntaps, psf->kh, psf->kw,
+    if (launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, psf->kh, psf->kw,
                            rp, dev_status, s) != cudaSuccess)
       return DB_ERR_CUDA;
     src = dst;

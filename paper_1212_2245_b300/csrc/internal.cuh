@@ -7,12 +7,13 @@
 
 namespace db {
 
-// One non-zero PSF tap: weight and offset (dy, dx) from the origin.
-struct Tap {
-  float w;
-  int16_t dy, dx;
+// A run of up to three vertically adjacent taps of one PSF column: weights
+// w[k] at offsets (dy0 + k, dx) from the origin (unused weights are 0).
+struct TapGroup {
+  float w[3];
+  int16_t dy0, dx;
 };
-static_assert(sizeof(Tap) == 8, "Tap is 8 bytes");
+static_assert(sizeof(TapGroup) == 16, "TapGroup is 16 bytes");
 
 // RRRL parameters as the kernels consume them.
 struct RrlParams {
@@ -32,8 +33,8 @@ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 // Workspace layout for one image (offsets in bytes from ws).
 struct WsLayout {
-  size_t taps;     // Tap[kh*kw]
-  size_t ntaps;    // int
+  size_t taps;     // TapGroup[max_tap_groups(kh, kw)]
+  size_t ntaps;    // int: number of groups
   size_t utmp;     // float[H*W]  (RRRL ping-pong)
   size_t spec;     // float2[spec_elems]  (PSF spectrum)
   size_t work;     // float2[work_elems]  (FFT data)
@@ -42,15 +43,18 @@ struct WsLayout {
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv);
 
 // ---- launchers (return cudaError_t of the launch) --------------------------
-cudaError_t launch_compact_taps(const float* taps, int kh, int kw, int kind, Tap* out,
-                                int* nout, int* status, cudaStream_t s);
+int tap_group_height(int kh);
+int max_tap_groups(int kh, int kw);
+cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
+                                int* ngroups, int* status, cudaStream_t s);
+size_t rrl_spatial_smem(int kh, int kw);
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps,
                        int kh, int kw, float K, float floor_, void* ws, const WsLayout& L,
                        int* status, cudaStream_t s);
 
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
-                               int ldout, int H, int W, const Tap* taps, const int* ntaps,
+                               int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s);
 
 }  // namespace db

@@ -24,67 +24,92 @@
 namespace db {
 
 // ---------------------------------------------------------------------------
-// tap list: validate the dense taps and keep the non-zero ones (row-major)
+// tap preparation: validate the dense taps and build the tap groups.
+//
+// A group is a run of up to M vertically adjacent taps of one PSF column:
+// weights w[0..M-1] for offsets (dy0 + k, dx).  Within a column, a group
+// starts at the first non-zero tap not yet covered (moved up so that it ends
+// inside the PSF) and taps it covers twice get weight 0 in the later group.
+// Every non-zero tap lands in exactly one group, with its own weight.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_compact_taps(const float* __restrict__ taps, int kh, int kw,
-                                                      int kind, Tap* __restrict__ out,
-                                                      int* __restrict__ nout, int* status) {
-  __shared__ int warp_cnt[8];
+template <bool WRITE>
+__device__ int column_groups(const float* __restrict__ taps, int kh, int kw, int b, int M,
+                             TapGroup* out) {
+  const int cy = kh >> 1, cx = kw >> 1;
+  int covered = -1, n = 0;
+  while (true) {
+    int s = -1;
+    for (int r = covered + 1; r < kh; ++r)
+      if (__ldg(taps + r * kw + b) != 0.f) { s = r; break; }
+    if (s < 0) break;
+    const int st = min(s, kh - M);
+    if (WRITE) {
+      TapGroup g;
+      for (int k = 0; k < 3; ++k) {
+        const int r = st + k;
+        g.w[k] = (k < M && r > covered && r < kh) ? __ldg(taps + r * kw + b) : 0.f;
+      }
+      g.dy0 = (int16_t)(st - cy);
+      g.dx = (int16_t)(b - cx);
+      out[n] = g;
+    }
+    ++n;
+    covered = st + M - 1;
+  }
+  return n;
+}
+
+__global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ taps, int kh, int kw,
+                                                      int kind, int M, TapGroup* __restrict__ groups,
+                                                      int* __restrict__ ngroups, int* status) {
+  __shared__ int scan[256];
   __shared__ float warp_sum[8];
-  __shared__ int base;
   __shared__ int bad;
-  const int n = kh * kw, cy = kh >> 1, cx = kw >> 1;
+  const int n = kh * kw;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { base = 0; bad = 0; }
+  if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   const float t0 = __ldg(taps);
   float sum = 0.f;
-  for (int c0 = 0; c0 < n; c0 += 256) {
-    const int k = c0 + threadIdx.x;
-    float w = 0.f;
-    if (k < n) {
-      w = __ldg(taps + k);
-      if (!(w >= 0.f) || !isfinite(w)) atomicOr(&bad, DB_FLAG_TAPS);
-      if (kind == DB_PSF_BOX && w != t0) atomicOr(&bad, DB_FLAG_BOX);
-      sum += w;
-    }
-    const bool keep = (k < n) && (w != 0.f);
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) warp_cnt[wid] = __popc(m);
-    __syncthreads();
-    int off = base;
-    for (int i = 0; i < wid; ++i) off += warp_cnt[i];
-    off += __popc(m & ((1u << lane) - 1u));
-    if (keep) {
-      Tap t;
-      t.w = w;
-      t.dy = (int16_t)(k / kw - cy);
-      t.dx = (int16_t)(k % kw - cx);
-      out[off] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int i = 0; i < 8; ++i) tot += warp_cnt[i];
-      base += tot;
-    }
-    __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const float w = __ldg(taps + k);
+    if (!(w >= 0.f) || !isfinite(w)) atomicOr(&bad, DB_FLAG_TAPS);
+    if (kind == DB_PSF_BOX && w != t0) atomicOr(&bad, DB_FLAG_BOX);
+    sum += w;
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) warp_sum[wid] = sum;
+  // one thread per PSF column (kw <= 255): count, exclusive scan, write
+  const int b = threadIdx.x;
+  const int cnt = (b < kw) ? column_groups<false>(taps, kh, kw, b, M, nullptr) : 0;
+  scan[threadIdx.x] = cnt;
   __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int v = (threadIdx.x >= o) ? scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  if (b < kw) column_groups<true>(taps, kh, kw, b, M, groups + scan[threadIdx.x] - cnt);
   if (threadIdx.x == 0) {
     float s = 0.f;
     for (int i = 0; i < 8; ++i) s += warp_sum[i];
     if (!(s > 0.f)) bad |= DB_FLAG_TAPS;
-    *nout = base;
+    *ngroups = scan[255];
     if (bad && status) atomicOr(status, bad);
   }
 }
 
-cudaError_t launch_compact_taps(const float* taps, int kh, int kw, int kind, Tap* out, int* nout,
-                                int* status, cudaStream_t s) {
-  k_compact_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, out, nout, status);
+int tap_group_height(int kh) { return kh < 3 ? kh : 3; }
+
+int max_tap_groups(int kh, int kw) {
+  const int M = tap_group_height(kh);
+  return kw * ((kh + M - 1) / M);
+}
+
+cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
+                                int* ngroups, int* status, cudaStream_t s) {
+  k_prepare_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, tap_group_height(kh), groups, ngroups, status);
   count_launch();
   return cudaGetLastError();
 }
@@ -107,109 +132,205 @@ __device__ __forceinline__ float diffusivity(float gx, float gy, const RrlParams
 }
 
 // ---------------------------------------------------------------------------
-// fused iteration
+// fused iteration, register blocked.
+//
+// Each thread owns a vertical strip of R q-points (phase 1) or R outputs
+// (phase 2) in one column, so a tap group loaded once from shared memory
+// feeds M*R (phase 1) or 2*M*R (phase 2) FMAs from R+M-1 shared loads.
+// Lanes of a warp own adjacent columns: shared accesses are conflict-free.
+//
+// Geometry (virtual rows/cols may lie outside the image):
+//   q tile : rows i0-cy .. i0-cy+QHp-1, cols j0-cx .. j0-cx+QW-1
+//   u tile : rows i0-Ry .. i0-Ry+UH-1,  cols j0-Rx .. j0-Rx+US-1
+// u is staged as u(clamp(.)); q is first formed at every virtual position
+// from the clamped u and then, at virtual positions outside the image,
+// replaced by q at the clamped position.
 // ---------------------------------------------------------------------------
-template <int TH, int TW>
+template <int TH, int TW, int R, int M>
 __global__ void __launch_bounds__(256) k_rrl_spatial(const float* __restrict__ f, int ldf,
                                                      const float* __restrict__ uin, int ldin,
                                                      float* __restrict__ uout, int ldout, int H, int W,
-                                                     const Tap* __restrict__ taps_g,
-                                                     const int* __restrict__ ntaps_g, int kh, int kw,
-                                                     RrlParams p, int* status) {
+                                                     const TapGroup* __restrict__ groups_g,
+                                                     const int* __restrict__ ngroups_g, int kh, int kw,
+                                                     int ng_max, RrlParams p, int* status) {
+  static_assert(TH % R == 0, "output strips must tile TH");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cy = kh >> 1, cx = kw >> 1;
   const int Ry = max(kh - 1, 2), Rx = max(kw - 1, 2);
-  const int US = TW + 2 * Rx;             // u tile row stride
-  const int UH = TH + 2 * Ry;
-  const int QW = TW + kw - 1, QH = TH + kh - 1;
-  const int ntaps = *ntaps_g;
-  Tap* taps = (Tap*)smem_raw;
-  float* us = (float*)(smem_raw + (size_t)kh * kw * sizeof(Tap));
+  const int QH = TH + kh - 1, QW = TW + kw - 1;
+  const int NQS = (QH + R - 1) / R, QHp = NQS * R;
+  const int UH = Ry + max(QHp, TH + 2), US = TW + 2 * Rx;
+  const int ng = *ngroups_g;
+  float4* gu = (float4*)smem_raw;
+  float4* gq = gu + ng_max;
+  float* us = (float*)(gq + ng_max);
   float2* qs = (float2*)(us + ((UH * US + 1) & ~1));
   const int i0 = blockIdx.y * TH, j0 = blockIdx.x * TW;
 
-  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) taps[t] = taps_g[t];
-  // u(clamp) over the halo region
-  for (int idx = threadIdx.x; idx < UH * US; idx += blockDim.x) {
-    const int r = idx / US, c = idx - r * US;
+  // tap groups with shared-memory offsets for both phases
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const TapGroup t = groups_g[g];
+    const int offu = (Ry - cy - t.dy0 - (M - 1)) * US + (Rx - cx - t.dx);
+    const int offq = (cy + t.dy0) * QW + (cx + t.dx);
+    gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
+    gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
+  }
+  // u(clamp) over the tile
+  for (int r = threadIdx.y; r < UH; r += blockDim.y) {
     const int gi = min(max(i0 - Ry + r, 0), H - 1);
-    const int gj = min(max(j0 - Rx + c, 0), W - 1);
-    us[idx] = __ldg(uin + (size_t)gi * ldin + gj);
+    const float* src = uin + (size_t)gi * ldin;
+    for (int c = threadIdx.x; c < US; c += blockDim.x)
+      us[r * US + c] = __ldg(src + min(max(j0 - Rx + c, 0), W - 1));
   }
   __syncthreads();
 
-  // q1 = W f / b, q2 = W at clamped positions of the correlation footprint
-  for (int idx = threadIdx.x; idx < QH * QW; idx += blockDim.x) {
-    const int qr = idx / QW, qc = idx - qr * QW;
-    const int ai = min(max(i0 - cy + qr, 0), H - 1);
+  // phase 1: q1 = W f / b, q2 = W on the q tile (virtual positions)
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int item = tid; item < NQS * QW; item += nth) {
+    const int s = item / QW, qc = item - s * QW;
+    const int qr0 = s * R;
+    const float* base = us + qr0 * US + qc;
+    float b[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) b[r] = 0.f;
+#pragma unroll 2
+    for (int g = 0; g < ng; ++g) {
+      const float4 G = gu[g];
+      const float* pu = base + __float_as_int(G.w);
+      float v[R + M - 1];
+#pragma unroll
+      for (int t = 0; t < R + M - 1; ++t) v[t] = pu[t * US];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        b[r] = fmaf(G.x, v[r + M - 1], b[r]);
+        if (M > 1) b[r] = fmaf(G.y, v[r + M - 2], b[r]);
+        if (M > 2) b[r] = fmaf(G.z, v[r + M - 3], b[r]);
+      }
+    }
     const int aj = min(max(j0 - cx + qc, 0), W - 1);
-    const float* ub = us + (ai - i0 + Ry) * US + (aj - j0 + Rx);
-    float b = 0.f;
-    for (int t = 0; t < ntaps; ++t) {
-      const Tap tp = taps[t];
-      b = fmaf(tp.w, ub[-tp.dy * US - tp.dx], b);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int ai = min(max(i0 - cy + qr0 + r, 0), H - 1);
+      const float fv = fmaxf(__ldg(f + (size_t)ai * ldf + aj), p.floor);
+      const float w = robust_weight(b[r], fv, p);
+      qs[(qr0 + r) * QW + qc] = make_float2(w * fv / b[r], w);
     }
-    const float fv = fmaxf(__ldg(f + (size_t)ai * ldf + aj), p.floor);
-    const float w = robust_weight(b, fv, p);
-    qs[idx] = make_float2(w * fv / b, w);
   }
   __syncthreads();
-
-  // outputs
-  for (int idx = threadIdx.x; idx < TH * TW; idx += blockDim.x) {
-    const int oi = idx / TW, oj = idx - oi * TW;
-    const int i = i0 + oi, j = j0 + oj;
-    if (i >= H || j >= W) continue;
-    const float2* qb = qs + (oi + cy) * QW + (oj + cx);
-    float A = 0.f, B = 0.f;
-    for (int t = 0; t < ntaps; ++t) {
-      const Tap tp = taps[t];
-      const float2 q = qb[tp.dy * QW + tp.dx];
-      A = fmaf(tp.w, q.x, A);
-      B = fmaf(tp.w, q.y, B);
+  // continuation of q across the image boundary (border tiles only)
+  const bool border = (i0 - cy < 0) || (j0 - cx < 0) || (i0 - cy + QH > H) || (j0 - cx + QW > W);
+  if (border) {
+    // writes only positions outside the image, reads only positions inside
+    // it: no ordering between threads is needed within this pass
+    for (int idx = tid; idx < QH * QW; idx += nth) {
+      const int qr = idx / QW, qc = idx - qr * QW;
+      const int vi = i0 - cy + qr, vj = j0 - cx + qc;
+      const int ci = min(max(vi, 0), H - 1), cj = min(max(vj, 0), W - 1);
+      if (ci != vi || cj != vj) qs[idx] = qs[(ci - (i0 - cy)) * QW + (cj - (j0 - cx))];
     }
-    // diffusion term on the diamond of radius 2 around (i, j)
-    const float* uc = us + (oi + Ry) * US + (oj + Rx);
-    const float c = uc[0];
-    const float e = uc[1], w_ = uc[-1], n = uc[-US], s = uc[US];
-    const float gc = diffusivity(0.5f * (e - w_), 0.5f * (s - n), p);
-    const float ge = diffusivity(0.5f * (uc[2] - c), 0.5f * (uc[US + 1] - uc[-US + 1]), p);
-    const float gw = diffusivity(0.5f * (c - uc[-2]), 0.5f * (uc[US - 1] - uc[-US - 1]), p);
-    const float gs = diffusivity(0.5f * (uc[US + 1] - uc[US - 1]), 0.5f * (uc[2 * US] - c), p);
-    const float gn = diffusivity(0.5f * (uc[-US + 1] - uc[-US - 1]), 0.5f * (c - uc[-2 * US]), p);
-    const float D = 0.5f * ((ge + gc) * (e - c) - (gc + gw) * (c - w_) + (gs + gc) * (s - c) -
-                            (gc + gn) * (c - n));
-    const float num = A + p.alpha * fmaxf(D, 0.f);
-    const float den = B - p.alpha * fminf(D, 0.f);
-    const float un = c * num / den;
-    if (!isfinite(un) && status) atomicOr(status, DB_FLAG_NONFINITE);
-    uout[(size_t)i * ldout + j] = un;
+    __syncthreads();
+  }
+
+  // phase 2: A = q1*h*, B = q2*h*, diffusion, update
+  for (int item = tid; item < (TH / R) * TW; item += nth) {
+    const int s = item / TW, oj = item - s * TW;
+    const int oi0 = s * R;
+    const float2* base = qs + oi0 * QW + oj;
+    float A[R], B[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { A[r] = 0.f; B[r] = 0.f; }
+#pragma unroll 2
+    for (int g = 0; g < ng; ++g) {
+      const float4 G = gq[g];
+      const float2* pq = base + __float_as_int(G.w);
+      float2 v[R + M - 1];
+#pragma unroll
+      for (int t = 0; t < R + M - 1; ++t) v[t] = pq[t * QW];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        A[r] = fmaf(G.x, v[r].x, A[r]);
+        B[r] = fmaf(G.x, v[r].y, B[r]);
+        if (M > 1) { A[r] = fmaf(G.y, v[r + 1].x, A[r]); B[r] = fmaf(G.y, v[r + 1].y, B[r]); }
+        if (M > 2) { A[r] = fmaf(G.z, v[r + 2].x, A[r]); B[r] = fmaf(G.z, v[r + 2].y, B[r]); }
+      }
+    }
+    const int j = j0 + oj;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + oi0 + r;
+      const float* uc = us + (oi0 + r + Ry) * US + (oj + Rx);
+      const float c = uc[0];
+      const float e = uc[1], w_ = uc[-1], n = uc[-US], so = uc[US];
+      const float gc = diffusivity(0.5f * (e - w_), 0.5f * (so - n), p);
+      const float ge = diffusivity(0.5f * (uc[2] - c), 0.5f * (uc[US + 1] - uc[-US + 1]), p);
+      const float gw = diffusivity(0.5f * (c - uc[-2]), 0.5f * (uc[US - 1] - uc[-US - 1]), p);
+      const float gs = diffusivity(0.5f * (uc[US + 1] - uc[US - 1]), 0.5f * (uc[2 * US] - c), p);
+      const float gn = diffusivity(0.5f * (uc[-US + 1] - uc[-US - 1]), 0.5f * (c - uc[-2 * US]), p);
+      const float D = 0.5f * ((ge + gc) * (e - c) - (gc + gw) * (c - w_) + (gs + gc) * (so - c) -
+                              (gc + gn) * (c - n));
+      const float num = A[r] + p.alpha * fmaxf(D, 0.f);
+      const float den = B[r] - p.alpha * fminf(D, 0.f);
+      const float un = c * num / den;
+      if (i < H && j < W) {
+        if (!isfinite(un) && status) atomicOr(status, DB_FLAG_NONFINITE);
+        uout[(size_t)i * ldout + j] = un;
+      }
+    }
   }
 }
 
-static size_t rrl_smem_bytes(int TH, int TW, int kh, int kw) {
+struct SpatialGeom {
+  int QHp, UH, US, QW;
+  size_t smem;
+};
+
+template <int TH, int TW, int R>
+static SpatialGeom spatial_geom(int kh, int kw, int ng_max) {
+  SpatialGeom g;
   const int Ry = kh - 1 > 2 ? kh - 1 : 2, Rx = kw - 1 > 2 ? kw - 1 : 2;
-  const size_t us = (size_t)((TH + 2 * Ry) * (TW + 2 * Rx) + 1) & ~size_t(1);
-  const size_t q = (size_t)(TH + kh - 1) * (TW + kw - 1);
-  return (size_t)kh * kw * sizeof(Tap) + us * sizeof(float) + q * sizeof(float2);
+  const int QH = TH + kh - 1;
+  g.QW = TW + kw - 1;
+  g.QHp = ((QH + R - 1) / R) * R;
+  g.UH = Ry + (g.QHp > TH + 2 ? g.QHp : TH + 2);
+  g.US = TW + 2 * Rx;
+  g.smem = (size_t)2 * ng_max * sizeof(float4) + (size_t)((g.UH * g.US + 1) & ~1) * sizeof(float) +
+           (size_t)g.QHp * g.QW * sizeof(float2);
+  return g;
+}
+
+constexpr int kTH = 64, kTW = 64, kR = 8;
+
+size_t rrl_spatial_smem(int kh, int kw) {
+  return spatial_geom<kTH, kTW, kR>(kh, kw, max_tap_groups(kh, kw)).smem;
+}
+
+template <int M>
+static cudaError_t launch_m(const float* f, int ldf, const float* uin, int ldin, float* uout,
+                            int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
+                            int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
+  const int ng_max = max_tap_groups(kh, kw);
+  const SpatialGeom g = spatial_geom<kTH, kTW, kR>(kh, kw, ng_max);
+  if (g.smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto kern = k_rrl_spatial<kTH, kTW, kR, M>;
+  if (g.smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
+  kern<<<grid, dim3(64, 4), g.smem, s>>>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh,
+                                          kw, ng_max, p, status);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
-                               int ldout, int H, int W, const Tap* taps, const int* ntaps, int kh,
-                               int kw, const RrlParams& p, int* status, cudaStream_t s) {
-  constexpr int TH = 32, TW = 64;
-  const size_t smem = rrl_smem_bytes(TH, TW, kh, kw);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_rrl_spatial<TH, TW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+                               int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
+                               int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
+  switch (tap_group_height(kh)) {
+    case 1: return launch_m<1>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, p, status, s);
+    case 2: return launch_m<2>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, p, status, s);
+    default: return launch_m<3>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, p, status, s);
   }
-  dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH);
-  k_rrl_spatial<TH, TW><<<grid, 256, smem, s>>>(f, ldf, uin, ldin, uout, ldout, H, W, taps, ntaps,
-                                                 kh, kw, p, status);
-  count_launch();
-  return cudaGetLastError();
 }
 
 }  // namespace db
