@@ -138,6 +138,19 @@ db_status db_status_from_flags(int flags);
 /* Library version string, e.g. "libdeblur 0.1 sm_103a". */
 const char* db_version(void);
 
+/* Kernel schedule of the spatial RRRL iteration (process-wide setting; the
+ * arithmetic is the same in every schedule):
+ *   DB_SCHED_AUTO  - split when u, f and q (16 bytes/pixel) fit comfortably in
+ *                    L2, fused otherwise (default)
+ *   DB_SCHED_FUSED - one launch per iteration; each tile recomputes the
+ *                    weighted ratio q on its halo (fewest HBM round trips)
+ *   DB_SCHED_SPLIT - two launches per iteration; q = (W f/b, W) goes through
+ *                    a global buffer in the workspace (no halo recompute) */
+#define DB_SCHED_AUTO 0
+#define DB_SCHED_FUSED 1
+#define DB_SCHED_SPLIT 2
+db_status db_set_schedule(int schedule);
+
 /* Number of CUDA kernels this library has enqueued in this process so far
  * (host-side counter; a CUDA-graph replay of captured calls adds nothing). */
 long long db_launch_count(void);

@@ -16,7 +16,7 @@ from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "version"]
+           "deblur", "set_schedule", "version"]
 
 
 class DeblurError(RuntimeError):
@@ -155,6 +155,12 @@ def deblur(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, k
     if check:
         ws.raise_on_flags("db_deblur")
     return u
+
+
+def set_schedule(name: str):
+    """Kernel schedule of the spatial iteration: "auto", "fused" or "split"."""
+    code = {"auto": _lib.SCHED_AUTO, "fused": _lib.SCHED_FUSED, "split": _lib.SCHED_SPLIT}[name]
+    _check(_lib.load().db_set_schedule(code), "db_set_schedule")
 
 
 def version() -> str:

@@ -22,6 +22,7 @@ class DbParams(ctypes.Structure):
 
 DB_PSF_GENERAL, DB_PSF_BOX = 0, 1
 DB_CONV_CLAMP, DB_CONV_PERIODIC = 0, 1
+SCHED_AUTO, SCHED_FUSED, SCHED_SPLIT = 0, 1, 2
 FLAG_TAPS, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOX = 0x1, 0x2, 0x4, 0x8
 
 P_PSF = ctypes.POINTER(DbPsf)
@@ -40,6 +41,7 @@ SIGNATURES = {
     "db_status_from_flags": (c_int, [c_int]),
     "db_version": (c_char_p, []),
     "db_launch_count": (ctypes.c_longlong, []),
+    "db_set_schedule": (c_int, [c_int]),
 }
 
 _lib = None

@@ -10,6 +10,7 @@
 namespace db {
 
 static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_schedule{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
@@ -19,6 +20,7 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
   L.ntaps = off; off += 256;
   L.utmp = off;  off += align256((size_t)H * W * sizeof(float));
+  L.qbuf = off;  off += align256((size_t)H * W * sizeof(float2));
   size_t spec_elems, work_elems;
   if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
   else if (kw == 1) { spec_elems = (size_t)H; work_elems = 0; }
@@ -126,7 +128,18 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
   TapGroup* groups = (TapGroup*)(base + L.taps);
   int* ngroups = (int*)(base + L.ntaps);
   float* tmp = (float*)(base + L.utmp);
-  if (rrl_spatial_smem(psf->kh, psf->kw) > 227 * 1024) return DB_ERR_UNSUPPORTED;
+  // schedule: split (q in a global buffer) when u, f and q stay resident in
+  // L2, fused (halo recompute, one pass per iteration) otherwise
+  int sched = g_schedule.load();
+  if (sched == DB_SCHED_AUTO)
+    sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
+  const size_t smem_need = sched == DB_SCHED_SPLIT
+                               ? (rrl_split_smem_q(psf->kh, psf->kw) > rrl_split_smem_update(psf->kh, psf->kw)
+                                      ? rrl_split_smem_q(psf->kh, psf->kw)
+                                      : rrl_split_smem_update(psf->kh, psf->kw))
+                               : rrl_spatial_smem(psf->kh, psf->kw);
+  if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
+  float2* qbuf = (float2*)(base + L.qbuf);
   if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, groups, ngroups, dev_status, s) !=
       cudaSuccess)
     return DB_ERR_CUDA;
@@ -142,9 +155,13 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
     }
     float* dst = (k % 2 == 0) ? tmp : u;
     const int ld_dst = (k % 2 == 0) ? W : ld;
-    if (launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, psf->kh, psf->kw,
-                           rp, dev_status, s) != cudaSuccess)
-      return DB_ERR_CUDA;
+    const cudaError_t e =
+        sched == DB_SCHED_SPLIT
+            ? launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, groups, ngroups, psf->kh,
+                               psf->kw, rp, dev_status, s)
+            : launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, psf->kh,
+                                 psf->kw, rp, dev_status, s);
+    if (e != cudaSuccess) return DB_ERR_CUDA;
     src = dst;
     ld_src = ld_dst;
   }
@@ -191,5 +208,12 @@ db_status db_status_from_flags(int flags) {
 const char* db_version(void) { return "libdeblur 0.1 sm_103a"; }
 
 long long db_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+db_status db_set_schedule(int schedule) {
+  if (schedule != DB_SCHED_AUTO && schedule != DB_SCHED_FUSED && schedule != DB_SCHED_SPLIT)
+    return DB_ERR_ARG;
+  g_schedule.store(schedule);
+  return DB_OK;
+}
 
 }  // extern "C"

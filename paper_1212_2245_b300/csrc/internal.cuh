@@ -36,6 +36,7 @@ struct WsLayout {
   size_t taps;     // TapGroup[max_tap_groups(kh, kw)]
   size_t ntaps;    // int: number of groups
   size_t utmp;     // float[H*W]  (RRRL ping-pong)
+  size_t qbuf;     // float2[H*W] (split schedule: q1, q2)
   size_t spec;     // float2[spec_elems]  (PSF spectrum)
   size_t work;     // float2[work_elems]  (FFT data)
   size_t total;
@@ -48,6 +49,12 @@ int max_tap_groups(int kh, int kw);
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s);
 size_t rrl_spatial_smem(int kh, int kw);
+size_t rrl_split_smem_q(int kh, int kw);
+size_t rrl_split_smem_update(int kh, int kw);
+cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
+                             int ldout, float2* q, int H, int W, const TapGroup* groups,
+                             const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
+                             cudaStream_t s);
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps,
                        int kh, int kw, float K, float floor_, void* ws, const WsLayout& L,
@@ -56,5 +63,21 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s);
+
+// Asynchronous global->shared copies (cp.async, sm_80+): each thread issues
+// its copies without waiting on any of them; cp_async_wait_all() then blocks
+// until this thread's copies have landed (a __syncthreads() must follow
+// before other threads read them).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
 
 }  // namespace db

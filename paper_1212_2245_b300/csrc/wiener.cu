@@ -32,6 +32,18 @@ struct FftArgs {
   float K, floor_, scale;
 };
 
+// The filter is linear, so it is applied to f0 - c (c = mid-grey) and the
+// exact response c * M(0) to the constant is added back: this keeps the
+// transform's rounding error, which scales with the signal norm, smaller.
+// M(0) = S0/(S0^2 + K) with S0 the zero-frequency PSF coefficient (element 0
+// of the spectrum in bit-reversed order is frequency 0).
+constexpr float kMidGrey = 128.0f;
+
+__device__ __forceinline__ float dc_response(const float2* spec, float K) {
+  const float2 S0 = __ldg(spec);
+  return kMidGrey * (S0.x / fmaf(S0.x, S0.x, fmaf(S0.y, S0.y, K)));
+}
+
 __device__ __forceinline__ float2 wiener_gain(float2 S, float2 X, float K) {
   // X * conj(S) / (|S|^2 + K)
   const float den = fmaf(S.x, S.x, fmaf(S.y, S.y, K));
@@ -61,13 +73,13 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
         const int ta = (q + cy) % a.nrows, tb = (c + cx) & (N - 1);
         if (ta < a.kh && tb < a.kw) v.x = __ldg(a.taps + ta * a.kw + tb);
       } else if (MODE == ROW_FWD_REAL) {
-        v.x = fmaxf(__ldg(a.fin + (size_t)q * a.ldf + c), a.floor_);
+        v.x = fmaxf(__ldg(a.fin + (size_t)q * a.ldf + c), a.floor_) - kMidGrey;
       } else if (MODE == ROW_INV_REAL) {
         v = a.cbuf[(size_t)q * a.ldc + c];
       } else {  // ROW_WIENER_1D: sequence q packs image rows 2q and 2q+1
         const int r0 = 2 * q, r1 = 2 * q + 1;
-        v.x = fmaxf(__ldg(a.fin + (size_t)r0 * a.ldf + c), a.floor_);
-        if (r1 < a.img_rows) v.y = fmaxf(__ldg(a.fin + (size_t)r1 * a.ldf + c), a.floor_);
+        v.x = fmaxf(__ldg(a.fin + (size_t)r0 * a.ldf + c), a.floor_) - kMidGrey;
+        if (r1 < a.img_rows) v.y = fmaxf(__ldg(a.fin + (size_t)r1 * a.ldf + c), a.floor_) - kMidGrey;
       }
     }
     x[idx] = v;
@@ -88,6 +100,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
     }
   }
   // ---- store
+  const float dc = (MODE == ROW_INV_REAL || MODE == ROW_WIENER_1D) ? dc_response(a.spec, a.K) : 0.f;
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
     const int r = idx >> a.logN, c = idx & (N - 1);
     const int q = q0 + r;
@@ -96,10 +109,10 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
     if (MODE == ROW_PSF || MODE == ROW_FWD_REAL) {
       a.cbuf[(size_t)q * a.ldc + c] = v;
     } else if (MODE == ROW_INV_REAL) {
-      a.uout[(size_t)q * a.ldu + c] = fmaxf(v.x * a.scale, a.floor_);
+      a.uout[(size_t)q * a.ldu + c] = fmaxf(fmaf(v.x, a.scale, dc), a.floor_);
     } else {
-      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(v.x * a.scale, a.floor_);
-      if (2 * q + 1 < a.img_rows) a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(v.y * a.scale, a.floor_);
+      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(fmaf(v.x, a.scale, dc), a.floor_);
+      if (2 * q + 1 < a.img_rows) a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(fmaf(v.y, a.scale, dc), a.floor_);
     }
   }
 }
@@ -123,8 +136,8 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
     if (q < nseq_total) {
       if (MODE == COL_WIENER_1D_REAL) {
         const int j0 = 2 * q, j1 = 2 * q + 1;
-        v.x = fmaxf(__ldg(a.fin + (size_t)k * a.ldf + j0), a.floor_);
-        if (j1 < a.nrows) v.y = fmaxf(__ldg(a.fin + (size_t)k * a.ldf + j1), a.floor_);
+        v.x = fmaxf(__ldg(a.fin + (size_t)k * a.ldf + j0), a.floor_) - kMidGrey;
+        if (j1 < a.nrows) v.y = fmaxf(__ldg(a.fin + (size_t)k * a.ldf + j1), a.floor_) - kMidGrey;
       } else {
         v = a.cbuf[(size_t)k * a.ldc + q];
       }
@@ -144,14 +157,15 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
     __syncthreads();
     fft_dit_inv(x, a.logN, C, C, 1, tw, 0, true);
   }
+  const float dc = (MODE == COL_WIENER_1D_REAL) ? dc_response(a.spec, a.K) : 0.f;
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - (idx / C) * C;
     const int q = c0 + c;
     if (q >= nseq_total) continue;
     const float2 v = x[idx];
     if (MODE == COL_WIENER_1D_REAL) {
-      a.uout[(size_t)k * a.ldu + 2 * q] = fmaxf(v.x * a.scale, a.floor_);
-      if (2 * q + 1 < a.nrows) a.uout[(size_t)k * a.ldu + 2 * q + 1] = fmaxf(v.y * a.scale, a.floor_);
+      a.uout[(size_t)k * a.ldu + 2 * q] = fmaxf(fmaf(v.x, a.scale, dc), a.floor_);
+      if (2 * q + 1 < a.nrows) a.uout[(size_t)k * a.ldu + 2 * q + 1] = fmaxf(fmaf(v.y, a.scale, dc), a.floor_);
     } else {
       a.cbuf[(size_t)k * a.ldc + q] = v;
     }
@@ -248,7 +262,7 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
   if ((e = launch_cols<COL_WIENER>(g, W, s)) != cudaSuccess) return e;
   FftArgs o = {};
   o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.logN = ilog2(W);
-  o.floor_ = floor_; o.scale = 1.0f / ((float)H * (float)W);
+  o.floor_ = floor_; o.scale = 1.0f / ((float)H * (float)W); o.spec = spec; o.K = K;
   return launch_rows<ROW_INV_REAL>(o, s);
 }
 

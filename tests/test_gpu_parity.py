@@ -29,19 +29,28 @@ def cuda(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32).cuda()
 
 
+@pytest.fixture(params=["fused", "split"])
+def sched(request, lib):
+    lib.set_schedule(request.param)
+    yield request.param
+    lib.set_schedule("auto")
+
+
 def oracle_pipeline(case):
     return oracle.ops.wr3l(case.f, case.h, case.params, case.iters)
 
 
 @pytest.mark.parametrize("maker", [synth.case_box256, synth.case_line1024])
-def test_full_pipeline_configs(lib, maker):
+def test_full_pipeline_configs(lib, maker, sched):
     case = maker()
     f, h = cuda(case.f), cuda(case.h)
     u0_ref, u_ref = oracle_pipeline(case)
     u0 = lib.wiener(f, h, case.params, kind=case.psf_kind)
-    assert_close(u0, u0_ref, f"{case.name} Wiener")
+    m0, r0 = assert_close(u0, u0_ref, f"{case.name} Wiener")
+    print(f"{case.name} Wiener max-abs {m0:.3e} rms {r0:.3e}")
     u = lib.rrl_iterate(f, u0.clone(), h, case.params, case.iters, kind=case.psf_kind)
-    assert_close(u, u_ref, f"{case.name} WR3L")
+    m, r = assert_close(u, u_ref, f"{case.name} WR3L")
+    print(f"{case.name} [{sched}] WR3L max-abs {m:.3e} rms {r:.3e}")
     ud = lib.deblur(f, h, case.params, case.iters, kind=case.psf_kind)
     assert torch.equal(ud, u)
 
@@ -56,7 +65,7 @@ def _iterate_case(H, W, h, iters, params, kind="general", seed=0, ld=None):
 
 @pytest.mark.parametrize("H,W", [(77, 131), (1, 1), (3, 200), (200, 3), (65, 64), (33, 97)])
 @pytest.mark.parametrize("psf", ["line", "box", "gauss", "col", "identity"])
-def test_iterations_ragged_shapes(lib, H, W, psf):
+def test_iterations_ragged_shapes(lib, H, W, psf, sched):
     rng = np.random.default_rng(H * 1000 + W)
     h = {"line": synth.line_psf(9, 30.0, 10.0), "box": synth.box_psf(7), "col": synth.raised_cosine_1d(5, "col"),
          "gauss": synth.gaussian_mixture_psf(7, rng), "identity": np.ones((1, 1), np.float32)}[psf]
@@ -71,7 +80,7 @@ def test_iterations_ragged_shapes(lib, H, W, psf):
     assert_close(u, ref, f"{psf} {H}x{W}")
 
 
-def test_pitched_rows_and_odd_iteration_count(lib):
+def test_pitched_rows_and_odd_iteration_count(lib, sched):
     H, W, ld = 70, 90, 128
     h = synth.line_psf(11, 30.0, 12.0)
     p = Params(alpha=0.01)
@@ -112,7 +121,7 @@ def test_wiener_shapes(lib, H, W, shape):
     assert_close(u0, ref, f"wiener {H}x{W} psf {shape}")
 
 
-def test_checkpoints_hold_intermediate_iterates(lib):
+def test_checkpoints_hold_intermediate_iterates(lib, sched):
     H, W = 64, 96
     h = synth.raised_cosine_1d(9)
     p = Params()
