@@ -150,9 +150,10 @@ __device__ __forceinline__ float diffusivity(float gx, float gy, const RrlParams
 // b[r] = (u*h) at R vertically adjacent pixels.  `base` points at the u
 // value that the first pixel's strip starts from; each group record holds
 // three weights and the shared-memory offset of its first load.
-template <int R, int M>
-__device__ __forceinline__ void blur_strip(const float* __restrict__ base, int stride,
+template <int R, int M, int STRIDE>
+__device__ __forceinline__ void blur_strip(const float* __restrict__ base,
                                            const float4* __restrict__ grp, int ng, float (&b)[R]) {
+  constexpr int stride = STRIDE;
 #pragma unroll
   for (int r = 0; r < R; ++r) b[r] = 0.f;
 #pragma unroll 2
@@ -172,10 +173,11 @@ __device__ __forceinline__ void blur_strip(const float* __restrict__ base, int s
 }
 
 // Delta[r] = (e*h*), B[r] = (W*h*) at R vertically adjacent pixels.
-template <int R, int M>
-__device__ __forceinline__ void correlate_strip(const float2* __restrict__ base, int stride,
+template <int R, int M, int STRIDE>
+__device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
                                                 const float4* __restrict__ grp, int ng, float (&dl)[R],
                                                 float (&B)[R]) {
+  constexpr int stride = STRIDE;
 #pragma unroll
   for (int r = 0; r < R; ++r) { dl[r] = 0.f; B[r] = 0.f; }
 #pragma unroll 2
@@ -201,9 +203,9 @@ __device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
 // and vertical fluxes shared by neighbouring rows of the strip are formed
 // once.  Across the image boundary the clamped copy makes every difference
 // vanish exactly: zero flux.
-template <int R>
-__device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, int S,
-                                                const RrlParams& p, float (&D)[R], float (&c)[R]) {
+template <int R, int S>
+__device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, const RrlParams& p,
+                                                float (&D)[R], float (&c)[R]) {
   float m[R + 4], e1[R + 2], w1[R + 2];
 #pragma unroll
   for (int t = 0; t < R + 4; ++t) m[t] = uc[(t - 2) * S];
@@ -251,7 +253,7 @@ __device__ __forceinline__ float rrl_update(float u, float dl, float B, float D,
 // position from the clamped u and then, at virtual positions outside the
 // image, replaced by q at the clamped position.
 // ---------------------------------------------------------------------------
-template <int TH, int TW, int R, int M>
+template <int TH, int TW, int R, int M, int P>
 __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict__ f, int ldf,
                                                      const float* __restrict__ uin, int ldin,
                                                      float* __restrict__ uout, int ldout, int H, int W,
@@ -259,12 +261,15 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
                                                      const int* __restrict__ ngroups_g, int kh, int kw,
                                                      int ng_max, RrlParams p, int* status) {
   static_assert(TH % R == 0, "output strips must tile TH");
+  // row strides padded to the halo class P >= kw - 1 (compile-time strides
+  // let every strip load use an immediate offset)
+  constexpr int US = TW + 2 * P, QS = TW + P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cy = kh >> 1, cx = kw >> 1;
-  const int Ry = max(kh - 1, 2), Rx = max(kw - 1, 2);
+  const int Ry = max(kh - 1, 2), Rx = P;
   const int QH = TH + kh - 1, QW = TW + kw - 1;
   const int NQS = (QH + R - 1) / R, QHp = NQS * R;
-  const int UH = Ry + max(QHp, TH + 2), US = TW + 2 * Rx;
+  const int UH = Ry + max(QHp, TH + 2);
   const int ng = *ngroups_g;
   float4* gu = (float4*)smem_raw;
   float4* gq = gu + ng_max;
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
   for (int g = tid; g < ng; g += nth) {
     const TapGroup t = groups_g[g];
     const int offu = (Ry - cy - t.dy0 - (M - 1)) * US + (Rx - cx - t.dx);
-    const int offq = (cy + t.dy0) * QW + (cx + t.dx);
+    const int offq = (cy + t.dy0) * QS + (cx + t.dx);
     gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
     gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
   }
@@ -301,9 +306,9 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
       fv[r] = fmaxf(__ldg(f + (size_t)ai * ldf + aj), p.floor);
     }
     float b[R];
-    blur_strip<R, M>(us + qr0 * US + qc, US, gu, ng, b);
+    blur_strip<R, M, US>(us + qr0 * US + qc, gu, ng, b);
 #pragma unroll
-    for (int r = 0; r < R; ++r) qs[(qr0 + r) * QW + qc] = weighted_residual(b[r], fv[r], p);
+    for (int r = 0; r < R; ++r) qs[(qr0 + r) * QS + qc] = weighted_residual(b[r], fv[r], p);
   }
   __syncthreads();
   const bool border = (i0 - cy < 0) || (j0 - cx < 0) || (i0 - cy + QH > H) || (j0 - cx + QW > W);
@@ -314,7 +319,7 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
       const int qr = idx / QW, qc = idx - qr * QW;
       const int vi = i0 - cy + qr, vj = j0 - cx + qc;
       const int ci = min(max(vi, 0), H - 1), cj = min(max(vj, 0), W - 1);
-      if (ci != vi || cj != vj) qs[idx] = qs[(ci - (i0 - cy)) * QW + (cj - (j0 - cx))];
+      if (ci != vi || cj != vj) qs[qr * QS + qc] = qs[(ci - (i0 - cy)) * QS + (cj - (j0 - cx))];
     }
     __syncthreads();
   }
@@ -324,8 +329,8 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
     const int s = item / TW, oj = item - s * TW;
     const int oi0 = s * R, j = j0 + oj;
     float dl[R], B[R], D[R], c[R];
-    correlate_strip<R, M>(qs + oi0 * QW + oj, QW, gq, ng, dl, B);
-    diffusion_strip<R>(us + (oi0 + Ry) * US + (oj + Rx), US, p, D, c);
+    correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
+    diffusion_strip<R, US>(us + (oi0 + Ry) * US + (oj + Rx), p, D, c);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = i0 + oi0 + r;
@@ -346,8 +351,8 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
 // the extra round trip of q costs no HBM traffic while the halo recompute of
 // the fused kernel disappears.
 // ---------------------------------------------------------------------------
-template <int TH, int TW, int R, int M>
-__global__ void __launch_bounds__(256) k_rrl_q(const float* __restrict__ f, int ldf,
+template <int TH, int TW, int R, int M, int P>
+__global__ void __launch_bounds__(256, 4) k_rrl_q(const float* __restrict__ f, int ldf,
                                                const float* __restrict__ uin, int ldin,
                                                float2* __restrict__ q, int ldq, int H, int W,
                                                const TapGroup* __restrict__ groups_g,
@@ -357,7 +362,8 @@ __global__ void __launch_bounds__(256) k_rrl_q(const float* __restrict__ f, int 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cy = kh >> 1, cx = kw >> 1;
   const int Ty = kh - 1 - cy, Tx = kw - 1 - cx;  // u rows/cols needed above/left of a pixel
-  const int UH = TH + kh - 1, US = TW + kw - 1;
+  constexpr int US = TW + P;                      // row stride, P >= kw - 1
+  const int UH = TH + kh - 1, UW = TW + kw - 1;
   const int ng = *ngroups_g;
   float4* gu = (float4*)smem_raw;
   float* us = (float*)(gu + ng_max);
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(256) k_rrl_q(const float* __restrict__ f, int 
   for (int r = threadIdx.y; r < UH; r += blockDim.y) {
     const int gi = min(max(i0 - Ty + r, 0), H - 1);
     const float* src = uin + (size_t)gi * ldin;
-    for (int c = threadIdx.x; c < US; c += blockDim.x)
+    for (int c = threadIdx.x; c < UW; c += blockDim.x)
       cp_async4(us + r * US + c, src + min(max(j0 - Tx + c, 0), W - 1));
   }
   cp_async_wait_all();
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(256) k_rrl_q(const float* __restrict__ f, int 
       fv[r] = fmaxf(__ldg(f + (size_t)i * ldf + j), p.floor);
     }
     float b[R];
-    blur_strip<R, M>(us + r0 * US + c, US, gu, ng, b);
+    blur_strip<R, M, US>(us + r0 * US + c, gu, ng, b);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = i0 + r0 + r;
@@ -396,8 +402,8 @@ __global__ void __launch_bounds__(256) k_rrl_q(const float* __restrict__ f, int 
   }
 }
 
-template <int TH, int TW, int R, int M>
-__global__ void __launch_bounds__(256) k_rrl_update(const float2* __restrict__ q, int ldq,
+template <int TH, int TW, int R, int M, int P>
+__global__ void __launch_bounds__(256, 4) k_rrl_update(const float2* __restrict__ q, int ldq,
                                                     const float* __restrict__ uin, int ldin,
                                                     float* __restrict__ uout, int ldout, int H, int W,
                                                     const TapGroup* __restrict__ groups_g,
@@ -407,16 +413,16 @@ __global__ void __launch_bounds__(256) k_rrl_update(const float2* __restrict__ q
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cy = kh >> 1, cx = kw >> 1;
   const int QH = TH + kh - 1, QW = TW + kw - 1;
-  const int UH = TH + 4, US = TW + 4;
+  constexpr int QS = TW + P, UH = TH + 4, US = TW + 4;  // row strides, P >= kw - 1
   const int ng = *ngroups_g;
   float4* gq = (float4*)smem_raw;
   float2* qs = (float2*)(gq + ng_max);
-  float* us = (float*)(qs + QH * QW);
+  float* us = (float*)(qs + QH * QS);
   const int i0 = blockIdx.y * TH, j0 = blockIdx.x * TW;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
   for (int g = tid; g < ng; g += nth) {
     const TapGroup t = groups_g[g];
-    const int offq = (cy + t.dy0) * QW + (cx + t.dx);
+    const int offq = (cy + t.dy0) * QS + (cx + t.dx);
     gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
   }
   // q(clamp) over the correlation footprint, u(clamp) with a 2-pixel halo
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(256) k_rrl_update(const float2* __restrict__ q
     const int gi = min(max(i0 - cy + r, 0), H - 1);
     const float2* src = q + (size_t)gi * ldq;
     for (int c = threadIdx.x; c < QW; c += blockDim.x)
-      cp_async8(qs + r * QW + c, src + min(max(j0 - cx + c, 0), W - 1));
+      cp_async8(qs + r * QS + c, src + min(max(j0 - cx + c, 0), W - 1));
   }
   for (int r = threadIdx.y; r < UH; r += blockDim.y) {
     const int gi = min(max(i0 - 2 + r, 0), H - 1);
@@ -439,8 +445,8 @@ __global__ void __launch_bounds__(256) k_rrl_update(const float2* __restrict__ q
     const int oi0 = s * R, j = j0 + oj;
     if (j >= W || i0 + oi0 >= H) continue;
     float dl[R], B[R], D[R], c[R];
-    correlate_strip<R, M>(qs + oi0 * QW + oj, QW, gq, ng, dl, B);
-    diffusion_strip<R>(us + (oi0 + 2) * US + (oj + 2), US, p, D, c);
+    correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
+    diffusion_strip<R, US>(us + (oi0 + 2) * US + (oj + 2), p, D, c);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = i0 + oi0 + r;
@@ -453,58 +459,37 @@ __global__ void __launch_bounds__(256) k_rrl_update(const float2* __restrict__ q
   }
 }
 
-struct SpatialGeom {
-  int QHp, UH, US, QW;
-  size_t smem;
-};
+// ---------------------------------------------------------------------------
+// host side: shared-memory sizes and launches.  The halo class P is the
+// smallest of 8, 16, 32, 64, 128, 256 that holds kw - 1 (and 2).
+// ---------------------------------------------------------------------------
+constexpr int kTH = 64, kTW = 64, kR = 8;        // fused tiles
+constexpr int kQTH = 32, kQTW = 64;              // split: q tiles
+constexpr int kUTH = 32, kUTW = 64;              // split: update tiles
 
-template <int TH, int TW, int R>
-static SpatialGeom spatial_geom(int kh, int kw, int ng_max) {
-  SpatialGeom g;
-  const int Ry = kh - 1 > 2 ? kh - 1 : 2, Rx = kw - 1 > 2 ? kw - 1 : 2;
-  const int QH = TH + kh - 1;
-  g.QW = TW + kw - 1;
-  g.QHp = ((QH + R - 1) / R) * R;
-  g.UH = Ry + (g.QHp > TH + 2 ? g.QHp : TH + 2);
-  g.US = TW + 2 * Rx;
-  g.smem = (size_t)2 * ng_max * sizeof(float4) + (size_t)((g.UH * g.US + 1) & ~1) * sizeof(float) +
-           (size_t)g.QHp * g.QW * sizeof(float2);
-  return g;
+static int halo_class(int kw) {
+  const int need = kw - 1 > 2 ? kw - 1 : 2;
+  int P = 8;
+  while (P < need) P *= 2;
+  return P;
 }
-
-constexpr int kTH = 64, kTW = 64, kR = 8;
 
 size_t rrl_spatial_smem(int kh, int kw) {
-  return spatial_geom<kTH, kTW, kR>(kh, kw, max_tap_groups(kh, kw)).smem;
+  const int ng_max = max_tap_groups(kh, kw), P = halo_class(kw);
+  const int Ry = kh - 1 > 2 ? kh - 1 : 2;
+  const int QHp = ((kTH + kh - 1 + kR - 1) / kR) * kR;
+  const int UH = Ry + (QHp > kTH + 2 ? QHp : kTH + 2);
+  const size_t us = (size_t)(UH * (kTW + 2 * P) + 1) & ~size_t(1);
+  return (size_t)2 * ng_max * sizeof(float4) + us * sizeof(float) + (size_t)QHp * (kTW + P) * sizeof(float2);
 }
-
-template <int M>
-static cudaError_t launch_m(const float* f, int ldf, const float* uin, int ldin, float* uout,
-                            int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
-                            int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
-  const int ng_max = max_tap_groups(kh, kw);
-  const SpatialGeom g = spatial_geom<kTH, kTW, kR>(kh, kw, ng_max);
-  if (g.smem > 227 * 1024) return cudaErrorInvalidValue;
-  auto kern = k_rrl_spatial<kTH, kTW, kR, M>;
-  if (g.smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-    if (e != cudaSuccess) return e;
-  }
-  dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-  kern<<<grid, dim3(64, 4), g.smem, s>>>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh,
-                                          kw, ng_max, p, status);
-  count_launch();
-  return cudaGetLastError();
-}
-
-constexpr int kQTH = 32, kQTW = 64, kUTH = 32, kUTW = 64;
-
 size_t rrl_split_smem_q(int kh, int kw) {
-  return (size_t)max_tap_groups(kh, kw) * sizeof(float4) + (size_t)(kQTH + kh - 1) * (kQTW + kw - 1) * sizeof(float);
+  return (size_t)max_tap_groups(kh, kw) * sizeof(float4) +
+         (size_t)(kQTH + kh - 1) * (kQTW + halo_class(kw)) * sizeof(float);
 }
 size_t rrl_split_smem_update(int kh, int kw) {
   return (size_t)max_tap_groups(kh, kw) * sizeof(float4) +
-         (size_t)(kUTH + kh - 1) * (kUTW + kw - 1) * sizeof(float2) + (size_t)(kUTH + 4) * (kUTW + 4) * sizeof(float);
+         (size_t)(kUTH + kh - 1) * (kUTW + halo_class(kw)) * sizeof(float2) +
+         (size_t)(kUTH + 4) * (kUTW + 4) * sizeof(float);
 }
 
 template <typename K>
@@ -514,48 +499,81 @@ static cudaError_t set_smem(K kern, size_t smem) {
   return cudaSuccess;
 }
 
-template <int M>
-static cudaError_t launch_split_m(const float* f, int ldf, const float* uin, int ldin, float* uout,
-                                  int ldout, float2* q, int H, int W, const TapGroup* groups,
-                                  const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                                  cudaStream_t s) {
-  const int ng_max = max_tap_groups(kh, kw);
-  const size_t sq = rrl_split_smem_q(kh, kw), su = rrl_split_smem_update(kh, kw);
-  if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
-  auto kq = k_rrl_q<kQTH, kQTW, kR, M>;
-  auto ku = k_rrl_update<kUTH, kUTW, kR, M>;
-  cudaError_t e;
-  if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
-  if ((e = set_smem(ku, su)) != cudaSuccess) return e;
-  kq<<<dim3((W + kQTW - 1) / kQTW, (H + kQTH - 1) / kQTH), dim3(64, 4), sq, s>>>(
-      f, ldf, uin, ldin, q, W, H, W, groups, ngroups, kh, kw, ng_max, p);
-  count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ku<<<dim3((W + kUTW - 1) / kUTW, (H + kUTH - 1) / kUTH), dim3(64, 4), su, s>>>(
-      q, W, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, ng_max, p, status);
+struct IterArgs {
+  const float* f; int ldf; const float* uin; int ldin; float* uout; int ldout; float2* q;
+  int H, W; const TapGroup* groups; const int* ngroups; int kh, kw; RrlParams p; int* status;
+};
+
+template <int M, int P>
+static cudaError_t launch_fused_mp(const IterArgs& a, cudaStream_t s) {
+  const int ng_max = max_tap_groups(a.kh, a.kw);
+  const size_t smem = rrl_spatial_smem(a.kh, a.kw);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto kern = k_rrl_spatial<kTH, kTW, kR, M, P>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH), dim3(64, 4), smem, s>>>(
+      a.f, a.ldf, a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups, a.ngroups, a.kh, a.kw, ng_max,
+      a.p, a.status);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
-                             int ldout, float2* q, int H, int W, const TapGroup* groups,
-                             const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             cudaStream_t s) {
-  switch (tap_group_height(kh)) {
-    case 1: return launch_split_m<1>(f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, s);
-    case 2: return launch_split_m<2>(f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, s);
-    default: return launch_split_m<3>(f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, s);
+template <int M, int P>
+static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
+  const int ng_max = max_tap_groups(a.kh, a.kw);
+  const size_t sq = rrl_split_smem_q(a.kh, a.kw), su = rrl_split_smem_update(a.kh, a.kw);
+  if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
+  auto kq = k_rrl_q<kQTH, kQTW, kR, M, P>;
+  auto ku = k_rrl_update<kUTH, kUTW, kR, M, P>;
+  cudaError_t e;
+  if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
+  if ((e = set_smem(ku, su)) != cudaSuccess) return e;
+  kq<<<dim3((a.W + kQTW - 1) / kQTW, (a.H + kQTH - 1) / kQTH), dim3(64, 4), sq, s>>>(
+      a.f, a.ldf, a.uin, a.ldin, a.q, a.W, a.H, a.W, a.groups, a.ngroups, a.kh, a.kw, ng_max, a.p);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ku<<<dim3((a.W + kUTW - 1) / kUTW, (a.H + kUTH - 1) / kUTH), dim3(64, 4), su, s>>>(
+      a.q, a.W, a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups, a.ngroups, a.kh, a.kw, ng_max,
+      a.p, a.status);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <bool SPLIT, int M>
+static cudaError_t dispatch_p(const IterArgs& a, cudaStream_t s) {
+  switch (halo_class(a.kw)) {
+    case 8: return SPLIT ? launch_split_mp<M, 8>(a, s) : launch_fused_mp<M, 8>(a, s);
+    case 16: return SPLIT ? launch_split_mp<M, 16>(a, s) : launch_fused_mp<M, 16>(a, s);
+    case 32: return SPLIT ? launch_split_mp<M, 32>(a, s) : launch_fused_mp<M, 32>(a, s);
+    case 64: return SPLIT ? launch_split_mp<M, 64>(a, s) : launch_fused_mp<M, 64>(a, s);
+    case 128: return SPLIT ? launch_split_mp<M, 128>(a, s) : launch_fused_mp<M, 128>(a, s);
+    default: return SPLIT ? launch_split_mp<M, 256>(a, s) : launch_fused_mp<M, 256>(a, s);
+  }
+}
+
+template <bool SPLIT>
+static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
+  switch (tap_group_height(a.kh)) {
+    case 1: return dispatch_p<SPLIT, 1>(a, s);
+    case 2: return dispatch_p<SPLIT, 2>(a, s);
+    default: return dispatch_p<SPLIT, 3>(a, s);
   }
 }
 
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
-  switch (tap_group_height(kh)) {
-    case 1: return launch_m<1>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, p, status, s);
-    case 2: return launch_m<2>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, p, status, s);
-    default: return launch_m<3>(f, ldf, uin, ldin, uout, ldout, H, W, groups, ngroups, kh, kw, p, status, s);
-  }
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status};
+  return dispatch<false>(a, s);
+}
+
+cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
+                             int ldout, float2* q, int H, int W, const TapGroup* groups,
+                             const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
+                             cudaStream_t s) {
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status};
+  return dispatch<true>(a, s);
 }
 
 }  // namespace db
