@@ -129,6 +129,34 @@ db_status db_deblur(const float* f, float* u, int H, int W, int ld,
                     const db_psf* psf, const db_params* p, int iters,
                     void* ws, size_t ws_bytes, int* dev_status, void* stream);
 
+/* Allocation-free RRRL iterations (no counterpart in the paper; an interface
+ * convenience).  Some callers cannot allocate device memory at run time:
+ * a deblurring step embedded in a fixed-latency frame loop (an inspection
+ * line that must finish every frame within its budget) cannot risk a
+ * cudaMalloc, which may synchronise the device and take unbounded time, and
+ * a plugin running inside a host framework that owns all GPU memory may have
+ * no allocator at all.  This call computes exactly what db_rrl_iterate
+ * computes (same arguments without checkpoints and workspace) but takes its
+ * scratch from a fixed array of DB_NOALLOC_SCRATCH_BYTES bytes compiled into
+ * the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *   - Images whose db_workspace_bytes(H, W, psf, p) exceeds
+ *     DB_NOALLOC_SCRATCH_BYTES are rejected with DB_ERR_WORKSPACE before
+ *     anything is enqueued (a 1024 x 1024 image with a 2D PSF fits).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current), which may load the library's module: make that
+ *     first call before any CUDA stream capture.
+ *   - All calls on a device share the one array.  Calls whose work overlaps
+ *     on the GPU (different streams, different host threads) race on it and
+ *     give undefined results; serialise them.  The array keeps the last
+ *     call's contents; every call writes the scratch it reads before
+ *     reading it, so no state carries over between calls.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called. */
+#define DB_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+db_status db_rrl_iterate_noalloc(const float* f, float* u, int H, int W, int ld,
+                                 const db_psf* psf, const db_params* p, int iters,
+                                 int* dev_status, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* db_status_string(db_status s);
 

@@ -16,7 +16,7 @@ from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "set_schedule", "version"]
+           "deblur", "rrl_iterate_noalloc", "set_schedule", "version"]
 
 
 class DeblurError(RuntimeError):
@@ -154,6 +154,26 @@ def deblur(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, k
                          int(iters), ws.ptr, ws.nbytes, ws.status.data_ptr(), _stream()), "db_deblur")
     if check:
         ws.raise_on_flags("db_deblur")
+    return u
+
+
+def rrl_iterate_noalloc(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, params: Params,
+                        iters: int, *, kind: str = "general", status: torch.Tensor | None = None):
+    """`iters` RRRL iterations in place on u without any device allocation:
+    for callers that cannot allocate at run time (a fixed-latency frame loop,
+    a plugin inside a framework that owns the GPU memory).  Scratch comes from
+    a fixed array inside the library (shared by all calls on a device: do not
+    overlap calls on the GPU).  `status`, if given, is a device int32 word the
+    library ORs error flags into; the caller zeroes and reads it."""
+    H, W, ld = _image(f, "f")
+    if _image(u, "u")[2] != ld or u.shape != f.shape:
+        raise ValueError("u must match f's shape and row stride")
+    lib = _lib.load()
+    psf, p = _db_psf(taps, kind), _db_params(params)
+    st = status.data_ptr() if status is not None else None
+    _check(lib.db_rrl_iterate_noalloc(f.data_ptr(), u.data_ptr(), H, W, ld, ctypes.byref(psf),
+                                      ctypes.byref(p), int(iters), st, _stream()),
+           "db_rrl_iterate_noalloc")
     return u
 
 

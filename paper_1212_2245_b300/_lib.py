@@ -23,6 +23,7 @@ class DbParams(ctypes.Structure):
 DB_PSF_GENERAL, DB_PSF_BOX = 0, 1
 DB_CONV_CLAMP, DB_CONV_PERIODIC = 0, 1
 SCHED_AUTO, SCHED_FUSED, SCHED_SPLIT = 0, 1, 2
+NOALLOC_SCRATCH_BYTES = 32 << 20  # DB_NOALLOC_SCRATCH_BYTES
 FLAG_TAPS, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOX = 0x1, 0x2, 0x4, 0x8
 
 P_PSF = ctypes.POINTER(DbPsf)
@@ -37,6 +38,8 @@ SIGNATURES = {
                                c_int, c_void_p, c_size_t, c_void_p, c_void_p]),
     "db_deblur": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, P_PSF, P_PAR, c_int, c_void_p,
                           c_size_t, c_void_p, c_void_p]),
+    "db_rrl_iterate_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, P_PSF, P_PAR, c_int,
+                                       c_void_p, c_void_p]),
     "db_status_string": (c_char_p, [c_int]),
     "db_status_from_flags": (c_int, [c_int]),
     "db_version": (c_char_p, []),
