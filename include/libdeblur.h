@@ -114,7 +114,10 @@ db_status db_wiener(const float* f, float* u0, int H, int W, int ld,
  *   A = (W f/b)*h*;  B = W*h*;  D = div(psi'(|grad u|^2) grad u)  (Eq. 11)
  *   u <- u (A + alpha [D]+) / (B - alpha [D]-),   [z]+- = (z +- |z|)/2 (Eq. 12)
  * with f0 = max(f, delta) in place of f.  D uses central differences and zero
- * flux across the image boundary (Sec. 4.1).  u must be > 0 on entry (the
+ * flux across the image boundary (Sec. 4.1).  p->conv selects spatial sums
+ * with constant continuation (any size) or Fourier-domain sums with periodic
+ * continuation (Sec. 4.3, general 2D variant; power-of-two H and W, else
+ * DB_ERR_UNSUPPORTED).  u must be > 0 on entry (the
  * Wiener output of db_wiener is).  If `ckpt` is not NULL, u before iteration
  * k is also written to ckpt + (k/ckpt_every)*H*W (packed, pitch W) for every
  * k that is a multiple of ckpt_every (k = 0 included); ckpt holds

@@ -14,7 +14,6 @@ static std::atomic<int> g_schedule{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
-  (void)conv;
   WsLayout L = {};
   size_t off = 0;
   L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
@@ -22,7 +21,8 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   L.utmp = off;  off += align256((size_t)H * W * sizeof(float));
   L.qbuf = off;  off += align256((size_t)H * W * sizeof(float2));
   size_t spec_elems, work_elems;
-  if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
+  if (conv == DB_CONV_PERIODIC) { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
+  else if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
   else if (kw == 1) { spec_elems = (size_t)H; work_elems = 0; }
   else { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
   L.spec = off;  off += align256(spec_elems * sizeof(float2));
@@ -121,10 +121,24 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
   if (f == u) return DB_ERR_ARG;
   const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv);
   if ((st = check_ws(ws, ws_bytes, L.total)) != DB_OK) return st;
-  if (p->conv != DB_CONV_CLAMP) return DB_ERR_UNSUPPORTED;
+  if (p->conv == DB_CONV_PERIODIC && !(is_pow2(H) && is_pow2(W))) return DB_ERR_UNSUPPORTED;
   if (iters == 0) return DB_OK;
   cudaStream_t s = (cudaStream_t)stream;
   char* base = (char*)ws;
+  if (p->conv == DB_CONV_PERIODIC) {
+    // blur and correlation through the Fourier domain (Sec. 4.3, general 2D)
+    TapGroup* groups = (TapGroup*)(base + L.taps);
+    if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, groups, (int*)(base + L.ntaps),
+                            dev_status, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    float2* S = (float2*)(base + L.spec);
+    if (run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, S, s) != cudaSuccess) return DB_ERR_CUDA;
+    if (run_rrl_fourier(f, ld, u, ld, (float*)(base + L.utmp), H, W, (float2*)(base + L.work),
+                        (float2*)(base + L.qbuf), S, to_rrl(p), iters, ckpt, ckpt_every, dev_status,
+                        s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    return DB_OK;
+  }
   TapGroup* groups = (TapGroup*)(base + L.taps);
   int* ngroups = (int*)(base + L.ntaps);
   float* tmp = (float*)(base + L.utmp);

@@ -60,6 +60,15 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
                        int kh, int kw, float K, float floor_, void* ws, const WsLayout& L,
                        int* status, cudaStream_t s);
 
+// PSF spectrum h^ on an H x W grid (bit-reversed order in both axes).
+cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float2* spec,
+                                cudaStream_t s);
+
+// Fourier-mode (periodic) RRRL iterations, in place on u.
+cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* utmp, int H, int W,
+                            float2* X, float2* Z, const float2* S, const RrlParams& p, int iters,
+                            float* ckpt, int ckpt_every, int* status, cudaStream_t s);
+
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s);

@@ -1,0 +1,233 @@
+// RRRL iteration with Fourier-domain (periodic) blur and correlation:
+// Sec. 2.3, Eq. 9-12, with the convolutions of Sec. 4.1 ("Convolution")
+// realised through the Fourier domain and periodic continuation (Sec. 4.2),
+// the paper's general 2D variant (Sec. 4.3).
+//
+// Per iteration, with S = h^ (bit-reversed order, from the same transforms):
+//   b      = IDFT(DFT(u) S)                      blur
+//   e, W   = W (f - b)/b, W = phi'(r_f(b))       weighted residual (Eq. 7, 10)
+//   Delta + iB = IDFT(DFT(e + iW) conj(S))       both correlations at once:
+//                                                 h is real, so the real and
+//                                                 imaginary parts stay apart
+//   D      = div(psi' grad u)                    spatial, zero flux (Eq. 11)
+//   u'     = u + u (Delta + alpha D)/(B - alpha [D]-)   (Eq. 9 in increment form)
+// as four passes over complex buffers X, Z (H x W, row pitch W):
+//   C1: columns of X: DIF, x S, DIT                 (X = row DIF of u)
+//   R2: rows of X: DIT -> b; (e, W); DIF -> Z
+//   C3: columns of Z: DIF, x conj(S), DIT
+//   R4: rows of Z: DIT -> Delta, B; D from 5 rows of u; update -> u';
+//       DIF of u' -> X for the next iteration
+// plus one initial row pass R0 (DIF of u -> X).
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "internal.cuh"
+
+namespace db {
+
+enum FRowMode { FR_U = 0, FR_MID = 1, FR_FIN = 2 };
+
+struct FourierArgs {
+  const float* f; int ldf;
+  const float* uin; int ldin;
+  float* uout; int ldout;
+  float2* X; float2* Z;      // complex buffers, pitch W
+  const float2* S;           // PSF spectrum, pitch W
+  int H, W, logW, logH;
+  float scale;               // 1/(H W)
+  int write_next;            // R4: also produce X for the next iteration
+  RrlParams p;
+  int* status;
+};
+
+__device__ __forceinline__ float robust_weight_f(float b, float f, const RrlParams& p) {
+  if (!p.phi_robust) return 1.0f;
+  const float t = __fdividef(b - f, f);
+  const float r = f * (t - log1pf(t));
+  return p.eps_phi * rsqrtf(fmaxf(r, 0.0f) + p.eps_phi * p.eps_phi);
+}
+
+__device__ __forceinline__ float diffusivity_f(float gx, float gy, const RrlParams& p) {
+  if (!p.psi_tv) return 1.0f;
+  return rsqrtf(fmaf(gx, gx, fmaf(gy, gy, p.eps_psi * p.eps_psi)));
+}
+
+// One row of length W per CTA.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
+  extern __shared__ float2 smem[];
+  const int W = a.W;
+  float2* tw = smem;
+  float2* x = smem + W;
+  float* u5 = (float*)(x + W);  // FR_FIN: rows i-2..i+2 of u (clamped)
+  fft_build_twiddles(tw, W);
+  const int i = blockIdx.x;
+  if (MODE == FR_U) {
+    for (int c = threadIdx.x; c < W; c += blockDim.x)
+      x[c] = make_float2(__ldg(a.uin + (size_t)i * a.ldin + c), 0.f);
+    __syncthreads();
+    fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[c];
+    return;
+  }
+  if (MODE == FR_MID) {
+    for (int c = threadIdx.x; c < W; c += blockDim.x) x[c] = a.X[(size_t)i * W + c];
+    __syncthreads();
+    fft_dit_inv(x, a.logW, 1, 1, W, tw, 0, false);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+      const float b = x[c].x * a.scale;
+      const float fv = fmaxf(__ldg(a.f + (size_t)i * a.ldf + c), a.p.floor);
+      const float w = robust_weight_f(b, fv, a.p);
+      x[c] = make_float2(__fdividef(w * (fv - b), b), w);
+    }
+    __syncthreads();
+    fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) a.Z[(size_t)i * W + c] = x[c];
+    return;
+  }
+  // FR_FIN
+  for (int c = threadIdx.x; c < W; c += blockDim.x) x[c] = a.Z[(size_t)i * W + c];
+  for (int idx = threadIdx.x; idx < 5 * W; idx += blockDim.x) {
+    const int r = idx / W, c = idx - r * W;
+    const int gi = min(max(i - 2 + r, 0), a.H - 1);
+    u5[idx] = __ldg(a.uin + (size_t)gi * a.ldin + c);
+  }
+  __syncthreads();
+  fft_dit_inv(x, a.logW, 1, 1, W, tw, 0, false);
+  const RrlParams& p = a.p;
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    const int cw = max(c - 1, 0), ce = min(c + 1, W - 1);
+    const int cww = max(c - 2, 0), cee = min(c + 2, W - 1);
+    const float* n2 = u5;
+    const float* n1 = u5 + W;
+    const float* m0 = u5 + 2 * W;
+    const float* s1 = u5 + 3 * W;
+    const float* s2 = u5 + 4 * W;
+    const float ctr = m0[c], e = m0[ce], w_ = m0[cw], n = n1[c], s = s1[c];
+    const float gc = diffusivity_f(0.5f * (e - w_), 0.5f * (s - n), p);
+    const float ge = diffusivity_f(0.5f * (m0[cee] - ctr), 0.5f * (s1[ce] - n1[ce]), p);
+    const float gw = diffusivity_f(0.5f * (ctr - m0[cww]), 0.5f * (s1[cw] - n1[cw]), p);
+    const float gs = diffusivity_f(0.5f * (s1[ce] - s1[cw]), 0.5f * (s2[c] - ctr), p);
+    const float gn = diffusivity_f(0.5f * (n1[ce] - n1[cw]), 0.5f * (ctr - n2[c]), p);
+    const float D = 0.5f * ((ge + gc) * (e - ctr) - (gc + gw) * (ctr - w_) + (gs + gc) * (s - ctr) -
+                            (gc + gn) * (ctr - n));
+    const float dl = x[c].x * a.scale, B = x[c].y * a.scale;
+    const float den = B - p.alpha * fminf(D, 0.f);
+    const float un = fmaf(ctr, __fdividef(fmaf(p.alpha, D, dl), den), ctr);
+    if (!isfinite(un) && a.status) atomicOr(a.status, DB_FLAG_NONFINITE);
+    a.uout[(size_t)i * a.ldout + c] = un;
+    x[c] = make_float2(un, 0.f);
+  }
+  if (!a.write_next) return;
+  __syncthreads();
+  fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
+  for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[c];
+}
+
+// C adjacent columns per CTA: DIF, multiply by S (or conj S), DIT, in place.
+template <bool CONJ, int C>
+__global__ void __launch_bounds__(256) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
+                                                      int H, int W, int logH) {
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* x = smem + H;
+  fft_build_twiddles(tw, H);
+  const int c0 = blockIdx.x * C;
+  for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
+    const int k = idx / C, c = idx - k * C;
+    x[idx] = (c0 + c < W) ? buf[(size_t)k * W + c0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_dif(x, logH, C, C, 1, tw, 0, true);
+  for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
+    const int k = idx / C, c = idx - k * C;
+    if (c0 + c < W) {
+      const float2 s = __ldg(S + (size_t)k * W + c0 + c);
+      x[idx] = CONJ ? cmulc(x[idx], s) : cmul(x[idx], s);
+    }
+  }
+  __syncthreads();
+  fft_dit_inv(x, logH, C, C, 1, tw, 0, true);
+  for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
+    const int k = idx / C, c = idx - k * C;
+    if (c0 + c < W) buf[(size_t)k * W + c0 + c] = x[idx];
+  }
+}
+
+template <typename K>
+static cudaError_t set_smem_f(K kern, size_t smem) {
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <int MODE>
+static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)2 * a.W * sizeof(float2) + (MODE == FR_FIN ? (size_t)5 * a.W * sizeof(float) : 0);
+  cudaError_t e = set_smem_f(k_fourier_rows<MODE>, smem);
+  if (e != cudaSuccess) return e;
+  k_fourier_rows<MODE><<<a.H, 256, smem, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <bool CONJ>
+static cudaError_t launch_fcol(float2* buf, const float2* S, int H, int W, cudaStream_t s) {
+  const int logH = ilog2(H);
+  if (H <= 2048) {
+    constexpr int C = 4;
+    const size_t smem = (size_t)(H + C * H) * sizeof(float2);
+    cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
+    if (e != cudaSuccess) return e;
+    k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, H, W, logH);
+  } else {
+    constexpr int C = 2;
+    const size_t smem = (size_t)(H + C * H) * sizeof(float2);
+    cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
+    if (e != cudaSuccess) return e;
+    k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, H, W, logH);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* utmp, int H, int W,
+                            float2* X, float2* Z, const float2* S, const RrlParams& p, int iters,
+                            float* ckpt, int ckpt_every, int* status, cudaStream_t s) {
+  FourierArgs a = {};
+  a.f = f; a.ldf = ldf; a.X = X; a.Z = Z; a.S = S;
+  a.H = H; a.W = W; a.logW = ilog2(W); a.logH = ilog2(H);
+  a.scale = 1.0f / ((float)H * (float)W);
+  a.p = p; a.status = status;
+  cudaError_t e;
+  a.uin = u; a.ldin = ld;
+  if ((e = launch_frow<FR_U>(a, s)) != cudaSuccess) return e;
+  const float* src = u;
+  int ld_src = ld;
+  for (int k = 0; k < iters; ++k) {
+    if (ckpt && k % ckpt_every == 0) {
+      float* dst = ckpt + (size_t)(k / ckpt_every) * H * W;
+      if ((e = cudaMemcpy2DAsync(dst, (size_t)W * sizeof(float), src, (size_t)ld_src * sizeof(float),
+                                 (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    }
+    float* dst = (k % 2 == 0) ? utmp : u;
+    const int ld_dst = (k % 2 == 0) ? W : ld;
+    if ((e = launch_fcol<false>(X, S, H, W, s)) != cudaSuccess) return e;
+    a.uin = src; a.ldin = ld_src;
+    if ((e = launch_frow<FR_MID>(a, s)) != cudaSuccess) return e;
+    if ((e = launch_fcol<true>(Z, S, H, W, s)) != cudaSuccess) return e;
+    a.uout = dst; a.ldout = ld_dst; a.write_next = (k + 1 < iters);
+    if ((e = launch_frow<FR_FIN>(a, s)) != cudaSuccess) return e;
+    src = dst;
+    ld_src = ld_dst;
+  }
+  if (src != u) {
+    if ((e = cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), src, (size_t)W * sizeof(float),
+                               (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace db

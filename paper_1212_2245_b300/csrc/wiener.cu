@@ -213,6 +213,18 @@ static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
   }
 }
 
+cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float2* spec,
+                                cudaStream_t s) {
+  FftArgs a = {};
+  a.taps = taps; a.kh = kh; a.kw = kw; a.nrows = H; a.logN = ilog2(W);
+  a.cbuf = spec; a.ldc = W;
+  cudaError_t e;
+  if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+  FftArgs c = {};
+  c.cbuf = spec; c.ldc = W; c.nrows = W; c.logN = ilog2(H);
+  return launch_cols<COL_FWD>(c, W, s);
+}
+
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps, int kh,
                        int kw, float K, float floor_, void* ws, const WsLayout& L, int* status,
                        cudaStream_t s) {

@@ -55,6 +55,49 @@ def test_full_pipeline_configs(lib, maker, sched):
     assert torch.equal(ud, u)
 
 
+def test_full_pipeline_fourier_gauss2048(lib):
+    """2048x2048, 31x31 Gaussian mixture, Wiener + 30 RRRL with Fourier-domain
+    (periodic) blur and correlation."""
+    case = synth.case_gauss2048()
+    f, h = cuda(case.f), cuda(case.h)
+    u0_ref, u_ref = oracle_pipeline(case)
+    u0 = lib.wiener(f, h, case.params)
+    m0, r0 = assert_close(u0, u0_ref, "gauss2048 Wiener")
+    u = lib.rrl_iterate(f, u0.clone(), h, case.params, case.iters)
+    m, r = assert_close(u, u_ref, "gauss2048 WR3L")
+    print(f"gauss2048 Wiener max-abs {m0:.3e} rms {r0:.3e}; WR3L max-abs {m:.3e} rms {r:.3e}")
+
+
+@pytest.mark.parametrize("H,W,psf", [(64, 64, "line"), (128, 32, "gauss"), (32, 256, "row"), (256, 512, "gauss"),
+                                     (16, 16, "identity"), (8, 1024, "row"), (1024, 8, "col")])
+def test_fourier_iterations_shapes(lib, H, W, psf):
+    rng = np.random.default_rng(H * 7 + W)
+    h = {"line": synth.line_psf(9, 30.0, 10.0), "row": synth.raised_cosine_1d(7), "col": synth.box_psf(5, "col"),
+         "gauss": synth.gaussian_mixture_psf(7, rng), "identity": np.ones((1, 1), np.float32)}[psf]
+    p = Params(conv="periodic")
+    f, u0 = _iterate_case(H, W, h, 4, p, seed=5)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 4)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 4)
+    assert_close(u, ref, f"fourier {psf} {H}x{W}")
+
+
+def test_fourier_checkpoints_and_pitch(lib):
+    H, W, ld = 64, 128, 160
+    h = synth.gaussian_mixture_psf(5, np.random.default_rng(3))
+    p = Params(conv="periodic")
+    f, u0 = _iterate_case(H, W, h, 5, p)
+    fp = torch.zeros(H, ld, device="cuda"); fp[:, :W] = cuda(f)
+    up = torch.full((H, ld), -3.0, device="cuda"); up[:, :W] = cuda(u0)
+    ck = torch.empty(3, H, W, device="cuda")
+    lib.rrl_iterate(fp[:, :W], up[:, :W], cuda(h), p, 5, ckpt=ck, ckpt_every=2)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 5)
+    assert_close(up[:, :W], ref, "fourier pitched")
+    assert torch.all(up[:, W:] == -3.0)
+    u2 = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 2)
+    u4 = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 4)
+    assert torch.equal(ck[0], cuda(u0)) and torch.equal(ck[1], u2) and torch.equal(ck[2], u4)
+
+
 def _iterate_case(H, W, h, iters, params, kind="general", seed=0, ld=None):
     rng = np.random.default_rng(seed)
     g = synth.scene(H, W, rng).astype(np.float32)
@@ -148,4 +191,4 @@ def test_device_flags_for_bad_taps(lib):
 def test_unsupported_is_reported(lib):
     f = cuda(np.full((32, 48), 100.0))
     with pytest.raises(lib.DeblurError, match="unsupported"):
-        lib.wiener(f, cuda(np.ones((3, 3)) / 9), Params())
+        lib.rrl_iterate(f, f.clone(), cuda(np.ones((3, 3)) / 9), Params(conv="periodic"), 1)
