@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="line1024",
+                    help="line1024 (default, the headline workload), box256, gauss2048")
     return ap.parse_args()
 
 
@@ -118,14 +120,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_case():
+def _spatial_model(case, ms_iter):
+    """Fused/split spatial iteration: FP32-issue bound; flops per pixel and
+    iteration = 3 tap sums (b, A, B) x 2 flops x nnz(h) + 60 pointwise."""
+    H, W = case.f.shape
+    nnz = int((case.h != 0).sum())
+    flops = (6 * nnz + 60) * H * W
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (ms_iter / 1e3) / 1e12
+    hbm_peak, hbm_src = peaks()
+    hbm_equiv = 12.0 * H * W / (ms_iter / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "one RRRL iteration (k_rrl_q + k_rrl_update, or k_rrl_spatial)",
+            "kernel_ms": ms_iter, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
+            "hbm_equiv_gbs": hbm_equiv, "hbm_equiv_frac": hbm_equiv / hbm_peak,
+            "hbm_peak_gbs": hbm_peak, "hbm_peak_src": hbm_src}
+
+
+def _fourier_model(case, ms_iter):
+    """Fourier iteration: four HBM passes over complex buffers; algorithmic
+    bytes per pixel and iteration = 24 (columns x S) + 20 (rows: b, e, W) +
+    24 (columns x conj S) + 24 (rows: update, next transform) = 92 B."""
+    H, W = case.f.shape
+    hbm_peak, hbm_src = peaks()
+    achieved = 92.0 * H * W / (ms_iter / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None,
+            "kernel": "one Fourier RRRL iteration (k_fourier_cols x2 + k_fourier_rows x2)",
+            "kernel_ms": ms_iter, "peak_src": hbm_src}
+
+
+def _make(name):
     from paper_1212_2245_b300 import synth
-    return synth.case_line1024()
+    return {"line1024": synth.case_line1024, "box256": synth.case_box256,
+            "gauss2048": synth.case_gauss2048}[name]()
+
+
+WORKLOADS = {
+    "line1024": ("line1024: 1024x1024 f32, 30deg line PSF L=31 (17x27, 71 taps), sigma=2 + 1% salt/pepper, "
+                 "Wiener K=0.01 + 20 RRRL (TV, alpha=0.003), spatial blur/correlation", _spatial_model),
+    "box256": ("box256: 256x256 f32, horizontal box L=15, sigma=2, row Wiener K=0.006 + 10 RRRL, spatial",
+               _spatial_model),
+    "gauss2048": ("gauss2048: 2048x2048 f32, 31x31 mixture of 3 Gaussians, sigma=1, Wiener K=0.006 + 30 RRRL "
+                  "with Fourier-domain (periodic) blur/correlation", _fourier_model),
+}
+
+
+def make_case(name="line1024"):
+    return _make(name)
 
 
 def cpu_baseline_oracle(case, n_iters=5):
     """The FP64 oracle as it stands, on the host cores: Wiener + n_iters RRRL
-    iterations on the full 1024x1024 image."""
+    iterations on the full image."""
     import oracle
     t0 = time.perf_counter()
     oracle.wr3l(case.f, case.h, case.params, n_iters)
@@ -142,9 +189,9 @@ def run_reference(args, ws_, rank):
     if rank != 0:
         return
     import oracle
-    case = make_case()
+    case = make_case(args.workload)
     p, h = case.params, case.h
-    rows = 128
+    rows = min(128, case.f.shape[0])
     f = case.f[:rows].astype(np.float64)
     f0 = oracle.condition_input(f, p.pos_floor)
     u = oracle.positivity_floor(torch.as_tensor(f), p.pos_floor)  # warm start for the sample
@@ -161,8 +208,7 @@ def run_reference(args, ws_, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "line1024: 1024x1024, 30deg line PSF L=31, Wiener + 20 RRRL",
-                       "sample": sample},
+            "config": {"workload": WORKLOADS[args.workload][0], "sample": sample},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -176,7 +222,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = _lib.load()
-    case = make_case()
+    case = make_case(args.workload)
+    desc, model = WORKLOADS[args.workload]
     H, W = case.f.shape
     iters, p = case.iters, case.params
     f = torch.as_tensor(case.f).to(dev)
@@ -279,31 +326,17 @@ def run_ours(args, world, rank, local):
         return
     px_iter = H * W * iters
     value = world * px_iter / (ms / 1e3) / 1e6
-    nnz = int((case.h != 0).sum())
-    # dominant kernel: the fused RRRL iteration (one launch per iteration)
-    k_ms = ms_iter / iters
-    flops_px = 6 * nnz + 60          # 3 tap sums (b, A, B) of 2 flops per tap + pointwise work
-    flops_launch = flops_px * H * W
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
-    achieved = flops_launch / (k_ms / 1e3) / 1e12
-    hbm_peak, hbm_src = peaks()
-    hbm_equiv = 12.0 * H * W / (k_ms / 1e3) / 1e9
+    roof = model(case, ms_iter / iters)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "line1024: 1024x1024 f32, 30deg line PSF L=31 (17x27, 71 taps), "
-                               "sigma=2 + 1% salt/pepper, Wiener K=0.01 + 20 RRRL (TV, alpha=0.003)",
-                   "H": H, "W": W, "iters": iters, "psf_nnz": nnz, "l2": "flushed before every step (256 MiB write)",
+        "config": {"workload": desc, "H": H, "W": W, "iters": iters, "psf": list(case.h.shape),
+                   "psf_nnz": int((case.h != 0).sum()), "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "rrrl_only_mpx_iter_s": world * px_iter / (ms_iter / 1e3) / 1e6,
         "wiener_ms": statistics.mean(wiener_ms),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp32, "traffic": None,
-                     "kernel": "k_rrl_spatial (fused RRRL iteration)", "kernel_ms": k_ms,
-                     "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
-                     "hbm_equiv_gbs": hbm_equiv, "hbm_equiv_frac": hbm_equiv / hbm_peak,
-                     "hbm_peak_gbs": hbm_peak, "hbm_peak_src": hbm_src},
+        "roofline": roof,
         "e2e": {"value": world * px_iter / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": H * W * 4, "d2h_bytes_per_step": H * W * 4, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * K,
@@ -312,7 +345,7 @@ def run_ours(args, world, rank, local):
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_oracle(case)
+        line["cpu_baseline"] = cpu_baseline_oracle(case, 5 if H * W <= (1 << 20) else 2)
     print(json.dumps(line), flush=True)
 
 

@@ -27,6 +27,7 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   else { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
   L.spec = off;  off += align256(spec_elems * sizeof(float2));
   L.work = off;  off += align256(work_elems * sizeof(float2));
+  L.tw = off;    off += align256((size_t)(W + H) * sizeof(float2));
   L.total = off;
   return L;
 }
@@ -132,10 +133,15 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
                             dev_status, s) != cudaSuccess)
       return DB_ERR_CUDA;
     float2* S = (float2*)(base + L.spec);
-    if (run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, S, s) != cudaSuccess) return DB_ERR_CUDA;
+    float2* twW = (float2*)(base + L.tw);
+    float2* twH = twW + W;
+    if (launch_twiddles(twW, W, s) != cudaSuccess || launch_twiddles(twH, H, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    if (run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, S, twW, twH, s) != cudaSuccess)
+      return DB_ERR_CUDA;
     if (run_rrl_fourier(f, ld, u, ld, (float*)(base + L.utmp), H, W, (float2*)(base + L.work),
-                        (float2*)(base + L.qbuf), S, to_rrl(p), iters, ckpt, ckpt_every, dev_status,
-                        s) != cudaSuccess)
+                        (float2*)(base + L.qbuf), S, twW, twH, to_rrl(p), iters, ckpt, ckpt_every,
+                        dev_status, s) != cudaSuccess)
       return DB_ERR_CUDA;
     return DB_OK;
   }

@@ -16,6 +16,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "internal.cuh"
+
 namespace db {
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -32,13 +34,11 @@ __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a
 // multiply by +i
 __device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a.x); }
 
-// tw[k] = exp(-2 pi i k / NT), k in [0, NT)
-__device__ inline void fft_build_twiddles(float2* tw, int NT) {
-  for (int k = threadIdx.x; k < NT; k += blockDim.x) {
-    float s, c;
-    sincospif(-2.0f * (float)k / (float)NT, &s, &c);
-    tw[k] = make_float2(c, s);
-  }
+// Twiddle table tw[k] = exp(-2 pi i k / NT), k in [0, NT), computed once per
+// call in double precision and rounded once to float (see k_twiddles), then
+// copied into shared memory by each CTA with asynchronous copies.
+__device__ inline void fft_load_twiddles(float2* tw, const float2* __restrict__ g, int NT) {
+  for (int k = threadIdx.x; k < NT; k += blockDim.x) cp_async8(tw + k, g + k);
 }
 
 // Forward DIF transform of `nseq` sequences of length N = 2^logN held in

@@ -39,6 +39,7 @@ struct WsLayout {
   size_t qbuf;     // float2[H*W] (split schedule: q1, q2)
   size_t spec;     // float2[spec_elems]  (PSF spectrum)
   size_t work;     // float2[work_elems]  (FFT data)
+  size_t tw;       // float2[W + H]       (twiddle tables for lengths W and H)
   size_t total;
 };
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv);
@@ -62,12 +63,14 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 
 // PSF spectrum h^ on an H x W grid (bit-reversed order in both axes).
 cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float2* spec,
-                                cudaStream_t s);
+                                const float2* twW, const float2* twH, cudaStream_t s);
+cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t s);
 
 // Fourier-mode (periodic) RRRL iterations, in place on u.
 cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* utmp, int H, int W,
-                            float2* X, float2* Z, const float2* S, const RrlParams& p, int iters,
-                            float* ckpt, int ckpt_every, int* status, cudaStream_t s);
+                            float2* X, float2* Z, const float2* S, const float2* twW,
+                            const float2* twH, const RrlParams& p, int iters, float* ckpt,
+                            int ckpt_every, int* status, cudaStream_t s);
 
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,

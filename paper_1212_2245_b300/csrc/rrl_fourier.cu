@@ -33,6 +33,7 @@ struct FourierArgs {
   float* uout; int ldout;
   float2* X; float2* Z;      // complex buffers, pitch W
   const float2* S;           // PSF spectrum, pitch W
+  const float2* twW;         // twiddle table for length W
   int H, W, logW, logH;
   float scale;               // 1/(H W)
   int write_next;            // R4: also produce X for the next iteration
@@ -52,31 +53,45 @@ __device__ __forceinline__ float diffusivity_f(float gx, float gy, const RrlPara
   return rsqrtf(fmaf(gx, gx, fmaf(gy, gy, p.eps_psi * p.eps_psi)));
 }
 
-// One row of length W per CTA.
+// One row of length W per CTA.  Every global input is staged with
+// asynchronous copies before the transform.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
   extern __shared__ float2 smem[];
   const int W = a.W;
   float2* tw = smem;
   float2* x = smem + W;
-  float* u5 = (float*)(x + W);  // FR_FIN: rows i-2..i+2 of u (clamped)
-  fft_build_twiddles(tw, W);
+  float* rs = (float*)(x + W);  // real rows: FR_U/FR_MID one row, FR_FIN rows i-2..i+2 of u
+  fft_load_twiddles(tw, a.twW, W);
   const int i = blockIdx.x;
   if (MODE == FR_U) {
-    for (int c = threadIdx.x; c < W; c += blockDim.x)
-      x[c] = make_float2(__ldg(a.uin + (size_t)i * a.ldin + c), 0.f);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async4(rs + c, a.uin + (size_t)i * a.ldin + c);
+  } else if (MODE == FR_MID) {
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+      cp_async8(x + c, a.X + (size_t)i * W + c);
+      cp_async4(rs + c, a.f + (size_t)i * a.ldf + c);
+    }
+  } else {
+    for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async8(x + c, a.Z + (size_t)i * W + c);
+    for (int r = 0; r < 5; ++r) {
+      const int gi = min(max(i - 2 + r, 0), a.H - 1);
+      for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async4(rs + r * W + c, a.uin + (size_t)gi * a.ldin + c);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (MODE == FR_U) {
+    for (int c = threadIdx.x; c < W; c += blockDim.x) x[c] = make_float2(rs[c], 0.f);
     __syncthreads();
     fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
     for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[c];
     return;
   }
   if (MODE == FR_MID) {
-    for (int c = threadIdx.x; c < W; c += blockDim.x) x[c] = a.X[(size_t)i * W + c];
-    __syncthreads();
     fft_dit_inv(x, a.logW, 1, 1, W, tw, 0, false);
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
       const float b = x[c].x * a.scale;
-      const float fv = fmaxf(__ldg(a.f + (size_t)i * a.ldf + c), a.p.floor);
+      const float fv = fmaxf(rs[c], a.p.floor);
       const float w = robust_weight_f(b, fv, a.p);
       x[c] = make_float2(__fdividef(w * (fv - b), b), w);
     }
@@ -86,23 +101,16 @@ __global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
     return;
   }
   // FR_FIN
-  for (int c = threadIdx.x; c < W; c += blockDim.x) x[c] = a.Z[(size_t)i * W + c];
-  for (int idx = threadIdx.x; idx < 5 * W; idx += blockDim.x) {
-    const int r = idx / W, c = idx - r * W;
-    const int gi = min(max(i - 2 + r, 0), a.H - 1);
-    u5[idx] = __ldg(a.uin + (size_t)gi * a.ldin + c);
-  }
-  __syncthreads();
   fft_dit_inv(x, a.logW, 1, 1, W, tw, 0, false);
   const RrlParams& p = a.p;
   for (int c = threadIdx.x; c < W; c += blockDim.x) {
     const int cw = max(c - 1, 0), ce = min(c + 1, W - 1);
     const int cww = max(c - 2, 0), cee = min(c + 2, W - 1);
-    const float* n2 = u5;
-    const float* n1 = u5 + W;
-    const float* m0 = u5 + 2 * W;
-    const float* s1 = u5 + 3 * W;
-    const float* s2 = u5 + 4 * W;
+    const float* n2 = rs;
+    const float* n1 = rs + W;
+    const float* m0 = rs + 2 * W;
+    const float* s1 = rs + 3 * W;
+    const float* s2 = rs + 4 * W;
     const float ctr = m0[c], e = m0[ce], w_ = m0[cw], n = n1[c], s = s1[c];
     const float gc = diffusivity_f(0.5f * (e - w_), 0.5f * (s - n), p);
     const float ge = diffusivity_f(0.5f * (m0[cee] - ctr), 0.5f * (s1[ce] - n1[ce]), p);
@@ -127,16 +135,18 @@ __global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
 // C adjacent columns per CTA: DIF, multiply by S (or conj S), DIT, in place.
 template <bool CONJ, int C>
 __global__ void __launch_bounds__(256) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
-                                                      int H, int W, int logH) {
+                                                      const float2* __restrict__ twH, int H, int W, int logH) {
   extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* x = smem + H;
-  fft_build_twiddles(tw, H);
+  fft_load_twiddles(tw, twH, H);
   const int c0 = blockIdx.x * C;
   for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
-    x[idx] = (c0 + c < W) ? buf[(size_t)k * W + c0 + c] : make_float2(0.f, 0.f);
+    if (c0 + c < W) cp_async8(x + idx, buf + (size_t)k * W + c0 + c);
+    else x[idx] = make_float2(0.f, 0.f);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_dif(x, logH, C, C, 1, tw, 0, true);
   for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
@@ -163,7 +173,7 @@ static cudaError_t set_smem_f(K kern, size_t smem) {
 
 template <int MODE>
 static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)2 * a.W * sizeof(float2) + (MODE == FR_FIN ? (size_t)5 * a.W * sizeof(float) : 0);
+  const size_t smem = (size_t)2 * a.W * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
   cudaError_t e = set_smem_f(k_fourier_rows<MODE>, smem);
   if (e != cudaSuccess) return e;
   k_fourier_rows<MODE><<<a.H, 256, smem, s>>>(a);
@@ -172,30 +182,31 @@ static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
 }
 
 template <bool CONJ>
-static cudaError_t launch_fcol(float2* buf, const float2* S, int H, int W, cudaStream_t s) {
+static cudaError_t launch_fcol(float2* buf, const float2* S, const float2* twH, int H, int W, cudaStream_t s) {
   const int logH = ilog2(H);
   if (H <= 2048) {
     constexpr int C = 4;
     const size_t smem = (size_t)(H + C * H) * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
     if (e != cudaSuccess) return e;
-    k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, H, W, logH);
+    k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, twH, H, W, logH);
   } else {
     constexpr int C = 2;
     const size_t smem = (size_t)(H + C * H) * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
     if (e != cudaSuccess) return e;
-    k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, H, W, logH);
+    k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, twH, H, W, logH);
   }
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* utmp, int H, int W,
-                            float2* X, float2* Z, const float2* S, const RrlParams& p, int iters,
-                            float* ckpt, int ckpt_every, int* status, cudaStream_t s) {
+                            float2* X, float2* Z, const float2* S, const float2* twW,
+                            const float2* twH, const RrlParams& p, int iters, float* ckpt,
+                            int ckpt_every, int* status, cudaStream_t s) {
   FourierArgs a = {};
-  a.f = f; a.ldf = ldf; a.X = X; a.Z = Z; a.S = S;
+  a.f = f; a.ldf = ldf; a.X = X; a.Z = Z; a.S = S; a.twW = twW;
   a.H = H; a.W = W; a.logW = ilog2(W); a.logH = ilog2(H);
   a.scale = 1.0f / ((float)H * (float)W);
   a.p = p; a.status = status;
@@ -213,10 +224,10 @@ cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* ut
     }
     float* dst = (k % 2 == 0) ? utmp : u;
     const int ld_dst = (k % 2 == 0) ? W : ld;
-    if ((e = launch_fcol<false>(X, S, H, W, s)) != cudaSuccess) return e;
+    if ((e = launch_fcol<false>(X, S, twH, H, W, s)) != cudaSuccess) return e;
     a.uin = src; a.ldin = ld_src;
     if ((e = launch_frow<FR_MID>(a, s)) != cudaSuccess) return e;
-    if ((e = launch_fcol<true>(Z, S, H, W, s)) != cudaSuccess) return e;
+    if ((e = launch_fcol<true>(Z, S, twH, H, W, s)) != cudaSuccess) return e;
     a.uout = dst; a.ldout = ld_dst; a.write_next = (k + 1 < iters);
     if ((e = launch_frow<FR_FIN>(a, s)) != cudaSuccess) return e;
     src = dst;

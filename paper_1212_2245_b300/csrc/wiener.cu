@@ -16,6 +16,22 @@
 
 namespace db {
 
+// tw[k] = exp(-2 pi i k / N) for k < N, correctly rounded from double.
+__global__ void k_twiddles(float2* __restrict__ tw, int N) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)N, &s, &c);
+    tw[k] = make_float2((float)c, (float)s);
+  }
+}
+
+cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t s) {
+  k_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+  count_launch();
+  return cudaGetLastError();
+}
+
 enum RowMode { ROW_PSF = 0, ROW_FWD_REAL = 1, ROW_INV_REAL = 2, ROW_WIENER_1D = 3 };
 enum ColMode { COL_FWD = 0, COL_WIENER = 1, COL_WIENER_1D_REAL = 2 };
 
@@ -26,6 +42,7 @@ struct FftArgs {
   const float2* spec;          // spectrum (bit-reversed order)
   int ldspec;
   const float* taps; int kh, kw;
+  const float2* twg;           // twiddle table for the transform length (global)
   int nrows;                   // rows (row kernels) or columns (column kernels) of data
   int img_rows;                // image rows (packed row-pair Wiener)
   int logN;                    // log2 of the transform length
@@ -52,16 +69,35 @@ __device__ __forceinline__ float2 wiener_gain(float2 S, float2 X, float K) {
   return make_float2(t.x * inv, t.y * inv);
 }
 
-// Row transforms: each CTA owns R consecutive sequences of length N.
+// Row transforms: each CTA owns R consecutive sequences of length N.  Global
+// inputs are staged with asynchronous copies (real inputs into the upper
+// half of each complex slot's memory first), so every load of the CTA is in
+// flight at once.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
   extern __shared__ float2 smem[];
   const int N = 1 << a.logN;
   float2* tw = smem;
   float2* x = smem + N;
-  fft_build_twiddles(tw, N);
+  float* stage = (float*)(x + R * N);  // real rows staged here (R*N floats, x2 for row pairs)
+  fft_load_twiddles(tw, a.twg, N);
   const int q0 = blockIdx.x * R;  // first sequence of this CTA
   // ---- load
+  for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+    const int r = idx >> a.logN, c = idx & (N - 1);
+    const int q = q0 + r;
+    if (q >= a.nrows) continue;
+    if (MODE == ROW_FWD_REAL) {
+      cp_async4(stage + idx, a.fin + (size_t)q * a.ldf + c);
+    } else if (MODE == ROW_INV_REAL) {
+      cp_async8(x + idx, a.cbuf + (size_t)q * a.ldc + c);
+    } else if (MODE == ROW_WIENER_1D) {
+      cp_async4(stage + 2 * idx, a.fin + (size_t)(2 * q) * a.ldf + c);
+      if (2 * q + 1 < a.img_rows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)(2 * q + 1) * a.ldf + c);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
     const int r = idx >> a.logN, c = idx & (N - 1);
     const int q = q0 + r;
@@ -73,13 +109,12 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
         const int ta = (q + cy) % a.nrows, tb = (c + cx) & (N - 1);
         if (ta < a.kh && tb < a.kw) v.x = __ldg(a.taps + ta * a.kw + tb);
       } else if (MODE == ROW_FWD_REAL) {
-        v.x = fmaxf(__ldg(a.fin + (size_t)q * a.ldf + c), a.floor_) - kMidGrey;
+        v.x = fmaxf(stage[idx], a.floor_) - kMidGrey;
       } else if (MODE == ROW_INV_REAL) {
-        v = a.cbuf[(size_t)q * a.ldc + c];
+        v = x[idx];
       } else {  // ROW_WIENER_1D: sequence q packs image rows 2q and 2q+1
-        const int r0 = 2 * q, r1 = 2 * q + 1;
-        v.x = fmaxf(__ldg(a.fin + (size_t)r0 * a.ldf + c), a.floor_) - kMidGrey;
-        if (r1 < a.img_rows) v.y = fmaxf(__ldg(a.fin + (size_t)r1 * a.ldf + c), a.floor_) - kMidGrey;
+        v.x = fmaxf(stage[2 * idx], a.floor_) - kMidGrey;
+        if (2 * q + 1 < a.img_rows) v.y = fmaxf(stage[2 * idx + 1], a.floor_) - kMidGrey;
       }
     }
     x[idx] = v;
@@ -126,23 +161,34 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
   const int N = 1 << a.logN;
   float2* tw = smem;
   float2* x = smem + N;
-  fft_build_twiddles(tw, N);
+  float* stage = (float*)(x + N * C);  // COL_WIENER_1D_REAL: 2*C real columns
+  fft_load_twiddles(tw, a.twg, N);
   const int c0 = blockIdx.x * C;  // first sequence
   const int nseq_total = (MODE == COL_WIENER_1D_REAL) ? (a.nrows + 1) / 2 : a.nrows;
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - (idx / C) * C;
     const int q = c0 + c;
-    float2 v = make_float2(0.f, 0.f);
-    if (q < nseq_total) {
-      if (MODE == COL_WIENER_1D_REAL) {
-        const int j0 = 2 * q, j1 = 2 * q + 1;
-        v.x = fmaxf(__ldg(a.fin + (size_t)k * a.ldf + j0), a.floor_) - kMidGrey;
-        if (j1 < a.nrows) v.y = fmaxf(__ldg(a.fin + (size_t)k * a.ldf + j1), a.floor_) - kMidGrey;
-      } else {
-        v = a.cbuf[(size_t)k * a.ldc + q];
-      }
+    if (q >= nseq_total) continue;
+    if (MODE == COL_WIENER_1D_REAL) {
+      cp_async4(stage + 2 * idx, a.fin + (size_t)k * a.ldf + 2 * q);
+      if (2 * q + 1 < a.nrows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)k * a.ldf + 2 * q + 1);
+    } else {
+      cp_async8(x + idx, a.cbuf + (size_t)k * a.ldc + q);
     }
-    x[idx] = v;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+    const int c = idx - (idx / C) * C;
+    const int q = c0 + c;
+    if (q >= nseq_total) {
+      x[idx] = make_float2(0.f, 0.f);
+    } else if (MODE == COL_WIENER_1D_REAL) {
+      float2 v;
+      v.x = fmaxf(stage[2 * idx], a.floor_) - kMidGrey;
+      v.y = (2 * q + 1 < a.nrows) ? fmaxf(stage[2 * idx + 1], a.floor_) - kMidGrey : 0.f;
+      x[idx] = v;
+    }
   }
   __syncthreads();
   fft_dif(x, a.logN, C, C, 1, tw, 0, true);
@@ -189,7 +235,7 @@ static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
   const int N = 1 << a.logN;
   const int R = N >= 2048 ? 1 : 2048 / N;
   const int grid = (a.nrows + R - 1) / R;
-  const size_t smem = (size_t)(N + R * N) * sizeof(float2);
+  const size_t smem = (size_t)(N + R * N) * sizeof(float2) + (size_t)2 * R * N * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fft_rows<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -202,26 +248,31 @@ static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
 template <int MODE>
 static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
   const int N = 1 << a.logN;
-  if (N <= 2048) {
+  const size_t st = (MODE == COL_WIENER_1D_REAL) ? 1 : 0;  // real staging only for packed real columns
+  if (N <= 1024) {
     constexpr int C = 8;
-    const size_t smem = (size_t)(N + C * N) * sizeof(float2);
+    const size_t smem = (size_t)(N + C * N) * sizeof(float2) + st * 2 * C * N * sizeof(float);
+    return launch_smem(k_fft_cols<MODE, C>, dim3((nseq + C - 1) / C), dim3(256), smem, s, a);
+  } else if (N <= 2048) {
+    constexpr int C = 4;
+    const size_t smem = (size_t)(N + C * N) * sizeof(float2) + st * 2 * C * N * sizeof(float);
     return launch_smem(k_fft_cols<MODE, C>, dim3((nseq + C - 1) / C), dim3(256), smem, s, a);
   } else {
-    constexpr int C = 4;
-    const size_t smem = (size_t)(N + C * N) * sizeof(float2);
+    constexpr int C = 2;
+    const size_t smem = (size_t)(N + C * N) * sizeof(float2) + st * 2 * C * N * sizeof(float);
     return launch_smem(k_fft_cols<MODE, C>, dim3((nseq + C - 1) / C), dim3(256), smem, s, a);
   }
 }
 
 cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float2* spec,
-                                cudaStream_t s) {
+                                const float2* twW, const float2* twH, cudaStream_t s) {
   FftArgs a = {};
   a.taps = taps; a.kh = kh; a.kw = kw; a.nrows = H; a.logN = ilog2(W);
-  a.cbuf = spec; a.ldc = W;
+  a.cbuf = spec; a.ldc = W; a.twg = twW;
   cudaError_t e;
   if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
   FftArgs c = {};
-  c.cbuf = spec; c.ldc = W; c.nrows = W; c.logN = ilog2(H);
+  c.cbuf = spec; c.ldc = W; c.nrows = W; c.logN = ilog2(H); c.twg = twH;
   return launch_cols<COL_FWD>(c, W, s);
 }
 
@@ -232,17 +283,21 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
   char* base = (char*)ws;
   float2* spec = (float2*)(base + L.spec);
   float2* work = (float2*)(base + L.work);
+  float2* twW = (float2*)(base + L.tw);
+  float2* twH = twW + W;
   cudaError_t e;
+  if (kw > 1 || kh == 1) { if ((e = launch_twiddles(twW, W, s)) != cudaSuccess) return e; }
+  if (kh > 1) { if ((e = launch_twiddles(twH, H, s)) != cudaSuccess) return e; }
   FftArgs a = {};
   a.K = K;
   a.floor_ = floor_;
   if (kh == 1) {
     // PSF along rows: 1D spectrum of length W, then packed row pairs.
     a.taps = taps; a.kh = 1; a.kw = kw; a.nrows = 1; a.logN = ilog2(W);
-    a.cbuf = spec; a.ldc = W;
+    a.cbuf = spec; a.ldc = W; a.twg = twW;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.twg = twW;
     b.nrows = (H + 1) / 2; b.img_rows = H; b.logN = ilog2(W);
     b.K = K; b.floor_ = floor_; b.scale = 1.0f / (float)W;
     return launch_rows<ROW_WIENER_1D>(b, s);
@@ -251,29 +306,26 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
     // PSF along columns: 1D spectrum of length H (a kh x 1 tap array has the
     // memory layout of a 1 x kh row), then packed column pairs.
     a.taps = taps; a.kh = 1; a.kw = kh; a.nrows = 1; a.logN = ilog2(H);
-    a.cbuf = spec; a.ldc = H;
+    a.cbuf = spec; a.ldc = H; a.twg = twH;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.twg = twH;
     b.nrows = W; b.logN = ilog2(H);
     b.K = K; b.floor_ = floor_; b.scale = 1.0f / (float)H;
     return launch_cols<COL_WIENER_1D_REAL>(b, (W + 1) / 2, s);
   }
   // General 2D PSF: spectrum (rows then columns), then the image.
-  a.taps = taps; a.kh = kh; a.kw = kw; a.nrows = H; a.logN = ilog2(W);
-  a.cbuf = spec; a.ldc = W;
-  if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
-  FftArgs c = {};
-  c.cbuf = spec; c.ldc = W; c.nrows = W; c.logN = ilog2(H);
-  if ((e = launch_cols<COL_FWD>(c, W, s)) != cudaSuccess) return e;
+  if ((e = run_psf_spectrum_2d(taps, kh, kw, H, W, spec, twW, twH, s)) != cudaSuccess) return e;
   FftArgs d = {};
   d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = W; d.nrows = H; d.logN = ilog2(W); d.floor_ = floor_;
+  d.twg = twW;
   if ((e = launch_rows<ROW_FWD_REAL>(d, s)) != cudaSuccess) return e;
   FftArgs g = {};
   g.cbuf = work; g.ldc = W; g.spec = spec; g.ldspec = W; g.nrows = W; g.logN = ilog2(H); g.K = K;
+  g.twg = twH;
   if ((e = launch_cols<COL_WIENER>(g, W, s)) != cudaSuccess) return e;
   FftArgs o = {};
-  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.logN = ilog2(W);
+  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.logN = ilog2(W); o.twg = twW;
   o.floor_ = floor_; o.scale = 1.0f / ((float)H * (float)W); o.spec = spec; o.K = K;
   return launch_rows<ROW_INV_REAL>(o, s);
 }
