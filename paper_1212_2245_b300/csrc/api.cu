@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fft_df.cuh"
 #include "internal.cuh"
 
 #include <atomic>
@@ -25,9 +26,10 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   else if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
   else if (kw == 1) { spec_elems = (size_t)H; work_elems = 0; }
   else { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
-  L.spec = off;  off += align256(spec_elems * sizeof(float2));
-  L.work = off;  off += align256(work_elems * sizeof(float2));
-  L.tw = off;    off += align256((size_t)(W + H) * sizeof(float2));
+  L.spec = off;  off += align256(spec_elems * sizeof(float4));
+  L.work = off;  off += align256(work_elems * sizeof(float4));
+  L.s32 = off;   off += (conv == DB_CONV_PERIODIC) ? align256((size_t)H * W * sizeof(float2)) : 0;
+  L.tw = off;    off += align256((dft_table_elems(W) + dft_table_elems(H)) * sizeof(float4));
   L.total = off;
   return L;
 }
@@ -64,9 +66,8 @@ static db_status check_ws(void* ws, size_t ws_bytes, size_t need) {
 }
 
 static bool wiener_supported(int H, int W, int kh, int kw) {
-  if (kh == 1) return is_pow2(W);
-  if (kw == 1) return is_pow2(H);
-  return is_pow2(H) && is_pow2(W);
+  (void)kh; (void)kw;
+  return H <= kMaxSide && W <= kMaxSide;  // any size: Bluestein covers other lengths
 }
 
 static RrlParams to_rrl(const db_params* p) {
@@ -132,15 +133,21 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
     if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, groups, (int*)(base + L.ntaps),
                             dev_status, s) != cudaSuccess)
       return DB_ERR_CUDA;
-    float2* S = (float2*)(base + L.spec);
-    float2* twW = (float2*)(base + L.tw);
-    float2* twH = twW + W;
-    if (launch_twiddles(twW, W, s) != cudaSuccess || launch_twiddles(twH, H, s) != cudaSuccess)
+    // PSF spectrum in float-float, rounded once to the FP32 copy the
+    // iterations multiply with
+    float4* Sff = (float4*)(base + L.spec);
+    float2* S = (float2*)(base + L.s32);
+    float4* tabW = (float4*)(base + L.tw);
+    float4* tabH = tabW + dft_table_elems(W);
+    Dft1ff FW, FH;
+    Dft1 DW, DH;
+    if (prepare_dft(W, tabW, &FW, &DW, s) != cudaSuccess || prepare_dft(H, tabH, &FH, &DH, s) != cudaSuccess)
       return DB_ERR_CUDA;
-    if (run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, S, twW, twH, s) != cudaSuccess)
+    if (run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, Sff, FW, FH, s) != cudaSuccess)
       return DB_ERR_CUDA;
+    if (round_spectrum(Sff, S, (size_t)H * W, s) != cudaSuccess) return DB_ERR_CUDA;
     if (run_rrl_fourier(f, ld, u, ld, (float*)(base + L.utmp), H, W, (float2*)(base + L.work),
-                        (float2*)(base + L.qbuf), S, twW, twH, to_rrl(p), iters, ckpt, ckpt_every,
+                        (float2*)(base + L.qbuf), S, DW.tw, DH.tw, to_rrl(p), iters, ckpt, ckpt_every,
                         dev_status, s) != cudaSuccess)
       return DB_ERR_CUDA;
     return DB_OK;

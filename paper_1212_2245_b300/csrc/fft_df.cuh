@@ -1,0 +1,225 @@
+// Float-float ("double-single") FFT building blocks for the Wiener filter.
+//
+// The RRRL update is multiplicative, so a pixel whose Wiener value is small
+// carries its relative error through every iteration while its value grows.
+// An FP32 transform leaves absolute errors of ~1e-4 grey levels everywhere,
+// which dark pixels turn into relative errors of 1e-4..1e-3.  Carrying every
+// value of the Wiener transforms as an unevaluated sum hi + lo of two floats
+// (about 44 significant bits) and rounding once at the end makes the output
+// error relative (half an FP32 ulp) instead.
+//
+// A complex value is a float4 (re.hi, re.lo, im.hi, im.lo).  Addition uses
+// Knuth's two-sum, multiplication the FMA-based exact product (Dekker/Knuth
+// error-free transformations), each followed by a renormalising fast
+// two-sum.  The sweep structure (DIF forward to bit-reversed order, DIT
+// inverse back, radix-2^2 butterflies, Bluestein for other lengths) is the
+// same as in fft.cuh.  Twiddle and chirp tables are float-float too and are
+// read from global memory (they stay in L1/L2).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace db {
+
+// ---- real float-float arithmetic (value = x + y, |y| <= ulp(x)/2) ----------
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = (a.x - (s - bb)) + (b.x - bb) + (a.y + b.y);
+  return ff_fast_two_sum(s, e);
+}
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return ff_fast_two_sum(p, e);
+}
+// a / b, one Newton-style correction of the float quotient
+__device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
+  const float q1 = a.x / b.x;
+  const float2 r = ff_sub(a, ff_mul(b, make_float2(q1, 0.f)));
+  const float q2 = r.x / b.x;
+  return ff_fast_two_sum(q1, q2);
+}
+
+// ---- complex float-float ---------------------------------------------------
+__device__ __forceinline__ float2 re_(float4 z) { return make_float2(z.x, z.y); }
+__device__ __forceinline__ float2 im_(float4 z) { return make_float2(z.z, z.w); }
+__device__ __forceinline__ float4 mkc(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
+__device__ __forceinline__ float4 zadd(float4 a, float4 b) { return mkc(ff_add(re_(a), re_(b)), ff_add(im_(a), im_(b))); }
+__device__ __forceinline__ float4 zsub(float4 a, float4 b) { return mkc(ff_sub(re_(a), re_(b)), ff_sub(im_(a), im_(b))); }
+__device__ __forceinline__ float4 zmul(float4 a, float4 b) {
+  return mkc(ff_sub(ff_mul(re_(a), re_(b)), ff_mul(im_(a), im_(b))),
+             ff_add(ff_mul(re_(a), im_(b)), ff_mul(im_(a), re_(b))));
+}
+// a * conj(b)
+__device__ __forceinline__ float4 zmulc(float4 a, float4 b) {
+  return mkc(ff_add(ff_mul(re_(a), re_(b)), ff_mul(im_(a), im_(b))),
+             ff_sub(ff_mul(im_(a), re_(b)), ff_mul(re_(a), im_(b))));
+}
+__device__ __forceinline__ float4 zmul_mi(float4 a) { return make_float4(a.z, a.w, -a.x, -a.y); }  // * (-i)
+__device__ __forceinline__ float4 zmul_pi(float4 a) { return make_float4(-a.z, -a.w, a.x, a.y); }  // * (+i)
+__device__ __forceinline__ float4 zconj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ float4 zscale(float4 a, float2 s) { return mkc(ff_mul(re_(a), s), ff_mul(im_(a), s)); }
+__device__ __forceinline__ float4 zzero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// A 1D DFT of length N in float-float (see Dft1 for the layout).
+struct Dft1ff {
+  int N, logM;
+  const float4* tw;  // exp(-2 pi i k / M), k < M
+  const float4* c;   // chirp, nullptr for power-of-two N
+  const float4* Bf;  // transform of the circular chirp
+};
+
+__device__ __forceinline__ void seq_item_ff(int it, int nseq, int len, bool seq_fast, int& q, int& k) {
+  if (seq_fast) { q = it % nseq; k = it / nseq; } else { q = it / len; k = it - q * len; }
+}
+
+// Forward DIF sweep (output bit-reversed); see fft_dif.  Ends with a barrier.
+__device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss, const float4* __restrict__ tw,
+                                  bool seq_fast) {
+  const int N = 1 << logN;
+  const int nb = N >> 2;
+  int logLen = logN;
+  while (logLen >= 2) {
+    const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
+    const int tstep = 1 << (logN - logLen);
+    for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
+      int q, b;
+      seq_item_ff(it, nseq, nb, seq_fast, q, b);
+      const int blk = b >> logm, j = b & (m - 1);
+      float4* p = x + q * ss + (blk * len + j) * es;
+      const int sm = m * es;
+      const float4 x0 = p[0], x1 = p[sm], x2 = p[2 * sm], x3 = p[3 * sm];
+      const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
+      const float4 y0 = zadd(x0, x2), y2 = zmul(zsub(x0, x2), w1);
+      const float4 y1 = zadd(x1, x3), y3 = zmul_mi(zmul(zsub(x1, x3), w1));
+      p[0] = zadd(y0, y1);
+      p[sm] = zmul(zsub(y0, y1), w2);
+      p[2 * sm] = zadd(y2, y3);
+      p[3 * sm] = zmul(zsub(y2, y3), w2);
+    }
+    __syncthreads();
+    logLen -= 2;
+  }
+  if (logLen == 1) {
+    for (int it = threadIdx.x; it < nseq * (N >> 1); it += blockDim.x) {
+      int q, b;
+      seq_item_ff(it, nseq, N >> 1, seq_fast, q, b);
+      float4* p = x + q * ss + (2 * b) * es;
+      const float4 a = p[0], c = p[es];
+      p[0] = zadd(a, c);
+      p[es] = zsub(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse DIT sweep (unnormalised), mirror of fft_dif_ff.  Ends with a barrier.
+__device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int ss,
+                                      const float4* __restrict__ tw, bool seq_fast) {
+  const int N = 1 << logN;
+  const int nb = N >> 2;
+  int logLen = (logN & 1) ? 1 : 0;
+  if (logLen == 1) {
+    for (int it = threadIdx.x; it < nseq * (N >> 1); it += blockDim.x) {
+      int q, b;
+      seq_item_ff(it, nseq, N >> 1, seq_fast, q, b);
+      float4* p = x + q * ss + (2 * b) * es;
+      const float4 a = p[0], c = p[es];
+      p[0] = zadd(a, c);
+      p[es] = zsub(a, c);
+    }
+    __syncthreads();
+  }
+  for (logLen += 2; logLen <= logN; logLen += 2) {
+    const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
+    const int tstep = 1 << (logN - logLen);
+    for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
+      int q, b;
+      seq_item_ff(it, nseq, nb, seq_fast, q, b);
+      const int blk = b >> logm, j = b & (m - 1);
+      float4* p = x + q * ss + (blk * len + j) * es;
+      const int sm = m * es;
+      const float4 z0 = p[0], z1 = p[sm], z2 = p[2 * sm], z3 = p[3 * sm];
+      const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
+      const float4 t1 = zmulc(z1, w2), t3 = zmulc(z3, w2);
+      const float4 y0 = zadd(z0, t1), y1 = zsub(z0, t1);
+      const float4 y2 = zadd(z2, t3), y3 = zsub(z2, t3);
+      const float4 u2 = zmulc(y2, w1), u3 = zmul_pi(zmulc(y3, w1));
+      p[0] = zadd(y0, u2);
+      p[2 * sm] = zsub(y0, u2);
+      p[sm] = zadd(y1, u3);
+      p[3 * sm] = zsub(y1, u3);
+    }
+    __syncthreads();
+  }
+}
+
+// Forward DFT (power of two: DIF, bit-reversed; else Bluestein, natural).
+// Same contract as dft_fwd.  Ends with a barrier.
+__device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
+  if (D.c == nullptr) {
+    fft_dif_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+    return;
+  }
+  const int N = D.N, M = 1 << D.logM;
+  for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    float4* p = x + q * ss + k * es;
+    *p = (k < N) ? zmulc(*p, __ldg(D.c + k)) : zzero();
+  }
+  __syncthreads();
+  fft_dif_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+  for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    float4* p = x + q * ss + k * es;
+    *p = zmul(*p, __ldg(D.Bf + k));
+  }
+  __syncthreads();
+  fft_dit_inv_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+  const float2 invM = make_float2(1.0f / (float)M, 0.f);  // exact: M is a power of two
+  for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, N, seq_fast, q, k);
+    float4* p = x + q * ss + k * es;
+    *p = zscale(zmulc(*p, __ldg(D.c + k)), invM);
+  }
+  __syncthreads();
+}
+
+// Inverse DFT (unnormalised), see dft_inv.  Ends with a barrier.
+__device__ inline void dft_inv_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
+  if (D.c == nullptr) {
+    fft_dit_inv_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+    return;
+  }
+  const int N = D.N;
+  for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, N, seq_fast, q, k);
+    float4* p = x + q * ss + k * es;
+    *p = zconj(*p);
+  }
+  __syncthreads();
+  dft_fwd_ff(x, nseq, es, ss, D, seq_fast);
+  for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, N, seq_fast, q, k);
+    float4* p = x + q * ss + k * es;
+    *p = zconj(*p);
+  }
+  __syncthreads();
+}
+
+}  // namespace db

@@ -21,6 +21,17 @@ struct RrlParams {
   int phi_robust, psi_tv;
 };
 
+// A 1D DFT of length N along one axis: a power-of-two transform of length
+// M = 2^logM (M == N), or Bluestein's form with chirp c (N values) and the
+// forward transform Bf of the circular chirp (M values, M >= 2N-1).  tw is the
+// twiddle table for length M.  All tables live in device memory.
+struct Dft1 {
+  int N, logM;
+  const float2* tw;
+  const float2* c;   // nullptr for power-of-two N
+  const float2* Bf;
+};
+
 constexpr int kMaxSide = 4096;   // largest H or W
 constexpr int kMaxTapSide = 255; // largest kh or kw
 
@@ -37,9 +48,10 @@ struct WsLayout {
   size_t ntaps;    // int: number of groups
   size_t utmp;     // float[H*W]  (RRRL ping-pong)
   size_t qbuf;     // float2[H*W] (split schedule: q1, q2)
-  size_t spec;     // float2[spec_elems]  (PSF spectrum)
-  size_t work;     // float2[work_elems]  (FFT data)
-  size_t tw;       // float2[W + H]       (twiddle tables for lengths W and H)
+  size_t spec;     // float4[spec_elems]  (PSF spectrum, float-float)
+  size_t work;     // float4[work_elems]  (Wiener rows, float-float; Fourier mode: X)
+  size_t s32;      // float2[H*W]         (Fourier mode: FP32 PSF spectrum)
+  size_t tw;       // float2[dft_table_elems(W) + dft_table_elems(H)]  (transform tables)
   size_t total;
 };
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv);
@@ -62,9 +74,13 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
                        int* status, cudaStream_t s);
 
 // PSF spectrum h^ on an H x W grid (bit-reversed order in both axes).
-cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float2* spec,
-                                const float2* twW, const float2* twH, cudaStream_t s);
-cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t s);
+struct Dft1ff;
+int dft_len_log2(int N);
+size_t dft_table_elems(int N);  // float4 units
+cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t s);
+cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float4* spec,
+                                const Dft1ff& DW, const Dft1ff& DH, cudaStream_t s);
+cudaError_t round_spectrum(const float4* in, float2* out, size_t n, cudaStream_t s);
 
 // Fourier-mode (periodic) RRRL iterations, in place on u.
 cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* utmp, int H, int W,
@@ -87,6 +103,10 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");

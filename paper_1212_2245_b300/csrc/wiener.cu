@@ -2,95 +2,133 @@
 //
 //   u0 = max( Re IDFT( DFT(f0) * conj(h^) / (|h^|^2 + K) ), delta ),  f0 = max(f, delta)
 //
-// h^ is the DFT of the PSF wrapped periodically with its origin at (0,0).
-// A PSF on one row (column) is filtered with 1D transforms along rows
-// (columns), the paper's 1D variant (Sec. 4.3); the general case uses a
-// row pass and a column pass of 1D transforms.  Two real rows (columns) are
-// packed into one complex sequence wherever the operator is applied to each
-// of them independently: multiplying by the spectrum of a real filter is
-// real-linear, so real and imaginary parts stay separate.
+// h^ is the DFT of the PSF wrapped periodically with its origin at (0,0), at
+// the native image size.  A PSF on one row (column) is filtered with 1D
+// transforms along rows (columns), the paper's 1D variant (Sec. 4.3); the
+// general case uses a row pass and a column pass of 1D transforms.  Two real
+// rows (columns) are packed into one complex sequence wherever the operator
+// is applied to each of them independently: multiplying by the spectrum of a
+// real filter is real-linear, so real and imaginary parts stay separate.
+//
+// All transform arithmetic is float-float (fft_df.cuh); the output is rounded
+// to float once.  Transform lengths: a power of two uses bit-reversed DIF/DIT
+// sweeps; any other length N uses Bluestein's chirp-z form of the same DFT,
+//   X_k = conj(c_k) sum_n (x_n conj(c_n)) c_{k-n},   c_m = exp(i pi m^2 / N),
+// evaluated as a circular convolution of length M >= 2N-1 (a power of two)
+// with the precomputed spectrum of the chirp.  Both produce the spectrum in
+// a fixed storage order (bit-reversed, resp. natural) and every spectrum
+// multiplied in goes through the same routine, so orders always match.
 #include <cuda_runtime.h>
 
-#include "fft.cuh"
+#include "fft_df.cuh"
 #include "internal.cuh"
 
 namespace db {
 
-// tw[k] = exp(-2 pi i k / N) for k < N, correctly rounded from double.
-__global__ void k_twiddles(float2* __restrict__ tw, int N) {
+// ---------------------------------------------------------------------------
+// per-axis transform tables (workspace, float4 units):
+//   [tw_ff (M) | c_ff (N) | Bf_ff (M) | tw32 (M float2 = M/2 float4)]
+// (c_ff and Bf_ff only for lengths that are not powers of two)
+// ---------------------------------------------------------------------------
+int dft_len_log2(int N) {
+  if (is_pow2(N)) return ilog2(N);
+  return ilog2(2 * N - 1);  // smallest power of two >= 2N-1
+}
+
+size_t dft_table_elems(int N) {  // in float4 units
+  const size_t M = (size_t)1 << dft_len_log2(N);
+  return (is_pow2(N) ? M : M + N + M) + (M + 1) / 2;
+}
+
+__device__ __forceinline__ float2 split_double(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// tw_ff[k] = exp(-2 pi i k / M) as float-float; tw32[k] the same rounded to
+// float (both from double).
+__global__ void k_twiddles(float4* __restrict__ tw_ff, float2* __restrict__ tw32, int M) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < N) {
+  if (k < M) {
     double s, c;
-    sincospi(-2.0 * (double)k / (double)N, &s, &c);
-    tw[k] = make_float2((float)c, (float)s);
+    sincospi(-2.0 * (double)k / (double)M, &s, &c);
+    const float2 re = split_double(c), im = split_double(s);
+    tw_ff[k] = make_float4(re.x, re.y, im.x, im.y);
+    tw32[k] = make_float2((float)c, (float)s);
   }
 }
 
-cudaError_t launch_twiddles(float2* tw, int N, cudaStream_t s) {
-  k_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
-  count_launch();
-  return cudaGetLastError();
+// Chirp c_m = exp(i pi m^2/N) for m < N (m^2 reduced mod 2N exactly), and
+// the circular sequence b of length M whose spectrum the convolution uses:
+// b_j = c_j (0 <= j < N), b_{M-j} = c_j (0 < j < N), 0 elsewhere.
+__global__ void k_chirp(float4* __restrict__ c, float4* __restrict__ b, int N, int M) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < N) {
+    const long long r = ((long long)m * m) % (2LL * N);
+    double s, co;
+    sincospi((double)r / (double)N, &s, &co);
+    const float2 re = split_double(co), im = split_double(s);
+    c[m] = make_float4(re.x, re.y, im.x, im.y);
+  }
+  if (m < M) {
+    int j = -1;
+    if (m < N) j = m;
+    else if (m > M - N) j = M - m;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j >= 0) {
+      const long long r = ((long long)j * j) % (2LL * N);
+      double s, co;
+      sincospi((double)r / (double)N, &s, &co);
+      const float2 re = split_double(co), im = split_double(s);
+      v = make_float4(re.x, re.y, im.x, im.y);
+    }
+    b[m] = v;
+  }
 }
 
-enum RowMode { ROW_PSF = 0, ROW_FWD_REAL = 1, ROW_INV_REAL = 2, ROW_WIENER_1D = 3 };
+enum RowMode { ROW_PSF = 0, ROW_FWD_REAL = 1, ROW_INV_REAL = 2, ROW_WIENER_1D = 3, ROW_FWD_CPLX = 4 };
 enum ColMode { COL_FWD = 0, COL_WIENER = 1, COL_WIENER_1D_REAL = 2 };
 
 struct FftArgs {
   const float* fin; int ldf;   // real input image
   float* uout; int ldu;        // real output image
-  float2* cbuf; int ldc;       // complex rows (row pitch ldc elements)
-  const float2* spec;          // spectrum (bit-reversed order)
+  float4* cbuf; int ldc;       // complex float-float rows (row pitch ldc elements)
+  const float4* spec;          // spectrum (storage order of the transform)
   int ldspec;
   const float* taps; int kh, kw;
-  const float2* twg;           // twiddle table for the transform length (global)
+  Dft1ff D;                    // transform along the kernel's axis
   int nrows;                   // rows (row kernels) or columns (column kernels) of data
   int img_rows;                // image rows (packed row-pair Wiener)
-  int logN;                    // log2 of the transform length
-  float K, floor_, scale;
+  float K, floor_;
+  float2 scale;                // 1/(transform size), float-float
 };
 
-// The filter is linear, so it is applied to f0 - c (c = mid-grey) and the
-// exact response c * M(0) to the constant is added back: this keeps the
-// transform's rounding error, which scales with the signal norm, smaller.
-// M(0) = S0/(S0^2 + K) with S0 the zero-frequency PSF coefficient (element 0
-// of the spectrum in bit-reversed order is frequency 0).
-constexpr float kMidGrey = 128.0f;
-
-__device__ __forceinline__ float dc_response(const float2* spec, float K) {
-  const float2 S0 = __ldg(spec);
-  return kMidGrey * (S0.x / fmaf(S0.x, S0.x, fmaf(S0.y, S0.y, K)));
+// X conj(S) / (|S|^2 + K) in float-float
+__device__ __forceinline__ float4 wiener_gain(float4 S, float4 X, float K) {
+  const float2 den = ff_add(ff_add(ff_mul(re_(S), re_(S)), ff_mul(im_(S), im_(S))), make_float2(K, 0.f));
+  const float4 t = zmulc(X, S);
+  return mkc(ff_div(re_(t), den), ff_div(im_(t), den));
 }
 
-__device__ __forceinline__ float2 wiener_gain(float2 S, float2 X, float K) {
-  // X * conj(S) / (|S|^2 + K)
-  const float den = fmaf(S.x, S.x, fmaf(S.y, S.y, K));
-  const float2 t = cmulc(X, S);
-  const float inv = 1.0f / den;
-  return make_float2(t.x * inv, t.y * inv);
-}
+__device__ __forceinline__ float ff_round(float2 v) { return v.x + v.y; }
 
-// Row transforms: each CTA owns R consecutive sequences of length N.  Global
-// inputs are staged with asynchronous copies (real inputs into the upper
-// half of each complex slot's memory first), so every load of the CTA is in
-// flight at once.
+// Row transforms: each CTA owns R consecutive sequences (capacity M each).
+// Global inputs are staged with asynchronous copies.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
-  extern __shared__ float2 smem[];
-  const int N = 1 << a.logN;
-  float2* tw = smem;
-  float2* x = smem + N;
-  float* stage = (float*)(x + R * N);  // real rows staged here (R*N floats, x2 for row pairs)
-  fft_load_twiddles(tw, a.twg, N);
-  const int q0 = blockIdx.x * R;  // first sequence of this CTA
-  // ---- load
+  extern __shared__ float4 smem4[];
+  const int N = a.D.N, logM = a.D.logM, M = 1 << logM;
+  float4* x = smem4;
+  float* stage = (float*)(x + R * M);  // real rows (x2 for row pairs)
+  const int q0 = blockIdx.x * R;
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-    const int r = idx >> a.logN, c = idx & (N - 1);
+    const int r = idx / N, c = idx - r * N;
     const int q = q0 + r;
     if (q >= a.nrows) continue;
     if (MODE == ROW_FWD_REAL) {
       cp_async4(stage + idx, a.fin + (size_t)q * a.ldf + c);
-    } else if (MODE == ROW_INV_REAL) {
-      cp_async8(x + idx, a.cbuf + (size_t)q * a.ldc + c);
+    } else if (MODE == ROW_INV_REAL || MODE == ROW_FWD_CPLX) {
+      cp_async16(x + r * M + c, a.cbuf + (size_t)q * a.ldc + c);
     } else if (MODE == ROW_WIENER_1D) {
       cp_async4(stage + 2 * idx, a.fin + (size_t)(2 * q) * a.ldf + c);
       if (2 * q + 1 < a.img_rows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)(2 * q + 1) * a.ldf + c);
@@ -98,82 +136,79 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-    const int r = idx >> a.logN, c = idx & (N - 1);
-    const int q = q0 + r;
-    float2 v = make_float2(0.f, 0.f);
-    if (q < a.nrows) {
-      if (MODE == ROW_PSF) {
-        // wrapped PSF image of a.nrows rows: row q holds tap row (q + cy) mod nrows
-        const int cy = a.kh >> 1, cx = a.kw >> 1;
-        const int ta = (q + cy) % a.nrows, tb = (c + cx) & (N - 1);
-        if (ta < a.kh && tb < a.kw) v.x = __ldg(a.taps + ta * a.kw + tb);
-      } else if (MODE == ROW_FWD_REAL) {
-        v.x = fmaxf(stage[idx], a.floor_) - kMidGrey;
-      } else if (MODE == ROW_INV_REAL) {
-        v = x[idx];
-      } else {  // ROW_WIENER_1D: sequence q packs image rows 2q and 2q+1
-        v.x = fmaxf(stage[2 * idx], a.floor_) - kMidGrey;
-        if (2 * q + 1 < a.img_rows) v.y = fmaxf(stage[2 * idx + 1], a.floor_) - kMidGrey;
+  if (MODE != ROW_INV_REAL && MODE != ROW_FWD_CPLX) {
+    for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+      const int r = idx / N, c = idx - r * N;
+      const int q = q0 + r;
+      float4 v = zzero();
+      if (q < a.nrows) {
+        if (MODE == ROW_PSF) {
+          // wrapped PSF image of a.nrows rows: row q holds tap row (q + cy) mod nrows
+          const int cy = a.kh >> 1, cx = a.kw >> 1;
+          const int ta = (q + cy) % a.nrows, tb = (c + cx) % N;
+          if (ta < a.kh && tb < a.kw) v.x = __ldg(a.taps + ta * a.kw + tb);
+        } else if (MODE == ROW_FWD_REAL) {
+          v.x = fmaxf(stage[idx], a.floor_);
+        } else {  // ROW_WIENER_1D: sequence q packs image rows 2q and 2q+1
+          v.x = fmaxf(stage[2 * idx], a.floor_);
+          if (2 * q + 1 < a.img_rows) v.z = fmaxf(stage[2 * idx + 1], a.floor_);
+        }
       }
+      x[r * M + c] = v;
     }
-    x[idx] = v;
   }
   __syncthreads();
-  // ---- transform
   if (MODE == ROW_INV_REAL) {
-    fft_dit_inv(x, a.logN, R, 1, N, tw, 0, false);
+    dft_inv_ff(x, R, 1, M, a.D, false);
   } else {
-    fft_dif(x, a.logN, R, 1, N, tw, 0, false);
+    dft_fwd_ff(x, R, 1, M, a.D, false);
     if (MODE == ROW_WIENER_1D) {
       for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-        const int c = idx & (N - 1);
-        x[idx] = wiener_gain(__ldg(&a.spec[c]), x[idx], a.K);
+        const int r = idx / N, c = idx - r * N;
+        x[r * M + c] = wiener_gain(__ldg(&a.spec[c]), x[r * M + c], a.K);
       }
       __syncthreads();
-      fft_dit_inv(x, a.logN, R, 1, N, tw, 0, false);
+      dft_inv_ff(x, R, 1, M, a.D, false);
     }
   }
-  // ---- store
-  const float dc = (MODE == ROW_INV_REAL || MODE == ROW_WIENER_1D) ? dc_response(a.spec, a.K) : 0.f;
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-    const int r = idx >> a.logN, c = idx & (N - 1);
+    const int r = idx / N, c = idx - r * N;
     const int q = q0 + r;
     if (q >= a.nrows) continue;
-    const float2 v = x[idx];
-    if (MODE == ROW_PSF || MODE == ROW_FWD_REAL) {
+    const float4 v = x[r * M + c];
+    if (MODE == ROW_PSF || MODE == ROW_FWD_REAL || MODE == ROW_FWD_CPLX) {
       a.cbuf[(size_t)q * a.ldc + c] = v;
     } else if (MODE == ROW_INV_REAL) {
-      a.uout[(size_t)q * a.ldu + c] = fmaxf(fmaf(v.x, a.scale, dc), a.floor_);
+      a.uout[(size_t)q * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
     } else {
-      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(fmaf(v.x, a.scale, dc), a.floor_);
-      if (2 * q + 1 < a.img_rows) a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(fmaf(v.y, a.scale, dc), a.floor_);
+      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
+      if (2 * q + 1 < a.img_rows)
+        a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
     }
   }
 }
 
 // Column transforms: each CTA owns C adjacent sequences laid out across a row
-// (element stride C in shared memory).  For COL_WIENER_1D_REAL, sequence c
-// packs image columns 2c and 2c+1 and a.nrows counts the image columns.
+// (element stride C in shared memory, capacity M each).  For
+// COL_WIENER_1D_REAL, sequence c packs image columns 2c and 2c+1 and a.nrows
+// counts the image columns.
 template <int MODE, int C>
 __global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
-  extern __shared__ float2 smem[];
-  const int N = 1 << a.logN;
-  float2* tw = smem;
-  float2* x = smem + N;
-  float* stage = (float*)(x + N * C);  // COL_WIENER_1D_REAL: 2*C real columns
-  fft_load_twiddles(tw, a.twg, N);
-  const int c0 = blockIdx.x * C;  // first sequence
+  extern __shared__ float4 smem4[];
+  const int N = a.D.N, logM = a.D.logM, M = 1 << logM;
+  float4* x = smem4;
+  float* stage = (float*)(x + M * C);  // COL_WIENER_1D_REAL: 2*C real columns
+  const int c0 = blockIdx.x * C;
   const int nseq_total = (MODE == COL_WIENER_1D_REAL) ? (a.nrows + 1) / 2 : a.nrows;
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-    const int k = idx / C, c = idx - (idx / C) * C;
+    const int k = idx / C, c = idx - k * C;
     const int q = c0 + c;
     if (q >= nseq_total) continue;
     if (MODE == COL_WIENER_1D_REAL) {
       cp_async4(stage + 2 * idx, a.fin + (size_t)k * a.ldf + 2 * q);
       if (2 * q + 1 < a.nrows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)k * a.ldf + 2 * q + 1);
     } else {
-      cp_async8(x + idx, a.cbuf + (size_t)k * a.ldc + q);
+      cp_async16(x + idx, a.cbuf + (size_t)k * a.ldc + q);
     }
   }
   cp_async_wait_all();
@@ -182,98 +217,156 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
     const int c = idx - (idx / C) * C;
     const int q = c0 + c;
     if (q >= nseq_total) {
-      x[idx] = make_float2(0.f, 0.f);
+      x[idx] = zzero();
     } else if (MODE == COL_WIENER_1D_REAL) {
-      float2 v;
-      v.x = fmaxf(stage[2 * idx], a.floor_) - kMidGrey;
-      v.y = (2 * q + 1 < a.nrows) ? fmaxf(stage[2 * idx + 1], a.floor_) - kMidGrey : 0.f;
+      float4 v = zzero();
+      v.x = fmaxf(stage[2 * idx], a.floor_);
+      if (2 * q + 1 < a.nrows) v.z = fmaxf(stage[2 * idx + 1], a.floor_);
       x[idx] = v;
     }
   }
   __syncthreads();
-  fft_dif(x, a.logN, C, C, 1, tw, 0, true);
+  dft_fwd_ff(x, C, C, 1, a.D, true);
   if (MODE != COL_FWD) {
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-      const int k = idx / C, c = idx - (idx / C) * C;
+      const int k = idx / C, c = idx - k * C;
       const int q = c0 + c;
       if (q >= nseq_total) continue;
-      const float2 S = (MODE == COL_WIENER) ? __ldg(&a.spec[(size_t)k * a.ldspec + q]) : __ldg(&a.spec[k]);
+      const float4 S = (MODE == COL_WIENER) ? __ldg(&a.spec[(size_t)k * a.ldspec + q]) : __ldg(&a.spec[k]);
       x[idx] = wiener_gain(S, x[idx], a.K);
     }
     __syncthreads();
-    fft_dit_inv(x, a.logN, C, C, 1, tw, 0, true);
+    dft_inv_ff(x, C, C, 1, a.D, true);
   }
-  const float dc = (MODE == COL_WIENER_1D_REAL) ? dc_response(a.spec, a.K) : 0.f;
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-    const int k = idx / C, c = idx - (idx / C) * C;
+    const int k = idx / C, c = idx - k * C;
     const int q = c0 + c;
     if (q >= nseq_total) continue;
-    const float2 v = x[idx];
+    const float4 v = x[idx];
     if (MODE == COL_WIENER_1D_REAL) {
-      a.uout[(size_t)k * a.ldu + 2 * q] = fmaxf(fmaf(v.x, a.scale, dc), a.floor_);
-      if (2 * q + 1 < a.nrows) a.uout[(size_t)k * a.ldu + 2 * q + 1] = fmaxf(fmaf(v.y, a.scale, dc), a.floor_);
+      a.uout[(size_t)k * a.ldu + 2 * q] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
+      if (2 * q + 1 < a.nrows)
+        a.uout[(size_t)k * a.ldu + 2 * q + 1] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
     } else {
       a.cbuf[(size_t)k * a.ldc + q] = v;
     }
   }
 }
 
+static constexpr size_t kSmemLimit = 227 * 1024;
+
 template <typename Kern>
-static cudaError_t launch_smem(Kern k, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                               const FftArgs& a) {
+static cudaError_t set_dyn_smem(Kern k, size_t smem) {
+  if (smem > kSmemLimit) return cudaErrorInvalidValue;  // never reaches the runtime
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return e; }
   }
-  k<<<grid, block, smem, s>>>(a);
-  count_launch();
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <int MODE>
 static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
-  const int N = 1 << a.logN;
-  const int R = N >= 2048 ? 1 : 2048 / N;
+  const int M = 1 << a.D.logM;
+  const int R = M >= 2048 ? 1 : 2048 / M;
   const int grid = (a.nrows + R - 1) / R;
-  const size_t smem = (size_t)(N + R * N) * sizeof(float2) + (size_t)2 * R * N * sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_fft_rows<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = (size_t)R * M * sizeof(float4) + (size_t)2 * R * a.D.N * sizeof(float);
+  cudaError_t e = set_dyn_smem(k_fft_rows<MODE>, smem);
+  if (e != cudaSuccess) return e;
   k_fft_rows<MODE><<<grid, 256, smem, s>>>(a, R);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int MODE, int C>
+static cudaError_t launch_cols_c(FftArgs a, int nseq, cudaStream_t s) {
+  const int M = 1 << a.D.logM;
+  const size_t st = (MODE == COL_WIENER_1D_REAL) ? 1 : 0;  // real staging only for packed real columns
+  const size_t smem = (size_t)C * M * sizeof(float4) + st * 2 * C * a.D.N * sizeof(float);
+  cudaError_t e = set_dyn_smem(k_fft_cols<MODE, C>, smem);
+  if (e != cudaSuccess) return e;
+  k_fft_cols<MODE, C><<<(nseq + C - 1) / C, 256, smem, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
-  const int N = 1 << a.logN;
-  const size_t st = (MODE == COL_WIENER_1D_REAL) ? 1 : 0;  // real staging only for packed real columns
-  if (N <= 1024) {
-    constexpr int C = 8;
-    const size_t smem = (size_t)(N + C * N) * sizeof(float2) + st * 2 * C * N * sizeof(float);
-    return launch_smem(k_fft_cols<MODE, C>, dim3((nseq + C - 1) / C), dim3(256), smem, s, a);
-  } else if (N <= 2048) {
-    constexpr int C = 4;
-    const size_t smem = (size_t)(N + C * N) * sizeof(float2) + st * 2 * C * N * sizeof(float);
-    return launch_smem(k_fft_cols<MODE, C>, dim3((nseq + C - 1) / C), dim3(256), smem, s, a);
-  } else {
-    constexpr int C = 2;
-    const size_t smem = (size_t)(N + C * N) * sizeof(float2) + st * 2 * C * N * sizeof(float);
-    return launch_smem(k_fft_cols<MODE, C>, dim3((nseq + C - 1) / C), dim3(256), smem, s, a);
-  }
+  const int M = 1 << a.D.logM;
+  if (M <= 1024) return launch_cols_c<MODE, 8>(a, nseq, s);
+  if (M <= 2048) return launch_cols_c<MODE, 4>(a, nseq, s);
+  if (M <= 4096) return launch_cols_c<MODE, 2>(a, nseq, s);
+  return launch_cols_c<MODE, 1>(a, nseq, s);
 }
 
-cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float2* spec,
-                                const float2* twW, const float2* twH, cudaStream_t s) {
+// Fill the tables of a length-N axis in `tab` (dft_table_elems(N) float4s).
+// `ff` receives the float-float descriptor, `f32` (optional) the FP32
+// twiddles for the power-of-two sweeps of fft.cuh.
+cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t s) {
+  Dft1ff D;
+  D.N = N;
+  D.logM = dft_len_log2(N);
+  const int M = 1 << D.logM;
+  D.tw = tab;
+  D.c = nullptr;
+  D.Bf = nullptr;
+  float4* rest = tab + M;
+  if (!is_pow2(N)) rest += (size_t)N + M;
+  float2* tw32 = (float2*)rest;
+  k_twiddles<<<(M + 255) / 256, 256, 0, s>>>(tab, tw32, M);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (!is_pow2(N)) {
+    float4* c = tab + M;
+    float4* Bf = c + N;
+    k_chirp<<<(M + 255) / 256, 256, 0, s>>>(c, Bf, N, M);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Bf <- forward power-of-two transform of the circular chirp (in place)
+    FftArgs a = {};
+    Dft1ff P;
+    P.N = M; P.logM = D.logM; P.tw = tab; P.c = nullptr; P.Bf = nullptr;
+    a.D = P; a.cbuf = Bf; a.ldc = M; a.nrows = 1;
+    if ((e = launch_rows<ROW_FWD_CPLX>(a, s)) != cudaSuccess) return e;
+    D.c = c;
+    D.Bf = Bf;
+  }
+  if (ff) *ff = D;
+  if (f32) {
+    f32->N = N; f32->logM = D.logM; f32->tw = tw32; f32->c = nullptr; f32->Bf = nullptr;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float4* spec,
+                                const Dft1ff& DW, const Dft1ff& DH, cudaStream_t s) {
   FftArgs a = {};
-  a.taps = taps; a.kh = kh; a.kw = kw; a.nrows = H; a.logN = ilog2(W);
-  a.cbuf = spec; a.ldc = W; a.twg = twW;
+  a.taps = taps; a.kh = kh; a.kw = kw; a.nrows = H; a.D = DW;
+  a.cbuf = spec; a.ldc = W;
   cudaError_t e;
   if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
   FftArgs c = {};
-  c.cbuf = spec; c.ldc = W; c.nrows = W; c.logN = ilog2(H); c.twg = twH;
+  c.cbuf = spec; c.ldc = W; c.nrows = W; c.D = DH;
   return launch_cols<COL_FWD>(c, W, s);
+}
+
+__global__ void k_round_spectrum(const float4* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = in[k];
+    out[k] = make_float2(v.x + v.y, v.z + v.w);
+  }
+}
+
+cudaError_t round_spectrum(const float4* in, float2* out, size_t n, cudaStream_t s) {
+  k_round_spectrum<<<592, 256, 0, s>>>(in, out, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+static float2 ff_const(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
 }
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps, int kh,
@@ -281,52 +374,51 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
                        cudaStream_t s) {
   (void)status;
   char* base = (char*)ws;
-  float2* spec = (float2*)(base + L.spec);
-  float2* work = (float2*)(base + L.work);
-  float2* twW = (float2*)(base + L.tw);
-  float2* twH = twW + W;
+  float4* spec = (float4*)(base + L.spec);
+  float4* work = (float4*)(base + L.work);
+  float4* tabW = (float4*)(base + L.tw);
+  float4* tabH = tabW + dft_table_elems(W);
   cudaError_t e;
-  if (kw > 1 || kh == 1) { if ((e = launch_twiddles(twW, W, s)) != cudaSuccess) return e; }
-  if (kh > 1) { if ((e = launch_twiddles(twH, H, s)) != cudaSuccess) return e; }
+  Dft1ff DW = {}, DH = {};
+  if (kw > 1 || kh == 1) { if ((e = prepare_dft(W, tabW, &DW, nullptr, s)) != cudaSuccess) return e; }
+  if (kh > 1) { if ((e = prepare_dft(H, tabH, &DH, nullptr, s)) != cudaSuccess) return e; }
   FftArgs a = {};
   a.K = K;
   a.floor_ = floor_;
   if (kh == 1) {
     // PSF along rows: 1D spectrum of length W, then packed row pairs.
-    a.taps = taps; a.kh = 1; a.kw = kw; a.nrows = 1; a.logN = ilog2(W);
-    a.cbuf = spec; a.ldc = W; a.twg = twW;
+    a.taps = taps; a.kh = 1; a.kw = kw; a.nrows = 1; a.D = DW;
+    a.cbuf = spec; a.ldc = W;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.twg = twW;
-    b.nrows = (H + 1) / 2; b.img_rows = H; b.logN = ilog2(W);
-    b.K = K; b.floor_ = floor_; b.scale = 1.0f / (float)W;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = DW;
+    b.nrows = (H + 1) / 2; b.img_rows = H;
+    b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / W);
     return launch_rows<ROW_WIENER_1D>(b, s);
   }
   if (kw == 1) {
     // PSF along columns: 1D spectrum of length H (a kh x 1 tap array has the
     // memory layout of a 1 x kh row), then packed column pairs.
-    a.taps = taps; a.kh = 1; a.kw = kh; a.nrows = 1; a.logN = ilog2(H);
-    a.cbuf = spec; a.ldc = H; a.twg = twH;
+    a.taps = taps; a.kh = 1; a.kw = kh; a.nrows = 1; a.D = DH;
+    a.cbuf = spec; a.ldc = H;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.twg = twH;
-    b.nrows = W; b.logN = ilog2(H);
-    b.K = K; b.floor_ = floor_; b.scale = 1.0f / (float)H;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = DH;
+    b.nrows = W;
+    b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / H);
     return launch_cols<COL_WIENER_1D_REAL>(b, (W + 1) / 2, s);
   }
   // General 2D PSF: spectrum (rows then columns), then the image.
-  if ((e = run_psf_spectrum_2d(taps, kh, kw, H, W, spec, twW, twH, s)) != cudaSuccess) return e;
+  if ((e = run_psf_spectrum_2d(taps, kh, kw, H, W, spec, DW, DH, s)) != cudaSuccess) return e;
   FftArgs d = {};
-  d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = W; d.nrows = H; d.logN = ilog2(W); d.floor_ = floor_;
-  d.twg = twW;
+  d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = W; d.nrows = H; d.D = DW; d.floor_ = floor_;
   if ((e = launch_rows<ROW_FWD_REAL>(d, s)) != cudaSuccess) return e;
   FftArgs g = {};
-  g.cbuf = work; g.ldc = W; g.spec = spec; g.ldspec = W; g.nrows = W; g.logN = ilog2(H); g.K = K;
-  g.twg = twH;
+  g.cbuf = work; g.ldc = W; g.spec = spec; g.ldspec = W; g.nrows = W; g.D = DH; g.K = K;
   if ((e = launch_cols<COL_WIENER>(g, W, s)) != cudaSuccess) return e;
   FftArgs o = {};
-  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.logN = ilog2(W); o.twg = twW;
-  o.floor_ = floor_; o.scale = 1.0f / ((float)H * (float)W); o.spec = spec; o.K = K;
+  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.D = DW;
+  o.floor_ = floor_; o.scale = ff_const(1.0 / ((double)H * (double)W)); o.spec = spec; o.K = K;
   return launch_rows<ROW_INV_REAL>(o, s);
 }
 

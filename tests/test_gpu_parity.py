@@ -150,7 +150,10 @@ def test_parameter_variants(lib, variant):
 
 @pytest.mark.parametrize("H,W,shape", [(128, 256, (1, 15)), (256, 128, (9, 1)), (64, 512, (5, 7)),
                                        (512, 64, (17, 27)), (1, 256, (1, 31)), (256, 1, (7, 1)),
-                                       (2, 2, (1, 1)), (4096, 16, (3, 5))])
+                                       (2, 2, (1, 1)), (4096, 16, (3, 5)),
+                                       (100, 150, (1, 15)), (77, 64, (9, 1)), (129, 127, (5, 7)),
+                                       (1021, 48, (1, 41)), (40, 1021, (25, 25)), (3, 5, (1, 3)),
+                                       (1000, 1000, (25, 25)), (4095, 33, (9, 1)), (1, 1, (1, 1))])
 def test_wiener_shapes(lib, H, W, shape):
     rng = np.random.default_rng(H + W)
     h = rng.uniform(0.1, 1.0, size=shape)
@@ -162,6 +165,20 @@ def test_wiener_shapes(lib, H, W, shape):
                                                          torch.tensor(h, dtype=torch.float64), p.K), p.pos_floor)
     u0 = lib.wiener(cuda(f), cuda(h), p)
     assert_close(u0, ref, f"wiener {H}x{W} psf {shape}")
+
+
+@pytest.mark.parametrize("index", [0, 1, 2, 3, 256, 257, 300, 511])
+def test_uneven_batch_images_single_calls(lib, index):
+    """Images of the uneven batch (non-power-of-two sides, 1D box / raised
+    cosine or 2D Gaussian-mixture PSFs) through the single-image pipeline."""
+    case = synth.batch_case(index)
+    f, h = cuda(case.f), cuda(case.h)
+    u0_ref, u_ref = oracle_pipeline(case)
+    u0 = lib.wiener(f, h, case.params, kind=case.psf_kind)
+    m0, r0 = assert_close(u0, u0_ref, f"{case.name} {case.f.shape} Wiener")
+    u = lib.rrl_iterate(f, u0.clone(), h, case.params, case.iters, kind=case.psf_kind)
+    m, r = assert_close(u, u_ref, f"{case.name} {case.f.shape} psf {case.h.shape} WR3L")
+    print(f"{case.name} {case.f.shape} psf {case.h.shape}: Wiener {m0:.2e}/{r0:.2e} WR3L {m:.2e}/{r:.2e}")
 
 
 def test_checkpoints_hold_intermediate_iterates(lib, sched):
