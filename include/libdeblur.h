@@ -132,6 +132,52 @@ db_status db_deblur(const float* f, float* u, int H, int W, int ld,
                     const db_psf* psf, const db_params* p, int iters,
                     void* ws, size_t ws_bytes, int* dev_status, void* stream);
 
+/* ---- batches of images ----------------------------------------------------
+ * Many images of uneven sizes, each with its own PSF and parameters (spatial
+ * mode only), deblurred by the whole WR3L pipeline of db_deblur: one image's
+ * result is the same as db_deblur's for that image.  No counterpart in the
+ * paper (its closest relative is the persistent worker threads of Sec. 4.5).
+ * A plan (db_batch_create) precomputes every transform table, PSF spectrum
+ * and tap list and uploads the work tables into the workspace; running it
+ * (db_batch_run) enqueues only launches and memsets, so it can be captured
+ * in a CUDA graph and replayed.  The run is five batched Wiener launches and
+ * one cooperative persistent launch for all RRRL iterations of all images,
+ * whose grid barriers wait a bounded time (db_set_spin_limit) and raise
+ * DB_FLAG_TIMEOUT instead of hanging.  The plan holds pointers into the
+ * workspace and to the images: keep them alive and unchanged in shape while
+ * the plan is used; pixel values may change between runs. */
+typedef struct {
+  const float* f;    /* DEVICE, H x W, pitch ld */
+  float* u;          /* DEVICE, result, same layout; may not alias f */
+  int H, W, ld;
+  db_psf psf;
+  db_params p;       /* p.conv must be DB_CONV_CLAMP */
+} db_image_desc;
+
+typedef struct db_batch db_batch;  /* opaque host-side plan */
+
+/* Workspace bytes for the batch (descs: HOST array of n descriptors); 0 if a
+ * descriptor is invalid. */
+size_t db_batch_workspace_bytes(const db_image_desc* descs, int n, int iters);
+
+/* Build the plan (enqueues set-up work and host-to-device copies on stream;
+ * not capturable).  On success *out owns a host object: db_batch_destroy. */
+db_status db_batch_create(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
+                          int* dev_status, void* stream, db_batch** out);
+
+/* Run the planned batch on stream (capturable). */
+db_status db_batch_run(db_batch* b, int* dev_status, void* stream);
+
+void db_batch_destroy(db_batch* b);
+
+/* db_batch_create + db_batch_run + db_batch_destroy. */
+db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
+                          int* dev_status, void* stream);
+
+/* Clock-cycle budget of every bounded device wait (grid barriers of the
+ * batch kernel); default 4e9 (about two seconds). */
+db_status db_set_spin_limit(long long cycles);
+
 /* Allocation-free RRRL iterations (no counterpart in the paper; an interface
  * convenience).  Some callers cannot allocate device memory at run time:
  * a deblurring step embedded in a fixed-latency frame loop (an inspection

@@ -16,7 +16,8 @@ from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "rrl_iterate_noalloc", "set_schedule", "version"]
+           "deblur", "Batch", "deblur_batch", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
+           "version"]
 
 
 class DeblurError(RuntimeError):
@@ -155,6 +156,77 @@ def deblur(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, k
     if check:
         ws.raise_on_flags("db_deblur")
     return u
+
+
+class Batch:
+    """A planned batch of images (uneven sizes, own PSF and parameters each):
+    `run()` deblurs all of them (Wiener + `iters` RRRL) with five batched
+    Wiener launches and one persistent RRRL launch; it enqueues launches and
+    memsets only, so it can be captured in a CUDA graph.  The plan refers to
+    the given tensors: keep them alive; their values may change between runs."""
+
+    def __init__(self, fs, taps, params, iters, *, kinds=None, outs=None):
+        n = len(fs)
+        if not (len(taps) == n and (not isinstance(params, (list, tuple)) or len(params) == n)):
+            raise ValueError("fs, taps and params must have the same length")
+        params = list(params) if isinstance(params, (list, tuple)) else [params] * n
+        kinds = list(kinds) if kinds is not None else ["general"] * n
+        self.fs = list(fs)
+        self.taps = list(taps)
+        self.us = list(outs) if outs is not None else [torch.empty_like(f) for f in self.fs]
+        descs = (_lib.DbImageDesc * n)()
+        for k in range(n):
+            H, W, ld = _image(self.fs[k], "f")
+            if _image(self.us[k], "u")[2] != ld or self.us[k].shape != self.fs[k].shape:
+                raise ValueError("outputs must match the inputs' shapes and row strides")
+            descs[k] = _lib.DbImageDesc(self.fs[k].data_ptr(), self.us[k].data_ptr(), H, W, ld,
+                                        _db_psf(self.taps[k], kinds[k]), _db_params(params[k]))
+        self._descs = descs
+        lib = _lib.load()
+        nbytes = lib.db_batch_workspace_bytes(descs, n, int(iters))
+        if nbytes == 0:
+            raise DeblurError("invalid batch descriptors")
+        self.ws = Workspace(nbytes)
+        self.ws.reset_status()
+        handle = ctypes.c_void_p()
+        _check(lib.db_batch_create(descs, n, int(iters), self.ws.ptr, self.ws.nbytes,
+                                   self.ws.status.data_ptr(), _stream(), ctypes.byref(handle)),
+               "db_batch_create")
+        self._h = handle
+        self.iters = iters
+
+    def run(self, check: bool = True):
+        if check:
+            self.ws.reset_status()
+        _check(_lib.load().db_batch_run(self._h, self.ws.status.data_ptr(), _stream()), "db_batch_run")
+        if check:
+            self.ws.raise_on_flags("db_batch_run")
+        return self.us
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().db_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def deblur_batch(fs, taps, params, iters, *, kinds=None, outs=None, check: bool = True):
+    """Deblur a list of images in one batched run; returns the outputs."""
+    b = Batch(fs, taps, params, iters, kinds=kinds, outs=outs)
+    try:
+        return b.run(check=check)
+    finally:
+        b.close()
+
+
+def set_spin_limit(cycles: int):
+    """Clock-cycle budget of the library's bounded device waits."""
+    _check(_lib.load().db_set_spin_limit(int(cycles)), "db_set_spin_limit")
 
 
 def rrl_iterate_noalloc(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, params: Params,

@@ -26,6 +26,11 @@ SCHED_AUTO, SCHED_FUSED, SCHED_SPLIT = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 32 << 20  # DB_NOALLOC_SCRATCH_BYTES
 FLAG_TAPS, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOX = 0x1, 0x2, 0x4, 0x8
 
+class DbImageDesc(ctypes.Structure):
+    _fields_ = [("f", c_void_p), ("u", c_void_p), ("H", c_int), ("W", c_int), ("ld", c_int),
+                ("psf", DbPsf), ("p", DbParams)]
+
+
 P_PSF = ctypes.POINTER(DbPsf)
 P_PAR = ctypes.POINTER(DbParams)
 
@@ -40,6 +45,14 @@ SIGNATURES = {
                           c_size_t, c_void_p, c_void_p]),
     "db_rrl_iterate_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, P_PSF, P_PAR, c_int,
                                        c_void_p, c_void_p]),
+    "db_batch_workspace_bytes": (c_size_t, [ctypes.POINTER(DbImageDesc), c_int, c_int]),
+    "db_batch_create": (c_int, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_void_p, c_size_t, c_void_p,
+                                c_void_p, ctypes.POINTER(c_void_p)]),
+    "db_batch_run": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "db_batch_destroy": (None, [c_void_p]),
+    "db_deblur_batch": (c_int, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_void_p, c_size_t, c_void_p,
+                                c_void_p]),
+    "db_set_spin_limit": (c_int, [ctypes.c_longlong]),
     "db_status_string": (c_char_p, [c_int]),
     "db_status_from_flags": (c_int, [c_int]),
     "db_version": (c_char_p, []),

@@ -1,0 +1,421 @@
+// Batched WR3L: many images of uneven sizes, each with its own PSF and
+// parameters, deblurred together (no counterpart in the paper; the closest is
+// its persistent worker threads, Sec. 4.5).  The arithmetic per image is
+// exactly the single-image pipeline's (same tile bodies, same transforms).
+//
+// Plan (host, once): per-axis transform tables, tap groups and PSF spectra
+// for every image, the batched-Wiener job tables, a table of RRRL tiles over
+// all images (sorted by cost), all uploaded into the caller's workspace.
+// Run (capturable: stream-ordered launches and memsets only):
+//   1. five batched Wiener launches (one per transform stage);
+//   2. one cooperative persistent launch that performs every RRRL iteration
+//      of every image: per iteration a q-phase and an update-phase over all
+//      tiles, tiles taken from an atomic work queue, phases separated by a
+//      grid barrier whose wait is bounded (on time-out it raises
+//      DB_FLAG_TIMEOUT and the kernel returns).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <vector>
+
+#include "fft_df.cuh"
+#include "internal.cuh"
+#include "rrl_tiles.cuh"
+
+namespace db {
+
+struct BatchImg {
+  const float* f;
+  float* A;      // holds u0; written by odd iterations
+  float* B;      // written by even iterations
+  float2* q;     // (e, W), pitch W
+  const TapGroup* groups;
+  const int* ngroups;
+  int ldf, ldA, ldB;
+  int H, W, kh, kw, ng_max, M, P;
+  RrlParams p;
+};
+
+constexpr int kBTH = 32, kBTW = 64, kBR = 8;  // tiles of the split schedule
+
+template <int M, int P>
+__device__ __noinline__ void batch_q(unsigned char* smem, const BatchImg& im, const float* src, int lds,
+                                     int i0, int j0) {
+  q_tile<kBTH, kBTW, kBR, M, P>(smem, im.f, im.ldf, src, lds, im.q, im.W, im.H, im.W, im.groups,
+                                im.ngroups, im.kh, im.kw, im.ng_max, im.p, i0, j0);
+}
+
+template <int M, int P>
+__device__ __noinline__ void batch_u(unsigned char* smem, const BatchImg& im, const float* src, int lds,
+                                     float* dst, int ldd, int* status, int i0, int j0) {
+  update_tile<kBTH, kBTW, kBR, M, P>(smem, im.q, im.W, src, lds, dst, ldd, im.H, im.W, im.groups,
+                                     im.ngroups, im.kh, im.kw, im.ng_max, im.p, status, i0, j0);
+}
+
+template <int M>
+__device__ __forceinline__ void batch_tile_m(int phase, unsigned char* smem, const BatchImg& im,
+                                             const float* src, int lds, float* dst, int ldd, int* status,
+                                             int i0, int j0) {
+#define DB_BATCH_CASE(PV)                                              \
+  case PV:                                                             \
+    if (phase == 0) batch_q<M, PV>(smem, im, src, lds, i0, j0);        \
+    else batch_u<M, PV>(smem, im, src, lds, dst, ldd, status, i0, j0); \
+    break;
+  switch (im.P) {
+    DB_BATCH_CASE(8)
+    DB_BATCH_CASE(16)
+    DB_BATCH_CASE(32)
+    DB_BATCH_CASE(64)
+    DB_BATCH_CASE(128)
+    default: DB_BATCH_CASE(256)
+  }
+#undef DB_BATCH_CASE
+}
+
+// Grid-wide barrier for a cooperatively launched grid.  bar[0] counts
+// arrivals, bar[1] is the generation.  The wait is bounded by `limit` clock
+// cycles; returns false (and raises DB_FLAG_TIMEOUT) if it gave up.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > limit) {
+          ok = 0;
+          if (status) atomicOr(status, DB_FLAG_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_rrl_batch(const BatchImg* __restrict__ imgs,
+                                                   const int4* __restrict__ tiles, int ntiles, int iters,
+                                                   unsigned* bar, int* work, int* status,
+                                                   long long spin_limit) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_t;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int k = 0; k < iters; ++k) {
+    const bool even = (k & 1) == 0;
+    for (int phase = 0; phase < 2; ++phase) {
+      while (true) {
+        if (tid == 0) s_t = atomicAdd(work + 2 * k + phase, 1);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const int4 T = tiles[t];
+        const BatchImg im = imgs[T.x];
+        const float* src = even ? im.A : im.B;
+        const int lds = even ? im.ldA : im.ldB;
+        float* dst = even ? im.B : im.A;
+        const int ldd = even ? im.ldB : im.ldA;
+        switch (im.M) {
+          case 1: batch_tile_m<1>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
+          case 2: batch_tile_m<2>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
+          default: batch_tile_m<3>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(bar, gridDim.x, status, spin_limit)) return;
+    }
+  }
+}
+
+static std::atomic<long long> g_spin_limit{4000000000LL};  // ~2 s at 2 GHz
+
+void set_spin_limit(long long cycles) { g_spin_limit.store(cycles); }
+
+// ---------------------------------------------------------------------------
+// host plan
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+  int n = 0, iters = 0;
+  WienerBatch* wb = nullptr;
+  std::vector<BatchImg> imgs;
+  std::vector<int4> tiles;
+  BatchImg* d_imgs = nullptr;
+  int4* d_tiles = nullptr;
+  unsigned* d_bar = nullptr;
+  int* d_work = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  ~BatchPlan() { if (wb) wiener_batch_delete(wb); }
+};
+
+static int halo_class_b(int kw) {
+  const int need = kw - 1 > 2 ? kw - 1 : 2;
+  int P = 8;
+  while (P < need) P *= 2;
+  return P;
+}
+
+// Per-image workspace regions, laid out in order.
+struct ImgRegions {
+  size_t groups, ngroups, utmp, q, spec, work, end;
+};
+
+static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
+  ImgRegions r;
+  r.groups = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
+  r.ngroups = off; off += 256;
+  r.utmp = off;    off += align256((size_t)H * W * sizeof(float));
+  r.q = off;       off += align256((size_t)H * W * sizeof(float2));
+  size_t spec = (kh == 1) ? (size_t)W : (kw == 1) ? (size_t)H : (size_t)H * W;
+  r.spec = off;    off += align256(spec * sizeof(float4));
+  r.work = off;    off += (kh > 1 && kw > 1) ? align256((size_t)H * W * sizeof(float4)) : 0;
+  r.end = off;
+  return r;
+}
+
+static size_t count_tiles(int H, int W) {
+  return (size_t)((H + kBTH - 1) / kBTH) * ((W + kBTW - 1) / kBTW);
+}
+
+// Bytes of workspace the whole batch needs; 0 if any descriptor is invalid.
+size_t batch_ws_bytes(const db_image_desc* d, int n, int iters, db_status* why) {
+  *why = DB_OK;
+  if (!d || n < 1 || iters < 0) { *why = DB_ERR_ARG; return 0; }
+  size_t off = 0;
+  std::map<int, bool> lens;
+  size_t ntiles = 0, nitems = 0;
+  for (int i = 0; i < n; ++i) {
+    const db_image_desc& x = d[i];
+    if (!x.f || !x.u || !x.psf.taps) { *why = DB_ERR_ARG; return 0; }
+    if (x.H < 1 || x.W < 1 || x.H > kMaxSide || x.W > kMaxSide || x.ld < x.W) { *why = DB_ERR_SHAPE; return 0; }
+    if (x.psf.kh < 1 || x.psf.kw < 1 || x.psf.kh > kMaxTapSide || x.psf.kw > kMaxTapSide ||
+        x.psf.kh > x.H || x.psf.kw > x.W) { *why = DB_ERR_PSF; return 0; }
+    if (x.psf.kind == DB_PSF_BOX && x.psf.kh != 1 && x.psf.kw != 1) { *why = DB_ERR_PSF; return 0; }
+    if (x.psf.kind != DB_PSF_GENERAL && x.psf.kind != DB_PSF_BOX) { *why = DB_ERR_ARG; return 0; }
+    if (!(x.p.K > 0.f) || !(x.p.alpha >= 0.f) || !(x.p.eps_phi > 0.f) || !(x.p.eps_psi > 0.f) ||
+        !(x.p.pos_floor > 0.f) || (x.p.phi_robust != 0 && x.p.phi_robust != 1) ||
+        (x.p.psi_tv != 0 && x.p.psi_tv != 1)) { *why = DB_ERR_ARG; return 0; }
+    if (x.p.conv != DB_CONV_CLAMP) { *why = DB_ERR_UNSUPPORTED; return 0; }
+    if (x.f == x.u) { *why = DB_ERR_ARG; return 0; }
+    if (rrl_split_smem_q(x.psf.kh, x.psf.kw) > 227 * 1024 || rrl_split_smem_update(x.psf.kh, x.psf.kw) > 227 * 1024) {
+      *why = DB_ERR_UNSUPPORTED; return 0;
+    }
+    off = image_regions(off, x.H, x.W, x.psf.kh, x.psf.kw).end;
+    if (x.psf.kw > 1 || x.psf.kh == 1) lens[x.W] = true;
+    if (x.psf.kh > 1) lens[x.H] = true;
+    ntiles += count_tiles(x.H, x.W);
+    nitems += (size_t)2 * x.H + x.W;  // upper bound on Wiener work items
+  }
+  for (auto& kv : lens) off += align256(dft_table_elems(kv.first) * sizeof(float4));
+  off += align256((size_t)n * sizeof(BatchImg));
+  off += align256(ntiles * sizeof(int4));
+  off += 256;                                         // barrier
+  off += align256((size_t)(2 * iters + 2) * sizeof(int));  // work counters
+  // batched-Wiener job tables: at most 3 jobs per image, one item per row
+  // (pair) or column group (bounded by nitems), plus alignment slack
+  off += 10 * 256 + (size_t)3 * n * wiener_job_bytes() + nitems * sizeof(int2);
+  return off;
+}
+
+db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_t ws_bytes,
+                       int* status, cudaStream_t s, BatchPlan** out) {
+  db_status why;
+  const size_t need = batch_ws_bytes(d, n, iters, &why);
+  if (need == 0) return why;
+  if (!ws || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return DB_ERR_WORKSPACE;
+  BatchPlan* P = new BatchPlan();
+  P->n = n;
+  P->iters = iters;
+  P->wb = wiener_batch_new();
+  char* base = (char*)ws;
+  size_t off = 0;
+  std::vector<ImgRegions> reg(n);
+  for (int i = 0; i < n; ++i) {
+    reg[i] = image_regions(off, d[i].H, d[i].W, d[i].psf.kh, d[i].psf.kw);
+    off = reg[i].end;
+  }
+  // transform tables per distinct axis length
+  std::map<int, std::pair<Dft1ff, Dft1>> dfts;
+  std::vector<int> lens;
+  for (int i = 0; i < n; ++i) {
+    if (d[i].psf.kw > 1 || d[i].psf.kh == 1) lens.push_back(d[i].W);
+    if (d[i].psf.kh > 1) lens.push_back(d[i].H);
+  }
+  std::sort(lens.begin(), lens.end());
+  lens.erase(std::unique(lens.begin(), lens.end()), lens.end());
+  cudaError_t e = cudaSuccess;
+  for (int N : lens) {
+    Dft1ff ff;
+    Dft1 f32;
+    e = prepare_dft(N, (float4*)(base + off), &ff, &f32, s);
+    if (e != cudaSuccess) { delete P; return DB_ERR_CUDA; }
+    dfts[N] = std::make_pair(ff, f32);
+    off += align256(dft_table_elems(N) * sizeof(float4));
+  }
+  // per image: tap groups, Wiener set-up, RRRL descriptor and tiles
+  P->imgs.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const db_image_desc& x = d[i];
+    const ImgRegions& r = reg[i];
+    const int kh = x.psf.kh, kw = x.psf.kw;
+    TapGroup* groups = (TapGroup*)(base + r.groups);
+    int* ngroups = (int*)(base + r.ngroups);
+    if (launch_prepare_taps(x.psf.taps, kh, kw, x.psf.kind, groups, ngroups, status, s) != cudaSuccess) {
+      delete P; return DB_ERR_CUDA;
+    }
+    float* utmp = (float*)(base + r.utmp);
+    float* A = (iters % 2 == 1) ? utmp : x.u;
+    const int ldA = (iters % 2 == 1) ? x.W : x.ld;
+    WienerImage wi = {};
+    wi.f = x.f; wi.ld = x.ld; wi.u0 = A; wi.ldu = ldA; wi.H = x.H; wi.W = x.W;
+    wi.taps = x.psf.taps; wi.kh = kh; wi.kw = kw; wi.K = x.p.K; wi.floor_ = x.p.pos_floor;
+    wi.spec = (float4*)(base + r.spec);
+    wi.work = (kh > 1 && kw > 1) ? (float4*)(base + r.work) : nullptr;
+    wi.pDW = (kw > 1 || kh == 1) ? &dfts[x.W].first : nullptr;
+    wi.pDH = (kh > 1) ? &dfts[x.H].first : nullptr;
+    if (wiener_batch_add(P->wb, wi, s) != cudaSuccess) { delete P; return DB_ERR_CUDA; }
+    BatchImg& bi = P->imgs[i];
+    bi.f = x.f; bi.A = A; bi.ldA = ldA;
+    bi.B = (iters % 2 == 1) ? x.u : utmp;
+    bi.ldB = (iters % 2 == 1) ? x.ld : x.W;
+    bi.q = (float2*)(base + r.q);
+    bi.groups = groups; bi.ngroups = ngroups;
+    bi.ldf = x.ld; bi.H = x.H; bi.W = x.W; bi.kh = kh; bi.kw = kw;
+    bi.ng_max = max_tap_groups(kh, kw);
+    bi.M = tap_group_height(kh);
+    bi.P = halo_class_b(kw);
+    bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
+    bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
+    const size_t sm = std::max(rrl_split_smem_q(kh, kw), rrl_split_smem_update(kh, kw));
+    if (sm > P->smem) P->smem = sm;
+    for (int i0 = 0; i0 < x.H; i0 += kBTH)
+      for (int j0 = 0; j0 < x.W; j0 += kBTW) P->tiles.push_back(make_int4(i, i0, j0, bi.ng_max));
+  }
+  // expensive tiles first (the work queue then ends on cheap ones)
+  std::stable_sort(P->tiles.begin(), P->tiles.end(),
+                   [](const int4& a, const int4& b) { return a.w > b.w; });
+  P->d_imgs = (BatchImg*)(base + off);
+  off += align256((size_t)n * sizeof(BatchImg));
+  P->d_tiles = (int4*)(base + off);
+  off += align256(P->tiles.size() * sizeof(int4));
+  P->d_bar = (unsigned*)(base + off);
+  off += 256;
+  P->d_work = (int*)(base + off);
+  off += align256((size_t)(2 * iters + 2) * sizeof(int));
+  const size_t wtab = wiener_batch_table_bytes(P->wb);
+  if (off + wtab > ws_bytes) { delete P; return DB_ERR_WORKSPACE; }
+  if (wiener_batch_upload(P->wb, base + off, s) != cudaSuccess) { delete P; return DB_ERR_CUDA; }
+  if (cudaMemcpyAsync(P->d_imgs, P->imgs.data(), (size_t)n * sizeof(BatchImg), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(P->d_tiles, P->tiles.data(), P->tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess) {
+    delete P; return DB_ERR_CUDA;
+  }
+  // persistent grid: every co-resident CTA
+  if (P->smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_rrl_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete P; return DB_ERR_UNSUPPORTED;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rrl_batch, 256, P->smem) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    delete P; return DB_ERR_CUDA;
+  }
+  P->grid = sms * per_sm;
+  *out = P;
+  return DB_OK;
+}
+
+db_status batch_run(const BatchPlan* P, int* status, cudaStream_t s) {
+  if (!P) return DB_ERR_ARG;
+  if (cudaMemsetAsync(P->d_bar, 0, 256, s) != cudaSuccess ||
+      cudaMemsetAsync(P->d_work, 0, (size_t)(2 * P->iters + 2) * sizeof(int), s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  if (wiener_batch_run(P->wb, s) != cudaSuccess) return DB_ERR_CUDA;
+  if (P->iters == 0) return DB_OK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P->grid);
+  cfg.blockDim = dim3(64, 4);
+  cfg.dynamicSmemBytes = P->smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const long long limit = g_spin_limit.load();
+  const int ntiles = (int)P->tiles.size();
+  if (cudaLaunchKernelEx(&cfg, k_rrl_batch, (const BatchImg*)P->d_imgs, (const int4*)P->d_tiles, ntiles,
+                         P->iters, P->d_bar, P->d_work, status, limit) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return DB_ERR_CUDA;
+  }
+  count_launch();
+  return DB_OK;
+}
+
+void batch_destroy(BatchPlan* P) { delete P; }
+
+}  // namespace db
+
+using namespace db;
+
+extern "C" {
+
+size_t db_batch_workspace_bytes(const db_image_desc* descs, int n, int iters) {
+  db_status why;
+  return batch_ws_bytes(descs, n, iters, &why);
+}
+
+db_status db_batch_create(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
+                          int* dev_status, void* stream, db_batch** out) {
+  if (!out) return DB_ERR_ARG;
+  *out = nullptr;
+  BatchPlan* P = nullptr;
+  const db_status st = batch_create(descs, n, iters, ws, ws_bytes, dev_status, (cudaStream_t)stream, &P);
+  if (st == DB_OK) *out = (db_batch*)P;
+  return st;
+}
+
+db_status db_batch_run(db_batch* b, int* dev_status, void* stream) {
+  return batch_run((BatchPlan*)b, dev_status, (cudaStream_t)stream);
+}
+
+void db_batch_destroy(db_batch* b) { batch_destroy((BatchPlan*)b); }
+
+db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
+                          int* dev_status, void* stream) {
+  db_batch* b = nullptr;
+  db_status st = db_batch_create(descs, n, iters, ws, ws_bytes, dev_status, stream, &b);
+  if (st != DB_OK) return st;
+  st = db_batch_run(b, dev_status, stream);
+  // the plan's host tables were uploaded with copies that have already read
+  // them, so the plan can go while the device work is still in flight
+  db_batch_destroy(b);
+  return st;
+}
+
+db_status db_set_spin_limit(long long cycles) {
+  if (cycles < 0) return DB_ERR_ARG;
+  set_spin_limit(cycles);
+  return DB_OK;
+}
+
+}  // extern "C"

@@ -82,6 +82,27 @@ cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W,
                                 const Dft1ff& DW, const Dft1ff& DH, cudaStream_t s);
 cudaError_t round_spectrum(const float4* in, float2* out, size_t n, cudaStream_t s);
 
+// batched Wiener filter (host-side plan)
+struct WienerImage {
+  const float* f; int ld;        // observed image
+  float* u0; int ldu;            // Wiener output (floored)
+  int H, W;
+  const float* taps; int kh, kw;
+  float K, floor_;
+  float4* spec;                  // PSF spectrum (1D: length of the axis; 2D: H x W)
+  float4* work;                  // 2D only: H x W complex rows
+  const Dft1ff* pDW;             // transforms (tables already prepared)
+  const Dft1ff* pDH;
+};
+struct WienerBatch;
+WienerBatch* wiener_batch_new();
+size_t wiener_job_bytes();
+void wiener_batch_delete(WienerBatch* b);
+cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t s);
+size_t wiener_batch_table_bytes(const WienerBatch* b);
+cudaError_t wiener_batch_upload(WienerBatch* b, void* dst, cudaStream_t s);
+cudaError_t wiener_batch_run(const WienerBatch* b, cudaStream_t s);
+
 // Fourier-mode (periodic) RRRL iterations, in place on u.
 cudaError_t run_rrl_fourier(const float* f, int ldf, float* u, int ld, float* utmp, int H, int W,
                             float2* X, float2* Z, const float2* S, const float2* twW,

@@ -1,0 +1,357 @@
+// Device pieces of the spatial RRRL iteration (Sec. 2.3, Eq. 9-12; spatial
+// sums with constant continuation, Sec. 4.1-4.2): pointwise formulas, the
+// register-blocked strip sums, and the tile bodies of the fused and split
+// schedules.  Shared by the single-image kernels and the batched persistent
+// kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace db {
+
+// ---------------------------------------------------------------------------
+// pointwise pieces
+//
+// The update of Eq. 9 is evaluated in increment form.  With
+//   e = W (f - b)/b   (so that W f/b = W + e),
+//   Delta = e*h*,  B = W*h*   (hence A = B + Delta),
+// the update u (A + alpha[D]+)/(B - alpha[D]-) equals exactly
+//   u + u (Delta + alpha D) / (B - alpha [D]-),
+// because [D]+ + [D]- = D.  In FP32 this keeps the correlation sums and the
+// final rounding on the small increment instead of on values near 1 and on
+// the full product, which cuts the rounding drift of 20 iterations about
+// sixfold against the FP64 reference.
+// ---------------------------------------------------------------------------
+// W = phi'(r_f(b)) (Eq. 7, 10) with r_f(b) = f (t - log(1+t)), t = (b - f)/f:
+// the same quantity as b - f - f ln(b/f) without its cancellation near b = f.
+__device__ __forceinline__ float robust_weight(float b, float f, const RrlParams& p) {
+  if (!p.phi_robust) return 1.0f;
+  const float t = __fdividef(b - f, f);
+  const float r = f * (t - log1pf(t));
+  return p.eps_phi * rsqrtf(fmaxf(r, 0.0f) + p.eps_phi * p.eps_phi);
+}
+
+// (e, W) for one pixel: W = phi'(r_f(b)), e = W (f - b)/b.
+__device__ __forceinline__ float2 weighted_residual(float b, float f, const RrlParams& p) {
+  const float w = robust_weight(b, f, p);
+  return make_float2(__fdividef(w * (f - b), b), w);
+}
+
+__device__ __forceinline__ float diffusivity(float gx, float gy, const RrlParams& p) {
+  if (!p.psi_tv) return 1.0f;
+  return rsqrtf(fmaf(gx, gx, fmaf(gy, gy, p.eps_psi * p.eps_psi)));
+}
+
+// b[r] = (u*h) at R vertically adjacent pixels.  `base` points at the u
+// value that the first pixel's strip starts from; each group record holds
+// three weights and the shared-memory offset of its first load.
+template <int R, int M, int STRIDE>
+__device__ __forceinline__ void blur_strip(const float* __restrict__ base,
+                                           const float4* __restrict__ grp, int ng, float (&b)[R]) {
+  constexpr int stride = STRIDE;
+#pragma unroll
+  for (int r = 0; r < R; ++r) b[r] = 0.f;
+#pragma unroll 2
+  for (int g = 0; g < ng; ++g) {
+    const float4 G = grp[g];
+    const float* pu = base + __float_as_int(G.w);
+    float v[R + M - 1];
+#pragma unroll
+    for (int t = 0; t < R + M - 1; ++t) v[t] = pu[t * stride];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      b[r] = fmaf(G.x, v[r + M - 1], b[r]);
+      if (M > 1) b[r] = fmaf(G.y, v[r + M - 2], b[r]);
+      if (M > 2) b[r] = fmaf(G.z, v[r + M - 3], b[r]);
+    }
+  }
+}
+
+// Delta[r] = (e*h*), B[r] = (W*h*) at R vertically adjacent pixels.
+template <int R, int M, int STRIDE>
+__device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
+                                                const float4* __restrict__ grp, int ng, float (&dl)[R],
+                                                float (&B)[R]) {
+  constexpr int stride = STRIDE;
+#pragma unroll
+  for (int r = 0; r < R; ++r) { dl[r] = 0.f; B[r] = 0.f; }
+#pragma unroll 2
+  for (int g = 0; g < ng; ++g) {
+    const float4 G = grp[g];
+    const float2* pq = base + __float_as_int(G.w);
+    float2 v[R + M - 1];
+#pragma unroll
+    for (int t = 0; t < R + M - 1; ++t) v[t] = pq[t * stride];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      dl[r] = fmaf(G.x, v[r].x, dl[r]);
+      B[r] = fmaf(G.x, v[r].y, B[r]);
+      if (M > 1) { dl[r] = fmaf(G.y, v[r + 1].x, dl[r]); B[r] = fmaf(G.y, v[r + 1].y, B[r]); }
+      if (M > 2) { dl[r] = fmaf(G.z, v[r + 2].x, dl[r]); B[r] = fmaf(G.z, v[r + 2].y, B[r]); }
+    }
+  }
+}
+
+// Diffusion term D = div(psi'(|grad u|^2) grad u) (Eq. 11) at R vertically
+// adjacent pixels.  uc points at the first pixel in a shared-memory copy of
+// u(clamp(.)) with at least 2 pixels of halo on every side.  Diffusivities
+// and vertical fluxes shared by neighbouring rows of the strip are formed
+// once.  Across the image boundary the clamped copy makes every difference
+// vanish exactly: zero flux.
+template <int R, int S>
+__device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, const RrlParams& p,
+                                                float (&D)[R], float (&c)[R]) {
+  float m[R + 4], e1[R + 2], w1[R + 2];
+#pragma unroll
+  for (int t = 0; t < R + 4; ++t) m[t] = uc[(t - 2) * S];
+#pragma unroll
+  for (int t = 0; t < R + 2; ++t) { e1[t] = uc[(t - 1) * S + 1]; w1[t] = uc[(t - 1) * S - 1]; }
+  float gC[R + 2];
+#pragma unroll
+  for (int t = 0; t < R + 2; ++t)  // rows -1..R
+    gC[t] = diffusivity(0.5f * (e1[t] - w1[t]), 0.5f * (m[t + 2] - m[t]), p);
+  float Fv[R + 1];
+#pragma unroll
+  for (int t = 0; t < R + 1; ++t)  // flux between rows t-1 and t
+    Fv[t] = 0.5f * (gC[t + 1] + gC[t]) * (m[t + 2] - m[t + 1]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float e2 = uc[r * S + 2], w2 = uc[r * S - 2];
+    const float ctr = m[r + 2];
+    const float gE = diffusivity(0.5f * (e2 - ctr), 0.5f * (e1[r + 2] - e1[r]), p);
+    const float gW = diffusivity(0.5f * (ctr - w2), 0.5f * (w1[r + 2] - w1[r]), p);
+    const float fe = 0.5f * (gE + gC[r + 1]) * (e1[r + 1] - ctr);
+    const float fw = 0.5f * (gC[r + 1] + gW) * (ctr - w1[r + 1]);
+    D[r] = (fe - fw) + (Fv[r + 1] - Fv[r]);
+    c[r] = ctr;
+  }
+}
+
+// u' = u + u (Delta + alpha D) / (B - alpha [D]-)
+__device__ __forceinline__ float rrl_update(float u, float dl, float B, float D, const RrlParams& p) {
+  const float den = B - p.alpha * fminf(D, 0.f);
+  return fmaf(u, __fdividef(fmaf(p.alpha, D, dl), den), u);
+}
+
+// ---------------------------------------------------------------------------
+// fused iteration, register blocked.
+//
+// Each thread owns a vertical strip of R q-points (phase 1) or R outputs
+// (phase 2) in one column, so a tap group loaded once from shared memory
+// feeds M*R (phase 1) or 2*M*R (phase 2) FMAs from R+M-1 shared loads.
+// Lanes of a warp own adjacent columns: shared accesses are conflict-free.
+//
+// Geometry (virtual rows/cols may lie outside the image):
+//   q tile : rows i0-cy .. i0-cy+QHp-1, cols j0-cx .. j0-cx+QW-1
+//   u tile : rows i0-Ry .. i0-Ry+UH-1,  cols j0-Rx .. j0-Rx+US-1
+// u is staged as u(clamp(.)); q = (e, W) is first formed at every virtual
+// position from the clamped u and then, at virtual positions outside the
+// image, replaced by q at the clamped position.
+// ---------------------------------------------------------------------------
+template <int TH, int TW, int R, int M, int P>
+__global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict__ f, int ldf,
+                                                     const float* __restrict__ uin, int ldin,
+                                                     float* __restrict__ uout, int ldout, int H, int W,
+                                                     const TapGroup* __restrict__ groups_g,
+                                                     const int* __restrict__ ngroups_g, int kh, int kw,
+                                                     int ng_max, RrlParams p, int* status) {
+  static_assert(TH % R == 0, "output strips must tile TH");
+  // row strides padded to the halo class P >= kw - 1 (compile-time strides
+  // let every strip load use an immediate offset)
+  constexpr int US = TW + 2 * P, QS = TW + P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cy = kh >> 1, cx = kw >> 1;
+  const int Ry = max(kh - 1, 2), Rx = P;
+  const int QH = TH + kh - 1, QW = TW + kw - 1;
+  const int NQS = (QH + R - 1) / R, QHp = NQS * R;
+  const int UH = Ry + max(QHp, TH + 2);
+  const int ng = *ngroups_g;
+  float4* gu = (float4*)smem_raw;
+  float4* gq = gu + ng_max;
+  float* us = (float*)(gq + ng_max);
+  float2* qs = (float2*)(us + ((UH * US + 1) & ~1));
+  const int i0 = blockIdx.y * TH, j0 = blockIdx.x * TW;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+
+  for (int g = tid; g < ng; g += nth) {
+    const TapGroup t = groups_g[g];
+    const int offu = (Ry - cy - t.dy0 - (M - 1)) * US + (Rx - cx - t.dx);
+    const int offq = (cy + t.dy0) * QS + (cx + t.dx);
+    gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
+    gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
+  }
+  for (int r = threadIdx.y; r < UH; r += blockDim.y) {
+    const int gi = min(max(i0 - Ry + r, 0), H - 1);
+    const float* src = uin + (size_t)gi * ldin;
+    for (int c = threadIdx.x; c < US; c += blockDim.x)
+      cp_async4(us + r * US + c, src + min(max(j0 - Rx + c, 0), W - 1));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // phase 1: (e, W) on the q tile (virtual positions)
+  for (int item = tid; item < NQS * QW; item += nth) {
+    const int s = item / QW, qc = item - s * QW;
+    const int qr0 = s * R;
+    const int aj = min(max(j0 - cx + qc, 0), W - 1);
+    float fv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int ai = min(max(i0 - cy + qr0 + r, 0), H - 1);
+      fv[r] = fmaxf(__ldg(f + (size_t)ai * ldf + aj), p.floor);
+    }
+    float b[R];
+    blur_strip<R, M, US>(us + qr0 * US + qc, gu, ng, b);
+#pragma unroll
+    for (int r = 0; r < R; ++r) qs[(qr0 + r) * QS + qc] = weighted_residual(b[r], fv[r], p);
+  }
+  __syncthreads();
+  const bool border = (i0 - cy < 0) || (j0 - cx < 0) || (i0 - cy + QH > H) || (j0 - cx + QW > W);
+  if (border) {
+    // writes only positions outside the image, reads only positions inside
+    // it: no ordering between threads is needed within this pass
+    for (int idx = tid; idx < QH * QW; idx += nth) {
+      const int qr = idx / QW, qc = idx - qr * QW;
+      const int vi = i0 - cy + qr, vj = j0 - cx + qc;
+      const int ci = min(max(vi, 0), H - 1), cj = min(max(vj, 0), W - 1);
+      if (ci != vi || cj != vj) qs[qr * QS + qc] = qs[(ci - (i0 - cy)) * QS + (cj - (j0 - cx))];
+    }
+    __syncthreads();
+  }
+
+  // phase 2: Delta = e*h*, B = W*h*, diffusion, update
+  for (int item = tid; item < (TH / R) * TW; item += nth) {
+    const int s = item / TW, oj = item - s * TW;
+    const int oi0 = s * R, j = j0 + oj;
+    float dl[R], B[R], D[R], c[R];
+    correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
+    diffusion_strip<R, US>(us + (oi0 + Ry) * US + (oj + Rx), p, D, c);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + oi0 + r;
+      const float un = rrl_update(c[r], dl[r], B[r], D[r], p);
+      if (i < H && j < W) {
+        if (!isfinite(un) && status) atomicOr(status, DB_FLAG_NONFINITE);
+        uout[(size_t)i * ldout + j] = un;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// split schedule: the same iteration as two launches.
+//   k_rrl_q      : q = (e, W) once per pixel into a global float2 buffer
+//   k_rrl_update : Delta, B from q (clamped reads), diffusion from u, update
+// Used when the image (u, f, q: 16 bytes per pixel) stays resident in L2, so
+// the extra round trip of q costs no HBM traffic while the halo recompute of
+// the fused kernel disappears.
+// ---------------------------------------------------------------------------
+// q = (e, W) on the TH x TW tile at (i0, j0).  smem_raw: rrl_split_smem_q bytes.
+template <int TH, int TW, int R, int M, int P>
+__device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __restrict__ f, int ldf,
+                                       const float* __restrict__ uin, int ldin,
+                                       float2* __restrict__ q, int ldq, int H, int W,
+                                       const TapGroup* __restrict__ groups_g,
+                                       const int* __restrict__ ngroups_g, int kh, int kw,
+                                       int ng_max, const RrlParams& p, int i0, int j0) {
+  static_assert(TH % R == 0, "strips must tile TH");
+  const int cy = kh >> 1, cx = kw >> 1;
+  const int Ty = kh - 1 - cy, Tx = kw - 1 - cx;  // u rows/cols needed above/left of a pixel
+  constexpr int US = TW + P;                      // row stride, P >= kw - 1
+  const int UH = TH + kh - 1, UW = TW + kw - 1;
+  const int ng = *ngroups_g;
+  float4* gu = (float4*)smem_raw;
+  float* us = (float*)(gu + ng_max);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int g = tid; g < ng; g += nth) {
+    const TapGroup t = groups_g[g];
+    const int offu = (Ty - t.dy0 - (M - 1)) * US + (Tx - t.dx);
+    gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
+  }
+  for (int r = threadIdx.y; r < UH; r += blockDim.y) {
+    const int gi = min(max(i0 - Ty + r, 0), H - 1);
+    const float* src = uin + (size_t)gi * ldin;
+    for (int c = threadIdx.x; c < UW; c += blockDim.x)
+      cp_async4(us + r * US + c, src + min(max(j0 - Tx + c, 0), W - 1));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int item = tid; item < (TH / R) * TW; item += nth) {
+    const int s = item / TW, c = item - s * TW;
+    const int r0 = s * R, j = j0 + c;
+    if (j >= W || i0 + r0 >= H) continue;
+    float fv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = min(i0 + r0 + r, H - 1);
+      fv[r] = fmaxf(__ldg(f + (size_t)i * ldf + j), p.floor);
+    }
+    float b[R];
+    blur_strip<R, M, US>(us + r0 * US + c, gu, ng, b);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + r0 + r;
+      if (i < H) q[(size_t)i * ldq + j] = weighted_residual(b[r], fv[r], p);
+    }
+  }
+}
+
+// Delta, B, D and the update on the TH x TW tile at (i0, j0).
+// smem_raw: rrl_split_smem_update bytes.
+template <int TH, int TW, int R, int M, int P>
+__device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float2* __restrict__ q, int ldq,
+                                            const float* __restrict__ uin, int ldin,
+                                            float* __restrict__ uout, int ldout, int H, int W,
+                                            const TapGroup* __restrict__ groups_g,
+                                            const int* __restrict__ ngroups_g, int kh, int kw,
+                                            int ng_max, const RrlParams& p, int* status, int i0, int j0) {
+  static_assert(TH % R == 0, "strips must tile TH");
+  const int cy = kh >> 1, cx = kw >> 1;
+  const int QH = TH + kh - 1, QW = TW + kw - 1;
+  constexpr int QS = TW + P, UH = TH + 4, US = TW + 4;  // row strides, P >= kw - 1
+  const int ng = *ngroups_g;
+  float4* gq = (float4*)smem_raw;
+  float2* qs = (float2*)(gq + ng_max);
+  float* us = (float*)(qs + QH * QS);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int g = tid; g < ng; g += nth) {
+    const TapGroup t = groups_g[g];
+    const int offq = (cy + t.dy0) * QS + (cx + t.dx);
+    gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
+  }
+  // q(clamp) over the correlation footprint, u(clamp) with a 2-pixel halo
+  for (int r = threadIdx.y; r < QH; r += blockDim.y) {
+    const int gi = min(max(i0 - cy + r, 0), H - 1);
+    const float2* src = q + (size_t)gi * ldq;
+    for (int c = threadIdx.x; c < QW; c += blockDim.x)
+      cp_async8(qs + r * QS + c, src + min(max(j0 - cx + c, 0), W - 1));
+  }
+  for (int r = threadIdx.y; r < UH; r += blockDim.y) {
+    const int gi = min(max(i0 - 2 + r, 0), H - 1);
+    const float* src = uin + (size_t)gi * ldin;
+    for (int c = threadIdx.x; c < US; c += blockDim.x)
+      cp_async4(us + r * US + c, src + min(max(j0 - 2 + c, 0), W - 1));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int item = tid; item < (TH / R) * TW; item += nth) {
+    const int s = item / TW, oj = item - s * TW;
+    const int oi0 = s * R, j = j0 + oj;
+    if (j >= W || i0 + oi0 >= H) continue;
+    float dl[R], B[R], D[R], c[R];
+    correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
+    diffusion_strip<R, US>(us + (oi0 + 2) * US + (oj + 2), p, D, c);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + oi0 + r;
+      const float un = rrl_update(c[r], dl[r], B[r], D[r], p);
+      if (i < H) {
+        if (!isfinite(un) && status) atomicOr(status, DB_FLAG_NONFINITE);
+        uout[(size_t)i * ldout + j] = un;
+      }
+    }
+  }
+}
+
+}  // namespace db

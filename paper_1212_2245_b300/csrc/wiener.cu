@@ -20,6 +20,8 @@
 // multiplied in goes through the same routine, so orders always match.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "fft_df.cuh"
 #include "internal.cuh"
 
@@ -112,15 +114,13 @@ __device__ __forceinline__ float4 wiener_gain(float4 S, float4 X, float K) {
 
 __device__ __forceinline__ float ff_round(float2 v) { return v.x + v.y; }
 
-// Row transforms: each CTA owns R consecutive sequences (capacity M each).
-// Global inputs are staged with asynchronous copies.
+// Row transforms: a CTA owns R consecutive sequences (capacity M each)
+// starting at q0.  Global inputs are staged with asynchronous copies.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
-  extern __shared__ float4 smem4[];
+__device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q0, int R) {
   const int N = a.D.N, logM = a.D.logM, M = 1 << logM;
   float4* x = smem4;
   float* stage = (float*)(x + R * M);  // real rows (x2 for row pairs)
-  const int q0 = blockIdx.x * R;
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
     const int r = idx / N, c = idx - r * N;
     const int q = q0 + r;
@@ -188,17 +188,31 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
   }
 }
 
-// Column transforms: each CTA owns C adjacent sequences laid out across a row
-// (element stride C in shared memory, capacity M each).  For
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
+  extern __shared__ float4 smem4[];
+  rows_body<MODE>(smem4, a, blockIdx.x * R, R);
+}
+
+// Batched form: CTA b transforms sequence items[b].y of job items[b].x.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fft_rows_batch(const FftArgs* __restrict__ jobs,
+                                                        const int2* __restrict__ items) {
+  extern __shared__ float4 smem4[];
+  const int2 it = items[blockIdx.x];
+  const FftArgs a = jobs[it.x];
+  rows_body<MODE>(smem4, a, it.y, 1);
+}
+
+// Column transforms: a CTA owns C adjacent sequences laid out across a row
+// (element stride C in shared memory, capacity M each) starting at c0.  For
 // COL_WIENER_1D_REAL, sequence c packs image columns 2c and 2c+1 and a.nrows
 // counts the image columns.
 template <int MODE, int C>
-__global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
-  extern __shared__ float4 smem4[];
+__device__ __forceinline__ void cols_body(float4* smem4, const FftArgs& a, int c0) {
   const int N = a.D.N, logM = a.D.logM, M = 1 << logM;
   float4* x = smem4;
   float* stage = (float*)(x + M * C);  // COL_WIENER_1D_REAL: 2*C real columns
-  const int c0 = blockIdx.x * C;
   const int nseq_total = (MODE == COL_WIENER_1D_REAL) ? (a.nrows + 1) / 2 : a.nrows;
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
@@ -251,6 +265,21 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
       a.cbuf[(size_t)k * a.ldc + q] = v;
     }
   }
+}
+
+template <int MODE, int C>
+__global__ void __launch_bounds__(256) k_fft_cols(FftArgs a) {
+  extern __shared__ float4 smem4[];
+  cols_body<MODE, C>(smem4, a, blockIdx.x * C);
+}
+
+template <int MODE, int C>
+__global__ void __launch_bounds__(256) k_fft_cols_batch(const FftArgs* __restrict__ jobs,
+                                                        const int2* __restrict__ items) {
+  extern __shared__ float4 smem4[];
+  const int2 it = items[blockIdx.x];
+  const FftArgs a = jobs[it.x];
+  cols_body<MODE, C>(smem4, a, it.y);
 }
 
 static constexpr size_t kSmemLimit = 227 * 1024;
@@ -420,6 +449,147 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
   o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.D = DW;
   o.floor_ = floor_; o.scale = ff_const(1.0 / ((double)H * (double)W)); o.spec = spec; o.K = K;
   return launch_rows<ROW_INV_REAL>(o, s);
+}
+
+// ---------------------------------------------------------------------------
+// batched Wiener filter: every image of a batch in five launches (one per
+// transform stage), each CTA working on one row (pair) or column group of
+// one image with that image's own transform lengths.
+// ---------------------------------------------------------------------------
+enum { WB_ROW_1D = 0, WB_ROW_FWD = 1, WB_COL_1D = 2, WB_COL_2D = 3, WB_ROW_INV = 4, WB_STAGES = 5 };
+constexpr int kBatchColC = 4;
+
+struct WienerBatch {
+  std::vector<FftArgs> jobs[WB_STAGES];
+  std::vector<int2> items[WB_STAGES];
+  FftArgs* d_jobs[WB_STAGES] = {};
+  int2* d_items[WB_STAGES] = {};
+  size_t smem[WB_STAGES] = {};
+};
+
+WienerBatch* wiener_batch_new() { return new WienerBatch(); }
+size_t wiener_job_bytes() { return sizeof(FftArgs); }
+void wiener_batch_delete(WienerBatch* b) { delete b; }
+
+// Precompute the image's PSF spectrum (untimed set-up) and append its jobs.
+cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t s) {
+  cudaError_t e;
+  const int H = im.H, W = im.W;
+  if (im.kh == 1) {
+    FftArgs a = {};
+    a.taps = im.taps; a.kh = 1; a.kw = im.kw; a.nrows = 1; a.D = (*im.pDW); a.cbuf = im.spec; a.ldc = W;
+    if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+    FftArgs j = {};
+    j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.D = (*im.pDW);
+    j.nrows = (H + 1) / 2; j.img_rows = H; j.K = im.K; j.floor_ = im.floor_; j.scale = ff_const(1.0 / W);
+    const int id = (int)b->jobs[WB_ROW_1D].size();
+    b->jobs[WB_ROW_1D].push_back(j);
+    for (int q = 0; q < j.nrows; ++q) b->items[WB_ROW_1D].push_back(make_int2(id, q));
+    const size_t sm = (size_t)(1 << (*im.pDW).logM) * sizeof(float4) + (size_t)2 * W * sizeof(float);
+    if (sm > b->smem[WB_ROW_1D]) b->smem[WB_ROW_1D] = sm;
+    return cudaSuccess;
+  }
+  if (im.kw == 1) {
+    FftArgs a = {};
+    a.taps = im.taps; a.kh = 1; a.kw = im.kh; a.nrows = 1; a.D = (*im.pDH); a.cbuf = im.spec; a.ldc = H;
+    if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+    FftArgs j = {};
+    j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.D = (*im.pDH);
+    j.nrows = W; j.K = im.K; j.floor_ = im.floor_; j.scale = ff_const(1.0 / H);
+    const int id = (int)b->jobs[WB_COL_1D].size();
+    b->jobs[WB_COL_1D].push_back(j);
+    const int nseq = (W + 1) / 2;
+    for (int c0 = 0; c0 < nseq; c0 += kBatchColC) b->items[WB_COL_1D].push_back(make_int2(id, c0));
+    const size_t sm = (size_t)kBatchColC * (1 << (*im.pDH).logM) * sizeof(float4) + (size_t)2 * kBatchColC * H * sizeof(float);
+    if (sm > b->smem[WB_COL_1D]) b->smem[WB_COL_1D] = sm;
+    return cudaSuccess;
+  }
+  if ((e = run_psf_spectrum_2d(im.taps, im.kh, im.kw, H, W, im.spec, (*im.pDW), (*im.pDH), s)) != cudaSuccess) return e;
+  FftArgs d = {};
+  d.fin = im.f; d.ldf = im.ld; d.cbuf = im.work; d.ldc = W; d.nrows = H; d.D = (*im.pDW); d.floor_ = im.floor_;
+  FftArgs g = {};
+  g.cbuf = im.work; g.ldc = W; g.spec = im.spec; g.ldspec = W; g.nrows = W; g.D = (*im.pDH); g.K = im.K;
+  FftArgs o = {};
+  o.cbuf = im.work; o.ldc = W; o.uout = im.u0; o.ldu = im.ldu; o.nrows = H; o.D = (*im.pDW);
+  o.floor_ = im.floor_; o.scale = ff_const(1.0 / ((double)H * (double)W)); o.spec = im.spec; o.K = im.K;
+  const int i1 = (int)b->jobs[WB_ROW_FWD].size(), i2 = (int)b->jobs[WB_COL_2D].size(),
+            i3 = (int)b->jobs[WB_ROW_INV].size();
+  b->jobs[WB_ROW_FWD].push_back(d);
+  b->jobs[WB_COL_2D].push_back(g);
+  b->jobs[WB_ROW_INV].push_back(o);
+  for (int q = 0; q < H; ++q) {
+    b->items[WB_ROW_FWD].push_back(make_int2(i1, q));
+    b->items[WB_ROW_INV].push_back(make_int2(i3, q));
+  }
+  for (int c0 = 0; c0 < W; c0 += kBatchColC) b->items[WB_COL_2D].push_back(make_int2(i2, c0));
+  const size_t smr = (size_t)(1 << (*im.pDW).logM) * sizeof(float4) + (size_t)2 * W * sizeof(float);
+  const size_t smc = (size_t)kBatchColC * (1 << (*im.pDH).logM) * sizeof(float4);
+  if (smr > b->smem[WB_ROW_FWD]) b->smem[WB_ROW_FWD] = smr;
+  if (smr > b->smem[WB_ROW_INV]) b->smem[WB_ROW_INV] = smr;
+  if (smc > b->smem[WB_COL_2D]) b->smem[WB_COL_2D] = smc;
+  return cudaSuccess;
+}
+
+size_t wiener_batch_table_bytes(const WienerBatch* b) {
+  size_t n = 0;
+  for (int k = 0; k < WB_STAGES; ++k)
+    n += align256(b->jobs[k].size() * sizeof(FftArgs)) + align256(b->items[k].size() * sizeof(int2));
+  return n;
+}
+
+// Upload the job tables into `dst` (wiener_batch_table_bytes bytes).
+cudaError_t wiener_batch_upload(WienerBatch* b, void* dst, cudaStream_t s) {
+  char* p = (char*)dst;
+  for (int k = 0; k < WB_STAGES; ++k) {
+    b->d_jobs[k] = (FftArgs*)p;
+    if (!b->jobs[k].empty()) {
+      cudaError_t e = cudaMemcpyAsync(p, b->jobs[k].data(), b->jobs[k].size() * sizeof(FftArgs),
+                                      cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+    p += align256(b->jobs[k].size() * sizeof(FftArgs));
+    b->d_items[k] = (int2*)p;
+    if (!b->items[k].empty()) {
+      cudaError_t e = cudaMemcpyAsync(p, b->items[k].data(), b->items[k].size() * sizeof(int2),
+                                      cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+    p += align256(b->items[k].size() * sizeof(int2));
+  }
+  for (int k = 0; k < WB_STAGES; ++k)
+    if (b->smem[k] > kSmemLimit) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+template <int MODE>
+static cudaError_t launch_rows_batch(const WienerBatch* b, int stage, cudaStream_t s) {
+  if (b->items[stage].empty()) return cudaSuccess;
+  cudaError_t e = set_dyn_smem(k_fft_rows_batch<MODE>, b->smem[stage]);
+  if (e != cudaSuccess) return e;
+  k_fft_rows_batch<MODE><<<(unsigned)b->items[stage].size(), 256, b->smem[stage], s>>>(b->d_jobs[stage],
+                                                                                     b->d_items[stage]);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_cols_batch(const WienerBatch* b, int stage, cudaStream_t s) {
+  if (b->items[stage].empty()) return cudaSuccess;
+  auto kern = k_fft_cols_batch<MODE, kBatchColC>;
+  cudaError_t e = set_dyn_smem(kern, b->smem[stage]);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)b->items[stage].size(), 256, b->smem[stage], s>>>(b->d_jobs[stage], b->d_items[stage]);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t wiener_batch_run(const WienerBatch* b, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = launch_rows_batch<ROW_WIENER_1D>(b, WB_ROW_1D, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_WIENER_1D_REAL>(b, WB_COL_1D, s)) != cudaSuccess) return e;
+  if ((e = launch_rows_batch<ROW_FWD_REAL>(b, WB_ROW_FWD, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_WIENER>(b, WB_COL_2D, s)) != cudaSuccess) return e;
+  return launch_rows_batch<ROW_INV_REAL>(b, WB_ROW_INV, s);
 }
 
 }  // namespace db
