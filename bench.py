@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="line1024",
-                    help="line1024 (default, the headline workload), box256, gauss2048")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512"], default="line1024",
+                    help="line1024 (default, the headline workload), box256, gauss2048, batch512")
     return ap.parse_args()
 
 
@@ -189,7 +189,7 @@ def run_reference(args, ws_, rank):
     if rank != 0:
         return
     import oracle
-    case = make_case(args.workload)
+    case = make_case(args.workload if args.workload != "batch512" else "line1024")
     p, h = case.params, case.h
     rows = min(128, case.f.shape[0])
     f = case.f[:rows].astype(np.float64)
@@ -349,6 +349,122 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, world, rank, local):
+    """512 uneven images (sides U{128..1024}), own PSF each, Wiener + 10 RRRL,
+    as one planned batch replayed from a CUDA graph."""
+    import paper_1212_2245_b300 as db
+    from paper_1212_2245_b300 import _lib, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+    t0 = time.perf_counter()
+    cases = [synth.batch_case(i) for i in range(512)]
+    gen_s = time.perf_counter() - t0
+    iters = cases[0].iters
+    fs = [torch.as_tensor(c.f).to(dev) for c in cases]
+    hs = [torch.as_tensor(c.h).to(dev).contiguous() for c in cases]
+    ps = [c.params for c in cases]
+    kinds = [c.psf_kind for c in cases]
+    px = sum(c.f.size for c in cases)
+    flops_iter = sum(c.f.size * (6 * int((c.h != 0).sum()) + 60) for c in cases)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        full = db.Batch(fs, hs, ps, iters, kinds=kinds)
+        wien = db.Batch(fs, hs, ps, 0, kinds=kinds, outs=[torch.empty_like(f) for f in fs])
+        stream.synchronize()
+        plan_s = time.perf_counter() - t0
+        full.run()
+        wien.run()
+        n0 = lib.db_launch_count()
+        g_full, g_w = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_full, stream=stream):
+            full.run(check=False)
+        n1 = lib.db_launch_count()
+        with torch.cuda.graph(g_w, stream=stream):
+            wien.run(check=False)
+        for _ in range(max(args.warmup, 3)):
+            g_full.replay()
+            g_w.replay()
+        stream.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    full.ws.reset_status()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                g_full.replay()
+                ev[k][1].record(stream)
+                flush.fill_(float(k))
+                ev[k][2].record(stream)
+                g_w.replay()
+                ev[k][3].record(stream)
+        torch.cuda.synchronize()
+    full.ws.raise_on_flags("timed region")
+    ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    ms_w = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    ms_rrl = ms - ms_w
+    # end to end: pinned host images in, results out, every step
+    f_host = [torch.as_tensor(c.f).pin_memory() for c in cases]
+    u_host = [torch.empty(c.f.shape, dtype=torch.float32).pin_memory() for c in cases]
+    e2e = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.fill_(float(k))
+            e2e[k][0].record(stream)
+            for fh, fd in zip(f_host, fs):
+                fd.copy_(fh, non_blocking=True)
+            g_full.replay()
+            for ud, uh in zip(full.us, u_host):
+                uh.copy_(ud, non_blocking=True)
+            e2e[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in e2e)
+    if rank != 0:
+        return
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops_iter * iters / (ms_rrl / 1e3) / 1e12
+    hbm_peak, hbm_src = peaks()
+    line = {
+        "metric": METRIC, "value": world * px * iters / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch512: 512 f32 images, sides U{128..1024}, half 1D motion (box/raised "
+                               "cosine, L 5-41), half 2D Gaussian mixtures 7x7..25x25, sigma=2, Wiener K=0.006 "
+                               "+ 10 RRRL; one planned batch replayed from a CUDA graph",
+                   "pixels": px, "iters": iters, "l2": "inputs 0.7 GB > L2; L2 flushed before every step",
+                   "parallelism": f"replicas x{world}"},
+        "rrrl_only_mpx_iter_s": world * px * iters / (ms_rrl / 1e3) / 1e6, "wiener_ms": ms_w,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_rrl_batch (persistent, all RRRL iterations of all images)",
+                     "kernel_ms": ms_rrl, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
+                     "hbm_equiv_gbs": 28.0 * px * iters / (ms_rrl / 1e3) / 1e9,
+                     "hbm_equiv_frac": 28.0 * px * iters / (ms_rrl / 1e3) / 1e9 / hbm_peak},
+        "e2e": {"value": world * px * iters / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * px, "d2h_bytes_per_step": 4 * px, "ms_per_step": e2e_ms},
+        "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0,
+        "plan_s": plan_s, "generate_s": gen_s, "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        sample_px = 0
+        for c in (cases[0], cases[256]):
+            oracle.wr3l(c.f, c.h, c.params, 2)
+            sample_px += c.f.size * 2
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sample_px / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(),
+                                "kind": "oracle", "sample": f"FP64 oracle, Wiener + 2 RRRL on images 0 and 256 "
+                                                            f"({cases[0].f.shape}, {cases[256].f.shape}), {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -360,6 +476,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "batch512":
+            run_batch(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -16,7 +16,7 @@ from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "Batch", "deblur_batch", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
+           "deblur", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
            "version"]
 
 
@@ -222,6 +222,74 @@ def deblur_batch(fs, taps, params, iters, *, kinds=None, outs=None, check: bool 
         return b.run(check=check)
     finally:
         b.close()
+
+
+def rrl_backward(f, ckpt, grad_u, taps, params, iters, ckpt_every, grad_taps, grad_alpha, grad_K, *,
+                 grad_f=None, ws=None, check: bool = True):
+    """Reverse mode of Wiener + `iters` RRRL for one image (db_rrl_backward).
+    grad_taps/grad_alpha/grad_K are float64 CUDA tensors accumulated in place."""
+    H, W, ld = _image(f, "f")
+    gf = grad_f if grad_f is not None else torch.empty_like(f)
+    lib = _lib.load()
+    psf, p = _db_psf(taps, "general"), _db_params(params)
+    if ws is None:
+        n = lib.db_backward_workspace_bytes(H, W, ctypes.byref(psf), int(ckpt_every))
+        if n == 0:
+            raise DeblurError("invalid arguments for the backward workspace query")
+        ws = Workspace(n)
+    if check:
+        ws.reset_status()
+    for t in (grad_taps, grad_alpha, grad_K):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("parameter gradients must be contiguous float64 CUDA tensors")
+    _check(lib.db_rrl_backward(f.data_ptr(), ckpt.data_ptr(), grad_u.data_ptr(), H, W, ld, ctypes.byref(psf),
+                               ctypes.byref(p), int(iters), int(ckpt_every), gf.data_ptr(), grad_taps.data_ptr(),
+                               grad_alpha.data_ptr(), grad_K.data_ptr(), ws.ptr, ws.nbytes,
+                               ws.status.data_ptr(), _stream()), "db_rrl_backward")
+    if check:
+        ws.raise_on_flags("db_rrl_backward")
+    return gf
+
+
+class DeblurFn(torch.autograd.Function):
+    """Differentiable WR3L for a batch f (N, H, W) with learnable one-row taps
+    (1, kw), alpha and K (0-dim tensors).  Forward: db_wiener + db_rrl_iterate
+    with checkpoints every `ckpt_every` iterations; backward: db_rrl_backward
+    per image (gradients for f, taps, alpha and K)."""
+
+    @staticmethod
+    def forward(ctx, f, taps, alpha, K, params, iters, ckpt_every):
+        import dataclasses
+        p = dataclasses.replace(params, alpha=float(alpha), K=float(K))
+        N, H, W = f.shape
+        taps_c = taps.detach().float().contiguous()
+        nck = (iters - 1) // ckpt_every + 1 if iters > 0 else 1
+        ckpts = torch.empty(N, nck, H, W, dtype=torch.float32, device=f.device)
+        out = torch.empty_like(f)
+        ws = Workspace.for_image(H, W, taps_c.shape[0], taps_c.shape[1], p)
+        for n in range(N):
+            wiener(f[n], taps_c, p, out=out[n], ws=ws, check=False)
+            if iters > 0:
+                rrl_iterate(f[n], out[n], taps_c, p, iters, ckpt=ckpts[n], ckpt_every=ckpt_every, ws=ws,
+                            check=False)
+            else:
+                ckpts[n, 0].copy_(out[n])
+        ctx.save_for_backward(f, taps_c, ckpts)
+        ctx.p, ctx.iters, ctx.every = p, iters, ckpt_every
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        f, taps_c, ckpts = ctx.saved_tensors
+        N, H, W = f.shape
+        grad_u = grad_u.contiguous().float()
+        gt = torch.zeros(taps_c.numel(), dtype=torch.float64, device=f.device)
+        ga = torch.zeros(1, dtype=torch.float64, device=f.device)
+        gk = torch.zeros(1, dtype=torch.float64, device=f.device)
+        gf = torch.empty_like(f)
+        for n in range(N):
+            rrl_backward(f[n], ckpts[n], grad_u[n], taps_c, ctx.p, ctx.iters, ctx.every, gt, ga, gk, grad_f=gf[n])
+        return gf, gt.reshape(taps_c.shape).float(), ga[0].float(), gk[0].float(), None, None, None
 
 
 def set_spin_limit(cycles: int):

@@ -1,0 +1,663 @@
+// Reverse mode (adjoint) of the WR3L chain for gradient-based tuning of the
+// PSF taps, alpha and K (no counterpart in the paper; it differentiates the
+// operators of Sec. 2.1, Eq. 2 and Sec. 2.3, Eq. 7-12 as evaluated here).
+//
+// Forward step (spatial mode, constant continuation), per pixel:
+//   b = C u,  r = r_f(b),  W = phi'(r),  q1 = W f/b,  q2 = W,
+//   A = C' q1,  B = C' q2,  D = div(psi'(|grad u|^2) grad u),
+//   u' = u (A + alpha [D]+) / (B - alpha [D]-)
+// with C the clamped convolution and C' the clamped correlation.  Neither is
+// the transpose of the other at the image border, so the reverse step uses
+// the exact transposes: (C^T y)(j) = sum_d h(d) sum_{i: clip(i-d) = j} y(i)
+// and (C'^T z)(j) = sum_d h(d) sum_{i: clip(i+d) = j} z(i); at border pixels
+// the inner sums run over a range of i.
+//
+// Reverse step, given the adjoint U' of u':
+//   num = A + alpha[D]+, den = B - alpha[D]-
+//   U   = U' num/den              Abar = U' u/den      Bbar = -U' u num/den^2
+//   Dbar = alpha (Abar 1[D>0] - Bbar 1[D<0]);  alpha_bar += Abar [D]+ - Bbar [D]-
+//   q1bar = C'^T Abar,  q2bar = C'^T Bbar
+//   Wbar = q1bar f/b + q2bar;  rbar = Wbar phi''(r)
+//   bbar = -q1bar W f/b^2 + rbar (1 - f/b);  fbar += q1bar W/b - rbar ln(b/f)
+//   U  += C^T bbar + (diffusion adjoint of Dbar)
+//   hbar(d) += sum_i Abar(i) q1(clip(i+d)) + Bbar(i) q2(clip(i+d)) + bbar(i) u(clip(i-d))
+// Derivative conventions at kinks: d[z]+/dz = 1[z>0], d[z]-/dz = 1[z<0],
+// d max(z, delta)/dz = 1[z>delta].
+//
+// Reductions (alpha, taps, K) are two-level and deterministic: per-CTA
+// partial sums in fixed order, then one CTA sums the partials in double.
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "fft_df.cuh"
+#include "internal.cuh"
+
+namespace db {
+
+constexpr int kAdjThreads = 256;
+constexpr int kAdjMaxTaps = 1024;  // kh * kw limit of the reverse pass
+
+struct AdjImage {
+  int H, W;        // packed pitch W for all internal arrays
+  const float* taps; int kh, kw;
+  RrlParams p;
+};
+
+// ---------------------------------------------------------------------------
+// forward recompute of the intermediates of one iteration
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
+
+__device__ __forceinline__ float phi_w(float b, float f, const RrlParams& p, float* r_out) {
+  const float t = (b - f) / f;
+  const float r = fmaxf(f * (t - log1pf(t)), 0.f);
+  *r_out = r;
+  if (!p.phi_robust) return 1.0f;
+  return p.eps_phi * rsqrtf(r + p.eps_phi * p.eps_phi);
+}
+
+// b = C u and q = (W f/b, W)
+__global__ void k_adj_fwd_q(const float* __restrict__ u, const float* __restrict__ f0, AdjImage im,
+                            float* __restrict__ b_out, float2* __restrict__ q_out) {
+  __shared__ float taps[kAdjMaxTaps];
+  const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
+  __syncthreads();
+  const int n = im.H * im.W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / im.W, j = idx - i * im.W;
+    float b = 0.f;
+    for (int a = 0; a < im.kh; ++a) {
+      const int ii = clampi(i - (a - cy), im.H);
+      for (int c = 0; c < im.kw; ++c) {
+        const float w = taps[a * im.kw + c];
+        if (w != 0.f) b = fmaf(w, u[ii * im.W + clampi(j - (c - cx), im.W)], b);
+      }
+    }
+    const float fv = f0[idx];
+    float r;
+    const float w = phi_w(b, fv, im.p, &r);
+    b_out[idx] = b;
+    q_out[idx] = make_float2(w * fv / b, w);
+  }
+}
+
+__device__ __forceinline__ float psi_g(float gx, float gy, const RrlParams& p) {
+  if (!p.psi_tv) return 1.0f;
+  return rsqrtf(fmaf(gx, gx, fmaf(gy, gy, p.eps_psi * p.eps_psi)));
+}
+
+// A, B = C' q;  g = psi'(|grad u|^2);  D = div(g grad u)  (zero flux)
+__global__ void k_adj_fwd_ab(const float* __restrict__ u, const float2* __restrict__ q, AdjImage im,
+                             float2* __restrict__ ab_out, float* __restrict__ g_out) {
+  __shared__ float taps[kAdjMaxTaps];
+  const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
+  __syncthreads();
+  const int n = im.H * im.W, W = im.W, H = im.H;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / W, j = idx - i * W;
+    float A = 0.f, B = 0.f;
+    for (int a = 0; a < im.kh; ++a) {
+      const int ii = clampi(i + (a - cy), H);
+      for (int c = 0; c < im.kw; ++c) {
+        const float w = taps[a * im.kw + c];
+        if (w != 0.f) {
+          const float2 v = q[ii * W + clampi(j + (c - cx), W)];
+          A = fmaf(w, v.x, A);
+          B = fmaf(w, v.y, B);
+        }
+      }
+    }
+    ab_out[idx] = make_float2(A, B);
+    const float gx = 0.5f * (u[i * W + clampi(j + 1, W)] - u[i * W + clampi(j - 1, W)]);
+    const float gy = 0.5f * (u[clampi(i + 1, H) * W + j] - u[clampi(i - 1, H) * W + j]);
+    g_out[idx] = psi_g(gx, gy, im.p);
+  }
+}
+
+// D from u and g (in-image neighbours only: zero flux across the border)
+__device__ __forceinline__ float diffusion_at(const float* u, const float* g, int i, int j, int H, int W) {
+  const int p = i * W + j;
+  const float up = u[p], gp = g[p];
+  float D = 0.f;
+  if (j + 1 < W) D += 0.5f * (g[p + 1] + gp) * (u[p + 1] - up);
+  if (j > 0) D += 0.5f * (g[p - 1] + gp) * (u[p - 1] - up);
+  if (i + 1 < H) D += 0.5f * (g[p + W] + gp) * (u[p + W] - up);
+  if (i > 0) D += 0.5f * (g[p - W] + gp) * (u[p - W] - up);
+  return D;
+}
+
+// Forward step output (used to rebuild checkpoint segments).
+__global__ void k_adj_fwd_update(const float* __restrict__ u, const float2* __restrict__ ab,
+                                 const float* __restrict__ g, AdjImage im, float* __restrict__ u_out) {
+  const int n = im.H * im.W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / im.W, j = idx - i * im.W;
+    const float D = diffusion_at(u, g, i, j, im.H, im.W);
+    const float2 v = ab[idx];
+    const float num = v.x + im.p.alpha * fmaxf(D, 0.f);
+    const float den = v.y - im.p.alpha * fminf(D, 0.f);
+    u_out[idx] = u[idx] * num / den;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reverse step
+// ---------------------------------------------------------------------------
+__device__ void block_reduce_add(float* partial_out, float v) {
+  __shared__ float red[kAdjThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int k = 0; k < kAdjThreads / 32; ++k) s += red[k];
+    *partial_out = s;
+  }
+  __syncthreads();
+}
+
+// U = U' num/den; Abar, Bbar; Dbar; partial alpha_bar per CTA
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_update(
+    const float* __restrict__ Ubar_next, const float* __restrict__ u, const float2* __restrict__ ab,
+    const float* __restrict__ g, AdjImage im, float* __restrict__ Uacc, float2* __restrict__ abbar,
+    float* __restrict__ Dbar, float* __restrict__ alpha_partial) {
+  const int n = im.H * im.W;
+  float asum = 0.f;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / im.W, j = idx - i * im.W;
+    const float D = diffusion_at(u, g, i, j, im.H, im.W);
+    const float2 v = ab[idx];
+    const float Dp = fmaxf(D, 0.f), Dm = fminf(D, 0.f);
+    const float num = v.x + im.p.alpha * Dp;
+    const float den = v.y - im.p.alpha * Dm;
+    const float ub = Ubar_next[idx], uu = u[idx];
+    const float Ab = ub * uu / den;
+    const float Bb = -ub * uu * num / (den * den);
+    Uacc[idx] = ub * num / den;
+    abbar[idx] = make_float2(Ab, Bb);
+    Dbar[idx] = im.p.alpha * ((D > 0.f ? Ab : 0.f) - (D < 0.f ? Bb : 0.f));
+    asum += Ab * Dp - Bb * Dm;
+  }
+  block_reduce_add(alpha_partial + blockIdx.x, asum);
+}
+
+// Index range {i in [0,n): clip(i + s) == j} for shift s (s = +d for the
+// correlation transpose, s = -d for the convolution transpose).
+__device__ __forceinline__ void preimage(int j, int s, int n, int* lo, int* hi) {
+  if (n == 1) { *lo = 0; *hi = 0; return; }
+  if (j == 0) { *lo = 0; *hi = min(-s, n - 1); return; }              // i + s <= 0
+  if (j == n - 1) { *lo = max(n - 1 - s, 0); *hi = n - 1; return; }   // i + s >= n-1
+  const int i = j - s;
+  *lo = i; *hi = (i >= 0 && i < n) ? i : i - 1;                        // empty if out of range
+}
+
+// qbar = C'^T (Abar, Bbar);  tap partials of Abar q1(clip(i+d)) + Bbar q2(clip(i+d))
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT(const float2* __restrict__ abbar,
+                                                                const float2* __restrict__ q, AdjImage im,
+                                                                float2* __restrict__ qbar,
+                                                                float* __restrict__ tap_partial) {
+  __shared__ float taps[kAdjMaxTaps];
+  const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
+  __syncthreads();
+  const int n = im.H * im.W, H = im.H, W = im.W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / W, j = idx - i * W;
+    float s1 = 0.f, s2 = 0.f;
+    for (int a = 0; a < im.kh; ++a) {
+      int ilo, ihi;
+      preimage(i, a - cy, H, &ilo, &ihi);
+      for (int c = 0; c < im.kw; ++c) {
+        const float w = taps[a * im.kw + c];
+        int jlo, jhi;
+        preimage(j, c - cx, W, &jlo, &jhi);
+        float z1 = 0.f, z2 = 0.f;
+        for (int ii = ilo; ii <= ihi; ++ii)
+          for (int jj = jlo; jj <= jhi; ++jj) {
+            const float2 v = abbar[ii * W + jj];
+            z1 += v.x;
+            z2 += v.y;
+          }
+        s1 = fmaf(w, z1, s1);
+        s2 = fmaf(w, z2, s2);
+      }
+    }
+    qbar[idx] = make_float2(s1, s2);
+  }
+  // tap gradient partials: each CTA covers a fixed slice of pixels
+  for (int t = 0; t < nt; ++t) {
+    const int dy = t / im.kw - cy, dx = t % im.kw - cx;
+    float acc = 0.f;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+      const int i = idx / W, j = idx - i * W;
+      const float2 v = abbar[idx];
+      const float2 qq = q[clampi(i + dy, H) * W + clampi(j + dx, W)];
+      acc = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc));
+    }
+    block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc);
+  }
+}
+
+// bbar and the f0 contribution from qbar
+__global__ void k_adj_rev_weight(const float2* __restrict__ qbar, const float* __restrict__ b,
+                                 const float* __restrict__ f0, AdjImage im, float* __restrict__ bbar,
+                                 float* __restrict__ f0bar) {
+  const int n = im.H * im.W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const float bv = b[idx], fv = f0[idx];
+    float r;
+    const float w = phi_w(bv, fv, im.p, &r);
+    const float2 qb = qbar[idx];
+    const float Wbar = qb.x * fv / bv + qb.y;
+    // phi''(r) = -phi'(r)^3 / (2 eps^2) for the regularised L1 penaliser
+    const float rbar = im.p.phi_robust ? Wbar * (-w * w * w / (2.f * im.p.eps_phi * im.p.eps_phi)) : 0.f;
+    bbar[idx] = -qb.x * w * fv / (bv * bv) + rbar * (1.f - fv / bv);
+    f0bar[idx] += qb.x * w / bv - rbar * logf(bv / fv);
+  }
+}
+
+// U += C^T bbar;  tap partials of bbar(i) u(clip(i-d))
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT(const float* __restrict__ bbar,
+                                                                const float* __restrict__ u, AdjImage im,
+                                                                float* __restrict__ Uacc,
+                                                                float* __restrict__ tap_partial) {
+  __shared__ float taps[kAdjMaxTaps];
+  const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
+  __syncthreads();
+  const int n = im.H * im.W, H = im.H, W = im.W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / W, j = idx - i * W;
+    float s = 0.f;
+    for (int a = 0; a < im.kh; ++a) {
+      int ilo, ihi;
+      preimage(i, -(a - cy), H, &ilo, &ihi);
+      for (int c = 0; c < im.kw; ++c) {
+        const float w = taps[a * im.kw + c];
+        int jlo, jhi;
+        preimage(j, -(c - cx), W, &jlo, &jhi);
+        float z = 0.f;
+        for (int ii = ilo; ii <= ihi; ++ii)
+          for (int jj = jlo; jj <= jhi; ++jj) z += bbar[ii * W + jj];
+        s = fmaf(w, z, s);
+      }
+    }
+    Uacc[idx] += s;
+  }
+  for (int t = 0; t < nt; ++t) {
+    const int dy = t / im.kw - cy, dx = t % im.kw - cx;
+    float acc = 0.f;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+      const int i = idx / W, j = idx - i * W;
+      acc = fmaf(bbar[idx], u[clampi(i - dy, H) * W + clampi(j - dx, W)], acc);
+    }
+    block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc);
+  }
+}
+
+// Diffusion adjoint, pass 1: flux part of U and the per-pixel terms
+// ah = sbar (u_E - u_W)/2, av = sbar (u_S - u_N)/2 with sbar = gbar psi''(s).
+__global__ void k_adj_rev_diff1(const float* __restrict__ Dbar, const float* __restrict__ u,
+                                const float* __restrict__ g, AdjImage im, float* __restrict__ Uacc,
+                                float2* __restrict__ a_out) {
+  const int n = im.H * im.W, H = im.H, W = im.W;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = p / W, j = p - i * W;
+    const float up = u[p], gp = g[p], dp = Dbar[p];
+    float ub = 0.f, gb = 0.f;
+    if (j + 1 < W) { const int q = p + 1; ub -= 0.5f * (dp - Dbar[q]) * (gp + g[q]); gb += 0.5f * (dp - Dbar[q]) * (u[q] - up); }
+    if (j > 0)     { const int q = p - 1; ub -= 0.5f * (dp - Dbar[q]) * (gp + g[q]); gb += 0.5f * (dp - Dbar[q]) * (u[q] - up); }
+    if (i + 1 < H) { const int q = p + W; ub -= 0.5f * (dp - Dbar[q]) * (gp + g[q]); gb += 0.5f * (dp - Dbar[q]) * (u[q] - up); }
+    if (i > 0)     { const int q = p - W; ub -= 0.5f * (dp - Dbar[q]) * (gp + g[q]); gb += 0.5f * (dp - Dbar[q]) * (u[q] - up); }
+    Uacc[p] += ub;
+    // psi''(s) = -psi'(s)^3 / 2 for TV; 0 for linear diffusion
+    const float sbar = im.p.psi_tv ? gb * (-0.5f * gp * gp * gp) : 0.f;
+    const float dxu = 0.5f * (u[i * W + clampi(j + 1, W)] - u[i * W + clampi(j - 1, W)]);
+    const float dyu = 0.5f * (u[clampi(i + 1, H) * W + j] - u[clampi(i - 1, H) * W + j]);
+    a_out[p] = make_float2(sbar * dxu, sbar * dyu);
+  }
+}
+
+// Diffusion adjoint, pass 2: gather of the neighbour-difference terms
+// (s_p depends on u at clip(p +- e_x), clip(p +- e_y)).
+__global__ void k_adj_rev_diff2(const float2* __restrict__ a, AdjImage im, float* __restrict__ Uacc) {
+  const int n = im.H * im.W, H = im.H, W = im.W;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = p / W, j = p - i * W;
+    float s = 0.f;
+    // east neighbour of (i, j-1) is (i, j); of (i, W-1) itself
+    if (j >= 1) s += a[p - 1].x;
+    if (j == W - 1) s += a[p].x;
+    // west neighbour of (i, j+1) is (i, j); of (i, 0) itself
+    if (j <= W - 2) s -= a[p + 1].x;
+    if (j == 0) s -= a[p].x;
+    if (i >= 1) s += a[p - W].y;
+    if (i == H - 1) s += a[p].y;
+    if (i <= H - 2) s -= a[p + W].y;
+    if (i == 0) s -= a[p].y;
+    Uacc[p] += s;
+  }
+}
+
+// Sum `nparts` partials of each of `nsum` sums in fixed order, in double,
+// and add them into out[k].
+__global__ void k_adj_reduce(const float* __restrict__ partials, int nsum, int nparts, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  if (k >= nsum) return;
+  __shared__ double red[kAdjThreads];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += (double)partials[(size_t)k * nparts + t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] += red[0];
+}
+
+__global__ void k_copy_pitched(const float* __restrict__ src, int lds, float* __restrict__ dst, int ldd,
+                               int H, int W, const float* __restrict__ mask_src, float mask_floor) {
+  const size_t n = (size_t)H * W;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / W), j = (int)(idx - (size_t)i * W);
+    float v = src[(size_t)i * lds + j];
+    if (mask_src) v = (mask_src[(size_t)i * lds + j] > mask_floor) ? v : 0.f;
+    dst[(size_t)i * ldd + j] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wiener adjoint for a PSF on one row (float-float transforms, one real row
+// per sequence):
+//   U0 = DFT(u0bar_row) (masked by 1[w > delta]),  F0 = DFT(f0_row)
+//   f0bar_row += Re IDFT(U0 conj(M)) / N          (transpose of the filter)
+//   P(k) = conj(U0(k)) F0(k)  (summed over rows)  for the K and tap gradients
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_wiener_rows(const float* __restrict__ u0bar,
+                                                         const float* __restrict__ f0, int W,
+                                                         const float4* __restrict__ spec, Dft1ff D, float K,
+                                                         float2 invN, float* __restrict__ f0bar,
+                                                         float2* __restrict__ prow) {
+  extern __shared__ float4 sm[];
+  const int M = 1 << D.logM;
+  float4* x = sm;       // DFT(u0bar)
+  float4* y = sm + M;   // DFT(f0)
+  const int r = blockIdx.x;
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    x[c] = make_float4(u0bar[(size_t)r * W + c], 0.f, 0.f, 0.f);
+    y[c] = make_float4(f0[(size_t)r * W + c], 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  dft_fwd_ff(x, 1, 1, M, D, false);
+  dft_fwd_ff(y, 1, 1, M, D, false);
+  for (int k = threadIdx.x; k < W; k += blockDim.x) {
+    const float4 U = x[k], F = y[k], S = __ldg(spec + k);
+    // P(k) = conj(U) F
+    const float4 P = zmulc(F, U);
+    prow[(size_t)r * W + k] = make_float2(P.x + P.y, P.z + P.w);
+    // U conj(M) = U S / (|S|^2 + K)
+    const float2 den = ff_add(ff_add(ff_mul(re_(S), re_(S)), ff_mul(im_(S), im_(S))), make_float2(K, 0.f));
+    const float4 t = zmul(U, S);
+    x[k] = mkc(ff_div(re_(t), den), ff_div(im_(t), den));
+  }
+  __syncthreads();
+  dft_inv_ff(x, 1, 1, M, D, false);
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    const float2 v = ff_mul(re_(x[c]), invN);
+    f0bar[(size_t)r * W + c] += v.x + v.y;
+  }
+}
+
+// Column sums of prow (rows x W complex) in double: P(k).
+__global__ void k_adj_psum(const float2* __restrict__ prow, int rows, int W, double2* __restrict__ P) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= W) return;
+  double sr = 0.0, si = 0.0;
+  for (int r = 0; r < rows; ++r) {
+    const float2 v = prow[(size_t)r * W + k];
+    sr += v.x;
+    si += v.y;
+  }
+  P[k] = make_double2(sr, si);
+}
+
+// K and tap gradients of the Wiener step from P(k):
+//   M = conj(S)/(|S|^2+K);  dM/dK = -conj(S)/(|S|^2+K)^2
+//   dM/dS = -conj(S)^2/(|S|^2+K)^2,  dM/dconj(S) = K/(|S|^2+K)^2
+//   d(loss) = Re sum_k P(k) dM(k) / N,  dS(k)/dh(d) = E_d(k) (spectrum of a
+//   unit tap at offset d, same storage order as S).
+// One CTA; thread t < kw handles tap t, thread kw handles K.
+__global__ void k_adj_wiener_params(const double2* __restrict__ P, const float4* __restrict__ spec,
+                                    const float4* __restrict__ unit_spec, int W, int kw, float K,
+                                    double* __restrict__ grad_taps, double* __restrict__ grad_K) {
+  for (int t = threadIdx.x; t <= kw; t += blockDim.x) {
+  double acc = 0.0;
+  for (int k = 0; k < W; ++k) {
+    const float4 Sf = spec[k];
+    const double sr = (double)Sf.x + (double)Sf.y, si = (double)Sf.z + (double)Sf.w;
+    const double den = sr * sr + si * si + (double)K;
+    const double pr = P[k].x, pi = P[k].y;
+    if (t == kw) {
+      // Re P * (-conj(S)/den^2)
+      acc += -(pr * sr + pi * si) / (den * den);
+    } else {
+      const float4 Ef = unit_spec[(size_t)t * W + k];
+      const double er = (double)Ef.x + (double)Ef.y, ei = (double)Ef.z + (double)Ef.w;
+      // dM/dS * E + dM/dconj(S) * conj(E)
+      const double c2r = sr * sr - si * si, c2i = -2.0 * sr * si;           // conj(S)^2
+      const double ar = -(c2r * er - c2i * ei) / (den * den);
+      const double ai = -(c2r * ei + c2i * er) / (den * den);
+      const double br = (double)K * er / (den * den), bi = -(double)K * ei / (den * den);
+      const double mr = ar + br, mi = ai + bi;
+      acc += pr * mr - pi * mi;
+    }
+  }
+  acc /= (double)W;
+  if (t == kw) *grad_K += acc;
+  else grad_taps[t] += acc;
+  }
+}
+
+// Spectra of unit taps at each offset of a one-row PSF: row t holds the
+// wrapped unit impulse at column (t - kw/2) mod W.
+__global__ void k_unit_taps(float* __restrict__ out, int kw) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < kw * kw; t += gridDim.x * blockDim.x)
+    out[t] = ((t / kw) == (t % kw)) ? 1.f : 0.f;
+}
+
+}  // namespace db
+
+namespace db {
+
+constexpr int kAdjBlocks = 296;  // 2 x 148 SMs, grid-stride
+
+struct AdjLayout {
+  size_t f0, seg, b, q, ab, g, ubar, uacc, abbar, dbar, qbar, bbar, f0bar, a, part, wraw, prow, psum,
+      spec, unit_taps, unit_spec, tabs, total;
+};
+
+static AdjLayout adj_layout(int H, int W, int kw, int ntaps, int every) {
+  AdjLayout L = {};
+  const size_t n = (size_t)H * W;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
+  L.f0 = take(n * 4);
+  L.seg = take(n * 4 * (size_t)(every + 1));
+  L.b = take(n * 4);
+  L.q = take(n * 8);
+  L.ab = take(n * 8);
+  L.g = take(n * 4);
+  L.ubar = take(n * 4);
+  L.uacc = take(n * 4);
+  L.abbar = take(n * 8);
+  L.dbar = take(n * 4);
+  L.qbar = take(n * 8);
+  L.bbar = take(n * 4);
+  L.f0bar = take(n * 4);
+  L.a = take(n * 8);
+  L.part = take((size_t)(ntaps + 1) * kAdjBlocks * 4);
+  L.wraw = take(n * 4);
+  L.prow = take(n * 8);
+  L.psum = take((size_t)W * 16);
+  L.spec = take((size_t)W * 16);
+  L.unit_taps = take((size_t)kw * kw * 4);
+  L.unit_spec = take((size_t)kw * W * 16);
+  L.tabs = take(dft_table_elems(W) * 16);
+  L.total = off;
+  return L;
+}
+
+size_t adj_ws_bytes(int H, int W, int kh, int kw, int every) {
+  return adj_layout(H, W, kw, kh * kw, every).total;
+}
+
+__global__ void k_floor_pack(const float* __restrict__ f, int ld, int H, int W, float delta, float* __restrict__ f0) {
+  const size_t n = (size_t)H * W;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / W), j = (int)(idx - (size_t)i * W);
+    f0[idx] = fmaxf(f[(size_t)i * ld + j], delta);
+  }
+}
+
+__global__ void k_grad_f_out(const float* __restrict__ f0bar, const float* __restrict__ f, int ld, int H, int W,
+                             float delta, float* __restrict__ grad_f) {
+  const size_t n = (size_t)H * W;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / W), j = (int)(idx - (size_t)i * W);
+    grad_f[(size_t)i * ld + j] = (f[(size_t)i * ld + j] > delta) ? f0bar[idx] : 0.f;
+  }
+}
+
+#define ADJ_CHECK(x) do { if ((x) != cudaSuccess) { (void)cudaGetLastError(); return DB_ERR_CUDA; } } while (0)
+#define ADJ_LAUNCH(...) do { __VA_ARGS__; count_launch(); ADJ_CHECK(cudaGetLastError()); } while (0)
+
+db_status adj_backward(const float* f, int ld, const float* ckpt, int iters, int every, const float* grad_u,
+                       int H, int W, const db_psf* psf, const db_params* p, float* grad_f, double* grad_taps,
+                       double* grad_alpha, double* grad_K, void* ws, size_t ws_bytes, int* status,
+                       cudaStream_t s) {
+  const int kh = psf->kh, kw = psf->kw, ntaps = kh * kw;
+  if (ntaps > kAdjMaxTaps || kh != 1) return DB_ERR_UNSUPPORTED;
+  const AdjLayout L = adj_layout(H, W, kw, ntaps, every);
+  if (!ws || ((uintptr_t)ws & 255u) != 0 || ws_bytes < L.total) return DB_ERR_WORKSPACE;
+  char* base = (char*)ws;
+  const size_t n = (size_t)H * W;
+  float* f0 = (float*)(base + L.f0);
+  float* seg = (float*)(base + L.seg);
+  float* b = (float*)(base + L.b);
+  float2* q = (float2*)(base + L.q);
+  float2* ab = (float2*)(base + L.ab);
+  float* g = (float*)(base + L.g);
+  float* ubar = (float*)(base + L.ubar);
+  float* uacc = (float*)(base + L.uacc);
+  float2* abbar = (float2*)(base + L.abbar);
+  float* dbar = (float*)(base + L.dbar);
+  float2* qbar = (float2*)(base + L.qbar);
+  float* bbar = (float*)(base + L.bbar);
+  float* f0bar = (float*)(base + L.f0bar);
+  float2* av = (float2*)(base + L.a);
+  float* part = (float*)(base + L.part);
+  float* wraw = (float*)(base + L.wraw);
+  float2* prow = (float2*)(base + L.prow);
+  double2* psum = (double2*)(base + L.psum);
+  float4* spec = (float4*)(base + L.spec);
+  float* unit_taps = (float*)(base + L.unit_taps);
+  float4* unit_spec = (float4*)(base + L.unit_spec);
+  float4* tabs = (float4*)(base + L.tabs);
+
+  AdjImage im;
+  im.H = H; im.W = W; im.taps = psf->taps; im.kh = kh; im.kw = kw;
+  im.p.alpha = p->alpha; im.p.eps_phi = p->eps_phi; im.p.eps_psi = p->eps_psi; im.p.floor = p->pos_floor;
+  im.p.phi_robust = p->phi_robust; im.p.psi_tv = p->psi_tv;
+  const int G = kAdjBlocks, T = kAdjThreads;
+
+  ADJ_LAUNCH(k_floor_pack<<<G, T, 0, s>>>(f, ld, H, W, p->pos_floor, f0));
+  ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(grad_u, ld, ubar, W, H, W, nullptr, 0.f));
+  ADJ_CHECK(cudaMemsetAsync(f0bar, 0, n * 4, s));
+
+  const int nseg = iters > 0 ? (iters - 1) / every + 1 : 0;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * every, k1 = (k0 + every < iters) ? k0 + every : iters;
+    ADJ_CHECK(cudaMemcpyAsync(seg, ckpt + (size_t)sg * n, n * 4, cudaMemcpyDeviceToDevice, s));
+    for (int k = k0; k + 1 < k1; ++k) {  // rebuild the segment's iterates
+      float* uk = seg + (size_t)(k - k0) * n;
+      ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
+      ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+      ADJ_LAUNCH(k_adj_fwd_update<<<G, T, 0, s>>>(uk, ab, g, im, uk + n));
+    }
+    for (int k = k1 - 1; k >= k0; --k) {  // reverse steps
+      const float* uk = seg + (size_t)(k - k0) * n;
+      ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
+      ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+      ADJ_LAUNCH(k_adj_rev_update<<<G, T, 0, s>>>(ubar, uk, ab, g, im, uacc, abbar, dbar, part));
+      ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
+      ADJ_LAUNCH(k_adj_rev_corrT<<<G, T, 0, s>>>(abbar, q, im, qbar, part));
+      ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
+      ADJ_LAUNCH(k_adj_rev_weight<<<G, T, 0, s>>>(qbar, b, f0, im, bbar, f0bar));
+      ADJ_LAUNCH(k_adj_rev_convT<<<G, T, 0, s>>>(bbar, uk, im, uacc, part));
+      ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
+      ADJ_LAUNCH(k_adj_rev_diff1<<<G, T, 0, s>>>(dbar, uk, g, im, uacc, av));
+      ADJ_LAUNCH(k_adj_rev_diff2<<<G, T, 0, s>>>(av, im, uacc));
+      float* t = ubar; ubar = uacc; uacc = t;
+    }
+  }
+  // Wiener step (row PSF): raw output w for the floor mask, then the adjoint
+  Dft1ff D;
+  ADJ_CHECK(prepare_dft(W, tabs, &D, nullptr, s));
+  {
+    WsLayout WL = {};
+    // run_wiener needs spec and table regions: the spectrum region (W
+    // float4) and the table region of this layout
+    WL.spec = L.spec;
+    WL.work = L.spec;  // not used for a one-row PSF
+    WL.tw = L.tabs;
+    ADJ_CHECK(run_wiener(f0, wraw, H, W, W, psf->taps, kh, kw, p->K, -FLT_MAX, ws, WL, status, s));
+  }
+  ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(ubar, W, uacc, W, H, W, wraw, p->pos_floor));
+  ADJ_CHECK(psf_row_spectrum(psf->taps, kw, D, spec, s));
+  ADJ_LAUNCH(k_unit_taps<<<(kw * kw + 255) / 256, 256, 0, s>>>(unit_taps, kw));
+  for (int t = 0; t < kw; ++t) ADJ_CHECK(psf_row_spectrum(unit_taps + (size_t)t * kw, kw, D, unit_spec + (size_t)t * W, s));
+  const int M = 1 << D.logM;
+  const size_t smem = (size_t)2 * M * sizeof(float4);
+  if (smem > 227 * 1024) return DB_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024) ADJ_CHECK(cudaFuncSetAttribute(k_adj_wiener_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const double invN = 1.0 / (double)W;
+  const float2 invNf = make_float2((float)invN, (float)(invN - (double)(float)invN));
+  ADJ_LAUNCH(k_adj_wiener_rows<<<H, 256, smem, s>>>(uacc, f0, W, spec, D, p->K, invNf, f0bar, prow));
+  ADJ_LAUNCH(k_adj_psum<<<(W + 255) / 256, 256, 0, s>>>(prow, H, W, psum));
+  ADJ_LAUNCH(k_adj_wiener_params<<<1, 1024, 0, s>>>(psum, spec, unit_spec, W, kw, p->K, grad_taps, grad_K));
+  ADJ_LAUNCH(k_grad_f_out<<<G, T, 0, s>>>(f0bar, f, ld, H, W, p->pos_floor, grad_f));
+  return DB_OK;
+}
+
+}  // namespace db
+
+using namespace db;
+
+extern "C" {
+
+size_t db_backward_workspace_bytes(int H, int W, const db_psf* psf, int ckpt_every) {
+  if (!psf || H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ckpt_every < 1) return 0;
+  if (psf->kh < 1 || psf->kw < 1 || psf->kh > H || psf->kw > W) return 0;
+  return adj_ws_bytes(H, W, psf->kh, psf->kw, ckpt_every);
+}
+
+db_status db_rrl_backward(const float* f, const float* ckpt, const float* grad_u, int H, int W, int ld,
+                          const db_psf* psf, const db_params* p, int iters, int ckpt_every, float* grad_f,
+                          double* grad_taps, double* grad_alpha, double* grad_K, void* ws, size_t ws_bytes,
+                          int* dev_status, void* stream) {
+  if (!f || !ckpt || !grad_u || !psf || !psf->taps || !p || !grad_f || !grad_taps || !grad_alpha || !grad_K)
+    return DB_ERR_ARG;
+  if (H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ld < W) return DB_ERR_SHAPE;
+  if (psf->kh < 1 || psf->kw < 1 || psf->kh > H || psf->kw > W) return DB_ERR_PSF;
+  if (iters < 0 || ckpt_every < 1) return DB_ERR_ARG;
+  if (!(p->K > 0.f) || !(p->alpha >= 0.f) || !(p->eps_phi > 0.f) || !(p->eps_psi > 0.f) || !(p->pos_floor > 0.f))
+    return DB_ERR_ARG;
+  if (p->conv != DB_CONV_CLAMP) return DB_ERR_UNSUPPORTED;
+  return adj_backward(f, ld, ckpt, iters, ckpt_every, grad_u, H, W, psf, p, grad_f, grad_taps, grad_alpha,
+                      grad_K, ws, ws_bytes, dev_status, (cudaStream_t)stream);
+}
+
+}  // extern "C"

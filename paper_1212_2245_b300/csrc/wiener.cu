@@ -380,6 +380,13 @@ cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W,
   return launch_cols<COL_FWD>(c, W, s);
 }
 
+// Spectrum (storage order of D) of a one-row PSF of kw taps.
+cudaError_t psf_row_spectrum(const float* taps, int kw, const Dft1ff& D, float4* out, cudaStream_t s) {
+  FftArgs a = {};
+  a.taps = taps; a.kh = 1; a.kw = kw; a.nrows = 1; a.D = D; a.cbuf = out; a.ldc = D.N;
+  return launch_rows<ROW_PSF>(a, s);
+}
+
 __global__ void k_round_spectrum(const float4* __restrict__ in, float2* __restrict__ out, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     const float4 v = in[k];
