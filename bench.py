@@ -19,6 +19,7 @@ image (independent replicas, weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -47,8 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512"], default="line1024",
-                    help="line1024 (default, the headline workload), box256, gauss2048, batch512")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512", "learn512"], default="line1024",
+                    help="line1024 (default, the headline workload), box256, gauss2048, batch512, learn512")
     return ap.parse_args()
 
 
@@ -189,7 +190,7 @@ def run_reference(args, ws_, rank):
     if rank != 0:
         return
     import oracle
-    case = make_case(args.workload if args.workload != "batch512" else "line1024")
+    case = make_case(args.workload if args.workload in WORKLOADS else "line1024")
     p, h = case.params, case.h
     rows = min(128, case.f.shape[0])
     f = case.f[:rows].astype(np.float64)
@@ -465,6 +466,103 @@ def run_batch(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_learn(args, world, rank, local):
+    """64 x 512^2 images, 21 learnable row taps, alpha and K: forward (Wiener +
+    15 RRRL, checkpoints every 5) + MSE loss gradient + backward (gradients for
+    f, taps, alpha, K), one CUDA graph per step; the forward alone beside it."""
+    import paper_1212_2245_b300 as db
+    from paper_1212_2245_b300 import _lib, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+    case = synth.case_learn512(64)
+    N, H, W = case.f.shape
+    iters, every, p = case.iters, 5, case.params
+    f = torch.as_tensor(case.f).to(dev)
+    g = torch.as_tensor(case.g).to(dev)
+    taps = torch.as_tensor(case.h).to(dev).contiguous()
+    u = torch.empty_like(f)
+    nck = (iters - 1) // every + 1
+    ck = torch.empty(N, nck, H, W, device=dev)
+    ws = db.Workspace.for_image(H, W, 1, taps.shape[1], p)
+    bws = db.Workspace(lib.db_backward_workspace_bytes(H, W, N, ctypes.byref(_lib.DbPsf(1, taps.shape[1], 0, taps.data_ptr())), every))
+    gt = torch.zeros(taps.numel(), dtype=torch.float64, device=dev)
+    ga = torch.zeros(1, dtype=torch.float64, device=dev)
+    gk = torch.zeros(1, dtype=torch.float64, device=dev)
+    gf = torch.empty_like(f)
+    gu = torch.empty_like(f)
+    stream = torch.cuda.Stream(device=dev)
+
+    def forward():
+        for n in range(N):
+            db.wiener(f[n], taps, p, out=u[n], ws=ws, check=False)
+            db.rrl_iterate(f[n], u[n], taps, p, iters, ckpt=ck[n], ckpt_every=every, ws=ws, check=False)
+
+    def step():
+        forward()
+        torch.sub(u, g, out=gu)
+        gu.mul_(2.0 / u.numel())
+        gt.zero_(); ga.zero_(); gk.zero_()
+        db.rrl_backward(f, ck, gu, taps, p, iters, every, gt, ga, gk, grad_f=gf, ws=bws, check=False)
+
+    with torch.cuda.stream(stream):
+        ws.reset_status(); bws.reset_status()
+        step()
+        stream.synchronize()
+        ws.raise_on_flags("forward"); bws.raise_on_flags("backward")
+        n0 = lib.db_launch_count()
+        g_step, g_fwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_step, stream=stream):
+            step()
+        n1 = lib.db_launch_count()
+        with torch.cuda.graph(g_fwd, stream=stream):
+            forward()
+        for _ in range(max(args.warmup, 3)):
+            g_step.replay()
+            g_fwd.replay()
+        stream.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                ev[k][0].record(stream)
+                g_step.replay()
+                ev[k][1].record(stream)
+                ev[k][2].record(stream)
+                g_fwd.replay()
+                ev[k][3].record(stream)
+        torch.cuda.synchronize()
+    ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    ms_f = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    ws.raise_on_flags("timed forward"); bws.raise_on_flags("timed backward")
+    if rank != 0:
+        return
+    pxi = N * H * W * iters
+    hbm_peak, hbm_src = peaks()
+    # algorithmic bytes per pixel and iteration: forward 12, backward (recompute
+    # 12 + reverse reads u, f, U', writes U') 28
+    ach = 40.0 * pxi / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC + " (forward + backward)", "value": world * pxi / (ms / 1e3) / 1e6, "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "learn512: 64 x 512x512 f32, 21 learnable row taps + alpha + K, row Wiener "
+                               "+ 15 RRRL (checkpoints every 5), MSE loss, full backward; one CUDA graph per step",
+                   "images": N, "H": H, "W": W, "iters": iters, "ckpt_every": every,
+                   "l2": "working set 0.6 GB > L2"},
+        "forward_only_mpx_iter_s": world * pxi / (ms_f / 1e3) / 1e6, "forward_ms": ms_f,
+        "backward_over_forward": (ms - ms_f) / ms_f,
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                     "traffic": None, "kernel": "whole fwd+bwd step (40 B/px*iter algorithmic)",
+                     "peak_src": hbm_src},
+        "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -478,6 +576,8 @@ def main():
             run_reference(args, world, rank)
         elif args.workload == "batch512":
             run_batch(args, world, rank, local)
+        elif args.workload == "learn512":
+            run_learn(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

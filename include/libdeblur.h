@@ -141,17 +141,21 @@ db_status db_deblur(const float* f, float* u, int H, int W, int ld,
  * conventions d[z]+/dz = 1[z>0], d[z]-/dz = 1[z<0], d max(z,delta)/dz =
  * 1[z>delta].  Supported: spatial mode (p->conv == DB_CONV_CLAMP), a PSF on
  * one row (kh == 1, the 1D motion case of Sec. 4.3), kw <= 1024.
- *   f       the forward's observed image (pitch ld)
+ * A batch of `batch` images that share the PSF and parameters is handled in
+ * one call; image n of f, grad_u and grad_f starts at n*H*ld.
+ *   f       the forward's observed images (pitch ld)
  *   ckpt    the checkpoints the forward db_rrl_iterate wrote with the same
- *           iters and ckpt_every (u0 first; packed, pitch W)
+ *           iters and ckpt_every, image after image: image n's checkpoints
+ *           start at n*nck*H*W, nck = (iters-1)/ckpt_every + 1 (u0 first;
+ *           packed, pitch W)
  *   grad_u  dLoss/du_iters (pitch ld)
  * Outputs: grad_f = dLoss/df (written, pitch ld); grad_taps (kh*kw doubles),
- * grad_alpha and grad_K (one double each) are ACCUMULATED (+=), so one
- * buffer can collect a batch; the caller zeroes them.  The iterates inside a
- * checkpoint segment are recomputed; all reductions are deterministic. */
-size_t db_backward_workspace_bytes(int H, int W, const db_psf* psf, int ckpt_every);
+ * grad_alpha and grad_K (one double each) are ACCUMULATED (+=) over the
+ * batch; the caller zeroes them.  The iterates inside a checkpoint segment
+ * are recomputed; all reductions are deterministic. */
+size_t db_backward_workspace_bytes(int H, int W, int batch, const db_psf* psf, int ckpt_every);
 db_status db_rrl_backward(const float* f, const float* ckpt, const float* grad_u, int H, int W, int ld,
-                          const db_psf* psf, const db_params* p, int iters, int ckpt_every,
+                          int batch, const db_psf* psf, const db_params* p, int iters, int ckpt_every,
                           float* grad_f, double* grad_taps, double* grad_alpha, double* grad_K,
                           void* ws, size_t ws_bytes, int* dev_status, void* stream);
 

@@ -226,14 +226,23 @@ def deblur_batch(fs, taps, params, iters, *, kinds=None, outs=None, check: bool 
 
 def rrl_backward(f, ckpt, grad_u, taps, params, iters, ckpt_every, grad_taps, grad_alpha, grad_K, *,
                  grad_f=None, ws=None, check: bool = True):
-    """Reverse mode of Wiener + `iters` RRRL for one image (db_rrl_backward).
-    grad_taps/grad_alpha/grad_K are float64 CUDA tensors accumulated in place."""
-    H, W, ld = _image(f, "f")
+    """Reverse mode of Wiener + `iters` RRRL (db_rrl_backward) for one image
+    (H, W) or a batch (N, H, W) sharing taps and parameters; ckpt holds each
+    image's checkpoints ((N,) nck, H, W).  grad_taps/grad_alpha/grad_K are
+    float64 CUDA tensors accumulated in place."""
+    batched = f.dim() == 3
+    fb = f if batched else f.unsqueeze(0)
+    N, H, W = fb.shape
+    if not (fb.is_cuda and fb.dtype == torch.float32 and fb.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    gu = grad_u.reshape(N, H, W)
+    if not gu.is_contiguous() or not ckpt.is_contiguous():
+        raise ValueError("grad_u and ckpt must be contiguous")
     gf = grad_f if grad_f is not None else torch.empty_like(f)
     lib = _lib.load()
     psf, p = _db_psf(taps, "general"), _db_params(params)
     if ws is None:
-        n = lib.db_backward_workspace_bytes(H, W, ctypes.byref(psf), int(ckpt_every))
+        n = lib.db_backward_workspace_bytes(H, W, N, ctypes.byref(psf), int(ckpt_every))
         if n == 0:
             raise DeblurError("invalid arguments for the backward workspace query")
         ws = Workspace(n)
@@ -242,7 +251,7 @@ def rrl_backward(f, ckpt, grad_u, taps, params, iters, ckpt_every, grad_taps, gr
     for t in (grad_taps, grad_alpha, grad_K):
         if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
             raise ValueError("parameter gradients must be contiguous float64 CUDA tensors")
-    _check(lib.db_rrl_backward(f.data_ptr(), ckpt.data_ptr(), grad_u.data_ptr(), H, W, ld, ctypes.byref(psf),
+    _check(lib.db_rrl_backward(fb.data_ptr(), ckpt.data_ptr(), gu.data_ptr(), H, W, W, N, ctypes.byref(psf),
                                ctypes.byref(p), int(iters), int(ckpt_every), gf.data_ptr(), grad_taps.data_ptr(),
                                grad_alpha.data_ptr(), grad_K.data_ptr(), ws.ptr, ws.nbytes,
                                ws.status.data_ptr(), _stream()), "db_rrl_backward")
@@ -287,8 +296,7 @@ class DeblurFn(torch.autograd.Function):
         ga = torch.zeros(1, dtype=torch.float64, device=f.device)
         gk = torch.zeros(1, dtype=torch.float64, device=f.device)
         gf = torch.empty_like(f)
-        for n in range(N):
-            rrl_backward(f[n], ckpts[n], grad_u[n], taps_c, ctx.p, ctx.iters, ctx.every, gt, ga, gk, grad_f=gf[n])
+        rrl_backward(f.contiguous(), ckpts, grad_u, taps_c, ctx.p, ctx.iters, ctx.every, gt, ga, gk, grad_f=gf)
         return gf, gt.reshape(taps_c.shape).float(), ga[0].float(), gk[0].float(), None, None, None
 
 

@@ -53,8 +53,8 @@ SIGNATURES = {
     "db_deblur_batch": (c_int, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_void_p, c_size_t, c_void_p,
                                 c_void_p]),
     "db_set_spin_limit": (c_int, [ctypes.c_longlong]),
-    "db_backward_workspace_bytes": (c_size_t, [c_int, c_int, P_PSF, c_int]),
-    "db_rrl_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, P_PSF, P_PAR, c_int, c_int,
+    "db_backward_workspace_bytes": (c_size_t, [c_int, c_int, c_int, P_PSF, c_int]),
+    "db_rrl_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, P_PSF, P_PAR, c_int, c_int,
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "db_status_string": (c_char_p, [c_int]),
     "db_status_from_flags": (c_int, [c_int]),

@@ -38,10 +38,20 @@ constexpr int kAdjThreads = 256;
 constexpr int kAdjMaxTaps = 1024;  // kh * kw limit of the reverse pass
 
 struct AdjImage {
-  int H, W;        // packed pitch W for all internal arrays
+  int N, H, W;     // N images of H x W, packed (pitch W, image stride H*W) internally
   const float* taps; int kh, kw;
   RrlParams p;
 };
+
+// Pixel loop over all N images: idx -> image offset `o`, row i, column j.
+#define ADJ_PIXELS(im)                                                                      \
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x, hw_ = (im).H * (im).W,              \
+           n_ = (im).N * hw_; idx < n_; idx += gridDim.x * blockDim.x)
+#define ADJ_DECOMPOSE(im)                                    \
+  const int img_ = idx / ((im).H * (im).W);                  \
+  const int o = img_ * (im).H * (im).W;                      \
+  const int rem_ = idx - o;                                  \
+  const int i = rem_ / (im).W, j = rem_ - i * (im).W;
 
 // ---------------------------------------------------------------------------
 // forward recompute of the intermediates of one iteration
@@ -63,15 +73,14 @@ __global__ void k_adj_fwd_q(const float* __restrict__ u, const float* __restrict
   const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
   __syncthreads();
-  const int n = im.H * im.W;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / im.W, j = idx - i * im.W;
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
     float b = 0.f;
     for (int a = 0; a < im.kh; ++a) {
       const int ii = clampi(i - (a - cy), im.H);
       for (int c = 0; c < im.kw; ++c) {
         const float w = taps[a * im.kw + c];
-        if (w != 0.f) b = fmaf(w, u[ii * im.W + clampi(j - (c - cx), im.W)], b);
+        if (w != 0.f) b = fmaf(w, u[o + ii * im.W + clampi(j - (c - cx), im.W)], b);
       }
     }
     const float fv = f0[idx];
@@ -94,29 +103,30 @@ __global__ void k_adj_fwd_ab(const float* __restrict__ u, const float2* __restri
   const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
   __syncthreads();
-  const int n = im.H * im.W, W = im.W, H = im.H;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / W, j = idx - i * W;
+  const int W = im.W, H = im.H;
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
     float A = 0.f, B = 0.f;
     for (int a = 0; a < im.kh; ++a) {
       const int ii = clampi(i + (a - cy), H);
       for (int c = 0; c < im.kw; ++c) {
         const float w = taps[a * im.kw + c];
         if (w != 0.f) {
-          const float2 v = q[ii * W + clampi(j + (c - cx), W)];
+          const float2 v = q[o + ii * W + clampi(j + (c - cx), W)];
           A = fmaf(w, v.x, A);
           B = fmaf(w, v.y, B);
         }
       }
     }
     ab_out[idx] = make_float2(A, B);
-    const float gx = 0.5f * (u[i * W + clampi(j + 1, W)] - u[i * W + clampi(j - 1, W)]);
-    const float gy = 0.5f * (u[clampi(i + 1, H) * W + j] - u[clampi(i - 1, H) * W + j]);
+    const float gx = 0.5f * (u[o + i * W + clampi(j + 1, W)] - u[o + i * W + clampi(j - 1, W)]);
+    const float gy = 0.5f * (u[o + clampi(i + 1, H) * W + j] - u[o + clampi(i - 1, H) * W + j]);
     g_out[idx] = psi_g(gx, gy, im.p);
   }
 }
 
-// D from u and g (in-image neighbours only: zero flux across the border)
+// D from u and g (in-image neighbours only: zero flux across the border);
+// u and g point at the image's first pixel.
 __device__ __forceinline__ float diffusion_at(const float* u, const float* g, int i, int j, int H, int W) {
   const int p = i * W + j;
   const float up = u[p], gp = g[p];
@@ -131,10 +141,9 @@ __device__ __forceinline__ float diffusion_at(const float* u, const float* g, in
 // Forward step output (used to rebuild checkpoint segments).
 __global__ void k_adj_fwd_update(const float* __restrict__ u, const float2* __restrict__ ab,
                                  const float* __restrict__ g, AdjImage im, float* __restrict__ u_out) {
-  const int n = im.H * im.W;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / im.W, j = idx - i * im.W;
-    const float D = diffusion_at(u, g, i, j, im.H, im.W);
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
+    const float D = diffusion_at(u + o, g + o, i, j, im.H, im.W);
     const float2 v = ab[idx];
     const float num = v.x + im.p.alpha * fmaxf(D, 0.f);
     const float den = v.y - im.p.alpha * fminf(D, 0.f);
@@ -163,11 +172,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_update(
     const float* __restrict__ Ubar_next, const float* __restrict__ u, const float2* __restrict__ ab,
     const float* __restrict__ g, AdjImage im, float* __restrict__ Uacc, float2* __restrict__ abbar,
     float* __restrict__ Dbar, float* __restrict__ alpha_partial) {
-  const int n = im.H * im.W;
   float asum = 0.f;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / im.W, j = idx - i * im.W;
-    const float D = diffusion_at(u, g, i, j, im.H, im.W);
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
+    const float D = diffusion_at(u + o, g + o, i, j, im.H, im.W);
     const float2 v = ab[idx];
     const float Dp = fmaxf(D, 0.f), Dm = fminf(D, 0.f);
     const float num = v.x + im.p.alpha * Dp;
@@ -193,7 +201,11 @@ __device__ __forceinline__ void preimage(int j, int s, int n, int* lo, int* hi) 
   *lo = i; *hi = (i >= 0 && i < n) ? i : i - 1;                        // empty if out of range
 }
 
-// qbar = C'^T (Abar, Bbar);  tap partials of Abar q1(clip(i+d)) + Bbar q2(clip(i+d))
+// qbar = C'^T (Abar, Bbar);  tap partials of Abar q1(clip(i+d)) + Bbar q2(clip(i+d)).
+// Tap sums: for at most kAdjRegTaps taps each thread keeps one partial per
+// tap in registers over its pixels (one pass); otherwise one pass per tap.
+constexpr int kAdjRegTaps = 32;
+
 __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT(const float2* __restrict__ abbar,
                                                                 const float2* __restrict__ q, AdjImage im,
                                                                 float2* __restrict__ qbar,
@@ -202,9 +214,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT(const float2* __r
   const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
   __syncthreads();
-  const int n = im.H * im.W, H = im.H, W = im.W;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / W, j = idx - i * W;
+  const int H = im.H, W = im.W;
+  float acc[kAdjRegTaps];
+#pragma unroll
+  for (int t = 0; t < kAdjRegTaps; ++t) acc[t] = 0.f;
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
     float s1 = 0.f, s2 = 0.f;
     for (int a = 0; a < im.kh; ++a) {
       int ilo, ihi;
@@ -216,7 +231,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT(const float2* __r
         float z1 = 0.f, z2 = 0.f;
         for (int ii = ilo; ii <= ihi; ++ii)
           for (int jj = jlo; jj <= jhi; ++jj) {
-            const float2 v = abbar[ii * W + jj];
+            const float2 v = abbar[o + ii * W + jj];
             z1 += v.x;
             z2 += v.y;
           }
@@ -225,18 +240,31 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT(const float2* __r
       }
     }
     qbar[idx] = make_float2(s1, s2);
+    if (nt <= kAdjRegTaps) {
+      const float2 v = abbar[idx];
+#pragma unroll
+      for (int t = 0; t < kAdjRegTaps; ++t) {
+        if (t < nt) {
+          const float2 qq = q[o + clampi(i + t / im.kw - cy, H) * W + clampi(j + t % im.kw - cx, W)];
+          acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
+        }
+      }
+    }
   }
-  // tap gradient partials: each CTA covers a fixed slice of pixels
+  if (nt <= kAdjRegTaps) {
+    for (int t = 0; t < nt; ++t) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
+    return;
+  }
   for (int t = 0; t < nt; ++t) {
     const int dy = t / im.kw - cy, dx = t % im.kw - cx;
-    float acc = 0.f;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-      const int i = idx / W, j = idx - i * W;
+    float a2 = 0.f;
+    ADJ_PIXELS(im) {
+      ADJ_DECOMPOSE(im)
       const float2 v = abbar[idx];
-      const float2 qq = q[clampi(i + dy, H) * W + clampi(j + dx, W)];
-      acc = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc));
+      const float2 qq = q[o + clampi(i + dy, H) * W + clampi(j + dx, W)];
+      a2 = fmaf(v.x, qq.x, fmaf(v.y, qq.y, a2));
     }
-    block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc);
+    block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, a2);
   }
 }
 
@@ -244,8 +272,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT(const float2* __r
 __global__ void k_adj_rev_weight(const float2* __restrict__ qbar, const float* __restrict__ b,
                                  const float* __restrict__ f0, AdjImage im, float* __restrict__ bbar,
                                  float* __restrict__ f0bar) {
-  const int n = im.H * im.W;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+  ADJ_PIXELS(im) {
     const float bv = b[idx], fv = f0[idx];
     float r;
     const float w = phi_w(bv, fv, im.p, &r);
@@ -267,9 +294,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT(const float* __re
   const int nt = im.kh * im.kw, cy = im.kh >> 1, cx = im.kw >> 1;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) taps[t] = im.taps[t];
   __syncthreads();
-  const int n = im.H * im.W, H = im.H, W = im.W;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / W, j = idx - i * W;
+  const int H = im.H, W = im.W;
+  float acc[kAdjRegTaps];
+#pragma unroll
+  for (int t = 0; t < kAdjRegTaps; ++t) acc[t] = 0.f;
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
     float s = 0.f;
     for (int a = 0; a < im.kh; ++a) {
       int ilo, ihi;
@@ -280,20 +310,31 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT(const float* __re
         preimage(j, -(c - cx), W, &jlo, &jhi);
         float z = 0.f;
         for (int ii = ilo; ii <= ihi; ++ii)
-          for (int jj = jlo; jj <= jhi; ++jj) z += bbar[ii * W + jj];
+          for (int jj = jlo; jj <= jhi; ++jj) z += bbar[o + ii * W + jj];
         s = fmaf(w, z, s);
       }
     }
     Uacc[idx] += s;
+    if (nt <= kAdjRegTaps) {
+      const float bv = bbar[idx];
+#pragma unroll
+      for (int t = 0; t < kAdjRegTaps; ++t) {
+        if (t < nt) acc[t] = fmaf(bv, u[o + clampi(i - (t / im.kw - cy), H) * W + clampi(j - (t % im.kw - cx), W)], acc[t]);
+      }
+    }
+  }
+  if (nt <= kAdjRegTaps) {
+    for (int t = 0; t < nt; ++t) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
+    return;
   }
   for (int t = 0; t < nt; ++t) {
     const int dy = t / im.kw - cy, dx = t % im.kw - cx;
-    float acc = 0.f;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-      const int i = idx / W, j = idx - i * W;
-      acc = fmaf(bbar[idx], u[clampi(i - dy, H) * W + clampi(j - dx, W)], acc);
+    float a2 = 0.f;
+    ADJ_PIXELS(im) {
+      ADJ_DECOMPOSE(im)
+      a2 = fmaf(bbar[idx], u[o + clampi(i - dy, H) * W + clampi(j - dx, W)], a2);
     }
-    block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc);
+    block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, a2);
   }
 }
 
@@ -302,9 +343,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT(const float* __re
 __global__ void k_adj_rev_diff1(const float* __restrict__ Dbar, const float* __restrict__ u,
                                 const float* __restrict__ g, AdjImage im, float* __restrict__ Uacc,
                                 float2* __restrict__ a_out) {
-  const int n = im.H * im.W, H = im.H, W = im.W;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int i = p / W, j = p - i * W;
+  const int H = im.H, W = im.W;
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
+    const int p = idx;
     const float up = u[p], gp = g[p], dp = Dbar[p];
     float ub = 0.f, gb = 0.f;
     if (j + 1 < W) { const int q = p + 1; ub -= 0.5f * (dp - Dbar[q]) * (gp + g[q]); gb += 0.5f * (dp - Dbar[q]) * (u[q] - up); }
@@ -314,8 +356,8 @@ __global__ void k_adj_rev_diff1(const float* __restrict__ Dbar, const float* __r
     Uacc[p] += ub;
     // psi''(s) = -psi'(s)^3 / 2 for TV; 0 for linear diffusion
     const float sbar = im.p.psi_tv ? gb * (-0.5f * gp * gp * gp) : 0.f;
-    const float dxu = 0.5f * (u[i * W + clampi(j + 1, W)] - u[i * W + clampi(j - 1, W)]);
-    const float dyu = 0.5f * (u[clampi(i + 1, H) * W + j] - u[clampi(i - 1, H) * W + j]);
+    const float dxu = 0.5f * (u[o + i * W + clampi(j + 1, W)] - u[o + i * W + clampi(j - 1, W)]);
+    const float dyu = 0.5f * (u[o + clampi(i + 1, H) * W + j] - u[o + clampi(i - 1, H) * W + j]);
     a_out[p] = make_float2(sbar * dxu, sbar * dyu);
   }
 }
@@ -323,9 +365,11 @@ __global__ void k_adj_rev_diff1(const float* __restrict__ Dbar, const float* __r
 // Diffusion adjoint, pass 2: gather of the neighbour-difference terms
 // (s_p depends on u at clip(p +- e_x), clip(p +- e_y)).
 __global__ void k_adj_rev_diff2(const float2* __restrict__ a, AdjImage im, float* __restrict__ Uacc) {
-  const int n = im.H * im.W, H = im.H, W = im.W;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int i = p / W, j = p - i * W;
+  const int H = im.H, W = im.W;
+  ADJ_PIXELS(im) {
+    ADJ_DECOMPOSE(im)
+    (void)o;
+    const int p = idx;
     float s = 0.f;
     // east neighbour of (i, j-1) is (i, j); of (i, W-1) itself
     if (j >= 1) s += a[p - 1].x;
@@ -479,9 +523,9 @@ struct AdjLayout {
       spec, unit_taps, unit_spec, tabs, total;
 };
 
-static AdjLayout adj_layout(int H, int W, int kw, int ntaps, int every) {
+static AdjLayout adj_layout(int N, int H, int W, int kw, int ntaps, int every) {
   AdjLayout L = {};
-  const size_t n = (size_t)H * W;
+  const size_t n = (size_t)N * H * W;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
   L.f0 = take(n * 4);
@@ -500,7 +544,7 @@ static AdjLayout adj_layout(int H, int W, int kw, int ntaps, int every) {
   L.a = take(n * 8);
   L.part = take((size_t)(ntaps + 1) * kAdjBlocks * 4);
   L.wraw = take(n * 4);
-  L.prow = take(n * 8);
+  L.prow = take(n * 8);  // (N*H) x W
   L.psum = take((size_t)W * 16);
   L.spec = take((size_t)W * 16);
   L.unit_taps = take((size_t)kw * kw * 4);
@@ -510,8 +554,8 @@ static AdjLayout adj_layout(int H, int W, int kw, int ntaps, int every) {
   return L;
 }
 
-size_t adj_ws_bytes(int H, int W, int kh, int kw, int every) {
-  return adj_layout(H, W, kw, kh * kw, every).total;
+size_t adj_ws_bytes(int N, int H, int W, int kh, int kw, int every) {
+  return adj_layout(N, H, W, kw, kh * kw, every).total;
 }
 
 __global__ void k_floor_pack(const float* __restrict__ f, int ld, int H, int W, float delta, float* __restrict__ f0) {
@@ -534,16 +578,17 @@ __global__ void k_grad_f_out(const float* __restrict__ f0bar, const float* __res
 #define ADJ_CHECK(x) do { if ((x) != cudaSuccess) { (void)cudaGetLastError(); return DB_ERR_CUDA; } } while (0)
 #define ADJ_LAUNCH(...) do { __VA_ARGS__; count_launch(); ADJ_CHECK(cudaGetLastError()); } while (0)
 
-db_status adj_backward(const float* f, int ld, const float* ckpt, int iters, int every, const float* grad_u,
-                       int H, int W, const db_psf* psf, const db_params* p, float* grad_f, double* grad_taps,
-                       double* grad_alpha, double* grad_K, void* ws, size_t ws_bytes, int* status,
-                       cudaStream_t s) {
+db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int iters, int every,
+                       const float* grad_u, int H, int W, const db_psf* psf, const db_params* p, float* grad_f,
+                       double* grad_taps, double* grad_alpha, double* grad_K, void* ws, size_t ws_bytes,
+                       int* status, cudaStream_t s) {
   const int kh = psf->kh, kw = psf->kw, ntaps = kh * kw;
   if (ntaps > kAdjMaxTaps || kh != 1) return DB_ERR_UNSUPPORTED;
-  const AdjLayout L = adj_layout(H, W, kw, ntaps, every);
+  if ((size_t)N * H * W >= (size_t)1 << 31) return DB_ERR_SHAPE;
+  const AdjLayout L = adj_layout(N, H, W, kw, ntaps, every);
   if (!ws || ((uintptr_t)ws & 255u) != 0 || ws_bytes < L.total) return DB_ERR_WORKSPACE;
   char* base = (char*)ws;
-  const size_t n = (size_t)H * W;
+  const size_t n = (size_t)N * H * W;  // all images, packed
   float* f0 = (float*)(base + L.f0);
   float* seg = (float*)(base + L.seg);
   float* b = (float*)(base + L.b);
@@ -568,19 +613,23 @@ db_status adj_backward(const float* f, int ld, const float* ckpt, int iters, int
   float4* tabs = (float4*)(base + L.tabs);
 
   AdjImage im;
-  im.H = H; im.W = W; im.taps = psf->taps; im.kh = kh; im.kw = kw;
+  im.N = N; im.H = H; im.W = W; im.taps = psf->taps; im.kh = kh; im.kw = kw;
   im.p.alpha = p->alpha; im.p.eps_phi = p->eps_phi; im.p.eps_psi = p->eps_psi; im.p.floor = p->pos_floor;
   im.p.phi_robust = p->phi_robust; im.p.psi_tv = p->psi_tv;
   const int G = kAdjBlocks, T = kAdjThreads;
 
-  ADJ_LAUNCH(k_floor_pack<<<G, T, 0, s>>>(f, ld, H, W, p->pos_floor, f0));
-  ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(grad_u, ld, ubar, W, H, W, nullptr, 0.f));
+  // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)
+  ADJ_LAUNCH(k_floor_pack<<<G, T, 0, s>>>(f, ld, N * H, W, p->pos_floor, f0));
+  ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(grad_u, ld, ubar, W, N * H, W, nullptr, 0.f));
   ADJ_CHECK(cudaMemsetAsync(f0bar, 0, n * 4, s));
 
   const int nseg = iters > 0 ? (iters - 1) / every + 1 : 0;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * every, k1 = (k0 + every < iters) ? k0 + every : iters;
-    ADJ_CHECK(cudaMemcpyAsync(seg, ckpt + (size_t)sg * n, n * 4, cudaMemcpyDeviceToDevice, s));
+    // checkpoint sg of every image (ckpt is N x nseg x H x W)
+    const size_t hw = (size_t)H * W;
+    ADJ_CHECK(cudaMemcpy2DAsync(seg, hw * 4, ckpt + (size_t)sg * hw, (size_t)nseg * hw * 4, hw * 4, N,
+                                cudaMemcpyDeviceToDevice, s));
     for (int k = k0; k + 1 < k1; ++k) {  // rebuild the segment's iterates
       float* uk = seg + (size_t)(k - k0) * n;
       ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
@@ -613,9 +662,10 @@ db_status adj_backward(const float* f, int ld, const float* ckpt, int iters, int
     WL.spec = L.spec;
     WL.work = L.spec;  // not used for a one-row PSF
     WL.tw = L.tabs;
-    ADJ_CHECK(run_wiener(f0, wraw, H, W, W, psf->taps, kh, kw, p->K, -FLT_MAX, ws, WL, status, s));
+    // a one-row PSF filters every row on its own: the batch is N*H rows
+    ADJ_CHECK(run_wiener(f0, wraw, N * H, W, W, psf->taps, kh, kw, p->K, -FLT_MAX, ws, WL, status, s));
   }
-  ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(ubar, W, uacc, W, H, W, wraw, p->pos_floor));
+  ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(ubar, W, uacc, W, N * H, W, wraw, p->pos_floor));
   ADJ_CHECK(psf_row_spectrum(psf->taps, kw, D, spec, s));
   ADJ_LAUNCH(k_unit_taps<<<(kw * kw + 255) / 256, 256, 0, s>>>(unit_taps, kw));
   for (int t = 0; t < kw; ++t) ADJ_CHECK(psf_row_spectrum(unit_taps + (size_t)t * kw, kw, D, unit_spec + (size_t)t * W, s));
@@ -625,10 +675,10 @@ db_status adj_backward(const float* f, int ld, const float* ckpt, int iters, int
   if (smem > 48 * 1024) ADJ_CHECK(cudaFuncSetAttribute(k_adj_wiener_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const double invN = 1.0 / (double)W;
   const float2 invNf = make_float2((float)invN, (float)(invN - (double)(float)invN));
-  ADJ_LAUNCH(k_adj_wiener_rows<<<H, 256, smem, s>>>(uacc, f0, W, spec, D, p->K, invNf, f0bar, prow));
-  ADJ_LAUNCH(k_adj_psum<<<(W + 255) / 256, 256, 0, s>>>(prow, H, W, psum));
+  ADJ_LAUNCH(k_adj_wiener_rows<<<N * H, 256, smem, s>>>(uacc, f0, W, spec, D, p->K, invNf, f0bar, prow));
+  ADJ_LAUNCH(k_adj_psum<<<(W + 255) / 256, 256, 0, s>>>(prow, N * H, W, psum));
   ADJ_LAUNCH(k_adj_wiener_params<<<1, 1024, 0, s>>>(psum, spec, unit_spec, W, kw, p->K, grad_taps, grad_K));
-  ADJ_LAUNCH(k_grad_f_out<<<G, T, 0, s>>>(f0bar, f, ld, H, W, p->pos_floor, grad_f));
+  ADJ_LAUNCH(k_grad_f_out<<<G, T, 0, s>>>(f0bar, f, ld, N * H, W, p->pos_floor, grad_f));
   return DB_OK;
 }
 
@@ -638,26 +688,27 @@ using namespace db;
 
 extern "C" {
 
-size_t db_backward_workspace_bytes(int H, int W, const db_psf* psf, int ckpt_every) {
-  if (!psf || H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ckpt_every < 1) return 0;
+size_t db_backward_workspace_bytes(int H, int W, int batch, const db_psf* psf, int ckpt_every) {
+  if (!psf || H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ckpt_every < 1 || batch < 1) return 0;
   if (psf->kh < 1 || psf->kw < 1 || psf->kh > H || psf->kw > W) return 0;
-  return adj_ws_bytes(H, W, psf->kh, psf->kw, ckpt_every);
+  return adj_ws_bytes(batch, H, W, psf->kh, psf->kw, ckpt_every);
 }
 
 db_status db_rrl_backward(const float* f, const float* ckpt, const float* grad_u, int H, int W, int ld,
-                          const db_psf* psf, const db_params* p, int iters, int ckpt_every, float* grad_f,
-                          double* grad_taps, double* grad_alpha, double* grad_K, void* ws, size_t ws_bytes,
-                          int* dev_status, void* stream) {
+                          int batch, const db_psf* psf, const db_params* p, int iters, int ckpt_every,
+                          float* grad_f, double* grad_taps, double* grad_alpha, double* grad_K, void* ws,
+                          size_t ws_bytes, int* dev_status, void* stream) {
   if (!f || !ckpt || !grad_u || !psf || !psf->taps || !p || !grad_f || !grad_taps || !grad_alpha || !grad_K)
     return DB_ERR_ARG;
+  if (batch < 1) return DB_ERR_ARG;
   if (H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ld < W) return DB_ERR_SHAPE;
   if (psf->kh < 1 || psf->kw < 1 || psf->kh > H || psf->kw > W) return DB_ERR_PSF;
   if (iters < 0 || ckpt_every < 1) return DB_ERR_ARG;
   if (!(p->K > 0.f) || !(p->alpha >= 0.f) || !(p->eps_phi > 0.f) || !(p->eps_psi > 0.f) || !(p->pos_floor > 0.f))
     return DB_ERR_ARG;
   if (p->conv != DB_CONV_CLAMP) return DB_ERR_UNSUPPORTED;
-  return adj_backward(f, ld, ckpt, iters, ckpt_every, grad_u, H, W, psf, p, grad_f, grad_taps, grad_alpha,
-                      grad_K, ws, ws_bytes, dev_status, (cudaStream_t)stream);
+  return adj_backward(f, ld, batch, ckpt, iters, ckpt_every, grad_u, H, W, psf, p, grad_f, grad_taps,
+                      grad_alpha, grad_K, ws, ws_bytes, dev_status, (cudaStream_t)stream);
 }
 
 }  // extern "C"
