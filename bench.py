@@ -121,6 +121,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# DRAM bytes of one RRRL iteration (k_rrl_q + k_rrl_update, split schedule) on
+# the line1024 workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, caches flushed before the capture).
+LINE1024_ITER_DRAM_BYTES = 8.408064e6 + 12.608256e6
+
+
 def _spatial_model(case, ms_iter):
     """Fused/split spatial iteration: FP32-issue bound; flops per pixel and
     iteration = 3 tap sums (b, A, B) x 2 flops x nnz(h) + 60 pointwise."""
@@ -131,8 +137,9 @@ def _spatial_model(case, ms_iter):
     achieved = flops / (ms_iter / 1e3) / 1e12
     hbm_peak, hbm_src = peaks()
     hbm_equiv = 12.0 * H * W / (ms_iter / 1e3) / 1e9
+    traffic = LINE1024_ITER_DRAM_BYTES if (H, W, int((case.h != 0).sum())) == (1024, 1024, 71) else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "one RRRL iteration (k_rrl_q + k_rrl_update, or k_rrl_spatial)",
+            "traffic": traffic, "kernel": "one RRRL iteration (k_rrl_q + k_rrl_update, or k_rrl_spatial)",
             "kernel_ms": ms_iter, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
             "hbm_equiv_gbs": hbm_equiv, "hbm_equiv_frac": hbm_equiv / hbm_peak,
             "hbm_peak_gbs": hbm_peak, "hbm_peak_src": hbm_src}
