@@ -233,6 +233,22 @@ db_status db_rrl_iterate_noalloc(const float* f, float* u, int H, int W, int ld,
                                  const db_psf* psf, const db_params* p, int iters,
                                  int* dev_status, void* stream);
 
+/* ---- prepared single-image pipeline ----------------------------------------
+ * The paper computes the PSF transform once and reuses it for every image of
+ * a given size (Sec. 5, the set-up excluded from its timings).  A plan does
+ * that set-up once -- transform tables, PSF spectrum, tap groups -- for one
+ * image size, PSF and parameter set; db_plan_run then applies the whole
+ * pipeline of db_deblur to an image: the Wiener image passes and `iters`
+ * RRRL iterations, enqueuing launches and async copies only (capturable in a
+ * CUDA graph).  The plan keeps pointers into ws and the PSF values taken at
+ * creation: re-create it when the taps change.  The result equals
+ * db_deblur's bit for bit. */
+typedef struct db_plan db_plan;
+db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_params* p, int iters, void* ws,
+                         size_t ws_bytes, int* dev_status, void* stream, db_plan** out);
+db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, void* stream);
+void db_plan_destroy(db_plan* plan);
+
 /* Human-readable name of a status code (static storage). */
 const char* db_status_string(db_status s);
 

@@ -16,7 +16,7 @@ from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
+           "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
            "version"]
 
 
@@ -156,6 +156,52 @@ def deblur(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, k
     if check:
         ws.raise_on_flags("db_deblur")
     return u
+
+
+class Plan:
+    """Prepared single-image pipeline (db_plan_create): transform tables, PSF
+    spectrum and tap groups computed once for an image size, PSF and
+    parameters; `run(f, out)` applies Wiener + `iters` RRRL (capturable).
+    The result equals deblur()'s bit for bit."""
+
+    def __init__(self, H: int, W: int, taps: torch.Tensor, params: Params, iters: int, *,
+                 kind: str = "general", ld: int | None = None):
+        ld = W if ld is None else ld
+        self.taps = taps
+        self.ws = Workspace.for_image(H, W, taps.shape[0], taps.shape[1], params)
+        self.ws.reset_status()
+        lib = _lib.load()
+        psf, p = _db_psf(taps, kind), _db_params(params)
+        h = ctypes.c_void_p()
+        _check(lib.db_plan_create(H, W, ld, ctypes.byref(psf), ctypes.byref(p), int(iters), self.ws.ptr,
+                                  self.ws.nbytes, self.ws.status.data_ptr(), _stream(), ctypes.byref(h)),
+               "db_plan_create")
+        self._h = h
+        self.shape, self.ld = (H, W), ld
+
+    def run(self, f: torch.Tensor, out: torch.Tensor | None = None, check: bool = True):
+        H, W, ld = _image(f, "f")
+        if (H, W) != self.shape or ld != self.ld:
+            raise ValueError("image shape or row stride differs from the plan's")
+        u = out if out is not None else torch.empty_like(f)
+        if check:
+            self.ws.reset_status()
+        _check(_lib.load().db_plan_run(self._h, f.data_ptr(), u.data_ptr(), self.ws.status.data_ptr(), _stream()),
+               "db_plan_run")
+        if check:
+            self.ws.raise_on_flags("db_plan_run")
+        return u
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().db_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

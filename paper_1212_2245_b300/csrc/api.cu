@@ -77,6 +77,55 @@ static RrlParams to_rrl(const db_params* p) {
   return r;
 }
 
+// Spatial-mode iterations with tap groups already prepared in the workspace.
+static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld, int kh, int kw,
+                                 const RrlParams& rp, int iters, float* ckpt, int ckpt_every, void* ws,
+                                 const WsLayout& L, int* dev_status, cudaStream_t s) {
+  char* base = (char*)ws;
+  TapGroup* groups = (TapGroup*)(base + L.taps);
+  int* ngroups = (int*)(base + L.ntaps);
+  float* tmp = (float*)(base + L.utmp);
+  float2* qbuf = (float2*)(base + L.qbuf);
+  // schedule: split (q in a global buffer) when u, f and q stay resident in
+  // L2, fused (halo recompute, one pass per iteration) otherwise
+  int sched = g_schedule.load();
+  if (sched == DB_SCHED_AUTO)
+    sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
+  const size_t smem_need = sched == DB_SCHED_SPLIT
+                               ? (rrl_split_smem_q(kh, kw) > rrl_split_smem_update(kh, kw)
+                                      ? rrl_split_smem_q(kh, kw)
+                                      : rrl_split_smem_update(kh, kw))
+                               : rrl_spatial_smem(kh, kw);
+  if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
+  const float* src = u;
+  int ld_src = ld;
+  for (int k = 0; k < iters; ++k) {
+    if (ckpt && k % ckpt_every == 0) {
+      float* dst = ckpt + (size_t)(k / ckpt_every) * H * W;
+      if (cudaMemcpy2DAsync(dst, (size_t)W * sizeof(float), src, (size_t)ld_src * sizeof(float),
+                            (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return DB_ERR_CUDA;
+    }
+    float* dst = (k % 2 == 0) ? tmp : u;
+    const int ld_dst = (k % 2 == 0) ? W : ld;
+    const cudaError_t e =
+        sched == DB_SCHED_SPLIT
+            ? launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, groups, ngroups, kh, kw, rp,
+                               dev_status, s)
+            : launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, kh, kw, rp,
+                                 dev_status, s);
+    if (e != cudaSuccess) return DB_ERR_CUDA;
+    src = dst;
+    ld_src = ld_dst;
+  }
+  if (src != u) {
+    if (cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), src, (size_t)W * sizeof(float),
+                          (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+  }
+  return DB_OK;
+}
+
 }  // namespace db
 
 using namespace db;
@@ -152,52 +201,11 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
       return DB_ERR_CUDA;
     return DB_OK;
   }
-  TapGroup* groups = (TapGroup*)(base + L.taps);
-  int* ngroups = (int*)(base + L.ntaps);
-  float* tmp = (float*)(base + L.utmp);
-  // schedule: split (q in a global buffer) when u, f and q stay resident in
-  // L2, fused (halo recompute, one pass per iteration) otherwise
-  int sched = g_schedule.load();
-  if (sched == DB_SCHED_AUTO)
-    sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
-  const size_t smem_need = sched == DB_SCHED_SPLIT
-                               ? (rrl_split_smem_q(psf->kh, psf->kw) > rrl_split_smem_update(psf->kh, psf->kw)
-                                      ? rrl_split_smem_q(psf->kh, psf->kw)
-                                      : rrl_split_smem_update(psf->kh, psf->kw))
-                               : rrl_spatial_smem(psf->kh, psf->kw);
-  if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
-  float2* qbuf = (float2*)(base + L.qbuf);
-  if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, groups, ngroups, dev_status, s) !=
-      cudaSuccess)
+  if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, (TapGroup*)(base + L.taps),
+                          (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
     return DB_ERR_CUDA;
-  const RrlParams rp = to_rrl(p);
-  const float* src = u;
-  int ld_src = ld;
-  for (int k = 0; k < iters; ++k) {
-    if (ckpt && k % ckpt_every == 0) {
-      float* dst = ckpt + (size_t)(k / ckpt_every) * H * W;
-      if (cudaMemcpy2DAsync(dst, (size_t)W * sizeof(float), src, (size_t)ld_src * sizeof(float),
-                            (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return DB_ERR_CUDA;
-    }
-    float* dst = (k % 2 == 0) ? tmp : u;
-    const int ld_dst = (k % 2 == 0) ? W : ld;
-    const cudaError_t e =
-        sched == DB_SCHED_SPLIT
-            ? launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, groups, ngroups, psf->kh,
-                               psf->kw, rp, dev_status, s)
-            : launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, psf->kh,
-                                 psf->kw, rp, dev_status, s);
-    if (e != cudaSuccess) return DB_ERR_CUDA;
-    src = dst;
-    ld_src = ld_dst;
-  }
-  if (src != u) {
-    if (cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), src, (size_t)W * sizeof(float),
-                          (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return DB_ERR_CUDA;
-  }
-  return DB_OK;
+  return iterate_spatial(f, u, H, W, ld, psf->kh, psf->kw, to_rrl(p), iters, ckpt, ckpt_every, ws, L,
+                         dev_status, s);
 }
 
 db_status db_deblur(const float* f, float* u, int H, int W, int ld, const db_psf* psf,
@@ -207,6 +215,90 @@ db_status db_deblur(const float* f, float* u, int H, int W, int ld, const db_psf
   if (st != DB_OK) return st;
   return db_rrl_iterate(f, u, H, W, ld, psf, p, iters, nullptr, 0, ws, ws_bytes, dev_status, stream);
 }
+
+}  // extern "C"
+
+namespace db {
+struct SinglePlan {
+  int H, W, ld, kh, kw, kind, iters, conv;
+  db_params p;
+  void* ws;
+  WsLayout L;
+  WienerState wst;
+  Dft1 DW32, DH32;  // periodic mode: FP32 twiddles of the iteration transforms
+};
+}  // namespace db
+
+extern "C" {
+
+db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_params* p, int iters, void* ws,
+                         size_t ws_bytes, int* dev_status, void* stream, db_plan** out) {
+  if (!out) return DB_ERR_ARG;
+  *out = nullptr;
+  db_status st;
+  if (H < 1 || W < 1 || H > kMaxSide || W > kMaxSide || ld < W) return DB_ERR_SHAPE;
+  if ((st = check_psf(psf, H, W)) != DB_OK) return st;
+  if ((st = check_params(p)) != DB_OK) return st;
+  if (iters < 0) return DB_ERR_ARG;
+  const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != DB_OK) return st;
+  if (p->conv == DB_CONV_PERIODIC && !(is_pow2(H) && is_pow2(W))) return DB_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  SinglePlan* P = new SinglePlan();
+  P->H = H; P->W = W; P->ld = ld; P->kh = psf->kh; P->kw = psf->kw; P->kind = psf->kind;
+  P->iters = iters; P->conv = p->conv; P->p = *p; P->ws = ws; P->L = L;
+  if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, (TapGroup*)(base + L.taps),
+                          (int*)(base + L.ntaps), dev_status, s) != cudaSuccess) {
+    delete P; return DB_ERR_CUDA;
+  }
+  if (p->conv == DB_CONV_PERIODIC) {
+    // Wiener in float-float with its own spectrum region, iteration spectrum in FP32
+    float4* Sff = (float4*)(base + L.spec);
+    float4* tabW = (float4*)(base + L.tw);
+    float4* tabH = tabW + dft_table_elems(W);
+    Dft1ff FW, FH;
+    if (prepare_dft(W, tabW, &FW, &P->DW32, s) != cudaSuccess || prepare_dft(H, tabH, &FH, &P->DH32, s) != cudaSuccess ||
+        run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, Sff, FW, FH, s) != cudaSuccess ||
+        round_spectrum(Sff, (float2*)(base + L.s32), (size_t)H * W, s) != cudaSuccess) {
+      delete P; return DB_ERR_CUDA;
+    }
+    // the Wiener state reuses the same tables and spectrum (2D transform)
+    P->wst.H = H; P->wst.W = W; P->wst.kh = psf->kh; P->wst.kw = psf->kw; P->wst.DW = FW; P->wst.DH = FH;
+    if (psf->kh == 1 || psf->kw == 1) {
+      // a one-axis PSF: the Wiener filter needs the 1D spectrum instead
+      if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {
+        delete P; return DB_ERR_CUDA;
+      }
+    }
+  } else {
+    if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {
+      delete P; return DB_ERR_CUDA;
+    }
+  }
+  *out = (db_plan*)P;
+  return DB_OK;
+}
+
+db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, void* stream) {
+  SinglePlan* P = (SinglePlan*)plan;
+  if (!P || !f || !u || f == u) return DB_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)P->ws;
+  if (wiener_apply(f, u, P->ld, P->p.K, P->p.pos_floor, P->ws, P->L, P->wst, s) != cudaSuccess) return DB_ERR_CUDA;
+  if (P->iters == 0) return DB_OK;
+  if (P->conv == DB_CONV_PERIODIC) {
+    if (run_rrl_fourier(f, P->ld, u, P->ld, (float*)(base + P->L.utmp), P->H, P->W, (float2*)(base + P->L.work),
+                        (float2*)(base + P->L.qbuf), (const float2*)(base + P->L.s32), P->DW32.tw, P->DH32.tw,
+                        to_rrl(&P->p), P->iters, nullptr, 0, dev_status, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    return DB_OK;
+  }
+  return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, to_rrl(&P->p), P->iters, nullptr, 0, P->ws, P->L,
+                         dev_status, s);
+}
+
+void db_plan_destroy(db_plan* plan) { delete (SinglePlan*)plan; }
 
 const char* db_status_string(db_status s) {
   switch (s) {

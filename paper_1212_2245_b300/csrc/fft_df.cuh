@@ -79,6 +79,13 @@ struct Dft1ff {
   const float4* Bf;  // transform of the circular chirp
 };
 
+// Host-side state of a prepared Wiener filter (tables and spectrum live in
+// the workspace).
+struct WienerState {
+  int H, W, kh, kw;
+  Dft1ff DW, DH;
+};
+
 __device__ __forceinline__ void seq_item_ff(int it, int nseq, int len, bool seq_fast, int& q, int& k) {
   if (seq_fast) { q = it % nseq; k = it / nseq; } else { q = it / len; k = it - q * len; }
 }

@@ -83,6 +83,13 @@ cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W,
 cudaError_t round_spectrum(const float4* in, float2* out, size_t n, cudaStream_t s);
 cudaError_t psf_row_spectrum(const float* taps, int kw, const Dft1ff& D, float4* out, cudaStream_t s);
 
+// Wiener filter in two parts: set-up (tables, PSF spectrum) and image passes.
+struct WienerState;
+cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, void* ws, const WsLayout& L,
+                           WienerState* st, cudaStream_t s);
+cudaError_t wiener_apply(const float* f, float* u0, int ld, float K, float floor_, void* ws, const WsLayout& L,
+                         const WienerState& S, cudaStream_t s);
+
 // batched Wiener filter (host-side plan)
 struct WienerImage {
   const float* f; int ld;        // observed image

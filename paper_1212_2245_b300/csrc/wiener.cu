@@ -405,57 +405,76 @@ static float2 ff_const(double v) {
   return make_float2(hi, (float)(v - (double)hi));
 }
 
-cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps, int kh,
-                       int kw, float K, float floor_, void* ws, const WsLayout& L, int* status,
-                       cudaStream_t s) {
-  (void)status;
+// Set-up part of the Wiener filter: transform tables and the PSF spectrum
+// (depends on the taps and the image size only).
+cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, void* ws, const WsLayout& L,
+                           WienerState* st, cudaStream_t s) {
   char* base = (char*)ws;
   float4* spec = (float4*)(base + L.spec);
-  float4* work = (float4*)(base + L.work);
   float4* tabW = (float4*)(base + L.tw);
   float4* tabH = tabW + dft_table_elems(W);
   cudaError_t e;
-  Dft1ff DW = {}, DH = {};
-  if (kw > 1 || kh == 1) { if ((e = prepare_dft(W, tabW, &DW, nullptr, s)) != cudaSuccess) return e; }
-  if (kh > 1) { if ((e = prepare_dft(H, tabH, &DH, nullptr, s)) != cudaSuccess) return e; }
+  WienerState S = {};
+  S.H = H; S.W = W; S.kh = kh; S.kw = kw;
+  if (kw > 1 || kh == 1) { if ((e = prepare_dft(W, tabW, &S.DW, nullptr, s)) != cudaSuccess) return e; }
+  if (kh > 1) { if ((e = prepare_dft(H, tabH, &S.DH, nullptr, s)) != cudaSuccess) return e; }
   FftArgs a = {};
-  a.K = K;
-  a.floor_ = floor_;
   if (kh == 1) {
-    // PSF along rows: 1D spectrum of length W, then packed row pairs.
-    a.taps = taps; a.kh = 1; a.kw = kw; a.nrows = 1; a.D = DW;
-    a.cbuf = spec; a.ldc = W;
+    a.taps = taps; a.kh = 1; a.kw = kw; a.nrows = 1; a.D = S.DW; a.cbuf = spec; a.ldc = W;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+  } else if (kw == 1) {
+    // a kh x 1 tap array has the memory layout of a 1 x kh row
+    a.taps = taps; a.kh = 1; a.kw = kh; a.nrows = 1; a.D = S.DH; a.cbuf = spec; a.ldc = H;
+    if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+  } else {
+    if ((e = run_psf_spectrum_2d(taps, kh, kw, H, W, spec, S.DW, S.DH, s)) != cudaSuccess) return e;
+  }
+  *st = S;
+  return cudaSuccess;
+}
+
+// Image part: the transforms of f, the gain and the inverse transforms.
+cudaError_t wiener_apply(const float* f, float* u0, int ld, float K, float floor_, void* ws, const WsLayout& L,
+                         const WienerState& S, cudaStream_t s) {
+  char* base = (char*)ws;
+  float4* spec = (float4*)(base + L.spec);
+  float4* work = (float4*)(base + L.work);
+  const int H = S.H, W = S.W;
+  if (S.kh == 1) {
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = DW;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = S.DW;
     b.nrows = (H + 1) / 2; b.img_rows = H;
     b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / W);
     return launch_rows<ROW_WIENER_1D>(b, s);
   }
-  if (kw == 1) {
-    // PSF along columns: 1D spectrum of length H (a kh x 1 tap array has the
-    // memory layout of a 1 x kh row), then packed column pairs.
-    a.taps = taps; a.kh = 1; a.kw = kh; a.nrows = 1; a.D = DH;
-    a.cbuf = spec; a.ldc = H;
-    if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+  if (S.kw == 1) {
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = DH;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = S.DH;
     b.nrows = W;
     b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / H);
     return launch_cols<COL_WIENER_1D_REAL>(b, (W + 1) / 2, s);
   }
-  // General 2D PSF: spectrum (rows then columns), then the image.
-  if ((e = run_psf_spectrum_2d(taps, kh, kw, H, W, spec, DW, DH, s)) != cudaSuccess) return e;
+  cudaError_t e;
   FftArgs d = {};
-  d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = W; d.nrows = H; d.D = DW; d.floor_ = floor_;
+  d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = W; d.nrows = H; d.D = S.DW; d.floor_ = floor_;
   if ((e = launch_rows<ROW_FWD_REAL>(d, s)) != cudaSuccess) return e;
   FftArgs g = {};
-  g.cbuf = work; g.ldc = W; g.spec = spec; g.ldspec = W; g.nrows = W; g.D = DH; g.K = K;
+  g.cbuf = work; g.ldc = W; g.spec = spec; g.ldspec = W; g.nrows = W; g.D = S.DH; g.K = K;
   if ((e = launch_cols<COL_WIENER>(g, W, s)) != cudaSuccess) return e;
   FftArgs o = {};
-  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.D = DW;
+  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.D = S.DW;
   o.floor_ = floor_; o.scale = ff_const(1.0 / ((double)H * (double)W)); o.spec = spec; o.K = K;
   return launch_rows<ROW_INV_REAL>(o, s);
+}
+
+cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps, int kh,
+                       int kw, float K, float floor_, void* ws, const WsLayout& L, int* status,
+                       cudaStream_t s) {
+  (void)status;
+  WienerState S;
+  cudaError_t e = wiener_prepare(H, W, taps, kh, kw, ws, L, &S, s);
+  if (e != cudaSuccess) return e;
+  return wiener_apply(f, u0, ld, K, floor_, ws, L, S, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -209,3 +209,20 @@ def test_unsupported_is_reported(lib):
     f = cuda(np.full((32, 48), 100.0))
     with pytest.raises(lib.DeblurError, match="unsupported"):
         lib.rrl_iterate(f, f.clone(), cuda(np.ones((3, 3)) / 9), Params(conv="periodic"), 1)
+
+
+@pytest.mark.parametrize("maker,kind", [(lambda: synth.case_line1024(256, 320, 5), "general"),
+                                        (lambda: synth.case_box256(200, 256, 4), "box_row"),
+                                        (lambda: synth.batch_case(2, size_cap=300), None),
+                                        (lambda: synth.case_gauss2048(256, 256, 4), "general")])
+def test_plan_equals_deblur(lib, maker, kind):
+    case = maker()
+    kind = kind or case.psf_kind
+    f, h = cuda(case.f), cuda(case.h)
+    H, W = case.f.shape
+    plan = lib.Plan(H, W, h, case.params, case.iters, kind=kind)
+    u1 = plan.run(f)
+    u2 = plan.run(f)
+    ref = lib.deblur(f, h, case.params, case.iters, kind=kind)
+    assert torch.equal(u1, ref) and torch.equal(u2, ref)
+    plan.close()
