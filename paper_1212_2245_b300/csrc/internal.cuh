@@ -141,4 +141,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialization attribute may start while the previous kernel in
+// the stream is still running.  pdl_trigger() lets the next kernel's CTAs be
+// scheduled; pdl_wait() blocks until the previous kernel has completed and
+// its writes are visible.  Every kernel below calls pdl_wait() before its
+// first global-memory access.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace db

@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(256, 4) k_rrl_q(const float* __restrict__ f, i
                                                const int* __restrict__ ngroups_g, int kh, int kw,
                                                int ng_max, RrlParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
+  pdl_wait();
   q_tile<TH, TW, R, M, P>(smem_raw, f, ldf, uin, ldin, q, ldq, H, W, groups_g, ngroups_g, kh, kw, ng_max, p,
                           blockIdx.y * TH, blockIdx.x * TW);
 }
@@ -138,6 +140,8 @@ __global__ void __launch_bounds__(256, 4) k_rrl_update(const float2* __restrict_
                                                     const int* __restrict__ ngroups_g, int kh, int kw,
                                                     int ng_max, RrlParams p, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
+  pdl_wait();
   update_tile<TH, TW, R, M, P>(smem_raw, q, ldq, uin, ldin, uout, ldout, H, W, groups_g, ngroups_g, kh, kw,
                                ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW);
 }
@@ -212,15 +216,27 @@ static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
   cudaError_t e;
   if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
   if ((e = set_smem(ku, su)) != cudaSuccess) return e;
-  kq<<<dim3((a.W + kQTW - 1) / kQTW, (a.H + kQTH - 1) / kQTH), dim3(64, 4), sq, s>>>(
-      a.f, a.ldf, a.uin, a.ldin, a.q, a.W, a.H, a.W, a.groups, a.ngroups, a.kh, a.kw, ng_max, a.p);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(64, 4);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((a.W + kQTW - 1) / kQTW, (a.H + kQTH - 1) / kQTH);
+  cfg.dynamicSmemBytes = sq;
+  if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, a.W, a.H, a.W, a.groups, a.ngroups, a.kh,
+                              a.kw, ng_max, a.p)) != cudaSuccess)
+    return e;
   count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ku<<<dim3((a.W + kUTW - 1) / kUTW, (a.H + kUTH - 1) / kUTH), dim3(64, 4), su, s>>>(
-      a.q, a.W, a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups, a.ngroups, a.kh, a.kw, ng_max,
-      a.p, a.status);
+  cfg.gridDim = dim3((a.W + kUTW - 1) / kUTW, (a.H + kUTH - 1) / kUTH);
+  cfg.dynamicSmemBytes = su;
+  if ((e = cudaLaunchKernelEx(&cfg, ku, (const float2*)a.q, a.W, a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups,
+                              a.ngroups, a.kh, a.kw, ng_max, a.p, a.status)) != cudaSuccess)
+    return e;
   count_launch();
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <bool SPLIT, int M>

@@ -322,7 +322,6 @@ static cudaError_t launch_cols_c(FftArgs a, int nseq, cudaStream_t s) {
 template <int MODE>
 static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
   const int M = 1 << a.D.logM;
-  if (M <= 1024) return launch_cols_c<MODE, 8>(a, nseq, s);
   if (M <= 2048) return launch_cols_c<MODE, 4>(a, nseq, s);
   if (M <= 4096) return launch_cols_c<MODE, 2>(a, nseq, s);
   return launch_cols_c<MODE, 1>(a, nseq, s);
