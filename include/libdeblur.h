@@ -242,7 +242,9 @@ db_status db_rrl_iterate_noalloc(const float* f, float* u, int H, int W, int ld,
  * RRRL iterations, enqueuing launches and async copies only (capturable in a
  * CUDA graph).  The plan keeps pointers into ws and the PSF values taken at
  * creation: re-create it when the taps change.  The result equals
- * db_deblur's bit for bit. */
+ * db_deblur's bit for bit.  db_plan_create synchronises `stream` once: it
+ * reads back the number of tap groups, which sizes the tap table that every
+ * RRRL launch of the plan keeps in shared memory. */
 typedef struct db_plan db_plan;
 db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_params* p, int iters, void* ws,
                          size_t ws_bytes, int* dev_status, void* stream, db_plan** out);

@@ -19,8 +19,8 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   size_t off = 0;
   L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
   L.ntaps = off; off += 256;
-  L.utmp = off;  off += align256((size_t)H * W * sizeof(float));
-  L.qbuf = off;  off += align256((size_t)H * W * sizeof(float2));
+  L.utmp = off;  off += align256((size_t)H * upitch(W) * sizeof(float));
+  L.qbuf = off;  off += align256((size_t)H * qpitch(W) * sizeof(float2));
   size_t spec_elems, work_elems;
   if (conv == DB_CONV_PERIODIC) { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
   else if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
@@ -78,9 +78,10 @@ static RrlParams to_rrl(const db_params* p) {
 }
 
 // Spatial-mode iterations with tap groups already prepared in the workspace.
+// ng_bound: the tap-group count when the caller knows it (0 otherwise).
 static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld, int kh, int kw,
                                  const RrlParams& rp, int iters, float* ckpt, int ckpt_every, void* ws,
-                                 const WsLayout& L, int* dev_status, cudaStream_t s) {
+                                 const WsLayout& L, int* dev_status, cudaStream_t s, int ng_bound = 0) {
   char* base = (char*)ws;
   TapGroup* groups = (TapGroup*)(base + L.taps);
   int* ngroups = (int*)(base + L.ntaps);
@@ -91,11 +92,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   int sched = g_schedule.load();
   if (sched == DB_SCHED_AUTO)
     sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
-  const size_t smem_need = sched == DB_SCHED_SPLIT
-                               ? (rrl_split_smem_q(kh, kw) > rrl_split_smem_update(kh, kw)
-                                      ? rrl_split_smem_q(kh, kw)
-                                      : rrl_split_smem_update(kh, kw))
-                               : rrl_spatial_smem(kh, kw);
+  const size_t smem_need = sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const float* src = u;
   int ld_src = ld;
@@ -107,11 +104,11 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
         return DB_ERR_CUDA;
     }
     float* dst = (k % 2 == 0) ? tmp : u;
-    const int ld_dst = (k % 2 == 0) ? W : ld;
+    const int ld_dst = (k % 2 == 0) ? upitch(W) : ld;
     const cudaError_t e =
         sched == DB_SCHED_SPLIT
             ? launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, groups, ngroups, kh, kw, rp,
-                               dev_status, s)
+                               dev_status, ng_bound, s)
             : launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, kh, kw, rp,
                                  dev_status, s);
     if (e != cudaSuccess) return DB_ERR_CUDA;
@@ -119,7 +116,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
     ld_src = ld_dst;
   }
   if (src != u) {
-    if (cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), src, (size_t)W * sizeof(float),
+    if (cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), src, (size_t)ld_src * sizeof(float),
                           (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return DB_ERR_CUDA;
   }
@@ -226,6 +223,7 @@ struct SinglePlan {
   WsLayout L;
   WienerState wst;
   Dft1 DW32, DH32;  // periodic mode: FP32 twiddles of the iteration transforms
+  int ng = 0;       // tap-group count (0: unknown)
 };
 }  // namespace db
 
@@ -252,6 +250,12 @@ db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_param
                           (int*)(base + L.ntaps), dev_status, s) != cudaSuccess) {
     delete P; return DB_ERR_CUDA;
   }
+  // the group count sizes the tap table in shared memory of every launch
+  if (cudaMemcpyAsync(&P->ng, base + L.ntaps, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    delete P; return DB_ERR_CUDA;
+  }
+  if (P->ng < 1 || P->ng > max_tap_groups(psf->kh, psf->kw)) P->ng = 0;
   if (p->conv == DB_CONV_PERIODIC) {
     // Wiener in float-float with its own spectrum region, iteration spectrum in FP32
     float4* Sff = (float4*)(base + L.spec);
@@ -295,7 +299,7 @@ db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, 
     return DB_OK;
   }
   return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, to_rrl(&P->p), P->iters, nullptr, 0, P->ws, P->L,
-                         dev_status, s);
+                         dev_status, s, P->ng);
 }
 
 void db_plan_destroy(db_plan* plan) { delete (SinglePlan*)plan; }

@@ -33,7 +33,7 @@ struct BatchImg {
   float2* q;     // (e, W), pitch W
   const TapGroup* groups;
   const int* ngroups;
-  int ldf, ldA, ldB;
+  int ldf, ldA, ldB, ldq;
   int H, W, kh, kw, ng_max, M, P;
   RrlParams p;
 };
@@ -43,14 +43,14 @@ constexpr int kBTH = 32, kBTW = 64, kBR = 8;  // tiles of the split schedule
 template <int M, int P>
 __device__ __noinline__ void batch_q(unsigned char* smem, const BatchImg& im, const float* src, int lds,
                                      int i0, int j0) {
-  q_tile<kBTH, kBTW, kBR, M, P>(smem, im.f, im.ldf, src, lds, im.q, im.W, im.H, im.W, im.groups,
+  q_tile<kBTH, kBTW, kBR, M, P>(smem, im.f, im.ldf, src, lds, im.q, im.ldq, im.H, im.W, im.groups,
                                 im.ngroups, im.kh, im.kw, im.ng_max, im.p, i0, j0);
 }
 
 template <int M, int P>
 __device__ __noinline__ void batch_u(unsigned char* smem, const BatchImg& im, const float* src, int lds,
                                      float* dst, int ldd, int* status, int i0, int j0) {
-  update_tile<kBTH, kBTW, kBR, M, P>(smem, im.q, im.W, src, lds, dst, ldd, im.H, im.W, im.groups,
+  update_tile<kBTH, kBTW, kBR, M, P>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.groups,
                                      im.ngroups, im.kh, im.kw, im.ng_max, im.p, status, i0, j0);
 }
 
@@ -161,13 +161,6 @@ struct BatchPlan {
   ~BatchPlan() { if (wb) wiener_batch_delete(wb); }
 };
 
-static int halo_class_b(int kw) {
-  const int need = kw - 1 > 2 ? kw - 1 : 2;
-  int P = 8;
-  while (P < need) P *= 2;
-  return P;
-}
-
 // Per-image workspace regions, laid out in order.
 struct ImgRegions {
   size_t groups, ngroups, utmp, q, spec, work, end;
@@ -177,8 +170,8 @@ static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
   ImgRegions r;
   r.groups = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
   r.ngroups = off; off += 256;
-  r.utmp = off;    off += align256((size_t)H * W * sizeof(float));
-  r.q = off;       off += align256((size_t)H * W * sizeof(float2));
+  r.utmp = off;    off += align256((size_t)H * upitch(W) * sizeof(float));
+  r.q = off;       off += align256((size_t)H * qpitch(W) * sizeof(float2));
   size_t spec = (kh == 1) ? (size_t)W : (kw == 1) ? (size_t)H : (size_t)H * W;
   r.spec = off;    off += align256(spec * sizeof(float4));
   r.work = off;    off += (kh > 1 && kw > 1) ? align256((size_t)H * W * sizeof(float4)) : 0;
@@ -210,7 +203,9 @@ size_t batch_ws_bytes(const db_image_desc* d, int n, int iters, db_status* why) 
         (x.p.psi_tv != 0 && x.p.psi_tv != 1)) { *why = DB_ERR_ARG; return 0; }
     if (x.p.conv != DB_CONV_CLAMP) { *why = DB_ERR_UNSUPPORTED; return 0; }
     if (x.f == x.u) { *why = DB_ERR_ARG; return 0; }
-    if (rrl_split_smem_q(x.psf.kh, x.psf.kw) > 227 * 1024 || rrl_split_smem_update(x.psf.kh, x.psf.kw) > 227 * 1024) {
+    const int ngm = max_tap_groups(x.psf.kh, x.psf.kw);
+    if (split_smem_q(kBTH, kBTW, x.psf.kh, x.psf.kw, ngm) > 227 * 1024 ||
+        split_smem_update(kBTH, kBTW, x.psf.kh, x.psf.kw, ngm) > 227 * 1024) {
       *why = DB_ERR_UNSUPPORTED; return 0;
     }
     off = image_regions(off, x.H, x.W, x.psf.kh, x.psf.kw).end;
@@ -278,7 +273,7 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     }
     float* utmp = (float*)(base + r.utmp);
     float* A = (iters % 2 == 1) ? utmp : x.u;
-    const int ldA = (iters % 2 == 1) ? x.W : x.ld;
+    const int ldA = (iters % 2 == 1) ? upitch(x.W) : x.ld;
     WienerImage wi = {};
     wi.f = x.f; wi.ld = x.ld; wi.u0 = A; wi.ldu = ldA; wi.H = x.H; wi.W = x.W;
     wi.taps = x.psf.taps; wi.kh = kh; wi.kw = kw; wi.K = x.p.K; wi.floor_ = x.p.pos_floor;
@@ -290,16 +285,17 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     BatchImg& bi = P->imgs[i];
     bi.f = x.f; bi.A = A; bi.ldA = ldA;
     bi.B = (iters % 2 == 1) ? x.u : utmp;
-    bi.ldB = (iters % 2 == 1) ? x.ld : x.W;
+    bi.ldB = (iters % 2 == 1) ? x.ld : upitch(x.W);
+    bi.ldq = qpitch(x.W);
     bi.q = (float2*)(base + r.q);
     bi.groups = groups; bi.ngroups = ngroups;
     bi.ldf = x.ld; bi.H = x.H; bi.W = x.W; bi.kh = kh; bi.kw = kw;
     bi.ng_max = max_tap_groups(kh, kw);
     bi.M = tap_group_height(kh);
-    bi.P = halo_class_b(kw);
+    bi.P = split_halo_class(kw);
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
     bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
-    const size_t sm = std::max(rrl_split_smem_q(kh, kw), rrl_split_smem_update(kh, kw));
+    const size_t sm = std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max), split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max));
     if (sm > P->smem) P->smem = sm;
     for (int i0 = 0; i0 < x.H; i0 += kBTH)
       for (int j0 = 0; j0 < x.W; j0 += kBTW) P->tiles.push_back(make_int4(i, i0, j0, bi.ng_max));

@@ -39,6 +39,10 @@ constexpr int kMaxTapSide = 255; // largest kh or kw
 void count_launch(int n = 1);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+// Row pitches of workspace images: float rows padded to 16 bytes, float2
+// (q) rows to an even count, so that tile staging can copy 16-byte chunks.
+inline int upitch(int W) { return (W + 3) & ~3; }
+inline int qpitch(int W) { return (W + 1) & ~1; }
 inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
@@ -46,8 +50,8 @@ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 struct WsLayout {
   size_t taps;     // TapGroup[max_tap_groups(kh, kw)]
   size_t ntaps;    // int: number of groups
-  size_t utmp;     // float[H*W]  (RRRL ping-pong)
-  size_t qbuf;     // float2[H*W] (split schedule: q1, q2)
+  size_t utmp;     // float[H*upitch(W)]  (RRRL ping-pong)
+  size_t qbuf;     // float2[H*qpitch(W)] (split schedule: q = (e, W); Fourier mode: Z)
   size_t spec;     // float4[spec_elems]  (PSF spectrum, float-float)
   size_t work;     // float4[work_elems]  (Wiener rows, float-float; Fourier mode: X)
   size_t s32;      // float2[H*W]         (Fourier mode: FP32 PSF spectrum)
@@ -62,12 +66,11 @@ int max_tap_groups(int kh, int kw);
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s);
 size_t rrl_spatial_smem(int kh, int kw);
-size_t rrl_split_smem_q(int kh, int kw);
-size_t rrl_split_smem_update(int kh, int kw);
+size_t rrl_split_smem(int kh, int kw);  // larger of the two split kernels
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             cudaStream_t s);
+                             int ng_bound, cudaStream_t s);
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps,
                        int kh, int kw, float K, float floor_, void* ws, const WsLayout& L,

@@ -116,34 +116,44 @@ cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, Tap
 }
 
 // ---------------------------------------------------------------------------
-// split schedule kernels (one tile per CTA)
+// split schedule kernels (one tile per CTA), chained by programmatic
+// dependent launch.  In the chain  ... update(k-1) -> q(k) -> update(k) ...
+// each kernel lets its successor start only once it has itself passed the
+// wait for its predecessor.  Hence when update(k) starts, update(k-1) (the
+// writer of u) has completed, and the part of each tile that runs before
+// the wait may read everything except its immediate predecessor's output:
+// q(k) stages f and the tap groups, update(k) the tap groups and u; the
+// wait then covers q(k)'s u and update(k)'s q.
 // ---------------------------------------------------------------------------
+struct PdlDep {
+  __device__ void operator()() const {
+    pdl_wait();
+    pdl_trigger();
+  }
+};
+
 template <int TH, int TW, int R, int M, int P>
-__global__ void __launch_bounds__(256, 4) k_rrl_q(const float* __restrict__ f, int ldf,
+__global__ void __launch_bounds__((TH / R) * TW, 8) k_rrl_q(const float* __restrict__ f, int ldf,
                                                const float* __restrict__ uin, int ldin,
                                                float2* __restrict__ q, int ldq, int H, int W,
                                                const TapGroup* __restrict__ groups_g,
                                                const int* __restrict__ ngroups_g, int kh, int kw,
                                                int ng_max, RrlParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_trigger();
-  pdl_wait();
   q_tile<TH, TW, R, M, P>(smem_raw, f, ldf, uin, ldin, q, ldq, H, W, groups_g, ngroups_g, kh, kw, ng_max, p,
-                          blockIdx.y * TH, blockIdx.x * TW);
+                          blockIdx.y * TH, blockIdx.x * TW, PdlDep());
 }
 
 template <int TH, int TW, int R, int M, int P>
-__global__ void __launch_bounds__(256, 4) k_rrl_update(const float2* __restrict__ q, int ldq,
+__global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* __restrict__ q, int ldq,
                                                     const float* __restrict__ uin, int ldin,
                                                     float* __restrict__ uout, int ldout, int H, int W,
                                                     const TapGroup* __restrict__ groups_g,
                                                     const int* __restrict__ ngroups_g, int kh, int kw,
                                                     int ng_max, RrlParams p, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_trigger();
-  pdl_wait();
   update_tile<TH, TW, R, M, P>(smem_raw, q, ldq, uin, ldin, uout, ldout, H, W, groups_g, ngroups_g, kh, kw,
-                               ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW);
+                               ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW, PdlDep());
 }
 
 // ---------------------------------------------------------------------------
@@ -151,8 +161,11 @@ __global__ void __launch_bounds__(256, 4) k_rrl_update(const float2* __restrict_
 // smallest of 8, 16, 32, 64, 128, 256 that holds kw - 1 (and 2).
 // ---------------------------------------------------------------------------
 constexpr int kTH = 64, kTW = 64, kR = 8;        // fused tiles
-constexpr int kQTH = 32, kQTW = 64;              // split: q tiles
-constexpr int kUTH = 32, kUTW = 64;              // split: update tiles
+// split tiles: 32 x 32 outputs, 128 threads (one 8-row strip each).  Small
+// tiles keep 7-8 CTAs resident per SM, so a 1024^2 image (1024 tiles) is
+// one balanced wave.
+constexpr int kQTH = 32, kQTW = 32;
+constexpr int kUTH = 32, kUTW = 32;
 
 static int halo_class(int kw) {
   const int need = kw - 1 > 2 ? kw - 1 : 2;
@@ -169,14 +182,16 @@ size_t rrl_spatial_smem(int kh, int kw) {
   const size_t us = (size_t)(UH * (kTW + 2 * P) + 1) & ~size_t(1);
   return (size_t)2 * ng_max * sizeof(float4) + us * sizeof(float) + (size_t)QHp * (kTW + P) * sizeof(float2);
 }
-size_t rrl_split_smem_q(int kh, int kw) {
-  return (size_t)max_tap_groups(kh, kw) * sizeof(float4) +
-         (size_t)(kQTH + kh - 1) * (kQTW + halo_class(kw)) * sizeof(float);
+static size_t split_smem_q_single(int kh, int kw, int ng_max) {
+  return split_smem_q(kQTH, kQTW, kh, kw, ng_max);
 }
-size_t rrl_split_smem_update(int kh, int kw) {
-  return (size_t)max_tap_groups(kh, kw) * sizeof(float4) +
-         (size_t)(kUTH + kh - 1) * (kUTW + halo_class(kw)) * sizeof(float2) +
-         (size_t)(kUTH + 4) * (kUTW + 4) * sizeof(float);
+static size_t split_smem_update_single(int kh, int kw, int ng_max) {
+  return split_smem_update(kUTH, kUTW, kh, kw, ng_max);
+}
+size_t rrl_split_smem(int kh, int kw) {
+  const size_t a = split_smem_q_single(kh, kw, max_tap_groups(kh, kw));
+  const size_t b = split_smem_update_single(kh, kw, max_tap_groups(kh, kw));
+  return a > b ? a : b;
 }
 
 template <typename K>
@@ -189,6 +204,7 @@ static cudaError_t set_smem(K kern, size_t smem) {
 struct IterArgs {
   const float* f; int ldf; const float* uin; int ldin; float* uout; int ldout; float2* q;
   int H, W; const TapGroup* groups; const int* ngroups; int kh, kw; RrlParams p; int* status;
+  int ng_bound;  // known upper bound of the group count (0: use max_tap_groups)
 };
 
 template <int M, int P>
@@ -208,31 +224,34 @@ static cudaError_t launch_fused_mp(const IterArgs& a, cudaStream_t s) {
 
 template <int M, int P>
 static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
-  const int ng_max = max_tap_groups(a.kh, a.kw);
-  const size_t sq = rrl_split_smem_q(a.kh, a.kw), su = rrl_split_smem_update(a.kh, a.kw);
+  const int ng_max = a.ng_bound > 0 ? a.ng_bound : max_tap_groups(a.kh, a.kw);
+  const size_t sq = split_smem_q_single(a.kh, a.kw, ng_max), su = split_smem_update_single(a.kh, a.kw, ng_max);
   if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
   auto kq = k_rrl_q<kQTH, kQTW, kR, M, P>;
   auto ku = k_rrl_update<kUTH, kUTW, kR, M, P>;
   cudaError_t e;
   if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
   if ((e = set_smem(ku, su)) != cudaSuccess) return e;
+  // all of L1 as shared memory: 7-8 tiles resident per SM
+  if ((e = cudaFuncSetAttribute(kq, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(ku, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(64, 4);
+  cfg.blockDim = dim3(32, 4);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.gridDim = dim3((a.W + kQTW - 1) / kQTW, (a.H + kQTH - 1) / kQTH);
   cfg.dynamicSmemBytes = sq;
-  if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, a.W, a.H, a.W, a.groups, a.ngroups, a.kh,
-                              a.kw, ng_max, a.p)) != cudaSuccess)
+  if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, qpitch(a.W), a.H, a.W, a.groups, a.ngroups,
+                              a.kh, a.kw, ng_max, a.p)) != cudaSuccess)
     return e;
   count_launch();
   cfg.gridDim = dim3((a.W + kUTW - 1) / kUTW, (a.H + kUTH - 1) / kUTH);
   cfg.dynamicSmemBytes = su;
-  if ((e = cudaLaunchKernelEx(&cfg, ku, (const float2*)a.q, a.W, a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups,
+  if ((e = cudaLaunchKernelEx(&cfg, ku, (const float2*)a.q, qpitch(a.W), a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups,
                               a.ngroups, a.kh, a.kw, ng_max, a.p, a.status)) != cudaSuccess)
     return e;
   count_launch();
@@ -241,7 +260,7 @@ static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
 
 template <bool SPLIT, int M>
 static cudaError_t dispatch_p(const IterArgs& a, cudaStream_t s) {
-  switch (halo_class(a.kw)) {
+  switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
     case 8: return SPLIT ? launch_split_mp<M, 8>(a, s) : launch_fused_mp<M, 8>(a, s);
     case 16: return SPLIT ? launch_split_mp<M, 16>(a, s) : launch_fused_mp<M, 16>(a, s);
     case 32: return SPLIT ? launch_split_mp<M, 32>(a, s) : launch_fused_mp<M, 32>(a, s);
@@ -263,15 +282,15 @@ static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status};
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status, 0};
   return dispatch<false>(a, s);
 }
 
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             cudaStream_t s) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status};
+                             int ng_bound, cudaStream_t s) {
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound};
   return dispatch<true>(a, s);
 }
 

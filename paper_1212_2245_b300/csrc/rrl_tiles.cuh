@@ -38,11 +38,6 @@ __device__ __forceinline__ float2 weighted_residual(float b, float f, const RrlP
   return make_float2(__fdividef(w * (f - b), b), w);
 }
 
-__device__ __forceinline__ float diffusivity(float gx, float gy, const RrlParams& p) {
-  if (!p.psi_tv) return 1.0f;
-  return rsqrtf(fmaf(gx, gx, fmaf(gy, gy, p.eps_psi * p.eps_psi)));
-}
-
 // b[r] = (u*h) at R vertically adjacent pixels.  `base` points at the u
 // value that the first pixel's strip starts from; each group record holds
 // three weights and the shared-memory offset of its first load.
@@ -102,6 +97,13 @@ __device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
 template <int R, int S>
 __device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, const RrlParams& p,
                                                 float (&D)[R], float (&c)[R]) {
+  // With g = psi'(|grad u|^2) and central differences, g = 2 g2 where
+  // g2 = 1/sqrt(dx^2 + dy^2 + 4 eps^2) on the undivided differences dx, dy;
+  // a flux 1/2 (g_a + g_b)(u_b - u_a) is then (g2_a + g2_b)(u_b - u_a).
+  // (Linear diffusion, psi' = 1: g2 = 1/2.)
+  const float e4 = 4.0f * p.eps_psi * p.eps_psi;
+  const bool tv = p.psi_tv != 0;
+  auto g2 = [&](float dx, float dy) { return tv ? rsqrtf(fmaf(dx, dx, fmaf(dy, dy, e4))) : 0.5f; };
   float m[R + 4], e1[R + 2], w1[R + 2];
 #pragma unroll
   for (int t = 0; t < R + 4; ++t) m[t] = uc[(t - 2) * S];
@@ -110,19 +112,19 @@ __device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, co
   float gC[R + 2];
 #pragma unroll
   for (int t = 0; t < R + 2; ++t)  // rows -1..R
-    gC[t] = diffusivity(0.5f * (e1[t] - w1[t]), 0.5f * (m[t + 2] - m[t]), p);
+    gC[t] = g2(e1[t] - w1[t], m[t + 2] - m[t]);
   float Fv[R + 1];
 #pragma unroll
   for (int t = 0; t < R + 1; ++t)  // flux between rows t-1 and t
-    Fv[t] = 0.5f * (gC[t + 1] + gC[t]) * (m[t + 2] - m[t + 1]);
+    Fv[t] = (gC[t + 1] + gC[t]) * (m[t + 2] - m[t + 1]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const float e2 = uc[r * S + 2], w2 = uc[r * S - 2];
     const float ctr = m[r + 2];
-    const float gE = diffusivity(0.5f * (e2 - ctr), 0.5f * (e1[r + 2] - e1[r]), p);
-    const float gW = diffusivity(0.5f * (ctr - w2), 0.5f * (w1[r + 2] - w1[r]), p);
-    const float fe = 0.5f * (gE + gC[r + 1]) * (e1[r + 1] - ctr);
-    const float fw = 0.5f * (gC[r + 1] + gW) * (ctr - w1[r + 1]);
+    const float gE = g2(e2 - ctr, e1[r + 2] - e1[r]);
+    const float gW = g2(ctr - w2, w1[r + 2] - w1[r]);
+    const float fe = (gE + gC[r + 1]) * (e1[r + 1] - ctr);
+    const float fw = (gC[r + 1] + gW) * (ctr - w1[r + 1]);
     D[r] = (fe - fw) + (Fv[r + 1] - Fv[r]);
     c[r] = ctr;
   }
@@ -246,70 +248,138 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
 // Used when the image (u, f, q: 16 bytes per pixel) stays resident in L2, so
 // the extra round trip of q costs no HBM traffic while the halo recompute of
 // the fused kernel disappears.
+//
+// Tiles are staged in 16-byte chunks.  The staged window starts at a column
+// rounded down to a chunk boundary; the few extra columns are absorbed by
+// the tap offsets.  A chunk that lies inside the image (and a source whose
+// rows are 16-byte aligned) is one cp.async of 16 bytes; any other chunk is
+// copied element by element with clamped indices (constant continuation).
 // ---------------------------------------------------------------------------
-// q = (e, W) on the TH x TW tile at (i0, j0).  smem_raw: rrl_split_smem_q bytes.
-template <int TH, int TW, int R, int M, int P>
+// Halo class of the split tiles: the smallest of 8, 16, ..., 256 that holds
+// kw + 2 (the kw - 1 halo columns plus up to 3 columns of chunk alignment).
+__host__ __device__ inline int split_halo_class(int kw) {
+  int P = 8;
+  while (P < kw + 2) P *= 2;
+  return P;
+}
+// Shared memory of one split tile of TH x TW outputs.
+__host__ __device__ inline size_t split_smem_q(int TH, int TW, int kh, int kw, int ng_max) {
+  return (size_t)ng_max * 16 + (size_t)TH * TW * sizeof(float) +
+         (size_t)(TH + kh - 1) * (TW + split_halo_class(kw)) * sizeof(float);
+}
+__host__ __device__ inline size_t split_smem_update(int TH, int TW, int kh, int kw, int ng_max) {
+  return (size_t)ng_max * 16 + (size_t)(TH + kh - 1) * (TW + split_halo_class(kw)) * 8 +
+         (size_t)(TH + 4) * (TW + 8) * sizeof(float);
+}
+
+// Stage rows y0 .. y0+nrows-1 and the nc chunks of EPC = 16/sizeof(T)
+// elements starting at column x0 (a multiple of EPC) of a T image into
+// shared rows of stride S elements.  Positions outside the image read the
+// clamped position.  vec: rows of src are 16-byte aligned.
+template <typename T, int S>
+__device__ __forceinline__ void stage_tile(T* dst, const T* __restrict__ src, int ld, int H, int W, int y0,
+                                           int nrows, int x0, int nc, bool vec) {
+  constexpr int EPC = 16 / (int)sizeof(T);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  const int lg = nc <= 1 ? 0 : min(5, 32 - __clz(nc - 1));  // 2^lg chunk slots per row
+  const int slots = 1 << lg;
+  const int cs = tid & (slots - 1);
+  for (int r = tid >> lg; r < nrows; r += nth >> lg) {
+    const T* srow = src + (size_t)min(max(y0 + r, 0), H - 1) * ld;
+    T* drow = dst + r * S;
+    for (int c = cs; c < nc; c += slots) {
+      const int x = x0 + EPC * c;
+      if (vec && x >= 0 && x + EPC <= W) {
+        cp_async16(drow + EPC * c, srow + x);
+      } else {
+#pragma unroll
+        for (int k = 0; k < EPC; ++k) {
+          if constexpr (sizeof(T) == 4) cp_async4(drow + EPC * c + k, srow + min(max(x + k, 0), W - 1));
+          else cp_async8(drow + EPC * c + k, srow + min(max(x + k, 0), W - 1));
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool rows_aligned16(const T* p, int ld) {
+  return (((uintptr_t)p) & 15) == 0 && ((size_t)ld * sizeof(T)) % 16 == 0;
+}
+
+// Ordering hook of the split tiles.  Each tile body first stages what does
+// not depend on the preceding launch (tap groups, f, and in the update
+// tile u), then calls `dep()`, then stages the data the preceding launch
+// wrote.  Under programmatic dependent launch dep() waits for the preceding
+// grid; in the batched kernel it is empty.
+struct NoDep {
+  __device__ void operator()() const {}
+};
+
+// q = (e, W) on the TH x TW tile at (i0, j0).  smem_raw: split_smem_q bytes.
+template <int TH, int TW, int R, int M, int P, typename Dep = NoDep>
 __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __restrict__ f, int ldf,
                                        const float* __restrict__ uin, int ldin,
                                        float2* __restrict__ q, int ldq, int H, int W,
                                        const TapGroup* __restrict__ groups_g,
                                        const int* __restrict__ ngroups_g, int kh, int kw,
-                                       int ng_max, const RrlParams& p, int i0, int j0) {
-  static_assert(TH % R == 0, "strips must tile TH");
+                                       int ng_max, const RrlParams& p, int i0, int j0, Dep dep = Dep()) {
+  static_assert(TH % R == 0 && TW % 4 == 0, "tile shape");
   const int cy = kh >> 1, cx = kw >> 1;
   const int Ty = kh - 1 - cy, Tx = kw - 1 - cx;  // u rows/cols needed above/left of a pixel
-  constexpr int US = TW + P;                      // row stride, P >= kw - 1
-  const int UH = TH + kh - 1, UW = TW + kw - 1;
+  constexpr int US = TW + P;                      // row stride, P >= kw + 2
+  const int UH = TH + kh - 1;
+  const int xs = (j0 - Tx) & ~3, ox = (j0 - Tx) - xs;  // staged window starts at column xs
+  const int nc = (TW + kw - 1 + ox + 3) >> 2;
   const int ng = *ngroups_g;
   float4* gu = (float4*)smem_raw;
-  float* us = (float*)(gu + ng_max);
+  float* fs = (float*)(gu + ng_max);  // TH x TW
+  float* us = fs + TH * TW;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
   for (int g = tid; g < ng; g += nth) {
     const TapGroup t = groups_g[g];
-    const int offu = (Ty - t.dy0 - (M - 1)) * US + (Tx - t.dx);
+    const int offu = (Ty - t.dy0 - (M - 1)) * US + (Tx + ox - t.dx);
     gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
   }
-  for (int r = threadIdx.y; r < UH; r += blockDim.y) {
-    const int gi = min(max(i0 - Ty + r, 0), H - 1);
-    const float* src = uin + (size_t)gi * ldin;
-    for (int c = threadIdx.x; c < UW; c += blockDim.x)
-      cp_async4(us + r * US + c, src + min(max(j0 - Tx + c, 0), W - 1));
-  }
+  stage_tile<float, TW>(fs, f, ldf, H, W, i0, TH, j0, TW / 4, rows_aligned16(f, ldf));
+  dep();
+  stage_tile<float, US>(us, uin, ldin, H, W, i0 - Ty, UH, xs, nc, rows_aligned16(uin, ldin));
   cp_async_wait_all();
   __syncthreads();
+  const bool full = i0 + TH <= H && j0 + TW <= W;
   for (int item = tid; item < (TH / R) * TW; item += nth) {
     const int s = item / TW, c = item - s * TW;
     const int r0 = s * R, j = j0 + c;
-    if (j >= W || i0 + r0 >= H) continue;
-    float fv[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = min(i0 + r0 + r, H - 1);
-      fv[r] = fmaxf(__ldg(f + (size_t)i * ldf + j), p.floor);
-    }
     float b[R];
     blur_strip<R, M, US>(us + r0 * US + c, gu, ng, b);
+    float2* qo = q + (size_t)(i0 + r0) * ldq + j;
+    if (full) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = i0 + r0 + r;
-      if (i < H) q[(size_t)i * ldq + j] = weighted_residual(b[r], fv[r], p);
+      for (int r = 0; r < R; ++r) qo[(size_t)r * ldq] = weighted_residual(b[r], fmaxf(fs[(r0 + r) * TW + c], p.floor), p);
+    } else if (j < W) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (i0 + r0 + r < H) qo[(size_t)r * ldq] = weighted_residual(b[r], fmaxf(fs[(r0 + r) * TW + c], p.floor), p);
     }
   }
 }
 
 // Delta, B, D and the update on the TH x TW tile at (i0, j0).
-// smem_raw: rrl_split_smem_update bytes.
-template <int TH, int TW, int R, int M, int P>
+// smem_raw: split_smem_update bytes.
+template <int TH, int TW, int R, int M, int P, typename Dep = NoDep>
 __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float2* __restrict__ q, int ldq,
                                             const float* __restrict__ uin, int ldin,
                                             float* __restrict__ uout, int ldout, int H, int W,
                                             const TapGroup* __restrict__ groups_g,
                                             const int* __restrict__ ngroups_g, int kh, int kw,
-                                            int ng_max, const RrlParams& p, int* status, int i0, int j0) {
-  static_assert(TH % R == 0, "strips must tile TH");
+                                            int ng_max, const RrlParams& p, int* status, int i0, int j0,
+                                            Dep dep = Dep()) {
+  static_assert(TH % R == 0 && TW % 4 == 0, "tile shape");
   const int cy = kh >> 1, cx = kw >> 1;
-  const int QH = TH + kh - 1, QW = TW + kw - 1;
-  constexpr int QS = TW + P, UH = TH + 4, US = TW + 4;  // row strides, P >= kw - 1
+  const int QH = TH + kh - 1;
+  constexpr int QS = TW + P, UH = TH + 4, US = TW + 8;  // row strides, P >= kw + 2
+  const int xq = (j0 - cx) & ~1, oq = (j0 - cx) - xq;    // q window starts at column xq
+  const int ncq = (TW + kw - 1 + oq + 1) >> 1;
   const int ng = *ngroups_g;
   float4* gq = (float4*)smem_raw;
   float2* qs = (float2*)(gq + ng_max);
@@ -317,41 +387,33 @@ __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
   for (int g = tid; g < ng; g += nth) {
     const TapGroup t = groups_g[g];
-    const int offq = (cy + t.dy0) * QS + (cx + t.dx);
+    const int offq = (cy + t.dy0) * QS + (cx + oq + t.dx);
     gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
   }
-  // q(clamp) over the correlation footprint, u(clamp) with a 2-pixel halo
-  for (int r = threadIdx.y; r < QH; r += blockDim.y) {
-    const int gi = min(max(i0 - cy + r, 0), H - 1);
-    const float2* src = q + (size_t)gi * ldq;
-    for (int c = threadIdx.x; c < QW; c += blockDim.x)
-      cp_async8(qs + r * QS + c, src + min(max(j0 - cx + c, 0), W - 1));
-  }
-  for (int r = threadIdx.y; r < UH; r += blockDim.y) {
-    const int gi = min(max(i0 - 2 + r, 0), H - 1);
-    const float* src = uin + (size_t)gi * ldin;
-    for (int c = threadIdx.x; c < US; c += blockDim.x)
-      cp_async4(us + r * US + c, src + min(max(j0 - 2 + c, 0), W - 1));
-  }
+  // u(clamp) with a 2-pixel halo (staged from column j0 - 4 so that every
+  // chunk is aligned), then q(clamp) over the correlation footprint
+  stage_tile<float, US>(us, uin, ldin, H, W, i0 - 2, UH, j0 - 4, TW / 4 + 2, rows_aligned16(uin, ldin));
+  dep();
+  stage_tile<float2, QS>(qs, q, ldq, H, W, i0 - cy, QH, xq, ncq, rows_aligned16(q, ldq));
   cp_async_wait_all();
   __syncthreads();
+  const bool full = i0 + TH <= H && j0 + TW <= W;
+  bool bad = false;
   for (int item = tid; item < (TH / R) * TW; item += nth) {
     const int s = item / TW, oj = item - s * TW;
     const int oi0 = s * R, j = j0 + oj;
-    if (j >= W || i0 + oi0 >= H) continue;
     float dl[R], B[R], D[R], c[R];
     correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
-    diffusion_strip<R, US>(us + (oi0 + 2) * US + (oj + 2), p, D, c);
+    diffusion_strip<R, US>(us + (oi0 + 2) * US + (oj + 4), p, D, c);
+    float* uo = uout + (size_t)(i0 + oi0) * ldout + j;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int i = i0 + oi0 + r;
       const float un = rrl_update(c[r], dl[r], B[r], D[r], p);
-      if (i < H) {
-        if (!isfinite(un) && status) atomicOr(status, DB_FLAG_NONFINITE);
-        uout[(size_t)i * ldout + j] = un;
-      }
+      bad |= !isfinite(un);
+      if (full || (j < W && i0 + oi0 + r < H)) uo[(size_t)r * ldout] = un;
     }
   }
+  if (bad && status) atomicOr(status, DB_FLAG_NONFINITE);
 }
 
 }  // namespace db
