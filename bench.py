@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512", "learn512"], default="line1024",
                     help="line1024 (default, the headline workload), box256, gauss2048, batch512, learn512")
+    ap.add_argument("--schedule", choices=["auto", "fused", "split", "flow"], default="auto",
+                    help="kernel schedule of the spatial RRRL iterations")
     return ap.parse_args()
 
 
@@ -575,6 +577,9 @@ def main():
             torch.cuda.set_device(local)
         torch.distributed.init_process_group(backend)
     try:
+        if args.impl == "ours" and args.schedule != "auto":
+            import paper_1212_2245_b300 as db
+            db.set_schedule(args.schedule)
         if args.impl == "reference":
             run_reference(args, world, rank)
         elif args.workload == "batch512":

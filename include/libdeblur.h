@@ -263,14 +263,22 @@ const char* db_version(void);
 /* Kernel schedule of the spatial RRRL iteration (process-wide setting; the
  * arithmetic is the same in every schedule):
  *   DB_SCHED_AUTO  - split when u, f and q (16 bytes/pixel) fit comfortably in
- *                    L2, fused otherwise (default)
+ *                    L2 (as flow from 512K pixels on), fused otherwise
+ *                    (default)
  *   DB_SCHED_FUSED - one launch per iteration; each tile recomputes the
  *                    weighted ratio q on its halo (fewest HBM round trips)
  *   DB_SCHED_SPLIT - two launches per iteration; q = (W f/b, W) goes through
- *                    a global buffer in the workspace (no halo recompute) */
+ *                    a global buffer in the workspace (no halo recompute)
+ *   DB_SCHED_FLOW  - the split tiles, all iterations in one cooperative
+ *                    persistent launch; tiles wait (bounded, DB_FLAG_TIMEOUT
+ *                    on expiry; db_set_spin_limit) only for the neighbouring
+ *                    tiles whose output they read, so the phases of
+ *                    successive iterations overlap.  Calls that request
+ *                    checkpoints run the split schedule. */
 #define DB_SCHED_AUTO 0
 #define DB_SCHED_FUSED 1
 #define DB_SCHED_SPLIT 2
+#define DB_SCHED_FLOW 3
 db_status db_set_schedule(int schedule);
 
 /* Number of CUDA kernels this library has enqueued in this process so far

@@ -30,6 +30,7 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
   L.work = off;  off += align256(work_elems * sizeof(float4));
   L.s32 = off;   off += (conv == DB_CONV_PERIODIC) ? align256((size_t)H * W * sizeof(float2)) : 0;
   L.tw = off;    off += align256((dft_table_elems(W) + dft_table_elems(H)) * sizeof(float4));
+  L.flow = off;  off += (conv == DB_CONV_PERIODIC) ? 0 : align256(flow_ws_bytes(H, W));
   L.total = off;
   return L;
 }
@@ -88,10 +89,28 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   float* tmp = (float*)(base + L.utmp);
   float2* qbuf = (float2*)(base + L.qbuf);
   // schedule: split (q in a global buffer) when u, f and q stay resident in
-  // L2, fused (halo recompute, one pass per iteration) otherwise
+  // L2, fused (halo recompute, one pass per iteration) otherwise; the flow
+  // form of the split schedule runs all iterations in one launch (it writes
+  // no checkpoints)
+  // (from about 512 tiles of 32 x 32 on, enough to keep every SM busy with
+  // overlapping phases)
   int sched = g_schedule.load();
-  if (sched == DB_SCHED_AUTO)
+  if (sched == DB_SCHED_AUTO) {
     sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
+    if (sched == DB_SCHED_SPLIT && (size_t)H * W >= (size_t)512 * 1024) sched = DB_SCHED_FLOW;
+  }
+  if (sched == DB_SCHED_FLOW && ckpt) sched = DB_SCHED_SPLIT;
+  if (sched == DB_SCHED_FLOW) {
+    if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw)) > 227 * 1024) return DB_ERR_UNSUPPORTED;
+    if (launch_rrl_flow(f, ld, u, ld, tmp, upitch(W), qbuf, H, W, groups, ngroups, kh, kw, ng_bound, rp, iters,
+                        base + L.flow, dev_status, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    if (iters % 2 == 1 &&
+        cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), tmp, (size_t)upitch(W) * sizeof(float),
+                          (size_t)W * sizeof(float), H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    return DB_OK;
+  }
   const size_t smem_need = sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const float* src = u;
@@ -333,7 +352,8 @@ const char* db_version(void) { return "libdeblur 0.1 sm_103a"; }
 long long db_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 db_status db_set_schedule(int schedule) {
-  if (schedule != DB_SCHED_AUTO && schedule != DB_SCHED_FUSED && schedule != DB_SCHED_SPLIT)
+  if (schedule != DB_SCHED_AUTO && schedule != DB_SCHED_FUSED && schedule != DB_SCHED_SPLIT &&
+      schedule != DB_SCHED_FLOW)
     return DB_ERR_ARG;
   g_schedule.store(schedule);
   return DB_OK;

@@ -142,7 +142,10 @@ __global__ void __launch_bounds__(256) k_rrl_batch(const BatchImg* __restrict__ 
 
 static std::atomic<long long> g_spin_limit{4000000000LL};  // ~2 s at 2 GHz
 
-void set_spin_limit(long long cycles) { g_spin_limit.store(cycles); }
+void set_spin_limit(long long cycles) {
+  g_spin_limit.store(cycles);
+  set_flow_spin_limit(cycles);
+}
 
 // ---------------------------------------------------------------------------
 // host plan

@@ -56,6 +56,7 @@ struct WsLayout {
   size_t work;     // float4[work_elems]  (Wiener rows, float-float; Fourier mode: X)
   size_t s32;      // float2[H*W]         (Fourier mode: FP32 PSF spectrum)
   size_t tw;       // float2[dft_table_elems(W) + dft_table_elems(H)]  (transform tables)
+  size_t flow;     // flow_ws_bytes(H, W): task counter and per-tile progress counters
   size_t total;
 };
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv);
@@ -71,6 +72,15 @@ cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
                              int ng_bound, cudaStream_t s);
+
+// all iterations in one persistent launch ordered by tile dependencies;
+// flow_ws: flow_ws_bytes(H, W), 256-byte aligned
+size_t flow_ws_bytes(int H, int W);
+size_t flow_smem(int kh, int kw, int ng_max);
+void set_flow_spin_limit(long long cycles);
+cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* utmp, int ldt, float2* q, int H, int W,
+                            const TapGroup* groups, const int* ngroups, int kh, int kw, int ng_bound,
+                            const RrlParams& p, int iters, void* flow_ws, int* status, cudaStream_t s);
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps,
                        int kh, int kw, float K, float floor_, void* ws, const WsLayout& L,

@@ -94,16 +94,15 @@ __device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
 // and vertical fluxes shared by neighbouring rows of the strip are formed
 // once.  Across the image boundary the clamped copy makes every difference
 // vanish exactly: zero flux.
-template <int R, int S>
-__device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, const RrlParams& p,
-                                                float (&D)[R], float (&c)[R]) {
+template <int R, int S, bool TV>
+__device__ __forceinline__ void diffusion_strip_t(const float* __restrict__ uc, const RrlParams& p,
+                                                  float (&D)[R], float (&c)[R]) {
   // With g = psi'(|grad u|^2) and central differences, g = 2 g2 where
   // g2 = 1/sqrt(dx^2 + dy^2 + 4 eps^2) on the undivided differences dx, dy;
   // a flux 1/2 (g_a + g_b)(u_b - u_a) is then (g2_a + g2_b)(u_b - u_a).
   // (Linear diffusion, psi' = 1: g2 = 1/2.)
   const float e4 = 4.0f * p.eps_psi * p.eps_psi;
-  const bool tv = p.psi_tv != 0;
-  auto g2 = [&](float dx, float dy) { return tv ? rsqrtf(fmaf(dx, dx, fmaf(dy, dy, e4))) : 0.5f; };
+  auto g2 = [&](float dx, float dy) { return TV ? rsqrtf(fmaf(dx, dx, fmaf(dy, dy, e4))) : 0.5f; };
   float m[R + 4], e1[R + 2], w1[R + 2];
 #pragma unroll
   for (int t = 0; t < R + 4; ++t) m[t] = uc[(t - 2) * S];
@@ -128,6 +127,13 @@ __device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, co
     D[r] = (fe - fw) + (Fv[r + 1] - Fv[r]);
     c[r] = ctr;
   }
+}
+
+template <int R, int S>
+__device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, const RrlParams& p,
+                                                float (&D)[R], float (&c)[R]) {
+  if (p.psi_tv) diffusion_strip_t<R, S, true>(uc, p, D, c);
+  else diffusion_strip_t<R, S, false>(uc, p, D, c);
 }
 
 // u' = u + u (Delta + alpha D) / (B - alpha [D]-)
@@ -284,6 +290,16 @@ __device__ __forceinline__ void stage_tile(T* dst, const T* __restrict__ src, in
   const int lg = nc <= 1 ? 0 : min(5, 32 - __clz(nc - 1));  // 2^lg chunk slots per row
   const int slots = 1 << lg;
   const int cs = tid & (slots - 1);
+  if (vec && x0 >= 0 && x0 + EPC * nc <= W) {
+    // the whole window lies inside the image horizontally: 16-byte copies,
+    // rows clamped
+    for (int r = tid >> lg; r < nrows; r += nth >> lg) {
+      const T* srow = src + (size_t)min(max(y0 + r, 0), H - 1) * ld + x0;
+      T* drow = dst + r * S;
+      for (int c = cs; c < nc; c += slots) cp_async16(drow + EPC * c, srow + EPC * c);
+    }
+    return;
+  }
   for (int r = tid >> lg; r < nrows; r += nth >> lg) {
     const T* srow = src + (size_t)min(max(y0 + r, 0), H - 1) * ld;
     T* drow = dst + r * S;

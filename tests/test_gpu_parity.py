@@ -29,7 +29,7 @@ def cuda(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32).cuda()
 
 
-@pytest.fixture(params=["fused", "split"])
+@pytest.fixture(params=["fused", "split", "flow"])
 def sched(request, lib):
     lib.set_schedule(request.param)
     yield request.param
@@ -226,3 +226,48 @@ def test_plan_equals_deblur(lib, maker, kind):
     ref = lib.deblur(f, h, case.params, case.iters, kind=kind)
     assert torch.equal(u1, ref) and torch.equal(u2, ref)
     plan.close()
+
+
+@pytest.mark.parametrize("H,W,psf", [(256, 320, "line"), (77, 131, "gauss"), (40, 300, "row"), (300, 40, "col")])
+def test_flow_equals_split_bitwise(lib, H, W, psf):
+    """The persistent dependency-ordered launch runs the split schedule's tile
+    bodies, so it must reproduce the split result exactly."""
+    rng = np.random.default_rng(H + W)
+    h = {"line": synth.line_psf(31, 30.0, 32.0), "row": synth.box_psf(15),
+         "col": synth.raised_cosine_1d(9, "col"), "gauss": synth.gaussian_mixture_psf(9, rng)}[psf]
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, 7, p, seed=11)
+    out = {}
+    try:
+        for name in ("split", "flow"):
+            lib.set_schedule(name)
+            out[name] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7)
+    finally:
+        lib.set_schedule("auto")
+    assert torch.equal(out["split"], out["flow"])
+
+
+def test_flow_bounded_waits_report_timeout(lib):
+    """With a zero wait budget every dependency wait of the persistent launch
+    gives up at once: the call returns, the status word carries the time-out
+    flag (unless no wait ever found a dependency pending) and the context
+    stays usable."""
+    h = synth.line_psf(31, 30.0, 32.0)
+    p = Params()
+    f, u0 = _iterate_case(256, 256, h, 6, p, seed=2)
+    ws = lib.Workspace.for_image(256, 256, h.shape[0], h.shape[1], p)
+    lib.set_schedule("flow")
+    lib.set_spin_limit(0)
+    try:
+        ws.reset_status()
+        lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6, ws=ws, check=False)
+        torch.cuda.synchronize()
+        flags = int(ws.status.item())
+    finally:
+        lib.set_spin_limit(4_000_000_000)
+        lib.set_schedule("auto")
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 2)
+    assert torch.isfinite(u).all()
+    if flags == 0:
+        pytest.skip("no wait found a dependency pending")
+    assert flags & 0x4, f"flags 0x{flags:x}"
