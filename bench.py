@@ -125,13 +125,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# DRAM bytes of one RRRL iteration (k_rrl_q + k_rrl_update, split schedule) on
-# the line1024 workload, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, caches flushed before the capture).
-LINE1024_ITER_DRAM_BYTES = 8.408064e6 + 12.608256e6
+# DRAM bytes per RRRL iteration on the line1024 workload under the default
+# (flow) schedule: one ncu capture of the persistent launch (20 iterations,
+# dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
+# capture), divided by the iteration count.
+LINE1024_FLOW_ITER_DRAM_BYTES = (8.462080e6 + 1.896192e6) / 20
 
 
-def _spatial_model(case, ms_iter):
+def _spatial_model(case, ms_iter, schedule="auto"):
     """Fused/split spatial iteration: FP32-issue bound; flops per pixel and
     iteration = 3 tap sums (b, A, B) x 2 flops x nnz(h) + 60 pointwise."""
     H, W = case.f.shape
@@ -141,15 +142,17 @@ def _spatial_model(case, ms_iter):
     achieved = flops / (ms_iter / 1e3) / 1e12
     hbm_peak, hbm_src = peaks()
     hbm_equiv = 12.0 * H * W / (ms_iter / 1e3) / 1e9
-    traffic = LINE1024_ITER_DRAM_BYTES if (H, W, int((case.h != 0).sum())) == (1024, 1024, 71) else None
+    line1024 = (H, W, int((case.h != 0).sum())) == (1024, 1024, 71)
+    traffic = LINE1024_FLOW_ITER_DRAM_BYTES if line1024 and schedule in ("auto", "flow") else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "one RRRL iteration (k_rrl_q + k_rrl_update, or k_rrl_spatial)",
+            "traffic": traffic,
+            "kernel": "one RRRL iteration (1/iters of k_rrl_flow; k_rrl_q + k_rrl_update; or k_rrl_spatial)",
             "kernel_ms": ms_iter, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
             "hbm_equiv_gbs": hbm_equiv, "hbm_equiv_frac": hbm_equiv / hbm_peak,
             "hbm_peak_gbs": hbm_peak, "hbm_peak_src": hbm_src}
 
 
-def _fourier_model(case, ms_iter):
+def _fourier_model(case, ms_iter, schedule="auto"):
     """Fourier iteration: four HBM passes over complex buffers; algorithmic
     bytes per pixel and iteration = 24 (columns x S) + 20 (rows: b, e, W) +
     24 (columns x conj S) + 24 (rows: update, next transform) = 92 B."""
@@ -332,7 +335,7 @@ def run_ours(args, world, rank, local):
         return
     px_iter = H * W * iters
     value = world * px_iter / (ms / 1e3) / 1e6
-    roof = model(case, ms_iter / iters)
+    roof = model(case, ms_iter / iters, args.schedule)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
