@@ -12,7 +12,7 @@ readings taken where the paper is silent or its formulas are garbled.
 """
 from .ops import (  # noqa: F401
     conv_clamp, corr_clamp, conv_periodic, corr_periodic, conv, corr,
-    box_running_sum_rows, box_running_sum_cols,
+    box_running_sum_rows, box_running_sum_cols, box_ends_running_sum_rows, box_ends_running_sum_cols,
     psf_transfer, wiener, wiener_rows, wiener_cols,
     info_divergence, phi_prime, psi_prime, diffusion,
     rrrl_step, rrrl, wr3l, rl_step, condition_input, positivity_floor,

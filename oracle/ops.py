@@ -171,6 +171,47 @@ def box_running_sum_cols(u, L, weight=None, adjoint=False):
     return box_running_sum_rows(_t(u).T.contiguous(), L, weight, adjoint).T.contiguous()
 
 
+def box_ends_running_sum_rows(u, taps, adjoint=False):
+    """Row convolution (correlation with adjoint=True), constant continuation,
+    with a box whose end taps may be lighter: taps = [e0, w, ..., w, e1] in
+    tap order (centre index L//2).  This is the non-integer blur length of
+    Sec. 4.3 ("Uniform linear motion"): single pixels of smaller weight at
+    one or both ends.  The window of interior pixels slides by one pixel per
+    output (one pixel enters, one leaves); the two end pixels are added with
+    their own weights, so each step costs at most two additions and two
+    subtractions beyond the products."""
+    u = _t(u)
+    taps = [float(t) for t in _t(taps).reshape(-1)]
+    H, W = u.shape
+    L = len(taps)
+    c = L // 2
+    col = lambda j: u[:, min(max(j, 0), W - 1)]  # noqa: E731  constant continuation
+    # output j reads positions p = j + c - k (conv) or p = j + k - c (corr) for
+    # tap k; `pos(j, k)` gives that position
+    pos = (lambda j, k: j + k - c) if adjoint else (lambda j, k: j + c - k)  # noqa: E731
+    out = torch.empty_like(u)
+    if L == 1:
+        for j in range(W):
+            out[:, j] = taps[0] * col(j)
+        return out
+    w = taps[1] if L > 2 else 0.0
+    inner = torch.zeros(H, dtype=F64)  # sum over taps 1..L-2 for output 0
+    for k in range(1, L - 1):
+        inner = inner + col(pos(0, k))
+    for j in range(W):
+        if j > 0 and L > 2:
+            # the interior window moves by one pixel: the pixel of tap 1 (or
+            # L-2) at j enters, the one that tap L-2 (or 1) read at j-1 leaves
+            enter, leave = (pos(j, 1), pos(j - 1, L - 2)) if not adjoint else (pos(j, L - 2), pos(j - 1, 1))
+            inner = inner + col(enter) - col(leave)
+        out[:, j] = w * inner + taps[0] * col(pos(j, 0)) + taps[L - 1] * col(pos(j, L - 1))
+    return out
+
+
+def box_ends_running_sum_cols(u, taps, adjoint=False):
+    return box_ends_running_sum_rows(_t(u).T.contiguous(), taps, adjoint).T.contiguous()
+
+
 # ---------------------------------------------------------------------------
 # Wiener filter (Sec. 2.1, Eq. 2), periodic, native size, literal (R4)
 # ---------------------------------------------------------------------------

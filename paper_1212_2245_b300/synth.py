@@ -84,6 +84,17 @@ def box_psf(L: int, axis: str = "row") -> np.ndarray:
     return _normalise(h if axis == "row" else h.T)
 
 
+def box_psf_frac(L: float, axis: str = "row") -> np.ndarray:
+    """Uniform linear motion of non-integer length L, centred on the middle
+    tap: each pixel's weight is the length of [-L/2, L/2] that falls inside
+    it, so the two end pixels carry the fractional remainder."""
+    half = 0.5 * float(L)
+    K = int(np.ceil(half - 0.5))
+    k = np.arange(-K, K + 1, dtype=np.float64)
+    w = np.clip(np.minimum(k + 0.5, half) - np.maximum(k - 0.5, -half), 0.0, None)[None, :]
+    return _normalise(w if axis == "row" else w.T)
+
+
 def raised_cosine_1d(L: int, axis: str = "row", period: float | None = None) -> np.ndarray:
     """Non-uniform linear motion: taps 0.5*(1+cos(2*pi*t/P)), t centred."""
     P = float(L + 1) if period is None else float(period)

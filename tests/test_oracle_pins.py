@@ -10,6 +10,7 @@ import scipy.ndimage as ndi
 import torch
 
 import oracle
+from paper_1212_2245_b300 import synth
 from oracle import ops
 
 RNG = np.random.default_rng(7)
@@ -101,6 +102,42 @@ def test_running_sum_equals_direct(L, W):
     np.testing.assert_allclose(oracle.box_running_sum_rows(u, L, adjoint=True), oracle.corr_clamp(u, h), rtol=1e-12)
     uc = rand_img(W, 2)
     np.testing.assert_allclose(oracle.box_running_sum_cols(uc, L), oracle.conv_clamp(uc, h.T), rtol=1e-12)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 9, 17, 41])
+@pytest.mark.parametrize("W", [1, 5, 64])
+def test_running_sum_with_light_ends_equals_direct(L, W):
+    """Box with lighter end taps (non-integer blur length, Sec. 4.3): the
+    sliding-window form equals the direct clamped sums with those taps, for
+    convolution and correlation, along rows and columns."""
+    rng = np.random.default_rng(L * 100 + W)
+    u = rng.uniform(0, 255, (3, W))
+    taps = np.full(L, 1.0)
+    taps[0], taps[-1] = rng.uniform(0.05, 1.0, 2) if L > 1 else (0.7, 0.7)
+    h = taps[None, :]
+    np.testing.assert_allclose(oracle.box_ends_running_sum_rows(u, taps), oracle.conv_clamp(u, h), rtol=1e-12)
+    np.testing.assert_allclose(oracle.box_ends_running_sum_rows(u, taps, adjoint=True), oracle.corr_clamp(u, h),
+                               rtol=1e-12)
+    uc = u.T.copy()
+    np.testing.assert_allclose(oracle.box_ends_running_sum_cols(uc, taps), oracle.conv_clamp(uc, h.T), rtol=1e-12)
+
+
+@pytest.mark.parametrize("L", [3.0, 4.5, 15.4, 26.9])
+def test_fractional_box_taps(L):
+    """The fractional box integrates a centred segment of length L over the
+    pixels: weights sum to L before normalisation, interior pixels get 1, the
+    two end pixels the same remainder, and an odd integer length gives a
+    plain box."""
+    h = synth.box_psf_frac(L)[0].astype(np.float64)
+    raw = h * L
+    assert abs(raw.sum() - L) < 1e-5
+    assert np.allclose(raw[1:-1], 1.0, atol=1e-5)
+    assert abs(raw[0] - raw[-1]) < 1e-6
+    n_int = len(raw) - 2
+    assert abs(2 * raw[0] - (L - n_int)) < 1e-5
+    if float(L).is_integer() and int(L) % 2 == 1:
+        assert np.allclose(raw, 1.0, atol=1e-6)
+
 
 
 # --------------------------------------------------------------------------
