@@ -53,7 +53,7 @@ typedef enum {
   DB_ERR_TIMEOUT = 7,      /* device flag: a bounded wait gave up            */
   DB_ERR_NONFINITE = 8,    /* device flag: NaN/Inf produced or consumed      */
   DB_ERR_TAPS = 9          /* device flag: negative/non-finite taps, sum<=0,
-                              or a "box" PSF whose taps are not uniform      */
+                              or a "box" PSF whose interior taps differ     */
 } db_status;
 
 /* Device status bits (OR-ed into *dev_status). */
@@ -64,9 +64,12 @@ typedef enum {
 
 typedef enum {
   DB_PSF_GENERAL = 0,  /* any non-negative kh x kw taps                      */
-  DB_PSF_BOX = 1       /* uniform motion along a coordinate axis: kh == 1 or
-                          kw == 1 and all taps equal (Sec. 4.3, "Uniform
-                          linear motion"); enables the running-sum blur     */
+  DB_PSF_BOX = 1       /* uniform motion along a coordinate axis (Sec. 4.3,
+                          "Uniform linear motion"): kh == 1 or kw == 1, all
+                          taps equal except possibly the first and the last
+                          (lighter end pixels of a non-integer blur length).
+                          The spatial iterations then blur and correlate by
+                          sliding-window sums (split schedule).            */
 } db_psf_kind;
 
 typedef enum {

@@ -80,7 +80,8 @@ static RrlParams to_rrl(const db_params* p) {
 
 // Spatial-mode iterations with tap groups already prepared in the workspace.
 // ng_bound: the tap-group count when the caller knows it (0 otherwise).
-static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld, int kh, int kw,
+// kind: DB_PSF_BOX runs the sliding-window form of the split schedule.
+static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld, int kh, int kw, int kind,
                                  const RrlParams& rp, int iters, float* ckpt, int ckpt_every, void* ws,
                                  const WsLayout& L, int* dev_status, cudaStream_t s, int ng_bound = 0) {
   char* base = (char*)ws;
@@ -99,7 +100,8 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
     sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
     if (sched == DB_SCHED_SPLIT && (size_t)H * W >= (size_t)512 * 1024) sched = DB_SCHED_FLOW;
   }
-  if (sched == DB_SCHED_FLOW && ckpt) sched = DB_SCHED_SPLIT;
+  const int box = kind == DB_PSF_BOX;
+  if ((sched == DB_SCHED_FLOW && ckpt) || box) sched = DB_SCHED_SPLIT;
   if (sched == DB_SCHED_FLOW) {
     if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw)) > 227 * 1024) return DB_ERR_UNSUPPORTED;
     if (launch_rrl_flow(f, ld, u, ld, tmp, upitch(W), qbuf, H, W, groups, ngroups, kh, kw, ng_bound, rp, iters,
@@ -111,7 +113,8 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
       return DB_ERR_CUDA;
     return DB_OK;
   }
-  const size_t smem_need = sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
+  const size_t smem_need = box ? rrl_box_smem(kh, kw)
+                               : sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const float* src = u;
   int ld_src = ld;
@@ -127,7 +130,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
     const cudaError_t e =
         sched == DB_SCHED_SPLIT
             ? launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, groups, ngroups, kh, kw, rp,
-                               dev_status, ng_bound, s)
+                               dev_status, ng_bound, box, s)
             : launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, kh, kw, rp,
                                  dev_status, s);
     if (e != cudaSuccess) return DB_ERR_CUDA;
@@ -220,7 +223,7 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
   if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, (TapGroup*)(base + L.taps),
                           (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
     return DB_ERR_CUDA;
-  return iterate_spatial(f, u, H, W, ld, psf->kh, psf->kw, to_rrl(p), iters, ckpt, ckpt_every, ws, L,
+  return iterate_spatial(f, u, H, W, ld, psf->kh, psf->kw, psf->kind, to_rrl(p), iters, ckpt, ckpt_every, ws, L,
                          dev_status, s);
 }
 
@@ -317,7 +320,8 @@ db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, 
       return DB_ERR_CUDA;
     return DB_OK;
   }
-  return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, to_rrl(&P->p), P->iters, nullptr, 0, P->ws, P->L,
+  return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, P->kind, to_rrl(&P->p), P->iters, nullptr, 0, P->ws,
+                         P->L,
                          dev_status, s, P->ng);
 }
 

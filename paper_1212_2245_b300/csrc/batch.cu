@@ -22,6 +22,7 @@
 
 #include "fft_df.cuh"
 #include "internal.cuh"
+#include "rrl_box.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -35,6 +36,7 @@ struct BatchImg {
   const int* ngroups;
   int ldf, ldA, ldB, ldq;
   int H, W, kh, kw, ng_max, M, P;
+  int box;       // 0: tap groups; 1, 2: horizontal, vertical box (sliding-window sums)
   RrlParams p;
 };
 
@@ -52,6 +54,17 @@ __device__ __noinline__ void batch_u(unsigned char* smem, const BatchImg& im, co
                                      float* dst, int ldd, int* status, int i0, int j0) {
   update_tile<kBTH, kBTW, kBR, M, P>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.groups,
                                      im.ngroups, im.kh, im.kw, im.ng_max, im.p, status, i0, j0);
+}
+
+template <bool HORIZ>
+__device__ __noinline__ void batch_box(int phase, unsigned char* smem, const BatchImg& im, const float* src, int lds,
+                                       float* dst, int ldd, int* status, int i0, int j0) {
+  if (phase == 0)
+    q_tile_box<kBTH, kBTW, kBR, HORIZ>(smem, im.f, im.ldf, src, lds, im.q, im.ldq, im.H, im.W, im.ngroups, im.p, i0,
+                                       j0);
+  else
+    update_tile_box<kBTH, kBTW, kBR, HORIZ>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.ngroups, im.p,
+                                            status, i0, j0);
 }
 
 template <int M>
@@ -106,7 +119,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long 
   return ok != 0;
 }
 
-__global__ void __launch_bounds__(256) k_rrl_batch(const BatchImg* __restrict__ imgs,
+__global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict__ imgs,
                                                    const int4* __restrict__ tiles, int ntiles, int iters,
                                                    unsigned* bar, int* work, int* status,
                                                    long long spin_limit) {
@@ -128,7 +141,9 @@ __global__ void __launch_bounds__(256) k_rrl_batch(const BatchImg* __restrict__ 
         const int lds = even ? im.ldA : im.ldB;
         float* dst = even ? im.B : im.A;
         const int ldd = even ? im.ldB : im.ldA;
-        switch (im.M) {
+        if (im.box == 1) batch_box<true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        else if (im.box == 2) batch_box<false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        else switch (im.M) {
           case 1: batch_tile_m<1>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
           case 2: batch_tile_m<2>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
           default: batch_tile_m<3>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
@@ -296,9 +311,13 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.ng_max = max_tap_groups(kh, kw);
     bi.M = tap_group_height(kh);
     bi.P = split_halo_class(kw);
+    bi.box = x.psf.kind == DB_PSF_BOX ? (kh == 1 ? 1 : 2) : 0;
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
     bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
-    const size_t sm = std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max), split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max));
+    const size_t sm = bi.box ? std::max(box_smem_q(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1),
+                                        box_smem_update(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1))
+                             : std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),
+                                        split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max));
     if (sm > P->smem) P->smem = sm;
     for (int i0 = 0; i0 < x.H; i0 += kBTH)
       for (int j0 = 0; j0 < x.W; j0 += kBTW) P->tiles.push_back(make_int4(i, i0, j0, bi.ng_max));

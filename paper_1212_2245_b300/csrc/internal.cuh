@@ -71,7 +71,8 @@ size_t rrl_split_smem(int kh, int kw);  // larger of the two split kernels
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             int ng_bound, cudaStream_t s);
+                             int ng_bound, int box, cudaStream_t s);
+size_t rrl_box_smem(int kh, int kw);  // split kernels of a box PSF (kh == 1 or kw == 1)
 
 // all iterations in one persistent launch ordered by tile dependencies;
 // flow_ws: flow_ws_bytes(H, W), 256-byte aligned

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
+#include "rrl_box.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -70,14 +71,18 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  const float t0 = __ldg(taps);
+  // a box is uniform except possibly for its two end taps (non-integer
+  // blur length, Sec. 4.3)
+  const float t1 = n > 2 ? __ldg(taps + 1) : 0.f;
   float sum = 0.f;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const float w = __ldg(taps + k);
     if (!(w >= 0.f) || !isfinite(w)) atomicOr(&bad, DB_FLAG_TAPS);
-    if (kind == DB_PSF_BOX && w != t0) atomicOr(&bad, DB_FLAG_BOX);
+    if (kind == DB_PSF_BOX && k >= 1 && k <= n - 2 && w != t1) atomicOr(&bad, DB_FLAG_BOX);
     sum += w;
   }
+  if (kind == DB_PSF_BOX && threadIdx.x == 0)  // (e0, w, e1, L) 16 bytes after the group count
+    reinterpret_cast<float4*>(ngroups + 4)[0] = make_float4(__ldg(taps), t1, __ldg(taps + n - 1), __int_as_float(n));
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) warp_sum[wid] = sum;
   // one thread per PSF column (kw <= 255): count, exclusive scan, write
@@ -156,6 +161,27 @@ __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* _
                                ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW, PdlDep());
 }
 
+// box PSFs: the same split pair with sliding-window sums (rrl_box.cuh)
+template <bool HORIZ>
+__global__ void __launch_bounds__(128) k_rrl_q_box(const float* __restrict__ f, int ldf,
+                                                  const float* __restrict__ uin, int ldin, float2* __restrict__ q,
+                                                  int ldq, int H, int W, const int* __restrict__ ngroups_g,
+                                                  RrlParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  q_tile_box<32, 32, 8, HORIZ>(smem_raw, f, ldf, uin, ldin, q, ldq, H, W, ngroups_g, p, blockIdx.y * 32,
+                               blockIdx.x * 32, PdlDep());
+}
+
+template <bool HORIZ>
+__global__ void __launch_bounds__(128) k_rrl_update_box(const float2* __restrict__ q, int ldq,
+                                                       const float* __restrict__ uin, int ldin,
+                                                       float* __restrict__ uout, int ldout, int H, int W,
+                                                       const int* __restrict__ ngroups_g, RrlParams p, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  update_tile_box<32, 32, 8, HORIZ>(smem_raw, q, ldq, uin, ldin, uout, ldout, H, W, ngroups_g, p, status,
+                                    blockIdx.y * 32, blockIdx.x * 32, PdlDep());
+}
+
 // ---------------------------------------------------------------------------
 // host side: shared-memory sizes and launches.  The halo class P is the
 // smallest of 8, 16, 32, 64, 128, 256 that holds kw - 1 (and 2).
@@ -205,6 +231,7 @@ struct IterArgs {
   const float* f; int ldf; const float* uin; int ldin; float* uout; int ldout; float2* q;
   int H, W; const TapGroup* groups; const int* ngroups; int kh, kw; RrlParams p; int* status;
   int ng_bound;  // known upper bound of the group count (0: use max_tap_groups)
+  int box;       // DB_PSF_BOX taps: sliding-window sums (split schedule only)
 };
 
 template <int M, int P>
@@ -258,6 +285,45 @@ static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
   return cudaSuccess;
 }
 
+template <bool HORIZ>
+static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
+  const int L = HORIZ ? a.kw : a.kh;
+  const size_t sq = box_smem_q(32, 32, L, HORIZ), su = box_smem_update(32, 32, L, HORIZ);
+  if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
+  auto kq = k_rrl_q_box<HORIZ>;
+  auto ku = k_rrl_update_box<HORIZ>;
+  cudaError_t e;
+  if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
+  if ((e = set_smem(ku, su)) != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(32, 4);
+  cfg.gridDim = dim3((a.W + 31) / 32, (a.H + 31) / 32);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.dynamicSmemBytes = sq;
+  if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, qpitch(a.W), a.H, a.W, a.ngroups, a.p)) !=
+      cudaSuccess)
+    return e;
+  count_launch();
+  cfg.dynamicSmemBytes = su;
+  if ((e = cudaLaunchKernelEx(&cfg, ku, (const float2*)a.q, qpitch(a.W), a.uin, a.ldin, a.uout, a.ldout, a.H, a.W,
+                              a.ngroups, a.p, a.status)) != cudaSuccess)
+    return e;
+  count_launch();
+  return cudaSuccess;
+}
+
+size_t rrl_box_smem(int kh, int kw) {
+  const bool horiz = kh == 1;
+  const int L = horiz ? kw : kh;
+  const size_t a = box_smem_q(32, 32, L, horiz), b = box_smem_update(32, 32, L, horiz);
+  return a > b ? a : b;
+}
+
 template <bool SPLIT, int M>
 static cudaError_t dispatch_p(const IterArgs& a, cudaStream_t s) {
   switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
@@ -282,15 +348,16 @@ static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status, 0};
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status, 0, 0};
   return dispatch<false>(a, s);
 }
 
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             int ng_bound, cudaStream_t s) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound};
+                             int ng_bound, int box, cudaStream_t s) {
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound, box};
+  if (box) return kh == 1 ? launch_split_box<true>(a, s) : launch_split_box<false>(a, s);
   return dispatch<true>(a, s);
 }
 

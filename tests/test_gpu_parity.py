@@ -200,7 +200,9 @@ def test_device_flags_for_bad_taps(lib):
     with pytest.raises(lib.DeblurError, match="taps"):
         lib.rrl_iterate(f, f.clone(), cuda(np.array([[0.5, -0.1, 0.6]])), p, 1)
     with pytest.raises(lib.DeblurError, match="taps"):
-        lib.rrl_iterate(f, f.clone(), cuda(np.array([[0.3, 0.4, 0.3]])), p, 1, kind="box")
+        lib.rrl_iterate(f, f.clone(), cuda(np.array([[0.2, 0.3, 0.1, 0.4]])), p, 1, kind="box")
+    # lighter end taps are a valid box (non-integer blur length)
+    lib.rrl_iterate(f, f.clone(), cuda(np.array([[0.3, 0.4, 0.3]])), p, 1, kind="box")
     with pytest.raises(lib.DeblurError):
         lib.wiener(f, cuda(np.zeros((1, 3))), p)
 
@@ -271,3 +273,33 @@ def test_flow_bounded_waits_report_timeout(lib):
     if flags == 0:
         pytest.skip("no wait found a dependency pending")
     assert flags & 0x4, f"flags 0x{flags:x}"
+
+
+@pytest.mark.parametrize("L,axis", [(15.4, "row"), (4.5, "col"), (26.9, "row"), (3.0, "row"), (1.0, "col"),
+                                    (41.0, "col"), (2.5, "row")])
+@pytest.mark.parametrize("H,W", [(77, 131), (64, 64), (200, 45)])
+def test_box_sliding_window_matches_oracle(lib, L, axis, H, W):
+    """Box PSFs, plain and of non-integer length (lighter end pixels, Sec.
+    4.3): the sliding-window iterations against the oracle's direct sums."""
+    h = synth.box_psf_frac(L, axis)
+    if h.shape[0] > H or h.shape[1] > W:
+        pytest.skip("PSF larger than image")
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, 6, p, seed=int(L * 10))
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 6)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6, kind="box")
+    assert_close(u, ref, f"box L={L} {axis} {H}x{W}")
+    ug = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6)  # tap groups
+    assert_close(u, ug.double().cpu().numpy(), "box vs tap groups")
+
+
+def test_box_full_pipeline_fractional(lib):
+    """Wiener + 10 RRRL on a 256x256 image blurred by a box of length 15.4."""
+    rng = np.random.default_rng(1540)
+    g = synth.scene(256, 256, rng).astype(np.float32)
+    h = synth.box_psf_frac(15.4)
+    f = synth.degrade(g, h, 2.0, rng)
+    p = Params()
+    u0_ref, u_ref = oracle.wr3l(f, h, p, 10)
+    u = lib.deblur(cuda(f), cuda(h), p, 10, kind="box")
+    assert_close(u, u_ref, "fractional box WR3L")
