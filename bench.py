@@ -367,10 +367,16 @@ def run_batch(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = _lib.load()
+    from paper_1212_2245_b300 import shard
     t0 = time.perf_counter()
-    cases = [synth.batch_case(i) for i in range(512)]
+    all_cases = [synth.batch_case(i) for i in range(512)]
     gen_s = time.perf_counter() - t0
-    iters = cases[0].iters
+    iters = all_cases[0].iters
+    px_total = sum(c.f.size for c in all_cases)
+    # N ranks: each deblurs its longest-processing-time share of the images
+    # (independent problems, no exchange); the whole batch's pixels count
+    mine = shard.rank_images(shard.image_costs([c.f.shape for c in all_cases], iters), world, rank)
+    cases = [all_cases[i] for i in mine]
     fs = [torch.as_tensor(c.f).to(dev) for c in cases]
     hs = [torch.as_tensor(c.h).to(dev).contiguous() for c in cases]
     ps = [c.params for c in cases]
@@ -401,6 +407,8 @@ def run_batch(args, world, rank, local):
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     full.ws.reset_status()
+    if world > 1:
+        torch.distributed.barrier()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
@@ -434,28 +442,38 @@ def run_batch(args, world, rank, local):
             e2e[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in e2e)
+    if world > 1:
+        t = torch.tensor([ms, ms_w, e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, ms_w, e2e_ms = (float(x) for x in t)
+        ms_rrl = ms - ms_w
+        ft = torch.tensor([flops_iter], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(ft)
+        flops_iter = float(ft[0])
     if rank != 0:
         return
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    px = px_total
+    peak = world * SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops_iter * iters / (ms_rrl / 1e3) / 1e12
     hbm_peak, hbm_src = peaks()
     line = {
-        "metric": METRIC, "value": world * px * iters / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
-        "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": px * iters / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch512: 512 f32 images, sides U{128..1024}, half 1D motion (box/raised "
                                "cosine, L 5-41), half 2D Gaussian mixtures 7x7..25x25, sigma=2, Wiener K=0.006 "
                                "+ 10 RRRL; one planned batch replayed from a CUDA graph",
                    "pixels": px, "iters": iters, "l2": "inputs 0.7 GB > L2; L2 flushed before every step",
-                   "parallelism": f"replicas x{world}"},
-        "rrrl_only_mpx_iter_s": world * px * iters / (ms_rrl / 1e3) / 1e6, "wiener_ms": ms_w,
+                   "parallelism": f"images sharded by LPT over {world} ranks" if world > 1 else "1 GPU"},
+        "rrrl_only_mpx_iter_s": px * iters / (ms_rrl / 1e3) / 1e6, "wiener_ms": ms_w,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_rrl_batch (persistent, all RRRL iterations of all images)",
                      "kernel_ms": ms_rrl, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
                      "hbm_equiv_gbs": 28.0 * px * iters / (ms_rrl / 1e3) / 1e9,
                      "hbm_equiv_frac": 28.0 * px * iters / (ms_rrl / 1e3) / 1e9 / hbm_peak},
-        "e2e": {"value": world * px * iters / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+        "e2e": {"value": px * iters / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * px, "d2h_bytes_per_step": 4 * px, "ms_per_step": e2e_ms},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0,
         "plan_s": plan_s, "generate_s": gen_s, "clocks": clk.summary(),
@@ -464,13 +482,14 @@ def run_batch(args, world, rank, local):
         import oracle
         t0 = time.perf_counter()
         sample_px = 0
-        for c in (cases[0], cases[256]):
+        for c in (all_cases[0], all_cases[256]):
             oracle.wr3l(c.f, c.h, c.params, 2)
             sample_px += c.f.size * 2
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": sample_px / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(),
                                 "kind": "oracle", "sample": f"FP64 oracle, Wiener + 2 RRRL on images 0 and 256 "
-                                                            f"({cases[0].f.shape}, {cases[256].f.shape}), {dt:.1f} s"}
+                                                            f"({all_cases[0].f.shape}, {all_cases[256].f.shape}), "
+                                                            f"{dt:.1f} s"}
     print(json.dumps(line), flush=True)
 
 
@@ -484,11 +503,16 @@ def run_learn(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = _lib.load()
+    from paper_1212_2245_b300 import shard
     case = synth.case_learn512(64)
-    N, H, W = case.f.shape
+    N_all, H, W = case.f.shape
     iters, every, p = case.iters, 5, case.params
-    f = torch.as_tensor(case.f).to(dev)
-    g = torch.as_tensor(case.g).to(dev)
+    # N ranks: each runs forward and backward on its share of the images;
+    # the parameter gradients are combined by one all-reduce per step
+    mine = shard.rank_images(shard.image_costs([(H, W)] * N_all, iters), world, rank)
+    N = len(mine)
+    f = torch.as_tensor(case.f[mine]).to(dev)
+    g = torch.as_tensor(case.g[mine]).to(dev)
     taps = torch.as_tensor(case.h).to(dev).contiguous()
     u = torch.empty_like(f)
     nck = (iters - 1) // every + 1
@@ -532,12 +556,16 @@ def run_learn(args, world, rank, local):
         stream.synchronize()
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    if world > 1:
+        torch.distributed.barrier()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             for k in range(K):
                 ev[k][0].record(stream)
                 g_step.replay()
+                if world > 1:
+                    shard.combine_param_grads([gt, ga, gk], N, N_all)
                 ev[k][1].record(stream)
                 ev[k][2].record(stream)
                 g_fwd.replay()
@@ -546,24 +574,30 @@ def run_learn(args, world, rank, local):
     ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     ms_f = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     ws.raise_on_flags("timed forward"); bws.raise_on_flags("timed backward")
+    if world > 1:
+        t = torch.tensor([ms, ms_f], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, ms_f = float(t[0]), float(t[1])
     if rank != 0:
         return
-    pxi = N * H * W * iters
+    pxi = N_all * H * W * iters
     hbm_peak, hbm_src = peaks()
     # algorithmic bytes per pixel and iteration: forward 12, backward (recompute
     # 12 + reverse reads u, f, U', writes U') 28
     ach = 40.0 * pxi / (ms / 1e3) / 1e9
     line = {
-        "metric": METRIC + " (forward + backward)", "value": world * pxi / (ms / 1e3) / 1e6, "unit": UNIT,
+        "metric": METRIC + " (forward + backward)", "value": pxi / (ms / 1e3) / 1e6, "unit": UNIT,
         "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "learn512: 64 x 512x512 f32, 21 learnable row taps + alpha + K, row Wiener "
                                "+ 15 RRRL (checkpoints every 5), MSE loss, full backward; one CUDA graph per step",
-                   "images": N, "H": H, "W": W, "iters": iters, "ckpt_every": every,
+                   "images": N_all, "H": H, "W": W, "iters": iters, "ckpt_every": every,
+                   "parallelism": f"images sharded over {world} ranks, gradient all-reduce" if world > 1 else "1 GPU",
                    "l2": "working set 0.6 GB > L2"},
-        "forward_only_mpx_iter_s": world * pxi / (ms_f / 1e3) / 1e6, "forward_ms": ms_f,
+        "forward_only_mpx_iter_s": pxi / (ms_f / 1e3) / 1e6, "forward_ms": ms_f,
         "backward_over_forward": (ms - ms_f) / ms_f,
-        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak * world, "unit": "GB/s",
+                     "frac": ach / (hbm_peak * world),
                      "traffic": None, "kernel": "whole fwd+bwd step (40 B/px*iter algorithmic)",
                      "peak_src": hbm_src},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0, "clocks": clk.summary(),
