@@ -17,7 +17,7 @@ from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
            "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
-           "version"]
+           "version", "FrameStream"]
 
 
 class DeblurError(RuntimeError):
@@ -380,3 +380,6 @@ def set_schedule(name: str):
 
 def version() -> str:
     return _lib.load().db_version().decode()
+
+
+from .stream import FrameStream  # noqa: E402  (uses Plan)

@@ -384,3 +384,19 @@ def test_reverse_mode_matches_central_differences():
         fm_[n, i, j] -= 1e-4
         fd = (L(h0.detach(), al.detach(), K.detach(), fp_) - L(h0.detach(), al.detach(), K.detach(), fm_)) / 2e-4
         assert abs(fd - float(fT.grad[n, i, j])) <= 1e-6 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_snr_closed_forms():
+    """SNR(u, u0) = 10 log10(var u / var(u - u0)) (Sec. 3.1) on patterns with
+    known variances: u = 2x with x = +-1 checkerboard gives 10 log10 4; u = x +
+    0.1 y with y = +-1 in stripes (orthogonal, zero mean) gives 10 log10 101."""
+    i, j = np.indices((8, 8))
+    x = np.where((i + j) % 2 == 0, 1.0, -1.0)
+    y = np.where(i % 2 == 0, 1.0, -1.0)
+    assert abs(oracle.snr_db(2 * x, x) - 10 * math.log10(4.0)) < 1e-12
+    assert abs(oracle.snr_db(x + 0.1 * y, x) - 10 * math.log10(101.0)) < 1e-9
+    # the library's helper computes the same quantity
+    from paper_1212_2245_b300 import quality
+    rng = np.random.default_rng(3)
+    a, b = rng.normal(size=(20, 30)), rng.normal(size=(20, 30))
+    assert abs(quality.snr_db(a + b, a) - oracle.snr_db(a + b, a)) < 1e-12
