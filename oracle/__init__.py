@@ -14,7 +14,8 @@ from .ops import (  # noqa: F401
     conv_clamp, corr_clamp, conv_periodic, corr_periodic, conv, corr,
     box_running_sum_rows, box_running_sum_cols, box_ends_running_sum_rows, box_ends_running_sum_cols,
     psf_transfer, wiener, wiener_rows, wiener_cols,
-    info_divergence, phi_prime, psi_prime, diffusion,
+    info_divergence, info_divergence_lut, r1, r1_lut, r1_lut_table, RF_LUT_N, RF_LUT_SMAX,
+    phi_prime, psi_prime, diffusion,
     rrrl_step, rrrl, wr3l, rl_step, condition_input, positivity_floor,
     mse_loss, wr3l_loss, snr_db,
 )

@@ -260,6 +260,49 @@ def info_divergence(s, f):
     return s - f - f * torch.log(s / f)
 
 
+# Lookup-table evaluation of r_1 (Sec. 4.1, "Function evaluations"): r_1 is
+# tabulated on (0, 65], r_f(s) = f r_1(s/f), with a linear continuation of r_1
+# beyond 65.  The paper gives no table resolution or interpolation rule; the
+# reading taken: RF_LUT_N entries at s_j = j h, h = 65 / RF_LUT_N, linear
+# interpolation between them, the closed form below the first entry.
+RF_LUT_N = 8192
+RF_LUT_SMAX = 65.0
+
+
+def r1(x):
+    """r_1(x) = x - 1 - ln x (Eq. 7 with f = 1)."""
+    x = _t(x)
+    return x - 1.0 - torch.log(x)
+
+
+def r1_lut_table():
+    h = RF_LUT_SMAX / RF_LUT_N
+    s = torch.arange(1, RF_LUT_N + 1, dtype=F64) * h
+    return r1(s)
+
+
+def r1_lut(x):
+    """r_1 from the table: linear interpolation between s_j = j h on
+    [h, 65], the closed form on (0, h), and beyond 65 the tangent line at 65
+    (r_1'(s) = 1 - 1/s)."""
+    x = _t(x)
+    T = r1_lut_table()
+    h = RF_LUT_SMAX / RF_LUT_N
+    k = x / h
+    j = torch.clamp(torch.floor(k), 1, RF_LUT_N - 1).long()
+    fr = k - j.to(F64)
+    inside = T[j - 1] + fr * (T[j] - T[j - 1])
+    beyond = T[-1] + (1.0 - 1.0 / RF_LUT_SMAX) * (x - RF_LUT_SMAX)
+    below = r1(torch.clamp(x, min=1e-300))
+    return torch.where(x < h, below, torch.where(x > RF_LUT_SMAX, beyond, inside))
+
+
+def info_divergence_lut(s, f):
+    """r_f(s) = f r_1(s/f) with r_1 from the table (Sec. 4.1)."""
+    s, f = _t(s), _t(f)
+    return f * r1_lut(s / f)
+
+
 def phi_prime(z, eps, robust=True):
     """Derivative of the data penaliser, normalised to phi'(0) = 1 (R2)."""
     z = _t(z)
@@ -307,7 +350,8 @@ def rrrl_step(u, f, h, p):
     u, f = _t(u), _t(f)
     mode = p.conv
     b = conv(u, h, mode)                                   # u^k * h
-    Wk = phi_prime(info_divergence(b, f), p.eps_phi, bool(p.phi_robust))  # Eq. 10
+    rf = info_divergence_lut(b, f) if getattr(p, "rf_eval", "log1p") == "lut" else info_divergence(b, f)
+    Wk = phi_prime(rf, p.eps_phi, bool(p.phi_robust))      # Eq. 10
     A = corr(Wk * f / b, h, mode)                          # (W f/(u*h)) * h*
     B = corr(Wk, h, mode)                                  # W * h*
     D = diffusion(u, p.eps_psi, bool(p.psi_tv))            # Eq. 11

@@ -14,3 +14,4 @@ class Params:
     phi_robust: int = 1       # 1: robust phi', 0: phi' == 1 (plain RL data term)
     psi_tv: int = 1           # 1: TV psi', 0: psi' == 1 (linear diffusion)
     conv: str = "clamp"       # "clamp" (spatial) or "periodic" (Fourier)
+    rf_eval: str = "log1p"    # r_f by log1p ("log1p") or by the lookup table of Sec. 4.1 ("lut")

@@ -400,3 +400,29 @@ def test_snr_closed_forms():
     rng = np.random.default_rng(3)
     a, b = rng.normal(size=(20, 30)), rng.normal(size=(20, 30))
     assert abs(quality.snr_db(a + b, a) - oracle.snr_db(a + b, a)) < 1e-12
+
+
+
+def test_r1_lookup_table_pins():
+    """Table evaluation of r_1 (Sec. 4.1): exact at the grid points, within
+    the linear-interpolation bound h^2/8 max r_1'' = h^2/(8 s_j^2) between
+    them, the closed form below the first entry, and beyond 65 the tangent
+    line (value and slope r_1'(65) = 1 - 1/65 continuous at 65)."""
+    h = oracle.RF_LUT_SMAX / oracle.RF_LUT_N
+    grid = torch.tensor([h, 2 * h, 0.5, 1.0, 7.3125, 64.0, 65.0], dtype=torch.float64)
+    grid = torch.round(grid / h) * h
+    assert torch.allclose(oracle.r1_lut(grid), oracle.r1(grid), rtol=1e-12, atol=1e-15)
+    x = torch.rand(20000, dtype=torch.float64, generator=torch.Generator().manual_seed(1)) * (65 - h) + h
+    sj = torch.floor(x / h) * h
+    bound = h * h / (8 * sj * sj)
+    assert torch.all((oracle.r1_lut(x) - oracle.r1(x)).abs() <= bound * (1 + 1e-9) + 1e-15)
+    # interpolation overestimates a convex function
+    assert torch.all(oracle.r1_lut(x) >= oracle.r1(x) - 1e-15)
+    small = torch.tensor([1e-6, 0.3 * h, 0.99 * h], dtype=torch.float64)
+    assert torch.allclose(oracle.r1_lut(small), oracle.r1(small), rtol=1e-14)
+    big = torch.tensor([65.0 + 1e-9, 70.0, 200.0], dtype=torch.float64)
+    expect = oracle.r1(torch.tensor(65.0, dtype=torch.float64)) + (1 - 1 / 65) * (big - 65)
+    assert torch.allclose(oracle.r1_lut(big), expect, rtol=1e-12)
+    # r_f(s) = f r_1(s/f)
+    s, f = torch.tensor([30.0, 80.0]), torch.tensor([40.0, 20.0])
+    assert torch.allclose(oracle.info_divergence_lut(s, f), f.double() * oracle.r1_lut(s.double() / f.double()))
