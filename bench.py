@@ -56,6 +56,8 @@ def parse():
                          "stream1024 (line1024 frames with overlapped host<->device transfers)")
     ap.add_argument("--schedule", choices=["auto", "fused", "split", "flow"], default="auto",
                     help="kernel schedule of the spatial RRRL iterations")
+    ap.add_argument("--rf", choices=["log1p", "lut"], default="log1p",
+                    help="evaluation of r_f: log1p (default) or the lookup table of Sec. 4.1")
     return ap.parse_args()
 
 
@@ -698,6 +700,9 @@ def main():
         if args.impl == "ours" and args.schedule != "auto":
             import paper_1212_2245_b300 as db
             db.set_schedule(args.schedule)
+        if args.impl == "ours" and args.rf != "log1p":
+            import paper_1212_2245_b300 as db
+            db.set_rf_eval(args.rf)
         if args.impl == "reference":
             run_reference(args, world, rank)
         elif args.workload == "batch512":

@@ -284,6 +284,23 @@ const char* db_version(void);
 #define DB_SCHED_FLOW 3
 db_status db_set_schedule(int schedule);
 
+/* Evaluation of the information divergence r_f in the robust weight
+ * (process-wide setting, all devices):
+ *   DB_RF_LOG1P - r_f(b) = f (t - log1p t), t = (b - f)/f (default; exact up
+ *                 to FP32 rounding, no cancellation near b = f)
+ *   DB_RF_LUT   - r_f(b) = f r_1(b/f) with r_1(s) = s - 1 - ln s read from a
+ *                 table on (0, 65] (Sec. 4.1, "Function evaluations"): 8192
+ *                 entries at s_j = j * 65/8192, linear interpolation, the
+ *                 closed form below the first entry and the tangent line at
+ *                 65 beyond it.  Interpolation error <= h^2/(8 s^2), h = 65/8192.
+ * Selecting DB_RF_LUT fills the table on every visible device (synchronous
+ * copies; call it outside stream capture).  Plans and batches take the
+ * setting at creation.  db_rrl_backward returns DB_ERR_UNSUPPORTED while
+ * DB_RF_LUT is selected.  Returns DB_ERR_ARG for other modes. */
+#define DB_RF_LOG1P 0
+#define DB_RF_LUT 1
+db_status db_set_rf_eval(int mode);
+
 /* Number of CUDA kernels this library has enqueued in this process so far
  * (host-side counter; a CUDA-graph replay of captured calls adds nothing). */
 long long db_launch_count(void);

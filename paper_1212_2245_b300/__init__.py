@@ -17,7 +17,7 @@ from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
            "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
-           "version", "FrameStream"]
+           "set_rf_eval", "version", "FrameStream"]
 
 
 class DeblurError(RuntimeError):
@@ -376,6 +376,13 @@ def set_schedule(name: str):
     code = {"auto": _lib.SCHED_AUTO, "fused": _lib.SCHED_FUSED, "split": _lib.SCHED_SPLIT,
             "flow": _lib.SCHED_FLOW}[name]
     _check(_lib.load().db_set_schedule(code), "db_set_schedule")
+
+
+def set_rf_eval(name: str):
+    """Evaluation of r_f in the robust weight, process-wide: "log1p" (default)
+    or "lut" (the lookup table of Sec. 4.1)."""
+    code = {"log1p": _lib.RF_LOG1P, "lut": _lib.RF_LUT}[name]
+    _check(_lib.load().db_set_rf_eval(code), "db_set_rf_eval")
 
 
 def version() -> str:

@@ -616,6 +616,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   im.N = N; im.H = H; im.W = W; im.taps = psf->taps; im.kh = kh; im.kw = kw;
   im.p.alpha = p->alpha; im.p.eps_phi = p->eps_phi; im.p.eps_psi = p->eps_psi; im.p.floor = p->pos_floor;
   im.p.phi_robust = p->phi_robust; im.p.psi_tv = p->psi_tv;
+  im.p.rf_lut = nullptr;  // the reverse pass differentiates the log form
   const int G = kAdjBlocks, T = kAdjThreads;
 
   // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)
@@ -706,6 +707,7 @@ db_status db_rrl_backward(const float* f, const float* ckpt, const float* grad_u
   if (iters < 0 || ckpt_every < 1) return DB_ERR_ARG;
   if (!(p->K > 0.f) || !(p->alpha >= 0.f) || !(p->eps_phi > 0.f) || !(p->eps_psi > 0.f) || !(p->pos_floor > 0.f))
     return DB_ERR_ARG;
+  if (rf_mode() != DB_RF_LOG1P) return DB_ERR_UNSUPPORTED;  // table form has no derivative here
   if (p->conv != DB_CONV_CLAMP) return DB_ERR_UNSUPPORTED;
   return adj_backward(f, ld, batch, ckpt, iters, ckpt_every, grad_u, H, W, psf, p, grad_f, grad_taps,
                       grad_alpha, grad_K, ws, ws_bytes, dev_status, (cudaStream_t)stream);

@@ -75,6 +75,7 @@ static RrlParams to_rrl(const db_params* p) {
   RrlParams r;
   r.alpha = p->alpha; r.eps_phi = p->eps_phi; r.eps_psi = p->eps_psi; r.floor = p->pos_floor;
   r.phi_robust = p->phi_robust; r.psi_tv = p->psi_tv;
+  r.rf_lut = rf_lut_device();
   return r;
 }
 
@@ -246,6 +247,7 @@ struct SinglePlan {
   WienerState wst;
   Dft1 DW32, DH32;  // periodic mode: FP32 twiddles of the iteration transforms
   int ng = 0;       // tap-group count (0: unknown)
+  RrlParams rp;     // kernel parameters, r_f evaluation as selected at creation
 };
 }  // namespace db
 
@@ -267,7 +269,7 @@ db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_param
   char* base = (char*)ws;
   SinglePlan* P = new SinglePlan();
   P->H = H; P->W = W; P->ld = ld; P->kh = psf->kh; P->kw = psf->kw; P->kind = psf->kind;
-  P->iters = iters; P->conv = p->conv; P->p = *p; P->ws = ws; P->L = L;
+  P->iters = iters; P->conv = p->conv; P->p = *p; P->ws = ws; P->L = L; P->rp = to_rrl(p);
   if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, (TapGroup*)(base + L.taps),
                           (int*)(base + L.ntaps), dev_status, s) != cudaSuccess) {
     delete P; return DB_ERR_CUDA;
@@ -316,11 +318,11 @@ db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, 
   if (P->conv == DB_CONV_PERIODIC) {
     if (run_rrl_fourier(f, P->ld, u, P->ld, (float*)(base + P->L.utmp), P->H, P->W, (float2*)(base + P->L.work),
                         (float2*)(base + P->L.qbuf), (const float2*)(base + P->L.s32), P->DW32.tw, P->DH32.tw,
-                        to_rrl(&P->p), P->iters, nullptr, 0, dev_status, s) != cudaSuccess)
+                        P->rp, P->iters, nullptr, 0, dev_status, s) != cudaSuccess)
       return DB_ERR_CUDA;
     return DB_OK;
   }
-  return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, P->kind, to_rrl(&P->p), P->iters, nullptr, 0, P->ws,
+  return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, P->kind, P->rp, P->iters, nullptr, 0, P->ws,
                          P->L,
                          dev_status, s, P->ng);
 }

@@ -314,6 +314,7 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.box = x.psf.kind == DB_PSF_BOX ? (kh == 1 ? 1 : 2) : 0;
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
     bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
+    bi.p.rf_lut = rf_lut_device();
     const size_t sm = bi.box ? std::max(box_smem_q(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1),
                                         box_smem_update(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1))
                              : std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),

@@ -19,7 +19,39 @@ static_assert(sizeof(TapGroup) == 16, "TapGroup is 16 bytes");
 struct RrlParams {
   float alpha, eps_phi, eps_psi, floor;
   int phi_robust, psi_tv;
+  const float* rf_lut;  // table of r_1 (DB_RF_LUT), nullptr: log1p form
 };
+
+// Table of r_1 for DB_RF_LUT (rf_lut.cu): entries at s_j = j * 65/kRfLutN.
+constexpr int kRfLutN = 8192;
+constexpr float kRfLutSmax = 65.0f;
+const float* rf_lut_device();  // this device's table, or nullptr in log1p mode
+int rf_mode();
+
+// r_f(b) = b - f - f ln(b/f) (Eq. 7).  log1p form: f (t - log1p t) with
+// t = (b - f)/f, free of cancellation near b = f.  Table form (Sec. 4.1):
+// f r_1(b/f), r_1 interpolated linearly between table entries, the closed
+// form below the first entry, the tangent at 65 beyond the table.
+__device__ __forceinline__ float rf_divergence(float b, float f, const RrlParams& p) {
+  if (p.rf_lut) {
+    const float x = __fdividef(b, f);
+    const float k = x * ((float)kRfLutN / kRfLutSmax);
+    float r1;
+    if (k < 1.0f) {
+      r1 = x - 1.0f - logf(x);
+    } else if (x > kRfLutSmax) {
+      r1 = fmaf(1.0f - 1.0f / kRfLutSmax, x - kRfLutSmax, __ldg(p.rf_lut + kRfLutN - 1));
+    } else {
+      const int j = min((int)k, kRfLutN - 1);
+      const float fr = k - (float)j;
+      const float a = __ldg(p.rf_lut + j - 1), c = __ldg(p.rf_lut + j);
+      r1 = fmaf(fr, c - a, a);
+    }
+    return f * r1;
+  }
+  const float t = __fdividef(b - f, f);
+  return f * (t - log1pf(t));
+}
 
 // A 1D DFT of length N along one axis: a power-of-two transform of length
 // M = 2^logM (M == N), or Bluestein's form with chirp c (N values) and the

@@ -43,8 +43,7 @@ struct FourierArgs {
 
 __device__ __forceinline__ float robust_weight_f(float b, float f, const RrlParams& p) {
   if (!p.phi_robust) return 1.0f;
-  const float t = __fdividef(b - f, f);
-  const float r = f * (t - log1pf(t));
+  const float r = rf_divergence(b, f, p);
   return p.eps_phi * rsqrtf(fmaxf(r, 0.0f) + p.eps_phi * p.eps_phi);
 }
 

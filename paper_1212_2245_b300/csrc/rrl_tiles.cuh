@@ -23,12 +23,10 @@ namespace db {
 // the full product, which cuts the rounding drift of 20 iterations about
 // sixfold against the FP64 reference.
 // ---------------------------------------------------------------------------
-// W = phi'(r_f(b)) (Eq. 7, 10) with r_f(b) = f (t - log(1+t)), t = (b - f)/f:
-// the same quantity as b - f - f ln(b/f) without its cancellation near b = f.
+// W = phi'(r_f(b)) (Eq. 7, 10), r_f by rf_divergence.
 __device__ __forceinline__ float robust_weight(float b, float f, const RrlParams& p) {
   if (!p.phi_robust) return 1.0f;
-  const float t = __fdividef(b - f, f);
-  const float r = f * (t - log1pf(t));
+  const float r = rf_divergence(b, f, p);
   return p.eps_phi * rsqrtf(fmaxf(r, 0.0f) + p.eps_phi * p.eps_phi);
 }
 
