@@ -291,13 +291,11 @@ db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_param
         round_spectrum(Sff, (float2*)(base + L.s32), (size_t)H * W, s) != cudaSuccess) {
       delete P; return DB_ERR_CUDA;
     }
-    // the Wiener state reuses the same tables and spectrum (2D transform)
-    P->wst.H = H; P->wst.W = W; P->wst.kh = psf->kh; P->wst.kw = psf->kw; P->wst.DW = FW; P->wst.DH = FH;
-    if (psf->kh == 1 || psf->kw == 1) {
-      // a one-axis PSF: the Wiener filter needs the 1D spectrum instead
-      if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {
-        delete P; return DB_ERR_CUDA;
-      }
+    // the Wiener filter's own spectrum (1D, or the 2D half spectrum of the
+    // real-pair passes) replaces the full one, already rounded for the
+    // iterations; the transform tables it rebuilds are the same
+    if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {
+      delete P; return DB_ERR_CUDA;
     }
   } else {
     if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {

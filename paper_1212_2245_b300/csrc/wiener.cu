@@ -88,7 +88,8 @@ __global__ void k_chirp(float4* __restrict__ c, float4* __restrict__ b, int N, i
   }
 }
 
-enum RowMode { ROW_PSF = 0, ROW_FWD_REAL = 1, ROW_INV_REAL = 2, ROW_WIENER_1D = 3, ROW_FWD_CPLX = 4 };
+enum RowMode { ROW_PSF = 0, ROW_FWD_REAL = 1, ROW_INV_REAL = 2, ROW_WIENER_1D = 3, ROW_FWD_CPLX = 4,
+               ROW_FWD_R2C = 5, ROW_PSF_R2C = 6, ROW_INV_C2R = 7 };
 enum ColMode { COL_FWD = 0, COL_WIENER = 1, COL_WIENER_1D_REAL = 2 };
 
 struct FftArgs {
@@ -114,6 +115,23 @@ __device__ __forceinline__ float4 wiener_gain(float4 S, float4 X, float K) {
 
 __device__ __forceinline__ float ff_round(float2 v) { return v.x + v.y; }
 
+// Storage position of frequency k in a transformed sequence: bit-reversed
+// for the power-of-two sweeps, natural for Bluestein's form.
+__device__ __forceinline__ int spec_pos(const Dft1ff& D, int k) {
+  if (D.c != nullptr || D.logM == 0) return k;
+  return (int)(__brev((unsigned)k) >> (32 - D.logM));
+}
+
+// Real rows in pairs (ROW_*_R2C, ROW_INV_C2R): sequence q carries image rows
+// 2q (real part) and 2q+1 (imaginary part).  A real row's spectrum is
+// Hermitian, X(N-k) = conj X(k), so columns k = 0..N/2 hold all of it.
+// From Z = X1 + i X2:  X1 = (Z(k) + conj Z(N-k))/2,  X2 = -i (Z(k) - conj Z(N-k))/2.
+__device__ __forceinline__ void unpack_pair(float4 Zk, float4 Zm, float4& X1, float4& X2) {
+  const float2 h = make_float2(0.5f, 0.f);
+  X1 = mkc(ff_mul(ff_add(re_(Zk), re_(Zm)), h), ff_mul(ff_sub(im_(Zk), im_(Zm)), h));
+  X2 = mkc(ff_mul(ff_add(im_(Zk), im_(Zm)), h), ff_mul(ff_sub(re_(Zm), re_(Zk)), h));
+}
+
 // Row transforms: a CTA owns R consecutive sequences (capacity M each)
 // starting at q0.  Global inputs are staged with asynchronous copies.
 template <int MODE>
@@ -129,14 +147,32 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
       cp_async4(stage + idx, a.fin + (size_t)q * a.ldf + c);
     } else if (MODE == ROW_INV_REAL || MODE == ROW_FWD_CPLX) {
       cp_async16(x + r * M + c, a.cbuf + (size_t)q * a.ldc + c);
-    } else if (MODE == ROW_WIENER_1D) {
+    } else if (MODE == ROW_WIENER_1D || MODE == ROW_FWD_R2C) {
       cp_async4(stage + 2 * idx, a.fin + (size_t)(2 * q) * a.ldf + c);
       if (2 * q + 1 < a.img_rows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)(2 * q + 1) * a.ldf + c);
     }
   }
   cp_async_wait_all();
   __syncthreads();
-  if (MODE != ROW_INV_REAL && MODE != ROW_FWD_CPLX) {
+  if (MODE == ROW_INV_C2R) {
+    // full Hermitian spectra of rows 2q, 2q+1 from their halves, packed as
+    // Z = Y1 + i Y2, placed in transform order
+    const int Nh = N / 2 + 1;
+    for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+      const int r = idx / N, k = idx - r * N;
+      const int q = q0 + r;
+      float4 Z = zzero();
+      if (q < a.nrows) {
+        const bool lo = k < Nh;
+        const int kk = lo ? k : N - k;
+        float4 Y1 = __ldg(a.cbuf + (size_t)(2 * q) * a.ldc + kk);
+        float4 Y2 = (2 * q + 1 < a.img_rows) ? __ldg(a.cbuf + (size_t)(2 * q + 1) * a.ldc + kk) : zzero();
+        if (!lo) { Y1 = zconj(Y1); Y2 = zconj(Y2); }
+        Z = zadd(Y1, zmul_pi(Y2));
+      }
+      x[r * M + spec_pos(a.D, k)] = Z;
+    }
+  } else if (MODE != ROW_INV_REAL && MODE != ROW_FWD_CPLX) {
     for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
       const int r = idx / N, c = idx - r * N;
       const int q = q0 + r;
@@ -147,6 +183,13 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
           const int cy = a.kh >> 1, cx = a.kw >> 1;
           const int ta = (q + cy) % a.nrows, tb = (c + cx) % N;
           if (ta < a.kh && tb < a.kw) v.x = __ldg(a.taps + ta * a.kw + tb);
+        } else if (MODE == ROW_PSF_R2C) {
+          // rows 2q, 2q+1 of the wrapped PSF image of a.img_rows rows
+          const int cy = a.kh >> 1, cx = a.kw >> 1;
+          const int tb = (c + cx) % N;
+          const int ta0 = (2 * q + cy) % a.img_rows, ta1 = (2 * q + 1 + cy) % a.img_rows;
+          if (ta0 < a.kh && tb < a.kw) v.x = __ldg(a.taps + ta0 * a.kw + tb);
+          if (2 * q + 1 < a.img_rows && ta1 < a.kh && tb < a.kw) v.z = __ldg(a.taps + ta1 * a.kw + tb);
         } else if (MODE == ROW_FWD_REAL) {
           v.x = fmaxf(stage[idx], a.floor_);
         } else {  // ROW_WIENER_1D: sequence q packs image rows 2q and 2q+1
@@ -158,7 +201,7 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
     }
   }
   __syncthreads();
-  if (MODE == ROW_INV_REAL) {
+  if (MODE == ROW_INV_REAL || MODE == ROW_INV_C2R) {
     dft_inv_ff(x, R, 1, M, a.D, false);
   } else {
     dft_fwd_ff(x, R, 1, M, a.D, false);
@@ -171,12 +214,29 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
       dft_inv_ff(x, R, 1, M, a.D, false);
     }
   }
+  if (MODE == ROW_FWD_R2C || MODE == ROW_PSF_R2C) {
+    const int Nh = N / 2 + 1;
+    for (int idx = threadIdx.x; idx < R * Nh; idx += blockDim.x) {
+      const int r = idx / Nh, k = idx - r * Nh;
+      const int q = q0 + r;
+      if (q >= a.nrows) continue;
+      float4 X1, X2;
+      unpack_pair(x[r * M + spec_pos(a.D, k)], x[r * M + spec_pos(a.D, k == 0 ? 0 : N - k)], X1, X2);
+      a.cbuf[(size_t)(2 * q) * a.ldc + k] = X1;
+      if (2 * q + 1 < a.img_rows) a.cbuf[(size_t)(2 * q + 1) * a.ldc + k] = X2;
+    }
+    return;
+  }
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
     const int r = idx / N, c = idx - r * N;
     const int q = q0 + r;
     if (q >= a.nrows) continue;
     const float4 v = x[r * M + c];
-    if (MODE == ROW_PSF || MODE == ROW_FWD_REAL || MODE == ROW_FWD_CPLX) {
+    if (MODE == ROW_INV_C2R) {
+      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
+      if (2 * q + 1 < a.img_rows)
+        a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
+    } else if (MODE == ROW_PSF || MODE == ROW_FWD_REAL || MODE == ROW_FWD_CPLX) {
       a.cbuf[(size_t)q * a.ldc + c] = v;
     } else if (MODE == ROW_INV_REAL) {
       a.uout[(size_t)q * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
@@ -379,6 +439,21 @@ cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W,
   return launch_cols<COL_FWD>(c, W, s);
 }
 
+// Half spectrum of a 2D PSF for the real-pair Wiener passes: H rows (column
+// transform order) x (W/2 + 1) columns (natural order), pitch W/2 + 1.
+cudaError_t run_psf_spectrum_half(const float* taps, int kh, int kw, int H, int W, float4* spec,
+                                  const Dft1ff& DW, const Dft1ff& DH, cudaStream_t s) {
+  const int Wh = W / 2 + 1;
+  FftArgs a = {};
+  a.taps = taps; a.kh = kh; a.kw = kw; a.nrows = (H + 1) / 2; a.img_rows = H; a.D = DW;
+  a.cbuf = spec; a.ldc = Wh;
+  cudaError_t e;
+  if ((e = launch_rows<ROW_PSF_R2C>(a, s)) != cudaSuccess) return e;
+  FftArgs c = {};
+  c.cbuf = spec; c.ldc = Wh; c.nrows = Wh; c.D = DH;
+  return launch_cols<COL_FWD>(c, Wh, s);
+}
+
 // Spectrum (storage order of D) of a one-row PSF of kw taps.
 cudaError_t psf_row_spectrum(const float* taps, int kw, const Dft1ff& D, float4* out, cudaStream_t s) {
   FftArgs a = {};
@@ -426,7 +501,7 @@ cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, void
     a.taps = taps; a.kh = 1; a.kw = kh; a.nrows = 1; a.D = S.DH; a.cbuf = spec; a.ldc = H;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
   } else {
-    if ((e = run_psf_spectrum_2d(taps, kh, kw, H, W, spec, S.DW, S.DH, s)) != cudaSuccess) return e;
+    if ((e = run_psf_spectrum_half(taps, kh, kw, H, W, spec, S.DW, S.DH, s)) != cudaSuccess) return e;
   }
   *st = S;
   return cudaSuccess;
@@ -453,17 +528,21 @@ cudaError_t wiener_apply(const float* f, float* u0, int ld, float K, float floor
     b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / H);
     return launch_cols<COL_WIENER_1D_REAL>(b, (W + 1) / 2, s);
   }
+  // real rows in pairs; only the W/2 + 1 columns of the Hermitian half
+  // spectrum go through the column pass
   cudaError_t e;
+  const int Wh = W / 2 + 1;
   FftArgs d = {};
-  d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = W; d.nrows = H; d.D = S.DW; d.floor_ = floor_;
-  if ((e = launch_rows<ROW_FWD_REAL>(d, s)) != cudaSuccess) return e;
+  d.fin = f; d.ldf = ld; d.cbuf = work; d.ldc = Wh; d.nrows = (H + 1) / 2; d.img_rows = H; d.D = S.DW;
+  d.floor_ = floor_;
+  if ((e = launch_rows<ROW_FWD_R2C>(d, s)) != cudaSuccess) return e;
   FftArgs g = {};
-  g.cbuf = work; g.ldc = W; g.spec = spec; g.ldspec = W; g.nrows = W; g.D = S.DH; g.K = K;
-  if ((e = launch_cols<COL_WIENER>(g, W, s)) != cudaSuccess) return e;
+  g.cbuf = work; g.ldc = Wh; g.spec = spec; g.ldspec = Wh; g.nrows = Wh; g.D = S.DH; g.K = K;
+  if ((e = launch_cols<COL_WIENER>(g, Wh, s)) != cudaSuccess) return e;
   FftArgs o = {};
-  o.cbuf = work; o.ldc = W; o.uout = u0; o.ldu = ld; o.nrows = H; o.D = S.DW;
-  o.floor_ = floor_; o.scale = ff_const(1.0 / ((double)H * (double)W)); o.spec = spec; o.K = K;
-  return launch_rows<ROW_INV_REAL>(o, s);
+  o.cbuf = work; o.ldc = Wh; o.uout = u0; o.ldu = ld; o.nrows = (H + 1) / 2; o.img_rows = H; o.D = S.DW;
+  o.floor_ = floor_; o.scale = ff_const(1.0 / ((double)H * (double)W));
+  return launch_rows<ROW_INV_C2R>(o, s);
 }
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps, int kh,
@@ -529,24 +608,27 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     if (sm > b->smem[WB_COL_1D]) b->smem[WB_COL_1D] = sm;
     return cudaSuccess;
   }
-  if ((e = run_psf_spectrum_2d(im.taps, im.kh, im.kw, H, W, im.spec, (*im.pDW), (*im.pDH), s)) != cudaSuccess) return e;
+  if ((e = run_psf_spectrum_half(im.taps, im.kh, im.kw, H, W, im.spec, (*im.pDW), (*im.pDH), s)) != cudaSuccess)
+    return e;
+  const int Wh = W / 2 + 1, Hp = (H + 1) / 2;
   FftArgs d = {};
-  d.fin = im.f; d.ldf = im.ld; d.cbuf = im.work; d.ldc = W; d.nrows = H; d.D = (*im.pDW); d.floor_ = im.floor_;
+  d.fin = im.f; d.ldf = im.ld; d.cbuf = im.work; d.ldc = Wh; d.nrows = Hp; d.img_rows = H; d.D = (*im.pDW);
+  d.floor_ = im.floor_;
   FftArgs g = {};
-  g.cbuf = im.work; g.ldc = W; g.spec = im.spec; g.ldspec = W; g.nrows = W; g.D = (*im.pDH); g.K = im.K;
+  g.cbuf = im.work; g.ldc = Wh; g.spec = im.spec; g.ldspec = Wh; g.nrows = Wh; g.D = (*im.pDH); g.K = im.K;
   FftArgs o = {};
-  o.cbuf = im.work; o.ldc = W; o.uout = im.u0; o.ldu = im.ldu; o.nrows = H; o.D = (*im.pDW);
-  o.floor_ = im.floor_; o.scale = ff_const(1.0 / ((double)H * (double)W)); o.spec = im.spec; o.K = im.K;
+  o.cbuf = im.work; o.ldc = Wh; o.uout = im.u0; o.ldu = im.ldu; o.nrows = Hp; o.img_rows = H; o.D = (*im.pDW);
+  o.floor_ = im.floor_; o.scale = ff_const(1.0 / ((double)H * (double)W));
   const int i1 = (int)b->jobs[WB_ROW_FWD].size(), i2 = (int)b->jobs[WB_COL_2D].size(),
             i3 = (int)b->jobs[WB_ROW_INV].size();
   b->jobs[WB_ROW_FWD].push_back(d);
   b->jobs[WB_COL_2D].push_back(g);
   b->jobs[WB_ROW_INV].push_back(o);
-  for (int q = 0; q < H; ++q) {
+  for (int q = 0; q < Hp; ++q) {
     b->items[WB_ROW_FWD].push_back(make_int2(i1, q));
     b->items[WB_ROW_INV].push_back(make_int2(i3, q));
   }
-  for (int c0 = 0; c0 < W; c0 += kBatchColC) b->items[WB_COL_2D].push_back(make_int2(i2, c0));
+  for (int c0 = 0; c0 < Wh; c0 += kBatchColC) b->items[WB_COL_2D].push_back(make_int2(i2, c0));
   const size_t smr = (size_t)(1 << (*im.pDW).logM) * sizeof(float4) + (size_t)2 * W * sizeof(float);
   const size_t smc = (size_t)kBatchColC * (1 << (*im.pDH).logM) * sizeof(float4);
   if (smr > b->smem[WB_ROW_FWD]) b->smem[WB_ROW_FWD] = smr;
@@ -612,9 +694,9 @@ cudaError_t wiener_batch_run(const WienerBatch* b, cudaStream_t s) {
   cudaError_t e;
   if ((e = launch_rows_batch<ROW_WIENER_1D>(b, WB_ROW_1D, s)) != cudaSuccess) return e;
   if ((e = launch_cols_batch<COL_WIENER_1D_REAL>(b, WB_COL_1D, s)) != cudaSuccess) return e;
-  if ((e = launch_rows_batch<ROW_FWD_REAL>(b, WB_ROW_FWD, s)) != cudaSuccess) return e;
+  if ((e = launch_rows_batch<ROW_FWD_R2C>(b, WB_ROW_FWD, s)) != cudaSuccess) return e;
   if ((e = launch_cols_batch<COL_WIENER>(b, WB_COL_2D, s)) != cudaSuccess) return e;
-  return launch_rows_batch<ROW_INV_REAL>(b, WB_ROW_INV, s);
+  return launch_rows_batch<ROW_INV_C2R>(b, WB_ROW_INV, s);
 }
 
 }  // namespace db
