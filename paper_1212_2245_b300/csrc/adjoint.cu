@@ -385,6 +385,233 @@ __global__ void k_adj_rev_diff2(const float2* __restrict__ a, AdjImage im, float
   }
 }
 
+// ---------------------------------------------------------------------------
+// Row kernels for one-row PSFs with kw <= kAdjRowTaps.  With kh == 1 the
+// blur, the correlation and their transposes act along rows only, so a CTA
+// stages whole rows in shared memory, padded by kAdjRowPad columns on each
+// side: constant continuation for u and q, zeros for the adjoint images.  The
+// exact transposes of the clamped sums equal the zero-padded sums except at
+// the two end pixels of a row, where the preimage ranges of the clamp are
+// summed explicitly.  Per pixel the arithmetic is that of the generic
+// kernels above, term for term.
+// ---------------------------------------------------------------------------
+constexpr int kAdjRowTaps = 32, kAdjRowPad = 32;
+constexpr int kAdjRowBlock = 4;  // rows staged per CTA and step
+
+__device__ __forceinline__ float zero_of(float) { return 0.f; }
+__device__ __forceinline__ float2 zero_of(float2) { return make_float2(0.f, 0.f); }
+
+// Stage rows R0..R0+nr-1 (pitch W, packed) into s, row r at s + r*(W + 2 pad)
+// + pad, padded by kAdjRowPad columns: constant continuation or zeros.
+template <typename T, bool CLAMP>
+__device__ __forceinline__ void stage_rows(T* s, const T* __restrict__ src, int R0, int nr, int W) {
+  const int L = W + 2 * kAdjRowPad;
+  for (int k = threadIdx.x; k < nr * L; k += blockDim.x) {
+    const int r = k / L, j = k - r * L - kAdjRowPad;
+    const T* row = src + (size_t)(R0 + r) * W;
+    T v;
+    if (CLAMP) v = row[clampi(j, W)];
+    else v = (j >= 0 && j < W) ? row[j] : zero_of(T());
+    s[k] = v;
+  }
+}
+
+__device__ __forceinline__ void load_row_taps(float* taps, const AdjImage& im) {
+  if ((int)threadIdx.x < im.kw) taps[threadIdx.x] = im.taps[threadIdx.x];
+}
+
+// Row-block loop: the CTA takes kAdjRowBlock rows at a time (grid-stride).
+#define ADJ_ROW_BLOCKS(rows)                                                                       \
+  for (int R0 = blockIdx.x * kAdjRowBlock; R0 < (rows); R0 += gridDim.x * kAdjRowBlock)
+#define ADJ_ROW_ITEMS(nr, W)                                                                       \
+  for (int it = threadIdx.x; it < (nr) * (W); it += blockDim.x)
+
+// b = C u and q = (W f/b, W)
+__global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_q_rows(const float* __restrict__ u,
+                                                                 const float* __restrict__ f0, AdjImage im,
+                                                                 float* __restrict__ b_out,
+                                                                 float2* __restrict__ q_out) {
+  extern __shared__ __align__(16) unsigned char adj_sm[];
+  __shared__ float taps[kAdjRowTaps];
+  float* su = (float*)adj_sm;
+  const int kw = im.kw, cx = kw >> 1, W = im.W, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  load_row_taps(taps, im);
+  ADJ_ROW_BLOCKS(rows) {
+    const int nr = min(kAdjRowBlock, rows - R0);
+    __syncthreads();
+    stage_rows<float, true>(su, u, R0, nr, W);
+    __syncthreads();
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float* sr = su + r * L + kAdjRowPad;
+      float b = 0.f;
+      for (int c = 0; c < kw; ++c) {
+        const float w = taps[c];
+        if (w != 0.f) b = fmaf(w, sr[j - (c - cx)], b);
+      }
+      const size_t idx = (size_t)R0 * W + it;
+      const float fv = f0[idx];
+      float rr;
+      const float w = phi_w(b, fv, im.p, &rr);
+      b_out[idx] = b;
+      q_out[idx] = make_float2(w * fv / b, w);
+    }
+  }
+}
+
+// A, B = C' q;  g = psi'(|grad u|^2)
+__global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_ab_rows(const float* __restrict__ u,
+                                                                  const float2* __restrict__ q, AdjImage im,
+                                                                  float2* __restrict__ ab_out,
+                                                                  float* __restrict__ g_out) {
+  extern __shared__ __align__(16) unsigned char adj_sm[];
+  __shared__ float taps[kAdjRowTaps];
+  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  float2* sq = (float2*)adj_sm;
+  float* su = (float*)(sq + kAdjRowBlock * L);
+  load_row_taps(taps, im);
+  ADJ_ROW_BLOCKS(rows) {
+    const int nr = min(kAdjRowBlock, rows - R0);
+    __syncthreads();
+    stage_rows<float2, true>(sq, q, R0, nr, W);
+    stage_rows<float, true>(su, u, R0, nr, W);
+    __syncthreads();
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float2* qr = sq + r * L + kAdjRowPad;
+      const float* ur = su + r * L + kAdjRowPad;
+      float A = 0.f, B = 0.f;
+      for (int c = 0; c < kw; ++c) {
+        const float w = taps[c];
+        if (w != 0.f) {
+          const float2 v = qr[j + (c - cx)];
+          A = fmaf(w, v.x, A);
+          B = fmaf(w, v.y, B);
+        }
+      }
+      const int R = R0 + r, n = R / H, i = R - n * H;
+      const float* img = u + (size_t)n * H * W;
+      const size_t idx = (size_t)R * W + j;
+      ab_out[idx] = make_float2(A, B);
+      const float gx = 0.5f * (ur[j + 1] - ur[j - 1]);
+      const float gy = 0.5f * (img[(size_t)clampi(i + 1, H) * W + j] - img[(size_t)clampi(i - 1, H) * W + j]);
+      g_out[idx] = psi_g(gx, gy, im.p);
+    }
+  }
+}
+
+// qbar = C'^T (Abar, Bbar);  tap partials of Abar q1(clip(j+d)) + Bbar q2(clip(j+d))
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT_rows(const float2* __restrict__ abbar,
+                                                                     const float2* __restrict__ q, AdjImage im,
+                                                                     float2* __restrict__ qbar,
+                                                                     float* __restrict__ tap_partial) {
+  extern __shared__ __align__(16) unsigned char adj_sm[];
+  __shared__ float taps[kAdjRowTaps];
+  const int kw = im.kw, cx = kw >> 1, W = im.W, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  float2* sa = (float2*)adj_sm;
+  float2* sq = sa + kAdjRowBlock * L;
+  load_row_taps(taps, im);
+  float acc[kAdjRowTaps];
+#pragma unroll
+  for (int t = 0; t < kAdjRowTaps; ++t) acc[t] = 0.f;
+  ADJ_ROW_BLOCKS(rows) {
+    const int nr = min(kAdjRowBlock, rows - R0);
+    __syncthreads();
+    stage_rows<float2, false>(sa, abbar, R0, nr, W);
+    stage_rows<float2, true>(sq, q, R0, nr, W);
+    __syncthreads();
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float2* ar = sa + r * L + kAdjRowPad;
+      const float2* qr = sq + r * L + kAdjRowPad;
+      float s1 = 0.f, s2 = 0.f;
+      if (j > 0 && j < W - 1) {
+        for (int c = 0; c < kw; ++c) {
+          const float w = taps[c];
+          const float2 v = ar[j - (c - cx)];
+          s1 = fmaf(w, v.x, s1);
+          s2 = fmaf(w, v.y, s2);
+        }
+      } else {
+        for (int c = 0; c < kw; ++c) {
+          int lo, hi;
+          preimage(j, c - cx, W, &lo, &hi);
+          float z1 = 0.f, z2 = 0.f;
+          for (int jj = lo; jj <= hi; ++jj) {
+            const float2 v = ar[jj];
+            z1 += v.x;
+            z2 += v.y;
+          }
+          s1 = fmaf(taps[c], z1, s1);
+          s2 = fmaf(taps[c], z2, s2);
+        }
+      }
+      qbar[(size_t)R0 * W + it] = make_float2(s1, s2);
+      const float2 v = ar[j];
+#pragma unroll
+      for (int t = 0; t < kAdjRowTaps; ++t) {
+        if (t < kw) {
+          const float2 qq = qr[j + t - cx];
+          acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
+        }
+      }
+    }
+  }
+  // (static indices keep acc in registers; kw is uniform, so every thread
+  // takes the same branches to the barriers inside)
+#pragma unroll
+  for (int t = 0; t < kAdjRowTaps; ++t)
+    if (t < kw) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
+}
+
+// U += C^T bbar;  tap partials of bbar(j) u(clip(j-d))
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT_rows(const float* __restrict__ bbar,
+                                                                     const float* __restrict__ u, AdjImage im,
+                                                                     float* __restrict__ Uacc,
+                                                                     float* __restrict__ tap_partial) {
+  extern __shared__ __align__(16) unsigned char adj_sm[];
+  __shared__ float taps[kAdjRowTaps];
+  const int kw = im.kw, cx = kw >> 1, W = im.W, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  float* sb = (float*)adj_sm;
+  float* su = sb + kAdjRowBlock * L;
+  load_row_taps(taps, im);
+  float acc[kAdjRowTaps];
+#pragma unroll
+  for (int t = 0; t < kAdjRowTaps; ++t) acc[t] = 0.f;
+  ADJ_ROW_BLOCKS(rows) {
+    const int nr = min(kAdjRowBlock, rows - R0);
+    __syncthreads();
+    stage_rows<float, false>(sb, bbar, R0, nr, W);
+    stage_rows<float, true>(su, u, R0, nr, W);
+    __syncthreads();
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float* br = sb + r * L + kAdjRowPad;
+      const float* ur = su + r * L + kAdjRowPad;
+      float sacc = 0.f;
+      if (j > 0 && j < W - 1) {
+        for (int c = 0; c < kw; ++c) sacc = fmaf(taps[c], br[j + (c - cx)], sacc);
+      } else {
+        for (int c = 0; c < kw; ++c) {
+          int lo, hi;
+          preimage(j, -(c - cx), W, &lo, &hi);
+          float z = 0.f;
+          for (int jj = lo; jj <= hi; ++jj) z += br[jj];
+          sacc = fmaf(taps[c], z, sacc);
+        }
+      }
+      Uacc[(size_t)R0 * W + it] += sacc;
+      const float bv = br[j];
+#pragma unroll
+      for (int t = 0; t < kAdjRowTaps; ++t)
+        if (t < kw) acc[t] = fmaf(bv, ur[j - (t - cx)], acc[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kAdjRowTaps; ++t)
+    if (t < kw) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
+}
+
 // Sum `nparts` partials of each of `nsum` sums in fixed order, in double,
 // and add them into out[k].
 __global__ void k_adj_reduce(const float* __restrict__ partials, int nsum, int nparts, double* __restrict__ out) {
@@ -455,13 +682,28 @@ __global__ void __launch_bounds__(256) k_adj_wiener_rows(const float* __restrict
   }
 }
 
-// Column sums of prow (rows x W complex) in double: P(k).
-__global__ void k_adj_psum(const float2* __restrict__ prow, int rows, int W, double2* __restrict__ P) {
+// Column sums of prow (rows x W complex) in double: P(k), in two levels of
+// fixed order: chunks of kPsumRows rows (one thread per column and chunk),
+// then the chunk sums in chunk order.
+constexpr int kPsumRows = 256;
+__global__ void k_adj_psum_part(const float2* __restrict__ prow, int rows, int W, double2* __restrict__ part) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, ch = blockIdx.y;
+  if (k >= W) return;
+  double sr = 0.0, si = 0.0;
+  const int r1 = min(rows, (ch + 1) * kPsumRows);
+  for (int r = ch * kPsumRows; r < r1; ++r) {
+    const float2 v = prow[(size_t)r * W + k];
+    sr += v.x;
+    si += v.y;
+  }
+  part[(size_t)ch * W + k] = make_double2(sr, si);
+}
+__global__ void k_adj_psum(const double2* __restrict__ part, int nch, int W, double2* __restrict__ P) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= W) return;
   double sr = 0.0, si = 0.0;
-  for (int r = 0; r < rows; ++r) {
-    const float2 v = prow[(size_t)r * W + k];
+  for (int c = 0; c < nch; ++c) {
+    const double2 v = part[(size_t)c * W + k];
     sr += v.x;
     si += v.y;
   }
@@ -474,12 +716,17 @@ __global__ void k_adj_psum(const float2* __restrict__ prow, int rows, int W, dou
 //   d(loss) = Re sum_k P(k) dM(k) / N,  dS(k)/dh(d) = E_d(k) (spectrum of a
 //   unit tap at offset d, same storage order as S).
 // One CTA; thread t < kw handles tap t, thread kw handles K.
-__global__ void k_adj_wiener_params(const double2* __restrict__ P, const float4* __restrict__ spec,
-                                    const float4* __restrict__ unit_spec, int W, int kw, float K,
-                                    double* __restrict__ grad_taps, double* __restrict__ grad_K) {
-  for (int t = threadIdx.x; t <= kw; t += blockDim.x) {
+// One CTA per output (taps 0..kw-1, then K): the sum over frequencies in
+// double, each thread a strided share, combined by a fixed-order tree.
+__global__ void __launch_bounds__(256) k_adj_wiener_params(const double2* __restrict__ P,
+                                                           const float4* __restrict__ spec,
+                                                           const float4* __restrict__ unit_spec, int W, int kw,
+                                                           float K, double* __restrict__ grad_taps,
+                                                           double* __restrict__ grad_K) {
+  __shared__ double red[256];
+  const int t = blockIdx.x;
   double acc = 0.0;
-  for (int k = 0; k < W; ++k) {
+  for (int k = threadIdx.x; k < W; k += blockDim.x) {
     const float4 Sf = spec[k];
     const double sr = (double)Sf.x + (double)Sf.y, si = (double)Sf.z + (double)Sf.w;
     const double den = sr * sr + si * si + (double)K;
@@ -499,9 +746,16 @@ __global__ void k_adj_wiener_params(const double2* __restrict__ P, const float4*
       acc += pr * mr - pi * mi;
     }
   }
-  acc /= (double)W;
-  if (t == kw) *grad_K += acc;
-  else grad_taps[t] += acc;
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double v = red[0] / (double)W;
+    if (t == kw) *grad_K += v;
+    else grad_taps[t] += v;
   }
 }
 
@@ -516,10 +770,10 @@ __global__ void k_unit_taps(float* __restrict__ out, int kw) {
 
 namespace db {
 
-constexpr int kAdjBlocks = 296;  // 2 x 148 SMs, grid-stride
+constexpr int kAdjBlocks = 592;  // 4 x 148 SMs, grid-stride
 
 struct AdjLayout {
-  size_t f0, seg, b, q, ab, g, ubar, uacc, abbar, dbar, qbar, bbar, f0bar, a, part, wraw, prow, psum,
+  size_t f0, seg, b, q, ab, g, ubar, uacc, abbar, dbar, qbar, bbar, f0bar, a, part, wraw, prow, ppart, psum,
       spec, unit_taps, unit_spec, tabs, total;
 };
 
@@ -545,6 +799,7 @@ static AdjLayout adj_layout(int N, int H, int W, int kw, int ntaps, int every) {
   L.part = take((size_t)(ntaps + 1) * kAdjBlocks * 4);
   L.wraw = take(n * 4);
   L.prow = take(n * 8);  // (N*H) x W
+  L.ppart = take((size_t)((N * H + kPsumRows - 1) / kPsumRows) * W * 16);
   L.psum = take((size_t)W * 16);
   L.spec = take((size_t)W * 16);
   L.unit_taps = take((size_t)kw * kw * 4);
@@ -618,6 +873,18 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   im.p.phi_robust = p->phi_robust; im.p.psi_tv = p->psi_tv;
   im.p.rf_lut = nullptr;  // the reverse pass differentiates the log form
   const int G = kAdjBlocks, T = kAdjThreads;
+  // row kernels (kw <= kAdjRowTaps): shared memory of the staged rows
+  const size_t rowlen = ((size_t)W + 2 * kAdjRowPad) * kAdjRowBlock;
+  const size_t smq = rowlen * 4, smab = rowlen * 12, smct = rowlen * 16, smcv = rowlen * 8;
+  const bool rowk = kw <= kAdjRowTaps && smct <= 227 * 1024;
+  if (rowk) {
+    if (smab > 48 * 1024)
+      ADJ_CHECK(cudaFuncSetAttribute(k_adj_fwd_ab_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
+    if (smct > 48 * 1024)
+      ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_corrT_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smct));
+    if (smcv > 48 * 1024)
+      ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_convT_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smcv));
+  }
 
   // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)
   ADJ_LAUNCH(k_floor_pack<<<G, T, 0, s>>>(f, ld, N * H, W, p->pos_floor, f0));
@@ -633,20 +900,32 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
                                 cudaMemcpyDeviceToDevice, s));
     for (int k = k0; k + 1 < k1; ++k) {  // rebuild the segment's iterates
       float* uk = seg + (size_t)(k - k0) * n;
-      ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
-      ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+      if (rowk) {
+        ADJ_LAUNCH(k_adj_fwd_q_rows<<<G, T, smq, s>>>(uk, f0, im, b, q));
+        ADJ_LAUNCH(k_adj_fwd_ab_rows<<<G, T, smab, s>>>(uk, q, im, ab, g));
+      } else {
+        ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
+        ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+      }
       ADJ_LAUNCH(k_adj_fwd_update<<<G, T, 0, s>>>(uk, ab, g, im, uk + n));
     }
     for (int k = k1 - 1; k >= k0; --k) {  // reverse steps
       const float* uk = seg + (size_t)(k - k0) * n;
-      ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
-      ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+      if (rowk) {
+        ADJ_LAUNCH(k_adj_fwd_q_rows<<<G, T, smq, s>>>(uk, f0, im, b, q));
+        ADJ_LAUNCH(k_adj_fwd_ab_rows<<<G, T, smab, s>>>(uk, q, im, ab, g));
+      } else {
+        ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
+        ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+      }
       ADJ_LAUNCH(k_adj_rev_update<<<G, T, 0, s>>>(ubar, uk, ab, g, im, uacc, abbar, dbar, part));
       ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
-      ADJ_LAUNCH(k_adj_rev_corrT<<<G, T, 0, s>>>(abbar, q, im, qbar, part));
+      if (rowk) ADJ_LAUNCH(k_adj_rev_corrT_rows<<<G, T, smct, s>>>(abbar, q, im, qbar, part));
+      else ADJ_LAUNCH(k_adj_rev_corrT<<<G, T, 0, s>>>(abbar, q, im, qbar, part));
       ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
       ADJ_LAUNCH(k_adj_rev_weight<<<G, T, 0, s>>>(qbar, b, f0, im, bbar, f0bar));
-      ADJ_LAUNCH(k_adj_rev_convT<<<G, T, 0, s>>>(bbar, uk, im, uacc, part));
+      if (rowk) ADJ_LAUNCH(k_adj_rev_convT_rows<<<G, T, smcv, s>>>(bbar, uk, im, uacc, part));
+      else ADJ_LAUNCH(k_adj_rev_convT<<<G, T, 0, s>>>(bbar, uk, im, uacc, part));
       ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
       ADJ_LAUNCH(k_adj_rev_diff1<<<G, T, 0, s>>>(dbar, uk, g, im, uacc, av));
       ADJ_LAUNCH(k_adj_rev_diff2<<<G, T, 0, s>>>(av, im, uacc));
@@ -677,8 +956,13 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const double invN = 1.0 / (double)W;
   const float2 invNf = make_float2((float)invN, (float)(invN - (double)(float)invN));
   ADJ_LAUNCH(k_adj_wiener_rows<<<N * H, 256, smem, s>>>(uacc, f0, W, spec, D, p->K, invNf, f0bar, prow));
-  ADJ_LAUNCH(k_adj_psum<<<(W + 255) / 256, 256, 0, s>>>(prow, N * H, W, psum));
-  ADJ_LAUNCH(k_adj_wiener_params<<<1, 1024, 0, s>>>(psum, spec, unit_spec, W, kw, p->K, grad_taps, grad_K));
+  {
+    const int nch = (N * H + kPsumRows - 1) / kPsumRows;
+    double2* ppart = (double2*)(base + L.ppart);
+    ADJ_LAUNCH(k_adj_psum_part<<<dim3((W + 255) / 256, nch), 256, 0, s>>>(prow, N * H, W, ppart));
+    ADJ_LAUNCH(k_adj_psum<<<(W + 255) / 256, 256, 0, s>>>(ppart, nch, W, psum));
+  }
+  ADJ_LAUNCH(k_adj_wiener_params<<<kw + 1, 256, 0, s>>>(psum, spec, unit_spec, W, kw, p->K, grad_taps, grad_K));
   ADJ_LAUNCH(k_grad_f_out<<<G, T, 0, s>>>(f0bar, f, ld, N * H, W, p->pos_floor, grad_f));
   return DB_OK;
 }
