@@ -521,7 +521,6 @@ def run_learn(args, world, rank, local):
     u = torch.empty_like(f)
     nck = (iters - 1) // every + 1
     ck = torch.empty(N, nck, H, W, device=dev)
-    ws = db.Workspace.for_image(H, W, 1, taps.shape[1], p)
     bws = db.Workspace(lib.db_backward_workspace_bytes(H, W, N, ctypes.byref(_lib.DbPsf(1, taps.shape[1], 0, taps.data_ptr())), every))
     gt = torch.zeros(taps.numel(), dtype=torch.float64, device=dev)
     ga = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -530,10 +529,10 @@ def run_learn(args, world, rank, local):
     gu = torch.empty_like(f)
     stream = torch.cuda.Stream(device=dev)
 
-    def forward():
-        for n in range(N):
-            db.wiener(f[n], taps, p, out=u[n], ws=ws, check=False)
-            db.rrl_iterate(f[n], u[n], taps, p, iters, ckpt=ck[n], ckpt_every=every, ws=ws, check=False)
+    wsn = db.Workspace(db.workspace_bytes_n(H, W, N, 1, taps.shape[1], p))
+
+    def forward():  # all images of the rank in one db_deblur_n call
+        db.deblur_n(f, taps, p, iters, out=u, ckpt=ck, ckpt_every=every, ws=wsn, check=False)
 
     def step():
         forward()
@@ -543,10 +542,10 @@ def run_learn(args, world, rank, local):
         db.rrl_backward(f, ck, gu, taps, p, iters, every, gt, ga, gk, grad_f=gf, ws=bws, check=False)
 
     with torch.cuda.stream(stream):
-        ws.reset_status(); bws.reset_status()
+        wsn.reset_status(); bws.reset_status()
         step()
         stream.synchronize()
-        ws.raise_on_flags("forward"); bws.raise_on_flags("backward")
+        wsn.raise_on_flags("forward"); bws.raise_on_flags("backward")
         n0 = lib.db_launch_count()
         g_step, g_fwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
         with torch.cuda.graph(g_step, stream=stream):
@@ -577,7 +576,7 @@ def run_learn(args, world, rank, local):
         torch.cuda.synchronize()
     ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     ms_f = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
-    ws.raise_on_flags("timed forward"); bws.raise_on_flags("timed backward")
+    wsn.raise_on_flags("timed forward"); bws.raise_on_flags("timed backward")
     if world > 1:
         t = torch.tensor([ms, ms_f], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

@@ -236,6 +236,23 @@ db_status db_rrl_iterate_noalloc(const float* f, float* u, int H, int W, int ld,
                                  const db_psf* psf, const db_params* p, int iters,
                                  int* dev_status, void* stream);
 
+/* ---- N equally sized images --------------------------------------------------
+ * n images of H x W (pitch ld) sharing one PSF and one parameter set, image k
+ * at f + k*img_stride (u likewise; img_stride >= H*ld elements): the Wiener
+ * filter (Eq. 2) and `iters` RRRL iterations (Eq. 9-12) on all of them, the
+ * iterations as launches over all images at once (spatial mode, constant
+ * continuation; DB_CONV_PERIODIC gives DB_ERR_UNSUPPORTED).  The result of
+ * each image equals db_deblur's on that image alone under the split
+ * schedule.  ckpt (nullable, device, n x ((iters-1)/ckpt_every+1) x H x W
+ * packed): image k's iterate at iteration c*ckpt_every is stored at
+ * ckpt + (k*nck + c)*H*W -- the layout db_rrl_backward reads.  Workspace:
+ * db_workspace_bytes_n.  The same ownership and error behaviour as
+ * db_deblur. */
+size_t db_workspace_bytes_n(int H, int W, int n, const db_psf* psf, const db_params* p);
+db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, long long img_stride,
+                      const db_psf* psf, const db_params* p, int iters, float* ckpt, int ckpt_every,
+                      void* ws, size_t ws_bytes, int* dev_status, void* stream);
+
 /* ---- prepared single-image pipeline ----------------------------------------
  * The paper computes the PSF transform once and reuses it for every image of
  * a given size (Sec. 5, the set-up excluded from its timings).  A plan does

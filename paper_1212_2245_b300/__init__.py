@@ -17,7 +17,7 @@ from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
            "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
-           "set_rf_eval", "version", "FrameStream"]
+           "set_rf_eval", "version", "FrameStream", "deblur_n", "workspace_bytes_n"]
 
 
 class DeblurError(RuntimeError):
@@ -64,6 +64,15 @@ def workspace_bytes(H: int, W: int, kh: int, kw: int, params: Params) -> int:
     if n == 0:
         raise DeblurError("invalid size or parameters for workspace query")
     return int(n)
+
+
+def workspace_bytes_n(H: int, W: int, n: int, kh: int, kw: int, params: Params) -> int:
+    """Workspace of db_deblur_n for n images of H x W."""
+    psf = _lib.DbPsf(kh, kw, 0, None)
+    nbytes = _lib.load().db_workspace_bytes_n(H, W, n, ctypes.byref(psf), ctypes.byref(_db_params(params)))
+    if nbytes == 0:
+        raise DeblurError("invalid size or parameters for db_deblur_n")
+    return int(nbytes)
 
 
 class Workspace:
@@ -155,6 +164,42 @@ def deblur(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, k
                          int(iters), ws.ptr, ws.nbytes, ws.status.data_ptr(), _stream()), "db_deblur")
     if check:
         ws.raise_on_flags("db_deblur")
+    return u
+
+
+def deblur_n(f: torch.Tensor, taps: torch.Tensor, params: Params, iters: int, *, kind: str = "general",
+             out: torch.Tensor | None = None, ckpt: torch.Tensor | None = None, ckpt_every: int = 0,
+             ws: Workspace | None = None, check: bool = True):
+    """WR3L on a stack f (N, H, W) of equally sized images sharing taps and
+    parameters (db_deblur_n): the iterations run as launches over all images
+    at once.  ckpt (N, nck, H, W), if given, receives every image's iterate
+    at iterations 0, ckpt_every, 2*ckpt_every, ... (nck = (iters-1)//ckpt_every+1)."""
+    if f.dim() != 3 or not f.is_cuda or f.dtype != torch.float32 or f.stride(2) != 1:
+        raise ValueError("f must be a (N, H, W) float32 CUDA tensor with unit column stride")
+    N, H, W = f.shape
+    ld, zs = f.stride(1), f.stride(0)
+    u = out if out is not None else torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device)
+    if u.shape != f.shape or u.stride() != f.stride():
+        raise ValueError("out must match f's shape and strides")
+    ck, every = 0, 0
+    if ckpt is not None:
+        if ckpt_every < 1:
+            raise ValueError("ckpt_every must be >= 1")
+        nck = (iters - 1) // ckpt_every + 1 if iters > 0 else 1
+        if not (ckpt.is_cuda and ckpt.dtype == torch.float32 and ckpt.is_contiguous()
+                and ckpt.numel() >= N * nck * H * W):
+            raise ValueError("ckpt must be a contiguous float32 CUDA tensor of N x nck images")
+        ck, every = ckpt.data_ptr(), int(ckpt_every)
+    lib = _lib.load()
+    psf, p = _db_psf(taps, kind), _db_params(params)
+    if ws is None:
+        ws = Workspace(workspace_bytes_n(H, W, N, taps.shape[0], taps.shape[1], params))
+    elif check:
+        ws.reset_status()
+    _check(lib.db_deblur_n(f.data_ptr(), u.data_ptr(), H, W, ld, N, zs, ctypes.byref(psf), ctypes.byref(p),
+                           int(iters), ck, every, ws.ptr, ws.nbytes, ws.status.data_ptr(), _stream()), "db_deblur_n")
+    if check:
+        ws.raise_on_flags("db_deblur_n")
     return u
 
 
@@ -320,15 +365,8 @@ class DeblurFn(torch.autograd.Function):
         taps_c = taps.detach().float().contiguous()
         nck = (iters - 1) // ckpt_every + 1 if iters > 0 else 1
         ckpts = torch.empty(N, nck, H, W, dtype=torch.float32, device=f.device)
-        out = torch.empty_like(f)
-        ws = Workspace.for_image(H, W, taps_c.shape[0], taps_c.shape[1], p)
-        for n in range(N):
-            wiener(f[n], taps_c, p, out=out[n], ws=ws, check=False)
-            if iters > 0:
-                rrl_iterate(f[n], out[n], taps_c, p, iters, ckpt=ckpts[n], ckpt_every=ckpt_every, ws=ws,
-                            check=False)
-            else:
-                ckpts[n, 0].copy_(out[n])
+        f = f.contiguous()
+        out = deblur_n(f, taps_c, p, iters, ckpt=ckpts, ckpt_every=ckpt_every, check=False)
         ctx.save_for_backward(f, taps_c, ckpts)
         ctx.p, ctx.iters, ctx.every = p, iters, ckpt_every
         return out

@@ -44,6 +44,9 @@ SIGNATURES = {
                                c_int, c_void_p, c_size_t, c_void_p, c_void_p]),
     "db_deblur": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, P_PSF, P_PAR, c_int, c_void_p,
                           c_size_t, c_void_p, c_void_p]),
+    "db_workspace_bytes_n": (c_size_t, [c_int, c_int, c_int, P_PSF, P_PAR]),
+    "db_deblur_n": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, ctypes.c_longlong, P_PSF, P_PAR, c_int,
+                            c_void_p, c_int, c_void_p, c_size_t, c_void_p, c_void_p]),
     "db_rrl_iterate_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, P_PSF, P_PAR, c_int,
                                        c_void_p, c_void_p]),
     "db_batch_workspace_bytes": (c_size_t, [ctypes.POINTER(DbImageDesc), c_int, c_int]),

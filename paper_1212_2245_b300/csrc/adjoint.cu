@@ -43,15 +43,16 @@ struct AdjImage {
   RrlParams p;
 };
 
-// Pixel loop over all N images: idx -> image offset `o`, row i, column j.
-#define ADJ_PIXELS(im)                                                                      \
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x, hw_ = (im).H * (im).W,              \
-           n_ = (im).N * hw_; idx < n_; idx += gridDim.x * blockDim.x)
+// Pixel loop over all N images, row by row (rows of all images packed, one
+// CTA per row, grid-stride; threads across the row): idx is the packed pixel
+// index; ADJ_DECOMPOSE gives the image offset `o`, row i and column j.
+#define ADJ_PIXELS(im)                                                                        \
+  for (int R_ = blockIdx.x; R_ < (im).N * (im).H; R_ += gridDim.x)                            \
+    for (int j_ = threadIdx.x, idx = R_ * (im).W + j_; j_ < (im).W; j_ += blockDim.x, idx += blockDim.x)
 #define ADJ_DECOMPOSE(im)                                    \
-  const int img_ = idx / ((im).H * (im).W);                  \
+  const int img_ = R_ / (im).H;                              \
   const int o = img_ * (im).H * (im).W;                      \
-  const int rem_ = idx - o;                                  \
-  const int i = rem_ / (im).W, j = rem_ - i * (im).W;
+  const int i = R_ - img_ * (im).H, j = j_;
 
 // ---------------------------------------------------------------------------
 // forward recompute of the intermediates of one iteration

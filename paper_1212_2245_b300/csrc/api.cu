@@ -14,13 +14,13 @@ static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_schedule{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-WsLayout ws_layout(int H, int W, int kh, int kw, int conv) {
+WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n) {
   WsLayout L = {};
   size_t off = 0;
   L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
   L.ntaps = off; off += 256;
-  L.utmp = off;  off += align256((size_t)H * upitch(W) * sizeof(float));
-  L.qbuf = off;  off += align256((size_t)H * qpitch(W) * sizeof(float2));
+  L.utmp = off;  off += align256((size_t)n * H * upitch(W) * sizeof(float));
+  L.qbuf = off;  off += align256((size_t)n * H * qpitch(W) * sizeof(float2));
   size_t spec_elems, work_elems;
   if (conv == DB_CONV_PERIODIC) { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
   else if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
@@ -234,6 +234,78 @@ db_status db_deblur(const float* f, float* u, int H, int W, int ld, const db_psf
   db_status st = db_wiener(f, u, H, W, ld, psf, p, ws, ws_bytes, dev_status, stream);
   if (st != DB_OK) return st;
   return db_rrl_iterate(f, u, H, W, ld, psf, p, iters, nullptr, 0, ws, ws_bytes, dev_status, stream);
+}
+
+// ---- N equally sized images ------------------------------------------------
+size_t db_workspace_bytes_n(int H, int W, int n, const db_psf* psf, const db_params* p) {
+  if (n < 1 || db_workspace_bytes(H, W, psf, p) == 0 || p->conv != DB_CONV_CLAMP) return 0;
+  return ws_layout(H, W, psf->kh, psf->kw, p->conv, n).total;
+}
+
+db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, long long img_stride,
+                      const db_psf* psf, const db_params* p, int iters, float* ckpt, int ckpt_every, void* ws,
+                      size_t ws_bytes, int* dev_status, void* stream) {
+  db_status st;
+  if ((st = check_image(f, u, H, W, ld)) != DB_OK) return st;
+  if (n < 1 || img_stride < (long long)H * ld) return DB_ERR_SHAPE;
+  if ((st = check_psf(psf, H, W)) != DB_OK) return st;
+  if ((st = check_params(p)) != DB_OK) return st;
+  if (p->conv != DB_CONV_CLAMP) return DB_ERR_UNSUPPORTED;
+  if (iters < 0 || (ckpt && ckpt_every < 1)) return DB_ERR_ARG;
+  const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv, n);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != DB_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  // Wiener: prepared once; a one-row PSF filters rows on their own, so the
+  // images of a contiguous stack of even height go through as one image of
+  // n*H rows (the row pairs of the packed transforms stay those of each image)
+  WienerState S;
+  if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &S, s) != cudaSuccess) return DB_ERR_CUDA;
+  if (psf->kh == 1 && img_stride == (long long)H * ld && H % 2 == 0) {  // same row pairs as one image
+    WienerState Sn = S;
+    Sn.H = n * H;
+    if (wiener_apply(f, u, ld, p->K, p->pos_floor, ws, L, Sn, s) != cudaSuccess) return DB_ERR_CUDA;
+  } else {
+    for (int z = 0; z < n; ++z)
+      if (wiener_apply(f + z * img_stride, u + z * img_stride, ld, p->K, p->pos_floor, ws, L, S, s) != cudaSuccess)
+        return DB_ERR_CUDA;
+  }
+  if (launch_prepare_taps(psf->taps, psf->kh, psf->kw, psf->kind, (TapGroup*)(base + L.taps),
+                          (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  if (iters == 0 && !ckpt) return DB_OK;
+  const size_t smem_need = psf->kind == DB_PSF_BOX ? rrl_box_smem(psf->kh, psf->kw) : rrl_split_smem(psf->kh, psf->kw);
+  if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
+  const RrlParams rp = to_rrl(p);
+  float* tmp = (float*)(base + L.utmp);
+  float2* qbuf = (float2*)(base + L.qbuf);
+  const int ldt = upitch(W);
+  const long long zt = (long long)H * ldt, zq = (long long)H * qpitch(W), hw = (long long)H * W;
+  const int nck = ckpt ? (iters > 0 ? (iters - 1) / ckpt_every + 1 : 1) : 0;
+  const float* src = u;
+  int ld_src = ld;
+  long long z_src = img_stride;
+  for (int k = 0; k < iters || (k == 0 && ckpt); ++k) {
+    if (ckpt && k % ckpt_every == 0 && k / ckpt_every < nck) {
+      // image z's checkpoint c goes to ckpt + (z * nck + c) * H * W
+      if (copy_images(src, ld_src, z_src, ckpt + (size_t)(k / ckpt_every) * hw, W, nck * hw, H, W, n, s) !=
+          cudaSuccess)
+        return DB_ERR_CUDA;
+    }
+    if (k >= iters) break;
+    float* dst = (k % 2 == 0) ? tmp : u;
+    const int ld_dst = (k % 2 == 0) ? ldt : ld;
+    const long long z_dst = (k % 2 == 0) ? zt : img_stride;
+    if (launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, (TapGroup*)(base + L.taps),
+                         (int*)(base + L.ntaps), psf->kh, psf->kw, rp, dev_status, 0, psf->kind == DB_PSF_BOX, s, n,
+                         img_stride, z_src, z_dst, zq) != cudaSuccess)
+      return DB_ERR_CUDA;
+    src = dst;
+    ld_src = ld_dst;
+    z_src = z_dst;
+  }
+  if (src != u && copy_images(src, ld_src, z_src, u, ld, img_stride, H, W, n, s) != cudaSuccess) return DB_ERR_CUDA;
+  return DB_OK;
 }
 
 }  // extern "C"

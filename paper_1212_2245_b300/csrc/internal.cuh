@@ -91,7 +91,10 @@ struct WsLayout {
   size_t flow;     // flow_ws_bytes(H, W): task counter and per-tile progress counters
   size_t total;
 };
-WsLayout ws_layout(int H, int W, int kh, int kw, int conv);
+WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n = 1);  // n: images sharing it
+// Copy n images of H x W: image z from src + z*zsrc (pitch lds) to dst + z*zdst (pitch ldd).
+cudaError_t copy_images(const float* src, int lds, long long zsrc, float* dst, int ldd, long long zdst, int H, int W,
+                        int n, cudaStream_t s);
 
 // ---- launchers (return cudaError_t of the launch) --------------------------
 int tap_group_height(int kh);
@@ -103,7 +106,8 @@ size_t rrl_split_smem(int kh, int kw);  // larger of the two split kernels
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             int ng_bound, int box, cudaStream_t s);
+                             int ng_bound, int box, cudaStream_t s, int nz = 1, long long zf = 0,
+                             long long zin = 0, long long zout = 0, long long zq = 0);
 size_t rrl_box_smem(int kh, int kw);  // split kernels of a box PSF (kh == 1 or kw == 1)
 
 // all iterations in one persistent launch ordered by tile dependencies;

@@ -137,16 +137,23 @@ struct PdlDep {
   }
 };
 
+// Equally sized images side by side: image z of a launch with gridDim.z > 1
+// is at these element offsets times z (zero for one image).
+struct ZStride {
+  long long f, in, out, q;
+};
+
 template <int TH, int TW, int R, int M, int P>
 __global__ void __launch_bounds__((TH / R) * TW, 8) k_rrl_q(const float* __restrict__ f, int ldf,
                                                const float* __restrict__ uin, int ldin,
                                                float2* __restrict__ q, int ldq, int H, int W,
                                                const TapGroup* __restrict__ groups_g,
                                                const int* __restrict__ ngroups_g, int kh, int kw,
-                                               int ng_max, RrlParams p) {
+                                               int ng_max, RrlParams p, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  q_tile<TH, TW, R, M, P>(smem_raw, f, ldf, uin, ldin, q, ldq, H, W, groups_g, ngroups_g, kh, kw, ng_max, p,
-                          blockIdx.y * TH, blockIdx.x * TW, PdlDep());
+  const long long z = blockIdx.z;
+  q_tile<TH, TW, R, M, P>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W, groups_g,
+                          ngroups_g, kh, kw, ng_max, p, blockIdx.y * TH, blockIdx.x * TW, PdlDep());
 }
 
 template <int TH, int TW, int R, int M, int P>
@@ -155,10 +162,12 @@ __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* _
                                                     float* __restrict__ uout, int ldout, int H, int W,
                                                     const TapGroup* __restrict__ groups_g,
                                                     const int* __restrict__ ngroups_g, int kh, int kw,
-                                                    int ng_max, RrlParams p, int* status) {
+                                                    int ng_max, RrlParams p, int* status, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  update_tile<TH, TW, R, M, P>(smem_raw, q, ldq, uin, ldin, uout, ldout, H, W, groups_g, ngroups_g, kh, kw,
-                               ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW, PdlDep());
+  const long long z = blockIdx.z;
+  update_tile<TH, TW, R, M, P>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H, W,
+                               groups_g, ngroups_g, kh, kw, ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW,
+                               PdlDep());
 }
 
 // box PSFs: the same split pair with sliding-window sums (rrl_box.cuh)
@@ -166,20 +175,23 @@ template <bool HORIZ>
 __global__ void __launch_bounds__(128) k_rrl_q_box(const float* __restrict__ f, int ldf,
                                                   const float* __restrict__ uin, int ldin, float2* __restrict__ q,
                                                   int ldq, int H, int W, const int* __restrict__ ngroups_g,
-                                                  RrlParams p) {
+                                                  RrlParams p, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  q_tile_box<32, 32, 8, HORIZ>(smem_raw, f, ldf, uin, ldin, q, ldq, H, W, ngroups_g, p, blockIdx.y * 32,
-                               blockIdx.x * 32, PdlDep());
+  const long long z = blockIdx.z;
+  q_tile_box<32, 32, 8, HORIZ>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W,
+                               ngroups_g, p, blockIdx.y * 32, blockIdx.x * 32, PdlDep());
 }
 
 template <bool HORIZ>
 __global__ void __launch_bounds__(128) k_rrl_update_box(const float2* __restrict__ q, int ldq,
                                                        const float* __restrict__ uin, int ldin,
                                                        float* __restrict__ uout, int ldout, int H, int W,
-                                                       const int* __restrict__ ngroups_g, RrlParams p, int* status) {
+                                                       const int* __restrict__ ngroups_g, RrlParams p, int* status,
+                                                       ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  update_tile_box<32, 32, 8, HORIZ>(smem_raw, q, ldq, uin, ldin, uout, ldout, H, W, ngroups_g, p, status,
-                                    blockIdx.y * 32, blockIdx.x * 32, PdlDep());
+  const long long z = blockIdx.z;
+  update_tile_box<32, 32, 8, HORIZ>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H,
+                                    W, ngroups_g, p, status, blockIdx.y * 32, blockIdx.x * 32, PdlDep());
 }
 
 // ---------------------------------------------------------------------------
@@ -232,6 +244,8 @@ struct IterArgs {
   int H, W; const TapGroup* groups; const int* ngroups; int kh, kw; RrlParams p; int* status;
   int ng_bound;  // known upper bound of the group count (0: use max_tap_groups)
   int box;       // DB_PSF_BOX taps: sliding-window sums (split schedule only)
+  int nz;        // images per launch (split schedule), offsets zs
+  ZStride zs;
 };
 
 template <int M, int P>
@@ -270,16 +284,16 @@ static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.gridDim = dim3((a.W + kQTW - 1) / kQTW, (a.H + kQTH - 1) / kQTH);
+  cfg.gridDim = dim3((a.W + kQTW - 1) / kQTW, (a.H + kQTH - 1) / kQTH, a.nz);
   cfg.dynamicSmemBytes = sq;
   if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, qpitch(a.W), a.H, a.W, a.groups, a.ngroups,
-                              a.kh, a.kw, ng_max, a.p)) != cudaSuccess)
+                              a.kh, a.kw, ng_max, a.p, a.zs)) != cudaSuccess)
     return e;
   count_launch();
-  cfg.gridDim = dim3((a.W + kUTW - 1) / kUTW, (a.H + kUTH - 1) / kUTH);
+  cfg.gridDim = dim3((a.W + kUTW - 1) / kUTW, (a.H + kUTH - 1) / kUTH, a.nz);
   cfg.dynamicSmemBytes = su;
   if ((e = cudaLaunchKernelEx(&cfg, ku, (const float2*)a.q, qpitch(a.W), a.uin, a.ldin, a.uout, a.ldout, a.H, a.W, a.groups,
-                              a.ngroups, a.kh, a.kw, ng_max, a.p, a.status)) != cudaSuccess)
+                              a.ngroups, a.kh, a.kw, ng_max, a.p, a.status, a.zs)) != cudaSuccess)
     return e;
   count_launch();
   return cudaSuccess;
@@ -300,21 +314,37 @@ static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(32, 4);
-  cfg.gridDim = dim3((a.W + 31) / 32, (a.H + 31) / 32);
+  cfg.gridDim = dim3((a.W + 31) / 32, (a.H + 31) / 32, a.nz);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.dynamicSmemBytes = sq;
-  if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, qpitch(a.W), a.H, a.W, a.ngroups, a.p)) !=
-      cudaSuccess)
+  if ((e = cudaLaunchKernelEx(&cfg, kq, a.f, a.ldf, a.uin, a.ldin, a.q, qpitch(a.W), a.H, a.W, a.ngroups, a.p,
+                              a.zs)) != cudaSuccess)
     return e;
   count_launch();
   cfg.dynamicSmemBytes = su;
   if ((e = cudaLaunchKernelEx(&cfg, ku, (const float2*)a.q, qpitch(a.W), a.uin, a.ldin, a.uout, a.ldout, a.H, a.W,
-                              a.ngroups, a.p, a.status)) != cudaSuccess)
+                              a.ngroups, a.p, a.status, a.zs)) != cudaSuccess)
     return e;
   count_launch();
   return cudaSuccess;
+}
+
+__global__ void k_copy_images(const float* __restrict__ src, int lds, long long zsrc, float* __restrict__ dst,
+                              int ldd, long long zdst, int H, int W) {
+  const int z = blockIdx.z;
+  for (int i = blockIdx.y; i < H; i += gridDim.y)
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < W; j += gridDim.x * blockDim.x)
+      dst[z * zdst + (long long)i * ldd + j] = src[z * zsrc + (long long)i * lds + j];
+}
+
+cudaError_t copy_images(const float* src, int lds, long long zsrc, float* dst, int ldd, long long zdst, int H, int W,
+                        int n, cudaStream_t s) {
+  const dim3 grid((W + 255) / 256, H < 256 ? H : 256, n);
+  k_copy_images<<<grid, 256, 0, s>>>(src, lds, zsrc, dst, ldd, zdst, H, W);
+  count_launch();
+  return cudaGetLastError();
 }
 
 size_t rrl_box_smem(int kh, int kw) {
@@ -348,15 +378,17 @@ static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
 cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ldin, float* uout,
                                int ldout, int H, int W, const TapGroup* groups, const int* ngroups,
                                int kh, int kw, const RrlParams& p, int* status, cudaStream_t s) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status, 0, 0};
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, nullptr, H, W, groups, ngroups, kh, kw, p, status, 0, 0, 1, {}};
   return dispatch<false>(a, s);
 }
 
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             int ng_bound, int box, cudaStream_t s) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound, box};
+                             int ng_bound, int box, cudaStream_t s, int nz, long long zf, long long zin,
+                             long long zout, long long zq) {
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound, box,
+                      nz, {zf, zin, zout, zq}};
   if (box) return kh == 1 ? launch_split_box<true>(a, s) : launch_split_box<false>(a, s);
   return dispatch<true>(a, s);
 }
