@@ -613,6 +613,206 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT_rows(const float*
     if (t < kw) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
 }
 
+// Forward recompute of one iteration for one-row PSFs, fused: b = C u and
+// q = (W f/b, W) into a shared row, then A, B = C' q and g from it.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __restrict__ u,
+                                                               const float* __restrict__ f0, AdjImage im,
+                                                               float* __restrict__ b_out,
+                                                               float2* __restrict__ q_out,
+                                                               float2* __restrict__ ab_out,
+                                                               float* __restrict__ g_out) {
+  extern __shared__ __align__(16) unsigned char adj_sm[];
+  __shared__ float taps[kAdjRowTaps];
+  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  float2* sq = (float2*)adj_sm;
+  float* su = (float*)(sq + kAdjRowBlock * L);
+  load_row_taps(taps, im);
+  ADJ_ROW_BLOCKS(rows) {
+    const int nr = min(kAdjRowBlock, rows - R0);
+    __syncthreads();
+    stage_rows<float, true>(su, u, R0, nr, W);
+    __syncthreads();
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float* ur = su + r * L + kAdjRowPad;
+      float bb = 0.f;
+      for (int c = 0; c < kw; ++c) {
+        const float w = taps[c];
+        if (w != 0.f) bb = fmaf(w, ur[j - (c - cx)], bb);
+      }
+      const size_t idx = (size_t)R0 * W + it;
+      const float fv = f0[idx];
+      float rr;
+      const float w = phi_w(bb, fv, im.p, &rr);
+      const float2 qv = make_float2(w * fv / bb, w);
+      b_out[idx] = bb;
+      q_out[idx] = qv;
+      sq[r * L + kAdjRowPad + j] = qv;
+    }
+    __syncthreads();
+    // constant continuation of q beyond the row ends
+    for (int k = threadIdx.x; k < nr * 2 * kAdjRowPad; k += blockDim.x) {
+      const int r = k / (2 * kAdjRowPad), t = k - r * 2 * kAdjRowPad;
+      float2* qr = sq + r * L + kAdjRowPad;
+      if (t < kAdjRowPad) qr[-1 - t] = qr[0];
+      else qr[W + (t - kAdjRowPad)] = qr[W - 1];
+    }
+    __syncthreads();
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float2* qr = sq + r * L + kAdjRowPad;
+      const float* ur = su + r * L + kAdjRowPad;
+      float A = 0.f, B = 0.f;
+      for (int c = 0; c < kw; ++c) {
+        const float w = taps[c];
+        if (w != 0.f) {
+          const float2 v = qr[j + (c - cx)];
+          A = fmaf(w, v.x, A);
+          B = fmaf(w, v.y, B);
+        }
+      }
+      const int R = R0 + r, n = R / H, i = R - n * H;
+      const float* img = u + (size_t)n * H * W;
+      const size_t idx = (size_t)R * W + j;
+      ab_out[idx] = make_float2(A, B);
+      const float gx = 0.5f * (ur[j + 1] - ur[j - 1]);
+      const float gy = 0.5f * (img[(size_t)clampi(i + 1, H) * W + j] - img[(size_t)clampi(i - 1, H) * W + j]);
+      g_out[idx] = psi_g(gx, gy, im.p);
+    }
+  }
+}
+
+// One reverse step for one-row PSFs, fused row by row:
+//   U = U' num/den, Abar, Bbar, Dbar          (as k_adj_rev_update)
+//   qbar = C'^T (Abar, Bbar)                  (as k_adj_rev_corrT)
+//   bbar, f0bar                               (as k_adj_rev_weight)
+//   U += C^T bbar                             (as k_adj_rev_convT)
+// with the alpha partial in part[0 .. G) and the tap partials (both
+// transposes, summed per tap) in part[G + t G ...].  The diffusion adjoint
+// (k_adj_rev_diff1/2) follows: it needs Dbar of the neighbouring rows.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
+    const float* __restrict__ Ubar_next, const float* __restrict__ u, const float2* __restrict__ ab,
+    const float* __restrict__ g, const float2* __restrict__ q, const float* __restrict__ b,
+    const float* __restrict__ f0, AdjImage im, float* __restrict__ Uacc, float* __restrict__ Dbar,
+    float* __restrict__ f0bar, float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char adj_sm[];
+  __shared__ float taps[kAdjRowTaps];
+  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  float2* sa = (float2*)adj_sm;
+  float2* sq = sa + kAdjRowBlock * L;
+  float* sb = (float*)(sq + kAdjRowBlock * L);
+  float* su = sb + kAdjRowBlock * L;
+  load_row_taps(taps, im);
+  float acc[kAdjRowTaps];
+#pragma unroll
+  for (int t = 0; t < kAdjRowTaps; ++t) acc[t] = 0.f;
+  float asum = 0.f;
+  ADJ_ROW_BLOCKS(rows) {
+    const int nr = min(kAdjRowBlock, rows - R0);
+    __syncthreads();
+    stage_rows<float2, true>(sq, q, R0, nr, W);
+    stage_rows<float, true>(su, u, R0, nr, W);
+    for (int k = threadIdx.x; k < nr * 2 * kAdjRowPad; k += blockDim.x) {  // zero pads of abbar, bbar
+      const int r = k / (2 * kAdjRowPad), t = k - r * 2 * kAdjRowPad;
+      const int off = r * L + (t < kAdjRowPad ? t : W + t);
+      sa[off] = make_float2(0.f, 0.f);
+      sb[off] = 0.f;
+    }
+    // U = U' num/den, Abar, Bbar, Dbar
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const int R = R0 + r, n = R / H, i = R - n * H;
+      const size_t o = (size_t)n * H * W, idx = (size_t)R0 * W + it;
+      const float D = diffusion_at(u + o, g + o, i, j, H, W);
+      const float2 v = ab[idx];
+      const float Dp = fmaxf(D, 0.f), Dm = fminf(D, 0.f);
+      const float num = v.x + im.p.alpha * Dp;
+      const float den = v.y - im.p.alpha * Dm;
+      const float ub = Ubar_next[idx], uu = u[idx];
+      const float Ab = ub * uu / den;
+      const float Bb = -ub * uu * num / (den * den);
+      Uacc[idx] = ub * num / den;
+      sa[r * L + kAdjRowPad + j] = make_float2(Ab, Bb);
+      Dbar[idx] = im.p.alpha * ((D > 0.f ? Ab : 0.f) - (D < 0.f ? Bb : 0.f));
+      asum += Ab * Dp - Bb * Dm;
+    }
+    __syncthreads();
+    // qbar = C'^T (Abar, Bbar); bbar and f0bar; correlation tap partials
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float2* ar = sa + r * L + kAdjRowPad;
+      const float2* qr = sq + r * L + kAdjRowPad;
+      float s1 = 0.f, s2 = 0.f;
+      if (j > 0 && j < W - 1) {
+        for (int c = 0; c < kw; ++c) {
+          const float w = taps[c];
+          const float2 v = ar[j - (c - cx)];
+          s1 = fmaf(w, v.x, s1);
+          s2 = fmaf(w, v.y, s2);
+        }
+      } else {
+        for (int c = 0; c < kw; ++c) {
+          int lo, hi;
+          preimage(j, c - cx, W, &lo, &hi);
+          float z1 = 0.f, z2 = 0.f;
+          for (int jj = lo; jj <= hi; ++jj) {
+            const float2 v = ar[jj];
+            z1 += v.x;
+            z2 += v.y;
+          }
+          s1 = fmaf(taps[c], z1, s1);
+          s2 = fmaf(taps[c], z2, s2);
+        }
+      }
+      const float2 v = ar[j];
+#pragma unroll
+      for (int t = 0; t < kAdjRowTaps; ++t) {
+        if (t < kw) {
+          const float2 qq = qr[j + t - cx];
+          acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
+        }
+      }
+      const size_t idx = (size_t)R0 * W + it;
+      const float bv = b[idx], fv = f0[idx];
+      float rr;
+      const float w = phi_w(bv, fv, im.p, &rr);
+      const float Wbar = s1 * fv / bv + s2;
+      // phi''(r) = -phi'(r)^3 / (2 eps^2) for the regularised L1 penaliser
+      const float rbar = im.p.phi_robust ? Wbar * (-w * w * w / (2.f * im.p.eps_phi * im.p.eps_phi)) : 0.f;
+      sb[r * L + kAdjRowPad + j] = -s1 * w * fv / (bv * bv) + rbar * (1.f - fv / bv);
+      f0bar[idx] += s1 * w / bv - rbar * logf(bv / fv);
+    }
+    __syncthreads();
+    // U += C^T bbar; convolution tap partials
+    ADJ_ROW_ITEMS(nr, W) {
+      const int r = it / W, j = it - r * W;
+      const float* br = sb + r * L + kAdjRowPad;
+      const float* ur = su + r * L + kAdjRowPad;
+      float sacc = 0.f;
+      if (j > 0 && j < W - 1) {
+        for (int c = 0; c < kw; ++c) sacc = fmaf(taps[c], br[j + (c - cx)], sacc);
+      } else {
+        for (int c = 0; c < kw; ++c) {
+          int lo, hi;
+          preimage(j, -(c - cx), W, &lo, &hi);
+          float z = 0.f;
+          for (int jj = lo; jj <= hi; ++jj) z += br[jj];
+          sacc = fmaf(taps[c], z, sacc);
+        }
+      }
+      Uacc[(size_t)R0 * W + it] += sacc;
+      const float bv = br[j];
+#pragma unroll
+      for (int t = 0; t < kAdjRowTaps; ++t)
+        if (t < kw) acc[t] = fmaf(bv, ur[j - (t - cx)], acc[t]);
+    }
+  }
+  block_reduce_add(part + blockIdx.x, asum);
+#pragma unroll
+  for (int t = 0; t < kAdjRowTaps; ++t)
+    if (t < kw) block_reduce_add(part + (size_t)(1 + t) * gridDim.x + blockIdx.x, acc[t]);
+}
+
 // Sum `nparts` partials of each of `nsum` sums in fixed order, in double,
 // and add them into out[k].
 __global__ void k_adj_reduce(const float* __restrict__ partials, int nsum, int nparts, double* __restrict__ out) {
@@ -876,9 +1076,14 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const int G = kAdjBlocks, T = kAdjThreads;
   // row kernels (kw <= kAdjRowTaps): shared memory of the staged rows
   const size_t rowlen = ((size_t)W + 2 * kAdjRowPad) * kAdjRowBlock;
-  const size_t smq = rowlen * 4, smab = rowlen * 12, smct = rowlen * 16, smcv = rowlen * 8;
-  const bool rowk = kw <= kAdjRowTaps && smct <= 227 * 1024;
+  const size_t smq = rowlen * 4, smab = rowlen * 12, smct = rowlen * 16, smcv = rowlen * 8, smrev = rowlen * 24;
+  const bool rowk = kw <= kAdjRowTaps && smrev <= 227 * 1024;
+  (void)smq; (void)smct; (void)smcv;
   if (rowk) {
+    if (smrev > 48 * 1024)
+      ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smrev));
+    if (smab > 48 * 1024)
+      ADJ_CHECK(cudaFuncSetAttribute(k_adj_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
     if (smab > 48 * 1024)
       ADJ_CHECK(cudaFuncSetAttribute(k_adj_fwd_ab_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
     if (smct > 48 * 1024)
@@ -902,8 +1107,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     for (int k = k0; k + 1 < k1; ++k) {  // rebuild the segment's iterates
       float* uk = seg + (size_t)(k - k0) * n;
       if (rowk) {
-        ADJ_LAUNCH(k_adj_fwd_q_rows<<<G, T, smq, s>>>(uk, f0, im, b, q));
-        ADJ_LAUNCH(k_adj_fwd_ab_rows<<<G, T, smab, s>>>(uk, q, im, ab, g));
+        ADJ_LAUNCH(k_adj_fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
       } else {
         ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
         ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
@@ -913,21 +1117,21 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     for (int k = k1 - 1; k >= k0; --k) {  // reverse steps
       const float* uk = seg + (size_t)(k - k0) * n;
       if (rowk) {
-        ADJ_LAUNCH(k_adj_fwd_q_rows<<<G, T, smq, s>>>(uk, f0, im, b, q));
-        ADJ_LAUNCH(k_adj_fwd_ab_rows<<<G, T, smab, s>>>(uk, q, im, ab, g));
+        ADJ_LAUNCH(k_adj_fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
+        ADJ_LAUNCH(k_adj_rev_rows<<<G, T, smrev, s>>>(ubar, uk, ab, g, q, b, f0, im, uacc, dbar, f0bar, part));
+        ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
+        ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part + G, ntaps, G, grad_taps));
       } else {
         ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
         ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+        ADJ_LAUNCH(k_adj_rev_update<<<G, T, 0, s>>>(ubar, uk, ab, g, im, uacc, abbar, dbar, part));
+        ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
+        ADJ_LAUNCH(k_adj_rev_corrT<<<G, T, 0, s>>>(abbar, q, im, qbar, part));
+        ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
+        ADJ_LAUNCH(k_adj_rev_weight<<<G, T, 0, s>>>(qbar, b, f0, im, bbar, f0bar));
+        ADJ_LAUNCH(k_adj_rev_convT<<<G, T, 0, s>>>(bbar, uk, im, uacc, part));
+        ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
       }
-      ADJ_LAUNCH(k_adj_rev_update<<<G, T, 0, s>>>(ubar, uk, ab, g, im, uacc, abbar, dbar, part));
-      ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
-      if (rowk) ADJ_LAUNCH(k_adj_rev_corrT_rows<<<G, T, smct, s>>>(abbar, q, im, qbar, part));
-      else ADJ_LAUNCH(k_adj_rev_corrT<<<G, T, 0, s>>>(abbar, q, im, qbar, part));
-      ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
-      ADJ_LAUNCH(k_adj_rev_weight<<<G, T, 0, s>>>(qbar, b, f0, im, bbar, f0bar));
-      if (rowk) ADJ_LAUNCH(k_adj_rev_convT_rows<<<G, T, smcv, s>>>(bbar, uk, im, uacc, part));
-      else ADJ_LAUNCH(k_adj_rev_convT<<<G, T, 0, s>>>(bbar, uk, im, uacc, part));
-      ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
       ADJ_LAUNCH(k_adj_rev_diff1<<<G, T, 0, s>>>(dbar, uk, g, im, uacc, av));
       ADJ_LAUNCH(k_adj_rev_diff2<<<G, T, 0, s>>>(av, im, uacc));
       float* t = ubar; ubar = uacc; uacc = t;
