@@ -136,6 +136,12 @@ class ClockSampler:
 LINE1024_FLOW_ITER_DRAM_BYTES = (8.472576e6 + 1.853440e6) / 20
 
 
+def step_stats(ms_list):
+    """Median, minimum and standard deviation of the per-step times (ms)."""
+    v = list(ms_list)
+    return {"median": statistics.median(v), "min": min(v), "sd": statistics.pstdev(v) if len(v) > 1 else 0.0}
+
+
 def _spatial_model(case, ms_iter, schedule="auto"):
     """Fused/split spatial iteration: FP32-issue bound; flops per pixel and
     iteration = 3 tap sums (b, A, B) x 2 flops x nnz(h) + 60 pointwise."""
@@ -342,8 +348,8 @@ def run_ours(args, world, rank, local):
     roof = model(case, ms_iter / iters, args.schedule)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": ms, "ms_stats": step_stats(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "H": H, "W": W, "iters": iters, "psf": list(case.h.shape),
                    "psf_nnz": int((case.h != 0).sum()), "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
