@@ -427,191 +427,9 @@ __device__ __forceinline__ void load_row_taps(float* taps, const AdjImage& im) {
 #define ADJ_ROW_ITEMS(nr, W)                                                                       \
   for (int it = threadIdx.x; it < (nr) * (W); it += blockDim.x)
 
-// b = C u and q = (W f/b, W)
-__global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_q_rows(const float* __restrict__ u,
-                                                                 const float* __restrict__ f0, AdjImage im,
-                                                                 float* __restrict__ b_out,
-                                                                 float2* __restrict__ q_out) {
-  extern __shared__ __align__(16) unsigned char adj_sm[];
-  __shared__ float taps[kAdjRowTaps];
-  float* su = (float*)adj_sm;
-  const int kw = im.kw, cx = kw >> 1, W = im.W, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
-  load_row_taps(taps, im);
-  ADJ_ROW_BLOCKS(rows) {
-    const int nr = min(kAdjRowBlock, rows - R0);
-    __syncthreads();
-    stage_rows<float, true>(su, u, R0, nr, W);
-    __syncthreads();
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float* sr = su + r * L + kAdjRowPad;
-      float b = 0.f;
-      for (int c = 0; c < kw; ++c) {
-        const float w = taps[c];
-        if (w != 0.f) b = fmaf(w, sr[j - (c - cx)], b);
-      }
-      const size_t idx = (size_t)R0 * W + it;
-      const float fv = f0[idx];
-      float rr;
-      const float w = phi_w(b, fv, im.p, &rr);
-      b_out[idx] = b;
-      q_out[idx] = make_float2(w * fv / b, w);
-    }
-  }
-}
 
-// A, B = C' q;  g = psi'(|grad u|^2)
-__global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_ab_rows(const float* __restrict__ u,
-                                                                  const float2* __restrict__ q, AdjImage im,
-                                                                  float2* __restrict__ ab_out,
-                                                                  float* __restrict__ g_out) {
-  extern __shared__ __align__(16) unsigned char adj_sm[];
-  __shared__ float taps[kAdjRowTaps];
-  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
-  float2* sq = (float2*)adj_sm;
-  float* su = (float*)(sq + kAdjRowBlock * L);
-  load_row_taps(taps, im);
-  ADJ_ROW_BLOCKS(rows) {
-    const int nr = min(kAdjRowBlock, rows - R0);
-    __syncthreads();
-    stage_rows<float2, true>(sq, q, R0, nr, W);
-    stage_rows<float, true>(su, u, R0, nr, W);
-    __syncthreads();
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float2* qr = sq + r * L + kAdjRowPad;
-      const float* ur = su + r * L + kAdjRowPad;
-      float A = 0.f, B = 0.f;
-      for (int c = 0; c < kw; ++c) {
-        const float w = taps[c];
-        if (w != 0.f) {
-          const float2 v = qr[j + (c - cx)];
-          A = fmaf(w, v.x, A);
-          B = fmaf(w, v.y, B);
-        }
-      }
-      const int R = R0 + r, n = R / H, i = R - n * H;
-      const float* img = u + (size_t)n * H * W;
-      const size_t idx = (size_t)R * W + j;
-      ab_out[idx] = make_float2(A, B);
-      const float gx = 0.5f * (ur[j + 1] - ur[j - 1]);
-      const float gy = 0.5f * (img[(size_t)clampi(i + 1, H) * W + j] - img[(size_t)clampi(i - 1, H) * W + j]);
-      g_out[idx] = psi_g(gx, gy, im.p);
-    }
-  }
-}
 
-// qbar = C'^T (Abar, Bbar);  tap partials of Abar q1(clip(j+d)) + Bbar q2(clip(j+d))
-__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_corrT_rows(const float2* __restrict__ abbar,
-                                                                     const float2* __restrict__ q, AdjImage im,
-                                                                     float2* __restrict__ qbar,
-                                                                     float* __restrict__ tap_partial) {
-  extern __shared__ __align__(16) unsigned char adj_sm[];
-  __shared__ float taps[kAdjRowTaps];
-  const int kw = im.kw, cx = kw >> 1, W = im.W, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
-  float2* sa = (float2*)adj_sm;
-  float2* sq = sa + kAdjRowBlock * L;
-  load_row_taps(taps, im);
-  float acc[kAdjRowTaps];
-#pragma unroll
-  for (int t = 0; t < kAdjRowTaps; ++t) acc[t] = 0.f;
-  ADJ_ROW_BLOCKS(rows) {
-    const int nr = min(kAdjRowBlock, rows - R0);
-    __syncthreads();
-    stage_rows<float2, false>(sa, abbar, R0, nr, W);
-    stage_rows<float2, true>(sq, q, R0, nr, W);
-    __syncthreads();
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float2* ar = sa + r * L + kAdjRowPad;
-      const float2* qr = sq + r * L + kAdjRowPad;
-      float s1 = 0.f, s2 = 0.f;
-      if (j > 0 && j < W - 1) {
-        for (int c = 0; c < kw; ++c) {
-          const float w = taps[c];
-          const float2 v = ar[j - (c - cx)];
-          s1 = fmaf(w, v.x, s1);
-          s2 = fmaf(w, v.y, s2);
-        }
-      } else {
-        for (int c = 0; c < kw; ++c) {
-          int lo, hi;
-          preimage(j, c - cx, W, &lo, &hi);
-          float z1 = 0.f, z2 = 0.f;
-          for (int jj = lo; jj <= hi; ++jj) {
-            const float2 v = ar[jj];
-            z1 += v.x;
-            z2 += v.y;
-          }
-          s1 = fmaf(taps[c], z1, s1);
-          s2 = fmaf(taps[c], z2, s2);
-        }
-      }
-      qbar[(size_t)R0 * W + it] = make_float2(s1, s2);
-      const float2 v = ar[j];
-#pragma unroll
-      for (int t = 0; t < kAdjRowTaps; ++t) {
-        if (t < kw) {
-          const float2 qq = qr[j + t - cx];
-          acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
-        }
-      }
-    }
-  }
-  // (static indices keep acc in registers; kw is uniform, so every thread
-  // takes the same branches to the barriers inside)
-#pragma unroll
-  for (int t = 0; t < kAdjRowTaps; ++t)
-    if (t < kw) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
-}
 
-// U += C^T bbar;  tap partials of bbar(j) u(clip(j-d))
-__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_convT_rows(const float* __restrict__ bbar,
-                                                                     const float* __restrict__ u, AdjImage im,
-                                                                     float* __restrict__ Uacc,
-                                                                     float* __restrict__ tap_partial) {
-  extern __shared__ __align__(16) unsigned char adj_sm[];
-  __shared__ float taps[kAdjRowTaps];
-  const int kw = im.kw, cx = kw >> 1, W = im.W, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
-  float* sb = (float*)adj_sm;
-  float* su = sb + kAdjRowBlock * L;
-  load_row_taps(taps, im);
-  float acc[kAdjRowTaps];
-#pragma unroll
-  for (int t = 0; t < kAdjRowTaps; ++t) acc[t] = 0.f;
-  ADJ_ROW_BLOCKS(rows) {
-    const int nr = min(kAdjRowBlock, rows - R0);
-    __syncthreads();
-    stage_rows<float, false>(sb, bbar, R0, nr, W);
-    stage_rows<float, true>(su, u, R0, nr, W);
-    __syncthreads();
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float* br = sb + r * L + kAdjRowPad;
-      const float* ur = su + r * L + kAdjRowPad;
-      float sacc = 0.f;
-      if (j > 0 && j < W - 1) {
-        for (int c = 0; c < kw; ++c) sacc = fmaf(taps[c], br[j + (c - cx)], sacc);
-      } else {
-        for (int c = 0; c < kw; ++c) {
-          int lo, hi;
-          preimage(j, -(c - cx), W, &lo, &hi);
-          float z = 0.f;
-          for (int jj = lo; jj <= hi; ++jj) z += br[jj];
-          sacc = fmaf(taps[c], z, sacc);
-        }
-      }
-      Uacc[(size_t)R0 * W + it] += sacc;
-      const float bv = br[j];
-#pragma unroll
-      for (int t = 0; t < kAdjRowTaps; ++t)
-        if (t < kw) acc[t] = fmaf(bv, ur[j - (t - cx)], acc[t]);
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < kAdjRowTaps; ++t)
-    if (t < kw) block_reduce_add(tap_partial + (size_t)t * gridDim.x + blockIdx.x, acc[t]);
-}
 
 // Forward recompute of one iteration for one-row PSFs, fused: b = C u and
 // q = (W f/b, W) into a shared row, then A, B = C' q and g from it.
@@ -1076,20 +894,13 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const int G = kAdjBlocks, T = kAdjThreads;
   // row kernels (kw <= kAdjRowTaps): shared memory of the staged rows
   const size_t rowlen = ((size_t)W + 2 * kAdjRowPad) * kAdjRowBlock;
-  const size_t smq = rowlen * 4, smab = rowlen * 12, smct = rowlen * 16, smcv = rowlen * 8, smrev = rowlen * 24;
+  const size_t smab = rowlen * 12, smrev = rowlen * 24;
   const bool rowk = kw <= kAdjRowTaps && smrev <= 227 * 1024;
-  (void)smq; (void)smct; (void)smcv;
   if (rowk) {
     if (smrev > 48 * 1024)
       ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smrev));
     if (smab > 48 * 1024)
       ADJ_CHECK(cudaFuncSetAttribute(k_adj_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
-    if (smab > 48 * 1024)
-      ADJ_CHECK(cudaFuncSetAttribute(k_adj_fwd_ab_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
-    if (smct > 48 * 1024)
-      ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_corrT_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smct));
-    if (smcv > 48 * 1024)
-      ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_convT_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smcv));
   }
 
   // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)

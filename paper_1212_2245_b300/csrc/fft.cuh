@@ -12,7 +12,8 @@
 //
 // Pairs of radix-2 stages are fused into one radix-2^2 butterfly held in
 // registers, halving the shared-memory sweeps.  Twiddles come from a table
-// tw[k] = exp(-2 pi i k / NT) computed once per call in double precision.
+// tw[k] = exp(-2 pi i k / NT) in global memory (computed once per call in
+// double precision), read through the read-only cache.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -33,13 +34,6 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
 // multiply by +i
 __device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a.x); }
-
-// Twiddle table tw[k] = exp(-2 pi i k / NT), k in [0, NT), computed once per
-// call in double precision and rounded once to float (see k_twiddles), then
-// copied into shared memory by each CTA with asynchronous copies.
-__device__ inline void fft_load_twiddles(float2* tw, const float2* __restrict__ g, int NT) {
-  for (int k = threadIdx.x; k < NT; k += blockDim.x) cp_async8(tw + k, g + k);
-}
 
 // Forward DIF transform of `nseq` sequences of length N = 2^logN held in
 // shared memory: element k of sequence q is x[q*ss + k*es].  Output is in
@@ -63,7 +57,7 @@ __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, co
       float2* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
       float2 x0 = p[0], x1 = p[sm], x2 = p[2 * sm], x3 = p[3 * sm];
-      const float2 w1 = tw[j * tstep], w2 = tw[2 * j * tstep];
+      const float2 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
       float2 y0 = cadd(x0, x2), y2 = cmul(csub(x0, x2), w1);
       float2 y1 = cadd(x1, x3), y3 = cmul_mi(cmul(csub(x1, x3), w1));
       p[0] = cadd(y0, y1);
@@ -119,7 +113,7 @@ __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss
       float2* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
       float2 z0 = p[0], z1 = p[sm], z2 = p[2 * sm], z3 = p[3 * sm];
-      const float2 w1 = tw[j * tstep], w2 = tw[2 * j * tstep];
+      const float2 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
       float2 t1 = cmulc(z1, w2), t3 = cmulc(z3, w2);
       float2 y0 = cadd(z0, t1), y1 = csub(z0, t1);
       float2 y2 = cadd(z2, t3), y3 = csub(z2, t3);

@@ -58,10 +58,9 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
   extern __shared__ float2 smem[];
   const int W = a.W;
-  float2* tw = smem;
-  float2* x = smem + W;
+  const float2* tw = a.twW;
+  float2* x = smem;
   float* rs = (float*)(x + W);  // real rows: FR_U/FR_MID one row, FR_FIN rows i-2..i+2 of u
-  fft_load_twiddles(tw, a.twW, W);
   const int i = blockIdx.x;
   if (MODE == FR_U) {
     for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async4(rs + c, a.uin + (size_t)i * a.ldin + c);
@@ -136,9 +135,8 @@ template <bool CONJ, int C>
 __global__ void __launch_bounds__(256) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
                                                       const float2* __restrict__ twH, int H, int W, int logH) {
   extern __shared__ float2 smem[];
-  float2* tw = smem;
-  float2* x = smem + H;
-  fft_load_twiddles(tw, twH, H);
+  const float2* tw = twH;
+  float2* x = smem;
   const int c0 = blockIdx.x * C;
   for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
@@ -172,7 +170,7 @@ static cudaError_t set_smem_f(K kern, size_t smem) {
 
 template <int MODE>
 static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)2 * a.W * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
+  const size_t smem = (size_t)a.W * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
   cudaError_t e = set_smem_f(k_fourier_rows<MODE>, smem);
   if (e != cudaSuccess) return e;
   k_fourier_rows<MODE><<<a.H, 256, smem, s>>>(a);
@@ -185,13 +183,13 @@ static cudaError_t launch_fcol(float2* buf, const float2* S, const float2* twH, 
   const int logH = ilog2(H);
   if (H <= 2048) {
     constexpr int C = 4;
-    const size_t smem = (size_t)(H + C * H) * sizeof(float2);
+    const size_t smem = (size_t)C * H * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
     if (e != cudaSuccess) return e;
     k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, twH, H, W, logH);
   } else {
     constexpr int C = 2;
-    const size_t smem = (size_t)(H + C * H) * sizeof(float2);
+    const size_t smem = (size_t)C * H * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
     if (e != cudaSuccess) return e;
     k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, twH, H, W, logH);
