@@ -4,9 +4,9 @@
 //
 // The work is the task list  (k, phase, tile)  for k = 0..iters-1, phase 0
 // (q = (e, W) of a tile from u^k) and phase 1 (the update of a tile from q
-// and u^k, writing u^{k+1}), dispensed in that order from an atomic counter
-// to co-resident CTAs (cooperative launch).  A task waits only for the tiles
-// whose output it reads:
+// and u^k, writing u^{k+1}), numbered in that order and dealt round-robin to
+// co-resident CTAs (cooperative launch): CTA c runs tasks c, c + G, c + 2G,
+// ... in order.  A task waits only for the tiles whose output it reads:
 //   q_k(T)      needs u^k     on T's blur footprint:  update_{k-1} done there
 //   update_k(T) needs q_k     on T's correlation footprint
 // Both footprints lie within ry tile rows and rx tile columns of T, with the
@@ -17,9 +17,10 @@
 // update_k(T) overwrites held u^{k-1}; its readers near T (q_{k-1} and
 // update_{k-1} within one radius) finished before the q_k tiles that
 // update_k(T) waited for could start, so write-after-read needs no extra
-// wait, and likewise for the q buffer.  Every task waits only for tasks
-// dispensed before it, all held by resident CTAs, so the run cannot
-// deadlock; each wait is bounded all the same (time-out: DB_FLAG_TIMEOUT,
+// wait, and likewise for the q buffer.  Every task waits only for tasks of
+// lower number; the lowest unfinished task belongs to a resident CTA that has
+// finished all its earlier (lower) tasks, so it runs and the run cannot
+// deadlock.  Each wait is bounded all the same (time-out: DB_FLAG_TIMEOUT,
 // the run aborts its waits and finishes).
 #include <cuda_runtime.h>
 
@@ -40,7 +41,6 @@ struct FlowArgs {
   RrlParams p;
   int tx, ty, rx, ry;       // tile grid and dependency radius (tiles)
   int iters;
-  int* next;                // task counter
   int* abort_;              // set on a time-out: later waits are skipped
   int* done_q; int* done_u; // per-tile counters: iterations completed
   int* status;
@@ -72,16 +72,11 @@ __device__ bool flow_wait(const FlowArgs& a, const int* cnt, int bi, int bj, int
 template <int M, int P>
 __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_task;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int ntiles = a.tx * a.ty;
   const int total = a.iters * 2 * ntiles;
-  while (true) {
-    if (tid == 0) s_task = atomicAdd(a.next, 1);
-    __syncthreads();
-    const int t = s_task;
-    __syncthreads();
-    if (t >= total) break;
+  // tasks are dealt round-robin: CTA c runs c, c + G, c + 2G, ... in order
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int k = t / (2 * ntiles), rem = t - k * 2 * ntiles;
     const int phase = rem >= ntiles ? 1 : 0, T = rem - phase * ntiles;
     const int bi = T / a.tx, bj = T - bi * a.tx;
@@ -193,7 +188,7 @@ cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* u
   a.ry = (hy + kFTH - 1) / kFTH; a.rx = (hx + kFTW - 1) / kFTW;
   a.iters = iters;
   int* w = (int*)flow_ws;
-  a.next = w; a.abort_ = w + 1;
+  a.abort_ = w;
   a.done_q = w + 64; a.done_u = w + 64 + a.tx * a.ty;
   a.status = status;
   a.spin_limit = g_flow_spin;
