@@ -50,6 +50,23 @@ __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, co
     const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
     const int tstep = 1 << (logN - logLen + tw_shift);  // NT / len
     const int items = nseq * nb;
+    if (m == 1) {  // blocks of 4: every twiddle is 1
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        int q, b;
+        if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+        float2* p = x + q * ss + (b * 4) * es;
+        float2 x0 = p[0], x1 = p[es], x2 = p[2 * es], x3 = p[3 * es];
+        float2 y0 = cadd(x0, x2), y2 = csub(x0, x2);
+        float2 y1 = cadd(x1, x3), y3 = cmul_mi(csub(x1, x3));
+        p[0] = cadd(y0, y1);
+        p[es] = csub(y0, y1);
+        p[2 * es] = cadd(y2, y3);
+        p[3 * es] = csub(y2, y3);
+      }
+      __syncthreads();
+      logLen -= 2;
+      continue;
+    }
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int q, b;
       if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
@@ -106,6 +123,22 @@ __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss
     const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
     const int tstep = 1 << (logN - logLen + tw_shift);
     const int items = nseq * nb;
+    if (m == 1) {  // blocks of 4: every twiddle is 1
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        int q, b;
+        if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+        float2* p = x + q * ss + (b * 4) * es;
+        float2 z0 = p[0], z1 = p[es], z2 = p[2 * es], z3 = p[3 * es];
+        float2 y0 = cadd(z0, z1), y1 = csub(z0, z1);
+        float2 y2 = cadd(z2, z3), u3 = cmul_pi(csub(z2, z3));
+        p[0] = cadd(y0, y2);
+        p[2 * es] = csub(y0, y2);
+        p[es] = cadd(y1, u3);
+        p[3 * es] = csub(y1, u3);
+      }
+      __syncthreads();
+      continue;
+    }
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int q, b;
       if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }

@@ -99,6 +99,23 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
   while (logLen >= 2) {
     const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
     const int tstep = 1 << (logN - logLen);
+    if (m == 1) {  // blocks of 4: every twiddle is 1
+      for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
+        int q, b;
+        seq_item_ff(it, nseq, nb, seq_fast, q, b);
+        float4* p = x + q * ss + (b * 4) * es;
+        const float4 x0 = p[0], x1 = p[es], x2 = p[2 * es], x3 = p[3 * es];
+        const float4 y0 = zadd(x0, x2), y2 = zsub(x0, x2);
+        const float4 y1 = zadd(x1, x3), y3 = zmul_mi(zsub(x1, x3));
+        p[0] = zadd(y0, y1);
+        p[es] = zsub(y0, y1);
+        p[2 * es] = zadd(y2, y3);
+        p[3 * es] = zsub(y2, y3);
+      }
+      __syncthreads();
+      logLen -= 2;
+      continue;
+    }
     for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
       int q, b;
       seq_item_ff(it, nseq, nb, seq_fast, q, b);
@@ -150,6 +167,22 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
   for (logLen += 2; logLen <= logN; logLen += 2) {
     const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
     const int tstep = 1 << (logN - logLen);
+    if (m == 1) {  // blocks of 4: every twiddle is 1
+      for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
+        int q, b;
+        seq_item_ff(it, nseq, nb, seq_fast, q, b);
+        float4* p = x + q * ss + (b * 4) * es;
+        const float4 z0 = p[0], z1 = p[es], z2 = p[2 * es], z3 = p[3 * es];
+        const float4 y0 = zadd(z0, z1), y1 = zsub(z0, z1);
+        const float4 y2 = zadd(z2, z3), u3 = zmul_pi(zsub(z2, z3));
+        p[0] = zadd(y0, y2);
+        p[2 * es] = zsub(y0, y2);
+        p[es] = zadd(y1, u3);
+        p[3 * es] = zsub(y1, u3);
+      }
+      __syncthreads();
+      continue;
+    }
     for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
       int q, b;
       seq_item_ff(it, nseq, nb, seq_fast, q, b);
