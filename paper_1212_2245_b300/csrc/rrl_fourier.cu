@@ -181,7 +181,7 @@ static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
 template <bool CONJ>
 static cudaError_t launch_fcol(float2* buf, const float2* S, const float2* twH, int H, int W, cudaStream_t s) {
   const int logH = ilog2(H);
-  if (H <= 2048) {
+  if (H <= 1024) {
     constexpr int C = 4;
     const size_t smem = (size_t)C * H * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
