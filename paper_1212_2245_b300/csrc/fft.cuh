@@ -35,6 +35,13 @@ __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a
 // multiply by +i
 __device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a.x); }
 
+// Work item -> (sequence q, item b) with shifts: nseq = 2^lns sequences of
+// 2^lnb items each (both powers of two in every sweep below).
+__device__ __forceinline__ void split_item(int it, int lns, int lnb, bool seq_fast, int& q, int& b) {
+  if (seq_fast) { q = it & ((1 << lns) - 1); b = it >> lns; }
+  else { q = it >> lnb; b = it & ((1 << lnb) - 1); }
+}
+
 // Forward DIF transform of `nseq` sequences of length N = 2^logN held in
 // shared memory: element k of sequence q is x[q*ss + k*es].  Output is in
 // bit-reversed order.  `seq_fast` chooses the thread->work mapping: true when
@@ -43,7 +50,7 @@ __device__ __forceinline__ float2 cmul_pi(float2 a) { return make_float2(-a.y, a
 // Ends with __syncthreads().
 __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, const float2* tw,
                                int tw_shift, bool seq_fast) {
-  const int N = 1 << logN;
+  const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
   const int nb = N >> 2;  // radix-4 butterflies per sequence
   int logLen = logN;
   while (logLen >= 2) {
@@ -53,7 +60,7 @@ __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, co
     if (m == 1) {  // blocks of 4: every twiddle is 1
       for (int it = threadIdx.x; it < items; it += blockDim.x) {
         int q, b;
-        if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+        split_item(it, lns, logN - 2, seq_fast, q, b);
         float2* p = x + q * ss + (b * 4) * es;
         float2 x0 = p[0], x1 = p[es], x2 = p[2 * es], x3 = p[3 * es];
         float2 y0 = cadd(x0, x2), y2 = csub(x0, x2);
@@ -69,7 +76,7 @@ __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, co
     }
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int q, b;
-      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+      split_item(it, lns, logN - 2, seq_fast, q, b);
       const int blk = b >> logm, j = b & (m - 1);
       float2* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
@@ -89,7 +96,7 @@ __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, co
     const int items = nseq * (N >> 1);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int q, b;
-      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / (N >> 1); b = it - q * (N >> 1); }
+      split_item(it, lns, logN - 1, seq_fast, q, b);
       float2* p = x + q * ss + (2 * b) * es;
       float2 a = p[0], c = p[es];
       p[0] = cadd(a, c);
@@ -104,14 +111,14 @@ __device__ inline void fft_dif(float2* x, int logN, int nseq, int es, int ss, co
 // Ends with __syncthreads().
 __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss, const float2* tw,
                                    int tw_shift, bool seq_fast) {
-  const int N = 1 << logN;
+  const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
   const int nb = N >> 2;
   int logLen = (logN & 1) ? 1 : 0;
   if (logLen == 1) {
     const int items = nseq * (N >> 1);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int q, b;
-      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / (N >> 1); b = it - q * (N >> 1); }
+      split_item(it, lns, logN - 1, seq_fast, q, b);
       float2* p = x + q * ss + (2 * b) * es;
       float2 a = p[0], c = p[es];
       p[0] = cadd(a, c);
@@ -126,7 +133,7 @@ __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss
     if (m == 1) {  // blocks of 4: every twiddle is 1
       for (int it = threadIdx.x; it < items; it += blockDim.x) {
         int q, b;
-        if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+        split_item(it, lns, logN - 2, seq_fast, q, b);
         float2* p = x + q * ss + (b * 4) * es;
         float2 z0 = p[0], z1 = p[es], z2 = p[2 * es], z3 = p[3 * es];
         float2 y0 = cadd(z0, z1), y1 = csub(z0, z1);
@@ -141,7 +148,7 @@ __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss
     }
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       int q, b;
-      if (seq_fast) { q = it % nseq; b = it / nseq; } else { q = it / nb; b = it - q * nb; }
+      split_item(it, lns, logN - 2, seq_fast, q, b);
       const int blk = b >> logm, j = b & (m - 1);
       float2* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;

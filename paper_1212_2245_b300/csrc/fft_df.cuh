@@ -89,11 +89,16 @@ struct WienerState {
 __device__ __forceinline__ void seq_item_ff(int it, int nseq, int len, bool seq_fast, int& q, int& k) {
   if (seq_fast) { q = it % nseq; k = it / nseq; } else { q = it / len; k = it - q * len; }
 }
+// The same with shifts: nseq = 2^lns sequences of 2^lnb items each.
+__device__ __forceinline__ void split_item_ff(int it, int lns, int lnb, bool seq_fast, int& q, int& b) {
+  if (seq_fast) { q = it & ((1 << lns) - 1); b = it >> lns; }
+  else { q = it >> lnb; b = it & ((1 << lnb) - 1); }
+}
 
 // Forward DIF sweep (output bit-reversed); see fft_dif.  Ends with a barrier.
 __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss, const float4* __restrict__ tw,
                                   bool seq_fast) {
-  const int N = 1 << logN;
+  const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
   const int nb = N >> 2;
   int logLen = logN;
   while (logLen >= 2) {
@@ -102,7 +107,7 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
     if (m == 1) {  // blocks of 4: every twiddle is 1
       for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
         int q, b;
-        seq_item_ff(it, nseq, nb, seq_fast, q, b);
+        split_item_ff(it, lns, logN - 2, seq_fast, q, b);
         float4* p = x + q * ss + (b * 4) * es;
         const float4 x0 = p[0], x1 = p[es], x2 = p[2 * es], x3 = p[3 * es];
         const float4 y0 = zadd(x0, x2), y2 = zsub(x0, x2);
@@ -118,7 +123,7 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
     }
     for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
       int q, b;
-      seq_item_ff(it, nseq, nb, seq_fast, q, b);
+      split_item_ff(it, lns, logN - 2, seq_fast, q, b);
       const int blk = b >> logm, j = b & (m - 1);
       float4* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
@@ -137,7 +142,7 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
   if (logLen == 1) {
     for (int it = threadIdx.x; it < nseq * (N >> 1); it += blockDim.x) {
       int q, b;
-      seq_item_ff(it, nseq, N >> 1, seq_fast, q, b);
+      split_item_ff(it, lns, logN - 1, seq_fast, q, b);
       float4* p = x + q * ss + (2 * b) * es;
       const float4 a = p[0], c = p[es];
       p[0] = zadd(a, c);
@@ -150,13 +155,13 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
 // Inverse DIT sweep (unnormalised), mirror of fft_dif_ff.  Ends with a barrier.
 __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int ss,
                                       const float4* __restrict__ tw, bool seq_fast) {
-  const int N = 1 << logN;
+  const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
   const int nb = N >> 2;
   int logLen = (logN & 1) ? 1 : 0;
   if (logLen == 1) {
     for (int it = threadIdx.x; it < nseq * (N >> 1); it += blockDim.x) {
       int q, b;
-      seq_item_ff(it, nseq, N >> 1, seq_fast, q, b);
+      split_item_ff(it, lns, logN - 1, seq_fast, q, b);
       float4* p = x + q * ss + (2 * b) * es;
       const float4 a = p[0], c = p[es];
       p[0] = zadd(a, c);
@@ -170,7 +175,7 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
     if (m == 1) {  // blocks of 4: every twiddle is 1
       for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
         int q, b;
-        seq_item_ff(it, nseq, nb, seq_fast, q, b);
+        split_item_ff(it, lns, logN - 2, seq_fast, q, b);
         float4* p = x + q * ss + (b * 4) * es;
         const float4 z0 = p[0], z1 = p[es], z2 = p[2 * es], z3 = p[3 * es];
         const float4 y0 = zadd(z0, z1), y1 = zsub(z0, z1);
@@ -185,7 +190,7 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
     }
     for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
       int q, b;
-      seq_item_ff(it, nseq, nb, seq_fast, q, b);
+      split_item_ff(it, lns, logN - 2, seq_fast, q, b);
       const int blk = b >> logm, j = b & (m - 1);
       float4* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
