@@ -167,6 +167,108 @@ __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked form of the same transforms.  The radix-2 stages are taken
+// in blocks of up to four: a work item loads the 2^NB elements whose indices
+// differ only in the block's bits, runs the block's stages in registers and
+// stores them back, so a length-2048 transform makes three shared-memory
+// sweeps.  Each stage is the plain radix-2 DIF butterfly
+//   a' = a + c,  c' = (a - c) w^e,  e = (i mod h) 2^s   (stage s, span h),
+// and the inverse runs the mirrored butterflies a + c conj(w^e), a - c conj(w^e)
+// in the reverse stage order (unnormalised inverse): storage orders are those
+// of fft_dif / fft_dit_inv (bit-reversed spectra).
+//
+// Shared layout: element k of a sequence sits at fft_pad(k) = k + k/16 (one
+// gap every 16 elements), so the strided loads of every block spread over
+// the banks.  A sequence of length N needs fft_padded(N) slots.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int fft_pad(int k) { return k + (k >> 4); }
+__host__ __device__ __forceinline__ int fft_padded(int n) { return n + (n >> 4); }
+
+template <int NB, bool INV>
+__device__ __forceinline__ void fft_block(float2* x, int logN, int hb, int nseq, int es, int ss,
+                                          const float2* __restrict__ tw, bool seq_fast) {
+  constexpr int R = 1 << NB;
+  const int lo = hb - NB + 1, lowmask = (1 << lo) - 1;
+  const int lns = 31 - __clz(nseq), lng = logN - NB;
+  const int items = nseq << lng;
+  const int s0 = logN - 1 - hb;  // stage of the block's top bit
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    int q, g;
+    split_item(it, lns, lng, seq_fast, q, g);
+    const int base = ((g >> lo) << (hb + 1)) | (g & lowmask);
+    float2* p = x + q * ss;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = p[fft_pad(base + (r << lo)) * es];
+    const int bl = base & lowmask;
+    if (!INV) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const int rb = NB - 1 - k, s = s0 + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r & (1 << rb)) continue;
+          const float2 a = v[r], c = v[r + (1 << rb)];
+          const int e = (bl + ((r & ((1 << rb) - 1)) << lo)) << s;
+          v[r] = cadd(a, c);
+          v[r + (1 << rb)] = cmul(csub(a, c), __ldg(tw + e));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = NB - 1; k >= 0; --k) {
+        const int rb = NB - 1 - k, s = s0 + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r & (1 << rb)) continue;
+          const float2 a = v[r];
+          const int e = (bl + ((r & ((1 << rb) - 1)) << lo)) << s;
+          const float2 t = cmulc(v[r + (1 << rb)], __ldg(tw + e));
+          v[r] = cadd(a, t);
+          v[r + (1 << rb)] = csub(a, t);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[fft_pad(base + (r << lo)) * es] = v[r];
+  }
+  __syncthreads();
+}
+
+// Forward DIF (output bit-reversed) on the padded layout: element k of
+// sequence q at x[q*ss + fft_pad(k)*es].  nseq: a power of two.  Ends with a
+// barrier.
+__device__ inline void fft_dif_blk(float2* x, int logN, int nseq, int es, int ss, const float2* __restrict__ tw,
+                                   bool seq_fast) {
+  for (int hb = logN - 1; hb >= 0;) {
+    const int nb = hb + 1 < 4 ? hb + 1 : 4;
+    switch (nb) {
+      case 4: fft_block<4, false>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+      case 3: fft_block<3, false>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+      case 2: fft_block<2, false>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+      default: fft_block<1, false>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+    }
+    hb -= nb;
+  }
+}
+
+// Inverse (unnormalised) from bit-reversed to natural order, padded layout.
+__device__ inline void fft_dit_inv_blk(float2* x, int logN, int nseq, int es, int ss,
+                                       const float2* __restrict__ tw, bool seq_fast) {
+  for (int lo = 0; lo < logN;) {
+    const int nb = logN - lo < 4 ? logN - lo : 4;
+    const int hb = lo + nb - 1;
+    switch (nb) {
+      case 4: fft_block<4, true>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+      case 3: fft_block<3, true>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+      case 2: fft_block<2, true>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+      default: fft_block<1, true>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
+    }
+    lo += nb;
+  }
+}
+
 // Thread -> (sequence q, element k) mapping shared by the routines below.
 __device__ __forceinline__ void seq_item(int it, int nseq, int len, bool seq_fast, int& q, int& k) {
   if (seq_fast) { q = it % nseq; k = it / nseq; } else { q = it / len; k = it - q * len; }

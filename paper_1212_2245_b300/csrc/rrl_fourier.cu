@@ -55,22 +55,22 @@ __device__ __forceinline__ float diffusivity_f(float gx, float gy, const RrlPara
 // One row of length W per CTA.  Every global input is staged with
 // asynchronous copies before the transform.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
+__global__ void __launch_bounds__(256, 3) k_fourier_rows(FourierArgs a) {
   extern __shared__ float2 smem[];
   const int W = a.W;
   const float2* tw = a.twW;
-  float2* x = smem;
-  float* rs = (float*)(x + W);  // real rows: FR_U/FR_MID one row, FR_FIN rows i-2..i+2 of u
+  float2* x = smem;                            // padded layout: element c at x[fft_pad(c)]
+  float* rs = (float*)(x + fft_padded(W));     // real rows: FR_U/FR_MID one row, FR_FIN rows i-2..i+2 of u
   const int i = blockIdx.x;
   if (MODE == FR_U) {
     for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async4(rs + c, a.uin + (size_t)i * a.ldin + c);
   } else if (MODE == FR_MID) {
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
-      cp_async8(x + c, a.X + (size_t)i * W + c);
+      cp_async8(x + fft_pad(c), a.X + (size_t)i * W + c);
       cp_async4(rs + c, a.f + (size_t)i * a.ldf + c);
     }
   } else {
-    for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async8(x + c, a.Z + (size_t)i * W + c);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async8(x + fft_pad(c), a.Z + (size_t)i * W + c);
     for (int r = 0; r < 5; ++r) {
       const int gi = min(max(i - 2 + r, 0), a.H - 1);
       for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async4(rs + r * W + c, a.uin + (size_t)gi * a.ldin + c);
@@ -79,27 +79,27 @@ __global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
   cp_async_wait_all();
   __syncthreads();
   if (MODE == FR_U) {
-    for (int c = threadIdx.x; c < W; c += blockDim.x) x[c] = make_float2(rs[c], 0.f);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) x[fft_pad(c)] = make_float2(rs[c], 0.f);
     __syncthreads();
-    fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
-    for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[c];
+    fft_dif_blk(x, a.logW, 1, 1, 0, tw, false);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[fft_pad(c)];
     return;
   }
   if (MODE == FR_MID) {
-    fft_dit_inv(x, a.logW, 1, 1, W, tw, 0, false);
+    fft_dit_inv_blk(x, a.logW, 1, 1, 0, tw, false);
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
-      const float b = x[c].x * a.scale;
+      const float b = x[fft_pad(c)].x * a.scale;
       const float fv = fmaxf(rs[c], a.p.floor);
       const float w = robust_weight_f(b, fv, a.p);
-      x[c] = make_float2(__fdividef(w * (fv - b), b), w);
+      x[fft_pad(c)] = make_float2(__fdividef(w * (fv - b), b), w);
     }
     __syncthreads();
-    fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
-    for (int c = threadIdx.x; c < W; c += blockDim.x) a.Z[(size_t)i * W + c] = x[c];
+    fft_dif_blk(x, a.logW, 1, 1, 0, tw, false);
+    for (int c = threadIdx.x; c < W; c += blockDim.x) a.Z[(size_t)i * W + c] = x[fft_pad(c)];
     return;
   }
   // FR_FIN
-  fft_dit_inv(x, a.logW, 1, 1, W, tw, 0, false);
+  fft_dit_inv_blk(x, a.logW, 1, 1, 0, tw, false);
   const RrlParams& p = a.p;
   for (int c = threadIdx.x; c < W; c += blockDim.x) {
     const int cw = max(c - 1, 0), ce = min(c + 1, W - 1);
@@ -117,22 +117,24 @@ __global__ void __launch_bounds__(256) k_fourier_rows(FourierArgs a) {
     const float gn = diffusivity_f(0.5f * (n1[ce] - n1[cw]), 0.5f * (ctr - n2[c]), p);
     const float D = 0.5f * ((ge + gc) * (e - ctr) - (gc + gw) * (ctr - w_) + (gs + gc) * (s - ctr) -
                             (gc + gn) * (ctr - n));
-    const float dl = x[c].x * a.scale, B = x[c].y * a.scale;
+    const float2 xv = x[fft_pad(c)];
+    const float dl = xv.x * a.scale, B = xv.y * a.scale;
     const float den = B - p.alpha * fminf(D, 0.f);
     const float un = fmaf(ctr, __fdividef(fmaf(p.alpha, D, dl), den), ctr);
     if (!isfinite(un) && a.status) atomicOr(a.status, DB_FLAG_NONFINITE);
     a.uout[(size_t)i * a.ldout + c] = un;
-    x[c] = make_float2(un, 0.f);
+    x[fft_pad(c)] = make_float2(un, 0.f);
   }
   if (!a.write_next) return;
   __syncthreads();
-  fft_dif(x, a.logW, 1, 1, W, tw, 0, false);
-  for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[c];
+  fft_dif_blk(x, a.logW, 1, 1, 0, tw, false);
+  for (int c = threadIdx.x; c < W; c += blockDim.x) a.X[(size_t)i * W + c] = x[fft_pad(c)];
 }
 
 // C adjacent columns per CTA: DIF, multiply by S (or conj S), DIT, in place.
+// Shared layout: element k of column c at x[fft_pad(k) * C + c].
 template <bool CONJ, int C>
-__global__ void __launch_bounds__(256) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
+__global__ void __launch_bounds__(256, 3) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
                                                       const float2* __restrict__ twH, int H, int W, int logH) {
   extern __shared__ float2 smem[];
   const float2* tw = twH;
@@ -140,24 +142,26 @@ __global__ void __launch_bounds__(256) k_fourier_cols(float2* __restrict__ buf, 
   const int c0 = blockIdx.x * C;
   for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
-    if (c0 + c < W) cp_async8(x + idx, buf + (size_t)k * W + c0 + c);
-    else x[idx] = make_float2(0.f, 0.f);
+    float2* d = x + fft_pad(k) * C + c;
+    if (c0 + c < W) cp_async8(d, buf + (size_t)k * W + c0 + c);
+    else *d = make_float2(0.f, 0.f);
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_dif(x, logH, C, C, 1, tw, 0, true);
+  fft_dif_blk(x, logH, C, C, 1, tw, true);
   for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
     if (c0 + c < W) {
-      const float2 s = __ldg(S + (size_t)k * W + c0 + c);
-      x[idx] = CONJ ? cmulc(x[idx], s) : cmul(x[idx], s);
+      float2* d = x + fft_pad(k) * C + c;
+      const float2 sv = __ldg(S + (size_t)k * W + c0 + c);
+      *d = CONJ ? cmulc(*d, sv) : cmul(*d, sv);
     }
   }
   __syncthreads();
-  fft_dit_inv(x, logH, C, C, 1, tw, 0, true);
+  fft_dit_inv_blk(x, logH, C, C, 1, tw, true);
   for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
-    if (c0 + c < W) buf[(size_t)k * W + c0 + c] = x[idx];
+    if (c0 + c < W) buf[(size_t)k * W + c0 + c] = x[fft_pad(k) * C + c];
   }
 }
 
@@ -170,7 +174,7 @@ static cudaError_t set_smem_f(K kern, size_t smem) {
 
 template <int MODE>
 static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)a.W * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
+  const size_t smem = (size_t)fft_padded(a.W) * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
   cudaError_t e = set_smem_f(k_fourier_rows<MODE>, smem);
   if (e != cudaSuccess) return e;
   k_fourier_rows<MODE><<<a.H, 256, smem, s>>>(a);
@@ -183,13 +187,13 @@ static cudaError_t launch_fcol(float2* buf, const float2* S, const float2* twH, 
   const int logH = ilog2(H);
   if (H <= 1024) {
     constexpr int C = 4;
-    const size_t smem = (size_t)C * H * sizeof(float2);
+    const size_t smem = (size_t)C * fft_padded(H) * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
     if (e != cudaSuccess) return e;
     k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, twH, H, W, logH);
   } else {
     constexpr int C = 2;
-    const size_t smem = (size_t)C * H * sizeof(float2);
+    const size_t smem = (size_t)C * fft_padded(H) * sizeof(float2);
     cudaError_t e = set_smem_f(k_fourier_cols<CONJ, C>, smem);
     if (e != cudaSuccess) return e;
     k_fourier_cols<CONJ, C><<<(W + C - 1) / C, 256, smem, s>>>(buf, S, twH, H, W, logH);
