@@ -183,6 +183,7 @@ __device__ inline void fft_dit_inv(float2* x, int logN, int nseq, int es, int ss
 // the banks.  A sequence of length N needs fft_padded(N) slots.
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int fft_pad(int k) { return k + (k >> 4); }
+constexpr int kFftBlock = 3;  // stages per shared sweep (register block of 2^3 elements)
 __host__ __device__ __forceinline__ int fft_padded(int n) { return n + (n >> 4); }
 
 template <int NB, bool INV>
@@ -242,7 +243,7 @@ __device__ __forceinline__ void fft_block(float2* x, int logN, int hb, int nseq,
 __device__ inline void fft_dif_blk(float2* x, int logN, int nseq, int es, int ss, const float2* __restrict__ tw,
                                    bool seq_fast) {
   for (int hb = logN - 1; hb >= 0;) {
-    const int nb = hb + 1 < 4 ? hb + 1 : 4;
+    const int nb = hb + 1 < kFftBlock ? hb + 1 : kFftBlock;
     switch (nb) {
       case 4: fft_block<4, false>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
       case 3: fft_block<3, false>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;
@@ -257,7 +258,7 @@ __device__ inline void fft_dif_blk(float2* x, int logN, int nseq, int es, int ss
 __device__ inline void fft_dit_inv_blk(float2* x, int logN, int nseq, int es, int ss,
                                        const float2* __restrict__ tw, bool seq_fast) {
   for (int lo = 0; lo < logN;) {
-    const int nb = logN - lo < 4 ? logN - lo : 4;
+    const int nb = logN - lo < kFftBlock ? logN - lo : kFftBlock;
     const int hb = lo + nb - 1;
     switch (nb) {
       case 4: fft_block<4, true>(x, logN, hb, nseq, es, ss, tw, seq_fast); break;

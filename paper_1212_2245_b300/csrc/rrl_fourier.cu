@@ -55,7 +55,7 @@ __device__ __forceinline__ float diffusivity_f(float gx, float gy, const RrlPara
 // One row of length W per CTA.  Every global input is staged with
 // asynchronous copies before the transform.
 template <int MODE>
-__global__ void __launch_bounds__(256, 3) k_fourier_rows(FourierArgs a) {
+__global__ void __launch_bounds__(256, 4) k_fourier_rows(FourierArgs a) {
   extern __shared__ float2 smem[];
   const int W = a.W;
   const float2* tw = a.twW;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256, 3) k_fourier_rows(FourierArgs a) {
 // C adjacent columns per CTA: DIF, multiply by S (or conj S), DIT, in place.
 // Shared layout: element k of column c at x[fft_pad(k) * C + c].
 template <bool CONJ, int C>
-__global__ void __launch_bounds__(256, 3) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
+__global__ void __launch_bounds__(256, 4) k_fourier_cols(float2* __restrict__ buf, const float2* __restrict__ S,
                                                       const float2* __restrict__ twH, int H, int W, int logH) {
   extern __shared__ float2 smem[];
   const float2* tw = twH;
