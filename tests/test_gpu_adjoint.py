@@ -73,6 +73,9 @@ def test_backward_full_size_against_reverse_mode_and_fd(lib):
     alpha, K = p.alpha, p.K
     _, gf, gt, ga, gk = _gpu_grads(lib, fs, gs, h0, alpha, K, p, 15, 5)
     _, of, ot, oa, ok = _oracle_grads(fs, gs, h0, alpha, K, p, 15)
+    print(f"learn512 (2 images) gradient rel. errors: f {float((gf - of).abs().max() / of.abs().max()):.2e} "
+          f"taps {float((gt - ot).abs().max() / ot.abs().max()):.2e} alpha {abs(ga - oa) / abs(oa):.2e} "
+          f"K {abs(gk - ok) / abs(ok):.2e}")
     assert float((gf - of).abs().max()) <= REL * float(of.abs().max()), "grad f"
     assert float((gt - ot).abs().max()) <= REL * float(ot.abs().max()), "grad taps"
     assert abs(ga - oa) <= REL * abs(oa) and abs(gk - ok) <= REL * abs(ok)
