@@ -11,7 +11,7 @@ with no blocking or fusion: see `oracle.ops` for the citations and the
 readings taken where the paper is silent or its formulas are garbled.
 """
 from .ops import (  # noqa: F401
-    conv_clamp, corr_clamp, conv_periodic, corr_periodic, conv, corr,
+    conv_clamp, corr_clamp, conv_clamp_T, corr_clamp_T, conv_periodic, corr_periodic, conv, corr,
     box_running_sum_rows, box_running_sum_cols, box_ends_running_sum_rows, box_ends_running_sum_cols,
     psf_transfer, wiener, wiener_rows, wiener_cols,
     info_divergence, info_divergence_lut, r1, r1_lut, r1_lut_table, RF_LUT_N, RF_LUT_SMAX,

@@ -85,6 +85,33 @@ def corr_clamp(v, h):
     return out
 
 
+def conv_clamp_T(y, h):
+    """Exact transpose of conv_clamp: (C^T y)(j) = sum_d h(d) sum_{i: clip(i-d) = j} y(i),
+    by scatter-adding every term of the forward sum to the pixel it read."""
+    y, h = _t(y), _t(h)
+    H, W = y.shape
+    ri, cj = torch.arange(H), torch.arange(W)
+    out = torch.zeros_like(y)
+    for dy, dx, w in _offsets(h):
+        rows = (ri - dy).clamp(0, H - 1)
+        cols = (cj - dx).clamp(0, W - 1)
+        out.index_put_((rows[:, None].expand(H, W), cols[None, :].expand(H, W)), w * y, accumulate=True)
+    return out
+
+
+def corr_clamp_T(z, h):
+    """Exact transpose of corr_clamp: (C'^T z)(j) = sum_d h(d) sum_{i: clip(i+d) = j} z(i)."""
+    z, h = _t(z), _t(h)
+    H, W = z.shape
+    ri, cj = torch.arange(H), torch.arange(W)
+    out = torch.zeros_like(z)
+    for dy, dx, w in _offsets(h):
+        rows = (ri + dy).clamp(0, H - 1)
+        cols = (cj + dx).clamp(0, W - 1)
+        out.index_put_((rows[:, None].expand(H, W), cols[None, :].expand(H, W)), w * z, accumulate=True)
+    return out
+
+
 def conv_periodic(u, h):
     """(u*h)(i,j) = sum h[a,b] u((i-dy) mod H, (j-dx) mod W)."""
     u, h = _t(u), _t(h)

@@ -303,3 +303,26 @@ def test_box_full_pipeline_fractional(lib):
     u0_ref, u_ref = oracle.wr3l(f, h, p, 10)
     u = lib.deblur(cuda(f), cuda(h), p, 10, kind="box")
     assert_close(u, u_ref, "fractional box WR3L")
+
+
+@pytest.mark.parametrize("sched", ["split", "flow", "fused"])
+def test_nonfinite_values_raise_the_device_flag(lib, sched):
+    """A NaN in the iterate or an infinite grey value does not trap: it is
+    reported through the device status word (DB_FLAG_NONFINITE) and the call
+    raises on the host afterwards."""
+    h = synth.line_psf(9, 30.0, 10.0)
+    p = Params()
+    f, u0 = _iterate_case(64, 96, h, 2, p, seed=3)
+    lib.set_schedule(sched)
+    try:
+        u = cuda(u0)
+        u[10, 20] = float("nan")
+        with pytest.raises(lib.DeblurError, match="non-finite|nonfinite|NaN"):
+            lib.rrl_iterate(cuda(f), u, cuda(h), p, 2)
+        fi = cuda(f)
+        fi[5, 5] = float("inf")
+        with pytest.raises(lib.DeblurError, match="non-finite|nonfinite|NaN"):
+            lib.rrl_iterate(fi, cuda(u0), cuda(h), p, 2)
+    finally:
+        lib.set_schedule("auto")
+    assert torch.isfinite(lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 2)).all()

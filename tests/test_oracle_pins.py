@@ -426,3 +426,31 @@ def test_r1_lookup_table_pins():
     # r_f(s) = f r_1(s/f)
     s, f = torch.tensor([30.0, 80.0]), torch.tensor([40.0, 20.0])
     assert torch.allclose(oracle.info_divergence_lut(s, f), f.double() * oracle.r1_lut(s.double() / f.double()))
+
+
+
+@pytest.mark.parametrize("H,W,shape", [(7, 9, (1, 5)), (6, 11, (3, 4)), (1, 8, (1, 3)), (9, 2, (5, 1)), (5, 5, (5, 5))])
+def test_clamped_transposes_dot_product(H, W, shape):
+    """<C x, y> = <x, C^T y> and <C' x, y> = <x, C'^T y> for the clamped
+    (constant-continuation) convolution and correlation, whose transposes
+    differ from each other at the borders; and the transposes equal the
+    preimage form the reverse mode uses on rows: at an end pixel j of a row,
+    the sum over i with clip(i - d) = j."""
+    rng = np.random.default_rng(H * 31 + W)
+    h = rng.uniform(0.1, 1.0, shape)
+    x, y = rng.normal(size=(H, W)), rng.normal(size=(H, W))
+    lhs = float((oracle.conv_clamp(x, h) * torch.as_tensor(y)).sum())
+    rhs = float((torch.as_tensor(x) * oracle.conv_clamp_T(y, h)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    lhs = float((oracle.corr_clamp(x, h) * torch.as_tensor(y)).sum())
+    rhs = float((torch.as_tensor(x) * oracle.corr_clamp_T(y, h)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    if shape[0] == 1:  # row PSF: preimage sums along the row
+        cx = shape[1] // 2
+        ref = np.zeros((H, W))
+        for j in range(W):
+            for c in range(shape[1]):
+                d = c - cx
+                pre = [i for i in range(W) if min(max(i - d, 0), W - 1) == j]
+                ref[:, j] += h[0, c] * y[:, pre].sum(axis=1)
+        np.testing.assert_allclose(oracle.conv_clamp_T(y, h), ref, rtol=1e-12, atol=1e-12)
