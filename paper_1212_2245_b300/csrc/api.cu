@@ -18,7 +18,7 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n) {
   WsLayout L = {};
   size_t off = 0;
   L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
-  L.ntaps = off; off += 256;
+  L.ntaps = off; off += kAuxBytes;
   L.utmp = off;  off += align256((size_t)n * H * upitch(W) * sizeof(float));
   L.qbuf = off;  off += align256((size_t)n * H * qpitch(W) * sizeof(float2));
   size_t spec_elems, work_elems;
@@ -81,7 +81,8 @@ static RrlParams to_rrl(const db_params* p) {
 
 // Spatial-mode iterations with tap groups already prepared in the workspace.
 // ng_bound: the tap-group count when the caller knows it (0 otherwise).
-// kind: DB_PSF_BOX runs the sliding-window form of the split schedule.
+// kind: one-axis PSFs (a box, or kh == 1 or kw == 1) run the one-axis form of
+// the split schedule unless the flow or fused schedule is set explicitly.
 static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld, int kh, int kw, int kind,
                                  const RrlParams& rp, int iters, float* ckpt, int ckpt_every, void* ws,
                                  const WsLayout& L, int* dev_status, cudaStream_t s, int ng_bound = 0) {
@@ -97,12 +98,17 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   // (from about 512 tiles of 32 x 32 on, enough to keep every SM busy with
   // overlapping phases)
   int sched = g_schedule.load();
+  int axis = axis_mode(kind, kh, kw);
   if (sched == DB_SCHED_AUTO) {
     sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
     if (sched == DB_SCHED_SPLIT && (size_t)H * W >= (size_t)512 * 1024) sched = DB_SCHED_FLOW;
+    if (axis) sched = DB_SCHED_SPLIT;
   }
-  const int box = kind == DB_PSF_BOX;
-  if ((sched == DB_SCHED_FLOW && ckpt) || box) sched = DB_SCHED_SPLIT;
+  // the flow schedule writes no checkpoints: the split schedule stands in,
+  // with the same tap-group sums (bitwise equal to the flow result)
+  const bool flow_ckpt = sched == DB_SCHED_FLOW && ckpt;
+  if (flow_ckpt || axis == 1) sched = DB_SCHED_SPLIT;
+  if (sched != DB_SCHED_SPLIT || (flow_ckpt && axis == 2)) axis = 0;
   if (sched == DB_SCHED_FLOW) {
     if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw)) > 227 * 1024) return DB_ERR_UNSUPPORTED;
     if (launch_rrl_flow(f, ld, u, ld, tmp, upitch(W), qbuf, H, W, groups, ngroups, kh, kw, ng_bound, rp, iters,
@@ -114,7 +120,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
       return DB_ERR_CUDA;
     return DB_OK;
   }
-  const size_t smem_need = box ? rrl_box_smem(kh, kw)
+  const size_t smem_need = axis ? rrl_box_smem(kh, kw)
                                : sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const float* src = u;
@@ -131,7 +137,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
     const cudaError_t e =
         sched == DB_SCHED_SPLIT
             ? launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, groups, ngroups, kh, kw, rp,
-                               dev_status, ng_bound, box, s)
+                               dev_status, ng_bound, axis, s)
             : launch_rrl_spatial(f, ld, src, ld_src, dst, ld_dst, H, W, groups, ngroups, kh, kw, rp,
                                  dev_status, s);
     if (e != cudaSuccess) return DB_ERR_CUDA;
@@ -274,7 +280,8 @@ db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, lon
                           (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
     return DB_ERR_CUDA;
   if (iters == 0 && !ckpt) return DB_OK;
-  const size_t smem_need = psf->kind == DB_PSF_BOX ? rrl_box_smem(psf->kh, psf->kw) : rrl_split_smem(psf->kh, psf->kw);
+  const int axis = axis_mode(psf->kind, psf->kh, psf->kw);
+  const size_t smem_need = axis ? rrl_box_smem(psf->kh, psf->kw) : rrl_split_smem(psf->kh, psf->kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const RrlParams rp = to_rrl(p);
   float* tmp = (float*)(base + L.utmp);
@@ -297,7 +304,7 @@ db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, lon
     const int ld_dst = (k % 2 == 0) ? ldt : ld;
     const long long z_dst = (k % 2 == 0) ? zt : img_stride;
     if (launch_rrl_split(f, ld, src, ld_src, dst, ld_dst, qbuf, H, W, (TapGroup*)(base + L.taps),
-                         (int*)(base + L.ntaps), psf->kh, psf->kw, rp, dev_status, 0, psf->kind == DB_PSF_BOX, s, n,
+                         (int*)(base + L.ntaps), psf->kh, psf->kw, rp, dev_status, 0, axis, s, n,
                          img_stride, z_src, z_dst, zq) != cudaSuccess)
       return DB_ERR_CUDA;
     src = dst;

@@ -36,7 +36,8 @@ struct BatchImg {
   const int* ngroups;
   int ldf, ldA, ldB, ldq;
   int H, W, kh, kw, ng_max, M, P;
-  int box;       // 0: tap groups; 1, 2: horizontal, vertical box (sliding-window sums)
+  int box;       // 0: tap groups; 1, 2: horizontal, vertical box (sliding-window sums);
+                 // 3, 4: other horizontal, vertical one-axis PSF (register windows)
   RrlParams p;
 };
 
@@ -56,15 +57,15 @@ __device__ __noinline__ void batch_u(unsigned char* smem, const BatchImg& im, co
                                      im.ngroups, im.kh, im.kw, im.ng_max, im.p, status, i0, j0);
 }
 
-template <bool HORIZ>
+template <bool HORIZ, bool BOX>
 __device__ __noinline__ void batch_box(int phase, unsigned char* smem, const BatchImg& im, const float* src, int lds,
                                        float* dst, int ldd, int* status, int i0, int j0) {
   if (phase == 0)
-    q_tile_box<kBTH, kBTW, kBR, HORIZ>(smem, im.f, im.ldf, src, lds, im.q, im.ldq, im.H, im.W, im.ngroups, im.p, i0,
-                                       j0);
+    q_tile_box<kBTH, kBTW, kBR, HORIZ, BOX>(smem, im.f, im.ldf, src, lds, im.q, im.ldq, im.H, im.W, im.ngroups, im.p,
+                                            i0, j0);
   else
-    update_tile_box<kBTH, kBTW, kBR, HORIZ>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.ngroups, im.p,
-                                            status, i0, j0);
+    update_tile_box<kBTH, kBTW, kBR, HORIZ, BOX>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.ngroups,
+                                                 im.p, status, i0, j0);
 }
 
 template <int M>
@@ -141,8 +142,10 @@ __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict
         const int lds = even ? im.ldA : im.ldB;
         float* dst = even ? im.B : im.A;
         const int ldd = even ? im.ldB : im.ldA;
-        if (im.box == 1) batch_box<true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
-        else if (im.box == 2) batch_box<false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        if (im.box == 1) batch_box<true, true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        else if (im.box == 2) batch_box<false, true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        else if (im.box == 3) batch_box<true, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        else if (im.box == 4) batch_box<false, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else switch (im.M) {
           case 1: batch_tile_m<1>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
           case 2: batch_tile_m<2>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
@@ -187,7 +190,7 @@ struct ImgRegions {
 static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
   ImgRegions r;
   r.groups = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
-  r.ngroups = off; off += 256;
+  r.ngroups = off; off += kAuxBytes;
   r.utmp = off;    off += align256((size_t)H * upitch(W) * sizeof(float));
   r.q = off;       off += align256((size_t)H * qpitch(W) * sizeof(float2));
   size_t spec = (kh == 1) ? (size_t)W : (kw == 1) ? (size_t)H : (size_t)H * W;
@@ -311,7 +314,8 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.ng_max = max_tap_groups(kh, kw);
     bi.M = tap_group_height(kh);
     bi.P = split_halo_class(kw);
-    bi.box = x.psf.kind == DB_PSF_BOX ? (kh == 1 ? 1 : 2) : 0;
+    const int axis = axis_mode(x.psf.kind, kh, kw);
+    bi.box = axis == 0 ? 0 : (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
     bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
     bi.p.rf_lut = rf_lut_device();

@@ -71,6 +71,15 @@ constexpr int kMaxTapSide = 255; // largest kh or kw
 void count_launch(int n = 1);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+// Bytes k_prepare_taps writes next to the tap groups: the group count (int),
+// at +16 the box weights (e0, w, e1, L), at +32 the taps of a one-axis PSF.
+constexpr size_t kAuxBytes = 1280;
+// Form of the split schedule for a PSF: 0 tap groups, 1 box (sliding-window
+// sums), 2 other one-axis PSF (register-window tap sums).
+inline int axis_mode(int kind, int kh, int kw) {
+  if (kind == DB_PSF_BOX) return 1;
+  return (kh == 1 || kw == 1) ? 2 : 0;
+}
 // Row pitches of workspace images: float rows padded to 16 bytes, float2
 // (q) rows to an even count, so that tile staging can copy 16-byte chunks.
 inline int upitch(int W) { return (W + 3) & ~3; }
@@ -81,7 +90,7 @@ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 // Workspace layout for one image (offsets in bytes from ws).
 struct WsLayout {
   size_t taps;     // TapGroup[max_tap_groups(kh, kw)]
-  size_t ntaps;    // int: number of groups
+  size_t ntaps;    // kAuxBytes: group count, one-axis weights and taps
   size_t utmp;     // float[H*upitch(W)]  (RRRL ping-pong)
   size_t qbuf;     // float2[H*qpitch(W)] (split schedule: q = (e, W); Fourier mode: Z)
   size_t spec;     // float4[spec_elems]  (PSF spectrum, float-float)
@@ -106,9 +115,9 @@ size_t rrl_split_smem(int kh, int kw);  // larger of the two split kernels
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             int ng_bound, int box, cudaStream_t s, int nz = 1, long long zf = 0,
+                             int ng_bound, int axis, cudaStream_t s, int nz = 1, long long zf = 0,
                              long long zin = 0, long long zout = 0, long long zq = 0);
-size_t rrl_box_smem(int kh, int kw);  // split kernels of a box PSF (kh == 1 or kw == 1)
+size_t rrl_box_smem(int kh, int kw);  // split kernels of a one-axis PSF (kh == 1 or kw == 1)
 
 // all iterations in one persistent launch ordered by tile dependencies;
 // flow_ws: flow_ws_bytes(H, W), 256-byte aligned

@@ -1,5 +1,7 @@
-// Box PSFs -- uniform linear motion along a coordinate axis (Sec. 4.3,
-// "Uniform linear motion"): the blur b = u*h and both correlations e*h*,
+// One-axis PSFs (Sec. 4.3, "Uniform linear motion" and "Non-uniform linear
+// motion"): the PSF lies on one row or one column.
+//
+// Box PSFs -- uniform linear motion along a coordinate axis: the blur b = u*h and both correlations e*h*,
 // W*h* by sliding-window sums instead of tap sums.  The taps are
 // [e0, w, ..., w, e1] in tap order: a plain box (e0 = e1 = w) or a box of
 // non-integer length with lighter end pixels.  Along the blur axis each
@@ -73,6 +75,46 @@ __device__ __forceinline__ void box_run(const T* src, int step, int L, float eL,
   }
 }
 
+// Any other one-axis PSF (non-uniform linear motion): the same runs of
+// kBoxSeg outputs, each a plain tap sum.  The kBoxSeg window pixels live in a
+// register ring: output s at tap m needs pixel m + s, so after tap m the slot
+// of pixel m (no longer needed) takes pixel m + kBoxSeg.  Unrolled over
+// blocks of kBoxSeg taps the ring indices are compile-time constants: one
+// shared load and kBoxSeg FMAs per tap.  The window weight of pixel m + s for
+// output s is taps[L-1-m] (REV, convolution) or taps[m] (correlation); the
+// largest pixel read is L - 2 + kBoxSeg.
+__device__ __forceinline__ float ax_fma(float w, float a, float acc) { return fmaf(w, a, acc); }
+__device__ __forceinline__ float2 ax_fma(float w, float2 a, float2 acc) {
+  return make_float2(fmaf(w, a.x, acc.x), fmaf(w, a.y, acc.y));
+}
+template <typename T, bool REV>
+__device__ __forceinline__ void axis_run(const T* src, int step, int L, const float* __restrict__ taps, T* dst,
+                                         int dstep) {
+  T acc[kBoxSeg], x[kBoxSeg];
+#pragma unroll
+  for (int s = 0; s < kBoxSeg; ++s) { acc[s] = bx_zero(T()); x[s] = src[s * step]; }
+  for (int mb = 0; mb < L; mb += kBoxSeg) {
+#pragma unroll
+    for (int t = 0; t < kBoxSeg; ++t) {
+      const int m = mb + t;
+      if (m < L) {
+        const float w = taps[REV ? L - 1 - m : m];
+#pragma unroll
+        for (int s = 0; s < kBoxSeg; ++s) acc[s] = ax_fma(w, x[(t + s) % kBoxSeg], acc[s]);
+        if (m + 1 < L) x[t] = src[(m + kBoxSeg) * step];
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kBoxSeg; ++s) dst[s * dstep] = acc[s];
+}
+
+// The taps of a one-axis PSF as k_prepare_taps stores them, 32 bytes after the
+// group count (tap order, L = kh * kw of them).
+__device__ __forceinline__ const float* axis_taps(const int* ngroups) {
+  return reinterpret_cast<const float*>(ngroups + 8);
+}
+
 // Copy rows y0.. (nrows) x columns x0.. (ncols) of a T image into shared rows
 // of stride S elements, one element per copy, with clamped indices.
 template <typename T>
@@ -92,22 +134,25 @@ __host__ __device__ inline int box_window_stride(int TW, int L, bool horiz, int 
 }
 __host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Shared memory of the box tiles (L: box length along its axis).
+// Shared memory of the one-axis tiles (L: PSF length along its axis); the
+// tap array (general taps) comes first.
+constexpr int kAxisTapsSmem = 1024;  // 256 floats
 __host__ __device__ inline size_t box_smem_q(int TH, int TW, int L, bool horiz) {
-  const size_t fs = (size_t)TH * TW * 4, bs = round16((size_t)TH * (TW + 1) * 4);
+  const size_t fs = (size_t)TH * TW * 4 + kAxisTapsSmem, bs = round16((size_t)TH * (TW + 1) * 4);
   const size_t us = horiz ? (size_t)TH * box_window_stride(TW, L, true, 4) * 4
                           : (size_t)(TH + L - 1) * box_window_stride(TW, L, false, 4) * 4;
   return fs + bs + us;
 }
 __host__ __device__ inline size_t box_smem_update(int TH, int TW, int L, bool horiz) {
-  const size_t ds = round16((size_t)TH * (TW + 1) * 8), ud = (size_t)(TH + 4) * (TW + 8) * 4;
+  const size_t ds = round16((size_t)TH * (TW + 1) * 8) + kAxisTapsSmem, ud = (size_t)(TH + 4) * (TW + 8) * 4;
   const size_t qs = horiz ? (size_t)TH * box_window_stride(TW, L, true, 2) * 8
                           : (size_t)(TH + L - 1) * box_window_stride(TW, L, false, 2) * 8;
   return ds + ud + qs;
 }
 
-// q = (e, W) on the TH x TW tile at (i0, j0) for a box PSF.
-template <int TH, int TW, int R, bool HORIZ, typename Dep = NoDep>
+// q = (e, W) on the TH x TW tile at (i0, j0) for a one-axis PSF: box (BOX,
+// sliding-window sums) or general taps (register windows).
+template <int TH, int TW, int R, bool HORIZ, bool BOX = true, typename Dep = NoDep>
 __device__ __forceinline__ void q_tile_box(unsigned char* smem_raw, const float* __restrict__ f, int ldf,
                                            const float* __restrict__ uin, int ldin, float2* __restrict__ q, int ldq,
                                            int H, int W, const int* __restrict__ ngroups_g, const RrlParams& p,
@@ -117,10 +162,13 @@ __device__ __forceinline__ void q_tile_box(unsigned char* smem_raw, const float*
   const int L = __float_as_int(bw.w), before = L - 1 - (L >> 1);  // conv window: L-1-c before, c after
   constexpr int BS = TW + 1;
   const int US = box_window_stride(TW, L, HORIZ, 4);
-  float* fs = (float*)smem_raw;
+  float* taps = (float*)smem_raw;  // general taps (kAxisTapsSmem bytes)
+  float* fs = taps + kAxisTapsSmem / 4;
   float* bs = fs + TH * TW;
   float* us = (float*)((unsigned char*)bs + round16((size_t)TH * BS * 4));
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  if (!BOX)
+    for (int k = tid; k < L; k += nth) taps[k] = __ldg(axis_taps(ngroups_g) + k);
   stage_tile<float, TW>(fs, f, ldf, H, W, i0, TH, j0, TW / 4, rows_aligned16(f, ldf));
   dep();
   if (HORIZ) stage_elems<float>(us, US, uin, ldin, H, W, i0, TH, j0 - before, TW + L - 1);
@@ -131,10 +179,12 @@ __device__ __forceinline__ void q_tile_box(unsigned char* smem_raw, const float*
   for (int item = tid; item < TH * TW / kBoxSeg; item += nth) {
     if (HORIZ) {
       const int r = item % TH, x0 = (item / TH) * kBoxSeg;
-      box_run<float>(us + r * US + x0, 1, L, bw.z, bw.y, bw.x, bs + r * BS + x0, 1);
+      if (BOX) box_run<float>(us + r * US + x0, 1, L, bw.z, bw.y, bw.x, bs + r * BS + x0, 1);
+      else axis_run<float, true>(us + r * US + x0, 1, L, taps, bs + r * BS + x0, 1);
     } else {
       const int c = item % TW, y0 = (item / TW) * kBoxSeg;
-      box_run<float>(us + y0 * US + c, US, L, bw.z, bw.y, bw.x, bs + y0 * BS + c, BS);
+      if (BOX) box_run<float>(us + y0 * US + c, US, L, bw.z, bw.y, bw.x, bs + y0 * BS + c, BS);
+      else axis_run<float, true>(us + y0 * US + c, US, L, taps, bs + y0 * BS + c, BS);
     }
   }
   __syncthreads();
@@ -150,8 +200,8 @@ __device__ __forceinline__ void q_tile_box(unsigned char* smem_raw, const float*
   }
 }
 
-// Delta, B (sliding sums of q), D and the update on the TH x TW tile at (i0, j0).
-template <int TH, int TW, int R, bool HORIZ, typename Dep = NoDep>
+// Delta, B (one-axis sums of q), D and the update on the TH x TW tile at (i0, j0).
+template <int TH, int TW, int R, bool HORIZ, bool BOX = true, typename Dep = NoDep>
 __device__ __forceinline__ void update_tile_box(unsigned char* smem_raw, const float2* __restrict__ q, int ldq,
                                                 const float* __restrict__ uin, int ldin, float* __restrict__ uout,
                                                 int ldout, int H, int W, const int* __restrict__ ngroups_g,
@@ -161,10 +211,13 @@ __device__ __forceinline__ void update_tile_box(unsigned char* smem_raw, const f
   const int L = __float_as_int(bw.w), c0 = L >> 1;  // correlation window: c before, L-1-c after
   constexpr int DS = TW + 1, UH = TH + 4, US = TW + 8;
   const int QS = box_window_stride(TW, L, HORIZ, 2);
-  float2* ds = (float2*)smem_raw;
-  float* us = (float*)(smem_raw + round16((size_t)TH * DS * 8));
+  float* taps = (float*)smem_raw;  // general taps (kAxisTapsSmem bytes)
+  float2* ds = (float2*)(smem_raw + kAxisTapsSmem);
+  float* us = (float*)((unsigned char*)ds + round16((size_t)TH * DS * 8));
   float2* qs = (float2*)(us + UH * US);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  if (!BOX)
+    for (int k = tid; k < L; k += nth) taps[k] = __ldg(axis_taps(ngroups_g) + k);
   stage_tile<float, US>(us, uin, ldin, H, W, i0 - 2, UH, j0 - 4, TW / 4 + 2, rows_aligned16(uin, ldin));
   dep();
   if (HORIZ) stage_elems<float2>(qs, QS, q, ldq, H, W, i0, TH, j0 - c0, TW + L - 1);
@@ -175,10 +228,12 @@ __device__ __forceinline__ void update_tile_box(unsigned char* smem_raw, const f
   for (int item = tid; item < TH * TW / kBoxSeg; item += nth) {
     if (HORIZ) {
       const int r = item % TH, x0 = (item / TH) * kBoxSeg;
-      box_run<float2>(qs + r * QS + x0, 1, L, bw.x, bw.y, bw.z, ds + r * DS + x0, 1);
+      if (BOX) box_run<float2>(qs + r * QS + x0, 1, L, bw.x, bw.y, bw.z, ds + r * DS + x0, 1);
+      else axis_run<float2, false>(qs + r * QS + x0, 1, L, taps, ds + r * DS + x0, 1);
     } else {
       const int c = item % TW, y0 = (item / TW) * kBoxSeg;
-      box_run<float2>(qs + y0 * QS + c, QS, L, bw.x, bw.y, bw.z, ds + y0 * DS + c, DS);
+      if (BOX) box_run<float2>(qs + y0 * QS + c, QS, L, bw.x, bw.y, bw.z, ds + y0 * DS + c, DS);
+      else axis_run<float2, false>(qs + y0 * QS + c, QS, L, taps, ds + y0 * DS + c, DS);
     }
   }
   __syncthreads();

@@ -81,8 +81,12 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
     if (kind == DB_PSF_BOX && k >= 1 && k <= n - 2 && w != t1) atomicOr(&bad, DB_FLAG_BOX);
     sum += w;
   }
-  if (kind == DB_PSF_BOX && threadIdx.x == 0)  // (e0, w, e1, L) 16 bytes after the group count
+  // one-axis PSFs: (e0, w, e1, L) 16 bytes after the group count, the taps
+  // themselves 32 bytes after it
+  if ((kh == 1 || kw == 1) && threadIdx.x == 0)
     reinterpret_cast<float4*>(ngroups + 4)[0] = make_float4(__ldg(taps), t1, __ldg(taps + n - 1), __int_as_float(n));
+  if (kh == 1 || kw == 1)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) reinterpret_cast<float*>(ngroups + 8)[k] = __ldg(taps + k);
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) warp_sum[wid] = sum;
   // one thread per PSF column (kw <= 255): count, exclusive scan, write
@@ -170,19 +174,20 @@ __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* _
                                PdlDep());
 }
 
-// box PSFs: the same split pair with sliding-window sums (rrl_box.cuh)
-template <bool HORIZ>
+// one-axis PSFs: the same split pair with sliding-window sums (box) or
+// register-window tap sums (rrl_box.cuh)
+template <bool HORIZ, bool BOX>
 __global__ void __launch_bounds__(128) k_rrl_q_box(const float* __restrict__ f, int ldf,
                                                   const float* __restrict__ uin, int ldin, float2* __restrict__ q,
                                                   int ldq, int H, int W, const int* __restrict__ ngroups_g,
                                                   RrlParams p, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long z = blockIdx.z;
-  q_tile_box<32, 32, 8, HORIZ>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W,
+  q_tile_box<32, 32, 8, HORIZ, BOX>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W,
                                ngroups_g, p, blockIdx.y * 32, blockIdx.x * 32, PdlDep());
 }
 
-template <bool HORIZ>
+template <bool HORIZ, bool BOX>
 __global__ void __launch_bounds__(128) k_rrl_update_box(const float2* __restrict__ q, int ldq,
                                                        const float* __restrict__ uin, int ldin,
                                                        float* __restrict__ uout, int ldout, int H, int W,
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(128) k_rrl_update_box(const float2* __restrict
                                                        ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long z = blockIdx.z;
-  update_tile_box<32, 32, 8, HORIZ>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H,
+  update_tile_box<32, 32, 8, HORIZ, BOX>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H,
                                     W, ngroups_g, p, status, blockIdx.y * 32, blockIdx.x * 32, PdlDep());
 }
 
@@ -243,7 +248,7 @@ struct IterArgs {
   const float* f; int ldf; const float* uin; int ldin; float* uout; int ldout; float2* q;
   int H, W; const TapGroup* groups; const int* ngroups; int kh, kw; RrlParams p; int* status;
   int ng_bound;  // known upper bound of the group count (0: use max_tap_groups)
-  int box;       // DB_PSF_BOX taps: sliding-window sums (split schedule only)
+  int axis;      // axis_mode(): one-axis form of the split schedule (1 box, 2 general taps)
   int nz;        // images per launch (split schedule), offsets zs
   ZStride zs;
 };
@@ -299,13 +304,13 @@ static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
   return cudaSuccess;
 }
 
-template <bool HORIZ>
+template <bool HORIZ, bool BOX>
 static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
   const int L = HORIZ ? a.kw : a.kh;
   const size_t sq = box_smem_q(32, 32, L, HORIZ), su = box_smem_update(32, 32, L, HORIZ);
   if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
-  auto kq = k_rrl_q_box<HORIZ>;
-  auto ku = k_rrl_update_box<HORIZ>;
+  auto kq = k_rrl_q_box<HORIZ, BOX>;
+  auto ku = k_rrl_update_box<HORIZ, BOX>;
   cudaError_t e;
   if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
   if ((e = set_smem(ku, su)) != cudaSuccess) return e;
@@ -385,11 +390,12 @@ cudaError_t launch_rrl_spatial(const float* f, int ldf, const float* uin, int ld
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,
-                             int ng_bound, int box, cudaStream_t s, int nz, long long zf, long long zin,
+                             int ng_bound, int axis, cudaStream_t s, int nz, long long zf, long long zin,
                              long long zout, long long zq) {
-  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound, box,
+  const IterArgs a = {f, ldf, uin, ldin, uout, ldout, q, H, W, groups, ngroups, kh, kw, p, status, ng_bound, axis,
                       nz, {zf, zin, zout, zq}};
-  if (box) return kh == 1 ? launch_split_box<true>(a, s) : launch_split_box<false>(a, s);
+  if (axis == 1) return kh == 1 ? launch_split_box<true, true>(a, s) : launch_split_box<false, true>(a, s);
+  if (axis == 2) return kh == 1 ? launch_split_box<true, false>(a, s) : launch_split_box<false, false>(a, s);
   return dispatch<true>(a, s);
 }
 

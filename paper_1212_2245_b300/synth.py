@@ -103,6 +103,17 @@ def raised_cosine_1d(L: int, axis: str = "row", period: float | None = None) -> 
     return _normalise(h if axis == "row" else h.T)
 
 
+def random_motion_1d(L: int, rng: np.random.Generator, axis: str = "row", zeros: float = 0.15) -> np.ndarray:
+    """Non-uniform linear motion along a coordinate axis with an irregular
+    speed profile: L positive dwell weights U(0.05, 1), about `zeros` of the
+    interior ones set to zero (the camera skipping pixels)."""
+    w = rng.uniform(0.05, 1.0, L)
+    if L > 2:
+        w[1:-1][rng.random(L - 2) < zeros] = 0.0
+    h = w[None, :]
+    return _normalise(h if axis == "row" else h.T)
+
+
 def line_psf(L: int = 31, angle_deg: float = 30.0, period: float = 32.0) -> np.ndarray:
     """Motion along a line at `angle_deg` (counter-clockwise from the +x axis,
     rows pointing down).  Samples t_j = j-(L-1)/2 of a raised-cosine profile

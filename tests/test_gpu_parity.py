@@ -233,10 +233,13 @@ def test_plan_equals_deblur(lib, maker, kind):
 @pytest.mark.parametrize("H,W,psf", [(256, 320, "line"), (77, 131, "gauss"), (40, 300, "row"), (300, 40, "col")])
 def test_flow_equals_split_bitwise(lib, H, W, psf):
     """The persistent dependency-ordered launch runs the split schedule's tile
-    bodies, so it must reproduce the split result exactly."""
+    bodies, so it must reproduce the split result exactly.  For one-axis PSFs
+    the split schedule itself uses register windows; its tap-group form runs
+    when checkpoints are asked of the flow schedule."""
     rng = np.random.default_rng(H + W)
     h = {"line": synth.line_psf(31, 30.0, 32.0), "row": synth.box_psf(15),
          "col": synth.raised_cosine_1d(9, "col"), "gauss": synth.gaussian_mixture_psf(9, rng)}[psf]
+    one_axis = h.shape[0] == 1 or h.shape[1] == 1
     p = Params()
     f, u0 = _iterate_case(H, W, h, 7, p, seed=11)
     out = {}
@@ -244,9 +247,16 @@ def test_flow_equals_split_bitwise(lib, H, W, psf):
         for name in ("split", "flow"):
             lib.set_schedule(name)
             out[name] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7)
+        if one_axis:
+            ck = torch.empty(1, H, W, device="cuda")
+            out["groups"] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7, ckpt=ck, ckpt_every=7)
     finally:
         lib.set_schedule("auto")
-    assert torch.equal(out["split"], out["flow"])
+    if one_axis:
+        assert torch.equal(out["groups"], out["flow"])
+        assert_close(out["split"], out["flow"].double().cpu().numpy(), "register windows vs flow")
+    else:
+        assert torch.equal(out["split"], out["flow"])
 
 
 def test_flow_bounded_waits_report_timeout(lib):
@@ -291,6 +301,36 @@ def test_box_sliding_window_matches_oracle(lib, L, axis, H, W):
     assert_close(u, ref, f"box L={L} {axis} {H}x{W}")
     ug = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6)  # tap groups
     assert_close(u, ug.double().cpu().numpy(), "box vs tap groups")
+
+
+@pytest.mark.parametrize("L", [1, 2, 7, 8, 9, 16, 33, 100, 255])
+@pytest.mark.parametrize("axis", ["row", "col"])
+def test_one_axis_register_windows_match_oracle(lib, L, axis):
+    """Non-uniform one-axis PSFs with irregular weights (zeros included): the
+    register-window tap sums of the split schedule against the oracle, and
+    against the tap-group form of the fused schedule, on ragged shapes."""
+    rng = np.random.default_rng(1000 + L)
+    h = synth.random_motion_1d(L, rng, axis)
+    H, W = 61, max(L, 37) + 13
+    if axis == "col":
+        H, W = W, H
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, 4, p, seed=L)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 4)
+    lib.set_schedule("split")
+    ug = None
+    try:
+        u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 4)
+        lib.set_schedule("fused")
+        try:  # the fused tiles hold a halo of kw columns: not every width fits
+            ug = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 4)
+        except lib.DeblurError as e:
+            assert "unsupported" in str(e) and L > 128
+    finally:
+        lib.set_schedule("auto")
+    assert_close(u, ref, f"1D L={L} {axis} {H}x{W}")
+    if ug is not None:
+        assert_close(u, ug.double().cpu().numpy(), "register windows vs tap groups")
 
 
 def test_box_full_pipeline_fractional(lib):
