@@ -301,6 +301,17 @@ const char* db_version(void);
 #define DB_SCHED_FLOW 3
 db_status db_set_schedule(int schedule);
 
+/* One-axis PSFs (kh == 1 or kw == 1) in the split and flow schedules: a box
+ * (DB_PSF_BOX) is always summed by sliding windows; another one-axis PSF of
+ * length L = kh * kw is summed with register windows (one shared-memory load
+ * and 8 FMAs per tap for 8 outputs) when L >= min_len, with tap groups
+ * otherwise.  Process-wide; min_len in 1..256 (256: never).  0 restores the
+ * default: register windows for one-row PSFs from 16 taps and one-column
+ * PSFs from 32 taps (shorter ones are faster as tap groups on B300).  The
+ * result differs between the two forms by FP32 rounding only.  DB_ERR_ARG
+ * for other values. */
+db_status db_set_one_axis_min(int min_len);
+
 /* Evaluation of the information divergence r_f in the robust weight
  * (process-wide setting, all devices):
  *   DB_RF_LOG1P - r_f(b) = f (t - log1p t), t = (b - f)/f (default; exact up

@@ -16,7 +16,7 @@ from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_spin_limit",
+           "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_one_axis_min", "set_spin_limit",
            "set_rf_eval", "version", "FrameStream", "deblur_n", "workspace_bytes_n"]
 
 
@@ -414,6 +414,13 @@ def set_schedule(name: str):
     code = {"auto": _lib.SCHED_AUTO, "fused": _lib.SCHED_FUSED, "split": _lib.SCHED_SPLIT,
             "flow": _lib.SCHED_FLOW}[name]
     _check(_lib.load().db_set_schedule(code), "db_set_schedule")
+
+
+def set_one_axis_min(min_len: int = 0):
+    """Shortest non-box one-axis PSF summed with register windows in the split
+    and flow schedules (shorter ones use tap groups); 256 = never, 0 = the
+    default (rows from 16 taps, columns from 32).  Process-wide."""
+    _check(_lib.load().db_set_one_axis_min(int(min_len)), "db_set_one_axis_min")
 
 
 def set_rf_eval(name: str):

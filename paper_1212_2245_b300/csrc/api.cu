@@ -12,6 +12,11 @@ namespace db {
 
 static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_schedule{0};
+static std::atomic<int> g_one_axis_min{0};
+int one_axis_min(bool row) {
+  const int v = g_one_axis_min.load(std::memory_order_relaxed);
+  return v > 0 ? v : row ? 16 : 32;
+}
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n) {
@@ -102,17 +107,16 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   if (sched == DB_SCHED_AUTO) {
     sched = ((size_t)H * W * 16 <= (size_t)48 << 20) ? DB_SCHED_SPLIT : DB_SCHED_FUSED;
     if (sched == DB_SCHED_SPLIT && (size_t)H * W >= (size_t)512 * 1024) sched = DB_SCHED_FLOW;
-    if (axis) sched = DB_SCHED_SPLIT;
   }
-  // the flow schedule writes no checkpoints: the split schedule stands in,
-  // with the same tap-group sums (bitwise equal to the flow result)
-  const bool flow_ckpt = sched == DB_SCHED_FLOW && ckpt;
-  if (flow_ckpt || axis == 1) sched = DB_SCHED_SPLIT;
-  if (sched != DB_SCHED_SPLIT || (flow_ckpt && axis == 2)) axis = 0;
+  // the flow schedule writes no checkpoints: the split schedule (same tile
+  // bodies, bitwise equal result) stands in; a box keeps its window sums
+  if ((sched == DB_SCHED_FLOW && ckpt) || (sched == DB_SCHED_FUSED && axis == 1)) sched = DB_SCHED_SPLIT;
+  if (sched == DB_SCHED_FUSED) axis = 0;
   if (sched == DB_SCHED_FLOW) {
-    if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw)) > 227 * 1024) return DB_ERR_UNSUPPORTED;
+    if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw), axis) > 227 * 1024)
+      return DB_ERR_UNSUPPORTED;
     if (launch_rrl_flow(f, ld, u, ld, tmp, upitch(W), qbuf, H, W, groups, ngroups, kh, kw, ng_bound, rp, iters,
-                        base + L.flow, dev_status, s) != cudaSuccess)
+                        base + L.flow, dev_status, s, axis) != cudaSuccess)
       return DB_ERR_CUDA;
     if (iters % 2 == 1 &&
         cudaMemcpy2DAsync(u, (size_t)ld * sizeof(float), tmp, (size_t)upitch(W) * sizeof(float),
@@ -433,6 +437,12 @@ db_status db_status_from_flags(int flags) {
 const char* db_version(void) { return "libdeblur 0.1 sm_103a"; }
 
 long long db_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+db_status db_set_one_axis_min(int min_len) {
+  if (min_len < 0 || min_len > kMaxTapSide + 1) return DB_ERR_ARG;
+  g_one_axis_min.store(min_len);
+  return DB_OK;
+}
 
 db_status db_set_schedule(int schedule) {
   if (schedule != DB_SCHED_AUTO && schedule != DB_SCHED_FUSED && schedule != DB_SCHED_SPLIT &&

@@ -74,11 +74,13 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Bytes k_prepare_taps writes next to the tap groups: the group count (int),
 // at +16 the box weights (e0, w, e1, L), at +32 the taps of a one-axis PSF.
 constexpr size_t kAuxBytes = 1280;
-// Form of the split schedule for a PSF: 0 tap groups, 1 box (sliding-window
-// sums), 2 other one-axis PSF (register-window tap sums).
+// Form of the split and flow tiles for a PSF: 0 tap groups, 1 box
+// (sliding-window sums), 2 other one-axis PSF of length >= one_axis_min()
+// (register-window tap sums).
+int one_axis_min(bool row);
 inline int axis_mode(int kind, int kh, int kw) {
   if (kind == DB_PSF_BOX) return 1;
-  return (kh == 1 || kw == 1) ? 2 : 0;
+  return (kh == 1 || kw == 1) && kh * kw >= one_axis_min(kh == 1) ? 2 : 0;
 }
 // Row pitches of workspace images: float rows padded to 16 bytes, float2
 // (q) rows to an even count, so that tile staging can copy 16-byte chunks.
@@ -122,11 +124,12 @@ size_t rrl_box_smem(int kh, int kw);  // split kernels of a one-axis PSF (kh == 
 // all iterations in one persistent launch ordered by tile dependencies;
 // flow_ws: flow_ws_bytes(H, W), 256-byte aligned
 size_t flow_ws_bytes(int H, int W);
-size_t flow_smem(int kh, int kw, int ng_max);
+size_t flow_smem(int kh, int kw, int ng_max, int axis = 0);  // axis: axis_mode() form of the tiles
 void set_flow_spin_limit(long long cycles);
 cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* utmp, int ldt, float2* q, int H, int W,
                             const TapGroup* groups, const int* ngroups, int kh, int kw, int ng_bound,
-                            const RrlParams& p, int iters, void* flow_ws, int* status, cudaStream_t s);
+                            const RrlParams& p, int iters, void* flow_ws, int* status, cudaStream_t s,
+                            int axis = 0);
 
 cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const float* taps,
                        int kh, int kw, float K, float floor_, void* ws, const WsLayout& L,

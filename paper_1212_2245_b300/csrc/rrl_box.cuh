@@ -79,34 +79,55 @@ __device__ __forceinline__ void box_run(const T* src, int step, int L, float eL,
 // kBoxSeg outputs, each a plain tap sum.  The kBoxSeg window pixels live in a
 // register ring: output s at tap m needs pixel m + s, so after tap m the slot
 // of pixel m (no longer needed) takes pixel m + kBoxSeg.  Unrolled over
-// blocks of kBoxSeg taps the ring indices are compile-time constants: one
-// shared load and kBoxSeg FMAs per tap.  The window weight of pixel m + s for
-// output s is taps[L-1-m] (REV, convolution) or taps[m] (correlation); the
-// largest pixel read is L - 2 + kBoxSeg.
+// blocks of kBoxSeg taps the ring indices are compile-time constants.  Full
+// blocks (all taps and all pixel loads present) run without conditions, with
+// their weights read as two 16-byte words; the last block checks each tap.
+// wts[m] is the weight of window pixel m + s for output s: the taps reversed
+// for the convolution, in tap order for the correlation (16-byte aligned,
+// shared).  The largest pixel read is L - 2 + kBoxSeg.
 __device__ __forceinline__ float ax_fma(float w, float a, float acc) { return fmaf(w, a, acc); }
 __device__ __forceinline__ float2 ax_fma(float w, float2 a, float2 acc) {
   return make_float2(fmaf(w, a.x, acc.x), fmaf(w, a.y, acc.y));
 }
-template <typename T, bool REV>
-__device__ __forceinline__ void axis_run(const T* src, int step, int L, const float* __restrict__ taps, T* dst,
+static_assert(kBoxSeg == 8, "two float4 weight words per block");
+template <typename T>
+__device__ __forceinline__ void axis_run(const T* src, int step, int L, const float* __restrict__ wts, T* dst,
                                          int dstep) {
   T acc[kBoxSeg], x[kBoxSeg];
 #pragma unroll
   for (int s = 0; s < kBoxSeg; ++s) { acc[s] = bx_zero(T()); x[s] = src[s * step]; }
-  for (int mb = 0; mb < L; mb += kBoxSeg) {
+  int mb = 0;
+  for (; mb + kBoxSeg < L; mb += kBoxSeg) {
+    const float4 w0 = *reinterpret_cast<const float4*>(wts + mb);
+    const float4 w1 = *reinterpret_cast<const float4*>(wts + mb + 4);
+    const float w[kBoxSeg] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
     for (int t = 0; t < kBoxSeg; ++t) {
-      const int m = mb + t;
-      if (m < L) {
-        const float w = taps[REV ? L - 1 - m : m];
 #pragma unroll
-        for (int s = 0; s < kBoxSeg; ++s) acc[s] = ax_fma(w, x[(t + s) % kBoxSeg], acc[s]);
-        if (m + 1 < L) x[t] = src[(m + kBoxSeg) * step];
-      }
+      for (int s = 0; s < kBoxSeg; ++s) acc[s] = ax_fma(w[t], x[(t + s) % kBoxSeg], acc[s]);
+      x[t] = src[(mb + t + kBoxSeg) * step];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kBoxSeg; ++t) {
+    const int m = mb + t;
+    if (m < L) {
+      const float w = wts[m];
+#pragma unroll
+      for (int s = 0; s < kBoxSeg; ++s) acc[s] = ax_fma(w, x[(t + s) % kBoxSeg], acc[s]);
+      if (m + 1 < L) x[t] = src[(m + kBoxSeg) * step];
     }
   }
 #pragma unroll
   for (int s = 0; s < kBoxSeg; ++s) dst[s * dstep] = acc[s];
+}
+
+// Shared copy of a one-axis PSF's taps for axis_run: REV (convolution) holds
+// them reversed.
+template <bool REV>
+__device__ __forceinline__ void load_axis_weights(float* wts, const float* __restrict__ taps, int L) {
+  for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < L; k += blockDim.x * blockDim.y)
+    wts[k] = __ldg(taps + (REV ? L - 1 - k : k));
 }
 
 // The taps of a one-axis PSF as k_prepare_taps stores them, 32 bytes after the
@@ -162,13 +183,12 @@ __device__ __forceinline__ void q_tile_box(unsigned char* smem_raw, const float*
   const int L = __float_as_int(bw.w), before = L - 1 - (L >> 1);  // conv window: L-1-c before, c after
   constexpr int BS = TW + 1;
   const int US = box_window_stride(TW, L, HORIZ, 4);
-  float* taps = (float*)smem_raw;  // general taps (kAxisTapsSmem bytes)
+  float* taps = (float*)smem_raw;  // general taps, reversed (kAxisTapsSmem bytes)
   float* fs = taps + kAxisTapsSmem / 4;
   float* bs = fs + TH * TW;
   float* us = (float*)((unsigned char*)bs + round16((size_t)TH * BS * 4));
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  if (!BOX)
-    for (int k = tid; k < L; k += nth) taps[k] = __ldg(axis_taps(ngroups_g) + k);
+  if (!BOX) load_axis_weights<true>(taps, axis_taps(ngroups_g), L);
   stage_tile<float, TW>(fs, f, ldf, H, W, i0, TH, j0, TW / 4, rows_aligned16(f, ldf));
   dep();
   if (HORIZ) stage_elems<float>(us, US, uin, ldin, H, W, i0, TH, j0 - before, TW + L - 1);
@@ -180,11 +200,11 @@ __device__ __forceinline__ void q_tile_box(unsigned char* smem_raw, const float*
     if (HORIZ) {
       const int r = item % TH, x0 = (item / TH) * kBoxSeg;
       if (BOX) box_run<float>(us + r * US + x0, 1, L, bw.z, bw.y, bw.x, bs + r * BS + x0, 1);
-      else axis_run<float, true>(us + r * US + x0, 1, L, taps, bs + r * BS + x0, 1);
+      else axis_run<float>(us + r * US + x0, 1, L, taps, bs + r * BS + x0, 1);
     } else {
       const int c = item % TW, y0 = (item / TW) * kBoxSeg;
       if (BOX) box_run<float>(us + y0 * US + c, US, L, bw.z, bw.y, bw.x, bs + y0 * BS + c, BS);
-      else axis_run<float, true>(us + y0 * US + c, US, L, taps, bs + y0 * BS + c, BS);
+      else axis_run<float>(us + y0 * US + c, US, L, taps, bs + y0 * BS + c, BS);
     }
   }
   __syncthreads();
@@ -216,8 +236,7 @@ __device__ __forceinline__ void update_tile_box(unsigned char* smem_raw, const f
   float* us = (float*)((unsigned char*)ds + round16((size_t)TH * DS * 8));
   float2* qs = (float2*)(us + UH * US);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  if (!BOX)
-    for (int k = tid; k < L; k += nth) taps[k] = __ldg(axis_taps(ngroups_g) + k);
+  if (!BOX) load_axis_weights<false>(taps, axis_taps(ngroups_g), L);
   stage_tile<float, US>(us, uin, ldin, H, W, i0 - 2, UH, j0 - 4, TW / 4 + 2, rows_aligned16(uin, ldin));
   dep();
   if (HORIZ) stage_elems<float2>(qs, QS, q, ldq, H, W, i0, TH, j0 - c0, TW + L - 1);
@@ -229,11 +248,11 @@ __device__ __forceinline__ void update_tile_box(unsigned char* smem_raw, const f
     if (HORIZ) {
       const int r = item % TH, x0 = (item / TH) * kBoxSeg;
       if (BOX) box_run<float2>(qs + r * QS + x0, 1, L, bw.x, bw.y, bw.z, ds + r * DS + x0, 1);
-      else axis_run<float2, false>(qs + r * QS + x0, 1, L, taps, ds + r * DS + x0, 1);
+      else axis_run<float2>(qs + r * QS + x0, 1, L, taps, ds + r * DS + x0, 1);
     } else {
       const int c = item % TW, y0 = (item / TW) * kBoxSeg;
       if (BOX) box_run<float2>(qs + y0 * QS + c, QS, L, bw.x, bw.y, bw.z, ds + y0 * DS + c, DS);
-      else axis_run<float2, false>(qs + y0 * QS + c, QS, L, taps, ds + y0 * DS + c, DS);
+      else axis_run<float2>(qs + y0 * QS + c, QS, L, taps, ds + y0 * DS + c, DS);
     }
   }
   __syncthreads();

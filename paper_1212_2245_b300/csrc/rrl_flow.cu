@@ -21,10 +21,12 @@
 // lower number; the lowest unfinished task belongs to a resident CTA that has
 // finished all its earlier (lower) tasks, so it runs and the run cannot
 // deadlock.  Each wait is bounded all the same (time-out: DB_FLAG_TIMEOUT,
-// the run aborts its waits and finishes).
+// the run aborts its waits and finishes).  One-axis PSFs run the one-axis
+// tile bodies of the split schedule (box sums or register windows).
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
+#include "rrl_box.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -69,7 +71,9 @@ __device__ bool flow_wait(const FlowArgs& a, const int* cnt, int bi, int bj, int
   return __all_sync(0xffffffffu, ok);
 }
 
-template <int M, int P>
+// AX: 0 tap groups (M, P); 1, 2 horizontal, vertical box; 3, 4 horizontal,
+// vertical one-axis PSF with register windows.
+template <int M, int P, int AX>
 __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -91,14 +95,23 @@ __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a)
     const bool even = (k & 1) == 0;
     const float* src = even ? a.A : a.B;
     const int lds = even ? a.ldA : a.ldB;
+    constexpr bool HORIZ = AX == 1 || AX == 3, BOX = AX <= 2;
     if (phase == 0) {
-      q_tile<kFTH, kFTW, kFR, M, P>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.groups, a.ngroups, a.kh,
-                                    a.kw, a.ng_max, a.p, bi * kFTH, bj * kFTW);
+      if constexpr (AX == 0)
+        q_tile<kFTH, kFTW, kFR, M, P>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.groups, a.ngroups, a.kh,
+                                      a.kw, a.ng_max, a.p, bi * kFTH, bj * kFTW);
+      else
+        q_tile_box<kFTH, kFTW, kFR, HORIZ, BOX>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.ngroups, a.p,
+                                                bi * kFTH, bj * kFTW);
     } else {
       float* dst = even ? a.B : a.A;
       const int ldd = even ? a.ldB : a.ldA;
-      update_tile<kFTH, kFTW, kFR, M, P>(smem, a.q, a.ldq, src, lds, dst, ldd, a.H, a.W, a.groups, a.ngroups,
-                                         a.kh, a.kw, a.ng_max, a.p, a.status, bi * kFTH, bj * kFTW);
+      if constexpr (AX == 0)
+        update_tile<kFTH, kFTW, kFR, M, P>(smem, a.q, a.ldq, src, lds, dst, ldd, a.H, a.W, a.groups, a.ngroups,
+                                           a.kh, a.kw, a.ng_max, a.p, a.status, bi * kFTH, bj * kFTW);
+      else
+        update_tile_box<kFTH, kFTW, kFR, HORIZ, BOX>(smem, a.q, a.ldq, src, lds, dst, ldd, a.H, a.W, a.ngroups,
+                                                     a.p, a.status, bi * kFTH, bj * kFTW);
     }
     __syncthreads();
     if (tid == 0) {
@@ -108,8 +121,11 @@ __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a)
   }
 }
 
-size_t flow_smem(int kh, int kw, int ng_max) {
-  const size_t sq = split_smem_q(kFTH, kFTW, kh, kw, ng_max), su = split_smem_update(kFTH, kFTW, kh, kw, ng_max);
+size_t flow_smem(int kh, int kw, int ng_max, int axis) {
+  const bool horiz = kh == 1;
+  const int L = horiz ? kw : kh;
+  const size_t sq = axis ? box_smem_q(kFTH, kFTW, L, horiz) : split_smem_q(kFTH, kFTW, kh, kw, ng_max);
+  const size_t su = axis ? box_smem_update(kFTH, kFTW, L, horiz) : split_smem_update(kFTH, kFTW, kh, kw, ng_max);
   return sq > su ? sq : su;
 }
 
@@ -120,9 +136,9 @@ size_t flow_ws_bytes(int H, int W) { return (size_t)(2 * flow_tiles(H, W) + 64) 
 static long long g_flow_spin = 4000000000LL;  // ~2 s at 2 GHz
 void set_flow_spin_limit(long long cycles) { g_flow_spin = cycles; }
 
-template <int M, int P>
+template <int M, int P, int AX = 0>
 static cudaError_t launch_flow_mp(FlowArgs a, size_t smem, cudaStream_t s) {
-  auto kern = k_rrl_flow<M, P>;
+  auto kern = k_rrl_flow<M, P, AX>;
   cudaError_t e;
   if (smem > 48 * 1024 &&
       (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -166,7 +182,7 @@ static cudaError_t launch_flow_m(const FlowArgs& a, size_t smem, cudaStream_t s)
 
 cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* utmp, int ldt, float2* q, int H, int W,
                             const TapGroup* groups, const int* ngroups, int kh, int kw, int ng_bound,
-                            const RrlParams& p, int iters, void* flow_ws, int* status, cudaStream_t s) {
+                            const RrlParams& p, int iters, void* flow_ws, int* status, cudaStream_t s, int axis) {
   if (iters <= 0) return cudaSuccess;
   FlowArgs a = {};
   a.f = f; a.ldf = ldf;
@@ -194,12 +210,22 @@ cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* u
   a.spin_limit = g_flow_spin;
   cudaError_t e;
   if ((e = cudaMemsetAsync(flow_ws, 0, flow_ws_bytes(H, W), s)) != cudaSuccess) return e;
-  const size_t smem = flow_smem(kh, kw, a.ng_max);
+  const size_t smem = flow_smem(kh, kw, a.ng_max, axis);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  switch (tap_group_height(kh)) {
-    case 1: e = launch_flow_m<1>(a, smem, s); break;
-    case 2: e = launch_flow_m<2>(a, smem, s); break;
-    default: e = launch_flow_m<3>(a, smem, s); break;
+  if (axis) {
+    const int ax = (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
+    switch (ax) {
+      case 1: e = launch_flow_mp<1, 8, 1>(a, smem, s); break;
+      case 2: e = launch_flow_mp<1, 8, 2>(a, smem, s); break;
+      case 3: e = launch_flow_mp<1, 8, 3>(a, smem, s); break;
+      default: e = launch_flow_mp<1, 8, 4>(a, smem, s); break;
+    }
+  } else {
+    switch (tap_group_height(kh)) {
+      case 1: e = launch_flow_m<1>(a, smem, s); break;
+      case 2: e = launch_flow_m<2>(a, smem, s); break;
+      default: e = launch_flow_m<3>(a, smem, s); break;
+    }
   }
   if (e != cudaSuccess) (void)cudaGetLastError();
   return e;

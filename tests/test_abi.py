@@ -83,3 +83,13 @@ def test_argument_errors_are_synchronous(lib):
     bad = _args(K=0.0)[1]
     assert call(p=bad) == 1
     assert call(f=fake_u) == 1                  # f aliases u
+
+
+def test_process_wide_knobs_validate_their_arguments(lib):
+    for bad in (-1, 4, 99):
+        assert lib.db_set_schedule(bad) == 1
+    assert lib.db_set_schedule(0) == 0
+    for bad in (-1, 257, 1000):
+        assert lib.db_set_one_axis_min(bad) == 1
+    for good in (1, 16, 256, 0):
+        assert lib.db_set_one_axis_min(good) == 0

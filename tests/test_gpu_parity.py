@@ -230,33 +230,30 @@ def test_plan_equals_deblur(lib, maker, kind):
     plan.close()
 
 
-@pytest.mark.parametrize("H,W,psf", [(256, 320, "line"), (77, 131, "gauss"), (40, 300, "row"), (300, 40, "col")])
-def test_flow_equals_split_bitwise(lib, H, W, psf):
+@pytest.mark.parametrize("H,W,psf,kind", [(256, 320, "line", "general"), (77, 131, "gauss", "general"),
+                                          (40, 300, "row", "general"), (300, 40, "col", "general"),
+                                          (130, 300, "row", "box"), (97, 200, "rowrnd", "general")])
+def test_flow_equals_split_bitwise(lib, H, W, psf, kind):
     """The persistent dependency-ordered launch runs the split schedule's tile
-    bodies, so it must reproduce the split result exactly.  For one-axis PSFs
-    the split schedule itself uses register windows; its tap-group form runs
-    when checkpoints are asked of the flow schedule."""
+    bodies (tap groups, box sums or register windows), so it must reproduce
+    the split result exactly."""
     rng = np.random.default_rng(H + W)
-    h = {"line": synth.line_psf(31, 30.0, 32.0), "row": synth.box_psf(15),
+    h = {"line": synth.line_psf(31, 30.0, 32.0), "row": synth.box_psf(15), "rowrnd": synth.random_motion_1d(23, rng),
          "col": synth.raised_cosine_1d(9, "col"), "gauss": synth.gaussian_mixture_psf(9, rng)}[psf]
-    one_axis = h.shape[0] == 1 or h.shape[1] == 1
     p = Params()
     f, u0 = _iterate_case(H, W, h, 7, p, seed=11)
     out = {}
     try:
-        for name in ("split", "flow"):
-            lib.set_schedule(name)
-            out[name] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7)
-        if one_axis:
-            ck = torch.empty(1, H, W, device="cuda")
-            out["groups"] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7, ckpt=ck, ckpt_every=7)
+        for knob in (1, 256):  # one-axis PSFs: register windows, then tap groups
+            lib.set_one_axis_min(knob)
+            for name in ("split", "flow"):
+                lib.set_schedule(name)
+                out[name, knob] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 7, kind=kind)
     finally:
         lib.set_schedule("auto")
-    if one_axis:
-        assert torch.equal(out["groups"], out["flow"])
-        assert_close(out["split"], out["flow"].double().cpu().numpy(), "register windows vs flow")
-    else:
-        assert torch.equal(out["split"], out["flow"])
+        lib.set_one_axis_min(0)
+    for knob in (1, 256):
+        assert torch.equal(out["split", knob], out["flow", knob])
 
 
 def test_flow_bounded_waits_report_timeout(lib):
@@ -318,6 +315,7 @@ def test_one_axis_register_windows_match_oracle(lib, L, axis):
     f, u0 = _iterate_case(H, W, h, 4, p, seed=L)
     ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 4)
     lib.set_schedule("split")
+    lib.set_one_axis_min(1)  # register windows at every length
     ug = None
     try:
         u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 4)
@@ -328,6 +326,7 @@ def test_one_axis_register_windows_match_oracle(lib, L, axis):
             assert "unsupported" in str(e) and L > 128
     finally:
         lib.set_schedule("auto")
+        lib.set_one_axis_min(0)
     assert_close(u, ref, f"1D L={L} {axis} {H}x{W}")
     if ug is not None:
         assert_close(u, ug.double().cpu().numpy(), "register windows vs tap groups")
