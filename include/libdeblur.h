@@ -69,7 +69,8 @@ typedef enum {
                           taps equal except possibly the first and the last
                           (lighter end pixels of a non-integer blur length).
                           The spatial iterations then blur and correlate by
-                          sliding-window sums (split schedule).            */
+                          sliding-window sums (split and flow schedules; a
+                          fused schedule request runs split).               */
 } db_psf_kind;
 
 typedef enum {
