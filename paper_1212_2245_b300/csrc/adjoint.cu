@@ -407,19 +407,32 @@ __device__ __forceinline__ float2 zero_of(float2) { return make_float2(0.f, 0.f)
 template <typename T, bool CLAMP>
 __device__ __forceinline__ void stage_rows(T* s, const T* __restrict__ src, int R0, int nr, int W) {
   const int L = W + 2 * kAdjRowPad;
-  for (int k = threadIdx.x; k < nr * L; k += blockDim.x) {
-    const int r = k / L, j = k - r * L - kAdjRowPad;
+  for (int r = 0; r < nr; ++r) {
     const T* row = src + (size_t)(R0 + r) * W;
-    T v;
-    if (CLAMP) v = row[clampi(j, W)];
-    else v = (j >= 0 && j < W) ? row[j] : zero_of(T());
-    s[k] = v;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+      const int j = k - kAdjRowPad;
+      T v;
+      if (CLAMP) v = row[clampi(j, W)];
+      else v = (j >= 0 && j < W) ? row[j] : zero_of(T());
+      s[r * L + k] = v;
+    }
   }
 }
 
+// The taps of a one-row PSF, zero beyond kw up to KWB (the tap loops below
+// run over KWB taps with compile-time offsets; a zero tap adds exactly zero
+// to a finite sum).
+template <int KWB>
 __device__ __forceinline__ void load_row_taps(float* taps, const AdjImage& im) {
-  if ((int)threadIdx.x < im.kw) taps[threadIdx.x] = im.taps[threadIdx.x];
+  if ((int)threadIdx.x < KWB) taps[threadIdx.x] = (int)threadIdx.x < im.kw ? im.taps[threadIdx.x] : 0.f;
 }
+
+// A tap weight read from shared memory at each use (volatile: the weights
+// stay out of registers, which the row kernels need for occupancy).
+__device__ __forceinline__ float tap_at(const float* taps, int c) { return *((volatile const float*)taps + c); }
+
+// Smallest tap-loop length of the row kernels that holds kw taps.
+inline int row_taps_bucket(int kw) { return kw <= 8 ? 8 : kw <= 16 ? 16 : kw <= 24 ? 24 : 32; }
 
 // Row-block loop: the CTA takes kAdjRowBlock rows at a time (grid-stride).
 #define ADJ_ROW_BLOCKS(rows)                                                                       \
@@ -433,18 +446,19 @@ __device__ __forceinline__ void load_row_taps(float* taps, const AdjImage& im) {
 
 // Forward recompute of one iteration for one-row PSFs, fused: b = C u and
 // q = (W f/b, W) into a shared row, then A, B = C' q and g from it.
+template <int KWB>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __restrict__ u,
-                                                               const float* __restrict__ f0, AdjImage im,
-                                                               float* __restrict__ b_out,
-                                                               float2* __restrict__ q_out,
-                                                               float2* __restrict__ ab_out,
-                                                               float* __restrict__ g_out) {
+                                                                  const float* __restrict__ f0, AdjImage im,
+                                                                  float* __restrict__ b_out,
+                                                                  float2* __restrict__ q_out,
+                                                                  float2* __restrict__ ab_out,
+                                                                  float* __restrict__ g_out) {
   extern __shared__ __align__(16) unsigned char adj_sm[];
-  __shared__ float taps[kAdjRowTaps];
+  __shared__ float taps[KWB];
   const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
   float2* sq = (float2*)adj_sm;
   float* su = (float*)(sq + kAdjRowBlock * L);
-  load_row_taps(taps, im);
+  load_row_taps<KWB>(taps, im);
   ADJ_ROW_BLOCKS(rows) {
     const int nr = min(kAdjRowBlock, rows - R0);
     __syncthreads();
@@ -452,12 +466,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
     __syncthreads();
     ADJ_ROW_ITEMS(nr, W) {
       const int r = it / W, j = it - r * W;
-      const float* ur = su + r * L + kAdjRowPad;
+      const float* ub = su + r * L + kAdjRowPad + j + cx;  // ub[-c] = u(j - (c - cx))
       float bb = 0.f;
-      for (int c = 0; c < kw; ++c) {
-        const float w = taps[c];
-        if (w != 0.f) bb = fmaf(w, ur[j - (c - cx)], bb);
-      }
+#pragma unroll
+      for (int c = 0; c < KWB; ++c) bb = fmaf(tap_at(taps, c), ub[-c], bb);
       const size_t idx = (size_t)R0 * W + it;
       const float fv = f0[idx];
       float rr;
@@ -478,16 +490,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
     __syncthreads();
     ADJ_ROW_ITEMS(nr, W) {
       const int r = it / W, j = it - r * W;
-      const float2* qr = sq + r * L + kAdjRowPad;
+      const float2* qb = sq + r * L + kAdjRowPad + j - cx;  // qb[c] = q(j + (c - cx))
       const float* ur = su + r * L + kAdjRowPad;
       float A = 0.f, B = 0.f;
-      for (int c = 0; c < kw; ++c) {
-        const float w = taps[c];
-        if (w != 0.f) {
-          const float2 v = qr[j + (c - cx)];
-          A = fmaf(w, v.x, A);
-          B = fmaf(w, v.y, B);
-        }
+#pragma unroll
+      for (int c = 0; c < KWB; ++c) {
+        const float w = tap_at(taps, c);
+        const float2 v = qb[c];
+        A = fmaf(w, v.x, A);
+        B = fmaf(w, v.y, B);
       }
       const int R = R0 + r, n = R / H, i = R - n * H;
       const float* img = u + (size_t)n * H * W;
@@ -508,22 +519,23 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
 // with the alpha partial in part[0 .. G) and the tap partials (both
 // transposes, summed per tap) in part[G + t G ...].  The diffusion adjoint
 // (k_adj_rev_diff1/2) follows: it needs Dbar of the neighbouring rows.
+template <int KWB>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
     const float* __restrict__ Ubar_next, const float* __restrict__ u, const float2* __restrict__ ab,
     const float* __restrict__ g, const float2* __restrict__ q, const float* __restrict__ b,
     const float* __restrict__ f0, AdjImage im, float* __restrict__ Uacc, float* __restrict__ Dbar,
     float* __restrict__ f0bar, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char adj_sm[];
-  __shared__ float taps[kAdjRowTaps];
+  __shared__ float taps[KWB];
   const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
   float2* sa = (float2*)adj_sm;
   float2* sq = sa + kAdjRowBlock * L;
   float* sb = (float*)(sq + kAdjRowBlock * L);
   float* su = sb + kAdjRowBlock * L;
-  load_row_taps(taps, im);
-  float acc[kAdjRowTaps];
+  load_row_taps<KWB>(taps, im);
+  float acc[KWB];  // tap partials (entries from kw on are never reduced)
 #pragma unroll
-  for (int t = 0; t < kAdjRowTaps; ++t) acc[t] = 0.f;
+  for (int t = 0; t < KWB; ++t) acc[t] = 0.f;
   float asum = 0.f;
   ADJ_ROW_BLOCKS(rows) {
     const int nr = min(kAdjRowBlock, rows - R0);
@@ -562,9 +574,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
       const float2* qr = sq + r * L + kAdjRowPad;
       float s1 = 0.f, s2 = 0.f;
       if (j > 0 && j < W - 1) {
-        for (int c = 0; c < kw; ++c) {
-          const float w = taps[c];
-          const float2 v = ar[j - (c - cx)];
+        const float2* abase = ar + j + cx;  // abase[-c] = abar(j - (c - cx))
+#pragma unroll
+        for (int c = 0; c < KWB; ++c) {
+          const float w = tap_at(taps, c);
+          const float2 v = abase[-c];
           s1 = fmaf(w, v.x, s1);
           s2 = fmaf(w, v.y, s2);
         }
@@ -583,12 +597,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
         }
       }
       const float2 v = ar[j];
+      const float2* qb = qr + j - cx;  // qb[t] = q(j + t - cx)
 #pragma unroll
-      for (int t = 0; t < kAdjRowTaps; ++t) {
-        if (t < kw) {
-          const float2 qq = qr[j + t - cx];
-          acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
-        }
+      for (int t = 0; t < KWB; ++t) {
+        const float2 qq = qb[t];
+        acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
       }
       const size_t idx = (size_t)R0 * W + it;
       const float bv = b[idx], fv = f0[idx];
@@ -608,7 +621,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
       const float* ur = su + r * L + kAdjRowPad;
       float sacc = 0.f;
       if (j > 0 && j < W - 1) {
-        for (int c = 0; c < kw; ++c) sacc = fmaf(taps[c], br[j + (c - cx)], sacc);
+        const float* bbase = br + j - cx;  // bbase[c] = bbar(j + (c - cx))
+#pragma unroll
+        for (int c = 0; c < KWB; ++c) sacc = fmaf(tap_at(taps, c), bbase[c], sacc);
       } else {
         for (int c = 0; c < kw; ++c) {
           int lo, hi;
@@ -620,14 +635,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
       }
       Uacc[(size_t)R0 * W + it] += sacc;
       const float bv = br[j];
+      const float* ubase = ur + j + cx;  // ubase[-t] = u(j - (t - cx))
 #pragma unroll
-      for (int t = 0; t < kAdjRowTaps; ++t)
-        if (t < kw) acc[t] = fmaf(bv, ur[j - (t - cx)], acc[t]);
+      for (int t = 0; t < KWB; ++t) acc[t] = fmaf(bv, ubase[-t], acc[t]);
     }
   }
   block_reduce_add(part + blockIdx.x, asum);
 #pragma unroll
-  for (int t = 0; t < kAdjRowTaps; ++t)
+  for (int t = 0; t < KWB; ++t)
     if (t < kw) block_reduce_add(part + (size_t)(1 + t) * gridDim.x + blockIdx.x, acc[t]);
 }
 
@@ -896,11 +911,19 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const size_t rowlen = ((size_t)W + 2 * kAdjRowPad) * kAdjRowBlock;
   const size_t smab = rowlen * 12, smrev = rowlen * 24;
   const bool rowk = kw <= kAdjRowTaps && smrev <= 227 * 1024;
+  auto fwd_rows = k_adj_fwd_rows<32>;
+  auto rev_rows = k_adj_rev_rows<32>;
+  switch (row_taps_bucket(kw)) {
+    case 8: fwd_rows = k_adj_fwd_rows<8>; rev_rows = k_adj_rev_rows<8>; break;
+    case 16: fwd_rows = k_adj_fwd_rows<16>; rev_rows = k_adj_rev_rows<16>; break;
+    case 24: fwd_rows = k_adj_fwd_rows<24>; rev_rows = k_adj_rev_rows<24>; break;
+    default: break;
+  }
   if (rowk) {
     if (smrev > 48 * 1024)
-      ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smrev));
+      ADJ_CHECK(cudaFuncSetAttribute(rev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smrev));
     if (smab > 48 * 1024)
-      ADJ_CHECK(cudaFuncSetAttribute(k_adj_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
+      ADJ_CHECK(cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
   }
 
   // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)
@@ -918,7 +941,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     for (int k = k0; k + 1 < k1; ++k) {  // rebuild the segment's iterates
       float* uk = seg + (size_t)(k - k0) * n;
       if (rowk) {
-        ADJ_LAUNCH(k_adj_fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
+        ADJ_LAUNCH(fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
       } else {
         ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
         ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
@@ -928,8 +951,8 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     for (int k = k1 - 1; k >= k0; --k) {  // reverse steps
       const float* uk = seg + (size_t)(k - k0) * n;
       if (rowk) {
-        ADJ_LAUNCH(k_adj_fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
-        ADJ_LAUNCH(k_adj_rev_rows<<<G, T, smrev, s>>>(ubar, uk, ab, g, q, b, f0, im, uacc, dbar, f0bar, part));
+        ADJ_LAUNCH(fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
+        ADJ_LAUNCH(rev_rows<<<G, T, smrev, s>>>(ubar, uk, ab, g, q, b, f0, im, uacc, dbar, f0bar, part));
         ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
         ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part + G, ntaps, G, grad_taps));
       } else {
