@@ -431,6 +431,36 @@ __device__ __forceinline__ void load_row_taps(float* taps, const AdjImage& im) {
 // stay out of registers, which the row kernels need for occupancy).
 __device__ __forceinline__ float tap_at(const float* taps, int c) { return *((volatile const float*)taps + c); }
 
+// Exact transpose of a clamped one-row sum at a row end (j = 0: first, or
+// j = n - 1): sum over taps c of w[c] times the sum of x over the clamp's
+// preimage of the shift sgn (c - cx).  At j = 0 the preimage of a shift s
+// is [0, min(-s, n-1)] (empty for s > 0), at j = n - 1 it is
+// [max(n-1-s, 0), n-1] (empty for s < 0).  With d = |s| the preimages of
+// the taps with nonempty ranges are nested, so one running prefix (suffix)
+// sum visits every x once: O(kw) per end pixel.
+__device__ __forceinline__ float2 x_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float x_add(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 x_fma(float w, float2 a, float2 acc) {
+  return make_float2(fmaf(w, a.x, acc.x), fmaf(w, a.y, acc.y));
+}
+__device__ __forceinline__ float x_fma(float w, float a, float acc) { return fmaf(w, a, acc); }
+template <typename T>
+__device__ T row_end_transpose(const T* x, const float* taps, int kw, int cx, int n, bool first, int sgn) {
+  T out = zero_of(T());
+  if (n == 1) {
+    for (int c = 0; c < kw; ++c) out = x_fma(taps[c], x[0], out);
+    return out;
+  }
+  const int dmax = (first == (sgn > 0)) ? cx : kw - 1 - cx;
+  const int e = first ? -sgn : sgn;  // tap c = cx + e d
+  T run = zero_of(T());
+  for (int d = 0; d <= dmax; ++d) {
+    if (d < n) run = x_add(run, x[first ? d : n - 1 - d]);
+    out = x_fma(taps[cx + e * d], run, out);
+  }
+  return out;
+}
+
 // Smallest tap-loop length of the row kernels that holds kw taps.
 inline int row_taps_bucket(int kw) { return kw <= 8 ? 8 : kw <= 16 ? 16 : kw <= 24 ? 24 : 32; }
 
@@ -583,18 +613,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
           s2 = fmaf(w, v.y, s2);
         }
       } else {
-        for (int c = 0; c < kw; ++c) {
-          int lo, hi;
-          preimage(j, c - cx, W, &lo, &hi);
-          float z1 = 0.f, z2 = 0.f;
-          for (int jj = lo; jj <= hi; ++jj) {
-            const float2 v = ar[jj];
-            z1 += v.x;
-            z2 += v.y;
-          }
-          s1 = fmaf(taps[c], z1, s1);
-          s2 = fmaf(taps[c], z2, s2);
-        }
+        const float2 z = row_end_transpose<float2>(ar, taps, kw, cx, W, j == 0, +1);
+        s1 = z.x;
+        s2 = z.y;
       }
       const float2 v = ar[j];
       const float2* qb = qr + j - cx;  // qb[t] = q(j + t - cx)
@@ -625,13 +646,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
 #pragma unroll
         for (int c = 0; c < KWB; ++c) sacc = fmaf(tap_at(taps, c), bbase[c], sacc);
       } else {
-        for (int c = 0; c < kw; ++c) {
-          int lo, hi;
-          preimage(j, -(c - cx), W, &lo, &hi);
-          float z = 0.f;
-          for (int jj = lo; jj <= hi; ++jj) z += br[jj];
-          sacc = fmaf(taps[c], z, sacc);
-        }
+        sacc = row_end_transpose<float>(br, taps, kw, cx, W, j == 0, -1);
       }
       Uacc[(size_t)R0 * W + it] += sacc;
       const float bv = br[j];
