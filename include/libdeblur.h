@@ -156,7 +156,10 @@ db_status db_deblur(const float* f, float* u, int H, int W, int ld,
  * Outputs: grad_f = dLoss/df (written, pitch ld); grad_taps (kh*kw doubles),
  * grad_alpha and grad_K (one double each) are ACCUMULATED (+=) over the
  * batch; the caller zeroes them.  The iterates inside a checkpoint segment
- * are recomputed; all reductions are deterministic. */
+ * are recomputed once, with their intermediates (b, q, A, B, g) kept for the
+ * segment's reverse steps: the workspace holds about (64 + 28 ckpt_every)
+ * bytes per pixel of the batch plus fixed terms (db_backward_workspace_bytes);
+ * all reductions are deterministic. */
 size_t db_backward_workspace_bytes(int H, int W, int batch, const db_psf* psf, int ckpt_every);
 db_status db_rrl_backward(const float* f, const float* ckpt, const float* grad_u, int H, int W, int ld,
                           int batch, const db_psf* psf, const db_params* p, int iters, int ckpt_every,

@@ -833,10 +833,12 @@ static AdjLayout adj_layout(int N, int H, int W, int kw, int ntaps, int every) {
   auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
   L.f0 = take(n * 4);
   L.seg = take(n * 4 * (size_t)(every + 1));
-  L.b = take(n * 4);
-  L.q = take(n * 8);
-  L.ab = take(n * 8);
-  L.g = take(n * 4);
+  // forward intermediates of every iterate of a segment (computed while the
+  // segment is rebuilt, read again by its reverse steps)
+  L.b = take(n * 4 * (size_t)every);
+  L.q = take(n * 8 * (size_t)every);
+  L.ab = take(n * 8 * (size_t)every);
+  L.g = take(n * 4 * (size_t)every);
   L.ubar = take(n * 4);
   L.uacc = take(n * 4);
   L.abbar = take(n * 8);
@@ -895,10 +897,14 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const size_t n = (size_t)N * H * W;  // all images, packed
   float* f0 = (float*)(base + L.f0);
   float* seg = (float*)(base + L.seg);
-  float* b = (float*)(base + L.b);
+  float* b = (float*)(base + L.b);      // every x n (per iterate of a segment)
   float2* q = (float2*)(base + L.q);
   float2* ab = (float2*)(base + L.ab);
   float* g = (float*)(base + L.g);
+  float* const L_b = b;
+  float2* const L_q = q;
+  float2* const L_ab = ab;
+  float* const L_g = g;
   float* ubar = (float*)(base + L.ubar);
   float* uacc = (float*)(base + L.uacc);
   float2* abbar = (float2*)(base + L.abbar);
@@ -953,26 +959,30 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     const size_t hw = (size_t)H * W;
     ADJ_CHECK(cudaMemcpy2DAsync(seg, hw * 4, ckpt + (size_t)sg * hw, (size_t)nseg * hw * 4, hw * 4, N,
                                 cudaMemcpyDeviceToDevice, s));
-    for (int k = k0; k + 1 < k1; ++k) {  // rebuild the segment's iterates
+    // the segment's iterates u_k and their intermediates b, q, (A, B), g
+    for (int k = k0; k < k1; ++k) {
       float* uk = seg + (size_t)(k - k0) * n;
+      const size_t z = (size_t)(k - k0) * n;
       if (rowk) {
-        ADJ_LAUNCH(fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
+        ADJ_LAUNCH(fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b + z, q + z, ab + z, g + z));
       } else {
-        ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
-        ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
+        ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b + z, q + z));
+        ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q + z, im, ab + z, g + z));
       }
-      ADJ_LAUNCH(k_adj_fwd_update<<<G, T, 0, s>>>(uk, ab, g, im, uk + n));
+      if (k + 1 < k1) ADJ_LAUNCH(k_adj_fwd_update<<<G, T, 0, s>>>(uk, ab + z, g + z, im, uk + n));
     }
     for (int k = k1 - 1; k >= k0; --k) {  // reverse steps
       const float* uk = seg + (size_t)(k - k0) * n;
+      const size_t z = (size_t)(k - k0) * n;
+      const float* b = L_b + z;
+      const float2* q = L_q + z;
+      const float2* ab = L_ab + z;
+      const float* g = L_g + z;
       if (rowk) {
-        ADJ_LAUNCH(fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b, q, ab, g));
         ADJ_LAUNCH(rev_rows<<<G, T, smrev, s>>>(ubar, uk, ab, g, q, b, f0, im, uacc, dbar, f0bar, part));
         ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
         ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part + G, ntaps, G, grad_taps));
       } else {
-        ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b, q));
-        ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q, im, ab, g));
         ADJ_LAUNCH(k_adj_rev_update<<<G, T, 0, s>>>(ubar, uk, ab, g, im, uacc, abbar, dbar, part));
         ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
         ADJ_LAUNCH(k_adj_rev_corrT<<<G, T, 0, s>>>(abbar, q, im, qbar, part));
