@@ -35,7 +35,7 @@ struct BatchImg {
   const TapGroup* groups;
   const int* ngroups;
   int ldf, ldA, ldB, ldq;
-  int H, W, kh, kw, ng_max, M, P;
+  int H, W, kh, kw, ng_max, P;
   int box;       // 0: tap groups; 1, 2: horizontal, vertical box (sliding-window sums);
                  // 3, 4: other horizontal, vertical one-axis PSF (register windows)
   RrlParams p;
@@ -43,17 +43,17 @@ struct BatchImg {
 
 constexpr int kBTH = 32, kBTW = 64, kBR = 8;  // tiles of the split schedule
 
-template <int M, int P>
+template <int P>
 __device__ __noinline__ void batch_q(unsigned char* smem, const BatchImg& im, const float* src, int lds,
                                      int i0, int j0) {
-  q_tile<kBTH, kBTW, kBR, M, P>(smem, im.f, im.ldf, src, lds, im.q, im.ldq, im.H, im.W, im.groups,
+  q_tile<kBTH, kBTW, kBR, P>(smem, im.f, im.ldf, src, lds, im.q, im.ldq, im.H, im.W, im.groups,
                                 im.ngroups, im.kh, im.kw, im.ng_max, im.p, i0, j0);
 }
 
-template <int M, int P>
+template <int P>
 __device__ __noinline__ void batch_u(unsigned char* smem, const BatchImg& im, const float* src, int lds,
                                      float* dst, int ldd, int* status, int i0, int j0) {
-  update_tile<kBTH, kBTW, kBR, M, P>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.groups,
+  update_tile<kBTH, kBTW, kBR, P>(smem, im.q, im.ldq, src, lds, dst, ldd, im.H, im.W, im.groups,
                                      im.ngroups, im.kh, im.kw, im.ng_max, im.p, status, i0, j0);
 }
 
@@ -68,14 +68,12 @@ __device__ __noinline__ void batch_box(int phase, unsigned char* smem, const Bat
                                                  im.p, status, i0, j0);
 }
 
-template <int M>
-__device__ __forceinline__ void batch_tile_m(int phase, unsigned char* smem, const BatchImg& im,
-                                             const float* src, int lds, float* dst, int ldd, int* status,
-                                             int i0, int j0) {
-#define DB_BATCH_CASE(PV)                                              \
-  case PV:                                                             \
-    if (phase == 0) batch_q<M, PV>(smem, im, src, lds, i0, j0);        \
-    else batch_u<M, PV>(smem, im, src, lds, dst, ldd, status, i0, j0); \
+__device__ __forceinline__ void batch_tile(int phase, unsigned char* smem, const BatchImg& im, const float* src,
+                                           int lds, float* dst, int ldd, int* status, int i0, int j0) {
+#define DB_BATCH_CASE(PV)                                           \
+  case PV:                                                          \
+    if (phase == 0) batch_q<PV>(smem, im, src, lds, i0, j0);        \
+    else batch_u<PV>(smem, im, src, lds, dst, ldd, status, i0, j0); \
     break;
   switch (im.P) {
     DB_BATCH_CASE(8)
@@ -146,11 +144,7 @@ __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict
         else if (im.box == 2) batch_box<false, true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else if (im.box == 3) batch_box<true, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else if (im.box == 4) batch_box<false, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
-        else switch (im.M) {
-          case 1: batch_tile_m<1>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
-          case 2: batch_tile_m<2>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
-          default: batch_tile_m<3>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z); break;
-        }
+        else batch_tile(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         __syncthreads();
       }
       if (!grid_barrier(bar, gridDim.x, status, spin_limit)) return;
@@ -312,7 +306,6 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.groups = groups; bi.ngroups = ngroups;
     bi.ldf = x.ld; bi.H = x.H; bi.W = x.W; bi.kh = kh; bi.kw = kw;
     bi.ng_max = max_tap_groups(kh, kw);
-    bi.M = tap_group_height(kh);
     bi.P = split_halo_class(kw);
     const int axis = axis_mode(x.psf.kind, kh, kw);
     bi.box = axis == 0 ? 0 : (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);

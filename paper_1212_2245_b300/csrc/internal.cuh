@@ -7,13 +7,22 @@
 
 namespace db {
 
-// A run of up to three vertically adjacent taps of one PSF column: weights
-// w[k] at offsets (dy0 + k, dx) from the origin (unused weights are 0).
+// A run of up to kMaxGroupH vertically adjacent taps of one PSF column:
+// weights w[k] at offsets (dy0 + k, dx) from the origin (weights beyond the
+// group's height are 0).  Groups are stored sorted by height; the height
+// classes are delimited by the class starts (group_class_starts).
+constexpr int kMaxGroupH = 7;
 struct TapGroup {
-  float w[3];
+  float w[7];  // kMaxGroupH <= 7
   int16_t dy0, dx;
 };
-static_assert(sizeof(TapGroup) == 16, "TapGroup is 16 bytes");
+static_assert(sizeof(TapGroup) == 32, "TapGroup is 32 bytes");
+// Shared-memory record of a group: (w0, w1, w2, offset bits), (w3 .. w6).
+constexpr int kGroupRecordBytes = 32;
+// Class starts written by k_prepare_taps next to the group count: starts[m-1]
+// is the first group of height m, starts[kMaxGroupH] the group count.
+__host__ __device__ inline const int* group_class_starts(const int* ngroups) { return ngroups + 264; }
+__host__ __device__ inline int* group_class_starts(int* ngroups) { return ngroups + 264; }
 
 // RRRL parameters as the kernels consume them.
 struct RrlParams {
@@ -72,7 +81,8 @@ void count_launch(int n = 1);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Bytes k_prepare_taps writes next to the tap groups: the group count (int),
-// at +16 the box weights (e0, w, e1, L), at +32 the taps of a one-axis PSF.
+// at +16 the box weights (e0, w, e1, L), at +32 the taps of a one-axis PSF,
+// at +1056 the group class starts (kMaxGroupH + 1 ints).
 constexpr size_t kAuxBytes = 1280;
 // Form of the split and flow tiles for a PSF: 0 tap groups, 1 box
 // (sliding-window sums), 2 other one-axis PSF of length >= one_axis_min()
@@ -108,7 +118,6 @@ cudaError_t copy_images(const float* src, int lds, long long zsrc, float* dst, i
                         int n, cudaStream_t s);
 
 // ---- launchers (return cudaError_t of the launch) --------------------------
-int tap_group_height(int kh);
 int max_tap_groups(int kh, int kw);
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s);

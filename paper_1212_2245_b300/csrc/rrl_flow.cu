@@ -71,9 +71,9 @@ __device__ bool flow_wait(const FlowArgs& a, const int* cnt, int bi, int bj, int
   return __all_sync(0xffffffffu, ok);
 }
 
-// AX: 0 tap groups (M, P); 1, 2 horizontal, vertical box; 3, 4 horizontal,
-// vertical one-axis PSF with register windows.
-template <int M, int P, int AX>
+// AX: 0 tap groups (halo class P); 1, 2 horizontal, vertical box; 3, 4
+// horizontal, vertical one-axis PSF with register windows.
+template <int P, int AX>
 __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a)
     constexpr bool HORIZ = AX == 1 || AX == 3, BOX = AX <= 2;
     if (phase == 0) {
       if constexpr (AX == 0)
-        q_tile<kFTH, kFTW, kFR, M, P>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.groups, a.ngroups, a.kh,
+        q_tile<kFTH, kFTW, kFR, P>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.groups, a.ngroups, a.kh,
                                       a.kw, a.ng_max, a.p, bi * kFTH, bj * kFTW);
       else
         q_tile_box<kFTH, kFTW, kFR, HORIZ, BOX>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.ngroups, a.p,
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a)
       float* dst = even ? a.B : a.A;
       const int ldd = even ? a.ldB : a.ldA;
       if constexpr (AX == 0)
-        update_tile<kFTH, kFTW, kFR, M, P>(smem, a.q, a.ldq, src, lds, dst, ldd, a.H, a.W, a.groups, a.ngroups,
+        update_tile<kFTH, kFTW, kFR, P>(smem, a.q, a.ldq, src, lds, dst, ldd, a.H, a.W, a.groups, a.ngroups,
                                            a.kh, a.kw, a.ng_max, a.p, a.status, bi * kFTH, bj * kFTW);
       else
         update_tile_box<kFTH, kFTW, kFR, HORIZ, BOX>(smem, a.q, a.ldq, src, lds, dst, ldd, a.H, a.W, a.ngroups,
@@ -136,9 +136,9 @@ size_t flow_ws_bytes(int H, int W) { return (size_t)(2 * flow_tiles(H, W) + 64) 
 static long long g_flow_spin = 4000000000LL;  // ~2 s at 2 GHz
 void set_flow_spin_limit(long long cycles) { g_flow_spin = cycles; }
 
-template <int M, int P, int AX = 0>
-static cudaError_t launch_flow_mp(FlowArgs a, size_t smem, cudaStream_t s) {
-  auto kern = k_rrl_flow<M, P, AX>;
+template <int P, int AX = 0>
+static cudaError_t launch_flow_p(FlowArgs a, size_t smem, cudaStream_t s) {
+  auto kern = k_rrl_flow<P, AX>;
   cudaError_t e;
   if (smem > 48 * 1024 &&
       (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -168,15 +168,14 @@ static cudaError_t launch_flow_mp(FlowArgs a, size_t smem, cudaStream_t s) {
   return cudaSuccess;
 }
 
-template <int M>
-static cudaError_t launch_flow_m(const FlowArgs& a, size_t smem, cudaStream_t s) {
+static cudaError_t launch_flow_groups(const FlowArgs& a, size_t smem, cudaStream_t s) {
   switch (split_halo_class(a.kw)) {
-    case 8: return launch_flow_mp<M, 8>(a, smem, s);
-    case 16: return launch_flow_mp<M, 16>(a, smem, s);
-    case 32: return launch_flow_mp<M, 32>(a, smem, s);
-    case 64: return launch_flow_mp<M, 64>(a, smem, s);
-    case 128: return launch_flow_mp<M, 128>(a, smem, s);
-    default: return launch_flow_mp<M, 256>(a, smem, s);
+    case 8: return launch_flow_p<8>(a, smem, s);
+    case 16: return launch_flow_p<16>(a, smem, s);
+    case 32: return launch_flow_p<32>(a, smem, s);
+    case 64: return launch_flow_p<64>(a, smem, s);
+    case 128: return launch_flow_p<128>(a, smem, s);
+    default: return launch_flow_p<256>(a, smem, s);
   }
 }
 
@@ -215,17 +214,13 @@ cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* u
   if (axis) {
     const int ax = (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
     switch (ax) {
-      case 1: e = launch_flow_mp<1, 8, 1>(a, smem, s); break;
-      case 2: e = launch_flow_mp<1, 8, 2>(a, smem, s); break;
-      case 3: e = launch_flow_mp<1, 8, 3>(a, smem, s); break;
-      default: e = launch_flow_mp<1, 8, 4>(a, smem, s); break;
+      case 1: e = launch_flow_p<8, 1>(a, smem, s); break;
+      case 2: e = launch_flow_p<8, 2>(a, smem, s); break;
+      case 3: e = launch_flow_p<8, 3>(a, smem, s); break;
+      default: e = launch_flow_p<8, 4>(a, smem, s); break;
     }
   } else {
-    switch (tap_group_height(kh)) {
-      case 1: e = launch_flow_m<1>(a, smem, s); break;
-      case 2: e = launch_flow_m<2>(a, smem, s); break;
-      default: e = launch_flow_m<3>(a, smem, s); break;
-    }
+    e = launch_flow_groups(a, smem, s);
   }
   if (e != cudaSuccess) (void)cudaGetLastError();
   return e;

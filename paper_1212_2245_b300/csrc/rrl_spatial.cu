@@ -28,43 +28,55 @@ namespace db {
 // ---------------------------------------------------------------------------
 // tap preparation: validate the dense taps and build the tap groups.
 //
-// A group is a run of up to M vertically adjacent taps of one PSF column:
-// weights w[0..M-1] for offsets (dy0 + k, dx).  Within a column, a group
-// starts at the first non-zero tap not yet covered (moved up so that it ends
-// inside the PSF) and taps it covers twice get weight 0 in the later group.
-// Every non-zero tap lands in exactly one group, with its own weight.
+// A group is a run of up to kMaxGroupH vertically adjacent rows of one PSF
+// column, starting and ending on a non-zero tap: weights w[0..h-1] for
+// offsets (dy0 + k, dx).  Within a column, a group starts at the first
+// non-zero tap not yet covered.  The cluster from there (non-zero taps at
+// most one zero row apart) becomes one group if it has at most kMaxGroupH
+// rows, otherwise the first of ceil(n / kMaxGroupH) nearly equal parts
+// (ending on its last non-zero tap).  Every non-zero tap lands in exactly
+// one group, with its own weight; a column of kh rows yields at most
+// ceil(kh / 3) groups (a group either spans at least 4 rows or ends a
+// cluster, which is followed by at least 2 zero rows).  Groups are written
+// sorted by height (then by column, then top to bottom), with the class
+// starts next to the group count.
 // ---------------------------------------------------------------------------
-template <bool WRITE>
-__device__ int column_groups(const float* __restrict__ taps, int kh, int kw, int b, int M,
-                             TapGroup* out) {
-  const int cy = kh >> 1, cx = kw >> 1;
-  int covered = -1, n = 0;
+__device__ __forceinline__ bool tap_nz(const float* __restrict__ taps, int kw, int r, int b) {
+  return __ldg(taps + r * kw + b) != 0.f;
+}
+
+// The group of column b that starts after row `covered`: first row s and
+// height h (h = 0: no non-zero tap left).
+__device__ void next_group(const float* __restrict__ taps, int kh, int kw, int b, int covered, int* s_out,
+                           int* h_out) {
+  int s = -1;
+  for (int r = covered + 1; r < kh; ++r)
+    if (tap_nz(taps, kw, r, b)) { s = r; break; }
+  *s_out = s;
+  if (s < 0) { *h_out = 0; return; }
+  int e = s;
   while (true) {
-    int s = -1;
-    for (int r = covered + 1; r < kh; ++r)
-      if (__ldg(taps + r * kw + b) != 0.f) { s = r; break; }
-    if (s < 0) break;
-    const int st = min(s, kh - M);
-    if (WRITE) {
-      TapGroup g;
-      for (int k = 0; k < 3; ++k) {
-        const int r = st + k;
-        g.w[k] = (k < M && r > covered && r < kh) ? __ldg(taps + r * kw + b) : 0.f;
-      }
-      g.dy0 = (int16_t)(st - cy);
-      g.dx = (int16_t)(b - cx);
-      out[n] = g;
-    }
-    ++n;
-    covered = st + M - 1;
+    int nxt = -1;
+    for (int r = e + 1; r < kh && r <= e + 2; ++r)
+      if (tap_nz(taps, kw, r, b)) { nxt = r; break; }
+    if (nxt < 0) break;
+    e = nxt;
   }
-  return n;
+  const int n = e - s + 1;
+  int h = n;
+  if (n > kMaxGroupH) {
+    const int parts = (n + kMaxGroupH - 1) / kMaxGroupH;
+    h = (n + parts - 1) / parts;
+    while (!tap_nz(taps, kw, s + h - 1, b)) --h;
+  }
+  *h_out = h;
 }
 
 __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ taps, int kh, int kw,
-                                                      int kind, int M, TapGroup* __restrict__ groups,
+                                                      int kind, int max_groups, TapGroup* __restrict__ groups,
                                                       int* __restrict__ ngroups, int* status) {
   __shared__ int scan[256];
+  __shared__ int cstart[kMaxGroupH + 1];
   __shared__ float warp_sum[8];
   __shared__ int bad;
   const int n = kh * kw;
@@ -89,37 +101,77 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
     for (int k = threadIdx.x; k < n; k += blockDim.x) reinterpret_cast<float*>(ngroups + 8)[k] = __ldg(taps + k);
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) warp_sum[wid] = sum;
-  // one thread per PSF column (kw <= 255): count, exclusive scan, write
+  // one thread per PSF column (kw <= 255): groups per height class, then
+  // per class an exclusive scan over the columns
   const int b = threadIdx.x;
-  const int cnt = (b < kw) ? column_groups<false>(taps, kh, kw, b, M, nullptr) : 0;
-  scan[threadIdx.x] = cnt;
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const int v = (threadIdx.x >= o) ? scan[threadIdx.x - o] : 0;
+  int cnt[kMaxGroupH];
+#pragma unroll
+  for (int m = 0; m < kMaxGroupH; ++m) cnt[m] = 0;
+  if (b < kw) {
+    int covered = -1, s0, h;
+    while (true) {
+      next_group(taps, kh, kw, b, covered, &s0, &h);
+      if (h == 0) break;
+#pragma unroll
+      for (int m = 0; m < kMaxGroupH; ++m) cnt[m] += (h == m + 1);
+      covered = s0 + h - 1;
+    }
+  }
+  int pos[kMaxGroupH];
+  if (threadIdx.x == 0) cstart[0] = 0;
+#pragma unroll
+  for (int m = 0; m < kMaxGroupH; ++m) {
     __syncthreads();
-    scan[threadIdx.x] += v;
+    scan[threadIdx.x] = cnt[m];
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+      const int v = (threadIdx.x >= o) ? scan[threadIdx.x - o] : 0;
+      __syncthreads();
+      scan[threadIdx.x] += v;
+      __syncthreads();
+    }
+    pos[m] = scan[threadIdx.x] - cnt[m];  // within the class
+    if (threadIdx.x == 0) cstart[m + 1] = cstart[m] + scan[255];
     __syncthreads();
   }
-  if (b < kw) column_groups<true>(taps, kh, kw, b, M, groups + scan[threadIdx.x] - cnt);
+  const int total = cstart[kMaxGroupH];
+  if (total > max_groups) {
+    if (threadIdx.x == 0) atomicOr(&bad, DB_FLAG_TAPS);
+  } else if (b < kw) {
+    const int cy = kh >> 1, cx = kw >> 1;
+    int covered = -1, s0, h;
+    while (true) {
+      next_group(taps, kh, kw, b, covered, &s0, &h);
+      if (h == 0) break;
+      TapGroup g;
+#pragma unroll
+      for (int k = 0; k < kMaxGroupH; ++k) g.w[k] = k < h ? __ldg(taps + (s0 + k) * kw + b) : 0.f;
+      g.dy0 = (int16_t)(s0 - cy);
+      g.dx = (int16_t)(b - cx);
+      int slot = 0;
+#pragma unroll
+      for (int m = 0; m < kMaxGroupH; ++m)
+        if (h == m + 1) slot = cstart[m] + pos[m]++;
+      groups[slot] = g;
+      covered = s0 + h - 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x <= kMaxGroupH) group_class_starts(ngroups)[threadIdx.x] = total > max_groups ? 0 : cstart[threadIdx.x];
   if (threadIdx.x == 0) {
     float s = 0.f;
     for (int i = 0; i < 8; ++i) s += warp_sum[i];
     if (!(s > 0.f)) bad |= DB_FLAG_TAPS;
-    *ngroups = scan[255];
+    *ngroups = total > max_groups ? 0 : total;
     if (bad && status) atomicOr(status, bad);
   }
 }
 
-int tap_group_height(int kh) { return kh < 3 ? kh : 3; }
-
-int max_tap_groups(int kh, int kw) {
-  const int M = tap_group_height(kh);
-  return kw * ((kh + M - 1) / M);
-}
+int max_tap_groups(int kh, int kw) { return kw * ((kh + 2) / 3); }
 
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s) {
-  k_prepare_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, tap_group_height(kh), groups, ngroups, status);
+  k_prepare_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, max_tap_groups(kh, kw), groups, ngroups, status);
   count_launch();
   return cudaGetLastError();
 }
@@ -147,7 +199,7 @@ struct ZStride {
   long long f, in, out, q;
 };
 
-template <int TH, int TW, int R, int M, int P>
+template <int TH, int TW, int R, int P>
 __global__ void __launch_bounds__((TH / R) * TW, 8) k_rrl_q(const float* __restrict__ f, int ldf,
                                                const float* __restrict__ uin, int ldin,
                                                float2* __restrict__ q, int ldq, int H, int W,
@@ -156,11 +208,11 @@ __global__ void __launch_bounds__((TH / R) * TW, 8) k_rrl_q(const float* __restr
                                                int ng_max, RrlParams p, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long z = blockIdx.z;
-  q_tile<TH, TW, R, M, P>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W, groups_g,
+  q_tile<TH, TW, R, P>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W, groups_g,
                           ngroups_g, kh, kw, ng_max, p, blockIdx.y * TH, blockIdx.x * TW, PdlDep());
 }
 
-template <int TH, int TW, int R, int M, int P>
+template <int TH, int TW, int R, int P>
 __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* __restrict__ q, int ldq,
                                                     const float* __restrict__ uin, int ldin,
                                                     float* __restrict__ uout, int ldout, int H, int W,
@@ -169,7 +221,7 @@ __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* _
                                                     int ng_max, RrlParams p, int* status, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long z = blockIdx.z;
-  update_tile<TH, TW, R, M, P>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H, W,
+  update_tile<TH, TW, R, P>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H, W,
                                groups_g, ngroups_g, kh, kw, ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW,
                                PdlDep());
 }
@@ -223,7 +275,7 @@ size_t rrl_spatial_smem(int kh, int kw) {
   const int QHp = ((kTH + kh - 1 + kR - 1) / kR) * kR;
   const int UH = Ry + (QHp > kTH + 2 ? QHp : kTH + 2);
   const size_t us = (size_t)(UH * (kTW + 2 * P) + 1) & ~size_t(1);
-  return (size_t)2 * ng_max * sizeof(float4) + us * sizeof(float) + (size_t)QHp * (kTW + P) * sizeof(float2);
+  return 32 + (size_t)2 * ng_max * kGroupRecordBytes + us * sizeof(float) + (size_t)QHp * (kTW + P) * sizeof(float2);
 }
 static size_t split_smem_q_single(int kh, int kw, int ng_max) {
   return split_smem_q(kQTH, kQTW, kh, kw, ng_max);
@@ -253,12 +305,12 @@ struct IterArgs {
   ZStride zs;
 };
 
-template <int M, int P>
-static cudaError_t launch_fused_mp(const IterArgs& a, cudaStream_t s) {
+template <int P>
+static cudaError_t launch_fused_p(const IterArgs& a, cudaStream_t s) {
   const int ng_max = max_tap_groups(a.kh, a.kw);
   const size_t smem = rrl_spatial_smem(a.kh, a.kw);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  auto kern = k_rrl_spatial<kTH, kTW, kR, M, P>;
+  auto kern = k_rrl_spatial<kTH, kTW, kR, P>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH), dim3(64, 4), smem, s>>>(
@@ -268,13 +320,13 @@ static cudaError_t launch_fused_mp(const IterArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int M, int P>
-static cudaError_t launch_split_mp(const IterArgs& a, cudaStream_t s) {
+template <int P>
+static cudaError_t launch_split_p(const IterArgs& a, cudaStream_t s) {
   const int ng_max = a.ng_bound > 0 ? a.ng_bound : max_tap_groups(a.kh, a.kw);
   const size_t sq = split_smem_q_single(a.kh, a.kw, ng_max), su = split_smem_update_single(a.kh, a.kw, ng_max);
   if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
-  auto kq = k_rrl_q<kQTH, kQTW, kR, M, P>;
-  auto ku = k_rrl_update<kUTH, kUTW, kR, M, P>;
+  auto kq = k_rrl_q<kQTH, kQTW, kR, P>;
+  auto ku = k_rrl_update<kUTH, kUTW, kR, P>;
   cudaError_t e;
   if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
   if ((e = set_smem(ku, su)) != cudaSuccess) return e;
@@ -359,24 +411,15 @@ size_t rrl_box_smem(int kh, int kw) {
   return a > b ? a : b;
 }
 
-template <bool SPLIT, int M>
-static cudaError_t dispatch_p(const IterArgs& a, cudaStream_t s) {
-  switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
-    case 8: return SPLIT ? launch_split_mp<M, 8>(a, s) : launch_fused_mp<M, 8>(a, s);
-    case 16: return SPLIT ? launch_split_mp<M, 16>(a, s) : launch_fused_mp<M, 16>(a, s);
-    case 32: return SPLIT ? launch_split_mp<M, 32>(a, s) : launch_fused_mp<M, 32>(a, s);
-    case 64: return SPLIT ? launch_split_mp<M, 64>(a, s) : launch_fused_mp<M, 64>(a, s);
-    case 128: return SPLIT ? launch_split_mp<M, 128>(a, s) : launch_fused_mp<M, 128>(a, s);
-    default: return SPLIT ? launch_split_mp<M, 256>(a, s) : launch_fused_mp<M, 256>(a, s);
-  }
-}
-
 template <bool SPLIT>
 static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
-  switch (tap_group_height(a.kh)) {
-    case 1: return dispatch_p<SPLIT, 1>(a, s);
-    case 2: return dispatch_p<SPLIT, 2>(a, s);
-    default: return dispatch_p<SPLIT, 3>(a, s);
+  switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
+    case 8: return SPLIT ? launch_split_p<8>(a, s) : launch_fused_p<8>(a, s);
+    case 16: return SPLIT ? launch_split_p<16>(a, s) : launch_fused_p<16>(a, s);
+    case 32: return SPLIT ? launch_split_p<32>(a, s) : launch_fused_p<32>(a, s);
+    case 64: return SPLIT ? launch_split_p<64>(a, s) : launch_fused_p<64>(a, s);
+    case 128: return SPLIT ? launch_split_p<128>(a, s) : launch_fused_p<128>(a, s);
+    default: return SPLIT ? launch_split_p<256>(a, s) : launch_fused_p<256>(a, s);
   }
 }
 

@@ -36,54 +36,128 @@ __device__ __forceinline__ float2 weighted_residual(float b, float f, const RrlP
   return make_float2(__fdividef(w * (f - b), b), w);
 }
 
-// b[r] = (u*h) at R vertically adjacent pixels.  `base` points at the u
-// value that the first pixel's strip starts from; each group record holds
-// three weights and the shared-memory offset of its first load.
-template <int R, int M, int STRIDE>
-__device__ __forceinline__ void blur_strip(const float* __restrict__ base,
-                                           const float4* __restrict__ grp, int ng, float (&b)[R]) {
-  constexpr int stride = STRIDE;
-#pragma unroll
-  for (int r = 0; r < R; ++r) b[r] = 0.f;
-#pragma unroll 2
-  for (int g = 0; g < ng; ++g) {
-    const float4 G = grp[g];
-    const float* pu = base + __float_as_int(G.w);
-    float v[R + M - 1];
-#pragma unroll
-    for (int t = 0; t < R + M - 1; ++t) v[t] = pu[t * stride];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      b[r] = fmaf(G.x, v[r + M - 1], b[r]);
-      if (M > 1) b[r] = fmaf(G.y, v[r + M - 2], b[r]);
-      if (M > 2) b[r] = fmaf(G.z, v[r + M - 3], b[r]);
-    }
+// ---------------------------------------------------------------------------
+// tap groups in shared memory
+//
+// Each group is staged as two float4: (w0, w1, w2, offset of its first load
+// as int bits) and (w3 .. w6).  Groups are sorted by height, so the strip
+// sums run one loop per height class with compile-time height M: a group
+// loaded once from shared memory feeds M*R (blur) or 2*M*R (correlation)
+// FMAs from R+M-1 shared loads.  `cls` holds the class starts (kMaxGroupH+1
+// ints, staged next to the records).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stage_group(float4* dst, const TapGroup& t, int off) {
+  dst[0] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(off));
+  dst[1] = make_float4(t.w[3], t.w[4], t.w[5], t.w[6]);
+}
+
+// Height of group g (classes delimited by cls).
+__device__ __forceinline__ int group_height(const int* cls, int g) {
+  int m = 1;
+  while (m < kMaxGroupH && g >= cls[m]) ++m;
+  return m;
+}
+
+// Stage the class starts and the records of all groups; off(t, m) gives a
+// group's offset from its tap group and height.
+template <typename Off>
+__device__ __forceinline__ void stage_groups(int* cls_s, float4* rec, const TapGroup* __restrict__ groups_g,
+                                             const int* __restrict__ ngroups_g, Off off) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  const int* cls_g = group_class_starts(ngroups_g);
+  if (tid <= kMaxGroupH) cls_s[tid] = __ldg(cls_g + tid);
+  const int ng = __ldg(ngroups_g);
+  for (int g = tid; g < ng; g += nth) {
+    const TapGroup t = groups_g[g];
+    int m = 1;
+    while (m < kMaxGroupH && g >= __ldg(cls_g + m)) ++m;
+    stage_group(rec + 2 * g, t, off(t, m));
   }
 }
 
-// Delta[r] = (e*h*), B[r] = (W*h*) at R vertically adjacent pixels.
+template <int M>
+__device__ __forceinline__ void group_weights(const float4* __restrict__ rec, float (&w)[kMaxGroupH], int& off) {
+  const float4 A = rec[0];
+  w[0] = A.x; w[1] = A.y; w[2] = A.z;
+  off = __float_as_int(A.w);
+  if (M > 3) {
+    const float4 B = rec[1];
+    w[3] = B.x; w[4] = B.y; w[5] = B.z;
+    if (kMaxGroupH > 6) w[6] = B.w;
+  }
+}
+
+// b[r] += (u*h) over the groups g0..g1-1 of height M, at R vertically
+// adjacent pixels; `base` points at the u value the first pixel's strip
+// starts from.
 template <int R, int M, int STRIDE>
-__device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
-                                                const float4* __restrict__ grp, int ng, float (&dl)[R],
-                                                float (&B)[R]) {
-  constexpr int stride = STRIDE;
-#pragma unroll
-  for (int r = 0; r < R; ++r) { dl[r] = 0.f; B[r] = 0.f; }
+__device__ __forceinline__ void blur_class(const float* __restrict__ base, const float4* __restrict__ rec, int g0,
+                                           int g1, float (&b)[R]) {
 #pragma unroll 2
-  for (int g = 0; g < ng; ++g) {
-    const float4 G = grp[g];
-    const float2* pq = base + __float_as_int(G.w);
+  for (int g = g0; g < g1; ++g) {
+    float w[kMaxGroupH];
+    int off;
+    group_weights<M>(rec + 2 * g, w, off);
+    const float* pu = base + off;
+    float v[R + M - 1];
+#pragma unroll
+    for (int t = 0; t < R + M - 1; ++t) v[t] = pu[t * STRIDE];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int k = 0; k < M; ++k) b[r] = fmaf(w[k], v[r + M - 1 - k], b[r]);
+  }
+}
+
+template <int R, int STRIDE>
+__device__ __forceinline__ void blur_strip(const float* __restrict__ base, const float4* __restrict__ rec,
+                                           const int* __restrict__ cls, float (&b)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) b[r] = 0.f;
+  blur_class<R, 1, STRIDE>(base, rec, cls[0], cls[1], b);
+  blur_class<R, 2, STRIDE>(base, rec, cls[1], cls[2], b);
+  blur_class<R, 3, STRIDE>(base, rec, cls[2], cls[3], b);
+  blur_class<R, 4, STRIDE>(base, rec, cls[3], cls[4], b);
+  blur_class<R, 5, STRIDE>(base, rec, cls[4], cls[5], b);
+  if constexpr (kMaxGroupH >= 6) blur_class<R, 6, STRIDE>(base, rec, cls[5], cls[6], b);
+  if constexpr (kMaxGroupH >= 7) blur_class<R, 7, STRIDE>(base, rec, cls[6], cls[7], b);
+}
+
+// Delta[r] += (e*h*), B[r] += (W*h*) over the groups of height M.
+template <int R, int M, int STRIDE>
+__device__ __forceinline__ void correlate_class(const float2* __restrict__ base, const float4* __restrict__ rec,
+                                                int g0, int g1, float (&dl)[R], float (&B)[R]) {
+#pragma unroll 2
+  for (int g = g0; g < g1; ++g) {
+    float w[kMaxGroupH];
+    int off;
+    group_weights<M>(rec + 2 * g, w, off);
+    const float2* pq = base + off;
     float2 v[R + M - 1];
 #pragma unroll
-    for (int t = 0; t < R + M - 1; ++t) v[t] = pq[t * stride];
+    for (int t = 0; t < R + M - 1; ++t) v[t] = pq[t * STRIDE];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      dl[r] = fmaf(G.x, v[r].x, dl[r]);
-      B[r] = fmaf(G.x, v[r].y, B[r]);
-      if (M > 1) { dl[r] = fmaf(G.y, v[r + 1].x, dl[r]); B[r] = fmaf(G.y, v[r + 1].y, B[r]); }
-      if (M > 2) { dl[r] = fmaf(G.z, v[r + 2].x, dl[r]); B[r] = fmaf(G.z, v[r + 2].y, B[r]); }
-    }
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        dl[r] = fmaf(w[k], v[r + k].x, dl[r]);
+        B[r] = fmaf(w[k], v[r + k].y, B[r]);
+      }
   }
+}
+
+template <int R, int STRIDE>
+__device__ __forceinline__ void correlate_strip(const float2* __restrict__ base, const float4* __restrict__ rec,
+                                                const int* __restrict__ cls, float (&dl)[R], float (&B)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) { dl[r] = 0.f; B[r] = 0.f; }
+  correlate_class<R, 1, STRIDE>(base, rec, cls[0], cls[1], dl, B);
+  correlate_class<R, 2, STRIDE>(base, rec, cls[1], cls[2], dl, B);
+  correlate_class<R, 3, STRIDE>(base, rec, cls[2], cls[3], dl, B);
+  correlate_class<R, 4, STRIDE>(base, rec, cls[3], cls[4], dl, B);
+  correlate_class<R, 5, STRIDE>(base, rec, cls[4], cls[5], dl, B);
+  if constexpr (kMaxGroupH >= 6) correlate_class<R, 6, STRIDE>(base, rec, cls[5], cls[6], dl, B);
+  if constexpr (kMaxGroupH >= 7) correlate_class<R, 7, STRIDE>(base, rec, cls[6], cls[7], dl, B);
 }
 
 // Diffusion term D = div(psi'(|grad u|^2) grad u) (Eq. 11) at R vertically
@@ -144,9 +218,10 @@ __device__ __forceinline__ float rrl_update(float u, float dl, float B, float D,
 // fused iteration, register blocked.
 //
 // Each thread owns a vertical strip of R q-points (phase 1) or R outputs
-// (phase 2) in one column, so a tap group loaded once from shared memory
-// feeds M*R (phase 1) or 2*M*R (phase 2) FMAs from R+M-1 shared loads.
-// Lanes of a warp own adjacent columns: shared accesses are conflict-free.
+// (phase 2) in one column, so a tap group of height M loaded once from
+// shared memory feeds M*R (phase 1) or 2*M*R (phase 2) FMAs from R+M-1
+// shared loads.  Lanes of a warp own adjacent columns: shared accesses are
+// conflict-free.
 //
 // Geometry (virtual rows/cols may lie outside the image):
 //   q tile : rows i0-cy .. i0-cy+QHp-1, cols j0-cx .. j0-cx+QW-1
@@ -155,7 +230,7 @@ __device__ __forceinline__ float rrl_update(float u, float dl, float B, float D,
 // position from the clamped u and then, at virtual positions outside the
 // image, replaced by q at the clamped position.
 // ---------------------------------------------------------------------------
-template <int TH, int TW, int R, int M, int P>
+template <int TH, int TW, int R, int P>
 __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict__ f, int ldf,
                                                      const float* __restrict__ uin, int ldin,
                                                      float* __restrict__ uout, int ldout, int H, int W,
@@ -172,21 +247,18 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
   const int QH = TH + kh - 1, QW = TW + kw - 1;
   const int NQS = (QH + R - 1) / R, QHp = NQS * R;
   const int UH = Ry + max(QHp, TH + 2);
-  const int ng = *ngroups_g;
-  float4* gu = (float4*)smem_raw;
-  float4* gq = gu + ng_max;
-  float* us = (float*)(gq + ng_max);
+  int* cls = (int*)smem_raw;
+  float4* gu = (float4*)(smem_raw + 32);
+  float4* gq = gu + 2 * ng_max;
+  float* us = (float*)(gq + 2 * ng_max);
   float2* qs = (float2*)(us + ((UH * US + 1) & ~1));
   const int i0 = blockIdx.y * TH, j0 = blockIdx.x * TW;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
 
-  for (int g = tid; g < ng; g += nth) {
-    const TapGroup t = groups_g[g];
-    const int offu = (Ry - cy - t.dy0 - (M - 1)) * US + (Rx - cx - t.dx);
-    const int offq = (cy + t.dy0) * QS + (cx + t.dx);
-    gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
-    gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
-  }
+  stage_groups(cls, gu, groups_g, ngroups_g,
+               [&](const TapGroup& t, int m) { return (Ry - cy - t.dy0 - (m - 1)) * US + (Rx - cx - t.dx); });
+  stage_groups(cls, gq, groups_g, ngroups_g,
+               [&](const TapGroup& t, int m) { return (cy + t.dy0) * QS + (cx + t.dx); });
   for (int r = threadIdx.y; r < UH; r += blockDim.y) {
     const int gi = min(max(i0 - Ry + r, 0), H - 1);
     const float* src = uin + (size_t)gi * ldin;
@@ -208,7 +280,7 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
       fv[r] = fmaxf(__ldg(f + (size_t)ai * ldf + aj), p.floor);
     }
     float b[R];
-    blur_strip<R, M, US>(us + qr0 * US + qc, gu, ng, b);
+    blur_strip<R, US>(us + qr0 * US + qc, gu, cls, b);
 #pragma unroll
     for (int r = 0; r < R; ++r) qs[(qr0 + r) * QS + qc] = weighted_residual(b[r], fv[r], p);
   }
@@ -231,7 +303,7 @@ __global__ void __launch_bounds__(256, 2) k_rrl_spatial(const float* __restrict_
     const int s = item / TW, oj = item - s * TW;
     const int oi0 = s * R, j = j0 + oj;
     float dl[R], B[R], D[R], c[R];
-    correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
+    correlate_strip<R, QS>(qs + oi0 * QS + oj, gq, cls, dl, B);
     diffusion_strip<R, US>(us + (oi0 + Ry) * US + (oj + Rx), p, D, c);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -266,13 +338,15 @@ __host__ __device__ inline int split_halo_class(int kw) {
   while (P < kw + 2) P *= 2;
   return P;
 }
-// Shared memory of one split tile of TH x TW outputs.
+// Shared memory of one split tile of TH x TW outputs (class starts, group
+// records, staged images).
+__host__ __device__ inline size_t groups_smem(int ng_max) { return 32 + (size_t)ng_max * kGroupRecordBytes; }
 __host__ __device__ inline size_t split_smem_q(int TH, int TW, int kh, int kw, int ng_max) {
-  return (size_t)ng_max * 16 + (size_t)TH * TW * sizeof(float) +
+  return groups_smem(ng_max) + (size_t)TH * TW * sizeof(float) +
          (size_t)(TH + kh - 1) * (TW + split_halo_class(kw)) * sizeof(float);
 }
 __host__ __device__ inline size_t split_smem_update(int TH, int TW, int kh, int kw, int ng_max) {
-  return (size_t)ng_max * 16 + (size_t)(TH + kh - 1) * (TW + split_halo_class(kw)) * 8 +
+  return groups_smem(ng_max) + (size_t)(TH + kh - 1) * (TW + split_halo_class(kw)) * 8 +
          (size_t)(TH + 4) * (TW + 8) * sizeof(float);
 }
 
@@ -331,7 +405,7 @@ struct NoDep {
 };
 
 // q = (e, W) on the TH x TW tile at (i0, j0).  smem_raw: split_smem_q bytes.
-template <int TH, int TW, int R, int M, int P, typename Dep = NoDep>
+template <int TH, int TW, int R, int P, typename Dep = NoDep>
 __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __restrict__ f, int ldf,
                                        const float* __restrict__ uin, int ldin,
                                        float2* __restrict__ q, int ldq, int H, int W,
@@ -345,16 +419,13 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
   const int UH = TH + kh - 1;
   const int xs = (j0 - Tx) & ~3, ox = (j0 - Tx) - xs;  // staged window starts at column xs
   const int nc = (TW + kw - 1 + ox + 3) >> 2;
-  const int ng = *ngroups_g;
-  float4* gu = (float4*)smem_raw;
-  float* fs = (float*)(gu + ng_max);  // TH x TW
+  int* cls = (int*)smem_raw;
+  float4* gu = (float4*)(smem_raw + 32);
+  float* fs = (float*)(gu + 2 * ng_max);  // TH x TW
   float* us = fs + TH * TW;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  for (int g = tid; g < ng; g += nth) {
-    const TapGroup t = groups_g[g];
-    const int offu = (Ty - t.dy0 - (M - 1)) * US + (Tx + ox - t.dx);
-    gu[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offu));
-  }
+  stage_groups(cls, gu, groups_g, ngroups_g,
+               [&](const TapGroup& t, int m) { return (Ty - t.dy0 - (m - 1)) * US + (Tx + ox - t.dx); });
   stage_tile<float, TW>(fs, f, ldf, H, W, i0, TH, j0, TW / 4, rows_aligned16(f, ldf));
   dep();
   stage_tile<float, US>(us, uin, ldin, H, W, i0 - Ty, UH, xs, nc, rows_aligned16(uin, ldin));
@@ -365,7 +436,7 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
     const int s = item / TW, c = item - s * TW;
     const int r0 = s * R, j = j0 + c;
     float b[R];
-    blur_strip<R, M, US>(us + r0 * US + c, gu, ng, b);
+    blur_strip<R, US>(us + r0 * US + c, gu, cls, b);
     float2* qo = q + (size_t)(i0 + r0) * ldq + j;
     if (full) {
 #pragma unroll
@@ -380,7 +451,7 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
 
 // Delta, B, D and the update on the TH x TW tile at (i0, j0).
 // smem_raw: split_smem_update bytes.
-template <int TH, int TW, int R, int M, int P, typename Dep = NoDep>
+template <int TH, int TW, int R, int P, typename Dep = NoDep>
 __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float2* __restrict__ q, int ldq,
                                             const float* __restrict__ uin, int ldin,
                                             float* __restrict__ uout, int ldout, int H, int W,
@@ -394,16 +465,13 @@ __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float
   constexpr int QS = TW + P, UH = TH + 4, US = TW + 8;  // row strides, P >= kw + 2
   const int xq = (j0 - cx) & ~1, oq = (j0 - cx) - xq;    // q window starts at column xq
   const int ncq = (TW + kw - 1 + oq + 1) >> 1;
-  const int ng = *ngroups_g;
-  float4* gq = (float4*)smem_raw;
-  float2* qs = (float2*)(gq + ng_max);
+  int* cls = (int*)smem_raw;
+  float4* gq = (float4*)(smem_raw + 32);
+  float2* qs = (float2*)(gq + 2 * ng_max);
   float* us = (float*)(qs + QH * QS);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  for (int g = tid; g < ng; g += nth) {
-    const TapGroup t = groups_g[g];
-    const int offq = (cy + t.dy0) * QS + (cx + oq + t.dx);
-    gq[g] = make_float4(t.w[0], t.w[1], t.w[2], __int_as_float(offq));
-  }
+  stage_groups(cls, gq, groups_g, ngroups_g,
+               [&](const TapGroup& t, int m) { return (cy + t.dy0) * QS + (cx + oq + t.dx); });
   // u(clamp) with a 2-pixel halo (staged from column j0 - 4 so that every
   // chunk is aligned), then q(clamp) over the correlation footprint
   stage_tile<float, US>(us, uin, ldin, H, W, i0 - 2, UH, j0 - 4, TW / 4 + 2, rows_aligned16(uin, ldin));
@@ -417,7 +485,7 @@ __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float
     const int s = item / TW, oj = item - s * TW;
     const int oi0 = s * R, j = j0 + oj;
     float dl[R], B[R], D[R], c[R];
-    correlate_strip<R, M, QS>(qs + oi0 * QS + oj, gq, ng, dl, B);
+    correlate_strip<R, QS>(qs + oi0 * QS + oj, gq, cls, dl, B);
     diffusion_strip<R, US>(us + (oi0 + 2) * US + (oj + 4), p, D, c);
     float* uo = uout + (size_t)(i0 + oi0) * ldout + j;
 #pragma unroll
