@@ -149,12 +149,22 @@ __global__ void __launch_bounds__(256, 4) k_fourier_cols(float2* __restrict__ bu
   cp_async_wait_all();
   __syncthreads();
   fft_dif_blk(x, logH, C, C, 1, tw, true);
-  for (int idx = threadIdx.x; idx < H * C; idx += blockDim.x) {
-    const int k = idx / C, c = idx - k * C;
-    if (c0 + c < W) {
-      float2* d = x + fft_pad(k) * C + c;
-      const float2 sv = __ldg(S + (size_t)k * W + c0 + c);
-      *d = CONJ ? cmulc(*d, sv) : cmul(*d, sv);
+  // the spectrum in batches of kSBatch loads per thread, issued together
+  constexpr int kSBatch = 8;
+  for (int base = threadIdx.x; base < H * C; base += kSBatch * blockDim.x) {
+    float2 sv[kSBatch];
+#pragma unroll
+    for (int t = 0; t < kSBatch; ++t) {
+      const int idx = base + t * blockDim.x, k = idx / C, c = idx - k * C;
+      sv[t] = (idx < H * C && c0 + c < W) ? __ldg(S + (size_t)k * W + c0 + c) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < kSBatch; ++t) {
+      const int idx = base + t * blockDim.x, k = idx / C, c = idx - k * C;
+      if (idx < H * C && c0 + c < W) {
+        float2* d = x + fft_pad(k) * C + c;
+        *d = CONJ ? cmulc(*d, sv[t]) : cmul(*d, sv[t]);
+      }
     }
   }
   __syncthreads();
