@@ -386,6 +386,67 @@ __global__ void k_adj_rev_diff2(const float2* __restrict__ a, AdjImage im, float
   }
 }
 
+// Both diffusion passes in one launch: a CTA takes kDiffRows rows of one
+// image, forms pass 1 (flux part of U, and (ah, av)) on those rows and the
+// row above and below into shared memory, then pass 2 on its own rows, and
+// adds both parts to U once.  The halo rows are formed twice (by both
+// neighbouring CTAs) instead of going through global memory.
+constexpr int kDiffRows = 4;
+__host__ __device__ inline size_t diff_smem(int W) { return (size_t)W * (8 * (kDiffRows + 2) + 4 * kDiffRows); }
+
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_diff(const float* __restrict__ Dbar,
+                                                             const float* __restrict__ u,
+                                                             const float* __restrict__ g, AdjImage im,
+                                                             float* __restrict__ Uacc) {
+  extern __shared__ __align__(16) unsigned char diff_sm[];
+  const int H = im.H, W = im.W;
+  float2* sa = (float2*)diff_sm;                    // rows i0-1 .. i0+kDiffRows of (ah, av)
+  float* sub = (float*)(sa + (kDiffRows + 2) * W);  // rows i0 .. of the flux part
+  const int nblk = (H + kDiffRows - 1) / kDiffRows;
+  for (int blk = blockIdx.x; blk < im.N * nblk; blk += gridDim.x) {
+    const int n = blk / nblk, i0 = (blk - n * nblk) * kDiffRows, i1 = min(i0 + kDiffRows, H);
+    const float* ui = u + (size_t)n * H * W;
+    const float* gi = g + (size_t)n * H * W;
+    const float* di = Dbar + (size_t)n * H * W;
+    __syncthreads();  // the previous block's reads of sa and sub are done
+    for (int i = max(i0 - 1, 0); i < min(i1 + 1, H); ++i) {
+      for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const int p = i * W + j;
+        const float up = ui[p], gp = gi[p], dp = di[p];
+        float ub = 0.f, gb = 0.f;
+        if (j + 1 < W) { const int q = p + 1; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
+        if (j > 0)     { const int q = p - 1; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
+        if (i + 1 < H) { const int q = p + W; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
+        if (i > 0)     { const int q = p - W; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
+        // psi''(s) = -psi'(s)^3 / 2 for TV; 0 for linear diffusion
+        const float sbar = im.p.psi_tv ? gb * (-0.5f * gp * gp * gp) : 0.f;
+        const float dxu = 0.5f * (ui[i * W + clampi(j + 1, W)] - ui[i * W + clampi(j - 1, W)]);
+        const float dyu = 0.5f * (ui[clampi(i + 1, H) * W + j] - ui[clampi(i - 1, H) * W + j]);
+        sa[(i - i0 + 1) * W + j] = make_float2(sbar * dxu, sbar * dyu);
+        if (i >= i0 && i < i1) sub[(i - i0) * W + j] = ub;
+      }
+    }
+    __syncthreads();
+    for (int i = i0; i < i1; ++i) {
+      const float2* a = sa + (i - i0 + 1) * W;  // row i; a - W: row i-1, a + W: row i+1
+      for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        float s = 0.f;
+        // east neighbour of (i, j-1) is (i, j); of (i, W-1) itself
+        if (j >= 1) s += a[j - 1].x;
+        if (j == W - 1) s += a[j].x;
+        // west neighbour of (i, j+1) is (i, j); of (i, 0) itself
+        if (j <= W - 2) s -= a[j + 1].x;
+        if (j == 0) s -= a[j].x;
+        if (i >= 1) s += a[j - W].y;
+        if (i == H - 1) s += a[j].y;
+        if (i <= H - 2) s -= a[j + W].y;
+        if (i == 0) s -= a[j].y;
+        Uacc[(size_t)n * H * W + (size_t)i * W + j] += sub[(i - i0) * W + j] + s;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Row kernels for one-row PSFs with kw <= kAdjRowTaps.  With kh == 1 the
 // blur, the correlation and their transposes act along rows only, so a CTA
@@ -548,7 +609,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
 //   U += C^T bbar                             (as k_adj_rev_convT)
 // with the alpha partial in part[0 .. G) and the tap partials (both
 // transposes, summed per tap) in part[G + t G ...].  The diffusion adjoint
-// (k_adj_rev_diff1/2) follows: it needs Dbar of the neighbouring rows.
+// (k_adj_rev_diff) follows: it needs Dbar of the neighbouring rows.
 template <int KWB>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
     const float* __restrict__ Ubar_next, const float* __restrict__ u, const float2* __restrict__ ab,
@@ -947,6 +1008,10 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
       ADJ_CHECK(cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
   }
 
+  const size_t smdiff = diff_smem(W);
+  if (smdiff > 48 * 1024 && smdiff <= 227 * 1024)
+    ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_diff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smdiff));
+
   // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)
   ADJ_LAUNCH(k_floor_pack<<<G, T, 0, s>>>(f, ld, N * H, W, p->pos_floor, f0));
   ADJ_LAUNCH(k_copy_pitched<<<G, T, 0, s>>>(grad_u, ld, ubar, W, N * H, W, nullptr, 0.f));
@@ -991,8 +1056,12 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
         ADJ_LAUNCH(k_adj_rev_convT<<<G, T, 0, s>>>(bbar, uk, im, uacc, part));
         ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
       }
-      ADJ_LAUNCH(k_adj_rev_diff1<<<G, T, 0, s>>>(dbar, uk, g, im, uacc, av));
-      ADJ_LAUNCH(k_adj_rev_diff2<<<G, T, 0, s>>>(av, im, uacc));
+      if (smdiff <= 227 * 1024) {
+        ADJ_LAUNCH(k_adj_rev_diff<<<G, T, smdiff, s>>>(dbar, uk, g, im, uacc));
+      } else {
+        ADJ_LAUNCH(k_adj_rev_diff1<<<G, T, 0, s>>>(dbar, uk, g, im, uacc, av));
+        ADJ_LAUNCH(k_adj_rev_diff2<<<G, T, 0, s>>>(av, im, uacc));
+      }
       float* t = ubar; ubar = uacc; uacc = t;
     }
   }
