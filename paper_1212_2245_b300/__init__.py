@@ -410,7 +410,7 @@ def rrl_iterate_noalloc(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, pa
 
 
 def set_schedule(name: str):
-    """Kernel schedule of the spatial iteration: "auto", "fused" or "split"."""
+    """Kernel schedule of the spatial iteration: "auto", "fused", "split" or "flow"."""
     code = {"auto": _lib.SCHED_AUTO, "fused": _lib.SCHED_FUSED, "split": _lib.SCHED_SPLIT,
             "flow": _lib.SCHED_FLOW}[name]
     _check(_lib.load().db_set_schedule(code), "db_set_schedule")
