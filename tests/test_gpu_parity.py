@@ -300,6 +300,35 @@ def test_box_sliding_window_matches_oracle(lib, L, axis, H, W):
     assert_close(u, ug.double().cpu().numpy(), "box vs tap groups")
 
 
+def _sparse_psf(kind, rng):
+    if kind == "random":      # irregular zero gaps: clusters of every length
+        h = rng.uniform(0.1, 1.0, (15, 11)) * (rng.random((15, 11)) < 0.45)
+    elif kind == "tall":      # columns longer than a group: split into parts
+        h = rng.uniform(0.1, 1.0, (41, 3))
+    elif kind == "dotted":    # taps one and two zero rows apart
+        h = np.zeros((13, 5))
+        h[[0, 2, 4, 7, 10, 12], :] = rng.uniform(0.1, 1.0, (6, 5))
+    else:                     # checkerboard
+        h = ((np.add.outer(np.arange(9), np.arange(9)) % 2) == 0) * rng.uniform(0.1, 1.0, (9, 9))
+    h[h.shape[0] // 2, h.shape[1] // 2] += 0.5
+    return (h / h.sum()).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["random", "tall", "dotted", "checker"])
+def test_tap_groups_of_every_height_match_oracle(lib, kind, sched):
+    """PSFs whose columns cut into tap groups of every height 1..7 (zero gaps
+    of one and two rows, columns longer than a group): the grouped sums
+    against the oracle's direct sums, in every schedule."""
+    rng = np.random.default_rng({"random": 1, "tall": 2, "dotted": 3, "checker": 4}[kind])
+    h = _sparse_psf(kind, rng)
+    H, W = 77, 131
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, 4, p, seed=5)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 4)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 4)
+    assert_close(u, ref, f"{kind} {h.shape}")
+
+
 @pytest.mark.parametrize("L", [1, 2, 7, 8, 9, 16, 33, 100, 255])
 @pytest.mark.parametrize("axis", ["row", "col"])
 def test_one_axis_register_windows_match_oracle(lib, L, axis):
