@@ -44,7 +44,7 @@ struct FourierArgs {
 __device__ __forceinline__ float robust_weight_f(float b, float f, const RrlParams& p) {
   if (!p.phi_robust) return 1.0f;
   const float r = rf_divergence(b, f, p);
-  return p.eps_phi * rsqrtf(fmaxf(r, 0.0f) + p.eps_phi * p.eps_phi);
+  return p.eps_phi * rsqrtf(fmaf(p.eps_phi, p.eps_phi, fmaxf(r, 0.0f)));  // explicit FMA: same rounding in every kernel shape
 }
 
 __device__ __forceinline__ float diffusivity_f(float gx, float gy, const RrlParams& p) {

@@ -228,18 +228,20 @@ __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* _
 
 // one-axis PSFs: the same split pair with sliding-window sums (box) or
 // register-window tap sums (rrl_box.cuh)
-template <bool HORIZ, bool BOX>
+// Tiles of TH x 32 outputs (TH = 32, or 16 for images with fewer 32 x 32
+// tiles than SMs), 128 threads with strips of TH / 4 rows.
+template <bool HORIZ, bool BOX, int TH>
 __global__ void __launch_bounds__(128) k_rrl_q_box(const float* __restrict__ f, int ldf,
                                                   const float* __restrict__ uin, int ldin, float2* __restrict__ q,
                                                   int ldq, int H, int W, const int* __restrict__ ngroups_g,
                                                   RrlParams p, ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long z = blockIdx.z;
-  q_tile_box<32, 32, 8, HORIZ, BOX>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W,
-                               ngroups_g, p, blockIdx.y * 32, blockIdx.x * 32, PdlDep());
+  q_tile_box<TH, 32, TH / 4, HORIZ, BOX>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H,
+                                         W, ngroups_g, p, blockIdx.y * TH, blockIdx.x * 32, PdlDep());
 }
 
-template <bool HORIZ, bool BOX>
+template <bool HORIZ, bool BOX, int TH>
 __global__ void __launch_bounds__(128) k_rrl_update_box(const float2* __restrict__ q, int ldq,
                                                        const float* __restrict__ uin, int ldin,
                                                        float* __restrict__ uout, int ldout, int H, int W,
@@ -247,8 +249,9 @@ __global__ void __launch_bounds__(128) k_rrl_update_box(const float2* __restrict
                                                        ZStride zs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long z = blockIdx.z;
-  update_tile_box<32, 32, 8, HORIZ, BOX>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H,
-                                    W, ngroups_g, p, status, blockIdx.y * 32, blockIdx.x * 32, PdlDep());
+  update_tile_box<TH, 32, TH / 4, HORIZ, BOX>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out,
+                                              ldout, H, W, ngroups_g, p, status, blockIdx.y * TH, blockIdx.x * 32,
+                                              PdlDep());
 }
 
 // ---------------------------------------------------------------------------
@@ -356,13 +359,25 @@ static cudaError_t launch_split_p(const IterArgs& a, cudaStream_t s) {
   return cudaSuccess;
 }
 
-template <bool HORIZ, bool BOX>
-static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      n = v;
+    else
+      n = 148;
+  }
+  return n;
+}
+
+template <bool HORIZ, bool BOX, int TH>
+static cudaError_t launch_split_box_th(const IterArgs& a, cudaStream_t s) {
   const int L = HORIZ ? a.kw : a.kh;
-  const size_t sq = box_smem_q(32, 32, L, HORIZ), su = box_smem_update(32, 32, L, HORIZ);
+  const size_t sq = box_smem_q(TH, 32, L, HORIZ), su = box_smem_update(TH, 32, L, HORIZ);
   if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
-  auto kq = k_rrl_q_box<HORIZ, BOX>;
-  auto ku = k_rrl_update_box<HORIZ, BOX>;
+  auto kq = k_rrl_q_box<HORIZ, BOX, TH>;
+  auto ku = k_rrl_update_box<HORIZ, BOX, TH>;
   cudaError_t e;
   if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
   if ((e = set_smem(ku, su)) != cudaSuccess) return e;
@@ -371,7 +386,7 @@ static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(32, 4);
-  cfg.gridDim = dim3((a.W + 31) / 32, (a.H + 31) / 32, a.nz);
+  cfg.gridDim = dim3((a.W + 31) / 32, (a.H + TH - 1) / TH, a.nz);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -386,6 +401,12 @@ static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
     return e;
   count_launch();
   return cudaSuccess;
+}
+
+template <bool HORIZ, bool BOX>
+static cudaError_t launch_split_box(const IterArgs& a, cudaStream_t s) {
+  const long long tiles = (long long)((a.W + 31) / 32) * ((a.H + 31) / 32) * a.nz;
+  return tiles < sm_count() ? launch_split_box_th<HORIZ, BOX, 16>(a, s) : launch_split_box_th<HORIZ, BOX, 32>(a, s);
 }
 
 __global__ void k_copy_images(const float* __restrict__ src, int lds, long long zsrc, float* __restrict__ dst,

@@ -27,7 +27,7 @@ namespace db {
 __device__ __forceinline__ float robust_weight(float b, float f, const RrlParams& p) {
   if (!p.phi_robust) return 1.0f;
   const float r = rf_divergence(b, f, p);
-  return p.eps_phi * rsqrtf(fmaxf(r, 0.0f) + p.eps_phi * p.eps_phi);
+  return p.eps_phi * rsqrtf(fmaf(p.eps_phi, p.eps_phi, fmaxf(r, 0.0f)));  // explicit FMA: same rounding in every kernel shape
 }
 
 // (e, W) for one pixel: W = phi'(r_f(b)), e = W (f - b)/b.
@@ -186,8 +186,9 @@ __device__ __forceinline__ void diffusion_strip_t(const float* __restrict__ uc, 
     gC[t] = g2(e1[t] - w1[t], m[t + 2] - m[t]);
   float Fv[R + 1];
 #pragma unroll
-  for (int t = 0; t < R + 1; ++t)  // flux between rows t-1 and t
-    Fv[t] = (gC[t + 1] + gC[t]) * (m[t + 2] - m[t + 1]);
+  for (int t = 0; t < R + 1; ++t)  // flux between rows t-1 and t (rounded on its own, so that
+    // no FMA contraction at a strip's ends makes the result depend on the strip height)
+    Fv[t] = __fmul_rn(gC[t + 1] + gC[t], m[t + 2] - m[t + 1]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const float e2 = uc[r * S + 2], w2 = uc[r * S - 2];
