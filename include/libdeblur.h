@@ -273,7 +273,22 @@ typedef struct db_plan db_plan;
 db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_params* p, int iters, void* ws,
                          size_t ws_bytes, int* dev_status, void* stream, db_plan** out);
 db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, void* stream);
+/* The plan's pipeline on an image in host memory: enqueues the copy of f_host
+ * (H x W, packed) into f_dev (device, pitch ld), db_plan_run(f_dev -> u_dev),
+ * and the copy of u_dev into u_host (H x W, packed), all on `stream`.  The
+ * copies overlap other work only when the host buffers are page-locked
+ * (db_host_alloc); the caller synchronises `stream` before reading u_host.
+ * The buffers stay the caller's.  DB_ERR_ARG for null pointers or
+ * f_dev == u_dev, DB_ERR_CUDA when a copy or launch fails. */
+db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, float* f_dev, float* u_dev,
+                           int* dev_status, void* stream);
 void db_plan_destroy(db_plan* plan);
+
+/* Page-locked host memory for db_plan_run_host (cudaHostAlloc): *out = a
+ * buffer of `bytes` bytes, released with db_host_free.  DB_ERR_ARG for a null
+ * out or zero bytes, DB_ERR_CUDA when the allocation fails (*out = NULL). */
+db_status db_host_alloc(size_t bytes, void** out);
+void db_host_free(void* p);
 
 /* Human-readable name of a status code (static storage). */
 const char* db_status_string(db_status s);

@@ -10,13 +10,14 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _lib
 from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
-           "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "set_schedule", "set_one_axis_min", "set_spin_limit",
+           "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "HostBuffer", "set_schedule", "set_one_axis_min", "set_spin_limit",
            "set_rf_eval", "version", "FrameStream", "deblur_n", "workspace_bytes_n"]
 
 
@@ -237,6 +238,30 @@ class Plan:
             self.ws.raise_on_flags("db_plan_run")
         return u
 
+    def run_host(self, f_host, u_host, check: bool = True, sync: bool = True):
+        """The pipeline on an image in host memory (db_plan_run_host): the
+        copy in, the run and the copy out are enqueued on the current stream,
+        which is synchronised before returning (unless sync=False; then
+        check must be False too).  f_host and u_host are H x W float32 host
+        buffers: HostBuffer (page-locked, the fast path) or contiguous CPU
+        tensors."""
+        if check and not sync:
+            raise ValueError("check=True needs sync=True")
+        H, W = self.shape
+        fp, up = _host_ptr(f_host, (H, W), "f_host"), _host_ptr(u_host, (H, W), "u_host")
+        if getattr(self, "_dev", None) is None:
+            self._dev = (torch.empty(H, self.ld, device="cuda"), torch.empty(H, self.ld, device="cuda"))
+        fd, ud = self._dev
+        if check:
+            self.ws.reset_status()
+        _check(_lib.load().db_plan_run_host(self._h, fp, up, fd.data_ptr(), ud.data_ptr(),
+                                            self.ws.status.data_ptr(), _stream()), "db_plan_run_host")
+        if sync:
+            torch.cuda.current_stream().synchronize()
+        if check:
+            self.ws.raise_on_flags("db_plan_run_host")
+        return u_host
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().db_plan_destroy(self._h)
@@ -247,6 +272,61 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class HostBuffer:
+    """Page-locked host memory from db_host_alloc, viewed as a float32 CPU
+    tensor (`.tensor`, which shares the memory: keep the HostBuffer alive
+    while using it).  Copies from and to it run at the link's full rate."""
+
+    def __init__(self, shape):
+        self.shape = tuple(int(x) for x in shape)
+        n = 1
+        for x in self.shape:
+            n *= x
+        ptr = ctypes.c_void_p()
+        _check(_lib.load().db_host_alloc(max(n, 1) * 4, ctypes.byref(ptr)), "db_host_alloc")
+        self._ptr = ptr
+        arr = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_float)), shape=self.shape)
+        self.tensor = torch.from_numpy(arr)
+
+    @property
+    def ptr(self) -> int:
+        return self._ptr.value
+
+    def copy_from(self, array) -> "HostBuffer":
+        """Fill from a host array of the same shape with one single-threaded
+        copy.  (Rows written by many host threads can sit dirty in the caches
+        of several cores; the device's reads of them then ran five times
+        slower on B300 hosts than after a single-threaded copy.)"""
+        a = np.ascontiguousarray(np.asarray(array, dtype=np.float32))
+        if a.shape != self.shape:
+            raise ValueError(f"shape {a.shape} != {self.shape}")
+        ctypes.memmove(self.ptr, a.ctypes.data, a.nbytes)
+        return self
+
+    def close(self):
+        if getattr(self, "_ptr", None) is not None and self._ptr.value:
+            self.tensor = None
+            _lib.load().db_host_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(buf, shape, what: str) -> int:
+    if isinstance(buf, HostBuffer):
+        if buf.shape != tuple(shape):
+            raise ValueError(f"{what}: shape {buf.shape} != {tuple(shape)}")
+        return buf.ptr
+    if not isinstance(buf, torch.Tensor) or buf.device.type != "cpu" or buf.dtype != torch.float32 \
+            or not buf.is_contiguous() or tuple(buf.shape) != tuple(shape):
+        raise ValueError(f"{what}: expected a contiguous float32 CPU tensor of shape {tuple(shape)} or a HostBuffer")
+    return buf.data_ptr()
 
 
 class Batch:

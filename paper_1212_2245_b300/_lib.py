@@ -63,7 +63,10 @@ SIGNATURES = {
     "db_plan_create": (c_int, [c_int, c_int, c_int, P_PSF, P_PAR, c_int, c_void_p, c_size_t, c_void_p, c_void_p,
                                ctypes.POINTER(c_void_p)]),
     "db_plan_run": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "db_plan_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "db_plan_destroy": (None, [c_void_p]),
+    "db_host_alloc": (c_int, [c_size_t, ctypes.POINTER(c_void_p)]),
+    "db_host_free": (None, [c_void_p]),
     "db_status_string": (c_char_p, [c_int]),
     "db_status_from_flags": (c_int, [c_int]),
     "db_version": (c_char_p, []),

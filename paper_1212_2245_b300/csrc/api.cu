@@ -408,7 +408,33 @@ db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, 
                          dev_status, s, P->ng);
 }
 
+db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, float* f_dev, float* u_dev,
+                           int* dev_status, void* stream) {
+  SinglePlan* P = (SinglePlan*)plan;
+  if (!P || !f_host || !u_host || !f_dev || !u_dev || f_dev == u_dev) return DB_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t row = (size_t)P->W * sizeof(float), pitch = (size_t)P->ld * sizeof(float);
+  if (cudaMemcpy2DAsync(f_dev, pitch, f_host, row, row, P->H, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  const db_status st = db_plan_run(plan, f_dev, u_dev, dev_status, stream);
+  if (st != DB_OK) return st;
+  if (cudaMemcpy2DAsync(u_host, row, u_dev, pitch, row, P->H, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  return DB_OK;
+}
+
 void db_plan_destroy(db_plan* plan) { delete (SinglePlan*)plan; }
+
+db_status db_host_alloc(size_t bytes, void** out) {
+  if (!out) return DB_ERR_ARG;
+  *out = nullptr;
+  if (bytes == 0) return DB_ERR_ARG;
+  return cudaHostAlloc(out, bytes, cudaHostAllocDefault) == cudaSuccess ? DB_OK : DB_ERR_CUDA;
+}
+
+void db_host_free(void* p) {
+  if (p) (void)cudaFreeHost(p);
+}
 
 const char* db_status_string(db_status s) {
   switch (s) {
