@@ -359,16 +359,12 @@ static cudaError_t launch_split_p(const IterArgs& a, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// SM count of the current device (per call: devices may differ).
 static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      n = v;
-    else
-      n = 148;
-  }
-  return n;
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+    return v;
+  return 148;
 }
 
 template <bool HORIZ, bool BOX, int TH>
