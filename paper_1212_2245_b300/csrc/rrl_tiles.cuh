@@ -93,7 +93,7 @@ __device__ __forceinline__ void group_weights(const float4* __restrict__ rec, fl
 template <int R, int M, int STRIDE>
 __device__ __forceinline__ void blur_class(const float* __restrict__ base, const float4* __restrict__ rec, int g0,
                                            int g1, float (&b)[R]) {
-#pragma unroll 2
+#pragma unroll(M > 3 ? 1 : 2)
   for (int g = g0; g < g1; ++g) {
     float w[kMaxGroupH];
     int off;
@@ -127,7 +127,7 @@ __device__ __forceinline__ void blur_strip(const float* __restrict__ base, const
 template <int R, int M, int STRIDE>
 __device__ __forceinline__ void correlate_class(const float2* __restrict__ base, const float4* __restrict__ rec,
                                                 int g0, int g1, float (&dl)[R], float (&B)[R]) {
-#pragma unroll 2
+#pragma unroll(M > 3 ? 1 : 2)
   for (int g = g0; g < g1; ++g) {
     float w[kMaxGroupH];
     int off;
