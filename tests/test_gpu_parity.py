@@ -81,6 +81,20 @@ def test_fourier_iterations_shapes(lib, H, W, psf):
     assert_close(u, ref, f"fourier {psf} {H}x{W}")
 
 
+@pytest.mark.parametrize("H,W", [(16, 4096), (4096, 16)])
+def test_fourier_iterations_at_the_largest_side(lib, H, W):
+    """Periodic iterations on images whose long side is the largest the
+    library takes (4096): row transforms of 4096 points, column passes of
+    4096 points."""
+    rng = np.random.default_rng(H + 3 * W)
+    h = synth.gaussian_mixture_psf(7, rng)
+    p = Params(conv="periodic")
+    f, u0 = _iterate_case(H, W, h, 3, p, seed=9)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 3)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 3)
+    assert_close(u, ref, f"fourier {H}x{W}")
+
+
 def test_fourier_checkpoints_and_pitch(lib):
     H, W, ld = 64, 128, 160
     h = synth.gaussian_mixture_psf(5, np.random.default_rng(3))
@@ -146,6 +160,20 @@ def test_parameter_variants(lib, variant):
     ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 6)
     u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6)
     assert_close(u, ref, str(variant))
+
+
+@pytest.mark.parametrize("H,W", [(16, 4096), (4096, 16), (40, 4095)])
+def test_iterations_at_the_largest_side(lib, H, W, sched):
+    """Spatial iterations and the whole pipeline on images whose long side is
+    the largest the library takes, in every schedule."""
+    h = synth.line_psf(9, 30.0, 10.0)
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, 3, p, seed=13)
+    ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, 3)
+    u = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 3)
+    assert_close(u, ref, f"{H}x{W}")
+    _, u_ref = oracle.wr3l(f, h, p, 3)
+    assert_close(lib.deblur(cuda(f), cuda(h), p, 3), u_ref, f"WR3L {H}x{W}")
 
 
 @pytest.mark.parametrize("H,W,shape", [(128, 256, (1, 15)), (256, 128, (9, 1)), (64, 512, (5, 7)),
