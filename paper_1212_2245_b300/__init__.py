@@ -18,7 +18,7 @@ from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
            "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "HostBuffer", "set_schedule", "set_one_axis_min", "set_spin_limit",
-           "set_rf_eval", "version", "FrameStream", "deblur_n", "workspace_bytes_n"]
+           "set_rf_eval", "version", "FrameStream", "BatchStream", "deblur_n", "workspace_bytes_n"]
 
 
 class DeblurError(RuntimeError):
@@ -515,3 +515,4 @@ def version() -> str:
 
 
 from .stream import FrameStream  # noqa: E402  (uses Plan)
+from .batch_stream import BatchStream  # noqa: E402  (uses Batch)
