@@ -618,10 +618,35 @@ def run_learn(args, world, rank, local):
     ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     ms_f = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     wsn.raise_on_flags("timed forward"); bws.raise_on_flags("timed backward")
+    # end to end: the step's images and targets in from page-locked host
+    # memory, the step (forward, loss gradient, backward), the loss and the
+    # parameter gradients back to the host
+    f_host, g_host = pinned_copy(case.f[mine]), pinned_copy(case.g[mine])
+    out_host = torch.empty(taps.numel() + 3, dtype=torch.float64).pin_memory()
+    out_dev = torch.empty(taps.numel() + 3, dtype=torch.float64, device=dev)
+    e2e = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K + 1)]
+    with torch.cuda.stream(stream):
+        for k in range(K + 1):  # the first pass is untimed (loads the loss kernels)
+            e2e[k][0].record(stream)
+            f.copy_(f_host, non_blocking=True)
+            g.copy_(g_host, non_blocking=True)
+            g_step.replay()
+            if world > 1:
+                shard.combine_param_grads([gt, ga, gk], N, N_all)
+            out_dev[0] = ((u - g) ** 2).mean()
+            out_dev[1:1 + taps.numel()].copy_(gt)
+            out_dev[1 + taps.numel()] = ga[0]
+            out_dev[2 + taps.numel()] = gk[0]
+            out_host.copy_(out_dev, non_blocking=True)
+            e2e[k][1].record(stream)
+            if k == 0:
+                stream.synchronize()
+    torch.cuda.synchronize()
+    e2e_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in e2e[1:])
     if world > 1:
-        t = torch.tensor([ms, ms_f], device=dev)
+        t = torch.tensor([ms, ms_f, e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_f = float(t[0]), float(t[1])
+        ms, ms_f, e2e_ms = float(t[0]), float(t[1]), float(t[2])
     if rank != 0:
         return
     pxi = N_all * H * W * iters
@@ -644,6 +669,9 @@ def run_learn(args, world, rank, local):
                      "frac": ach / (hbm_peak * world),
                      "traffic": None, "kernel": "whole fwd+bwd step (40 B/px*iter algorithmic)",
                      "peak_src": hbm_src},
+        "e2e": {"value": pxi / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * N_all * H * W * 4, "d2h_bytes_per_step": (taps.numel() + 3) * 8,
+                "ms_per_step": e2e_ms},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
