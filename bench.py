@@ -748,6 +748,9 @@ def run_stream(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "frames_per_s": world * n_frames / (ms / 1e3),
         "compute_only_ms": ms_compute, "transfer_overhead": ms / ms_compute - 1.0,
+        # the frames' iterations as in line1024 (per-iteration time from the
+        # compute-only replays, Wiener included: a lower bound of the kernel's rate)
+        "roofline": _spatial_model(case, ms_compute / n_frames / iters, "auto"),
         "e2e": {"value": world * pxi / (ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * n_frames * H * W, "d2h_bytes_per_step": 4 * n_frames * H * W,
                 "ms_per_step": ms},
