@@ -357,7 +357,13 @@ static cudaError_t set_dyn_smem(Kern k, size_t smem) {
 template <int MODE>
 static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
   const int M = 1 << a.D.logM;
-  const int R = M >= 2048 ? 1 : 2048 / M;
+  // up to 2048 / M sequences per CTA, but at least two CTAs per SM where the
+  // rows allow it
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
+  int R = M >= 2048 ? 1 : 2048 / M;
+  while (R > 1 && (a.nrows + R - 1) / R < 2 * sms) R >>= 1;
   const int grid = (a.nrows + R - 1) / R;
   const size_t smem = (size_t)R * M * sizeof(float4) + (size_t)2 * R * a.D.N * sizeof(float);
   cudaError_t e = set_dyn_smem(k_fft_rows<MODE>, smem);
