@@ -61,10 +61,11 @@ __device__ bool flow_wait(const FlowArgs& a, const int* cnt, int bi, int bj, int
     const int ni = bi + idx / nw - a.ry, nj = bj + idx % nw - a.rx;
     if (ni < 0 || ni >= a.ty || nj < 0 || nj >= a.tx) continue;
     const volatile int* c = cnt + ni * a.tx + nj;
+    // polled without a back-off: the waiting warp's CTA has nothing else to
+    // do, and a 32 ns sleep between polls measured 1.3% slower on line1024
     while (*c < need) {
       if (*ab != 0) break;
       if (clock64() - t0 > a.spin_limit) { ok = false; break; }
-      __nanosleep(32);
     }
   }
   __threadfence();
