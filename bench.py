@@ -133,7 +133,7 @@ class ClockSampler:
 # (flow) schedule: one ncu capture of the persistent launch (20 iterations,
 # dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # capture), divided by the iteration count.
-LINE1024_FLOW_ITER_DRAM_BYTES = (8.498432e6 + 1.255168e6) / 20
+LINE1024_FLOW_ITER_DRAM_BYTES = (8.489728e6 + 1.274112e6) / 20
 
 
 def pinned_copy(array):
