@@ -13,9 +13,11 @@
  *   - Images are float32, row-major, H rows x W columns, with a row pitch of
  *     `ld` elements (ld >= W).  Pixel (i, j) is at ptr[i*ld + j].
  *   - All image, tap, workspace and status pointers are DEVICE pointers owned
- *     by the caller.  The library allocates nothing; scratch space is the
- *     caller's workspace `ws` of `ws_bytes` bytes (see db_workspace_bytes),
- *     which must be 256-byte aligned.
+ *     by the caller, except the host images of db_plan_run_host.  The library
+ *     allocates no device memory (db_host_alloc hands out page-locked host
+ *     memory on request; plans and batches keep small host-side records);
+ *     scratch space is the caller's workspace `ws` of `ws_bytes` bytes (see
+ *     db_workspace_bytes), which must be 256-byte aligned.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *     enqueued asynchronously; no entry point synchronises the device.
  *   - Argument errors are returned synchronously as a db_status and nothing is
