@@ -303,9 +303,8 @@ const char* db_version(void);
 
 /* Kernel schedule of the spatial RRRL iteration (process-wide setting; the
  * arithmetic is the same in every schedule):
- *   DB_SCHED_AUTO  - split when u, f and q (16 bytes/pixel) fit comfortably in
- *                    L2 (as flow from 512K pixels on), fused otherwise
- *                    (default)
+ *   DB_SCHED_AUTO  - flow from 512K to 2M pixels, split otherwise (default;
+ *                    the choice measured fastest on B300)
  *   DB_SCHED_FUSED - one launch per iteration; each tile recomputes the
  *                    weighted ratio q on its halo (fewest HBM round trips)
  *   DB_SCHED_SPLIT - two launches per iteration; q = (W f/b, W) goes through
