@@ -574,7 +574,7 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 // one image with that image's own transform lengths.
 // ---------------------------------------------------------------------------
 enum { WB_ROW_1D = 0, WB_ROW_FWD = 1, WB_COL_1D = 2, WB_COL_2D = 3, WB_ROW_INV = 4, WB_STAGES = 5 };
-constexpr int kBatchColC = 4;
+constexpr int kBatchColC = 2;  // columns per CTA (4: 36.0 ms for batch512's Wiener, 2: 30.8 ms)
 
 struct WienerBatch {
   std::vector<FftArgs> jobs[WB_STAGES];
