@@ -72,6 +72,26 @@ __device__ bool flow_wait(const FlowArgs& a, const int* cnt, int bi, int bj, int
   return __all_sync(0xffffffffu, ok);
 }
 
+// Dependency wait run inside a tile body (the tile's hook between the copies
+// of what is ready anyway -- f, the tap records -- and of what the wait
+// guards), so those copies overlap the wait.  Warp 0 polls; a time-out sets
+// the abort flag and DB_FLAG_TIMEOUT.
+struct FlowDep {
+  const FlowArgs* a;
+  const int* cnt;
+  int bi, bj, need;
+  __device__ void operator()() const {
+    if (need > 0 && threadIdx.y == 0) {  // warp 0 (blockDim.x == 32)
+      const bool ok = flow_wait(*a, cnt, bi, bj, need);
+      if (!ok && threadIdx.x == 0) {
+        atomicExch(a->abort_, 1);
+        if (a->status) atomicOr(a->status, DB_FLAG_TIMEOUT);
+      }
+    }
+    __syncthreads();
+  }
+};
+
 // AX: 0 tap groups (halo class P); 1, 2 horizontal, vertical box; 3, 4
 // horizontal, vertical one-axis PSF with register windows.
 template <int P, int AX>
@@ -85,25 +105,21 @@ __global__ void __launch_bounds__((kFTH / kFR) * kFTW, 7) k_rrl_flow(FlowArgs a)
     const int k = t / (2 * ntiles), rem = t - k * 2 * ntiles;
     const int phase = rem >= ntiles ? 1 : 0, T = rem - phase * ntiles;
     const int bi = T / a.tx, bj = T - bi * a.tx;
-    if (threadIdx.y == 0 && (phase == 1 || k > 0)) {  // warp 0 (blockDim.x == 32)
-      const bool ok = phase == 0 ? flow_wait(a, a.done_u, bi, bj, k) : flow_wait(a, a.done_q, bi, bj, k + 1);
-      if (!ok && threadIdx.x == 0) {
-        atomicExch(a.abort_, 1);
-        if (a.status) atomicOr(a.status, DB_FLAG_TIMEOUT);
-      }
-    }
-    __syncthreads();
+    // update tasks wait before their first copy (their u window is guarded
+    // too); q tasks inside q_tile, after copying f and the tap records
+    if (phase == 1) FlowDep{&a, a.done_q, bi, bj, k + 1}();
     const bool even = (k & 1) == 0;
     const float* src = even ? a.A : a.B;
     const int lds = even ? a.ldA : a.ldB;
     constexpr bool HORIZ = AX == 1 || AX == 3, BOX = AX <= 2;
     if (phase == 0) {
+      const FlowDep dep{&a, a.done_u, bi, bj, k};  // k == 0: nothing to wait for (need 0)
       if constexpr (AX == 0)
         q_tile<kFTH, kFTW, kFR, P>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.groups, a.ngroups, a.kh,
-                                      a.kw, a.ng_max, a.p, bi * kFTH, bj * kFTW);
+                                      a.kw, a.ng_max, a.p, bi * kFTH, bj * kFTW, dep);
       else
         q_tile_box<kFTH, kFTW, kFR, HORIZ, BOX>(smem, a.f, a.ldf, src, lds, a.q, a.ldq, a.H, a.W, a.ngroups, a.p,
-                                                bi * kFTH, bj * kFTW);
+                                                bi * kFTH, bj * kFTW, dep);
     } else {
       float* dst = even ? a.B : a.A;
       const int ldd = even ? a.ldB : a.ldA;
