@@ -93,3 +93,14 @@ def test_process_wide_knobs_validate_their_arguments(lib):
         assert lib.db_set_one_axis_min(bad) == 1
     for good in (1, 16, 256, 0):
         assert lib.db_set_one_axis_min(good) == 0
+
+
+def test_host_path_arguments_are_checked_before_any_cuda_call(lib):
+    """db_plan_run_host and db_host_alloc reject null or empty arguments
+    synchronously (no plan, no allocation, nothing enqueued)."""
+    fake = 0x10000
+    assert lib.db_plan_run_host(None, fake, fake, fake, fake + 64, None, None) == 1
+    out = ctypes.c_void_p(123)
+    assert lib.db_host_alloc(0, ctypes.byref(out)) == 1 and out.value is None
+    assert lib.db_host_alloc(16, None) == 1
+    lib.db_host_free(None)  # a null pointer is ignored
