@@ -286,6 +286,20 @@ db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, fl
                            int* dev_status, void* stream);
 void db_plan_destroy(db_plan* plan);
 
+/* Choose the plan's kernel schedule by measurement: runs the plan on (f -> u)
+ * once per candidate -- the split, flow and fused schedules, and for a
+ * non-box one-axis PSF both the tap-group and the register-window form --
+ * `reps` times after one warm-up, timed with CUDA events on `stream`, and
+ * keeps the fastest for every later db_plan_run of this plan (instead of the
+ * process-wide db_set_schedule / db_set_one_axis_min settings).  Synchronises
+ * `stream`; not capturable.  Results of all forms agree to FP32 rounding.
+ * *chosen_schedule (DB_SCHED_*) and *chosen_axis (0 tap groups, 2 register
+ * windows, -1 not applicable) report the choice (both nullable; -1 for a
+ * periodic plan, which has one form).  DB_ERR_ARG for null pointers, f == u
+ * or reps < 1; DB_ERR_UNSUPPORTED if no form runs. */
+db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, int* dev_status, void* stream,
+                           int* chosen_schedule, int* chosen_axis);
+
 /* Page-locked host memory for db_plan_run_host (cudaHostAlloc): *out = a
  * buffer of `bytes` bytes, released with db_host_free.  DB_ERR_ARG for a null
  * out or zero bytes, DB_ERR_CUDA when the allocation fails (*out = NULL). */

@@ -238,6 +238,21 @@ class Plan:
             self.ws.raise_on_flags("db_plan_run")
         return u
 
+    def autotune(self, f: torch.Tensor, reps: int = 3):
+        """Pick this plan's schedule by timing every form on f (db_plan_autotune;
+        synchronises the current stream).  Returns (schedule, one_axis_form):
+        schedule one of "split", "flow", "fused" (None for a periodic plan),
+        form "groups", "windows" or None."""
+        u = torch.empty_like(f)
+        cs, ca = ctypes.c_int(-1), ctypes.c_int(-1)
+        self.ws.reset_status()
+        _check(_lib.load().db_plan_autotune(self._h, f.data_ptr(), u.data_ptr(), int(reps),
+                                            self.ws.status.data_ptr(), _stream(), ctypes.byref(cs),
+                                            ctypes.byref(ca)), "db_plan_autotune")
+        self.ws.raise_on_flags("db_plan_autotune")
+        names = {_lib.SCHED_SPLIT: "split", _lib.SCHED_FLOW: "flow", _lib.SCHED_FUSED: "fused"}
+        return names.get(cs.value), {0: "groups", 2: "windows"}.get(ca.value)
+
     def run_host(self, f_host, u_host, check: bool = True, sync: bool = True):
         """The pipeline on an image in host memory (db_plan_run_host): the
         copy in, the run and the copy out are enqueued on the current stream,

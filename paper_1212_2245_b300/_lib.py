@@ -65,6 +65,8 @@ SIGNATURES = {
     "db_plan_run": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "db_plan_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "db_plan_destroy": (None, [c_void_p]),
+    "db_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                 ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "db_host_alloc": (c_int, [c_size_t, ctypes.POINTER(c_void_p)]),
     "db_host_free": (None, [c_void_p]),
     "db_status_string": (c_char_p, [c_int]),

@@ -88,9 +88,12 @@ static RrlParams to_rrl(const db_params* p) {
 // ng_bound: the tap-group count when the caller knows it (0 otherwise).
 // kind: one-axis PSFs (a box, or kh == 1 or kw == 1) run the one-axis form of
 // the split schedule unless the flow or fused schedule is set explicitly.
+// sched_in, axis_in (>= 0): a plan's tuned schedule and one-axis form
+// (0 tap groups, 2 register windows), overriding the process-wide settings.
 static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld, int kh, int kw, int kind,
                                  const RrlParams& rp, int iters, float* ckpt, int ckpt_every, void* ws,
-                                 const WsLayout& L, int* dev_status, cudaStream_t s, int ng_bound = 0) {
+                                 const WsLayout& L, int* dev_status, cudaStream_t s, int ng_bound = 0,
+                                 int sched_in = -1, int axis_in = -1) {
   char* base = (char*)ws;
   TapGroup* groups = (TapGroup*)(base + L.taps);
   int* ngroups = (int*)(base + L.ntaps);
@@ -103,8 +106,9 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   // split / flow): 1024^2 line PSF 53 / 27 / 26; 1536^2 124 / 68 / 76; 4096^2
   // 752 / 348 / 425; the fused schedule's halo recompute costs more than q's
   // round trip at every size.
-  int sched = g_schedule.load();
+  int sched = sched_in >= 0 ? sched_in : g_schedule.load();
   int axis = axis_mode(kind, kh, kw);
+  if (axis_in >= 0 && axis != 1) axis = (axis_in == 2 && (kh == 1 || kw == 1)) ? 2 : 0;
   if (sched == DB_SCHED_AUTO) {
     const size_t px = (size_t)H * W;
     sched = (px >= (size_t)512 * 1024 && px <= (size_t)2 << 20) ? DB_SCHED_FLOW : DB_SCHED_SPLIT;
@@ -332,6 +336,8 @@ struct SinglePlan {
   Dft1 DW32, DH32;  // periodic mode: FP32 twiddles of the iteration transforms
   int ng = 0;       // tap-group count (0: unknown)
   RrlParams rp;     // kernel parameters, r_f evaluation as selected at creation
+  int sched = -1;   // tuned schedule (db_plan_autotune; -1: the process-wide setting)
+  int axis = -1;    // tuned one-axis form (0 tap groups, 2 register windows; -1: setting)
 };
 }  // namespace db
 
@@ -405,8 +411,52 @@ db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, 
     return DB_OK;
   }
   return iterate_spatial(f, u, P->H, P->W, P->ld, P->kh, P->kw, P->kind, P->rp, P->iters, nullptr, 0, P->ws,
-                         P->L,
-                         dev_status, s, P->ng);
+                         P->L, dev_status, s, P->ng, P->sched, P->axis);
+}
+
+db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, int* dev_status, void* stream,
+                           int* chosen_schedule, int* chosen_axis) {
+  SinglePlan* P = (SinglePlan*)plan;
+  if (!P || !f || !u || f == u || reps < 1) return DB_ERR_ARG;
+  if (chosen_schedule) *chosen_schedule = -1;
+  if (chosen_axis) *chosen_axis = -1;
+  if (P->conv == DB_CONV_PERIODIC || P->iters == 0) return DB_OK;  // one form only
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool one_axis = P->kind != DB_PSF_BOX && (P->kh == 1 || P->kw == 1);
+  const int scheds[3] = {DB_SCHED_SPLIT, DB_SCHED_FLOW, DB_SCHED_FUSED};
+  const int axes[2] = {0, 2};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return DB_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DB_ERR_CUDA; }
+  float best = -1.f;
+  int best_s = -1, best_a = -1;
+  db_status st = DB_OK;
+  for (int is = 0; is < 3 && st == DB_OK; ++is) {
+    const bool fused = scheds[is] == DB_SCHED_FUSED;
+    if (fused && P->kind == DB_PSF_BOX) continue;  // runs as split
+    for (int ia = 0; ia < (one_axis && !fused ? 2 : 1); ++ia) {
+      P->sched = scheds[is];
+      P->axis = one_axis ? axes[ia] : -1;
+      if (db_plan_run(plan, f, u, dev_status, stream) != DB_OK) continue;  // e.g. too large for this form
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = DB_ERR_CUDA; break; }
+      db_status r = DB_OK;
+      for (int k = 0; k < reps && r == DB_OK; ++k) r = db_plan_run(plan, f, u, dev_status, stream);
+      if (r != DB_OK) continue;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = DB_ERR_CUDA; break; }
+      if (best < 0.f || ms < best) { best = ms; best_s = P->sched; best_a = P->axis; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->sched = best_s;
+  P->axis = best_a;
+  if (st != DB_OK) return st;
+  if (best_s < 0) return DB_ERR_UNSUPPORTED;
+  if (chosen_schedule) *chosen_schedule = best_s;
+  if (chosen_axis) *chosen_axis = best_a;
+  return DB_OK;
 }
 
 db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, float* f_dev, float* u_dev,

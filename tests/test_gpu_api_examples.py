@@ -1,4 +1,5 @@
 """The usage shown in the README runs as written (smaller sizes)."""
+import numpy as np
 import pytest
 import torch
 
@@ -44,4 +45,43 @@ def test_plan_run_host_equals_device_run(lib):
         plan.run_host(fh, torch.empty(192, 160, dtype=torch.float64))
     fh.close()
     uh.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("form", ["line", "row", "col-box"])
+def test_plan_autotune_keeps_a_form_equal_to_the_global_setting(lib, form):
+    """db_plan_autotune times every schedule (and one-axis form) and keeps the
+    fastest for the plan: the tuned plan's result equals, bit for bit, a run
+    with that choice set process-wide, and stays within FP32 rounding of the
+    untuned plan's."""
+    rng = np.random.default_rng(11)
+    H, W, kind = 384, 352, "general"
+    if form == "line":
+        h = synth.line_psf(15, 30.0)
+    elif form == "row":
+        h = synth.random_motion_1d(31, rng, "row")
+    else:
+        h, kind = synth.box_psf(13, "col"), "box"
+    f = torch.as_tensor(rng.uniform(0.0, 255.0, (H, W)).astype(np.float32)).cuda()
+    taps = torch.as_tensor(np.ascontiguousarray(h, dtype=np.float32)).cuda()
+    p = Params()
+    plan = db.Plan(H, W, taps, p, 6, kind=kind)
+    base = plan.run(f).clone()
+    sched, axis = plan.autotune(f, reps=2)
+    assert sched in ("split", "flow", "fused")
+    if form == "row":
+        assert axis == "groups" if sched == "fused" else axis in ("groups", "windows")
+    else:
+        assert axis is None
+    tuned = plan.run(f).clone()
+    try:
+        db.set_schedule(sched)
+        if axis is not None:
+            db.set_one_axis_min(1 if axis == "windows" else 256)
+        assert torch.equal(tuned, db.deblur(f, taps, p, 6, kind=kind))
+    finally:
+        db.set_schedule("auto")
+        db.set_one_axis_min(0)
+    err = (tuned - base).abs().max().item()
+    assert err <= 1e-3 * max(1.0, base.abs().max().item()), err
     plan.close()
