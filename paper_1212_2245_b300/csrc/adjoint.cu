@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <float.h>
 
+#include <algorithm>
+
 #include "fft_df.cuh"
 #include "internal.cuh"
 
@@ -456,18 +458,47 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_diff(const float* __res
 // the two end pixels of a row, where the preimage ranges of the clamp are
 // summed explicitly.  Per pixel the arithmetic is that of the generic
 // kernels above, term for term.
+//
+// The tap loops run over runs of RUN adjacent outputs per thread (8 in the
+// forward kernel, 4 in the reverse kernel, which keeps the tap partials in
+// registers and needs the occupancy): a run slides a register window over the
+// KWB + RUN - 1 staged values its taps reach, so each value is read from
+// shared memory once per run instead of once per output and tap, and each
+// tap weight once per run.  Each output still sums its taps in tap order.
+//
+// Shared layout of a staged row: logical element e sits at e + floor(e/RUN),
+// one pad word after every RUN, so that lanes whose runs start RUN elements
+// apart hit distinct banks.  Column j of an array staged with shift sh in
+// [0, RUN) is element kAdjRowPad + sh + j.  The shift makes the first element
+// of every run's window a multiple of RUN -- sh = -cx mod RUN for the arrays
+// read at j + cx - c (u, Abar/Bbar), cx mod RUN for those read at j - cx + c
+// (q, bbar) -- so that every offset within the window is a compile-time
+// constant m + floor(m/RUN).
 // ---------------------------------------------------------------------------
 constexpr int kAdjRowTaps = 32, kAdjRowPad = 32;
 constexpr int kAdjRowBlock = 4;  // rows staged per CTA and step
+constexpr int kAdjRunFwd = 8, kAdjRunRev = 4;  // outputs per thread in the tap loops
 
 __device__ __forceinline__ float zero_of(float) { return 0.f; }
 __device__ __forceinline__ float2 zero_of(float2) { return make_float2(0.f, 0.f); }
 
-// Stage rows R0..R0+nr-1 (pitch W, packed) into s, row r at s + r*(W + 2 pad)
-// + pad, padded by kAdjRowPad columns: constant continuation or zeros.
-template <typename T, bool CLAMP>
-__device__ __forceinline__ void stage_rows(T* s, const T* __restrict__ src, int R0, int nr, int W) {
-  const int L = W + 2 * kAdjRowPad;
+template <int RUN>
+__host__ __device__ __forceinline__ int pidx(int e) {
+  static_assert(RUN == 4 || RUN == 8, "run length");
+  return e + (e >> (RUN == 8 ? 3 : 2));
+}
+// Elements per staged row (shifted logical range: kAdjRowPad + RUN-1 + W + kAdjRowPad).
+template <int RUN>
+__host__ __device__ inline int adj_row_pitch(int W) {
+  const int L = W + 2 * kAdjRowPad + RUN;
+  return pidx<RUN>(L) + 1;
+}
+
+// Stage rows R0..R0+nr-1 (pitch W, packed) with shift sh: row r at s + r*P,
+// columns -kAdjRowPad .. W+kAdjRowPad-1, constant continuation or zeros.
+template <int RUN, typename T, bool CLAMP>
+__device__ __forceinline__ void stage_rows(T* s, const T* __restrict__ src, int R0, int nr, int W, int sh) {
+  const int P = adj_row_pitch<RUN>(W), L = W + 2 * kAdjRowPad;
   for (int r = 0; r < nr; ++r) {
     const T* row = src + (size_t)(R0 + r) * W;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -475,9 +506,14 @@ __device__ __forceinline__ void stage_rows(T* s, const T* __restrict__ src, int 
       T v;
       if (CLAMP) v = row[clampi(j, W)];
       else v = (j >= 0 && j < W) ? row[j] : zero_of(T());
-      s[r * L + k] = v;
+      s[r * P + pidx<RUN>(k + sh)] = v;
     }
   }
+}
+
+// Column of pad slot t (0 .. 2 kAdjRowPad - 1) of a row: -1-t left, W+t' right.
+__device__ __forceinline__ int pad_column(int t, int W) {
+  return t < kAdjRowPad ? -1 - t : W + (t - kAdjRowPad);
 }
 
 // The taps of a one-row PSF, zero beyond kw up to KWB (the tap loops below
@@ -498,25 +534,25 @@ __device__ __forceinline__ float tap_at(const float* taps, int c) { return *((vo
 // is [0, min(-s, n-1)] (empty for s > 0), at j = n - 1 it is
 // [max(n-1-s, 0), n-1] (empty for s < 0).  With d = |s| the preimages of
 // the taps with nonempty ranges are nested, so one running prefix (suffix)
-// sum visits every x once: O(kw) per end pixel.
+// sum visits every x once: O(kw) per end pixel.  x(d) reads column d.
 __device__ __forceinline__ float2 x_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float x_add(float a, float b) { return a + b; }
 __device__ __forceinline__ float2 x_fma(float w, float2 a, float2 acc) {
   return make_float2(fmaf(w, a.x, acc.x), fmaf(w, a.y, acc.y));
 }
 __device__ __forceinline__ float x_fma(float w, float a, float acc) { return fmaf(w, a, acc); }
-template <typename T>
-__device__ T row_end_transpose(const T* x, const float* taps, int kw, int cx, int n, bool first, int sgn) {
+template <typename T, typename X>
+__device__ T row_end_transpose(X x, const float* taps, int kw, int cx, int n, bool first, int sgn) {
   T out = zero_of(T());
   if (n == 1) {
-    for (int c = 0; c < kw; ++c) out = x_fma(taps[c], x[0], out);
+    for (int c = 0; c < kw; ++c) out = x_fma(taps[c], x(0), out);
     return out;
   }
   const int dmax = (first == (sgn > 0)) ? cx : kw - 1 - cx;
   const int e = first ? -sgn : sgn;  // tap c = cx + e d
   T run = zero_of(T());
   for (int d = 0; d <= dmax; ++d) {
-    if (d < n) run = x_add(run, x[first ? d : n - 1 - d]);
+    if (d < n) run = x_add(run, x(first ? d : n - 1 - d));
     out = x_fma(taps[cx + e * d], run, out);
   }
   return out;
@@ -525,15 +561,83 @@ __device__ T row_end_transpose(const T* x, const float* taps, int kw, int cx, in
 // Smallest tap-loop length of the row kernels that holds kw taps.
 inline int row_taps_bucket(int kw) { return kw <= 8 ? 8 : kw <= 16 ? 16 : kw <= 24 ? 24 : 32; }
 
+// A run's values from / to global memory: n valid; vec: 16-byte aligned and
+// the run is full.
+__device__ __forceinline__ bool al16(const void* p) { return (((uintptr_t)p) & 15) == 0; }
+template <int RUN>
+__device__ __forceinline__ void run_load(float (&v)[RUN], const float* __restrict__ src, int n, bool vec) {
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < RUN / 4; ++k) {
+      const float4 a = reinterpret_cast<const float4*>(src)[k];
+      v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < RUN; ++s) v[s] = s < n ? src[s] : 0.f;
+  }
+}
+template <int RUN>
+__device__ __forceinline__ void run_store(float* dst, const float (&v)[RUN], int n, bool vec) {
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < RUN / 4; ++k)
+      reinterpret_cast<float4*>(dst)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int s = 0; s < RUN; ++s)
+      if (s < n) dst[s] = v[s];
+  }
+}
+template <int RUN>
+__device__ __forceinline__ void run_store(float2* dst, const float2 (&v)[RUN], int n, bool vec) {
+  if (vec) {
+#pragma unroll
+    for (int k = 0; k < RUN / 2; ++k)
+      reinterpret_cast<float4*>(dst)[k] = make_float4(v[2 * k].x, v[2 * k].y, v[2 * k + 1].x, v[2 * k + 1].y);
+  } else {
+#pragma unroll
+    for (int s = 0; s < RUN; ++s)
+      if (s < n) dst[s] = v[s];
+  }
+}
+
+// Sliding window over a run's tap reach: for c = 0..KWB-1 in order, f(c, win)
+// with win[s] = x[pidx(s + c)] (SGN > 0) or x[pidx(s - c)] (SGN < 0).  Every
+// value is read from shared memory once and then moves through the window
+// (register renaming once unrolled).
+template <int KWB, int SGN, int RUN, typename T, typename F>
+__device__ __forceinline__ void run_window(const T* x, F f) {
+  T win[RUN];
+#pragma unroll
+  for (int s = 0; s < RUN; ++s) win[s] = x[pidx<RUN>(s)];
+#pragma unroll
+  for (int c = 0; c < KWB; ++c) {
+    f(c, win);
+    if (c + 1 < KWB) {
+      if (SGN > 0) {
+#pragma unroll
+        for (int s = 0; s + 1 < RUN; ++s) win[s] = win[s + 1];
+        win[RUN - 1] = x[pidx<RUN>(c + RUN)];
+      } else {
+#pragma unroll
+        for (int s = RUN - 1; s > 0; --s) win[s] = win[s - 1];
+        win[0] = x[pidx<RUN>(-c - 1)];
+      }
+    }
+  }
+}
+
 // Row-block loop: the CTA takes kAdjRowBlock rows at a time (grid-stride).
 #define ADJ_ROW_BLOCKS(rows)                                                                       \
   for (int R0 = blockIdx.x * kAdjRowBlock; R0 < (rows); R0 += gridDim.x * kAdjRowBlock)
 #define ADJ_ROW_ITEMS(nr, W)                                                                       \
   for (int it = threadIdx.x; it < (nr) * (W); it += blockDim.x)
-
-
-
-
+// Run loop: run `it` of row r starts at column j0 and holds n outputs.
+#define ADJ_ROW_RUNS(nr, nrun, W)                                                                  \
+  for (int it = threadIdx.x; it < (nr) * (nrun); it += blockDim.x)
+#define ADJ_RUN_DECOMPOSE(nrun, W)                                                                 \
+  const int r = it / (nrun), j0 = (it - r * (nrun)) * RUN, n = min(RUN, (W) - j0);
 
 // Forward recompute of one iteration for one-row PSFs, fused: b = C u and
 // q = (W f/b, W) into a shared row, then A, B = C' q and g from it.
@@ -546,58 +650,88 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
                                                                   float* __restrict__ g_out) {
   extern __shared__ __align__(16) unsigned char adj_sm[];
   __shared__ float taps[KWB];
-  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  constexpr int RUN = kAdjRunFwd;
+  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H;
+  const int P = adj_row_pitch<RUN>(W), nrun = (W + RUN - 1) / RUN;
+  const int shu = (-cx) & (RUN - 1), shq = cx & (RUN - 1);  // u read at j + cx - c, q at j - cx + c
   float2* sq = (float2*)adj_sm;
-  float* su = (float*)(sq + kAdjRowBlock * L);
+  float* su = (float*)(sq + kAdjRowBlock * P);
+  const bool vec = (W & 3) == 0 && al16(u) && al16(f0) && al16(b_out) && al16(q_out) && al16(ab_out) && al16(g_out);
   load_row_taps<KWB>(taps, im);
   ADJ_ROW_BLOCKS(rows) {
     const int nr = min(kAdjRowBlock, rows - R0);
     __syncthreads();
-    stage_rows<float, true>(su, u, R0, nr, W);
+    stage_rows<RUN, float, true>(su, u, R0, nr, W, shu);
     __syncthreads();
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float* ub = su + r * L + kAdjRowPad + j + cx;  // ub[-c] = u(j - (c - cx))
-      float bb = 0.f;
+    ADJ_ROW_RUNS(nr, nrun, W) {
+      ADJ_RUN_DECOMPOSE(nrun, W)
+      const bool full = vec && n == RUN;
+      const float* ub = su + r * P + pidx<RUN>(kAdjRowPad + shu + j0 + cx);  // ub[pidx<RUN>(m)] = u(j0 + cx + m)
+      float bb[RUN];
 #pragma unroll
-      for (int c = 0; c < KWB; ++c) bb = fmaf(tap_at(taps, c), ub[-c], bb);
-      const size_t idx = (size_t)R0 * W + it;
-      const float fv = f0[idx];
-      float rr;
-      const float w = phi_w(bb, fv, im.p, &rr);
-      const float2 qv = make_float2(w * fv / bb, w);
-      b_out[idx] = bb;
-      q_out[idx] = qv;
-      sq[r * L + kAdjRowPad + j] = qv;
+      for (int s = 0; s < RUN; ++s) bb[s] = 0.f;
+      run_window<KWB, -1, RUN>(ub, [&](int c, const float(&win)[RUN]) {
+        const float w = tap_at(taps, c);
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) bb[s] = fmaf(w, win[s], bb[s]);
+      });
+      const size_t idx0 = (size_t)(R0 + r) * W + j0;
+      float fv[RUN];
+      run_load(fv, f0 + idx0, n, full);
+      float2 qv[RUN];
+      float2* qrow = sq + r * P;
+#pragma unroll
+      for (int s = 0; s < RUN; ++s) {
+        float rr;
+        const float w = phi_w(bb[s], fv[s], im.p, &rr);
+        qv[s] = make_float2(w * fv[s] / bb[s], w);
+        if (s < n) qrow[pidx<RUN>(kAdjRowPad + shq + j0 + s)] = qv[s];
+      }
+      run_store(b_out + idx0, bb, n, full);
+      run_store(q_out + idx0, qv, n, full);
     }
     __syncthreads();
     // constant continuation of q beyond the row ends
     for (int k = threadIdx.x; k < nr * 2 * kAdjRowPad; k += blockDim.x) {
       const int r = k / (2 * kAdjRowPad), t = k - r * 2 * kAdjRowPad;
-      float2* qr = sq + r * L + kAdjRowPad;
-      if (t < kAdjRowPad) qr[-1 - t] = qr[0];
-      else qr[W + (t - kAdjRowPad)] = qr[W - 1];
+      const int jj = pad_column(t, W), js = t < kAdjRowPad ? 0 : W - 1;
+      sq[r * P + pidx<RUN>(kAdjRowPad + shq + jj)] = sq[r * P + pidx<RUN>(kAdjRowPad + shq + js)];
     }
     __syncthreads();
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float2* qb = sq + r * L + kAdjRowPad + j - cx;  // qb[c] = q(j + (c - cx))
-      const float* ur = su + r * L + kAdjRowPad;
-      float A = 0.f, B = 0.f;
+    ADJ_ROW_RUNS(nr, nrun, W) {
+      ADJ_RUN_DECOMPOSE(nrun, W)
+      const bool full = vec && n == RUN;
+      const float2* qb = sq + r * P + pidx<RUN>(kAdjRowPad + shq + j0 - cx);  // qb[pidx<RUN>(m)] = q(j0 - cx + m)
+      float A[RUN], B[RUN];
 #pragma unroll
-      for (int c = 0; c < KWB; ++c) {
+      for (int s = 0; s < RUN; ++s) { A[s] = 0.f; B[s] = 0.f; }
+      run_window<KWB, 1, RUN>(qb, [&](int c, const float2(&win)[RUN]) {
         const float w = tap_at(taps, c);
-        const float2 v = qb[c];
-        A = fmaf(w, v.x, A);
-        B = fmaf(w, v.y, B);
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) {
+          A[s] = fmaf(w, win[s].x, A[s]);
+          B[s] = fmaf(w, win[s].y, B[s]);
+        }
+      });
+      const int Rr = R0 + r, img = Rr / H, i = Rr - img * H;
+      const float* ip = u + (size_t)img * H * W + j0;
+      const float* ur = su + r * P;
+      float up[RUN], dn[RUN];
+      run_load(up, ip + (size_t)clampi(i - 1, H) * W, n, full);
+      run_load(dn, ip + (size_t)clampi(i + 1, H) * W, n, full);
+      const size_t idx0 = (size_t)Rr * W + j0;
+      float2 abv[RUN];
+      float gv[RUN];
+#pragma unroll
+      for (int s = 0; s < RUN; ++s) {
+        const int j = j0 + s;
+        abv[s] = make_float2(A[s], B[s]);
+        const float gx = 0.5f * (ur[pidx<RUN>(kAdjRowPad + shu + j + 1)] - ur[pidx<RUN>(kAdjRowPad + shu + j - 1)]);
+        const float gy = 0.5f * (dn[s] - up[s]);
+        gv[s] = psi_g(gx, gy, im.p);
       }
-      const int R = R0 + r, n = R / H, i = R - n * H;
-      const float* img = u + (size_t)n * H * W;
-      const size_t idx = (size_t)R * W + j;
-      ab_out[idx] = make_float2(A, B);
-      const float gx = 0.5f * (ur[j + 1] - ur[j - 1]);
-      const float gy = 0.5f * (img[(size_t)clampi(i + 1, H) * W + j] - img[(size_t)clampi(i - 1, H) * W + j]);
-      g_out[idx] = psi_g(gx, gy, im.p);
+      run_store(ab_out + idx0, abv, n, full);
+      run_store(g_out + idx0, gv, n, full);
     }
   }
 }
@@ -618,11 +752,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
     float* __restrict__ f0bar, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char adj_sm[];
   __shared__ float taps[KWB];
-  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H, L = W + 2 * kAdjRowPad;
+  constexpr int RUN = kAdjRunRev;
+  const int kw = im.kw, cx = kw >> 1, W = im.W, H = im.H, rows = im.N * im.H;
+  const int P = adj_row_pitch<RUN>(W), nrun = (W + RUN - 1) / RUN;
+  const int shm = (-cx) & (RUN - 1), shp = cx & (RUN - 1);  // read at j + cx - c: u, Abar/Bbar; at j - cx + c: q, bbar
   float2* sa = (float2*)adj_sm;
-  float2* sq = sa + kAdjRowBlock * L;
-  float* sb = (float*)(sq + kAdjRowBlock * L);
-  float* su = sb + kAdjRowBlock * L;
+  float2* sq = sa + kAdjRowBlock * P;
+  float* sb = (float*)(sq + kAdjRowBlock * P);
+  float* su = sb + kAdjRowBlock * P;
+  const bool vec = (W & 3) == 0 && al16(b) && al16(f0) && al16(f0bar) && al16(Uacc);
   load_row_taps<KWB>(taps, im);
   float acc[KWB];  // tap partials (entries from kw on are never reduced)
 #pragma unroll
@@ -631,13 +769,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
   ADJ_ROW_BLOCKS(rows) {
     const int nr = min(kAdjRowBlock, rows - R0);
     __syncthreads();
-    stage_rows<float2, true>(sq, q, R0, nr, W);
-    stage_rows<float, true>(su, u, R0, nr, W);
-    for (int k = threadIdx.x; k < nr * 2 * kAdjRowPad; k += blockDim.x) {  // zero pads of abbar, bbar
-      const int r = k / (2 * kAdjRowPad), t = k - r * 2 * kAdjRowPad;
-      const int off = r * L + (t < kAdjRowPad ? t : W + t);
-      sa[off] = make_float2(0.f, 0.f);
-      sb[off] = 0.f;
+    stage_rows<RUN, float2, true>(sq, q, R0, nr, W, shp);
+    stage_rows<RUN, float, true>(su, u, R0, nr, W, shm);
+    for (int k = threadIdx.x; k < nr * 2 * kAdjRowPad; k += blockDim.x) {  // zero pads of abar, bbar
+      const int r = k / (2 * kAdjRowPad), jj = pad_column(k - r * 2 * kAdjRowPad, W);
+      sa[r * P + pidx<RUN>(kAdjRowPad + shm + jj)] = make_float2(0.f, 0.f);
+      sb[r * P + pidx<RUN>(kAdjRowPad + shp + jj)] = 0.f;
     }
     // U = U' num/den, Abar, Bbar, Dbar
     ADJ_ROW_ITEMS(nr, W) {
@@ -653,67 +790,103 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
       const float Ab = ub * uu / den;
       const float Bb = -ub * uu * num / (den * den);
       Uacc[idx] = ub * num / den;
-      sa[r * L + kAdjRowPad + j] = make_float2(Ab, Bb);
+      sa[r * P + pidx<RUN>(kAdjRowPad + shm + j)] = make_float2(Ab, Bb);
       Dbar[idx] = im.p.alpha * ((D > 0.f ? Ab : 0.f) - (D < 0.f ? Bb : 0.f));
       asum += Ab * Dp - Bb * Dm;
     }
     __syncthreads();
     // qbar = C'^T (Abar, Bbar); bbar and f0bar; correlation tap partials
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float2* ar = sa + r * L + kAdjRowPad;
-      const float2* qr = sq + r * L + kAdjRowPad;
-      float s1 = 0.f, s2 = 0.f;
-      if (j > 0 && j < W - 1) {
-        const float2* abase = ar + j + cx;  // abase[-c] = abar(j - (c - cx))
+    ADJ_ROW_RUNS(nr, nrun, W) {
+      ADJ_RUN_DECOMPOSE(nrun, W)
+      const bool full = vec && n == RUN;
+      const size_t idx0 = (size_t)(R0 + r) * W + j0;
+      float bv[RUN], fv[RUN], fb[RUN];  // issued ahead of the tap loops
+      run_load(bv, b + idx0, n, full);
+      run_load(fv, f0 + idx0, n, full);
+      run_load(fb, f0bar + idx0, n, full);
+      const float2* ar = sa + r * P;
+      const float2* a8 = ar + pidx<RUN>(kAdjRowPad + shm + j0 + cx);  // a8[pidx<RUN>(m)] = abar(j0 + cx + m)
+      float s1[RUN], s2[RUN];
 #pragma unroll
-        for (int c = 0; c < KWB; ++c) {
-          const float w = tap_at(taps, c);
-          const float2 v = abase[-c];
-          s1 = fmaf(w, v.x, s1);
-          s2 = fmaf(w, v.y, s2);
+      for (int s = 0; s < RUN; ++s) { s1[s] = 0.f; s2[s] = 0.f; }
+      run_window<KWB, -1, RUN>(a8, [&](int c, const float2(&win)[RUN]) {
+        const float w = tap_at(taps, c);
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) {
+          s1[s] = fmaf(w, win[s].x, s1[s]);
+          s2[s] = fmaf(w, win[s].y, s2[s]);
         }
-      } else {
-        const float2 z = row_end_transpose<float2>(ar, taps, kw, cx, W, j == 0, +1);
-        s1 = z.x;
-        s2 = z.y;
-      }
-      const float2 v = ar[j];
-      const float2* qb = qr + j - cx;  // qb[t] = q(j + t - cx)
+      });
+      // the two row-end pixels: exact transposes over the clamp's preimages
+      auto acol = [&](int d) { return ar[pidx<RUN>(kAdjRowPad + shm + d)]; };
+      const float2 z0 = j0 == 0 ? row_end_transpose<float2>(acol, taps, kw, cx, W, true, +1) : make_float2(0.f, 0.f);
+      const float2 z1 = j0 + n == W ? row_end_transpose<float2>(acol, taps, kw, cx, W, W == 1, +1)
+                                    : make_float2(0.f, 0.f);
+      float2 v[RUN];
 #pragma unroll
-      for (int t = 0; t < KWB; ++t) {
-        const float2 qq = qb[t];
-        acc[t] = fmaf(v.x, qq.x, fmaf(v.y, qq.y, acc[t]));
+      for (int s = 0; s < RUN; ++s) {
+        const int j = j0 + s;
+        if (j == 0) { s1[s] = z0.x; s2[s] = z0.y; }
+        else if (j == W - 1) { s1[s] = z1.x; s2[s] = z1.y; }
+        v[s] = ar[pidx<RUN>(kAdjRowPad + shm + j)];  // zero beyond the row
       }
-      const size_t idx = (size_t)R0 * W + it;
-      const float bv = b[idx], fv = f0[idx];
-      float rr;
-      const float w = phi_w(bv, fv, im.p, &rr);
-      const float Wbar = s1 * fv / bv + s2;
-      // phi''(r) = -phi'(r)^3 / (2 eps^2) for the regularised L1 penaliser
-      const float rbar = im.p.phi_robust ? Wbar * (-w * w * w / (2.f * im.p.eps_phi * im.p.eps_phi)) : 0.f;
-      sb[r * L + kAdjRowPad + j] = -s1 * w * fv / (bv * bv) + rbar * (1.f - fv / bv);
-      f0bar[idx] += s1 * w / bv - rbar * logf(bv / fv);
+      const float2* q8 = sq + r * P + pidx<RUN>(kAdjRowPad + shp + j0 - cx);  // q8[pidx<RUN>(m)] = q(j0 - cx + m)
+      run_window<KWB, 1, RUN>(q8, [&](int t, const float2(&win)[RUN]) {
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) acc[t] = fmaf(v[s].x, win[s].x, fmaf(v[s].y, win[s].y, acc[t]));
+      });
+      float* brow = sb + r * P;
+#pragma unroll
+      for (int s = 0; s < RUN; ++s) {
+        if (s < n) {
+          float rr;
+          const float w = phi_w(bv[s], fv[s], im.p, &rr);
+          const float Wbar = s1[s] * fv[s] / bv[s] + s2[s];
+          // phi''(r) = -phi'(r)^3 / (2 eps^2) for the regularised L1 penaliser
+          const float rbar = im.p.phi_robust ? Wbar * (-w * w * w / (2.f * im.p.eps_phi * im.p.eps_phi)) : 0.f;
+          brow[pidx<RUN>(kAdjRowPad + shp + j0 + s)] = -s1[s] * w * fv[s] / (bv[s] * bv[s]) + rbar * (1.f - fv[s] / bv[s]);
+          fb[s] += s1[s] * w / bv[s] - rbar * logf(bv[s] / fv[s]);
+        }
+      }
+      run_store(f0bar + idx0, fb, n, full);
     }
     __syncthreads();
     // U += C^T bbar; convolution tap partials
-    ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const float* br = sb + r * L + kAdjRowPad;
-      const float* ur = su + r * L + kAdjRowPad;
-      float sacc = 0.f;
-      if (j > 0 && j < W - 1) {
-        const float* bbase = br + j - cx;  // bbase[c] = bbar(j + (c - cx))
+    ADJ_ROW_RUNS(nr, nrun, W) {
+      ADJ_RUN_DECOMPOSE(nrun, W)
+      const bool full = vec && n == RUN;
+      const size_t idx0 = (size_t)(R0 + r) * W + j0;
+      float ua[RUN];  // issued ahead of the tap loops
+      run_load(ua, Uacc + idx0, n, full);
+      const float* br = sb + r * P;
+      const float* b8 = br + pidx<RUN>(kAdjRowPad + shp + j0 - cx);  // b8[pidx<RUN>(m)] = bbar(j0 - cx + m)
+      float sacc[RUN];
 #pragma unroll
-        for (int c = 0; c < KWB; ++c) sacc = fmaf(tap_at(taps, c), bbase[c], sacc);
-      } else {
-        sacc = row_end_transpose<float>(br, taps, kw, cx, W, j == 0, -1);
+      for (int s = 0; s < RUN; ++s) sacc[s] = 0.f;
+      run_window<KWB, 1, RUN>(b8, [&](int c, const float(&win)[RUN]) {
+        const float w = tap_at(taps, c);
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) sacc[s] = fmaf(w, win[s], sacc[s]);
+      });
+      auto bcol = [&](int d) { return br[pidx<RUN>(kAdjRowPad + shp + d)]; };
+      const float z0 = j0 == 0 ? row_end_transpose<float>(bcol, taps, kw, cx, W, true, -1) : 0.f;
+      const float z1 = j0 + n == W ? row_end_transpose<float>(bcol, taps, kw, cx, W, W == 1, -1) : 0.f;
+      float bvv[RUN];
+#pragma unroll
+      for (int s = 0; s < RUN; ++s) {
+        const int j = j0 + s;
+        if (j == 0) sacc[s] = z0;
+        else if (j == W - 1) sacc[s] = z1;
+        bvv[s] = br[pidx<RUN>(kAdjRowPad + shp + j)];  // zero beyond the row
       }
-      Uacc[(size_t)R0 * W + it] += sacc;
-      const float bv = br[j];
-      const float* ubase = ur + j + cx;  // ubase[-t] = u(j - (t - cx))
 #pragma unroll
-      for (int t = 0; t < KWB; ++t) acc[t] = fmaf(bv, ubase[-t], acc[t]);
+      for (int s = 0; s < RUN; ++s) ua[s] += sacc[s];
+      run_store(Uacc + idx0, ua, n, full);
+      const float* u8 = su + r * P + pidx<RUN>(kAdjRowPad + shm + j0 + cx);  // u8[pidx<RUN>(m)] = u(j0 + cx + m)
+      run_window<KWB, -1, RUN>(u8, [&](int t, const float(&win)[RUN]) {
+#pragma unroll
+        for (int s = 0; s < RUN; ++s) acc[t] = fmaf(bvv[s], win[s], acc[t]);
+      });
     }
   }
   block_reduce_add(part + blockIdx.x, asum);
@@ -990,8 +1163,8 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   im.p.rf_lut = nullptr;  // the reverse pass differentiates the log form
   const int G = kAdjBlocks, T = kAdjThreads;
   // row kernels (kw <= kAdjRowTaps): shared memory of the staged rows
-  const size_t rowlen = ((size_t)W + 2 * kAdjRowPad) * kAdjRowBlock;
-  const size_t smab = rowlen * 12, smrev = rowlen * 24;
+  const size_t smab = (size_t)adj_row_pitch<kAdjRunFwd>(W) * kAdjRowBlock * 12;
+  const size_t smrev = (size_t)adj_row_pitch<kAdjRunRev>(W) * kAdjRowBlock * 24;
   const bool rowk = kw <= kAdjRowTaps && smrev <= 227 * 1024;
   auto fwd_rows = k_adj_fwd_rows<32>;
   auto rev_rows = k_adj_rev_rows<32>;
@@ -1001,11 +1174,22 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     case 24: fwd_rows = k_adj_fwd_rows<24>; rev_rows = k_adj_rev_rows<24>; break;
     default: break;
   }
+  // row kernels: one wave of resident CTAs (their grid-stride loops give every
+  // CTA the same number of row blocks; a partial second wave would run at a
+  // fraction of the occupancy)
+  int Gfwd = G, Grev = G;
   if (rowk) {
     if (smrev > 48 * 1024)
       ADJ_CHECK(cudaFuncSetAttribute(rev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smrev));
     if (smab > 48 * 1024)
       ADJ_CHECK(cudaFuncSetAttribute(fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smab));
+    int dev = 0, sms = 0, of = 0, orv = 0;
+    ADJ_CHECK(cudaGetDevice(&dev));
+    ADJ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ADJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, fwd_rows, T, smab));
+    ADJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&orv, rev_rows, T, smrev));
+    if (of > 0) Gfwd = std::min(G, of * sms);
+    if (orv > 0) Grev = std::min(G, orv * sms);
   }
 
   const size_t smdiff = diff_smem(W);
@@ -1029,7 +1213,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
       float* uk = seg + (size_t)(k - k0) * n;
       const size_t z = (size_t)(k - k0) * n;
       if (rowk) {
-        ADJ_LAUNCH(fwd_rows<<<G, T, smab, s>>>(uk, f0, im, b + z, q + z, ab + z, g + z));
+        ADJ_LAUNCH(fwd_rows<<<Gfwd, T, smab, s>>>(uk, f0, im, b + z, q + z, ab + z, g + z));
       } else {
         ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b + z, q + z));
         ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q + z, im, ab + z, g + z));
@@ -1044,9 +1228,9 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
       const float2* ab = L_ab + z;
       const float* g = L_g + z;
       if (rowk) {
-        ADJ_LAUNCH(rev_rows<<<G, T, smrev, s>>>(ubar, uk, ab, g, q, b, f0, im, uacc, dbar, f0bar, part));
-        ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));
-        ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part + G, ntaps, G, grad_taps));
+        ADJ_LAUNCH(rev_rows<<<Grev, T, smrev, s>>>(ubar, uk, ab, g, q, b, f0, im, uacc, dbar, f0bar, part));
+        ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, Grev, grad_alpha));
+        ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part + Grev, ntaps, Grev, grad_taps));
       } else {
         ADJ_LAUNCH(k_adj_rev_update<<<G, T, 0, s>>>(ubar, uk, ab, g, im, uacc, abbar, dbar, part));
         ADJ_LAUNCH(k_adj_reduce<<<1, T, 0, s>>>(part, 1, G, grad_alpha));

@@ -111,3 +111,21 @@ def test_backward_rejects_2d_psf(lib):
     gk = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(lib.DeblurError):
         lib.rrl_backward(f, f.clone(), f.clone(), taps, Params(), 2, 1, gt, ga, gk)
+
+
+@pytest.mark.parametrize("H,W,kw", [(12, 53, 7), (10, 37, 15), (9, 61, 21), (8, 45, 31), (6, 27, 25), (5, 7, 7),
+                                    (4, 1, 1), (7, 16, 3)])
+def test_backward_row_runs_ragged_rows(lib, H, W, kw):
+    """The row kernels of the reverse pass take runs of 8 outputs per thread:
+    rows whose length is not a multiple of 8, a run longer than the row, a
+    row as long as the PSF, a single column, and every tap bucket (8, 16,
+    24, 32) against the FP64 reverse mode."""
+    gs, fs, h0 = _setup(2, H, W, kw, 100 + W + kw)
+    p = Params(alpha=0.02, K=0.01)
+    lg, gf, gt, ga, gk = _gpu_grads(lib, fs, gs, h0, 0.02, 0.01, p, 3, 2)
+    lo, of, ot, oa, ok = _oracle_grads(fs, gs, h0, 0.02, 0.01, p, 3)
+    assert abs(lg - lo) <= 1e-5 * abs(lo)
+    assert float((gf - of).abs().max()) <= REL * float(of.abs().max()), "grad f"
+    assert float((gt - ot).abs().max()) <= REL * float(ot.abs().max()), f"grad taps {gt} vs {ot}"
+    assert abs(ga - oa) <= REL * abs(oa) + 1e-9, f"grad alpha {ga} vs {oa}"
+    assert abs(gk - ok) <= REL * abs(ok) + 1e-9, f"grad K {gk} vs {ok}"
