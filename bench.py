@@ -54,7 +54,7 @@ def parse():
                     default="line1024",
                     help="line1024 (default, the headline workload), box256, gauss2048, batch512, learn512, "
                          "stream1024 (line1024 frames with overlapped host<->device transfers)")
-    ap.add_argument("--schedule", choices=["auto", "fused", "split", "flow"], default="auto",
+    ap.add_argument("--schedule", choices=["auto", "fused", "split", "flow", "cluster"], default="auto",
                     help="kernel schedule of the spatial RRRL iterations")
     ap.add_argument("--rf", choices=["log1p", "lut"], default="log1p",
                     help="evaluation of r_f: log1p (default) or the lookup table of Sec. 4.1")

@@ -287,7 +287,8 @@ db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, fl
 void db_plan_destroy(db_plan* plan);
 
 /* Choose the plan's kernel schedule by measurement: runs the plan on (f -> u)
- * once per candidate -- the split, flow and fused schedules, and for a
+ * once per candidate -- the split, flow, fused and (where it applies)
+ * cluster schedules, and for a
  * non-box one-axis PSF both the tap-group and the register-window form --
  * `reps` times after one warm-up, timed with CUDA events on `stream`, and
  * keeps the fastest for every later db_plan_run of this plan (instead of the
@@ -328,11 +329,20 @@ const char* db_version(void);
  *                    on expiry; db_set_spin_limit) only for the neighbouring
  *                    tiles whose output they read, so the phases of
  *                    successive iterations overlap.  Calls that request
- *                    checkpoints run the split schedule. */
+ *                    checkpoints run the split schedule.
+ *   DB_SCHED_CLUSTER - for one-row PSFs (kh == 1) on images with H a
+ *                    multiple of 64 and W a multiple of 8 that fit: the
+ *                    whole image stays in the shared memory of one cluster
+ *                    of 8 CTAs for all iterations (one launch; rows split
+ *                    across the CTAs, TV halo rows exchanged through
+ *                    distributed shared memory).  Same result as the split
+ *                    schedule bit for bit (a short non-box row PSF is summed
+ *                    with register windows here).  Other calls run split. */
 #define DB_SCHED_AUTO 0
 #define DB_SCHED_FUSED 1
 #define DB_SCHED_SPLIT 2
 #define DB_SCHED_FLOW 3
+#define DB_SCHED_CLUSTER 4
 db_status db_set_schedule(int schedule);
 
 /* One-axis PSFs (kh == 1 or kw == 1) in the split and flow schedules: a box

@@ -250,7 +250,8 @@ class Plan:
                                             self.ws.status.data_ptr(), _stream(), ctypes.byref(cs),
                                             ctypes.byref(ca)), "db_plan_autotune")
         self.ws.raise_on_flags("db_plan_autotune")
-        names = {_lib.SCHED_SPLIT: "split", _lib.SCHED_FLOW: "flow", _lib.SCHED_FUSED: "fused"}
+        names = {_lib.SCHED_SPLIT: "split", _lib.SCHED_FLOW: "flow", _lib.SCHED_FUSED: "fused",
+                 _lib.SCHED_CLUSTER: "cluster"}
         return names.get(cs.value), {0: "groups", 2: "windows"}.get(ca.value)
 
     def run_host(self, f_host, u_host, check: bool = True, sync: bool = True):
@@ -505,9 +506,10 @@ def rrl_iterate_noalloc(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, pa
 
 
 def set_schedule(name: str):
-    """Kernel schedule of the spatial iteration: "auto", "fused", "split" or "flow"."""
+    """Kernel schedule of the spatial iteration: "auto", "fused", "split", "flow" or
+    "cluster" (one-row PSFs on small images: the image resident in one cluster)."""
     code = {"auto": _lib.SCHED_AUTO, "fused": _lib.SCHED_FUSED, "split": _lib.SCHED_SPLIT,
-            "flow": _lib.SCHED_FLOW}[name]
+            "flow": _lib.SCHED_FLOW, "cluster": _lib.SCHED_CLUSTER}[name]
     _check(_lib.load().db_set_schedule(code), "db_set_schedule")
 
 

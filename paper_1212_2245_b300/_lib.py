@@ -22,7 +22,7 @@ class DbParams(ctypes.Structure):
 
 DB_PSF_GENERAL, DB_PSF_BOX = 0, 1
 DB_CONV_CLAMP, DB_CONV_PERIODIC = 0, 1
-SCHED_AUTO, SCHED_FUSED, SCHED_SPLIT, SCHED_FLOW = 0, 1, 2, 3
+SCHED_AUTO, SCHED_FUSED, SCHED_SPLIT, SCHED_FLOW, SCHED_CLUSTER = 0, 1, 2, 3, 4
 RF_LOG1P, RF_LUT = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 << 20  # DB_NOALLOC_SCRATCH_BYTES
 FLAG_TAPS, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOX = 0x1, 0x2, 0x4, 0x8

@@ -113,10 +113,18 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
     const size_t px = (size_t)H * W;
     sched = (px >= (size_t)512 * 1024 && px <= (size_t)2 << 20) ? DB_SCHED_FLOW : DB_SCHED_SPLIT;
   }
-  // the flow schedule writes no checkpoints: the split schedule (same tile
-  // bodies, bitwise equal result) stands in; a box keeps its window sums
+  // the flow and cluster schedules write no checkpoints: the split schedule
+  // (same tile bodies, bitwise equal result) stands in; a box keeps its
+  // window sums; the cluster schedule runs one-row PSFs on images that fit
+  if (sched == DB_SCHED_CLUSTER && kh == 1 && axis == 0) axis = 2;
+  if (sched == DB_SCHED_CLUSTER && (ckpt || !cluster_fits(H, W, kh, kw, axis))) sched = DB_SCHED_SPLIT;
   if ((sched == DB_SCHED_FLOW && ckpt) || (sched == DB_SCHED_FUSED && axis == 1)) sched = DB_SCHED_SPLIT;
   if (sched == DB_SCHED_FUSED) axis = 0;
+  if (sched == DB_SCHED_CLUSTER) {
+    if (launch_rrl_cluster(f, ld, u, ld, H, W, ngroups, kw, axis, rp, iters, dev_status, s) != cudaSuccess)
+      return DB_ERR_CUDA;
+    return DB_OK;
+  }
   if (sched == DB_SCHED_FLOW) {
     if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw), axis) > 227 * 1024)
       return DB_ERR_UNSUPPORTED;
@@ -423,7 +431,7 @@ db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, in
   if (P->conv == DB_CONV_PERIODIC || P->iters == 0) return DB_OK;  // one form only
   cudaStream_t s = (cudaStream_t)stream;
   const bool one_axis = P->kind != DB_PSF_BOX && (P->kh == 1 || P->kw == 1);
-  const int scheds[3] = {DB_SCHED_SPLIT, DB_SCHED_FLOW, DB_SCHED_FUSED};
+  const int scheds[4] = {DB_SCHED_SPLIT, DB_SCHED_FLOW, DB_SCHED_FUSED, DB_SCHED_CLUSTER};
   const int axes[2] = {0, 2};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return DB_ERR_CUDA;
@@ -431,9 +439,24 @@ db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, in
   float best = -1.f;
   int best_s = -1, best_a = -1;
   db_status st = DB_OK;
-  for (int is = 0; is < 3 && st == DB_OK; ++is) {
+  for (int is = 0; is < 4 && st == DB_OK; ++is) {
     const bool fused = scheds[is] == DB_SCHED_FUSED;
     if (fused && P->kind == DB_PSF_BOX) continue;  // runs as split
+    if (scheds[is] == DB_SCHED_CLUSTER) {  // one form (row PSFs on images that fit), else split
+      if (!cluster_fits(P->H, P->W, P->kh, P->kw, P->kind == DB_PSF_BOX ? 1 : 2)) continue;
+      P->sched = DB_SCHED_CLUSTER;
+      P->axis = -1;
+      if (db_plan_run(plan, f, u, dev_status, stream) != DB_OK) continue;
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = DB_ERR_CUDA; break; }
+      db_status r = DB_OK;
+      for (int k = 0; k < reps && r == DB_OK; ++k) r = db_plan_run(plan, f, u, dev_status, stream);
+      float ms = 0.f;
+      if (r != DB_OK) continue;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = DB_ERR_CUDA; break; }
+      if (best < 0.f || ms < best) { best = ms; best_s = P->sched; best_a = P->axis; }
+      continue;
+    }
     for (int ia = 0; ia < (one_axis && !fused ? 2 : 1); ++ia) {
       P->sched = scheds[is];
       P->axis = one_axis ? axes[ia] : -1;
@@ -523,7 +546,7 @@ db_status db_set_one_axis_min(int min_len) {
 
 db_status db_set_schedule(int schedule) {
   if (schedule != DB_SCHED_AUTO && schedule != DB_SCHED_FUSED && schedule != DB_SCHED_SPLIT &&
-      schedule != DB_SCHED_FLOW)
+      schedule != DB_SCHED_FLOW && schedule != DB_SCHED_CLUSTER)
     return DB_ERR_ARG;
   g_schedule.store(schedule);
   return DB_OK;

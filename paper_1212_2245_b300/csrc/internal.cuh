@@ -134,6 +134,15 @@ size_t rrl_box_smem(int kh, int kw);  // split kernels of a one-axis PSF (kh == 
 // flow_ws: flow_ws_bytes(H, W), 256-byte aligned
 size_t flow_ws_bytes(int H, int W);
 size_t flow_smem(int kh, int kw, int ng_max, int axis = 0);  // axis: axis_mode() form of the tiles
+
+// Cluster-resident schedule (rrl_cluster.cu): the whole image in the shared
+// memory of one cluster of kClusterCTAs CTAs, all iterations in one launch;
+// one-row PSFs (axis 1 box, 2 register windows), H a multiple of
+// 8 kClusterCTAs, W a multiple of 8, no checkpoints.
+constexpr int kClusterCTAs = 8;
+bool cluster_fits(int H, int W, int kh, int kw, int axis);
+cudaError_t launch_rrl_cluster(const float* f, int ldf, float* u, int ldu, int H, int W, const int* ngroups, int kw,
+                               int axis, const RrlParams& p, int iters, int* status, cudaStream_t s);
 void set_flow_spin_limit(long long cycles);
 cudaError_t launch_rrl_flow(const float* f, int ldf, float* u, int ldu, float* utmp, int ldt, float2* q, int H, int W,
                             const TapGroup* groups, const int* ngroups, int kh, int kw, int ng_bound,

@@ -166,9 +166,10 @@ __device__ __forceinline__ void correlate_strip(const float2* __restrict__ base,
 // and vertical fluxes shared by neighbouring rows of the strip are formed
 // once.  Across the image boundary the clamped copy makes every difference
 // vanish exactly: zero flux.
-template <int R, int S, bool TV>
+template <int R, int S0, bool TV>
 __device__ __forceinline__ void diffusion_strip_t(const float* __restrict__ uc, const RrlParams& p,
-                                                  float (&D)[R], float (&c)[R]) {
+                                                  float (&D)[R], float (&c)[R], int s_rt) {
+  const int S = S0 > 0 ? S0 : s_rt;  // row stride: compile-time, or given at run time (S0 = 0)
   // With g = psi'(|grad u|^2) and central differences, g = 2 g2 where
   // g2 = 1/sqrt(dx^2 + dy^2 + 4 eps^2) on the undivided differences dx, dy;
   // a flux 1/2 (g_a + g_b)(u_b - u_a) is then (g2_a + g2_b)(u_b - u_a).
@@ -204,9 +205,9 @@ __device__ __forceinline__ void diffusion_strip_t(const float* __restrict__ uc, 
 
 template <int R, int S>
 __device__ __forceinline__ void diffusion_strip(const float* __restrict__ uc, const RrlParams& p,
-                                                float (&D)[R], float (&c)[R]) {
-  if (p.psi_tv) diffusion_strip_t<R, S, true>(uc, p, D, c);
-  else diffusion_strip_t<R, S, false>(uc, p, D, c);
+                                                float (&D)[R], float (&c)[R], int s_rt = 0) {
+  if (p.psi_tv) diffusion_strip_t<R, S, true>(uc, p, D, c, s_rt);
+  else diffusion_strip_t<R, S, false>(uc, p, D, c, s_rt);
 }
 
 // u' = u + u (Delta + alpha D) / (B - alpha [D]-)

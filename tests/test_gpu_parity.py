@@ -29,7 +29,7 @@ def cuda(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32).cuda()
 
 
-@pytest.fixture(params=["fused", "split", "flow"])
+@pytest.fixture(params=["fused", "split", "flow", "cluster"])
 def sched(request, lib):
     lib.set_schedule(request.param)
     yield request.param
@@ -282,6 +282,40 @@ def test_flow_equals_split_bitwise(lib, H, W, psf, kind):
         lib.set_one_axis_min(0)
     for knob in (1, 256):
         assert torch.equal(out["split", knob], out["flow", knob])
+
+
+@pytest.mark.parametrize("H,W,psf,kind,iters", [(256, 256, "box15", "box", 10), (128, 64, "rowrnd31", "general", 7),
+                                                (64, 8, "box7", "box", 3), (64, 512, "rowrnd41", "general", 5),
+                                                (192, 200, "box1", "box", 4), (512, 128, "row5", "general", 6),
+                                                (128, 96, "box16", "box", 1), (100, 96, "box15", "box", 3)])
+def test_cluster_equals_split_bitwise(lib, H, W, psf, kind, iters):
+    """The cluster-resident schedule (whole image in one cluster's shared
+    memory, TV halo rows through distributed shared memory) computes every
+    pixel with the split schedule's one-axis device functions, so it must
+    reproduce the split result exactly -- at every row split across the 8
+    CTAs, for box and register-window sums, even box lengths, a box of
+    length 1, one iteration, and (100 rows: not a multiple of 64) the
+    fallback to the split schedule."""
+    rng = np.random.default_rng(H * 7 + W)
+    h = {"box15": synth.box_psf(15), "box7": synth.box_psf(7), "box1": synth.box_psf(1), "box16": synth.box_psf(16),
+         "rowrnd31": synth.random_motion_1d(31, rng), "rowrnd41": synth.random_motion_1d(41, rng),
+         "row5": synth.raised_cosine_1d(5)}[psf]
+    p = Params()
+    f, u0 = _iterate_case(H, W, h, iters, p, seed=5)
+    out = {}
+    try:
+        lib.set_one_axis_min(1)  # the split schedule sums non-box rows with register windows too
+        for name in ("split", "cluster"):
+            lib.set_schedule(name)
+            out[name] = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, iters, kind=kind)
+    finally:
+        lib.set_schedule("auto")
+        lib.set_one_axis_min(0)
+    assert torch.equal(out["split"], out["cluster"])
+    if psf == "box15" and H == 256:  # and the oracle, at the box256 workload's PSF
+        ref = oracle.rrrl(u0, oracle.condition_input(f, p.pos_floor), h, p, iters)
+        d = (out["cluster"].double().cpu() - torch.as_tensor(ref)).abs()
+        assert float(d.max()) <= 1e-3 and float(d.pow(2).mean().sqrt()) <= 1e-4
 
 
 def test_flow_bounded_waits_report_timeout(lib):
