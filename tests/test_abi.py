@@ -86,9 +86,10 @@ def test_argument_errors_are_synchronous(lib):
 
 
 def test_process_wide_knobs_validate_their_arguments(lib):
-    for bad in (-1, 4, 99):
+    for bad in (-1, 5, 99):
         assert lib.db_set_schedule(bad) == 1
-    assert lib.db_set_schedule(0) == 0
+    for good in (4, 0):  # the cluster schedule, then back to auto
+        assert lib.db_set_schedule(good) == 0
     for bad in (-1, 257, 1000):
         assert lib.db_set_one_axis_min(bad) == 1
     for good in (1, 16, 256, 0):
