@@ -411,27 +411,51 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_diff(const float* __res
     const float* gi = g + (size_t)n * H * W;
     const float* di = Dbar + (size_t)n * H * W;
     __syncthreads();  // the previous block's reads of sa and sub are done
-    for (int i = max(i0 - 1, 0); i < min(i1 + 1, H); ++i) {
-      for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const int p = i * W + j;
-        const float up = ui[p], gp = gi[p], dp = di[p];
+    // pass 1 on rows i0-1 .. i1 (those in the image), one column per thread:
+    // u, g and Dbar of rows i0-2 .. i1+1 and columns j-1 .. j+1 are loaded
+    // together (clamped indices; the in-image tests below decide which
+    // enter), so the loads of a column are in flight at once
+    constexpr int NR = kDiffRows + 4;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+      const int jw = clampi(j - 1, W), je = clampi(j + 1, W);
+      float U[NR][3], G[NR][3], Dd[NR][3];
+#pragma unroll
+      for (int t = 0; t < NR; ++t) {
+        const int row = clampi(i0 - 2 + t, H) * W;
+        U[t][0] = ui[row + jw]; U[t][1] = ui[row + j]; U[t][2] = ui[row + je];
+        G[t][0] = gi[row + jw]; G[t][1] = gi[row + j]; G[t][2] = gi[row + je];
+        Dd[t][0] = di[row + jw]; Dd[t][1] = di[row + j]; Dd[t][2] = di[row + je];
+      }
+#pragma unroll
+      for (int t = 1; t < NR - 1; ++t) {
+        const int i = i0 - 2 + t;
+        if (i < 0 || i >= H || i > i1) continue;
+        const float up = U[t][1], gp = G[t][1], dp = Dd[t][1];
         float ub = 0.f, gb = 0.f;
-        if (j + 1 < W) { const int q = p + 1; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
-        if (j > 0)     { const int q = p - 1; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
-        if (i + 1 < H) { const int q = p + W; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
-        if (i > 0)     { const int q = p - W; ub -= 0.5f * (dp - di[q]) * (gp + gi[q]); gb += 0.5f * (dp - di[q]) * (ui[q] - up); }
+        if (j + 1 < W) { ub -= 0.5f * (dp - Dd[t][2]) * (gp + G[t][2]); gb += 0.5f * (dp - Dd[t][2]) * (U[t][2] - up); }
+        if (j > 0)     { ub -= 0.5f * (dp - Dd[t][0]) * (gp + G[t][0]); gb += 0.5f * (dp - Dd[t][0]) * (U[t][0] - up); }
+        if (i + 1 < H) { ub -= 0.5f * (dp - Dd[t + 1][1]) * (gp + G[t + 1][1]); gb += 0.5f * (dp - Dd[t + 1][1]) * (U[t + 1][1] - up); }
+        if (i > 0)     { ub -= 0.5f * (dp - Dd[t - 1][1]) * (gp + G[t - 1][1]); gb += 0.5f * (dp - Dd[t - 1][1]) * (U[t - 1][1] - up); }
         // psi''(s) = -psi'(s)^3 / 2 for TV; 0 for linear diffusion
         const float sbar = im.p.psi_tv ? gb * (-0.5f * gp * gp * gp) : 0.f;
-        const float dxu = 0.5f * (ui[i * W + clampi(j + 1, W)] - ui[i * W + clampi(j - 1, W)]);
-        const float dyu = 0.5f * (ui[clampi(i + 1, H) * W + j] - ui[clampi(i - 1, H) * W + j]);
+        const float dxu = 0.5f * (U[t][2] - U[t][0]);
+        const float dyu = 0.5f * (U[t + 1][1] - U[t - 1][1]);  // rows clamped at the image's edges
         sa[(i - i0 + 1) * W + j] = make_float2(sbar * dxu, sbar * dyu);
         if (i >= i0 && i < i1) sub[(i - i0) * W + j] = ub;
       }
     }
     __syncthreads();
-    for (int i = i0; i < i1; ++i) {
-      const float2* a = sa + (i - i0 + 1) * W;  // row i; a - W: row i-1, a + W: row i+1
-      for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    // pass 2: the accumulations of a column issued together
+    float* Ub = Uacc + (size_t)n * H * W;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+      float acc[kDiffRows];
+#pragma unroll
+      for (int r = 0; r < kDiffRows; ++r) acc[r] = i0 + r < i1 ? Ub[(size_t)(i0 + r) * W + j] : 0.f;
+#pragma unroll
+      for (int r = 0; r < kDiffRows; ++r) {
+        const int i = i0 + r;
+        if (i >= i1) continue;
+        const float2* a = sa + (i - i0 + 1) * W;  // row i; a - W: row i-1, a + W: row i+1
         float s = 0.f;
         // east neighbour of (i, j-1) is (i, j); of (i, W-1) itself
         if (j >= 1) s += a[j - 1].x;
@@ -443,7 +467,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_diff(const float* __res
         if (i == H - 1) s += a[j].y;
         if (i <= H - 2) s -= a[j + W].y;
         if (i == 0) s -= a[j].y;
-        Uacc[(size_t)n * H * W + (size_t)i * W + j] += sub[(i - i0) * W + j] + s;
+        Ub[(size_t)i * W + j] = acc[r] + (sub[(i - i0) * W + j] + s);
       }
     }
   }
@@ -1195,6 +1219,14 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const size_t smdiff = diff_smem(W);
   if (smdiff > 48 * 1024 && smdiff <= 227 * 1024)
     ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_diff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smdiff));
+  int Gdiff = G;  // one resident wave, as for the row kernels
+  if (smdiff <= 227 * 1024) {
+    int dev = 0, sms = 0, od = 0;
+    ADJ_CHECK(cudaGetDevice(&dev));
+    ADJ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ADJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_adj_rev_diff, T, smdiff));
+    if (od > 0) Gdiff = std::min(G, od * sms);
+  }
 
   // pointwise copies treat the batch as one image of N*H rows (image stride H*ld)
   ADJ_LAUNCH(k_floor_pack<<<G, T, 0, s>>>(f, ld, N * H, W, p->pos_floor, f0));
@@ -1241,7 +1273,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
         ADJ_LAUNCH(k_adj_reduce<<<ntaps, T, 0, s>>>(part, ntaps, G, grad_taps));
       }
       if (smdiff <= 227 * 1024) {
-        ADJ_LAUNCH(k_adj_rev_diff<<<G, T, smdiff, s>>>(dbar, uk, g, im, uacc));
+        ADJ_LAUNCH(k_adj_rev_diff<<<Gdiff, T, smdiff, s>>>(dbar, uk, g, im, uacc));
       } else {
         ADJ_LAUNCH(k_adj_rev_diff1<<<G, T, 0, s>>>(dbar, uk, g, im, uacc, av));
         ADJ_LAUNCH(k_adj_rev_diff2<<<G, T, 0, s>>>(av, im, uacc));
