@@ -237,7 +237,7 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
       return DB_ERR_CUDA;
     if (run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, Sff, FW, FH, s) != cudaSuccess)
       return DB_ERR_CUDA;
-    if (round_spectrum(Sff, S, (size_t)H * W, s) != cudaSuccess) return DB_ERR_CUDA;
+    if (round_spectrum(Sff, S, H, W, s) != cudaSuccess) return DB_ERR_CUDA;
     if (run_rrl_fourier(f, ld, u, ld, (float*)(base + L.utmp), H, W, (float2*)(base + L.work),
                         (float2*)(base + L.qbuf), S, DW.tw, DH.tw, to_rrl(p), iters, ckpt, ckpt_every,
                         dev_status, s) != cudaSuccess)
@@ -386,7 +386,7 @@ db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_param
     Dft1ff FW, FH;
     if (prepare_dft(W, tabW, &FW, &P->DW32, s) != cudaSuccess || prepare_dft(H, tabH, &FH, &P->DH32, s) != cudaSuccess ||
         run_psf_spectrum_2d(psf->taps, psf->kh, psf->kw, H, W, Sff, FW, FH, s) != cudaSuccess ||
-        round_spectrum(Sff, (float2*)(base + L.s32), (size_t)H * W, s) != cudaSuccess) {
+        round_spectrum(Sff, (float2*)(base + L.s32), H, W, s) != cudaSuccess) {
       delete P; return DB_ERR_CUDA;
     }
     // the Wiener filter's own spectrum (1D, or the 2D half spectrum of the

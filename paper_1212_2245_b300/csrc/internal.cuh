@@ -160,7 +160,7 @@ size_t dft_table_elems(int N);  // float4 units
 cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t s);
 cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float4* spec,
                                 const Dft1ff& DW, const Dft1ff& DH, cudaStream_t s);
-cudaError_t round_spectrum(const float4* in, float2* out, size_t n, cudaStream_t s);
+cudaError_t round_spectrum(const float4* in, float2* out, int H, int W, cudaStream_t s);  // column-major out
 cudaError_t psf_row_spectrum(const float* taps, int kw, const Dft1ff& D, float4* out, cudaStream_t s);
 
 // Wiener filter in two parts: set-up (tables, PSF spectrum) and image passes.

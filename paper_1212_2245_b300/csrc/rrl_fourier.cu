@@ -32,7 +32,7 @@ struct FourierArgs {
   const float* uin; int ldin;
   float* uout; int ldout;
   float2* X; float2* Z;      // complex buffers, pitch W
-  const float2* S;           // PSF spectrum, pitch W
+  const float2* S;           // PSF spectrum, column by column (element (k, c) at c H + k)
   const float2* twW;         // twiddle table for length W
   int H, W, logW, logH;
   float scale;               // 1/(H W)
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256, 4) k_fourier_cols(float2* __restrict__ bu
 #pragma unroll
     for (int t = 0; t < kSBatch; ++t) {
       const int idx = base + t * blockDim.x, k = idx / C, c = idx - k * C;
-      sv[t] = (idx < H * C && c0 + c < W) ? __ldg(S + (size_t)k * W + c0 + c) : make_float2(0.f, 0.f);
+      sv[t] = (idx < H * C && c0 + c < W) ? __ldg(S + (size_t)(c0 + c) * H + k) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int t = 0; t < kSBatch; ++t) {

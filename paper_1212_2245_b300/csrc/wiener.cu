@@ -474,15 +474,20 @@ cudaError_t psf_row_spectrum(const float* taps, int kw, const Dft1ff& D, float4*
   return launch_rows<ROW_PSF>(a, s);
 }
 
-__global__ void k_round_spectrum(const float4* __restrict__ in, float2* __restrict__ out, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const float4 v = in[k];
-    out[k] = make_float2(v.x + v.y, v.z + v.w);
+// FP32 copy of an H x W float-float spectrum, stored column by column
+// (out[c H + k] = in[k W + c]): the column passes that multiply with it then
+// read each column as one contiguous run.
+__global__ void k_round_spectrum(const float4* __restrict__ in, float2* __restrict__ out, int H, int W) {
+  const size_t n = (size_t)H * W;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / W), c = (int)(e - (size_t)k * W);
+    const float4 v = in[e];
+    out[(size_t)c * H + k] = make_float2(v.x + v.y, v.z + v.w);
   }
 }
 
-cudaError_t round_spectrum(const float4* in, float2* out, size_t n, cudaStream_t s) {
-  k_round_spectrum<<<592, 256, 0, s>>>(in, out, n);
+cudaError_t round_spectrum(const float4* in, float2* out, int H, int W, cudaStream_t s) {
+  k_round_spectrum<<<592, 256, 0, s>>>(in, out, H, W);
   count_launch();
   return cudaGetLastError();
 }
