@@ -811,9 +811,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
       const float num = v.x + im.p.alpha * Dp;
       const float den = v.y - im.p.alpha * Dm;
       const float ub = Ubar_next[idx], uu = u[idx];
-      const float Ab = ub * uu / den;
-      const float Bb = -ub * uu * num / (den * den);
-      Uacc[idx] = ub * num / den;
+      const float rd = __fdividef(1.f, den);  // den >= B > 0
+      const float Ab = ub * uu * rd;
+      const float Bb = -ub * uu * num * (rd * rd);
+      Uacc[idx] = ub * num * rd;
       sa[r * P + pidx<RUN>(kAdjRowPad + shm + j)] = make_float2(Ab, Bb);
       Dbar[idx] = im.p.alpha * ((D > 0.f ? Ab : 0.f) - (D < 0.f ? Bb : 0.f));
       asum += Ab * Dp - Bb * Dm;
@@ -865,11 +866,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
         if (s < n) {
           float rr;
           const float w = phi_w(bv[s], fv[s], im.p, &rr);
-          const float Wbar = s1[s] * fv[s] / bv[s] + s2[s];
+          const float rb = __fdividef(1.f, bv[s]);  // b >= the floor > 0
+          const float Wbar = s1[s] * fv[s] * rb + s2[s];
           // phi''(r) = -phi'(r)^3 / (2 eps^2) for the regularised L1 penaliser
           const float rbar = im.p.phi_robust ? Wbar * (-w * w * w / (2.f * im.p.eps_phi * im.p.eps_phi)) : 0.f;
-          brow[pidx<RUN>(kAdjRowPad + shp + j0 + s)] = -s1[s] * w * fv[s] / (bv[s] * bv[s]) + rbar * (1.f - fv[s] / bv[s]);
-          fb[s] += s1[s] * w / bv[s] - rbar * logf(bv[s] / fv[s]);
+          brow[pidx<RUN>(kAdjRowPad + shp + j0 + s)] = -s1[s] * w * fv[s] * (rb * rb) + rbar * (1.f - fv[s] * rb);
+          fb[s] += s1[s] * w * rb - rbar * __logf(bv[s] * __fdividef(1.f, fv[s]));
         }
       }
       run_store(f0bar + idx0, fb, n, full);
