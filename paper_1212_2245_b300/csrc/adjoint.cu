@@ -949,47 +949,82 @@ __global__ void k_copy_pitched(const float* __restrict__ src, int lds, float* __
   }
 }
 
-// ---------------------------------------------------------------------------
-// Wiener adjoint for a PSF on one row (float-float transforms, one real row
-// per sequence):
-//   U0 = DFT(u0bar_row) (masked by 1[w > delta]),  F0 = DFT(f0_row)
-//   f0bar_row += Re IDFT(U0 conj(M)) / N          (transpose of the filter)
-//   P(k) = conj(U0(k)) F0(k)  (summed over rows)  for the K and tap gradients
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_adj_wiener_rows(const float* __restrict__ u0bar,
-                                                         const float* __restrict__ f0, int W,
-                                                         const float4* __restrict__ spec, Dft1ff D, float K,
-                                                         float2 invN, float* __restrict__ f0bar,
-                                                         float2* __restrict__ prow) {
+// Two real rows per CTA (rows 2b and 2b+1).  For each row z = u0bar + i f0
+// gives both spectra from one transform -- U(k) = (Z(k) + conj Z(-k))/2,
+// F(k) = (Z(k) - conj Z(-k))/(2i) -- and the inverse of the Hermitian G_a +
+// i G_b (G = U S/(|S|^2 + K)) returns row a's result in its real part and
+// row b's in its imaginary part: three transforms for two rows instead of
+// six.  Spectra are in the transform's storage order (bit-reversed for a
+// power of two, natural under Bluestein).
+__global__ void __launch_bounds__(256) k_adj_wiener_rows2(const float* __restrict__ u0bar,
+                                                          const float* __restrict__ f0, int W, int rows,
+                                                          const float4* __restrict__ spec, Dft1ff D, float K,
+                                                          float2 invN, float* __restrict__ f0bar,
+                                                          float2* __restrict__ prow) {
   extern __shared__ float4 sm[];
   const int M = 1 << D.logM;
-  float4* x = sm;       // DFT(u0bar)
-  float4* y = sm + M;   // DFT(f0)
-  const int r = blockIdx.x;
+  const bool pow2 = D.c == nullptr;
+  float4* x = sm;      // row a: Z, then the packed G_a + i G_b
+  float4* y = sm + M;  // row b: Z
+  const int ra = 2 * blockIdx.x, rb = ra + 1;
+  const bool has_b = rb < rows;
   for (int c = threadIdx.x; c < W; c += blockDim.x) {
-    x[c] = make_float4(u0bar[(size_t)r * W + c], 0.f, 0.f, 0.f);
-    y[c] = make_float4(f0[(size_t)r * W + c], 0.f, 0.f, 0.f);
+    x[c] = mkc(make_float2(u0bar[(size_t)ra * W + c], 0.f), make_float2(f0[(size_t)ra * W + c], 0.f));
+    y[c] = has_b ? mkc(make_float2(u0bar[(size_t)rb * W + c], 0.f), make_float2(f0[(size_t)rb * W + c], 0.f))
+                 : zzero();
   }
   __syncthreads();
   dft_fwd_ff(x, 1, 1, M, D, false);
   dft_fwd_ff(y, 1, 1, M, D, false);
-  for (int k = threadIdx.x; k < W; k += blockDim.x) {
-    const float4 U = x[k], F = y[k], S = __ldg(spec + k);
-    // P(k) = conj(U) F
-    const float4 P = zmulc(F, U);
-    prow[(size_t)r * W + k] = make_float2(P.x + P.y, P.z + P.w);
-    // U conj(M) = U S / (|S|^2 + K)
-    const float2 den = ff_add(ff_add(ff_mul(re_(S), re_(S)), ff_mul(im_(S), im_(S))), make_float2(K, 0.f));
-    const float4 t = zmul(U, S);
-    x[k] = mkc(ff_div(re_(t), den), ff_div(im_(t), den));
+  const float2 half = make_float2(0.5f, 0.f);
+  for (int si = threadIdx.x; si < W; si += blockDim.x) {
+    const int k = pow2 ? (D.logM ? (int)(__brev((unsigned)si) >> (32 - D.logM)) : 0) : si;
+    const int kn = k ? W - k : 0;
+    const int sn = pow2 ? (D.logM ? (int)(__brev((unsigned)kn) >> (32 - D.logM)) : 0) : kn;
+    if (si > sn) continue;  // each pair (k, -k) once, by the thread of its lower storage index
+    const float4 S0 = __ldg(spec + si), S1 = __ldg(spec + sn);
+    const float2 den0 = ff_add(ff_add(ff_mul(re_(S0), re_(S0)), ff_mul(im_(S0), im_(S0))), make_float2(K, 0.f));
+    const float2 den1 = ff_add(ff_add(ff_mul(re_(S1), re_(S1)), ff_mul(im_(S1), im_(S1))), make_float2(K, 0.f));
+    float4 G0[2], G1[2];
+    for (int row = 0; row < 2; ++row) {
+      const float4* z = row ? y : x;
+      const float4 Za = z[si], Zb = z[sn];
+      // U(k), F(k) and U(-k) = conj U(k), F(-k) = conj F(k) (real rows)
+      const float4 U0 = zscale(zadd(Za, zconj(Zb)), half);
+      const float4 dz = zsub(Za, zconj(Zb));
+      const float4 F0 = zscale(mkc(im_(dz), ff_neg(re_(dz))), half);  // dz / (2i)
+      const float4 U1 = zconj(U0), F1 = zconj(F0);
+      const int r = row ? rb : ra;
+      if (row == 0 || has_b) {
+        const float4 P0 = zmulc(F0, U0), P1 = zmulc(F1, U1);  // P(k) = conj(U) F
+        prow[(size_t)r * W + si] = make_float2(P0.x + P0.y, P0.z + P0.w);
+        prow[(size_t)r * W + sn] = make_float2(P1.x + P1.y, P1.z + P1.w);
+      }
+      const float4 t0 = zmul(U0, S0), t1 = zmul(U1, S1);
+      G0[row] = mkc(ff_div(re_(t0), den0), ff_div(im_(t0), den0));
+      G1[row] = mkc(ff_div(re_(t1), den1), ff_div(im_(t1), den1));
+    }
+    // packed Q = G_a + i G_b at k and -k (each pair is read and written by
+    // this thread only)
+    x[si] = mkc(ff_sub(re_(G0[0]), im_(G0[1])), ff_add(im_(G0[0]), re_(G0[1])));
+    x[sn] = mkc(ff_sub(re_(G1[0]), im_(G1[1])), ff_add(im_(G1[0]), re_(G1[1])));
   }
   __syncthreads();
   dft_inv_ff(x, 1, 1, M, D, false);
   for (int c = threadIdx.x; c < W; c += blockDim.x) {
-    const float2 v = ff_mul(re_(x[c]), invN);
-    f0bar[(size_t)r * W + c] += v.x + v.y;
+    const float2 va = ff_mul(re_(x[c]), invN), vb = ff_mul(im_(x[c]), invN);
+    f0bar[(size_t)ra * W + c] += va.x + va.y;
+    if (has_b) f0bar[(size_t)rb * W + c] += vb.x + vb.y;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Wiener adjoint for a PSF on one row (float-float transforms; two real rows
+// per CTA share three transforms, k_adj_wiener_rows2):
+//   U0 = DFT(u0bar_row) (masked by 1[w > delta]),  F0 = DFT(f0_row)
+//   f0bar_row += Re IDFT(U0 conj(M)) / N          (transpose of the filter)
+//   P(k) = conj(U0(k)) F0(k)  (summed over rows)  for the K and tap gradients
+// ---------------------------------------------------------------------------
 
 // Column sums of prow (rows x W complex) in double: P(k), in two levels of
 // fixed order: chunks of kPsumRows rows (one thread per column and chunk),
@@ -1303,10 +1338,11 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const int M = 1 << D.logM;
   const size_t smem = (size_t)2 * M * sizeof(float4);
   if (smem > 227 * 1024) return DB_ERR_UNSUPPORTED;
-  if (smem > 48 * 1024) ADJ_CHECK(cudaFuncSetAttribute(k_adj_wiener_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const double invN = 1.0 / (double)W;
   const float2 invNf = make_float2((float)invN, (float)(invN - (double)(float)invN));
-  ADJ_LAUNCH(k_adj_wiener_rows<<<N * H, 256, smem, s>>>(uacc, f0, W, spec, D, p->K, invNf, f0bar, prow));
+  if (smem > 48 * 1024) ADJ_CHECK(cudaFuncSetAttribute(k_adj_wiener_rows2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ADJ_LAUNCH(k_adj_wiener_rows2<<<(N * H + 1) / 2, 256, smem, s>>>(uacc, f0, W, N * H, spec, D, p->K, invNf, f0bar,
+                                                                  prow));
   {
     const int nch = (N * H + kPsumRows - 1) / kPsumRows;
     double2* ppart = (double2*)(base + L.ppart);
