@@ -121,9 +121,10 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   if ((sched == DB_SCHED_FLOW && ckpt) || (sched == DB_SCHED_FUSED && axis == 1)) sched = DB_SCHED_SPLIT;
   if (sched == DB_SCHED_FUSED) axis = 0;
   if (sched == DB_SCHED_CLUSTER) {
-    if (launch_rrl_cluster(f, ld, u, ld, H, W, ngroups, kw, axis, rp, iters, dev_status, s) != cudaSuccess)
-      return DB_ERR_CUDA;
-    return DB_OK;
+    const cudaError_t e = launch_rrl_cluster(f, ld, u, ld, H, W, ngroups, kw, axis, rp, iters, dev_status, s);
+    if (e == cudaSuccess) return DB_OK;
+    if (e != cudaErrorNotSupported) return DB_ERR_CUDA;
+    sched = DB_SCHED_SPLIT;  // no cluster of this shape fits on the device
   }
   if (sched == DB_SCHED_FLOW) {
     if (flow_smem(kh, kw, ng_bound > 0 ? ng_bound : max_tap_groups(kh, kw), axis) > 227 * 1024)

@@ -216,27 +216,38 @@ bool cluster_fits(int H, int W, int kh, int kw, int axis) {
 
 cudaError_t launch_rrl_cluster(const float* f, int ldf, float* u, int ldu, int H, int W, const int* ngroups, int kw,
                                int axis, const RrlParams& p, int iters, int* status, cudaStream_t s) {
-  const size_t smem = cluster_smem(H, W, kw);
-  const int nc = cluster_ctas(H);
   auto k = axis == 1 ? k_rrl_cluster<true> : k_rrl_cluster<false>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && nc > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = nc;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nc);
-  cfg.blockDim = dim3(kClusterThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if ((e = cudaLaunchKernelEx(&cfg, k, f, ldf, u, ldu, H, W, ngroups, p, iters, status)) != cudaSuccess) return e;
-  count_launch();
-  return cudaSuccess;
+  // 16 CTAs where the rows allow it and the device can place such a cluster,
+  // else 8; cudaErrorNotSupported when neither fits (the caller runs split)
+  for (int nc = cluster_ctas(H); nc >= kClusterCTAs; nc /= 2) {
+    const ClusterGeom g(H / nc, W, kw);
+    if (g.bytes > 227 * 1024) continue;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes)) != cudaSuccess)
+      return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = g.bytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) != cudaSuccess || nclusters < 1) {
+      (void)cudaGetLastError();  // clear a refused query
+      continue;
+    }
+    if ((e = cudaLaunchKernelEx(&cfg, k, f, ldf, u, ldu, H, W, ngroups, p, iters, status)) != cudaSuccess) return e;
+    count_launch();
+    return cudaSuccess;
+  }
+  return cudaErrorNotSupported;
 }
 
 }  // namespace db
