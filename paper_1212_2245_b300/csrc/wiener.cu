@@ -214,7 +214,7 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
       dft_inv_ff(x, R, 1, M, a.D, false);
     }
   }
-  if (MODE == ROW_FWD_R2C || MODE == ROW_PSF_R2C) {
+  if constexpr (MODE == ROW_FWD_R2C || MODE == ROW_PSF_R2C) {
     const int Nh = N / 2 + 1;
     for (int idx = threadIdx.x; idx < R * Nh; idx += blockDim.x) {
       const int r = idx / Nh, k = idx - r * Nh;
@@ -225,25 +225,25 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
       a.cbuf[(size_t)(2 * q) * a.ldc + k] = X1;
       if (2 * q + 1 < a.img_rows) a.cbuf[(size_t)(2 * q + 1) * a.ldc + k] = X2;
     }
-    return;
-  }
-  for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-    const int r = idx / N, c = idx - r * N;
-    const int q = q0 + r;
-    if (q >= a.nrows) continue;
-    const float4 v = x[r * M + c];
-    if (MODE == ROW_INV_C2R) {
-      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
-      if (2 * q + 1 < a.img_rows)
-        a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
-    } else if (MODE == ROW_PSF || MODE == ROW_FWD_REAL || MODE == ROW_FWD_CPLX) {
-      a.cbuf[(size_t)q * a.ldc + c] = v;
-    } else if (MODE == ROW_INV_REAL) {
-      a.uout[(size_t)q * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
-    } else {
-      a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
-      if (2 * q + 1 < a.img_rows)
-        a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
+  } else {
+    for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+      const int r = idx / N, c = idx - r * N;
+      const int q = q0 + r;
+      if (q >= a.nrows) continue;
+      const float4 v = x[r * M + c];
+      if (MODE == ROW_INV_C2R) {
+        a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
+        if (2 * q + 1 < a.img_rows)
+          a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
+      } else if (MODE == ROW_PSF || MODE == ROW_FWD_REAL || MODE == ROW_FWD_CPLX) {
+        a.cbuf[(size_t)q * a.ldc + c] = v;
+      } else if (MODE == ROW_INV_REAL) {
+        a.uout[(size_t)q * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
+      } else {
+        a.uout[(size_t)(2 * q) * a.ldu + c] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
+        if (2 * q + 1 < a.img_rows)
+          a.uout[(size_t)(2 * q + 1) * a.ldu + c] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
+      }
     }
   }
 }
