@@ -280,8 +280,14 @@ db_status db_plan_run(db_plan* plan, const float* f, float* u, int* dev_status, 
  * and the copy of u_dev into u_host (H x W, packed), all on `stream`.  The
  * copies overlap other work only when the host buffers are page-locked
  * (db_host_alloc); the caller synchronises `stream` before reading u_host.
- * The buffers stay the caller's.  DB_ERR_ARG for null pointers or
- * f_dev == u_dev, DB_ERR_CUDA when a copy or launch fails. */
+ * The run between the copies is one CUDA graph launch: the first call for a
+ * given (f_dev, u_dev, dev_status) captures the plan's run on a stream of
+ * the plan's own (host-side set-up, once), later calls replay it; a change
+ * of any process-wide setting (db_set_*) or of the plan's tuned form
+ * captures again.  If capture is not possible the run is launched directly.
+ * The call itself is not capturable.  The buffers stay the caller's.
+ * DB_ERR_ARG for null pointers or f_dev == u_dev, DB_ERR_CUDA when a copy or
+ * launch fails. */
 db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, float* f_dev, float* u_dev,
                            int* dev_status, void* stream);
 void db_plan_destroy(db_plan* plan);

@@ -12,6 +12,9 @@ namespace db {
 
 static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_schedule{0};
+static std::atomic<unsigned> g_settings_gen{0};
+void bump_settings() { g_settings_gen.fetch_add(1); }
+unsigned settings_gen() { return g_settings_gen.load(); }
 static std::atomic<int> g_one_axis_min{0};
 int one_axis_min(bool row) {
   const int v = g_one_axis_min.load(std::memory_order_relaxed);
@@ -347,6 +350,19 @@ struct SinglePlan {
   RrlParams rp;     // kernel parameters, r_f evaluation as selected at creation
   int sched = -1;   // tuned schedule (db_plan_autotune; -1: the process-wide setting)
   int axis = -1;    // tuned one-axis form (0 tap groups, 2 register windows; -1: setting)
+  // db_plan_run_host: the run captured as a CUDA graph for one set of device
+  // buffers, status word, settings generation and tuned form
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const float* g_f = nullptr;
+  float* g_u = nullptr;
+  int* g_status = nullptr;
+  unsigned g_gen = 0;
+  int g_sched = -2, g_axis = -2;
+  ~SinglePlan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 }  // namespace db
 
@@ -483,6 +499,47 @@ db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, in
   return DB_OK;
 }
 
+// The plan's run as an instantiated CUDA graph for these buffers, captured
+// on the plan's own stream on first use (and again after a settings change
+// or a new tuned form).  false: capture not possible; the caller runs eagerly.
+static bool plan_graph(SinglePlan* P, db_plan* plan, const float* f, float* u, int* status) {
+  const unsigned gen = settings_gen();
+  if (P->gexec && P->g_f == f && P->g_u == u && P->g_status == status && P->g_gen == gen &&
+      P->g_sched == P->sched && P->g_axis == P->axis)
+    return true;
+  if (P->gexec) {
+    cudaGraphExecDestroy(P->gexec);
+    P->gexec = nullptr;
+  }
+  if (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    P->cap_stream = nullptr;
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  const db_status rs = db_plan_run(plan, f, u, status, P->cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(P->cap_stream, &g);
+  cudaError_t ie = cudaErrorUnknown;
+  if (rs == DB_OK && ee == cudaSuccess && g) ie = cudaGraphInstantiate(&P->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    P->gexec = nullptr;
+    (void)cudaGetLastError();
+    return false;
+  }
+  P->g_f = f;
+  P->g_u = u;
+  P->g_status = status;
+  P->g_gen = gen;
+  P->g_sched = P->sched;
+  P->g_axis = P->axis;
+  return true;
+}
+
 db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, float* f_dev, float* u_dev,
                            int* dev_status, void* stream) {
   SinglePlan* P = (SinglePlan*)plan;
@@ -491,8 +548,12 @@ db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, fl
   const size_t row = (size_t)P->W * sizeof(float), pitch = (size_t)P->ld * sizeof(float);
   if (cudaMemcpy2DAsync(f_dev, pitch, f_host, row, row, P->H, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return DB_ERR_CUDA;
-  const db_status st = db_plan_run(plan, f_dev, u_dev, dev_status, stream);
-  if (st != DB_OK) return st;
+  if (plan_graph(P, plan, f_dev, u_dev, dev_status)) {
+    if (cudaGraphLaunch(P->gexec, s) != cudaSuccess) return DB_ERR_CUDA;
+  } else {
+    const db_status st = db_plan_run(plan, f_dev, u_dev, dev_status, stream);
+    if (st != DB_OK) return st;
+  }
   if (cudaMemcpy2DAsync(u_host, row, u_dev, pitch, row, P->H, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return DB_ERR_CUDA;
   return DB_OK;
@@ -542,6 +603,7 @@ long long db_launch_count(void) { return g_launches.load(std::memory_order_relax
 db_status db_set_one_axis_min(int min_len) {
   if (min_len < 0 || min_len > kMaxTapSide + 1) return DB_ERR_ARG;
   g_one_axis_min.store(min_len);
+  bump_settings();
   return DB_OK;
 }
 
@@ -550,6 +612,7 @@ db_status db_set_schedule(int schedule) {
       schedule != DB_SCHED_FLOW && schedule != DB_SCHED_CLUSTER)
     return DB_ERR_ARG;
   g_schedule.store(schedule);
+  bump_settings();
   return DB_OK;
 }
 

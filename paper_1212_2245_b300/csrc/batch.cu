@@ -431,6 +431,7 @@ db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws
 db_status db_set_spin_limit(long long cycles) {
   if (cycles < 0) return DB_ERR_ARG;
   set_spin_limit(cycles);
+  bump_settings();
   return DB_OK;
 }
 

@@ -140,6 +140,12 @@ size_t flow_smem(int kh, int kw, int ng_max, int axis = 0);  // axis: axis_mode(
 // one-row PSFs (axis 1 box, 2 register windows), H a multiple of
 // 8 kClusterCTAs, W a multiple of 8, no checkpoints.
 constexpr int kClusterCTAs = 8;
+
+// Generation count of the process-wide settings (schedule, one-axis form, r_f
+// evaluation, wait bound): every db_set_* call bumps it, so work captured
+// under older settings is captured again.
+void bump_settings();
+unsigned settings_gen();
 bool cluster_fits(int H, int W, int kh, int kw, int axis);
 cudaError_t launch_rrl_cluster(const float* f, int ldf, float* u, int ldu, int H, int W, const int* ngroups, int kw,
                                int axis, const RrlParams& p, int iters, int* status, cudaStream_t s);

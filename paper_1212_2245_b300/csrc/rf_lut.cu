@@ -37,6 +37,7 @@ using namespace db;
 
 extern "C" db_status db_set_rf_eval(int mode) {
   if (mode != DB_RF_LOG1P && mode != DB_RF_LUT) return DB_ERR_ARG;
+  db::bump_settings();
   if (mode == DB_RF_LUT) {
     std::vector<float> tab(kRfLutN);
     const double h = (double)kRfLutSmax / kRfLutN;
