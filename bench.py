@@ -575,12 +575,15 @@ def run_learn(args, world, rank, local):
     def forward():  # all images of the rank in one db_deblur_n call
         db.deblur_n(f, taps, p, iters, out=u, ckpt=ck, ckpt_every=every, ws=wsn, check=False)
 
-    def step():
-        forward()
+    def backward_part():  # loss gradient and reverse pass (needs the targets g)
         torch.sub(u, g, out=gu)
         gu.mul_(2.0 / u.numel())
         gt.zero_(); ga.zero_(); gk.zero_()
         db.rrl_backward(f, ck, gu, taps, p, iters, every, gt, ga, gk, grad_f=gf, ws=bws, check=False)
+
+    def step():
+        forward()
+        backward_part()
 
     with torch.cuda.stream(stream):
         wsn.reset_status(); bws.reset_status()
@@ -594,6 +597,9 @@ def run_learn(args, world, rank, local):
         n1 = lib.db_launch_count()
         with torch.cuda.graph(g_fwd, stream=stream):
             forward()
+        g_bwd = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_bwd, stream=stream):
+            backward_part()
         for _ in range(max(args.warmup, 3)):
             g_step.replay()
             g_fwd.replay()
@@ -620,17 +626,25 @@ def run_learn(args, world, rank, local):
     wsn.raise_on_flags("timed forward"); bws.raise_on_flags("timed backward")
     # end to end: the step's images and targets in from page-locked host
     # memory, the step (forward, loss gradient, backward), the loss and the
-    # parameter gradients back to the host
+    # parameter gradients back to the host.  The targets are needed only by
+    # the loss: their copy runs on a second stream while the forward runs.
     f_host, g_host = pinned_copy(case.f[mine]), pinned_copy(case.g[mine])
     out_host = torch.empty(taps.numel() + 3, dtype=torch.float64).pin_memory()
     out_dev = torch.empty(taps.numel() + 3, dtype=torch.float64, device=dev)
     e2e = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K + 1)]
+    side = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         for k in range(K + 1):  # the first pass is untimed (loads the loss kernels)
             e2e[k][0].record(stream)
             f.copy_(f_host, non_blocking=True)
-            g.copy_(g_host, non_blocking=True)
-            g_step.replay()
+            side.wait_event(e2e[k][0])  # the previous step no longer reads g
+            with torch.cuda.stream(side):
+                g.copy_(g_host, non_blocking=True)
+                g_in = torch.cuda.Event()
+                g_in.record(side)
+            g_fwd.replay()
+            stream.wait_event(g_in)
+            g_bwd.replay()
             if world > 1:
                 shard.combine_param_grads([gt, ga, gk], N, N_all)
             out_dev[0] = ((u - g) ** 2).mean()
