@@ -141,16 +141,55 @@ __device__ __forceinline__ float diffusion_at(const float* u, const float* g, in
   return D;
 }
 
-// Forward step output (used to rebuild checkpoint segments).
-__global__ void k_adj_fwd_update(const float* __restrict__ u, const float2* __restrict__ ab,
-                                 const float* __restrict__ g, AdjImage im, float* __restrict__ u_out) {
-  ADJ_PIXELS(im) {
-    ADJ_DECOMPOSE(im)
-    const float D = diffusion_at(u + o, g + o, i, j, im.H, im.W);
-    const float2 v = ab[idx];
-    const float num = v.x + im.p.alpha * fmaxf(D, 0.f);
-    const float den = v.y - im.p.alpha * fminf(D, 0.f);
-    u_out[idx] = u[idx] * num / den;
+// Forward step output (used to rebuild checkpoint segments).  A CTA takes
+// kFuRows rows of one image and a thread one column of them: the loads of
+// u, g and (A, B) for the column go out together and the rows share them
+// (D as diffusion_at forms it).
+constexpr int kFuRows = 8;
+__global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_update(const float* __restrict__ u,
+                                                                const float2* __restrict__ ab,
+                                                                const float* __restrict__ g, AdjImage im,
+                                                                float* __restrict__ u_out) {
+  const int H = im.H, W = im.W;
+  const int nblk = (H + kFuRows - 1) / kFuRows;
+  for (int blk = blockIdx.x; blk < im.N * nblk; blk += gridDim.x) {
+    const int n = blk / nblk, i0 = (blk - n * nblk) * kFuRows, i1 = min(i0 + kFuRows, H);
+    const size_t o = (size_t)n * H * W;
+    const float* ui = u + o;
+    const float* gi = g + o;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+      const int jw = clampi(j - 1, W), je = clampi(j + 1, W);
+      float Uc[kFuRows + 2], Gc[kFuRows + 2], Uw[kFuRows], Ue[kFuRows], Gw[kFuRows], Ge[kFuRows];
+      float2 abv[kFuRows];
+#pragma unroll
+      for (int t = 0; t < kFuRows + 2; ++t) {
+        const size_t row = (size_t)clampi(i0 - 1 + t, H) * W;
+        Uc[t] = ui[row + j];
+        Gc[t] = gi[row + j];
+      }
+#pragma unroll
+      for (int r = 0; r < kFuRows; ++r) {
+        const size_t row = (size_t)min(i0 + r, H - 1) * W;
+        Uw[r] = ui[row + jw]; Ue[r] = ui[row + je];
+        Gw[r] = gi[row + jw]; Ge[r] = gi[row + je];
+        abv[r] = ab[o + row + j];
+      }
+#pragma unroll
+      for (int r = 0; r < kFuRows; ++r) {
+        const int i = i0 + r;
+        if (i >= i1) continue;
+        const float up = Uc[r + 1], gp = Gc[r + 1];
+        float D = 0.f;
+        if (j + 1 < W) D += 0.5f * (Ge[r] + gp) * (Ue[r] - up);
+        if (j > 0) D += 0.5f * (Gw[r] + gp) * (Uw[r] - up);
+        if (i + 1 < H) D += 0.5f * (Gc[r + 2] + gp) * (Uc[r + 2] - up);
+        if (i > 0) D += 0.5f * (Gc[r] + gp) * (Uc[r] - up);
+        const float2 v = abv[r];
+        const float num = v.x + im.p.alpha * fmaxf(D, 0.f);
+        const float den = v.y - im.p.alpha * fminf(D, 0.f);
+        u_out[o + (size_t)i * W + j] = up * num / den;
+      }
+    }
   }
 }
 
@@ -1256,6 +1295,14 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   const size_t smdiff = diff_smem(W);
   if (smdiff > 48 * 1024 && smdiff <= 227 * 1024)
     ADJ_CHECK(cudaFuncSetAttribute(k_adj_rev_diff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smdiff));
+  int Gfu = G;    // one resident wave, as for the row kernels
+  {
+    int dev = 0, sms = 0, ou = 0;
+    ADJ_CHECK(cudaGetDevice(&dev));
+    ADJ_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ADJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_adj_fwd_update, T, 0));
+    if (ou > 0) Gfu = std::min(G, ou * sms);
+  }
   int Gdiff = G;  // one resident wave, as for the row kernels
   if (smdiff <= 227 * 1024) {
     int dev = 0, sms = 0, od = 0;
@@ -1287,7 +1334,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
         ADJ_LAUNCH(k_adj_fwd_q<<<G, T, 0, s>>>(uk, f0, im, b + z, q + z));
         ADJ_LAUNCH(k_adj_fwd_ab<<<G, T, 0, s>>>(uk, q + z, im, ab + z, g + z));
       }
-      if (k + 1 < k1) ADJ_LAUNCH(k_adj_fwd_update<<<G, T, 0, s>>>(uk, ab + z, g + z, im, uk + n));
+      if (k + 1 < k1) ADJ_LAUNCH(k_adj_fwd_update<<<Gfu, T, 0, s>>>(uk, ab + z, g + z, im, uk + n));
     }
     for (int k = k1 - 1; k >= k0; --k) {  // reverse steps
       const float* uk = seg + (size_t)(k - k0) * n;
