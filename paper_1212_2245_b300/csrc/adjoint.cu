@@ -561,16 +561,27 @@ __host__ __device__ inline int adj_row_pitch(int W) {
 // columns -kAdjRowPad .. W+kAdjRowPad-1, constant continuation or zeros.
 template <int RUN, typename T, bool CLAMP>
 __device__ __forceinline__ void stage_rows(T* s, const T* __restrict__ src, int R0, int nr, int W, int sh) {
-  const int P = adj_row_pitch<RUN>(W), L = W + 2 * kAdjRowPad;
-  for (int r = 0; r < nr; ++r) {
-    const T* row = src + (size_t)(R0 + r) * W;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) {
-      const int j = k - kAdjRowPad;
-      T v;
-      if (CLAMP) v = row[clampi(j, W)];
-      else v = (j >= 0 && j < W) ? row[j] : zero_of(T());
-      s[r * P + pidx<RUN>(k + sh)] = v;
+  const int P = adj_row_pitch<RUN>(W), L = W + 2 * kAdjRowPad, total = nr * L;
+  constexpr int B = 4;  // loads in flight per thread before their shared stores
+  for (int base = threadIdx.x; base < total; base += B * blockDim.x) {
+    T v[B];
+    int at[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int k = base + b * blockDim.x;
+      at[b] = -1;
+      v[b] = zero_of(T());
+      if (k < total) {
+        const int r = k / L, kk = k - r * L, j = kk - kAdjRowPad;
+        const T* row = src + (size_t)(R0 + r) * W;
+        if (CLAMP) v[b] = row[clampi(j, W)];
+        else if (j >= 0 && j < W) v[b] = row[j];
+        at[b] = r * P + pidx<RUN>(kk + sh);
+      }
     }
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+      if (at[b] >= 0) s[at[b]] = v[b];
   }
 }
 
