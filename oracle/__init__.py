@@ -16,6 +16,6 @@ from .ops import (  # noqa: F401
     psf_transfer, wiener, wiener_rows, wiener_cols,
     info_divergence, info_divergence_lut, r1, r1_lut, r1_lut_table, RF_LUT_N, RF_LUT_SMAX,
     phi_prime, psi_prime, diffusion,
-    rrrl_step, rrrl, wr3l, rl_step, condition_input, positivity_floor,
-    mse_loss, wr3l_loss, snr_db,
+    rrrl_step, rrrl, wr3l, condition_input, positivity_floor,
+    wr3l_loss, snr_db,
 )

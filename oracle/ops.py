@@ -394,12 +394,6 @@ def rrrl(u0, f, h, p, iters):
     return u
 
 
-def rl_step(u, f, h, mode="clamp"):
-    """Plain Richardson-Lucy (Eq. 3 with the correlation by h* restored)."""
-    u, f = _t(u), _t(f)
-    return u * corr(f / conv(u, h, mode), h, mode)
-
-
 def _wiener_any(f, h, K):
     kh, kw = h.shape
     if kh == 1:
@@ -421,58 +415,28 @@ def wr3l(f, h, p, iters):
 # ---------------------------------------------------------------------------
 # differentiable form (mean-square loss against the sharp image)
 # ---------------------------------------------------------------------------
-def mse_loss(u, g):
-    return ((_t(u) - _t(g)) ** 2).mean()
-
-
 def wr3l_loss(f, g, h, alpha, K, p, iters):
-    """MSE between WR3L(f; h, alpha, K) and g for a batch (N, H, W); every
-    argument may require grad, torch autograd provides the FP64 reverse mode."""
+    """Mean over a batch (N, H, W) and its pixels of (WR3L(f; h, alpha, K) - g)^2:
+    the same steps as `wr3l` (conditioning, Wiener of Eq. 2, floor, `iters`
+    steps of Eq. 9), with alpha and K taken from the arguments.  Every
+    argument may require grad; torch autograd then gives the FP64 reverse
+    mode (taps with gradients keep their zero entries, see `_offsets`)."""
     class _P:
         pass
     q = _P()
     for k in ("eps_phi", "eps_psi", "pos_floor", "phi_robust", "psi_tv", "conv"):
         setattr(q, k, getattr(p, k))
     q.alpha = alpha
+    h = _t(h)
+    f = _t(f)
     total = 0.0
-    f = _t(f) if not torch.is_tensor(f) else f
     for n in range(f.shape[0]):
         f0 = condition_input(f[n], p.pos_floor)
-        kh, kw = h.shape
-        if kh == 1:
-            u0 = _wiener_rows_tensor(f0, h, K)
-        else:
-            u0 = _wiener_2d_tensor(f0, h, K)
-        u = positivity_floor(u0, p.pos_floor)
+        u = positivity_floor(_wiener_any(f0, h, K), p.pos_floor)
         for _ in range(iters):
             u = rrrl_step(u, f0, h, q)
         total = total + ((u - _t(g[n])) ** 2).sum()
     return total / (f.shape[0] * f.shape[1] * f.shape[2])
-
-
-def _psf_transfer_tensor(h, H, W):
-    """psf_transfer for a tap tensor that may carry gradients."""
-    kh, kw = h.shape
-    cy, cx = kh // 2, kw // 2
-    hp = torch.zeros(H, W, dtype=h.dtype)
-    rows = torch.tensor([(a - cy) % H for a in range(kh)])
-    cols = torch.tensor([(b - cx) % W for b in range(kw)])
-    hp = hp.index_put((rows[:, None].expand(kh, kw).reshape(-1),
-                       cols[None, :].expand(kh, kw).reshape(-1)), h.reshape(-1),
-                      accumulate=True)
-    return torch.fft.fft2(hp)
-
-
-def _wiener_2d_tensor(f, h, K):
-    H, W = f.shape
-    hh = _psf_transfer_tensor(h, H, W)
-    return torch.fft.ifft2(torch.fft.fft2(f) * hh.conj() / (hh.abs() ** 2 + K)).real
-
-
-def _wiener_rows_tensor(f, h, K):
-    H, W = f.shape
-    hh = _psf_transfer_tensor(h, 1, W)[0]
-    return torch.fft.ifft(torch.fft.fft(f, dim=1) * hh.conj() / (hh.abs() ** 2 + K), dim=1).real
 
 
 # ---------------------------------------------------------------------------

@@ -347,6 +347,30 @@ def test_tiny_pipeline_brute_force(kshape):
     np.testing.assert_allclose(u, ref, rtol=1e-11, atol=1e-10)
 
 
+@pytest.mark.parametrize("kshape", [(1, 5), (3, 3), (3, 1)])
+@pytest.mark.parametrize("grad", [False, True])
+def test_loss_forward_equals_naive_pipeline(kshape, grad):
+    """The loss of the tuning workload (mean square error of WR3L against the
+    sharp image) equals the same mean taken over the independent naive
+    pipeline's outputs, with and without gradients on the taps, alpha and K
+    (the gradient path keeps zero taps and goes through the same Wiener
+    functions)."""
+    N, H, W, iters = 2, 8, 8, 3
+    fs = np.stack([rand_img(H, W, 0.0, 255.0) for _ in range(N)])
+    fs[1, 5, 2] = 0.0
+    gs = np.stack([rand_img(H, W) for _ in range(N)])
+    h = rand_psf(*kshape)
+    h.flat[0] = 0.0                                 # a zero tap
+    p = P(K=0.01, alpha=0.05)
+    ref = np.mean([(_naive_pipeline(fs[n], h, p.K, p.alpha, p.eps_phi, p.eps_psi, p.pos_floor, iters) - gs[n]) ** 2
+                   for n in range(N)])
+    hT = torch.tensor(h, dtype=torch.float64, requires_grad=grad)
+    aT = torch.tensor(p.alpha, dtype=torch.float64, requires_grad=grad)
+    kT = torch.tensor(p.K, dtype=torch.float64, requires_grad=grad)
+    loss = oracle.wr3l_loss(torch.tensor(fs, dtype=torch.float64), gs, hT, aT, kT, p, iters)
+    assert abs(float(loss) - ref) <= 1e-11 * ref
+
+
 # --------------------------------------------------------------------------
 # FP64 reverse mode (autograd through the oracle) against central differences
 # --------------------------------------------------------------------------
