@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch512", "learn512", "stream1024"],
-                    default="line1024",
-                    help="line1024 (default, the headline workload), box256, gauss2048, batch512, learn512, "
-                         "stream1024 (line1024 frames with overlapped host<->device transfers)")
+                    default="batch512",
+                    help="batch512 (default: the largest workload, 512 uneven images), line1024, box256, "
+                         "gauss2048, learn512, stream1024 (line1024 frames with overlapped host<->device "
+                         "transfers)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="batch512 at N=1: skip the line1024, gauss2048 and learn512 sub-measurements")
     ap.add_argument("--schedule", choices=["auto", "fused", "split", "flow", "cluster"], default="auto",
                     help="kernel schedule of the spatial RRRL iterations")
     ap.add_argument("--images", type=int, default=512,
@@ -139,6 +142,12 @@ class ClockSampler:
 LINE1024_FLOW_ITER_DRAM_BYTES = (8.489728e6 + 1.274112e6) / 20
 
 
+# DRAM bytes per pixel and iteration of k_rrl_batch (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over the launch's pixels x iterations);
+# None until a capture of the current kernel exists.
+BATCH_DRAM_BYTES_PER_PX_ITER = None
+
+
 def pinned_copy(array):
     """A page-locked float32 host tensor holding `array`, written by one
     single-threaded copy: rows written by many host threads can stay dirty in
@@ -156,37 +165,67 @@ def step_stats(ms_list):
     return {"median": statistics.median(v), "min": min(v), "sd": statistics.pstdev(v) if len(v) > 1 else 0.0}
 
 
+# Algorithmic bytes per pixel and iteration: what the method itself must read
+# and write once per iteration, halo re-reads and intermediates excluded.
+#   spatial iteration: read u, read f, write u'                        12 B
+#   periodic (FFT) iteration, four passes over complex spectra:
+#     columns fwd x S inv 12, rows C2R + ratio + packed C2C 16,
+#     columns fwd x conj S inv on the packed pair 20, rows inverse +
+#     regulariser + update + next forward 20                            68 B
+#   reverse mode (adjoint of one iteration): forward recompute 12 +
+#     reverse reads u, f, the adjoint and writes the adjoint 16         28 B
+ALGO_BYTES = {"spatial": 12.0, "fourier": 68.0, "adjoint": 28.0}
+
+
+def fp32_peak_tflops(world=1):
+    """Nominal FP32 FMA rate: 148 SMs x 128 lanes x 2 flop x 2032 MHz."""
+    return world * SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def flops_per_px_iter(h, kind="general"):
+    """Algorithmic FP32 flops per pixel and iteration: three tap sums (b, then
+    the two correlations) at 2 flops per non-zero tap, plus about 60 for the
+    pointwise work (weight, ratio, regulariser, update).  A box PSF is summed
+    by sliding windows: about 4 flops per sum whatever its length."""
+    if kind.startswith("box"):
+        return 3 * 4 + 60
+    return 6 * int((np.asarray(h) != 0).sum()) + 60
+
+
+def hbm_roofline(bytes_per_pxi, pxi, ms, kernel, traffic=None, flops=None, world=1, **extra):
+    """Roofline entry against the measured HBM copy bandwidth: achieved =
+    algorithmic bytes of the launch / its device time; the FP32 figure of the
+    same time is given beside it (`alu`)."""
+    hbm_peak, src = peaks()
+    ach = bytes_per_pxi * pxi / (ms / 1e3) / 1e9
+    d = {"bound": "hbm", "achieved": ach, "peak": hbm_peak * world, "unit": "GB/s",
+         "frac": ach / (hbm_peak * world), "traffic": traffic, "kernel": kernel, "kernel_ms": ms,
+         "algorithmic_bytes_per_px_iter": bytes_per_pxi, "units_per_launch_px_iter": pxi,
+         "peak_src": f"{src} (HBM copy bandwidth, of measured)" if src == "measured" else f"{src} (6.4 TB/s, of fallback)"}
+    if flops is not None:
+        a = flops / (ms / 1e3) / 1e12
+        d["alu"] = {"achieved": a, "peak": fp32_peak_tflops(world), "unit": "TFLOP/s",
+                    "frac": a / fp32_peak_tflops(world),
+                    "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz (nominal)"}
+    d.update(extra)
+    return d
+
+
 def _spatial_model(case, ms_iter, schedule="auto"):
-    """Fused/split spatial iteration: FP32-issue bound; flops per pixel and
-    iteration = 3 tap sums (b, A, B) x 2 flops x nnz(h) + 60 pointwise."""
+    """One spatial RRRL iteration (12 algorithmic B/px) with its FP32 figure."""
     H, W = case.f.shape
-    nnz = int((case.h != 0).sum())
-    flops = (6 * nnz + 60) * H * W
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops / (ms_iter / 1e3) / 1e12
-    hbm_peak, hbm_src = peaks()
-    hbm_equiv = 12.0 * H * W / (ms_iter / 1e3) / 1e9
     line1024 = (H, W, int((case.h != 0).sum())) == (1024, 1024, 71)
     traffic = LINE1024_FLOW_ITER_DRAM_BYTES if line1024 and schedule in ("auto", "flow") else None
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic,
-            "kernel": "one RRRL iteration (1/iters of k_rrl_flow; k_rrl_q + k_rrl_update; or k_rrl_spatial)",
-            "kernel_ms": ms_iter, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
-            "hbm_equiv_gbs": hbm_equiv, "hbm_equiv_frac": hbm_equiv / hbm_peak,
-            "hbm_peak_gbs": hbm_peak, "hbm_peak_src": hbm_src}
+    return hbm_roofline(ALGO_BYTES["spatial"], H * W, ms_iter,
+                        "one RRRL iteration (1/iters of k_rrl_flow; k_rrl_q + k_rrl_update; or k_rrl_spatial)",
+                        traffic=traffic, flops=flops_per_px_iter(case.h, case.psf_kind) * H * W)
 
 
 def _fourier_model(case, ms_iter, schedule="auto"):
-    """Fourier iteration: four HBM passes over complex buffers; algorithmic
-    bytes per pixel and iteration = 24 (columns x S) + 20 (rows: b, e, W) +
-    24 (columns x conj S) + 24 (rows: update, next transform) = 92 B."""
+    """One periodic RRRL iteration: 68 algorithmic B/px (four passes)."""
     H, W = case.f.shape
-    hbm_peak, hbm_src = peaks()
-    achieved = 92.0 * H * W / (ms_iter / 1e3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None,
-            "kernel": "one Fourier RRRL iteration (k_fourier_cols x2 + k_fourier_rows x2)",
-            "kernel_ms": ms_iter, "peak_src": hbm_src}
+    return hbm_roofline(ALGO_BYTES["fourier"], H * W, ms_iter,
+                        "one Fourier RRRL iteration (k_fourier_cols x2 + k_fourier_rows x2)")
 
 
 def _make(name):
@@ -203,6 +242,11 @@ WORKLOADS = {
     "gauss2048": ("gauss2048: 2048x2048 f32, 31x31 mixture of 3 Gaussians, sigma=1, Wiener K=0.006 + 30 RRRL "
                   "with Fourier-domain (periodic) blur/correlation", _fourier_model),
 }
+
+
+BATCH512_DESC = ("batch512: 512 f32 images, sides U{128..1024}, half 1D motion (box/raised cosine, L 5-41), "
+                 "half 2D Gaussian mixtures 7x7..25x25, sigma=2, Wiener K=0.006 + 10 RRRL; one planned batch "
+                 "replayed from a CUDA graph")
 
 
 def make_case(name="line1024"):
@@ -231,45 +275,60 @@ def cpu_baseline_oracle(case, budget_s=10.0, max_iters=None):
 
 
 def run_reference(args, ws_, rank):
-    """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
+    """Reference arm: the FP64 CPU oracle as it stands, on a bounded sample of
+    the same workload per step."""
     if rank != 0:
         return
     import oracle
-    case = make_case(args.workload if args.workload in WORKLOADS else "line1024")
-    p, h = case.params, case.h
-    rows = min(128, case.f.shape[0])
-    f = case.f[:rows].astype(np.float64)
-    f0 = oracle.condition_input(f, p.pos_floor)
-    u = oracle.positivity_floor(torch.as_tensor(f), p.pos_floor)  # warm start for the sample
+    if args.workload == "batch512":
+        from paper_1212_2245_b300 import synth
+        order = batch_sample_order(512)
+        n_steps = args.warmup + args.steps
+        cases = [synth.batch_case(order[s % len(order)]) for s in range(n_steps)]
+        desc = BATCH512_DESC
+        sample = ("one FP64 oracle RRRL iteration on one whole image of the batch per step, images taken "
+                  "alternately from its 1D-PSF and 2D-PSF halves")
+    else:
+        case = make_case(args.workload if args.workload in WORKLOADS else "line1024")
+        rows = min(128, case.f.shape[0])
+        strip = type(case)(case.name, case.g[:rows], case.f[:rows], case.h, case.iters, case.params, case.psf_kind)
+        cases = [strip] * (args.warmup + args.steps)
+        desc = WORKLOADS[args.workload if args.workload in WORKLOADS else "line1024"][0]
+        sample = f"one FP64 oracle RRRL iteration on a {rows}x{case.f.shape[1]} strip of the workload per step"
+    pxi, total = 0, 0.0
     times = []
-    for s in range(args.warmup + args.steps):
+    for s_, c in enumerate(cases):
+        f0 = oracle.condition_input(c.f.astype(np.float64), c.params.pos_floor)
+        u = oracle.positivity_floor(torch.as_tensor(c.f, dtype=torch.float64), c.params.pos_floor)  # warm start
         t0 = time.perf_counter()
-        u = oracle.rrrl_step(u, f0, h, p)
+        oracle.rrrl_step(u, f0, c.h, c.params)
         dt = time.perf_counter() - t0
-        if s >= args.warmup:
+        if s_ >= args.warmup:
             times.append(dt)
+            pxi += c.f.size
+            total += dt
+    val = pxi / total / 1e6
     ms = 1e3 * statistics.mean(times)
-    val = rows * f.shape[1] / (ms / 1e3) / 1e6
-    sample = f"one FP64 oracle RRRL iteration on a {rows}x{f.shape[1]} strip of the workload per step"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload][0], "sample": sample},
+            "config": {"workload": desc, "sample": sample},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, world, rank, local):
+def run_ours(args, world, rank, local, workload=None):
     import paper_1212_2245_b300 as db
     from paper_1212_2245_b300 import _lib
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = _lib.load()
-    case = make_case(args.workload)
-    desc, model = WORKLOADS[args.workload]
+    workload = workload or args.workload
+    case = make_case(workload)
+    desc, model = WORKLOADS[workload]
     H, W = case.f.shape
     iters, p = case.iters, case.params
     f = torch.as_tensor(case.f).to(dev)
@@ -389,7 +448,7 @@ def run_ours(args, world, rank, local):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(case)
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batch(args, world, rank, local):
@@ -417,7 +476,7 @@ def run_batch(args, world, rank, local):
     ps = [c.params for c in cases]
     kinds = [c.psf_kind for c in cases]
     px = sum(c.f.size for c in cases)
-    flops_iter = sum(c.f.size * (6 * int((c.h != 0).sum()) + 60) for c in cases)
+    flops_iter = sum(c.f.size * flops_per_px_iter(c.h, c.psf_kind) for c in cases)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     with torch.cuda.stream(stream):
@@ -461,34 +520,31 @@ def run_batch(args, world, rank, local):
     ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     ms_w = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     ms_rrl = ms - ms_w
-    # end to end: page-locked host images in, results out, every step, through
-    # BatchStream (4 planned sub-batches; copies overlap the other sub-batches'
-    # runs).  Each step starts after the previous one has fully finished.
+    # end to end through the C ABI (db_batch_stream_run_host): page-locked
+    # host images in, results out, every step; 4 sub-batches whose copies
+    # overlap the other sub-batches' runs.  Each step starts after the
+    # previous one has fully finished (the call's stream waits for its
+    # downloads).
     f_host = [pinned_copy(c.f) for c in cases]
     u_host = [torch.empty(c.f.shape, dtype=torch.float32).pin_memory() for c in cases]
-    bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=4, device=dev)
-    bs.run(f_host, u_host)
+    with torch.cuda.stream(stream):
+        bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=4, device=dev)
+        bs.run(f_host, u_host)
     for a, b_ in zip(u_host, full.us):
         if not torch.equal(a, b_.cpu()):
             raise RuntimeError("streamed batch differs from the single batch")
     e2e = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
-    prev = None
-    for k in range(K):
-        with torch.cuda.stream(stream):
-            if prev is not None:
-                stream.wait_event(prev)
+    bs.ws.reset_status()
+    with torch.cuda.stream(stream):
+        for k in range(K):
             flush.fill_(float(k))
-            fl = torch.cuda.Event()
-            fl.record(stream)
-        bs.up.wait_event(fl)
-        e2e[k][0].record(bs.up)
-        bs.run(f_host, u_host, sync=False)
-        e2e[k][1].record(bs.down)
-        prev = e2e[k][1]
+            e2e[k][0].record(stream)
+            bs.run(f_host, u_host, sync=False)
+            e2e[k][1].record(stream)
     torch.cuda.synchronize()
-    for b_ in bs.batches:
-        b_.ws.raise_on_flags("streamed batch")
+    bs.ws.raise_on_flags("streamed batch")
     e2e_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in e2e)
+    e2e_parts = bs.parts
     bs.close()
     if world > 1:
         t = torch.tensor([ms, ms_w, e2e_ms], device=dev)
@@ -501,45 +557,61 @@ def run_batch(args, world, rank, local):
     if rank != 0:
         return
     px = px_total
-    peak = world * SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops_iter * iters / (ms_rrl / 1e3) / 1e12
-    hbm_peak, hbm_src = peaks()
+    pxi = px * iters
     line = {
-        "metric": METRIC, "value": px * iters / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": pxi / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch512: 512 f32 images, sides U{128..1024}, half 1D motion (box/raised "
-                               "cosine, L 5-41), half 2D Gaussian mixtures 7x7..25x25, sigma=2, Wiener K=0.006 "
-                               "+ 10 RRRL; one planned batch replayed from a CUDA graph",
-                   "pixels": px, "iters": iters, "l2": "inputs 0.7 GB > L2; L2 flushed before every step",
+        "config": {"workload": BATCH512_DESC, "images": len(all_cases), "pixels": px, "iters": iters,
+                   "l2": "inputs 0.7 GB > L2; L2 flushed before every step (256 MiB write)",
                    "parallelism": f"images sharded by LPT over {world} ranks" if world > 1 else "1 GPU"},
-        "rrrl_only_mpx_iter_s": px * iters / (ms_rrl / 1e3) / 1e6, "wiener_ms": ms_w,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_rrl_batch (persistent, all RRRL iterations of all images)",
-                     "kernel_ms": ms_rrl, "peak_src": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x 2032 MHz",
-                     "hbm_equiv_gbs": 28.0 * px * iters / (ms_rrl / 1e3) / 1e9,
-                     "hbm_equiv_frac": 28.0 * px * iters / (ms_rrl / 1e3) / 1e9 / hbm_peak},
-        "e2e": {"value": px * iters / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+        "rrrl_only_mpx_iter_s": pxi / (ms_rrl / 1e3) / 1e6, "wiener_ms": ms_w, "rrrl_ms": ms_rrl,
+        "roofline": hbm_roofline(ALGO_BYTES["spatial"], pxi, ms_rrl,
+                                 "k_rrl_batch (persistent: all RRRL iterations of all images in one launch)",
+                                 traffic=(BATCH_DRAM_BYTES_PER_PX_ITER * pxi
+                                          if BATCH_DRAM_BYTES_PER_PX_ITER and len(all_cases) == 512 else None),
+                                 flops=flops_iter * iters, world=world),
+        "e2e": {"value": pxi / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * px, "d2h_bytes_per_step": 4 * px, "ms_per_step": e2e_ms,
-                "path": "BatchStream: 4 planned sub-batches, copies overlapped with the other sub-batches' runs"},
+                "path": f"db_batch_stream_run_host (C ABI): {e2e_parts} sub-batches, page-locked host images, "
+                        "copies overlapped with the other sub-batches' runs"},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0,
         "plan_s": plan_s, "generate_s": gen_s, "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
-        import oracle
-        t0 = time.perf_counter()
-        sample_px = 0
-        for c in (all_cases[0], all_cases[len(all_cases) // 2]):
-            oracle.wr3l(c.f, c.h, c.params, 2)
-            sample_px += c.f.size * 2
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": sample_px / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(),
-                                "kind": "oracle", "sample": f"FP64 oracle, Wiener + 2 RRRL on images 0 and 256 "
-                                                            f"({all_cases[0].f.shape}, {all_cases[len(all_cases) // 2].f.shape}), "
-                                                            f"{dt:.1f} s"}
-    print(json.dumps(line), flush=True)
+        line["cpu_baseline"] = cpu_baseline_batch(all_cases)
+    return line
+
+
+def batch_sample_order(n):
+    """Images of the batch interleaved from its two halves (1D PSFs, 2D
+    Gaussian mixtures): 0, n/2, 1, n/2+1, ..."""
+    half = n // 2
+    out = []
+    for i in range(half):
+        out += [i, half + i]
+    return out + list(range(2 * half, n))
+
+
+def cpu_baseline_batch(all_cases, budget_s=10.0):
+    """The FP64 oracle as it stands on the host cores: the whole pipeline
+    (Wiener + every RRRL iteration) on images of the batch in the interleaved
+    order, until about `budget_s` seconds have passed (at least two images)."""
+    import oracle
+    t0 = time.perf_counter()
+    pxi, done = 0, []
+    for i in batch_sample_order(len(all_cases)):
+        c = all_cases[i]
+        oracle.wr3l(c.f, c.h, c.params, c.iters)
+        pxi += c.f.size * c.iters
+        done.append(i)
+        if len(done) >= 2 and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pxi / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle (torch CPU ops), Wiener + {all_cases[0].iters} RRRL on {len(done)} of the "
+                      f"batch's images (1D and 2D PSFs alternating: {done}), {dt:.1f} s"}
 
 
 def run_learn(args, world, rank, local):
@@ -668,10 +740,6 @@ def run_learn(args, world, rank, local):
     if rank != 0:
         return
     pxi = N_all * H * W * iters
-    hbm_peak, hbm_src = peaks()
-    # algorithmic bytes per pixel and iteration: forward 12, backward (recompute
-    # 12 + reverse reads u, f, U', writes U') 28
-    ach = 40.0 * pxi / (ms / 1e3) / 1e9
     line = {
         "metric": METRIC + " (forward + backward)", "value": pxi / (ms / 1e3) / 1e6, "unit": UNIT,
         "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -683,16 +751,14 @@ def run_learn(args, world, rank, local):
                    "l2": "working set 0.6 GB > L2"},
         "forward_only_mpx_iter_s": pxi / (ms_f / 1e3) / 1e6, "forward_ms": ms_f,
         "backward_over_forward": (ms - ms_f) / ms_f,
-        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak * world, "unit": "GB/s",
-                     "frac": ach / (hbm_peak * world),
-                     "traffic": None, "kernel": "whole fwd+bwd step (40 B/px*iter algorithmic)",
-                     "peak_src": hbm_src},
+        "roofline": hbm_roofline(ALGO_BYTES["adjoint"], pxi, ms,
+                                 "whole fwd+bwd step (reverse mode: 28 algorithmic B/px*iter)", world=world),
         "e2e": {"value": pxi / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * N_all * H * W * 4, "d2h_bytes_per_step": (taps.numel() + 3) * 8,
                 "ms_per_step": e2e_ms},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0, "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_stream(args, world, rank, local):
@@ -774,7 +840,7 @@ def run_stream(args, world, rank, local):
                 "ms_per_step": ms},
         "gpu_launches": launches * K, "launches_per_step": launches, "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -794,14 +860,20 @@ def main():
             db.set_rf_eval(args.rf)
         if args.impl == "reference":
             run_reference(args, world, rank)
-        elif args.workload == "batch512":
-            run_batch(args, world, rank, local)
-        elif args.workload == "learn512":
-            run_learn(args, world, rank, local)
-        elif args.workload == "stream1024":
-            run_stream(args, world, rank, local)
-        else:
-            run_ours(args, world, rank, local)
+            return
+        runner = {"batch512": run_batch, "learn512": run_learn, "stream1024": run_stream}.get(args.workload, run_ours)
+        line = runner(args, world, rank, local)
+        if args.workload == "batch512" and world == 1 and not args.no_sub and args.images == 512:
+            # the other workloads at their own sizes, each with its roofline
+            sub_args = argparse.Namespace(**{**vars(args), "steps": min(args.steps, 10), "no_cpu_baseline": True})
+            line["workloads"] = {}
+            for name, fn in (("line1024", run_ours), ("gauss2048", run_ours), ("learn512", run_learn)):
+                r = fn(sub_args, world, rank, local, name) if fn is run_ours else fn(sub_args, world, rank, local)
+                if r is not None:
+                    line["workloads"][name] = {k: r[k] for k in ("value", "unit", "ms_per_step", "roofline", "e2e",
+                                                                 "config", "clocks") if k in r}
+        if line is not None:
+            print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -210,6 +210,41 @@ void db_batch_destroy(db_batch* b);
 db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
                           int* dev_status, void* stream);
 
+/* ---- batches from host memory ------------------------------------------------
+ * The batch above, fed from and returned to HOST memory, with the transfers
+ * overlapped with the work (the paper reports its host-device transfers
+ * separately, Sec. 5.3; this form hides most of them).  The images are split
+ * into `parts` sub-batches of about equal pixel count (longest processing
+ * time first; fewer when n < parts), each an ordinary batch plan over its
+ * share of the workspace.  db_batch_stream_run_host enqueues, per
+ * sub-batch k: the copies of its host images into the descriptors' DEVICE
+ * buffers f on an internal upload stream, its run on `stream` once those
+ * copies have landed, and the copies of its results (the descriptors'
+ * DEVICE buffers u) to the host on an internal download stream.  So the
+ * uploads of later sub-batches and the downloads of earlier ones overlap the
+ * runs.  The uploads start after all work enqueued on `stream` before the
+ * call; `stream` itself waits for every download before anything enqueued
+ * after the call, so synchronising `stream` makes u_host valid.  Each
+ * image's result equals db_deblur's for it, whatever `parts` is.
+ *   descs: HOST array of n descriptors (as for db_batch_create); the device
+ *     buffers f and u serve as staging and must stay allocated.
+ *   f_host[i], u_host[i]: HOST pointers to H x W floats (rows packed, no
+ *     pitch), preferably page-locked (db_host_alloc); pageable memory works
+ *     but its copies do not overlap.
+ *   Errors: DB_ERR_ARG (null pointers, parts < 1), DB_ERR_WORKSPACE, and the
+ *   codes of db_batch_create; the object owns two streams and a few events,
+ *   released by db_batch_stream_destroy (which does not synchronise: finish
+ *   the runs first).  Not capturable (it waits on events across streams). */
+typedef struct db_batch_stream db_batch_stream;
+size_t db_batch_stream_workspace_bytes(const db_image_desc* descs, int n, int iters, int parts);
+db_status db_batch_stream_create(const db_image_desc* descs, int n, int iters, int parts, void* ws,
+                                 size_t ws_bytes, int* dev_status, void* stream, db_batch_stream** out);
+db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_host, float* const* u_host,
+                                   int* dev_status, void* stream);
+/* Number of sub-batches actually planned. */
+int db_batch_stream_parts(const db_batch_stream* b);
+void db_batch_stream_destroy(db_batch_stream* b);
+
 /* Clock-cycle budget of every bounded device wait (grid barriers of the
  * batch kernel); default 4e9 (about two seconds). */
 db_status db_set_spin_limit(long long cycles);
@@ -225,12 +260,19 @@ db_status db_set_spin_limit(long long cycles);
  * scratch from a fixed array of DB_NOALLOC_SCRATCH_BYTES bytes compiled into
  * the library, which every GPU that loads the library keeps until the
  * process exits.
- *   - Images whose db_workspace_bytes(H, W, psf, p) exceeds
- *     DB_NOALLOC_SCRATCH_BYTES are rejected with DB_ERR_WORKSPACE before
- *     anything is enqueued (a 1024 x 1024 image with a 2D PSF fits).
+ *   - The scratch holds what db_rrl_iterate itself uses: the tap records,
+ *     one ping-pong image (H x W floats, rows padded to 4), the q buffer of
+ *     the split schedule (H x W float pairs, rows padded to 2) and the flow
+ *     schedule's counters -- about 12 bytes per pixel, so images up to
+ *     about 2.7 Mpx fit (1024 x 1024 with a 2D PSF takes 12.1 MiB; in
+ *     periodic mode the spectra count too, 44 MiB at 1024 x 1024).  Larger
+ *     requests are rejected with DB_ERR_WORKSPACE before anything is
+ *     enqueued.
  *   - The first call on a device looks up the array's device address (with
  *     that device current), which may load the library's module: make that
- *     first call before any CUDA stream capture.
+ *     first call before any CUDA stream capture.  The address is kept for
+ *     the life of the device's context; after cudaDeviceReset this entry
+ *     point must not be called again in the process.
  *   - All calls on a device share the one array.  Calls whose work overlaps
  *     on the GPU (different streams, different host threads) race on it and
  *     give undefined results; serialise them.  The array keeps the last

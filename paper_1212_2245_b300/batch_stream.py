@@ -1,25 +1,21 @@
 """A batch of host images deblurred with the transfers overlapped.
 
-The images are split into `parts` planned sub-batches of about equal work
-(longest-processing-time assignment on pixels x iterations).  An upload
-stream copies every sub-batch's images in from page-locked host memory; the
-compute stream replays sub-batch k's captured run as soon as its copies have
-landed; a download stream copies sub-batch k's results out as soon as its run
-has finished.  So the copies of later sub-batches overlap the runs of earlier
-ones, and the results of earlier ones go out while later ones run.  Events
-order the three queues:
-    upload(k) -> compute(k) -> download(k)
-and, across calls,
-    compute(k) of the previous call before upload(k) overwrites its inputs,
-    download(k) of the previous call before compute(k) overwrites its outputs.
-Each sub-batch is an ordinary Batch, whose images equal single-image runs bit
-for bit, so the results do not depend on `parts`.
+A thin binding of the library's streamed batch (db_batch_stream_*): the
+images are split into `parts` sub-batches of about equal pixel count; for
+each sub-batch the library copies its host images in on an upload stream,
+runs it on the caller's stream once they have landed, and copies its
+results out on a download stream, so the transfers of the other sub-batches
+overlap each run.  Synchronising the caller's stream makes the host results
+valid.  Each sub-batch is an ordinary planned batch, whose images equal
+single-image runs bit for bit, so the results do not depend on `parts`.
 """
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
-from . import Batch, shard
+from . import DeblurError, Workspace, _check, _db_params, _db_psf, _lib, _stream
 
 
 class BatchStream:
@@ -33,73 +29,62 @@ class BatchStream:
         kinds = list(kinds) if kinds is not None else ["general"] * n
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        # device staging buffers of the library's copies
         self.fs = [torch.empty(s, device=self.device) for s in self.shapes]
         self.us = [torch.empty(s, device=self.device) for s in self.shapes]
-        costs = shard.image_costs(self.shapes, iters)
-        self.parts = [p for p in shard.lpt_partition(costs, min(parts, n)) if p]
-        self.compute = torch.cuda.Stream(device=self.device)
-        self.up = torch.cuda.Stream(device=self.device)
-        self.down = torch.cuda.Stream(device=self.device)
-        self.batches, self.graphs = [], []
-        with torch.cuda.stream(self.compute):
-            for idx in self.parts:
-                for i in idx:  # any positive image for the first run
-                    self.fs[i].fill_(max(1.0, float(params[i].pos_floor)))
-                b = Batch([self.fs[i] for i in idx], [taps[i] for i in idx], [params[i] for i in idx], iters,
-                          kinds=[kinds[i] for i in idx], outs=[self.us[i] for i in idx])
-                b.run()  # first run outside capture: module loading, attributes
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g, stream=self.compute):
-                    b.run(check=False)
-                self.batches.append(b)
-                self.graphs.append(g)
-        self.compute.synchronize()
-        self._done = [None] * len(self.parts)   # compute finished (previous call)
-        self._down = [None] * len(self.parts)   # download finished (previous call)
+        self.taps = list(taps)
+        descs = (_lib.DbImageDesc * n)()
+        for k, (H, W) in enumerate(self.shapes):
+            descs[k] = _lib.DbImageDesc(self.fs[k].data_ptr(), self.us[k].data_ptr(), H, W, W,
+                                        _db_psf(self.taps[k], kinds[k]), _db_params(params[k]))
+        self._descs = descs
+        lib = _lib.load()
+        nbytes = lib.db_batch_stream_workspace_bytes(descs, n, int(iters), int(parts))
+        if nbytes == 0:
+            raise DeblurError("invalid batch descriptors")
+        self.ws = Workspace(nbytes, self.device)
+        self.ws.reset_status()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.db_batch_stream_create(descs, n, int(iters), int(parts), self.ws.ptr, self.ws.nbytes,
+                                              self.ws.status.data_ptr(), _stream(), ctypes.byref(h)),
+                   "db_batch_stream_create")
+        self._h = h
+        self.parts = int(lib.db_batch_stream_parts(h))
+        torch.cuda.current_stream(self.device).synchronize()
 
     def run(self, f_host, u_host, sync: bool = True):
-        """Deblur host images f_host[i] (page-locked float32, shape shapes[i])
-        into u_host[i].  With sync=False the call returns once everything is
-        enqueued; the caller synchronises the download stream (`self.down`)."""
-        if len(f_host) != len(self.shapes) or len(u_host) != len(self.shapes):
+        """Deblur host images f_host[i] (float32, shape shapes[i], contiguous;
+        page-locked for overlapped copies) into u_host[i], on the current
+        stream.  With sync=False the call returns once everything is enqueued;
+        the results are valid after the current stream has been synchronised."""
+        n = len(self.shapes)
+        if len(f_host) != n or len(u_host) != n:
             raise ValueError("one host input and one host output per image")
-        for b in self.batches:
-            with torch.cuda.stream(self.compute):
-                b.ws.reset_status()
-        ups = []
-        for k, idx in enumerate(self.parts):
-            with torch.cuda.stream(self.up):
-                if self._done[k] is not None:
-                    self.up.wait_event(self._done[k])  # the previous run no longer reads these inputs
-                for i in idx:
-                    self.fs[i].copy_(f_host[i], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self.up)
-                ups.append(ev)
-        for k, idx in enumerate(self.parts):
-            with torch.cuda.stream(self.compute):
-                self.compute.wait_event(ups[k])
-                if self._down[k] is not None:
-                    self.compute.wait_event(self._down[k])  # the previous download has read the outputs
-                self.graphs[k].replay()
-                done = torch.cuda.Event()
-                done.record(self.compute)
-                self._done[k] = done
-            with torch.cuda.stream(self.down):
-                self.down.wait_event(done)
-                for i in idx:
-                    u_host[i].copy_(self.us[i], non_blocking=True)
-                dn = torch.cuda.Event()
-                dn.record(self.down)
-                self._down[k] = dn
+        fp = (ctypes.c_void_p * n)()
+        up = (ctypes.c_void_p * n)()
+        for i, (a, b) in enumerate(zip(f_host, u_host)):
+            for t, what in ((a, "f_host"), (b, "u_host")):
+                if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous() or \
+                        tuple(t.shape) != self.shapes[i]:
+                    raise ValueError(f"{what}[{i}] must be a contiguous float32 host tensor of shape {self.shapes[i]}")
+            fp[i], up[i] = a.data_ptr(), b.data_ptr()
         if sync:
-            self.down.synchronize()
-            self.compute.synchronize()
-            for b in self.batches:
-                b.ws.raise_on_flags("streamed batch")
+            self.ws.reset_status()
+        _check(_lib.load().db_batch_stream_run_host(self._h, fp, up, self.ws.status.data_ptr(), _stream()),
+               "db_batch_stream_run_host")
+        if sync:
+            torch.cuda.current_stream(self.device).synchronize()
+            self.ws.raise_on_flags("streamed batch")
         return u_host
 
     def close(self):
-        for b in self.batches:
-            b.close()
-        self.batches = []
+        if getattr(self, "_h", None):
+            _lib.load().db_batch_stream_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

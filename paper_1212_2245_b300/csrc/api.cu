@@ -22,22 +22,24 @@ int one_axis_min(bool row) {
 }
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n) {
+WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n, bool iterate_only) {
+  const bool spatial_only = iterate_only && conv != DB_CONV_PERIODIC;
   WsLayout L = {};
   size_t off = 0;
-  L.taps = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
+  L.taps = off;  off += tap_region_bytes(kh, kw);
   L.ntaps = off; off += kAuxBytes;
   L.utmp = off;  off += align256((size_t)n * H * upitch(W) * sizeof(float));
-  L.qbuf = off;  off += align256((size_t)n * H * qpitch(W) * sizeof(float2));
+  L.qbuf = off;  off += align256((size_t)n * H * upitch(W) * sizeof(float2));
   size_t spec_elems, work_elems;
   if (conv == DB_CONV_PERIODIC) { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
   else if (kh == 1) { spec_elems = (size_t)W; work_elems = 0; }
   else if (kw == 1) { spec_elems = (size_t)H; work_elems = 0; }
   else { spec_elems = (size_t)H * W; work_elems = (size_t)H * W; }
+  if (spatial_only) { spec_elems = 0; work_elems = 0; }
   L.spec = off;  off += align256(spec_elems * sizeof(float4));
   L.work = off;  off += align256(work_elems * sizeof(float4));
   L.s32 = off;   off += (conv == DB_CONV_PERIODIC) ? align256((size_t)H * W * sizeof(float2)) : 0;
-  L.tw = off;    off += align256((dft_table_elems(W) + dft_table_elems(H)) * sizeof(float4));
+  L.tw = off;    off += spatial_only ? 0 : align256((dft_table_elems(W) + dft_table_elems(H)) * sizeof(float4));
   L.flow = off;  off += (conv == DB_CONV_PERIODIC) ? 0 : align256(flow_ws_bytes(H, W));
   L.total = off;
   return L;
@@ -121,7 +123,10 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   // window sums; the cluster schedule runs one-row PSFs on images that fit
   if (sched == DB_SCHED_CLUSTER && kh == 1 && axis == 0) axis = 2;
   if (sched == DB_SCHED_CLUSTER && (ckpt || !cluster_fits(H, W, kh, kw, axis))) sched = DB_SCHED_SPLIT;
-  if ((sched == DB_SCHED_FLOW && ckpt) || (sched == DB_SCHED_FUSED && axis == 1)) sched = DB_SCHED_SPLIT;
+  // dense-eligible 2D PSFs run the split pair with the dense tile bodies
+  if ((sched == DB_SCHED_FLOW && (ckpt || (axis == 0 && dense_eligible(kh, kw)))) ||
+      (sched == DB_SCHED_FUSED && axis == 1))
+    sched = DB_SCHED_SPLIT;
   if (sched == DB_SCHED_FUSED) axis = 0;
   if (sched == DB_SCHED_CLUSTER) {
     const cudaError_t e = launch_rrl_cluster(f, ld, u, ld, H, W, ngroups, kw, axis, rp, iters, dev_status, s);
@@ -217,7 +222,8 @@ db_status db_rrl_iterate(const float* f, float* u, int H, int W, int ld, const d
   if (iters < 0) return DB_ERR_ARG;
   if (ckpt && ckpt_every < 1) return DB_ERR_ARG;
   if (f == u) return DB_ERR_ARG;
-  const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv);
+  // spatial mode touches only the iteration regions (rrl_iterate_ws_bytes)
+  const WsLayout L = ws_layout(H, W, psf->kh, psf->kw, p->conv, 1, true);
   if ((st = check_ws(ws, ws_bytes, L.total)) != DB_OK) return st;
   if (p->conv == DB_CONV_PERIODIC && !(is_pow2(H) && is_pow2(W))) return DB_ERR_UNSUPPORTED;
   if (iters == 0) return DB_OK;
@@ -308,7 +314,7 @@ db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, lon
   float* tmp = (float*)(base + L.utmp);
   float2* qbuf = (float2*)(base + L.qbuf);
   const int ldt = upitch(W);
-  const long long zt = (long long)H * ldt, zq = (long long)H * qpitch(W), hw = (long long)H * W;
+  const long long zt = (long long)H * ldt, zq = (long long)H * upitch(W), hw = (long long)H * W;
   const int nck = ckpt ? (iters > 0 ? (iters - 1) / ckpt_every + 1 : 1) : 0;
   const float* src = u;
   int ld_src = ld;
@@ -337,6 +343,15 @@ db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, lon
 }
 
 }  // extern "C"
+
+namespace db {
+// Workspace db_rrl_iterate alone needs (no Wiener regions in spatial mode).
+size_t rrl_iterate_ws_bytes(int H, int W, const db_psf* psf, const db_params* p) {
+  if (db_workspace_bytes(H, W, psf, p) == 0) return 0;
+  return ws_layout(H, W, psf->kh, psf->kw, p->conv, 1, true).total;
+}
+}  // namespace db
+
 
 namespace db {
 struct SinglePlan {

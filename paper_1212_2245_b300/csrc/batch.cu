@@ -18,11 +18,13 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "fft_df.cuh"
 #include "internal.cuh"
 #include "rrl_box.cuh"
+#include "rrl_dense.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -38,6 +40,7 @@ struct BatchImg {
   int H, W, kh, kw, ng_max, P;
   int box;       // 0: tap groups; 1, 2: horizontal, vertical box (sliding-window sums);
                  // 3, 4: other horizontal, vertical one-axis PSF (register windows)
+  int kwd;       // dense-eligible 2D PSF: kw (the dense flag then picks the bodies); else 0
   RrlParams p;
 };
 
@@ -68,8 +71,38 @@ __device__ __noinline__ void batch_box(int phase, unsigned char* smem, const Bat
                                                  im.p, status, i0, j0);
 }
 
+template <int KW>
+__device__ __noinline__ void batch_dense(int phase, unsigned char* smem, const BatchImg& im, const float* src,
+                                         int lds, float* dst, int ldd, int* status, int i0, int j0) {
+  const int ldp = upitch(im.W);
+  float* qe = reinterpret_cast<float*>(im.q);
+  float* qw = qe + (size_t)im.H * ldp;
+  const float* tab = dense_taps(im.groups, im.kh, im.kw);
+  if (phase == 0)
+    q_tile_dense<kBTH, kBTW, KW>(smem, im.f, im.ldf, src, lds, qe, qw, ldp, im.H, im.W, tab, im.kh, im.p, i0, j0);
+  else
+    update_tile_dense<kBTH, kBTW, KW>(smem, qe, qw, ldp, src, lds, dst, ldd, im.H, im.W, tab, im.kh, im.p, status,
+                                      i0, j0);
+}
+
 __device__ __forceinline__ void batch_tile(int phase, unsigned char* smem, const BatchImg& im, const float* src,
                                            int lds, float* dst, int ldd, int* status, int i0, int j0) {
+  if (im.kwd && __ldg(dense_flag(im.ngroups))) {
+    switch (im.kwd) {
+      case 3: batch_dense<3>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 5: batch_dense<5>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 7: batch_dense<7>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 9: batch_dense<9>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 11: batch_dense<11>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 13: batch_dense<13>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 15: batch_dense<15>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 17: batch_dense<17>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 19: batch_dense<19>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 21: batch_dense<21>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      case 23: batch_dense<23>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+      default: batch_dense<25>(phase, smem, im, src, lds, dst, ldd, status, i0, j0); return;
+    }
+  }
 #define DB_BATCH_CASE(PV)                                           \
   case PV:                                                          \
     if (phase == 0) batch_q<PV>(smem, im, src, lds, i0, j0);        \
@@ -154,6 +187,22 @@ __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict
 
 static std::atomic<long long> g_spin_limit{4000000000LL};  // ~2 s at 2 GHz
 
+// Largest dynamic shared memory k_rrl_batch has been allowed on each device.
+static std::mutex g_smem_mutex;
+static std::map<int, size_t> g_smem_limit;
+
+static cudaError_t raise_batch_smem_limit(size_t smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_smem_mutex);
+  size_t& cur = g_smem_limit[dev];
+  if (smem <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_rrl_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) cur = smem;
+  return e;
+}
+
 void set_spin_limit(long long cycles) {
   g_spin_limit.store(cycles);
   set_flow_spin_limit(cycles);
@@ -183,10 +232,10 @@ struct ImgRegions {
 
 static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
   ImgRegions r;
-  r.groups = off;  off += align256((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup));
+  r.groups = off;  off += tap_region_bytes(kh, kw);
   r.ngroups = off; off += kAuxBytes;
   r.utmp = off;    off += align256((size_t)H * upitch(W) * sizeof(float));
-  r.q = off;       off += align256((size_t)H * qpitch(W) * sizeof(float2));
+  r.q = off;       off += align256((size_t)H * upitch(W) * sizeof(float2));
   size_t spec = (kh == 1) ? (size_t)W : (kw == 1) ? (size_t)H : (size_t)H * W;
   r.spec = off;    off += align256(spec * sizeof(float4));
   r.work = off;    off += (kh > 1 && kw > 1) ? align256((size_t)H * W * sizeof(float4)) : 0;
@@ -309,13 +358,16 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.P = split_halo_class(kw);
     const int axis = axis_mode(x.psf.kind, kh, kw);
     bi.box = axis == 0 ? 0 : (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
+    bi.kwd = (axis == 0 && dense_eligible(kh, kw)) ? kw : 0;
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
     bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
     bi.p.rf_lut = rf_lut_device();
-    const size_t sm = bi.box ? std::max(box_smem_q(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1),
-                                        box_smem_update(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1))
-                             : std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),
-                                        split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max));
+    size_t sm = bi.box ? std::max(box_smem_q(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1),
+                                  box_smem_update(kBTH, kBTW, kh == 1 ? kw : kh, kh == 1))
+                       : std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),
+                                  split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max));
+    if (bi.kwd)
+      sm = std::max(sm, std::max(dense_smem_q(kBTH, kBTW, kh, kw), dense_smem_update(kBTH, kBTW, kh, kw)));
     if (sm > P->smem) P->smem = sm;
     for (int i0 = 0; i0 < x.H; i0 += kBTH)
       for (int j0 = 0; j0 < x.W; j0 += kBTW) P->tiles.push_back(make_int4(i, i0, j0, bi.ng_max));
@@ -340,9 +392,10 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
           cudaSuccess) {
     delete P; return DB_ERR_CUDA;
   }
-  // persistent grid: every co-resident CTA
-  if (P->smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_rrl_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem) != cudaSuccess) {
+  // persistent grid: every co-resident CTA.  The kernel's shared-memory
+  // limit only ever grows (per device), so that plans made earlier with
+  // larger tiles keep launching.
+  if (P->smem > 48 * 1024 && raise_batch_smem_limit(P->smem) != cudaSuccess) {
     (void)cudaGetLastError();
     delete P; return DB_ERR_UNSUPPORTED;
   }
@@ -389,6 +442,71 @@ db_status batch_run(const BatchPlan* P, int* status, cudaStream_t s) {
 
 void batch_destroy(BatchPlan* P) { delete P; }
 
+// ---------------------------------------------------------------------------
+// streamed batch: host images in, results out, the copies overlapped with
+// the runs of other sub-batches
+// ---------------------------------------------------------------------------
+// Longest-processing-time partition of the images into `parts` groups by
+// pixel count (ties to the lowest group); each group keeps ascending image
+// order.  The largest group load is within 4/3 of the optimum.
+static std::vector<std::vector<int>> lpt_parts(const db_image_desc* d, int n, int parts) {
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)d[a].H * d[a].W > (long long)d[b].H * d[b].W;
+  });
+  std::vector<long long> load(parts, 0);
+  std::vector<std::vector<int>> out(parts);
+  for (int i : order) {
+    int k = 0;
+    for (int j = 1; j < parts; ++j)
+      if (load[j] < load[k]) k = j;
+    load[k] += (long long)d[i].H * d[i].W;
+    out[k].push_back(i);
+  }
+  for (auto& v : out) std::sort(v.begin(), v.end());
+  out.erase(std::remove_if(out.begin(), out.end(), [](const std::vector<int>& v) { return v.empty(); }),
+            out.end());
+  return out;
+}
+
+struct BatchStream {
+  std::vector<db_image_desc> descs;
+  std::vector<std::vector<int>> idx;
+  std::vector<BatchPlan*> plans;
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> ev_up, ev_done, ev_down;
+  ~BatchStream() {
+    for (BatchPlan* P : plans) delete P;
+    for (auto* v : {&ev_up, &ev_done, &ev_down})
+      for (cudaEvent_t e : *v)
+        if (e) cudaEventDestroy(e);
+    if (start) cudaEventDestroy(start);
+    if (up) cudaStreamDestroy(up);
+    if (down) cudaStreamDestroy(down);
+  }
+};
+
+static size_t stream_ws_bytes(const db_image_desc* d, int n, int iters, int parts, db_status* why,
+                              std::vector<std::vector<int>>* idx_out, std::vector<size_t>* sizes) {
+  *why = DB_OK;
+  if (!d || n < 1 || parts < 1 || iters < 0) { *why = DB_ERR_ARG; return 0; }
+  if (batch_ws_bytes(d, n, iters, why) == 0) return 0;  // validates every descriptor
+  std::vector<std::vector<int>> idx = lpt_parts(d, n, std::min(parts, n));
+  size_t total = 0;
+  for (const auto& v : idx) {
+    std::vector<db_image_desc> sub;
+    for (int i : v) sub.push_back(d[i]);
+    const size_t b = batch_ws_bytes(sub.data(), (int)sub.size(), iters, why);
+    if (b == 0) return 0;
+    if (sizes) sizes->push_back(align256(b));
+    total += align256(b);
+  }
+  if (idx_out) *idx_out = idx;
+  return total;
+}
+
 }  // namespace db
 
 using namespace db;
@@ -427,6 +545,100 @@ db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws
   db_batch_destroy(b);
   return st;
 }
+
+size_t db_batch_stream_workspace_bytes(const db_image_desc* descs, int n, int iters, int parts) {
+  db_status why;
+  return stream_ws_bytes(descs, n, iters, parts, &why, nullptr, nullptr);
+}
+
+db_status db_batch_stream_create(const db_image_desc* descs, int n, int iters, int parts, void* ws,
+                                 size_t ws_bytes, int* dev_status, void* stream, db_batch_stream** out) {
+  if (!out) return DB_ERR_ARG;
+  *out = nullptr;
+  db_status why;
+  std::vector<std::vector<int>> idx;
+  std::vector<size_t> sizes;
+  const size_t need = stream_ws_bytes(descs, n, iters, parts, &why, &idx, &sizes);
+  if (need == 0) return why;
+  if (!ws || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return DB_ERR_WORKSPACE;
+  BatchStream* B = new BatchStream();
+  B->descs.assign(descs, descs + n);
+  B->idx = idx;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  for (size_t k = 0; k < idx.size(); ++k) {
+    std::vector<db_image_desc> sub;
+    for (int i : idx[k]) sub.push_back(descs[i]);
+    BatchPlan* P = nullptr;
+    const db_status st = batch_create(sub.data(), (int)sub.size(), iters, base, sizes[k], dev_status, s, &P);
+    if (st != DB_OK) { delete B; return st; }
+    B->plans.push_back(P);
+    base += sizes[k];
+  }
+  const size_t np = idx.size();
+  B->ev_up.assign(np, nullptr);
+  B->ev_done.assign(np, nullptr);
+  B->ev_down.assign(np, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&B->up, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&B->down, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->start, cudaEventDisableTiming) == cudaSuccess;
+  for (size_t k = 0; ok && k < np; ++k)
+    ok = cudaEventCreateWithFlags(&B->ev_up[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&B->ev_done[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&B->ev_down[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) { (void)cudaGetLastError(); delete B; return DB_ERR_CUDA; }
+  *out = (db_batch_stream*)B;
+  return DB_OK;
+}
+
+db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_host, float* const* u_host,
+                                   int* dev_status, void* stream) {
+  BatchStream* B = (BatchStream*)b;
+  if (!B || !f_host || !u_host) return DB_ERR_ARG;
+  const int n = (int)B->descs.size();
+  for (int i = 0; i < n; ++i)
+    if (!f_host[i] || !u_host[i]) return DB_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the copies in start after everything enqueued on `stream` before this call
+  if (cudaEventRecord(B->start, s) != cudaSuccess || cudaStreamWaitEvent(B->up, B->start, 0) != cudaSuccess)
+    return DB_ERR_CUDA;
+  const size_t np = B->plans.size();
+  for (size_t k = 0; k < np; ++k) {
+    for (int i : B->idx[k]) {
+      const db_image_desc& x = B->descs[i];
+      const size_t row = (size_t)x.W * sizeof(float);
+      if (cudaMemcpy2DAsync((void*)x.f, (size_t)x.ld * sizeof(float), f_host[i], row, row, x.H,
+                            cudaMemcpyHostToDevice, B->up) != cudaSuccess)
+        return DB_ERR_CUDA;
+    }
+    if (cudaEventRecord(B->ev_up[k], B->up) != cudaSuccess) return DB_ERR_CUDA;
+  }
+  for (size_t k = 0; k < np; ++k) {
+    if (cudaStreamWaitEvent(s, B->ev_up[k], 0) != cudaSuccess) return DB_ERR_CUDA;
+    const db_status st = batch_run(B->plans[k], dev_status, s);
+    if (st != DB_OK) return st;
+    if (cudaEventRecord(B->ev_done[k], s) != cudaSuccess || cudaStreamWaitEvent(B->down, B->ev_done[k], 0) != cudaSuccess)
+      return DB_ERR_CUDA;
+    for (int i : B->idx[k]) {
+      const db_image_desc& x = B->descs[i];
+      const size_t row = (size_t)x.W * sizeof(float);
+      if (cudaMemcpy2DAsync(u_host[i], row, x.u, (size_t)x.ld * sizeof(float), row, x.H, cudaMemcpyDeviceToHost,
+                            B->down) != cudaSuccess)
+        return DB_ERR_CUDA;
+    }
+    if (cudaEventRecord(B->ev_down[k], B->down) != cudaSuccess) return DB_ERR_CUDA;
+  }
+  // `stream` completes only after every result has reached the host
+  for (size_t k = 0; k < np; ++k)
+    if (cudaStreamWaitEvent(s, B->ev_down[k], 0) != cudaSuccess) return DB_ERR_CUDA;
+  return DB_OK;
+}
+
+int db_batch_stream_parts(const db_batch_stream* b) {
+  return b ? (int)((const BatchStream*)b)->plans.size() : 0;
+}
+
+void db_batch_stream_destroy(db_batch_stream* b) { delete (BatchStream*)b; }
 
 db_status db_set_spin_limit(long long cycles) {
   if (cycles < 0) return DB_ERR_ARG;

@@ -94,17 +94,18 @@ inline int axis_mode(int kind, int kh, int kw) {
 }
 // Row pitches of workspace images: float rows padded to 16 bytes, float2
 // (q) rows to an even count, so that tile staging can copy 16-byte chunks.
-inline int upitch(int W) { return (W + 3) & ~3; }
-inline int qpitch(int W) { return (W + 1) & ~1; }
+__host__ __device__ inline int upitch(int W) { return (W + 3) & ~3; }
+__host__ __device__ inline int qpitch(int W) { return (W + 1) & ~1; }
 inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 // Workspace layout for one image (offsets in bytes from ws).
 struct WsLayout {
-  size_t taps;     // TapGroup[max_tap_groups(kh, kw)]
+  size_t taps;     // tap_region_bytes(kh, kw): TapGroup[max_tap_groups(kh, kw)], dense table
   size_t ntaps;    // kAuxBytes: group count, one-axis weights and taps
   size_t utmp;     // float[H*upitch(W)]  (RRRL ping-pong)
-  size_t qbuf;     // float2[H*qpitch(W)] (split schedule: q = (e, W); Fourier mode: Z)
+  size_t qbuf;     // float2[H*upitch(W)] (split schedule: q = (e, W) interleaved with pitch qpitch(W),
+                   // or planar e, W planes of pitch upitch(W) for dense PSFs; Fourier mode: Z)
   size_t spec;     // float4[spec_elems]  (PSF spectrum, float-float)
   size_t work;     // float4[work_elems]  (Wiener rows, float-float; Fourier mode: X)
   size_t s32;      // float2[H*W]         (Fourier mode: FP32 PSF spectrum)
@@ -112,13 +113,44 @@ struct WsLayout {
   size_t flow;     // flow_ws_bytes(H, W): task counter and per-tile progress counters
   size_t total;
 };
-WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n = 1);  // n: images sharing it
+// n: images sharing it.  iterate_only: the regions db_rrl_iterate reads in
+// spatial mode (taps, ping-pong, q, flow counters), without the Wiener
+// spectrum, work rows and transform tables.
+WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n = 1, bool iterate_only = false);
+// Bytes of the iterate_only layout (0 for invalid arguments).
+size_t rrl_iterate_ws_bytes(int H, int W, const db_psf* psf, const db_params* p);
 // Copy n images of H x W: image z from src + z*zsrc (pitch lds) to dst + z*zdst (pitch ldd).
 cudaError_t copy_images(const float* src, int lds, long long zsrc, float* dst, int ldd, long long zdst, int H, int W,
                         int n, cudaStream_t s);
 
+// ---- tap tables ----------------------------------------------------------
+// Upper bound of the tap-group count of a kh x kw PSF.
+__host__ __device__ inline int max_tap_groups(int kh, int kw) { return kw * ((kh + 2) / 3); }
+// Dense 2D PSFs (rrl_dense.cuh): odd sides from 3 to kDenseMaxSide.  For
+// these shapes k_prepare_taps also writes the taps as a dense table (kh rows
+// of dense_tap_stride(kw) floats, 16-byte aligned) after the tap groups, and
+// sets the flag word dense_flag(ngroups) when at least half the taps are
+// non-zero: the split and batched tile bodies then use the dense sums.
+constexpr int kDenseMaxSide = 25;
+__host__ __device__ inline bool dense_eligible(int kh, int kw) {
+  return (kh & 1) && (kw & 1) && kh >= 3 && kw >= 3 && kh <= kDenseMaxSide && kw <= kDenseMaxSide;
+}
+__host__ __device__ inline int dense_tap_stride(int kw) { return (kw + 3) & ~3; }
+__host__ __device__ inline size_t tap_groups_bytes(int kh, int kw) {
+  return ((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup) + 255) & ~size_t(255);
+}
+// Bytes of the tap region of a workspace: the groups and the dense table.
+__host__ __device__ inline size_t tap_region_bytes(int kh, int kw) {
+  return tap_groups_bytes(kh, kw) +
+         (dense_eligible(kh, kw) ? (((size_t)kh * dense_tap_stride(kw) * 4 + 255) & ~size_t(255)) : 0);
+}
+__host__ __device__ inline const float* dense_taps(const TapGroup* groups, int kh, int kw) {
+  return (const float*)((const char*)groups + tap_groups_bytes(kh, kw));
+}
+// Flag word next to the group count: 1 when the dense sums are used.
+__host__ __device__ inline const int* dense_flag(const int* ngroups) { return ngroups + 1; }
+
 // ---- launchers (return cudaError_t of the launch) --------------------------
-int max_tap_groups(int kh, int kw);
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s);
 size_t rrl_spatial_smem(int kh, int kw);

@@ -7,7 +7,7 @@
 
 #include <mutex>
 
-#include "libdeblur.h"
+#include "internal.cuh"
 
 namespace {
 
@@ -21,7 +21,9 @@ std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device; the first call
-// per device does the lookup (with that device current).
+// per device does the lookup (with that device current).  The address stays
+// valid while the device's context lives: a cudaDeviceReset (which unloads
+// the library's module) invalidates it.
 db_status scratch_on_current_device(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return DB_ERR_CUDA;
@@ -42,7 +44,9 @@ db_status scratch_on_current_device(void** out) {
 extern "C" db_status db_rrl_iterate_noalloc(const float* f, float* u, int H, int W, int ld,
                                             const db_psf* psf, const db_params* p, int iters,
                                             int* dev_status, void* stream) {
-  const size_t need = db_workspace_bytes(H, W, psf, p);
+  // only the iteration's regions: spatial mode needs no Wiener spectrum,
+  // work rows or transform tables
+  const size_t need = db::rrl_iterate_ws_bytes(H, W, psf, p);
   if (need == 0) return DB_ERR_ARG;
   if (need > DB_NOALLOC_SCRATCH_BYTES) return DB_ERR_WORKSPACE;
   void* ws = nullptr;

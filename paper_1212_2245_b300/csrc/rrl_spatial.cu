@@ -21,6 +21,7 @@
 
 #include "internal.cuh"
 #include "rrl_box.cuh"
+#include "rrl_dense.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -78,21 +79,35 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
   __shared__ int scan[256];
   __shared__ int cstart[kMaxGroupH + 1];
   __shared__ float warp_sum[8];
-  __shared__ int bad;
+  __shared__ int bad, s_nnz;
   const int n = kh * kw;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) bad = 0;
+  if (threadIdx.x == 0) { bad = 0; s_nnz = 0; }
   __syncthreads();
   // a box is uniform except possibly for its two end taps (non-integer
   // blur length, Sec. 4.3)
   const float t1 = n > 2 ? __ldg(taps + 1) : 0.f;
   float sum = 0.f;
+  int nnz = 0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const float w = __ldg(taps + k);
     if (!(w >= 0.f) || !isfinite(w)) atomicOr(&bad, DB_FLAG_TAPS);
     if (kind == DB_PSF_BOX && k >= 1 && k <= n - 2 && w != t1) atomicOr(&bad, DB_FLAG_BOX);
     sum += w;
+    nnz += (w != 0.f);
   }
+  // dense table of an eligible 2D PSF: kh rows of dense_tap_stride(kw)
+  // floats, zero beyond column kw
+  if (dense_eligible(kh, kw)) {
+    float* tab = const_cast<float*>(dense_taps(groups, kh, kw));
+    const int TS = dense_tap_stride(kw);
+    for (int k = threadIdx.x; k < kh * TS; k += blockDim.x) {
+      const int r = k / TS, c = k - r * TS;
+      tab[k] = c < kw ? __ldg(taps + r * kw + c) : 0.f;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+  if (lane == 0) atomicAdd(&s_nnz, nnz);
   // one-axis PSFs: (e0, w, e1, L) 16 bytes after the group count, the taps
   // themselves 32 bytes after it
   if ((kh == 1 || kw == 1) && threadIdx.x == 0)
@@ -163,11 +178,11 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
     for (int i = 0; i < 8; ++i) s += warp_sum[i];
     if (!(s > 0.f)) bad |= DB_FLAG_TAPS;
     *ngroups = total > max_groups ? 0 : total;
+    // dense sums when at least half of an eligible PSF's taps are non-zero
+    ngroups[1] = (dense_eligible(kh, kw) && 2 * s_nnz >= n) ? 1 : 0;
     if (bad && status) atomicOr(status, bad);
   }
 }
-
-int max_tap_groups(int kh, int kw) { return kw * ((kh + 2) / 3); }
 
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s) {
@@ -224,6 +239,48 @@ __global__ void __launch_bounds__((TH / R) * TW, 7) k_rrl_update(const float2* _
   update_tile<TH, TW, R, P>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H, W,
                                groups_g, ngroups_g, kh, kw, ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW,
                                PdlDep());
+}
+
+// Dense-eligible 2D PSFs (odd sides 3..25): the split pair with the dense
+// bodies when the prepared flag says so (at least half the taps non-zero),
+// else the tap-group bodies; q is planar for the dense bodies.
+template <int TH, int TW, int KW>
+__global__ void __launch_bounds__((TH / kDR) * (TW / kDC), 6) k_rrl_q_dense(
+    const float* __restrict__ f, int ldf, const float* __restrict__ uin, int ldin, float2* __restrict__ q, int ldq,
+    int H, int W, const TapGroup* __restrict__ groups_g, const int* __restrict__ ngroups_g, int kh, int kw,
+    int ng_max, RrlParams p, ZStride zs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long z = blockIdx.z;
+  if (__ldg(dense_flag(ngroups_g))) {
+    float* qe = reinterpret_cast<float*>(q + z * zs.q);
+    q_tile_dense<TH, TW, KW>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, qe, qe + (size_t)H * upitch(W),
+                             upitch(W), H, W, dense_taps(groups_g, kh, kw), kh, p, blockIdx.y * TH, blockIdx.x * TW,
+                             PdlDep());
+  } else {
+    constexpr int P = (KW + 2 <= 8) ? 8 : (KW + 2 <= 16) ? 16 : 32;
+    q_tile<TH, TW, 8, P>(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, q + z * zs.q, ldq, H, W, groups_g,
+                         ngroups_g, kh, kw, ng_max, p, blockIdx.y * TH, blockIdx.x * TW, PdlDep());
+  }
+}
+
+template <int TH, int TW, int KW>
+__global__ void __launch_bounds__((TH / kDR) * (TW / kDC), 6) k_rrl_update_dense(
+    const float2* __restrict__ q, int ldq, const float* __restrict__ uin, int ldin, float* __restrict__ uout,
+    int ldout, int H, int W, const TapGroup* __restrict__ groups_g, const int* __restrict__ ngroups_g, int kh, int kw,
+    int ng_max, RrlParams p, int* status, ZStride zs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long z = blockIdx.z;
+  if (__ldg(dense_flag(ngroups_g))) {
+    const float* qe = reinterpret_cast<const float*>(q + z * zs.q);
+    update_tile_dense<TH, TW, KW>(smem_raw, qe, qe + (size_t)H * upitch(W), upitch(W), uin + z * zs.in, ldin,
+                                  uout + z * zs.out, ldout, H, W, dense_taps(groups_g, kh, kw), kh, p, status,
+                                  blockIdx.y * TH, blockIdx.x * TW, PdlDep());
+  } else {
+    constexpr int P = (KW + 2 <= 8) ? 8 : (KW + 2 <= 16) ? 16 : 32;
+    update_tile<TH, TW, 8, P>(smem_raw, q + z * zs.q, ldq, uin + z * zs.in, ldin, uout + z * zs.out, ldout, H, W,
+                              groups_g, ngroups_g, kh, kw, ng_max, p, status, blockIdx.y * TH, blockIdx.x * TW,
+                              PdlDep());
+  }
 }
 
 // one-axis PSFs: the same split pair with sliding-window sums (box) or
@@ -287,8 +344,12 @@ static size_t split_smem_update_single(int kh, int kw, int ng_max) {
   return split_smem_update(kUTH, kUTW, kh, kw, ng_max);
 }
 size_t rrl_split_smem(int kh, int kw) {
-  const size_t a = split_smem_q_single(kh, kw, max_tap_groups(kh, kw));
-  const size_t b = split_smem_update_single(kh, kw, max_tap_groups(kh, kw));
+  size_t a = split_smem_q_single(kh, kw, max_tap_groups(kh, kw));
+  size_t b = split_smem_update_single(kh, kw, max_tap_groups(kh, kw));
+  if (dense_eligible(kh, kw)) {
+    a = a > dense_smem_q(kQTH, kQTW, kh, kw) ? a : dense_smem_q(kQTH, kQTW, kh, kw);
+    b = b > dense_smem_update(kUTH, kUTW, kh, kw) ? b : dense_smem_update(kUTH, kUTW, kh, kw);
+  }
   return a > b ? a : b;
 }
 
@@ -323,13 +384,33 @@ static cudaError_t launch_fused_p(const IterArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename KQ, typename KU>
+static cudaError_t launch_split_pair(const IterArgs& a, KQ kq, KU ku, int ng_max, size_t sq, size_t su,
+                                     cudaStream_t s);
+
 template <int P>
 static cudaError_t launch_split_p(const IterArgs& a, cudaStream_t s) {
   const int ng_max = a.ng_bound > 0 ? a.ng_bound : max_tap_groups(a.kh, a.kw);
   const size_t sq = split_smem_q_single(a.kh, a.kw, ng_max), su = split_smem_update_single(a.kh, a.kw, ng_max);
   if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
-  auto kq = k_rrl_q<kQTH, kQTW, kR, P>;
-  auto ku = k_rrl_update<kUTH, kUTW, kR, P>;
+  return launch_split_pair(a, k_rrl_q<kQTH, kQTW, kR, P>, k_rrl_update<kUTH, kUTW, kR, P>, ng_max, sq, su, s);
+}
+
+template <int KW>
+static cudaError_t launch_split_dense(const IterArgs& a, cudaStream_t s) {
+  static_assert(kQTH == kUTH && kQTW == kUTW, "one tile shape");
+  const int ng_max = a.ng_bound > 0 ? a.ng_bound : max_tap_groups(a.kh, a.kw);
+  size_t sq = split_smem_q_single(a.kh, a.kw, ng_max), su = split_smem_update_single(a.kh, a.kw, ng_max);
+  const size_t dq = dense_smem_q(kQTH, kQTW, a.kh, a.kw), du = dense_smem_update(kUTH, kUTW, a.kh, a.kw);
+  sq = sq > dq ? sq : dq;
+  su = su > du ? su : du;
+  if (sq > 227 * 1024 || su > 227 * 1024) return cudaErrorInvalidValue;
+  return launch_split_pair(a, k_rrl_q_dense<kQTH, kQTW, KW>, k_rrl_update_dense<kUTH, kUTW, KW>, ng_max, sq, su, s);
+}
+
+template <typename KQ, typename KU>
+static cudaError_t launch_split_pair(const IterArgs& a, KQ kq, KU ku, int ng_max, size_t sq, size_t su,
+                                     cudaStream_t s) {
   cudaError_t e;
   if ((e = set_smem(kq, sq)) != cudaSuccess) return e;
   if ((e = set_smem(ku, su)) != cudaSuccess) return e;
@@ -428,8 +509,26 @@ size_t rrl_box_smem(int kh, int kw) {
   return a > b ? a : b;
 }
 
+static cudaError_t dispatch_dense(const IterArgs& a, cudaStream_t s) {
+  switch (a.kw) {
+    case 3: return launch_split_dense<3>(a, s);
+    case 5: return launch_split_dense<5>(a, s);
+    case 7: return launch_split_dense<7>(a, s);
+    case 9: return launch_split_dense<9>(a, s);
+    case 11: return launch_split_dense<11>(a, s);
+    case 13: return launch_split_dense<13>(a, s);
+    case 15: return launch_split_dense<15>(a, s);
+    case 17: return launch_split_dense<17>(a, s);
+    case 19: return launch_split_dense<19>(a, s);
+    case 21: return launch_split_dense<21>(a, s);
+    case 23: return launch_split_dense<23>(a, s);
+    default: return launch_split_dense<25>(a, s);
+  }
+}
+
 template <bool SPLIT>
 static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
+  if (SPLIT && dense_eligible(a.kh, a.kw)) return dispatch_dense(a, s);
   switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
     case 8: return SPLIT ? launch_split_p<8>(a, s) : launch_fused_p<8>(a, s);
     case 16: return SPLIT ? launch_split_p<16>(a, s) : launch_fused_p<16>(a, s);

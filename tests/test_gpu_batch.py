@@ -117,3 +117,19 @@ def test_uneven_batch_512_subset_against_oracle(lib):
         worst = (max(worst[0], m), max(worst[1], r))
         assert m <= MAX_ABS and r <= RMS, f"{cases[i].name} {cases[i].f.shape}: {m:.3e} {r:.3e}"
     print(f"batch512 subset worst max-abs {worst[0]:.3e} rms {worst[1]:.3e}")
+
+
+def test_batch_plans_with_different_shared_memory_coexist(lib):
+    """A plan made after another one with smaller tiles (less shared memory
+    per CTA) must not stop the earlier plan from launching."""
+    big = small_batch([259], cap=160)     # 25x25 Gaussian mixture: large halo
+    small = small_batch([0], cap=160)     # 1D box: small tiles
+    fb, fs_ = [cuda(c.f) for c in big], [cuda(c.f) for c in small]
+    bb = lib.Batch(fb, [cuda(c.h) for c in big], [c.params for c in big], 3, kinds=[c.psf_kind for c in big])
+    bs = lib.Batch(fs_, [cuda(c.h) for c in small], [c.params for c in small], 3,
+                   kinds=[c.psf_kind for c in small])
+    for b, cases, fs in ((bb, big, fb), (bs, small, fs_)):
+        for c, f, u in zip(cases, fs, b.run()):
+            assert torch.equal(u, lib.deblur(f, cuda(c.h), c.params, 3, kind=c.psf_kind))
+    bb.close()
+    bs.close()

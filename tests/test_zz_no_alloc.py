@@ -19,8 +19,6 @@ from paper_1212_2245_b300.params import Params
 
 pytestmark = pytest.mark.gpu
 
-MAX_ABS, RMS = 1e-3, 1e-4  # the parity bar used by every GPU test
-
 
 def _inputs(H, W, h, seed):
     rng = np.random.default_rng(seed)
@@ -63,24 +61,28 @@ def _without_allocation(lib, f, u, h, p, iters):
     return u
 
 
-def _close(a, b):
-    d = (a.double() - b.double()).abs()
-    return float(d.max()) <= MAX_ABS and float(d.pow(2).mean().sqrt()) <= RMS
-
-
 def test_no_alloc_matches_workspace_entry_point_on_consecutive_calls():
+    """Both entry points launch the same kernels on the same inputs, so their
+    results must agree bit for bit, whichever call ran before on the shared
+    scratch.  The shapes cover the split schedule (below 512K pixels), the
+    flow schedule (512K to 2M pixels, whose dependency counters live in the
+    scratch and are cleared by each call), tap groups (2D PSFs) and one-axis
+    register windows (row PSFs)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     lib = _lib.load()
     p = Params()
     cases = [(_inputs(200, 300, synth.line_psf(15, 30.0, 16.0), 1), 6),
-             (_inputs(97, 131, synth.raised_cosine_1d(9), 2), 5)]
+             (_inputs(97, 131, synth.raised_cosine_1d(9), 2), 5),
+             (_inputs(1024, 1024, synth.raised_cosine_1d(31), 3), 4),
+             (_inputs(1024, 1024, synth.line_psf(31, 30.0, 32.0), 4), 3)]
     refs = [_with_workspace(lib, f, u0.clone(), h, p, it) for (f, u0, h), it in cases]
-    # two calls in a row (different shapes and PSFs), then the first again
-    for (f, u0, h), it in cases + cases[:1]:
-        k = 0 if f.shape[0] == 200 else 1
+    # every case twice in a row after a call of another shape, then the first
+    # again after the largest
+    for k in [0, 1, 2, 2, 1, 3, 3, 0]:
+        (f, u0, h), it = cases[k]
         out = _without_allocation(lib, f, u0.clone(), h, p, it)
-        assert _close(out, refs[k]), f"call on {tuple(f.shape)} differs from db_rrl_iterate"
+        assert torch.equal(out, refs[k]), f"call on {tuple(f.shape)} differs from db_rrl_iterate"
 
 
 def test_no_alloc_rejects_images_beyond_its_scratch():
