@@ -404,6 +404,16 @@ db_status db_set_schedule(int schedule);
  * for other values. */
 db_status db_set_one_axis_min(int min_len);
 
+/* Dense 2D PSFs (odd sides 3..25): the tap sums run as register-blocked
+ * dense sums (2 x 4 outputs per thread, every tap of the kh x kw window)
+ * when at least `percent` percent of the taps are non-zero, as tap groups
+ * otherwise.  The choice is made on the device when the taps are prepared
+ * (db_wiener, db_rrl_iterate, plans and batches: it applies to taps
+ * prepared after the call).  Process-wide; percent in 1..101 (101: never),
+ * 0 restores the default of 50.  The two forms differ by FP32 rounding
+ * only.  DB_ERR_ARG for other values. */
+db_status db_set_dense_min(int percent);
+
 /* Evaluation of the information divergence r_f in the robust weight
  * (process-wide setting, all devices):
  *   DB_RF_LOG1P - r_f(b) = f (t - log1p t), t = (b - f)/f (default; exact up

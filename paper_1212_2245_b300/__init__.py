@@ -18,7 +18,7 @@ from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
            "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "HostBuffer", "set_schedule", "set_one_axis_min", "set_spin_limit",
-           "set_rf_eval", "version", "FrameStream", "BatchStream", "deblur_n", "workspace_bytes_n"]
+           "set_rf_eval", "set_dense_min", "version", "FrameStream", "BatchStream", "deblur_n", "workspace_bytes_n"]
 
 
 class DeblurError(RuntimeError):
@@ -518,6 +518,13 @@ def set_one_axis_min(min_len: int = 0):
     and flow schedules (shorter ones use tap groups); 256 = never, 0 = the
     default (rows from 16 taps, columns from 32).  Process-wide."""
     _check(_lib.load().db_set_one_axis_min(int(min_len)), "db_set_one_axis_min")
+
+
+def set_dense_min(percent: int = 0):
+    """Smallest share (percent) of non-zero taps for which an eligible 2D PSF
+    (odd sides 3..25) is summed densely; 101 = never, 0 = the default (50).
+    Process-wide; applies to taps prepared after the call."""
+    _check(_lib.load().db_set_dense_min(int(percent)), "db_set_dense_min")
 
 
 def set_rf_eval(name: str):

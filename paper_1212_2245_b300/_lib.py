@@ -82,6 +82,7 @@ SIGNATURES = {
     "db_launch_count": (ctypes.c_longlong, []),
     "db_set_schedule": (c_int, [c_int]),
     "db_set_one_axis_min": (c_int, [c_int]),
+    "db_set_dense_min": (c_int, [c_int]),
     "db_set_rf_eval": (c_int, [c_int]),
 }
 

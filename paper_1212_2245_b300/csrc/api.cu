@@ -16,6 +16,8 @@ static std::atomic<unsigned> g_settings_gen{0};
 void bump_settings() { g_settings_gen.fetch_add(1); }
 unsigned settings_gen() { return g_settings_gen.load(); }
 static std::atomic<int> g_one_axis_min{0};
+static std::atomic<int> g_dense_min_pct{50};
+int dense_min_pct() { return g_dense_min_pct.load(std::memory_order_relaxed); }
 int one_axis_min(bool row) {
   const int v = g_one_axis_min.load(std::memory_order_relaxed);
   return v > 0 ? v : row ? 16 : 32;
@@ -618,6 +620,13 @@ long long db_launch_count(void) { return g_launches.load(std::memory_order_relax
 db_status db_set_one_axis_min(int min_len) {
   if (min_len < 0 || min_len > kMaxTapSide + 1) return DB_ERR_ARG;
   g_one_axis_min.store(min_len);
+  bump_settings();
+  return DB_OK;
+}
+
+db_status db_set_dense_min(int percent) {
+  if (percent < 0 || percent > 101) return DB_ERR_ARG;
+  g_dense_min_pct.store(percent == 0 ? 50 : percent);
   bump_settings();
   return DB_OK;
 }

@@ -88,6 +88,9 @@ constexpr size_t kAuxBytes = 1280;
 // (sliding-window sums), 2 other one-axis PSF of length >= one_axis_min()
 // (register-window tap sums).
 int one_axis_min(bool row);
+// Smallest share of non-zero taps (percent) for which k_prepare_taps selects
+// the dense bodies of an eligible 2D PSF (db_set_dense_min; 101: never).
+int dense_min_pct();
 inline int axis_mode(int kind, int kh, int kw) {
   if (kind == DB_PSF_BOX) return 1;
   return (kh == 1 || kw == 1) && kh * kw >= one_axis_min(kh == 1) ? 2 : 0;

@@ -2,18 +2,19 @@
 // bodies of the split schedule for PSFs whose taps are mostly non-zero
 // (Gaussian mixtures and the like), register blocked in two dimensions.
 //
-// Each thread owns a block of R = 2 rows x C = 4 columns of outputs.  For
-// one input row of the staged tile it loads the C + kw - 1 values its four
-// columns read (16-byte shared loads; consecutive lanes own consecutive
-// column blocks, so a warp's loads are conflict-free) and applies to them
-// every tap row that maps this input row onto one of its R output rows.  A
-// weight read once (a broadcast 16-byte load of four taps) feeds C FMAs,
-// and an input value up to R x C x kw / (C + kw - 1) of them, so the tap
+// Each thread owns a block of R = 2 rows x C = 4 columns of outputs.  It
+// walks the tap rows in order; at each it loads the one staged input row
+// (C + kw - 1 values, 16-byte shared loads; consecutive lanes own
+// consecutive column blocks, so a warp's loads are conflict-free) that the
+// tap row maps onto its first output row, keeps the previous one (which the
+// same tap row maps onto its second output row) in registers, and reads the
+// tap row once: a weight (a broadcast 16-byte load of four taps) feeds
+// R x C FMAs and an input value up to R x C x kw / (C + kw - 1), so the tap
 // sums are bound by the FMA pipe rather than by shared-memory wavefronts.
 //
 // Per output the sums run in a fixed order independent of the tile and of
-// the block shape (convolution: tap rows from kh-1 down to 0, correlation:
-// from 0 up to kh-1; taps of a row from 0 up to kw-1), so every schedule
+// the block shape (convolution: tap rows from 0 up to kh-1, correlation:
+// from kh-1 down to 0; taps of a row from 0 up to kw-1), so every schedule
 // and the batched kernel that use these bodies give the same bits.
 //
 // q = (e, W) goes through global memory in planar form for these PSFs: the
@@ -52,10 +53,12 @@ __device__ __forceinline__ void load_row(float* v, const float* __restrict__ src
   }
 }
 
-// acc[o][c] += sum_b w[b] * v[c + OFF(b)] for one tap row w (KW taps,
-// 16-byte aligned); CONV: OFF(b) = KW-1-b + OX, else b + OX.
+// acc0[c] += sum_b w[b] va[c + OFF(b)], acc1[c] += sum_b w[b] vb[c + OFF(b)]
+// for one tap row w (KW taps, 16-byte aligned): every weight read once
+// feeds 2 C FMAs.  CONV: OFF(b) = KW-1-b + OX, else b + OX.
 template <int KW, int OX, bool CONV>
-__device__ __forceinline__ void dense_row_taps(const float* __restrict__ w, const float* v, float (&acc)[kDC]) {
+__device__ __forceinline__ void dense_row_taps2(const float* __restrict__ w, const float* va, const float* vb,
+                                                float (&acc0)[kDC], float (&acc1)[kDC]) {
 #pragma unroll
   for (int g = 0; g < DenseGeom<KW>::KW4; ++g) {
     const float4 w4 = reinterpret_cast<const float4*>(w)[g];
@@ -65,56 +68,48 @@ __device__ __forceinline__ void dense_row_taps(const float* __restrict__ w, cons
       const int b = 4 * g + t;
       if (b < KW) {
 #pragma unroll
-        for (int c = 0; c < kDC; ++c) acc[c] = fmaf(wv[t], v[c + (CONV ? KW - 1 - b : b) + OX], acc[c]);
+        for (int c = 0; c < kDC; ++c) {
+          acc0[c] = fmaf(wv[t], va[c + (CONV ? KW - 1 - b : b) + OX], acc0[c]);
+          acc1[c] = fmaf(wv[t], vb[c + (CONV ? KW - 1 - b : b) + OX], acc1[c]);
+        }
       }
     }
   }
 }
 
-// Convolution b = u*h at the R x C block whose first output sits at row r0,
-// column c0 of the tile.  us: staged u(clamp) with row stride US, row 0 =
-// image row i0 - (kh-1)/2, column 0 = the window start; tab: dense taps,
-// row stride TS.
-template <int KW, int US>
-__device__ __forceinline__ void dense_blur(const float* __restrict__ us, const float* __restrict__ tab, int TS, int kh,
-                                           int r0, int c0, float (&acc)[kDR][kDC]) {
+// Tap sums at the 2 x C block whose first output sits at row r0, column c0
+// of the tile, over the staged plane `base` (row stride S; row 0 = image row
+// i0 - (kh-1)/2, column 0 = the window start).  Output row o meets staged
+// row s = o + kh - 1 - a of tap row a (convolution, b = u*h) or s = o + a
+// (correlation with h*).  Step k = 0 .. kh-1 applies tap row a = k
+// (convolution) or a = kh-1-k (correlation): in both cases output row 0
+// reads staged row kh-1-k, loaded at this step, and output row 1 the row
+// loaded one step earlier, so each staged row is loaded once and each tap
+// row read once.  Per output the taps are summed by tap row in step order,
+// within a row from b = 0 up.
+template <int KW, int S, bool CONV>
+__device__ __forceinline__ void dense_sum(const float* __restrict__ base, const float* __restrict__ tab, int TS,
+                                          int kh, int r0, int c0, float (&acc)[kDR][kDC]) {
+  static_assert(kDR == 2, "two output rows per block");
   using G = DenseGeom<KW>;
+  constexpr int OX = CONV ? G::OXB : G::OXC;
+  constexpr int NV = CONV ? G::NB : G::NC;
 #pragma unroll
   for (int o = 0; o < kDR; ++o)
 #pragma unroll
     for (int c = 0; c < kDC; ++c) acc[o][c] = 0.f;
-  const int ns = kDR + kh - 1;
+  float v0[NV], v1[NV];
+  const float* rowp = base + (r0 + kh) * S + c0;  // staged row kh: output row 1 at step 0
+  load_row(v1, rowp, NV / 4);
 #pragma unroll 1
-  for (int s = 0; s < ns; ++s) {
-    float v[G::NB];
-    load_row(v, us + (r0 + s) * US + c0, G::NB / 4);
-#pragma unroll
-    for (int o = 0; o < kDR; ++o) {
-      const int a = o + kh - 1 - s;  // tap row applied to input row s at output row o
-      if (a >= 0 && a < kh) dense_row_taps<KW, G::OXB, true>(tab + a * TS, v, acc[o]);
-    }
-  }
-}
-
-// Correlation of one plane with h* at the block: row 0 of the staged plane
-// is image row i0 - (kh-1)/2.
-template <int KW, int QS>
-__device__ __forceinline__ void dense_corr(const float* __restrict__ qs, const float* __restrict__ tab, int TS, int kh,
-                                           int r0, int c0, float (&acc)[kDR][kDC]) {
-  using G = DenseGeom<KW>;
-#pragma unroll
-  for (int o = 0; o < kDR; ++o)
-#pragma unroll
-    for (int c = 0; c < kDC; ++c) acc[o][c] = 0.f;
-  const int ns = kDR + kh - 1;
-#pragma unroll 1
-  for (int s = 0; s < ns; ++s) {
-    float v[G::NC];
-    load_row(v, qs + (r0 + s) * QS + c0, G::NC / 4);
-#pragma unroll
-    for (int o = 0; o < kDR; ++o) {
-      const int a = s - o;  // tap row applied to input row s at output row o
-      if (a >= 0 && a < kh) dense_row_taps<KW, G::OXC, false>(tab + a * TS, v, acc[o]);
+  for (int k = 0; k < kh; k += 2) {
+    rowp -= S;  // staged row kh-1-k
+    load_row(v0, rowp, NV / 4);
+    dense_row_taps2<KW, OX, CONV>(tab + (CONV ? k : kh - 1 - k) * TS, v0, v1, acc[0], acc[1]);
+    if (k + 1 < kh) {
+      rowp -= S;  // staged row kh-2-k
+      load_row(v1, rowp, NV / 4);
+      dense_row_taps2<KW, OX, CONV>(tab + (CONV ? k + 1 : kh - 2 - k) * TS, v1, v0, acc[0], acc[1]);
     }
   }
 }
@@ -168,7 +163,7 @@ __device__ __forceinline__ void q_tile_dense(unsigned char* smem_raw, const floa
     const int br = item / (TW / kDC), bc = item - br * (TW / kDC);
     const int r0 = br * kDR, c0 = bc * kDC;
     float b[kDR][kDC];
-    dense_blur<KW, US>(us, tab, TS, kh, r0, c0, b);
+    dense_sum<KW, US, true>(us, tab, TS, kh, r0, c0, b);
     const int j = j0 + c0;
 #pragma unroll
     for (int o = 0; o < kDR; ++o) {
@@ -229,8 +224,8 @@ __device__ __forceinline__ void update_tile_dense(unsigned char* smem_raw, const
     const int br = item / (TW / kDC), bc = item - br * (TW / kDC);
     const int r0 = br * kDR, c0 = bc * kDC;
     float dl[kDR][kDC], B[kDR][kDC];
-    dense_corr<KW, QS>(es, tab, TS, kh, r0, c0, dl);
-    dense_corr<KW, QS>(ws, tab, TS, kh, r0, c0, B);
+    dense_sum<KW, QS, false>(es, tab, TS, kh, r0, c0, dl);
+    dense_sum<KW, QS, false>(ws, tab, TS, kh, r0, c0, B);
     float un[kDR][kDC];
 #pragma unroll
     for (int c = 0; c < kDC; ++c) {

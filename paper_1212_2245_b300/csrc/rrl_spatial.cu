@@ -74,7 +74,8 @@ __device__ void next_group(const float* __restrict__ taps, int kh, int kw, int b
 }
 
 __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ taps, int kh, int kw,
-                                                      int kind, int max_groups, TapGroup* __restrict__ groups,
+                                                      int kind, int max_groups, int dense_pct,
+                                                      TapGroup* __restrict__ groups,
                                                       int* __restrict__ ngroups, int* status) {
   __shared__ int scan[256];
   __shared__ int cstart[kMaxGroupH + 1];
@@ -178,15 +179,17 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
     for (int i = 0; i < 8; ++i) s += warp_sum[i];
     if (!(s > 0.f)) bad |= DB_FLAG_TAPS;
     *ngroups = total > max_groups ? 0 : total;
-    // dense sums when at least half of an eligible PSF's taps are non-zero
-    ngroups[1] = (dense_eligible(kh, kw) && 2 * s_nnz >= n) ? 1 : 0;
+    // dense sums when at least dense_pct percent (default half) of an
+    // eligible PSF's taps are non-zero
+    ngroups[1] = (dense_eligible(kh, kw) && 100 * s_nnz >= dense_pct * n) ? 1 : 0;
     if (bad && status) atomicOr(status, bad);
   }
 }
 
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s) {
-  k_prepare_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, max_tap_groups(kh, kw), groups, ngroups, status);
+  k_prepare_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, max_tap_groups(kh, kw), dense_min_pct(), groups, ngroups,
+                                   status);
   count_launch();
   return cudaGetLastError();
 }
