@@ -46,6 +46,50 @@ struct BatchImg {
 
 constexpr int kBTH = 32, kBTW = 64, kBR = 8;  // tiles of the split schedule
 
+// Shared-memory slot of one queued tile: its index, (image, i0, j0, cost)
+// and a copy of its image's descriptor.
+struct TileSlot {
+  BatchImg im;
+  int4 T;
+  int t;
+};
+constexpr int kImgWords = (int)(sizeof(BatchImg) / 4);
+static_assert(sizeof(BatchImg) % 4 == 0 && kImgWords <= 64, "descriptor copied by one warp");
+
+// Warp 0 fills a slot: tile t (from the work queue) and its descriptor.
+__device__ __forceinline__ void fill_slot(TileSlot* slot, int t, const BatchImg* __restrict__ imgs,
+                                          const int4* __restrict__ tiles, int ntiles) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) slot->t = t;
+  if (t >= ntiles) return;
+  const int4 T = tiles[t];
+  if (lane == 0) slot->T = T;
+  const unsigned* src = reinterpret_cast<const unsigned*>(imgs + T.x);
+  unsigned* dst = reinterpret_cast<unsigned*>(&slot->im);
+  for (int w = lane; w < kImgWords; w += 32) dst[w] = __ldg(src + w);
+}
+
+// Work-queue state of a CTA of the persistent kernel: two tile slots and
+// the queue's tables (shared memory of the kernel, set up at its start).
+struct QueueState {
+  TileSlot slot[2];
+  const BatchImg* imgs;
+  const int4* tiles;
+  int ntiles;
+};
+__shared__ __align__(16) QueueState g_queue;
+
+// Warp 0 fills the other slot with the next tile of the queue, whose index
+// thread 0 requested when the current tile began (so the atomic's latency
+// is hidden behind the tile), and with its descriptor.  Done once the
+// current tile's work is issued; the CTA's barrier then publishes it.
+__device__ __forceinline__ void fetch_next(int slot, int next) {
+  if (threadIdx.y == 0 && threadIdx.x < 32) {
+    const int t = __shfl_sync(0xffffffffu, next, 0);
+    fill_slot(&g_queue.slot[slot], t, g_queue.imgs, g_queue.tiles, g_queue.ntiles);
+  }
+}
+
 template <int P>
 __device__ __noinline__ void batch_q(unsigned char* smem, const BatchImg& im, const float* src, int lds,
                                      int i0, int j0) {
@@ -156,19 +200,29 @@ __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict
                                                    unsigned* bar, int* work, int* status,
                                                    long long spin_limit) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_t;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    g_queue.imgs = imgs;
+    g_queue.tiles = tiles;
+    g_queue.ntiles = ntiles;
+  }
   for (int k = 0; k < iters; ++k) {
     const bool even = (k & 1) == 0;
     for (int phase = 0; phase < 2; ++phase) {
-      while (true) {
-        if (tid == 0) s_t = atomicAdd(work + 2 * k + phase, 1);
-        __syncthreads();
-        const int t = s_t;
-        __syncthreads();
-        if (t >= ntiles) break;
-        const int4 T = tiles[t];
-        const BatchImg im = imgs[T.x];
+      int* queue = work + 2 * k + phase;
+      // the phase's first tile, then each tile prefetches the next one
+      if (tid < 32) {
+        int t = 0;
+        if (tid == 0) t = atomicAdd(queue, 1);
+        fill_slot(&g_queue.slot[0], __shfl_sync(0xffffffffu, t, 0), imgs, tiles, ntiles);
+      }
+      __syncthreads();
+      int cur = 0;
+      while (g_queue.slot[cur].t < ntiles) {
+        int next = 0;
+        if (tid == 0) next = atomicAdd(queue, 1);
+        const BatchImg& im = g_queue.slot[cur].im;
+        const int4 T = g_queue.slot[cur].T;
         const float* src = even ? im.A : im.B;
         const int lds = even ? im.ldA : im.ldB;
         float* dst = even ? im.B : im.A;
@@ -178,7 +232,9 @@ __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict
         else if (im.box == 3) batch_box<true, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else if (im.box == 4) batch_box<false, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else batch_tile(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        fetch_next(cur ^ 1, next);
         __syncthreads();
+        cur ^= 1;
       }
       if (!grid_barrier(bar, gridDim.x, status, spin_limit)) return;
     }

@@ -169,10 +169,12 @@ __device__ __forceinline__ void q_tile_dense(unsigned char* smem_raw, const floa
     for (int o = 0; o < kDR; ++o) {
       const int i = i0 + r0 + o;
       if (i >= H) continue;
+      const float4 f4 = *reinterpret_cast<const float4*>(fs + (r0 + o) * TW + c0);
+      const float fv[kDC] = {f4.x, f4.y, f4.z, f4.w};
       float e4[kDC], w4[kDC];
 #pragma unroll
       for (int c = 0; c < kDC; ++c) {
-        const float2 q = weighted_residual(b[o][c], fmaxf(fs[(r0 + o) * TW + c0 + c], p.floor), p);
+        const float2 q = weighted_residual(b[o][c], fmaxf(fv[c], p.floor), p);
         e4[c] = q.x; w4[c] = q.y;
       }
       float* pe = qe + (size_t)i * ldqp + j;
