@@ -142,10 +142,11 @@ class ClockSampler:
 LINE1024_FLOW_ITER_DRAM_BYTES = (8.489728e6 + 1.274112e6) / 20
 
 
-# DRAM bytes per pixel and iteration of k_rrl_batch (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch over the launch's pixels x iterations);
-# None until a capture of the current kernel exists.
-BATCH_DRAM_BYTES_PER_PX_ITER = None
+# DRAM bytes per pixel and iteration of k_rrl_batch on batch512
+# (dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, 55.88 GB,
+# over its 1.735e9 pixel-iterations; profiles/batch512_launches.md).  Set to None
+# when the kernel changes, until it is captured again.
+BATCH_DRAM_BYTES_PER_PX_ITER = 32.20
 
 
 def pinned_copy(array):
@@ -521,14 +522,14 @@ def run_batch(args, world, rank, local):
     ms_w = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     ms_rrl = ms - ms_w
     # end to end through the C ABI (db_batch_stream_run_host): page-locked
-    # host images in, results out, every step; 4 sub-batches whose copies
+    # host images in, results out, every step; 8 sub-batches whose copies
     # overlap the other sub-batches' runs.  Each step starts after the
     # previous one has fully finished (the call's stream waits for its
     # downloads).
     f_host = [pinned_copy(c.f) for c in cases]
     u_host = [torch.empty(c.f.shape, dtype=torch.float32).pin_memory() for c in cases]
     with torch.cuda.stream(stream):
-        bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=4, device=dev)
+        bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=8, device=dev)
         bs.run(f_host, u_host)
     for a, b_ in zip(u_host, full.us):
         if not torch.equal(a, b_.cpu()):
