@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_adj_wiener_rows2(const float* __restric
                                                           float2 invN, float* __restrict__ f0bar,
                                                           float2* __restrict__ prow) {
   extern __shared__ float4 sm[];
-  const int M = 1 << D.logM;
+  const int M = dft_len(D);
   const bool pow2 = D.c == nullptr;
   float4* x = sm;      // row a: Z, then the packed G_a + i G_b
   float4* y = sm + M;  // row b: Z
@@ -1393,7 +1393,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
   ADJ_CHECK(psf_row_spectrum(psf->taps, kw, D, spec, s));
   ADJ_LAUNCH(k_unit_taps<<<(kw * kw + 255) / 256, 256, 0, s>>>(unit_taps, kw));
   for (int t = 0; t < kw; ++t) ADJ_CHECK(psf_row_spectrum(unit_taps + (size_t)t * kw, kw, D, unit_spec + (size_t)t * W, s));
-  const int M = 1 << D.logM;
+  const int M = dft_len(D);
   const size_t smem = (size_t)2 * M * sizeof(float4);
   if (smem > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const double invN = 1.0 / (double)W;

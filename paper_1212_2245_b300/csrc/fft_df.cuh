@@ -71,13 +71,25 @@ __device__ __forceinline__ float4 zconj(float4 a) { return make_float4(a.x, a.y,
 __device__ __forceinline__ float4 zscale(float4 a, float2 s) { return mkc(ff_mul(re_(a), s), ff_mul(im_(a), s)); }
 __device__ __forceinline__ float4 zzero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// A 1D DFT of length N in float-float (see Dft1 for the layout).
+// A 1D DFT of length N in float-float.  A power of two N is transformed
+// directly (M = N); any other N by Bluestein's chirp-z form as a circular
+// convolution of length M = 2^logM 3^M3 >= 2N - 1 (the smallest such number,
+// so that the convolution is at most about 1.125 times longer than needed;
+// a power of two alone would be up to twice as long).
 struct Dft1ff {
-  int N, logM;
+  int N, logM, M3;   // M = 2^logM * 3^M3 (M3 = 0 for power-of-two N)
+  float2 invM;       // 1/M, float-float
   const float4* tw;  // exp(-2 pi i k / M), k < M
   const float4* c;   // chirp, nullptr for power-of-two N
   const float4* Bf;  // transform of the circular chirp
 };
+__host__ __device__ inline int pow3i(int b) {
+  int r = 1;
+  while (b-- > 0) r *= 3;
+  return r;
+}
+// Transform length M of D (the capacity every sequence needs).
+__host__ __device__ inline int dft_len(const Dft1ff& D) { return (1 << D.logM) * pow3i(D.M3); }
 
 // Host-side state of a prepared Wiener filter (tables and spectrum live in
 // the workspace).
@@ -95,20 +107,34 @@ __device__ __forceinline__ void split_item_ff(int it, int lns, int lnb, bool seq
   else { q = it >> lnb; b = it & ((1 << lnb) - 1); }
 }
 
-// Forward DIF sweep (output bit-reversed); see fft_dif.  Ends with a barrier.
+// Item `it` of nseq (a power of two, 2^lns) sequences x nsub contiguous
+// sub-blocks x 2^lnb items: sequence q, sub-block u, item b.
+__device__ __forceinline__ void sub_item_ff(int it, int lns, int nsub, int lnb, bool seq_fast, int& q, int& u,
+                                            int& b) {
+  int r;
+  if (seq_fast) { q = it & ((1 << lns) - 1); r = it >> lns; }
+  else if (nsub == 1) { q = it >> lnb; r = it - (q << lnb); }
+  else { q = it / (nsub << lnb); r = it - q * (nsub << lnb); }
+  u = r >> lnb;
+  b = r & ((1 << lnb) - 1);
+}
+
+// Forward DIF sweep (output bit-reversed) of length 2^logN on each of nsub
+// contiguous sub-blocks of every sequence; the twiddle of exponent e is
+// tw[e * twmul] (tw: a table for length 2^logN * twmul).  Ends with a barrier.
 __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss, const float4* __restrict__ tw,
-                                  bool seq_fast) {
+                                  bool seq_fast, int nsub = 1, int twmul = 1) {
   const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
   const int nb = N >> 2;
   int logLen = logN;
   while (logLen >= 2) {
     const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
-    const int tstep = 1 << (logN - logLen);
+    const int tstep = (1 << (logN - logLen)) * twmul;
     if (m == 1) {  // blocks of 4: every twiddle is 1
-      for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
-        int q, b;
-        split_item_ff(it, lns, logN - 2, seq_fast, q, b);
-        float4* p = x + q * ss + (b * 4) * es;
+      for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
+        int q, u, b;
+        sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
+        float4* p = x + q * ss + ((u << logN) + b * 4) * es;
         const float4 x0 = p[0], x1 = p[es], x2 = p[2 * es], x3 = p[3 * es];
         const float4 y0 = zadd(x0, x2), y2 = zsub(x0, x2);
         const float4 y1 = zadd(x1, x3), y3 = zmul_mi(zsub(x1, x3));
@@ -121,11 +147,11 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
       logLen -= 2;
       continue;
     }
-    for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
-      int q, b;
-      split_item_ff(it, lns, logN - 2, seq_fast, q, b);
+    for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
+      int q, u, b;
+      sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
       const int blk = b >> logm, j = b & (m - 1);
-      float4* p = x + q * ss + (blk * len + j) * es;
+      float4* p = x + q * ss + ((u << logN) + blk * len + j) * es;
       const int sm = m * es;
       const float4 x0 = p[0], x1 = p[sm], x2 = p[2 * sm], x3 = p[3 * sm];
       const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
@@ -140,10 +166,10 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
     logLen -= 2;
   }
   if (logLen == 1) {
-    for (int it = threadIdx.x; it < nseq * (N >> 1); it += blockDim.x) {
-      int q, b;
-      split_item_ff(it, lns, logN - 1, seq_fast, q, b);
-      float4* p = x + q * ss + (2 * b) * es;
+    for (int it = threadIdx.x; it < nseq * nsub * (N >> 1); it += blockDim.x) {
+      int q, u, b;
+      sub_item_ff(it, lns, nsub, logN - 1, seq_fast, q, u, b);
+      float4* p = x + q * ss + ((u << logN) + 2 * b) * es;
       const float4 a = p[0], c = p[es];
       p[0] = zadd(a, c);
       p[es] = zsub(a, c);
@@ -154,15 +180,15 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
 
 // Inverse DIT sweep (unnormalised), mirror of fft_dif_ff.  Ends with a barrier.
 __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int ss,
-                                      const float4* __restrict__ tw, bool seq_fast) {
+                                      const float4* __restrict__ tw, bool seq_fast, int nsub = 1, int twmul = 1) {
   const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
   const int nb = N >> 2;
   int logLen = (logN & 1) ? 1 : 0;
   if (logLen == 1) {
-    for (int it = threadIdx.x; it < nseq * (N >> 1); it += blockDim.x) {
-      int q, b;
-      split_item_ff(it, lns, logN - 1, seq_fast, q, b);
-      float4* p = x + q * ss + (2 * b) * es;
+    for (int it = threadIdx.x; it < nseq * nsub * (N >> 1); it += blockDim.x) {
+      int q, u, b;
+      sub_item_ff(it, lns, nsub, logN - 1, seq_fast, q, u, b);
+      float4* p = x + q * ss + ((u << logN) + 2 * b) * es;
       const float4 a = p[0], c = p[es];
       p[0] = zadd(a, c);
       p[es] = zsub(a, c);
@@ -171,12 +197,12 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
   }
   for (logLen += 2; logLen <= logN; logLen += 2) {
     const int len = 1 << logLen, m = len >> 2, logm = logLen - 2;
-    const int tstep = 1 << (logN - logLen);
+    const int tstep = (1 << (logN - logLen)) * twmul;
     if (m == 1) {  // blocks of 4: every twiddle is 1
-      for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
-        int q, b;
-        split_item_ff(it, lns, logN - 2, seq_fast, q, b);
-        float4* p = x + q * ss + (b * 4) * es;
+      for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
+        int q, u, b;
+        sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
+        float4* p = x + q * ss + ((u << logN) + b * 4) * es;
         const float4 z0 = p[0], z1 = p[es], z2 = p[2 * es], z3 = p[3 * es];
         const float4 y0 = zadd(z0, z1), y1 = zsub(z0, z1);
         const float4 y2 = zadd(z2, z3), u3 = zmul_pi(zsub(z2, z3));
@@ -188,11 +214,11 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
       __syncthreads();
       continue;
     }
-    for (int it = threadIdx.x; it < nseq * nb; it += blockDim.x) {
-      int q, b;
-      split_item_ff(it, lns, logN - 2, seq_fast, q, b);
+    for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
+      int q, u, b;
+      sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
       const int blk = b >> logm, j = b & (m - 1);
-      float4* p = x + q * ss + (blk * len + j) * es;
+      float4* p = x + q * ss + ((u << logN) + blk * len + j) * es;
       const int sm = m * es;
       const float4 z0 = p[0], z1 = p[sm], z2 = p[2 * sm], z3 = p[3 * sm];
       const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
@@ -209,14 +235,90 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
   }
 }
 
+// sqrt(3)/2 as float-float: hi = the float nearest to it, lo = the float
+// nearest to the rest (sqrt(3)/2 = 0.86602540378443864676...)
+__device__ __forceinline__ float2 ff_sqrt3_half() { return make_float2(0x1.bb67aep-1f, 0x1.0b0996p-26f); }
+
+// Radix-3 stages of a length-M = 2^logM 3^M3 transform, spans M, M/3, ...,
+// 3 * 2^logM (decimation in frequency: the DFT of three points m apart,
+// then the twiddles exp(-2 pi i j k / len), k = 1, 2).  After them every
+// sequence consists of 3^M3 contiguous sub-blocks of length 2^logM that the
+// power-of-two sweep finishes.  With w = exp(-2 pi i / 3):
+//   y0 = x0 + x1 + x2,  y1,2 = (x0 - (x1 + x2)/2) -/+ i (sqrt 3 / 2)(x1 - x2).
+// Ends with a barrier.
+__device__ inline void fft3_dif_ff(float4* x, const Dft1ff& D, int nseq, int es, int ss, bool seq_fast) {
+  const int M = dft_len(D), nt = M / 3;  // triples per sequence and stage
+  const float2 s3 = ff_sqrt3_half(), half = make_float2(0.5f, 0.f);
+  int len = M;
+  for (int st = 0; st < D.M3; ++st, len /= 3) {
+    const int m = len / 3, tstep = M / len;
+    for (int it = threadIdx.x; it < nseq * nt; it += blockDim.x) {
+      int q, b;
+      seq_item_ff(it, nseq, nt, seq_fast, q, b);
+      const int blk = b / m, j = b - blk * m;
+      float4* p = x + q * ss + (blk * len + j) * es;
+      const int sm = m * es;
+      const float4 x0 = p[0], x1 = p[sm], x2 = p[2 * sm];
+      const float4 t1 = zadd(x1, x2);
+      const float4 t2 = zsub(x0, zscale(t1, half));
+      const float4 d = zsub(x1, x2);
+      const float4 t3 = zmul_mi(zscale(d, s3));  // -i sqrt(3)/2 (x1 - x2)
+      p[0] = zadd(x0, t1);
+      p[sm] = zmul(zadd(t2, t3), __ldg(D.tw + j * tstep));
+      p[2 * sm] = zmul(zsub(t2, t3), __ldg(D.tw + 2 * j * tstep));
+    }
+    __syncthreads();
+  }
+}
+
+// The inverse of fft3_dif_ff's stages (unnormalised), spans 3 * 2^logM up to
+// M: conjugate twiddles first, then the DFT of three points with
+// w = exp(+2 pi i / 3).  Ends with a barrier.
+__device__ inline void fft3_dit_inv_ff(float4* x, const Dft1ff& D, int nseq, int es, int ss, bool seq_fast) {
+  const int M = dft_len(D), nt = M / 3;
+  const float2 s3 = ff_sqrt3_half(), half = make_float2(0.5f, 0.f);
+  int len = 3 << D.logM;
+  for (int st = 0; st < D.M3; ++st, len *= 3) {
+    const int m = len / 3, tstep = M / len;
+    for (int it = threadIdx.x; it < nseq * nt; it += blockDim.x) {
+      int q, b;
+      seq_item_ff(it, nseq, nt, seq_fast, q, b);
+      const int blk = b / m, j = b - blk * m;
+      float4* p = x + q * ss + (blk * len + j) * es;
+      const int sm = m * es;
+      const float4 z0 = p[0];
+      const float4 z1 = zmulc(p[sm], __ldg(D.tw + j * tstep));
+      const float4 z2 = zmulc(p[2 * sm], __ldg(D.tw + 2 * j * tstep));
+      const float4 t1 = zadd(z1, z2);
+      const float4 t2 = zsub(z0, zscale(t1, half));
+      const float4 t3 = zmul_pi(zscale(zsub(z1, z2), s3));  // +i sqrt(3)/2 (z1 - z2)
+      p[0] = zadd(z0, t1);
+      p[sm] = zadd(t2, t3);
+      p[2 * sm] = zsub(t2, t3);
+    }
+    __syncthreads();
+  }
+}
+
+// The whole length-M forward sweep (radix-3 stages, then the power-of-two
+// sweep on every sub-block) and its inverse.  Both end with a barrier.
+__device__ inline void fft_fwd_m_ff(float4* x, const Dft1ff& D, int nseq, int es, int ss, bool seq_fast) {
+  if (D.M3 > 0) fft3_dif_ff(x, D, nseq, es, ss, seq_fast);
+  fft_dif_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast, pow3i(D.M3), pow3i(D.M3));
+}
+__device__ inline void fft_inv_m_ff(float4* x, const Dft1ff& D, int nseq, int es, int ss, bool seq_fast) {
+  fft_dit_inv_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast, pow3i(D.M3), pow3i(D.M3));
+  if (D.M3 > 0) fft3_dit_inv_ff(x, D, nseq, es, ss, seq_fast);
+}
+
 // Forward DFT (power of two: DIF, bit-reversed; else Bluestein, natural).
 // Same contract as dft_fwd.  Ends with a barrier.
 __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
   if (D.c == nullptr) {
-    fft_dif_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+    fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
     return;
   }
-  const int N = D.N, M = 1 << D.logM;
+  const int N = D.N, M = dft_len(D);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
     seq_item_ff(it, nseq, M, seq_fast, q, k);
@@ -224,7 +326,7 @@ __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft
     *p = (k < N) ? zmulc(*p, __ldg(D.c + k)) : zzero();
   }
   __syncthreads();
-  fft_dif_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+  fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
     seq_item_ff(it, nseq, M, seq_fast, q, k);
@@ -232,13 +334,12 @@ __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft
     *p = zmul(*p, __ldg(D.Bf + k));
   }
   __syncthreads();
-  fft_dit_inv_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
-  const float2 invM = make_float2(1.0f / (float)M, 0.f);  // exact: M is a power of two
+  fft_inv_m_ff(x, D, nseq, es, ss, seq_fast);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
     seq_item_ff(it, nseq, N, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
-    *p = zscale(zmulc(*p, __ldg(D.c + k)), invM);
+    *p = zscale(zmulc(*p, __ldg(D.c + k)), D.invM);
   }
   __syncthreads();
 }
@@ -246,7 +347,7 @@ __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft
 // Inverse DFT (unnormalised), see dft_inv.  Ends with a barrier.
 __device__ inline void dft_inv_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
   if (D.c == nullptr) {
-    fft_dit_inv_ff(x, D.logM, nseq, es, ss, D.tw, seq_fast);
+    fft_inv_m_ff(x, D, nseq, es, ss, seq_fast);
     return;
   }
   const int N = D.N;

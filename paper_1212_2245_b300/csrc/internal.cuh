@@ -196,7 +196,7 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 
 // PSF spectrum h^ on an H x W grid (bit-reversed order in both axes).
 struct Dft1ff;
-int dft_len_log2(int N);
+int dft_len_n(int N);  // transform length of an axis of N points (Bluestein: 2^a 3^b >= 2N-1)
 size_t dft_table_elems(int N);  // float4 units
 cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t s);
 cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float4* spec,

@@ -32,13 +32,27 @@ namespace db {
 //   [tw_ff (M) | c_ff (N) | Bf_ff (M) | tw32 (M float2 = M/2 float4)]
 // (c_ff and Bf_ff only for lengths that are not powers of two)
 // ---------------------------------------------------------------------------
-int dft_len_log2(int N) {
-  if (is_pow2(N)) return ilog2(N);
-  return ilog2(2 * N - 1);  // smallest power of two >= 2N-1
+// Transform length of an axis of N points: N itself for a power of two,
+// else the smallest M = 2^logM 3^M3 >= 2N - 1 for Bluestein's convolution.
+void dft_plan(int N, int* logM, int* M3) {
+  if (is_pow2(N)) { *logM = ilog2(N); *M3 = 0; return; }
+  long long best = -1;
+  for (int b = 0, p3 = 1; p3 < 4 * N; ++b, p3 *= 3) {
+    int a = 0;
+    while (((long long)p3 << a) < 2LL * N - 1) ++a;
+    const long long M = (long long)p3 << a;
+    if (best < 0 || M < best) { best = M; *logM = a; *M3 = b; }
+  }
+}
+
+int dft_len_n(int N) {
+  int a, b;
+  dft_plan(N, &a, &b);
+  return (1 << a) * pow3i(b);
 }
 
 size_t dft_table_elems(int N) {  // in float4 units
-  const size_t M = (size_t)1 << dft_len_log2(N);
+  const size_t M = (size_t)dft_len_n(N);
   return (is_pow2(N) ? M : M + N + M) + (M + 1) / 2;
 }
 
@@ -136,7 +150,7 @@ __device__ __forceinline__ void unpack_pair(float4 Zk, float4 Zm, float4& X1, fl
 // starting at q0.  Global inputs are staged with asynchronous copies.
 template <int MODE>
 __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q0, int R) {
-  const int N = a.D.N, logM = a.D.logM, M = 1 << logM;
+  const int N = a.D.N, M = dft_len(a.D);
   float4* x = smem4;
   float* stage = (float*)(x + R * M);  // real rows (x2 for row pairs)
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
@@ -270,7 +284,7 @@ __global__ void __launch_bounds__(256) k_fft_rows_batch(const FftArgs* __restric
 // counts the image columns.
 template <int MODE, int C>
 __device__ __forceinline__ void cols_body(float4* smem4, const FftArgs& a, int c0) {
-  const int N = a.D.N, logM = a.D.logM, M = 1 << logM;
+  const int N = a.D.N, M = dft_len(a.D);
   float4* x = smem4;
   float* stage = (float*)(x + M * C);  // COL_WIENER_1D_REAL: 2*C real columns
   const int nseq_total = (MODE == COL_WIENER_1D_REAL) ? (a.nrows + 1) / 2 : a.nrows;
@@ -356,13 +370,14 @@ static cudaError_t set_dyn_smem(Kern k, size_t smem) {
 
 template <int MODE>
 static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
-  const int M = 1 << a.D.logM;
-  // up to 2048 / M sequences per CTA, but at least two CTAs per SM where the
-  // rows allow it
+  const int M = dft_len(a.D);
+  // up to 2048 / M sequences per CTA (a power of two), but at least two
+  // CTAs per SM where the rows allow it
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 148;
-  int R = M >= 2048 ? 1 : 2048 / M;
+  int R = 1;
+  while (2 * R * M <= 2048) R *= 2;
   while (R > 1 && (a.nrows + R - 1) / R < 2 * sms) R >>= 1;
   const int grid = (a.nrows + R - 1) / R;
   const size_t smem = (size_t)R * M * sizeof(float4) + (size_t)2 * R * a.D.N * sizeof(float);
@@ -375,7 +390,7 @@ static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
 
 template <int MODE, int C>
 static cudaError_t launch_cols_c(FftArgs a, int nseq, cudaStream_t s) {
-  const int M = 1 << a.D.logM;
+  const int M = dft_len(a.D);
   const size_t st = (MODE == COL_WIENER_1D_REAL) ? 1 : 0;  // real staging only for packed real columns
   const size_t smem = (size_t)C * M * sizeof(float4) + st * 2 * C * a.D.N * sizeof(float);
   cudaError_t e = set_dyn_smem(k_fft_cols<MODE, C>, smem);
@@ -391,7 +406,7 @@ static cudaError_t launch_cols_c(FftArgs a, int nseq, cudaStream_t s) {
 // per CTA against 0.082 ms with four).
 template <int MODE>
 static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
-  const int M = 1 << a.D.logM;
+  const int M = dft_len(a.D);
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 148;
@@ -406,8 +421,10 @@ static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
 cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t s) {
   Dft1ff D;
   D.N = N;
-  D.logM = dft_len_log2(N);
-  const int M = 1 << D.logM;
+  dft_plan(N, &D.logM, &D.M3);
+  const int M = dft_len(D);
+  const double inv = 1.0 / (double)M;
+  D.invM = make_float2((float)inv, (float)(inv - (double)(float)inv));
   D.tw = tab;
   D.c = nullptr;
   D.Bf = nullptr;
@@ -427,7 +444,7 @@ cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t 
     // Bf <- forward power-of-two transform of the circular chirp (in place)
     FftArgs a = {};
     Dft1ff P;
-    P.N = M; P.logM = D.logM; P.tw = tab; P.c = nullptr; P.Bf = nullptr;
+    P.N = M; P.logM = D.logM; P.M3 = D.M3; P.invM = D.invM; P.tw = tab; P.c = nullptr; P.Bf = nullptr;
     a.D = P; a.cbuf = Bf; a.ldc = M; a.nrows = 1;
     if ((e = launch_rows<ROW_FWD_CPLX>(a, s)) != cudaSuccess) return e;
     D.c = c;
@@ -607,7 +624,7 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     const int id = (int)b->jobs[WB_ROW_1D].size();
     b->jobs[WB_ROW_1D].push_back(j);
     for (int q = 0; q < j.nrows; ++q) b->items[WB_ROW_1D].push_back(make_int2(id, q));
-    const size_t sm = (size_t)(1 << (*im.pDW).logM) * sizeof(float4) + (size_t)2 * W * sizeof(float);
+    const size_t sm = (size_t)dft_len(*im.pDW) * sizeof(float4) + (size_t)2 * W * sizeof(float);
     if (sm > b->smem[WB_ROW_1D]) b->smem[WB_ROW_1D] = sm;
     return cudaSuccess;
   }
@@ -622,7 +639,7 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     b->jobs[WB_COL_1D].push_back(j);
     const int nseq = (W + 1) / 2;
     for (int c0 = 0; c0 < nseq; c0 += kBatchColC) b->items[WB_COL_1D].push_back(make_int2(id, c0));
-    const size_t sm = (size_t)kBatchColC * (1 << (*im.pDH).logM) * sizeof(float4) + (size_t)2 * kBatchColC * H * sizeof(float);
+    const size_t sm = (size_t)kBatchColC * dft_len(*im.pDH) * sizeof(float4) + (size_t)2 * kBatchColC * H * sizeof(float);
     if (sm > b->smem[WB_COL_1D]) b->smem[WB_COL_1D] = sm;
     return cudaSuccess;
   }
@@ -647,8 +664,8 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     b->items[WB_ROW_INV].push_back(make_int2(i3, q));
   }
   for (int c0 = 0; c0 < Wh; c0 += kBatchColC) b->items[WB_COL_2D].push_back(make_int2(i2, c0));
-  const size_t smr = (size_t)(1 << (*im.pDW).logM) * sizeof(float4) + (size_t)2 * W * sizeof(float);
-  const size_t smc = (size_t)kBatchColC * (1 << (*im.pDH).logM) * sizeof(float4);
+  const size_t smr = (size_t)dft_len(*im.pDW) * sizeof(float4) + (size_t)2 * W * sizeof(float);
+  const size_t smc = (size_t)kBatchColC * dft_len(*im.pDH) * sizeof(float4);
   if (smr > b->smem[WB_ROW_FWD]) b->smem[WB_ROW_FWD] = smr;
   if (smr > b->smem[WB_ROW_INV]) b->smem[WB_ROW_INV] = smr;
   if (smc > b->smem[WB_COL_2D]) b->smem[WB_COL_2D] = smc;
