@@ -486,6 +486,10 @@ def run_batch(args, world, rank, local):
         wien = db.Batch(fs, hs, ps, 0, kinds=kinds, outs=[torch.empty_like(f) for f in fs])
         stream.synchronize()
         plan_s = time.perf_counter() - t0
+        # tile forms by measurement (dense sums, one-axis form), before capture
+        t0 = time.perf_counter()
+        tuned = full.autotune(reps=2)
+        tune_s = time.perf_counter() - t0
         full.run()
         wien.run()
         n0 = lib.db_launch_count()
@@ -528,9 +532,14 @@ def run_batch(args, world, rank, local):
     # downloads).
     f_host = [pinned_copy(c.f) for c in cases]
     u_host = [torch.empty(c.f.shape, dtype=torch.float32).pin_memory() for c in cases]
+    # the sub-batch plans take the tuned forms through the process-wide settings
+    db.set_dense_min(50 if tuned["dense"] else 101)
+    db.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[tuned["windows"]])
     with torch.cuda.stream(stream):
         bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=8, device=dev)
         bs.run(f_host, u_host)
+    db.set_dense_min(0)
+    db.set_one_axis_min(0)
     for a, b_ in zip(u_host, full.us):
         if not torch.equal(a, b_.cpu()):
             raise RuntimeError("streamed batch differs from the single batch")
@@ -578,7 +587,7 @@ def run_batch(args, world, rank, local):
                 "path": f"db_batch_stream_run_host (C ABI): {e2e_parts} sub-batches, page-locked host images, "
                         "copies overlapped with the other sub-batches' runs"},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0,
-        "plan_s": plan_s, "generate_s": gen_s, "clocks": clk.summary(),
+        "plan_s": plan_s, "autotune_s": tune_s, "autotuned": tuned, "generate_s": gen_s, "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_batch(all_cases)

@@ -206,6 +206,25 @@ db_status db_batch_run(db_batch* b, int* dev_status, void* stream);
 
 void db_batch_destroy(db_batch* b);
 
+/* Choose the batch's tile forms by measurement (the batched counterpart of
+ * db_plan_autotune): runs the whole batch `reps` times after one warm-up per
+ * candidate, timed with CUDA events on `stream`, for the dense sums on and
+ * off (images with dense-eligible 2D PSFs, odd sides 3..25) crossed with the
+ * forms of non-box one-axis PSFs (the size rule of db_set_one_axis_min's
+ * default, register windows for all, tap groups for all), and keeps the
+ * fastest combination for every later db_batch_run.  Classes absent from
+ * the batch are not tried.  The runs overwrite the images' outputs;
+ * synchronises `stream` (call it before capturing the run in a graph; a
+ * graph captured earlier keeps working and picks up the choice).
+ * *dense_out (nullable) receives 1 when the dense sums were chosen,
+ * *windows_out (nullable) 2 for the size rule, 1 for register windows, 0
+ * for tap groups.  The result of each image equals db_deblur's under the
+ * corresponding process-wide settings (db_set_dense_min 50 or 101;
+ * db_set_one_axis_min 0, 1 or 256).  DB_ERR_ARG for a null batch or
+ * reps < 1. */
+db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream, int* dense_out,
+                            int* windows_out);
+
 /* db_batch_create + db_batch_run + db_batch_destroy. */
 db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
                           int* dev_status, void* stream);

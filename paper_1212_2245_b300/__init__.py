@@ -390,6 +390,19 @@ class Batch:
             self.ws.raise_on_flags("db_batch_run")
         return self.us
 
+    def autotune(self, reps: int = 3):
+        """Choose the tile forms by timing whole runs (db_batch_autotune): the
+        dense sums on or off for dense-eligible 2D PSFs, register windows or
+        tap groups for non-box one-axis PSFs.  Overwrites the outputs and
+        synchronises the current stream.  Returns {"dense": bool, "windows": w} with w = "rule"
+        (the size rule of set_one_axis_min(0)), "all" (register windows) or "none" (tap groups)."""
+        d, w = ctypes.c_int(), ctypes.c_int()
+        self.ws.reset_status()
+        _check(_lib.load().db_batch_autotune(self._h, int(reps), self.ws.status.data_ptr(), _stream(),
+                                             ctypes.byref(d), ctypes.byref(w)), "db_batch_autotune")
+        self.ws.raise_on_flags("db_batch_autotune")
+        return {"dense": bool(d.value), "windows": {0: "none", 1: "all", 2: "rule"}[w.value]}
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().db_batch_destroy(self._h)

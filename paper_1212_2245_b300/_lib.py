@@ -54,6 +54,7 @@ SIGNATURES = {
                                 c_void_p, ctypes.POINTER(c_void_p)]),
     "db_batch_run": (c_int, [c_void_p, c_void_p, c_void_p]),
     "db_batch_destroy": (None, [c_void_p]),
+    "db_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "db_deblur_batch": (c_int, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_void_p, c_size_t, c_void_p,
                                 c_void_p]),
     "db_batch_stream_workspace_bytes": (c_size_t, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_int]),

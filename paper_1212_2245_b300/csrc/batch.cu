@@ -278,6 +278,10 @@ struct BatchPlan {
   int* d_work = nullptr;
   size_t smem = 0;
   int grid = 0;
+  // tunable forms (db_batch_autotune): per image the dense width of a
+  // dense-eligible 2D PSF (else 0), the register-window code of a non-box
+  // one-axis PSF (3 row, 4 column; else 0) and the code the size rule chose
+  std::vector<int> dense_kw, window_box, rule_box;
   ~BatchPlan() { if (wb) wiener_batch_delete(wb); }
 };
 
@@ -415,6 +419,9 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     const int axis = axis_mode(x.psf.kind, kh, kw);
     bi.box = axis == 0 ? 0 : (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
     bi.kwd = (axis == 0 && dense_eligible(kh, kw)) ? kw : 0;
+    P->dense_kw.push_back(bi.kwd);
+    P->window_box.push_back((x.psf.kind != DB_PSF_BOX && (kh == 1 || kw == 1)) ? (kh == 1 ? 3 : 4) : 0);
+    P->rule_box.push_back(bi.box);
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
     bi.p.floor = x.p.pos_floor; bi.p.phi_robust = x.p.phi_robust; bi.p.psi_tv = x.p.psi_tv;
     bi.p.rf_lut = rf_lut_device();
@@ -424,6 +431,12 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
                                   split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max));
     if (bi.kwd)
       sm = std::max(sm, std::max(dense_smem_q(kBTH, kBTW, kh, kw), dense_smem_update(kBTH, kBTW, kh, kw)));
+    if (P->window_box.back()) {  // both one-axis forms may be chosen later (db_batch_autotune)
+      const int L = kh == 1 ? kw : kh;
+      sm = std::max(sm, std::max(box_smem_q(kBTH, kBTW, L, kh == 1), box_smem_update(kBTH, kBTW, L, kh == 1)));
+      sm = std::max(sm, std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),
+                                 split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max)));
+    }
     if (sm > P->smem) P->smem = sm;
     for (int i0 = 0; i0 < x.H; i0 += kBTH)
       for (int j0 = 0; j0 < x.W; j0 += kBTW) P->tiles.push_back(make_int4(i, i0, j0, bi.ng_max));
@@ -497,6 +510,22 @@ db_status batch_run(const BatchPlan* P, int* status, cudaStream_t s) {
 }
 
 void batch_destroy(BatchPlan* P) { delete P; }
+
+// Set the tunable forms of every image (dense: dense bodies for the
+// dense-eligible 2D PSFs; windows for the non-box one-axis PSFs: 0 tap
+// groups, 1 register windows, 2 the size rule's choice) and upload the
+// descriptors (synchronises the stream: the host table is reused).
+static db_status batch_set_forms(BatchPlan* P, bool dense, int windows, cudaStream_t s) {
+  for (int i = 0; i < P->n; ++i) {
+    P->imgs[i].kwd = dense ? P->dense_kw[i] : 0;
+    if (P->window_box[i]) P->imgs[i].box = windows == 2 ? P->rule_box[i] : windows == 1 ? P->window_box[i] : 0;
+  }
+  if (cudaMemcpyAsync(P->d_imgs, P->imgs.data(), (size_t)P->n * sizeof(BatchImg), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DB_ERR_CUDA;
+  return DB_OK;
+}
 
 // ---------------------------------------------------------------------------
 // streamed batch: host images in, results out, the copies overlapped with
@@ -687,6 +716,50 @@ db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_hos
   // `stream` completes only after every result has reached the host
   for (size_t k = 0; k < np; ++k)
     if (cudaStreamWaitEvent(s, B->ev_down[k], 0) != cudaSuccess) return DB_ERR_CUDA;
+  return DB_OK;
+}
+
+db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream, int* dense_out,
+                            int* windows_out) {
+  BatchPlan* P = (BatchPlan*)b;
+  if (!P || reps < 1) return DB_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool has_dense = false, has_win = false;
+  for (int i = 0; i < P->n; ++i) {
+    has_dense |= P->dense_kw[i] != 0;
+    has_win |= P->window_box[i] != 0;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return DB_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DB_ERR_CUDA; }
+  float best = -1.f;
+  bool best_d = true;
+  int best_w = 2;
+  db_status st = DB_OK;
+  const int wforms[3] = {2, 1, 0};  // the size rule, register windows, tap groups
+  for (int d = 0; d < 2 && st == DB_OK; ++d) {
+    if (d == 1 && !has_dense) break;
+    for (int iw = 0; iw < 3 && st == DB_OK; ++iw) {
+      if (iw > 0 && !has_win) break;
+      const bool dense = d == 0;
+      const int windows = wforms[iw];
+      if ((st = batch_set_forms(P, dense, windows, s)) != DB_OK) break;
+      if ((st = batch_run(P, dev_status, s)) != DB_OK) break;  // warm-up
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = DB_ERR_CUDA; break; }
+      for (int k = 0; k < reps && st == DB_OK; ++k) st = batch_run(P, dev_status, s);
+      if (st != DB_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = DB_ERR_CUDA; break; }
+      if (best < 0.f || ms < best) { best = ms; best_d = dense; best_w = windows; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DB_OK) return st;
+  if ((st = batch_set_forms(P, best_d, best_w, s)) != DB_OK) return st;
+  if (dense_out) *dense_out = best_d ? 1 : 0;
+  if (windows_out) *windows_out = best_w;
   return DB_OK;
 }
 

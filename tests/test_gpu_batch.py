@@ -133,3 +133,29 @@ def test_batch_plans_with_different_shared_memory_coexist(lib):
             assert torch.equal(u, lib.deblur(f, cuda(c.h), c.params, 3, kind=c.psf_kind))
     bb.close()
     bs.close()
+
+
+def test_batch_autotune_keeps_the_results_of_the_chosen_forms(lib):
+    """The batch's autotuner times the dense-sum and one-axis forms and keeps
+    the fastest; every image then equals the single-image pipeline under the
+    matching process-wide settings, bit for bit, and the oracle."""
+    cases = small_batch([0, 1, 3, 5, 256, 257, 259, 300], cap=200)
+    fs = [cuda(c.f) for c in cases]
+    hs = [cuda(c.h) for c in cases]
+    b = lib.Batch(fs, hs, [c.params for c in cases], 4, kinds=[c.psf_kind for c in cases])
+    choice = b.autotune(reps=2)
+    assert set(choice) == {"dense", "windows"} and choice["windows"] in ("rule", "all", "none")
+    outs = [u.clone() for u in b.run()]
+    lib.set_dense_min(50 if choice["dense"] else 101)
+    lib.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[choice["windows"]])
+    try:
+        for c, f, h, u in zip(cases, fs, hs, outs):
+            assert torch.equal(u, lib.deblur(f, h, c.params, 4, kind=c.psf_kind)), c.name
+    finally:
+        lib.set_dense_min(0)
+        lib.set_one_axis_min(0)
+    for c, u in zip(cases[:2] + cases[4:6], outs[:2] + outs[4:6]):
+        _, ref = oracle.wr3l(c.f, c.h, c.params, 4)
+        d = (u.double().cpu() - ref).abs()
+        assert float(d.max()) <= MAX_ABS and float(d.pow(2).mean().sqrt()) <= RMS, c.name
+    b.close()
