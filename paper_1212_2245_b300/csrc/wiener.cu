@@ -116,6 +116,7 @@ struct FftArgs {
   Dft1ff D;                    // transform along the kernel's axis
   int nrows;                   // rows (row kernels) or columns (column kernels) of data
   int img_rows;                // image rows (packed row-pair Wiener)
+  int seqs_per_cta;            // batched row passes: sequences per CTA (items step by it)
   float K, floor_;
   float2 scale;                // 1/(transform size), float-float
 };
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256) k_fft_rows_batch(const FftArgs* __restric
   extern __shared__ float4 smem4[];
   const int2 it = items[blockIdx.x];
   const FftArgs a = jobs[it.x];
-  rows_body<MODE>(smem4, a, it.y, 1);
+  rows_body<MODE>(smem4, a, it.y, a.seqs_per_cta);
 }
 
 // Column transforms: a CTA owns C adjacent sequences laid out across a row
@@ -606,6 +607,25 @@ struct WienerBatch {
   size_t smem[WB_STAGES] = {};
 };
 
+// Sequences per CTA of a batched row job: as many as keep R x M <= 2048
+// (a power of two, at most the job's rows), so that short transforms still
+// give the CTA's 256 threads work in every stage.
+static int batch_row_seqs(int M, int nrows) {
+  int R = 1;
+  while (2 * R * M <= 2048 && 2 * R <= nrows) R *= 2;
+  return R;
+}
+
+// Append the items of a batched row job (one per group of seqs_per_cta rows)
+// and grow the stage's shared memory to the job's need.
+static void add_row_items(WienerBatch* b, int stage, int id, FftArgs& j, int N) {
+  const int M = dft_len(j.D), R = batch_row_seqs(M, j.nrows);
+  j.seqs_per_cta = R;
+  for (int q = 0; q < j.nrows; q += R) b->items[stage].push_back(make_int2(id, q));
+  const size_t sm = (size_t)R * M * sizeof(float4) + (size_t)2 * R * N * sizeof(float);
+  if (sm > b->smem[stage]) b->smem[stage] = sm;
+}
+
 WienerBatch* wiener_batch_new() { return new WienerBatch(); }
 size_t wiener_job_bytes() { return sizeof(FftArgs); }
 void wiener_batch_delete(WienerBatch* b) { delete b; }
@@ -622,10 +642,8 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.D = (*im.pDW);
     j.nrows = (H + 1) / 2; j.img_rows = H; j.K = im.K; j.floor_ = im.floor_; j.scale = ff_const(1.0 / W);
     const int id = (int)b->jobs[WB_ROW_1D].size();
+    add_row_items(b, WB_ROW_1D, id, j, W);
     b->jobs[WB_ROW_1D].push_back(j);
-    for (int q = 0; q < j.nrows; ++q) b->items[WB_ROW_1D].push_back(make_int2(id, q));
-    const size_t sm = (size_t)dft_len(*im.pDW) * sizeof(float4) + (size_t)2 * W * sizeof(float);
-    if (sm > b->smem[WB_ROW_1D]) b->smem[WB_ROW_1D] = sm;
     return cudaSuccess;
   }
   if (im.kw == 1) {
@@ -656,18 +674,13 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
   o.floor_ = im.floor_; o.scale = ff_const(1.0 / ((double)H * (double)W));
   const int i1 = (int)b->jobs[WB_ROW_FWD].size(), i2 = (int)b->jobs[WB_COL_2D].size(),
             i3 = (int)b->jobs[WB_ROW_INV].size();
+  add_row_items(b, WB_ROW_FWD, i1, d, W);
+  add_row_items(b, WB_ROW_INV, i3, o, W);
   b->jobs[WB_ROW_FWD].push_back(d);
   b->jobs[WB_COL_2D].push_back(g);
   b->jobs[WB_ROW_INV].push_back(o);
-  for (int q = 0; q < Hp; ++q) {
-    b->items[WB_ROW_FWD].push_back(make_int2(i1, q));
-    b->items[WB_ROW_INV].push_back(make_int2(i3, q));
-  }
   for (int c0 = 0; c0 < Wh; c0 += kBatchColC) b->items[WB_COL_2D].push_back(make_int2(i2, c0));
-  const size_t smr = (size_t)dft_len(*im.pDW) * sizeof(float4) + (size_t)2 * W * sizeof(float);
   const size_t smc = (size_t)kBatchColC * dft_len(*im.pDH) * sizeof(float4);
-  if (smr > b->smem[WB_ROW_FWD]) b->smem[WB_ROW_FWD] = smr;
-  if (smr > b->smem[WB_ROW_INV]) b->smem[WB_ROW_INV] = smr;
   if (smc > b->smem[WB_COL_2D]) b->smem[WB_COL_2D] = smc;
   return cudaSuccess;
 }
