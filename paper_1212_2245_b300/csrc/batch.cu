@@ -343,9 +343,10 @@ size_t batch_ws_bytes(const db_image_desc* d, int n, int iters, db_status* why) 
   off += align256(ntiles * sizeof(int4));
   off += 256;                                         // barrier
   off += align256((size_t)(2 * iters + 2) * sizeof(int));  // work counters
-  // batched-Wiener job tables: at most 3 jobs per image, one item per row
+  // batched-Wiener job tables (5 stages x (jobs + 3 item classes) regions):
+  // at most 3 jobs per image, one item per row
   // (pair) or column group (bounded by nitems), plus alignment slack
-  off += 10 * 256 + (size_t)3 * n * wiener_job_bytes() + nitems * sizeof(int2);
+  off += 20 * 256 + (size_t)3 * n * wiener_job_bytes() + nitems * sizeof(int2);
   return off;
 }
 

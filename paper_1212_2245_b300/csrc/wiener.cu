@@ -597,14 +597,24 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 // one image with that image's own transform lengths.
 // ---------------------------------------------------------------------------
 enum { WB_ROW_1D = 0, WB_ROW_FWD = 1, WB_COL_1D = 2, WB_COL_2D = 3, WB_ROW_INV = 4, WB_STAGES = 5 };
-constexpr int kBatchColC = 2;  // columns per CTA (4: 36.0 ms for batch512's Wiener, 2: 30.8 ms)
+// Column passes: columns per CTA by transform length, in classes launched
+// separately: 2 (the longest transforms: 4 per CTA left one CTA per SM,
+// 36.0 against 30.8 ms for batch512's Wiener), 4 or 8 while C x M <= 4096,
+// so that short transforms still give the CTA's threads work.
+constexpr int kColClasses = 3;
+__host__ __device__ constexpr int col_class_c(int k) { return 2 << k; }
+static int col_class(int M) {
+  int k = 0;
+  while (k + 1 < kColClasses && col_class_c(k + 1) * M <= 4096) ++k;
+  return k;
+}
 
 struct WienerBatch {
   std::vector<FftArgs> jobs[WB_STAGES];
-  std::vector<int2> items[WB_STAGES];
+  std::vector<int2> items[WB_STAGES][kColClasses];  // row stages use class 0 only
   FftArgs* d_jobs[WB_STAGES] = {};
-  int2* d_items[WB_STAGES] = {};
-  size_t smem[WB_STAGES] = {};
+  int2* d_items[WB_STAGES][kColClasses] = {};
+  size_t smem[WB_STAGES][kColClasses] = {};
 };
 
 // Sequences per CTA of a batched row job: as many as keep R x M <= 2048
@@ -621,9 +631,9 @@ static int batch_row_seqs(int M, int nrows) {
 static void add_row_items(WienerBatch* b, int stage, int id, FftArgs& j, int N) {
   const int M = dft_len(j.D), R = batch_row_seqs(M, j.nrows);
   j.seqs_per_cta = R;
-  for (int q = 0; q < j.nrows; q += R) b->items[stage].push_back(make_int2(id, q));
+  for (int q = 0; q < j.nrows; q += R) b->items[stage][0].push_back(make_int2(id, q));
   const size_t sm = (size_t)R * M * sizeof(float4) + (size_t)2 * R * N * sizeof(float);
-  if (sm > b->smem[stage]) b->smem[stage] = sm;
+  if (sm > b->smem[stage][0]) b->smem[stage][0] = sm;
 }
 
 WienerBatch* wiener_batch_new() { return new WienerBatch(); }
@@ -655,10 +665,10 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     j.nrows = W; j.K = im.K; j.floor_ = im.floor_; j.scale = ff_const(1.0 / H);
     const int id = (int)b->jobs[WB_COL_1D].size();
     b->jobs[WB_COL_1D].push_back(j);
-    const int nseq = (W + 1) / 2;
-    for (int c0 = 0; c0 < nseq; c0 += kBatchColC) b->items[WB_COL_1D].push_back(make_int2(id, c0));
-    const size_t sm = (size_t)kBatchColC * dft_len(*im.pDH) * sizeof(float4) + (size_t)2 * kBatchColC * H * sizeof(float);
-    if (sm > b->smem[WB_COL_1D]) b->smem[WB_COL_1D] = sm;
+    const int nseq = (W + 1) / 2, M = dft_len(*im.pDH), k = col_class(M), C = col_class_c(k);
+    for (int c0 = 0; c0 < nseq; c0 += C) b->items[WB_COL_1D][k].push_back(make_int2(id, c0));
+    const size_t sm = (size_t)C * M * sizeof(float4) + (size_t)2 * C * H * sizeof(float);
+    if (sm > b->smem[WB_COL_1D][k]) b->smem[WB_COL_1D][k] = sm;
     return cudaSuccess;
   }
   if ((e = run_psf_spectrum_half(im.taps, im.kh, im.kw, H, W, im.spec, (*im.pDW), (*im.pDH), s)) != cudaSuccess)
@@ -679,16 +689,19 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
   b->jobs[WB_ROW_FWD].push_back(d);
   b->jobs[WB_COL_2D].push_back(g);
   b->jobs[WB_ROW_INV].push_back(o);
-  for (int c0 = 0; c0 < Wh; c0 += kBatchColC) b->items[WB_COL_2D].push_back(make_int2(i2, c0));
-  const size_t smc = (size_t)kBatchColC * dft_len(*im.pDH) * sizeof(float4);
-  if (smc > b->smem[WB_COL_2D]) b->smem[WB_COL_2D] = smc;
+  const int MH = dft_len(*im.pDH), kc = col_class(MH), CC = col_class_c(kc);
+  for (int c0 = 0; c0 < Wh; c0 += CC) b->items[WB_COL_2D][kc].push_back(make_int2(i2, c0));
+  const size_t smc = (size_t)CC * MH * sizeof(float4);
+  if (smc > b->smem[WB_COL_2D][kc]) b->smem[WB_COL_2D][kc] = smc;
   return cudaSuccess;
 }
 
 size_t wiener_batch_table_bytes(const WienerBatch* b) {
   size_t n = 0;
-  for (int k = 0; k < WB_STAGES; ++k)
-    n += align256(b->jobs[k].size() * sizeof(FftArgs)) + align256(b->items[k].size() * sizeof(int2));
+  for (int k = 0; k < WB_STAGES; ++k) {
+    n += align256(b->jobs[k].size() * sizeof(FftArgs));
+    for (int c = 0; c < kColClasses; ++c) n += align256(b->items[k][c].size() * sizeof(int2));
+  }
   return n;
 }
 
@@ -703,39 +716,49 @@ cudaError_t wiener_batch_upload(WienerBatch* b, void* dst, cudaStream_t s) {
       if (e != cudaSuccess) return e;
     }
     p += align256(b->jobs[k].size() * sizeof(FftArgs));
-    b->d_items[k] = (int2*)p;
-    if (!b->items[k].empty()) {
-      cudaError_t e = cudaMemcpyAsync(p, b->items[k].data(), b->items[k].size() * sizeof(int2),
-                                      cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return e;
+    for (int c = 0; c < kColClasses; ++c) {
+      b->d_items[k][c] = (int2*)p;
+      if (!b->items[k][c].empty()) {
+        cudaError_t e = cudaMemcpyAsync(p, b->items[k][c].data(), b->items[k][c].size() * sizeof(int2),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+      }
+      p += align256(b->items[k][c].size() * sizeof(int2));
+      if (b->smem[k][c] > kSmemLimit) return cudaErrorInvalidValue;
     }
-    p += align256(b->items[k].size() * sizeof(int2));
   }
-  for (int k = 0; k < WB_STAGES; ++k)
-    if (b->smem[k] > kSmemLimit) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
 template <int MODE>
 static cudaError_t launch_rows_batch(const WienerBatch* b, int stage, cudaStream_t s) {
-  if (b->items[stage].empty()) return cudaSuccess;
-  cudaError_t e = set_dyn_smem(k_fft_rows_batch<MODE>, b->smem[stage]);
+  if (b->items[stage][0].empty()) return cudaSuccess;
+  cudaError_t e = set_dyn_smem(k_fft_rows_batch<MODE>, b->smem[stage][0]);
   if (e != cudaSuccess) return e;
-  k_fft_rows_batch<MODE><<<(unsigned)b->items[stage].size(), 256, b->smem[stage], s>>>(b->d_jobs[stage],
-                                                                                     b->d_items[stage]);
+  k_fft_rows_batch<MODE><<<(unsigned)b->items[stage][0].size(), 256, b->smem[stage][0], s>>>(
+      b->d_jobs[stage], b->d_items[stage][0]);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int MODE, int K>
+static cudaError_t launch_cols_batch_c(const WienerBatch* b, int stage, cudaStream_t s) {
+  if (b->items[stage][K].empty()) return cudaSuccess;
+  auto kern = k_fft_cols_batch<MODE, col_class_c(K)>;
+  cudaError_t e = set_dyn_smem(kern, b->smem[stage][K]);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)b->items[stage][K].size(), 256, b->smem[stage][K], s>>>(b->d_jobs[stage], b->d_items[stage][K]);
   count_launch();
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_cols_batch(const WienerBatch* b, int stage, cudaStream_t s) {
-  if (b->items[stage].empty()) return cudaSuccess;
-  auto kern = k_fft_cols_batch<MODE, kBatchColC>;
-  cudaError_t e = set_dyn_smem(kern, b->smem[stage]);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)b->items[stage].size(), 256, b->smem[stage], s>>>(b->d_jobs[stage], b->d_items[stage]);
-  count_launch();
-  return cudaGetLastError();
+  static_assert(kColClasses == 3, "one launch per column class");
+  cudaError_t e;
+  if ((e = launch_cols_batch_c<MODE, 0>(b, stage, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch_c<MODE, 1>(b, stage, s)) != cudaSuccess) return e;
+  return launch_cols_batch_c<MODE, 2>(b, stage, s);
 }
 
 cudaError_t wiener_batch_run(const WienerBatch* b, cudaStream_t s) {
