@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--images", type=int, default=512,
                     help="batch512 only: deblur an evenly spaced subset of this many of the 512 images "
                          "(a smaller case of the same kernels, for profiling)")
+    ap.add_argument("--forms", choices=["auto"] + [f"{d}/{w}" for d in ("dense", "groups")
+                                                    for w in ("all", "rule", "none")], default="auto",
+                    help="batch512 only: tile forms timed (auto: chosen by db_batch_autotune before capture) "
+                         "or fixed as <2D sums>/<one-axis register windows>, e.g. dense/all (for profiling: "
+                         "the autotuner's own runs are then not launched)")
     ap.add_argument("--rf", choices=["log1p", "lut"], default="log1p",
                     help="evaluation of r_f: log1p (default) or the lookup table of Sec. 4.1")
     return ap.parse_args()
@@ -480,6 +485,11 @@ def run_batch(args, world, rank, local):
     flops_iter = sum(c.f.size * flops_per_px_iter(c.h, c.psf_kind) for c in cases)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    fixed = None
+    if args.forms != "auto":
+        d, w = args.forms.split("/")
+        fixed = {"dense": d == "dense", "windows": w}
+        set_batch_forms(fixed)
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
         full = db.Batch(fs, hs, ps, iters, kinds=kinds)
@@ -488,7 +498,7 @@ def run_batch(args, world, rank, local):
         plan_s = time.perf_counter() - t0
         # tile forms by measurement (dense sums, one-axis form), before capture
         t0 = time.perf_counter()
-        tuned = full.autotune(reps=2)
+        tuned = full.autotune(reps=2) if fixed is None else fixed
         tune_s = time.perf_counter() - t0
         full.run()
         wien.run()
@@ -533,13 +543,11 @@ def run_batch(args, world, rank, local):
     f_host = [pinned_copy(c.f) for c in cases]
     u_host = [torch.empty(c.f.shape, dtype=torch.float32).pin_memory() for c in cases]
     # the sub-batch plans take the tuned forms through the process-wide settings
-    db.set_dense_min(50 if tuned["dense"] else 101)
-    db.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[tuned["windows"]])
+    set_batch_forms(tuned)
     with torch.cuda.stream(stream):
         bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=8, device=dev)
         bs.run(f_host, u_host)
-    db.set_dense_min(0)
-    db.set_one_axis_min(0)
+    set_batch_forms(None)
     for a, b_ in zip(u_host, full.us):
         if not torch.equal(a, b_.cpu()):
             raise RuntimeError("streamed batch differs from the single batch")
@@ -587,11 +595,25 @@ def run_batch(args, world, rank, local):
                 "path": f"db_batch_stream_run_host (C ABI): {e2e_parts} sub-batches, page-locked host images, "
                         "copies overlapped with the other sub-batches' runs"},
         "gpu_launches": (n1 - n0) * K, "launches_per_step": n1 - n0,
-        "plan_s": plan_s, "autotune_s": tune_s, "autotuned": tuned, "generate_s": gen_s, "clocks": clk.summary(),
+        "plan_s": plan_s, "autotune_s": tune_s if fixed is None else None,
+        "autotuned" if fixed is None else "forms": tuned, "generate_s": gen_s, "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_batch(all_cases)
     return line
+
+
+def set_batch_forms(forms):
+    """Process-wide settings under which a batch plan takes the given tile
+    forms ({"dense": bool, "windows": "all" | "rule" | "none"}; None: the
+    defaults)."""
+    import paper_1212_2245_b300 as db
+    if forms is None:
+        db.set_dense_min(0)
+        db.set_one_axis_min(0)
+        return
+    db.set_dense_min(50 if forms["dense"] else 101)
+    db.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[forms["windows"]])
 
 
 def batch_sample_order(n):
