@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "fft8.cuh"
 #include "internal.cuh"
 
 namespace db {
@@ -175,6 +176,120 @@ __global__ void __launch_bounds__(256, 4) k_fourier_cols(float2* __restrict__ bu
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident passes (fft8.cuh) for sides 64..4096: the same four
+// passes, with each transform's data in registers between shared-memory
+// exchanges, the pointwise work done on the registers of the last inverse
+// pass, and the column spectrum product between the forward and inverse
+// bottom passes.  C = f8::seqs(L) rows or columns per CTA, thread t C + c.
+// ---------------------------------------------------------------------------
+template <int L, int MODE>
+__global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_rows8(FourierArgs a) {
+  constexpr int C = f8::seqs(L), N = 1 << L, T = N / 8;
+  extern __shared__ float2 smem[];
+  const int q = threadIdx.x % C, t = threadIdx.x / C;
+  const int i = blockIdx.x * C + q;
+  const bool ok = i < a.H;
+  const int ic = ok ? i : a.H - 1;  // rows past the image load the last row and store nothing
+  float2 v[8];
+  if (MODE == FR_U) {
+    const float* ur = a.uin + (size_t)ic * a.ldin;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = make_float2(ur[t + T * r], 0.f);
+  } else {
+    const float4* src = (const float4*)((MODE == FR_MID ? a.X : a.Z) + (size_t)ic * N + 8 * t);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 x = src[u];
+      v[2 * u] = make_float2(x.x, x.y);
+      v[2 * u + 1] = make_float2(x.z, x.w);
+    }
+    f8::dit_chain<L, f8::bottom_hb(L), C>(v, smem, t, q, a.twW);
+    // v[r]: element t + T r, natural order
+    const RrlParams& p = a.p;
+    if (MODE == FR_MID) {
+      const float* fr = a.f + (size_t)ic * a.ldf;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float b = v[r].x * a.scale;
+        const float fv = fmaxf(fr[t + T * r], p.floor);
+        const float w = robust_weight_f(b, fv, p);
+        v[r] = make_float2(__fdividef(w * (fv - b), b), w);
+      }
+    } else {
+      const float* m0 = a.uin + (size_t)ic * a.ldin;
+      const float* n1 = a.uin + (size_t)max(ic - 1, 0) * a.ldin;
+      const float* n2 = a.uin + (size_t)max(ic - 2, 0) * a.ldin;
+      const float* s1 = a.uin + (size_t)min(ic + 1, a.H - 1) * a.ldin;
+      const float* s2 = a.uin + (size_t)min(ic + 2, a.H - 1) * a.ldin;
+      float* out = a.uout + (size_t)ic * a.ldout;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int c = t + T * r;
+        const int cw = max(c - 1, 0), ce = min(c + 1, N - 1);
+        const int cww = max(c - 2, 0), cee = min(c + 2, N - 1);
+        const float ctr = m0[c], e = m0[ce], w_ = m0[cw], n = n1[c], s = s1[c];
+        const float s1e = s1[ce], s1w = s1[cw], n1e = n1[ce], n1w = n1[cw];
+        const float gc = diffusivity_f(0.5f * (e - w_), 0.5f * (s - n), p);
+        const float ge = diffusivity_f(0.5f * (m0[cee] - ctr), 0.5f * (s1e - n1e), p);
+        const float gw = diffusivity_f(0.5f * (ctr - m0[cww]), 0.5f * (s1w - n1w), p);
+        const float gs = diffusivity_f(0.5f * (s1e - s1w), 0.5f * (s2[c] - ctr), p);
+        const float gn = diffusivity_f(0.5f * (n1e - n1w), 0.5f * (ctr - n2[c]), p);
+        const float D = 0.5f * ((ge + gc) * (e - ctr) - (gc + gw) * (ctr - w_) + (gs + gc) * (s - ctr) -
+                                (gc + gn) * (ctr - n));
+        const float dl = v[r].x * a.scale, B = v[r].y * a.scale;
+        const float den = B - p.alpha * fminf(D, 0.f);
+        const float un = fmaf(ctr, __fdividef(fmaf(p.alpha, D, dl), den), ctr);
+        if (ok) {
+          if (!isfinite(un) && a.status) atomicOr(a.status, DB_FLAG_NONFINITE);
+          out[c] = un;
+        }
+        v[r] = make_float2(un, 0.f);
+      }
+      if (!a.write_next) return;  // the same for every thread of the launch
+    }
+  }
+  f8::dif_chain<L, L - 1, C>(v, smem, t, q, a.twW);
+  if (!ok) return;
+  float4* dst = (float4*)((MODE == FR_MID ? a.Z : a.X) + (size_t)i * N + 8 * t);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[2 * u].x, v[2 * u].y, v[2 * u + 1].x, v[2 * u + 1].y);
+}
+
+// C = f8::seqs(L) columns of length H = 2^L per CTA: DIF, x S (or conj S)
+// on the bottom pass's registers, DIT, in place.
+template <int L, bool CONJ>
+__global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2)
+    k_fourier_cols8(float2* __restrict__ buf, const float2* __restrict__ S, const float2* __restrict__ twH, int W) {
+  constexpr int C = f8::seqs(L), H = 1 << L, T = H / 8;
+  extern __shared__ float2 smem[];
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  const int col = blockIdx.x * C + c;
+  const bool ok = col < W;
+  const int cc = ok ? col : W - 1;
+  // element (k, col) at buf[k W + col]; 32-bit offsets (H W <= 2^24), so
+  // that no 64-bit address has to live across the transforms
+  int off = t * W + cc;
+  const int step = T * W;
+  float2 v[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = buf[off + r * step];
+  f8::dif_chain<L, L - 1, C>(v, smem, t, c, twH);
+  const float4* s4 = (const float4*)(S + (size_t)cc * H + 8 * t);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float4 sv = __ldg(s4 + u);
+    const float2 s0 = make_float2(sv.x, sv.y), s1 = make_float2(sv.z, sv.w);
+    v[2 * u] = CONJ ? cmulc(v[2 * u], s0) : cmul(v[2 * u], s0);
+    v[2 * u + 1] = CONJ ? cmulc(v[2 * u + 1], s1) : cmul(v[2 * u + 1], s1);
+  }
+  f8::dit_chain<L, f8::bottom_hb(L), C>(v, smem, t, c, twH);
+  if (!ok) return;
+  asm volatile("" : "+r"(off));  // recompute the addresses rather than keep the loads' ones live
+#pragma unroll
+  for (int r = 0; r < 8; ++r) buf[off + r * step] = v[r];
+}
+
 template <typename K>
 static cudaError_t set_smem_f(K kern, size_t smem) {
   if (smem > 48 * 1024)
@@ -182,8 +297,40 @@ static cudaError_t set_smem_f(K kern, size_t smem) {
   return cudaSuccess;
 }
 
+template <int L, int MODE>
+static cudaError_t launch_frow8(const FourierArgs& a, cudaStream_t s) {
+  constexpr int C = f8::seqs(L);
+  const size_t smem = (size_t)C * f8::padded(1 << L) * sizeof(float2);
+  cudaError_t e = set_smem_f(k_fourier_rows8<L, MODE>, smem);
+  if (e != cudaSuccess) return e;
+  k_fourier_rows8<L, MODE><<<(a.H + C - 1) / C, f8::threads(L), smem, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int L, bool CONJ>
+static cudaError_t launch_fcol8(float2* buf, const float2* S, const float2* twH, int W, cudaStream_t s) {
+  constexpr int C = f8::seqs(L);
+  const size_t smem = (size_t)C * f8::padded(1 << L) * sizeof(float2);
+  cudaError_t e = set_smem_f(k_fourier_cols8<L, CONJ>, smem);
+  if (e != cudaSuccess) return e;
+  k_fourier_cols8<L, CONJ><<<(W + C - 1) / C, f8::threads(L), smem, s>>>(buf, S, twH, W);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int MODE>
 static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
+  switch (a.logW) {
+    case 6: return launch_frow8<6, MODE>(a, s);
+    case 7: return launch_frow8<7, MODE>(a, s);
+    case 8: return launch_frow8<8, MODE>(a, s);
+    case 9: return launch_frow8<9, MODE>(a, s);
+    case 10: return launch_frow8<10, MODE>(a, s);
+    case 11: return launch_frow8<11, MODE>(a, s);
+    case 12: return launch_frow8<12, MODE>(a, s);
+    default: break;
+  }
   const size_t smem = (size_t)fft_padded(a.W) * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
   cudaError_t e = set_smem_f(k_fourier_rows<MODE>, smem);
   if (e != cudaSuccess) return e;
@@ -195,6 +342,16 @@ static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
 template <bool CONJ>
 static cudaError_t launch_fcol(float2* buf, const float2* S, const float2* twH, int H, int W, cudaStream_t s) {
   const int logH = ilog2(H);
+  switch (logH) {
+    case 6: return launch_fcol8<6, CONJ>(buf, S, twH, W, s);
+    case 7: return launch_fcol8<7, CONJ>(buf, S, twH, W, s);
+    case 8: return launch_fcol8<8, CONJ>(buf, S, twH, W, s);
+    case 9: return launch_fcol8<9, CONJ>(buf, S, twH, W, s);
+    case 10: return launch_fcol8<10, CONJ>(buf, S, twH, W, s);
+    case 11: return launch_fcol8<11, CONJ>(buf, S, twH, W, s);
+    case 12: return launch_fcol8<12, CONJ>(buf, S, twH, W, s);
+    default: break;
+  }
   if (H <= 1024) {
     constexpr int C = 4;
     const size_t smem = (size_t)C * fft_padded(H) * sizeof(float2);
