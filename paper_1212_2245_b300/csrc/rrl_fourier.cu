@@ -182,25 +182,52 @@ __global__ void __launch_bounds__(256, 4) k_fourier_cols(float2* __restrict__ bu
 // exchanges, the pointwise work done on the registers of the last inverse
 // pass, and the column spectrum product between the forward and inverse
 // bottom passes.  C = f8::seqs(L) rows or columns per CTA, thread t C + c.
+//
+// Layout of X and Z when both sides take these passes (PAIRS): column pairs,
+// element (i, k) at float2 index ((k >> 1) H + i) 2 + (k & 1).  A column
+// pass then reads and writes each pair of columns as one contiguous block,
+// and a row pass moves 16 bytes per pair and row, which the CTA's other row
+// completes to a full 32-byte sector.  Otherwise (one side below 64, whose
+// passes are the shared-memory ones above) plain row-major, pitch W.
 // ---------------------------------------------------------------------------
-template <int L, int MODE>
+__host__ __device__ constexpr int tv_pad(int C) { return C >= 32 ? 1 : 32 / C; }
+
+template <int L, int MODE, bool PAIRS>
 __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_rows8(FourierArgs a) {
   constexpr int C = f8::seqs(L), N = 1 << L, T = N / 8;
+  constexpr int P = N + tv_pad(C);  // staged u rows (FR_FIN): conflict-free row pitch
   extern __shared__ float2 smem[];
   const int q = threadIdx.x % C, t = threadIdx.x / C;
-  const int i = blockIdx.x * C + q;
+  const int i0 = blockIdx.x * C, i = i0 + q;
   const bool ok = i < a.H;
   const int ic = ok ? i : a.H - 1;  // rows past the image load the last row and store nothing
+  // float2 offset of elements (ic, 8t + 2u), (ic, 8t + 2u + 1): u_off(u)
+  const size_t rbase = PAIRS ? ((size_t)(4 * t) * a.H + ic) * 2 : (size_t)ic * N + 8 * t;
+  const size_t ustep = PAIRS ? (size_t)2 * a.H : 2;
+  float* ust = (float*)(smem + C * f8::padded(N));  // FR_FIN: rows i0-2 .. i0+C+1 of u
   float2 v[8];
+  if (MODE == FR_FIN) {
+    const bool al = (a.ldin % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.uin) & 15) == 0);
+    for (int rr = 0; rr < C + 4; ++rr) {
+      const int gi = min(max(i0 - 2 + rr, 0), a.H - 1);
+      const float* src = a.uin + (size_t)gi * a.ldin;
+      float* dst = ust + rr * P;
+      if (al && P % 4 == 0) {
+        for (int c = 4 * threadIdx.x; c < N; c += 4 * blockDim.x) cp_async16(dst + c, src + c);
+      } else {
+        for (int c = threadIdx.x; c < N; c += blockDim.x) cp_async4(dst + c, src + c);
+      }
+    }
+  }
   if (MODE == FR_U) {
     const float* ur = a.uin + (size_t)ic * a.ldin;
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = make_float2(ur[t + T * r], 0.f);
   } else {
-    const float4* src = (const float4*)((MODE == FR_MID ? a.X : a.Z) + (size_t)ic * N + 8 * t);
+    const float2* src = (MODE == FR_MID ? a.X : a.Z) + rbase;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float4 x = src[u];
+      const float4 x = *(const float4*)(src + u * ustep);
       v[2 * u] = make_float2(x.x, x.y);
       v[2 * u + 1] = make_float2(x.z, x.w);
     }
@@ -217,11 +244,15 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_row
         v[r] = make_float2(__fdividef(w * (fv - b), b), w);
       }
     } else {
-      const float* m0 = a.uin + (size_t)ic * a.ldin;
-      const float* n1 = a.uin + (size_t)max(ic - 1, 0) * a.ldin;
-      const float* n2 = a.uin + (size_t)max(ic - 2, 0) * a.ldin;
-      const float* s1 = a.uin + (size_t)min(ic + 1, a.H - 1) * a.ldin;
-      const float* s2 = a.uin + (size_t)min(ic + 2, a.H - 1) * a.ldin;
+      cp_async_wait_all();
+      __syncthreads();
+      // rows ic-2 .. ic+2 of u: staged row rr holds image row
+      // clamp(i0 - 2 + rr), so the edge rows repeat by themselves
+      const float* m0 = ust + (ic - i0 + 2) * P;
+      const float* n2 = m0 - 2 * P;
+      const float* n1 = m0 - P;
+      const float* s1 = m0 + P;
+      const float* s2 = m0 + 2 * P;
       float* out = a.uout + (size_t)ic * a.ldout;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
@@ -249,16 +280,19 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_row
       if (!a.write_next) return;  // the same for every thread of the launch
     }
   }
-  f8::dif_chain<L, L - 1, C>(v, smem, t, q, a.twW);
+  int t2 = t;
+  asm volatile("" : "+r"(t2));  // recompute the per-pass indices (keeps them out of the registers above)
+  f8::dif_chain<L, L - 1, C>(v, smem, t2, q, a.twW);
   if (!ok) return;
-  float4* dst = (float4*)((MODE == FR_MID ? a.Z : a.X) + (size_t)i * N + 8 * t);
+  float2* dst = (MODE == FR_MID ? a.Z : a.X) + rbase;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[2 * u].x, v[2 * u].y, v[2 * u + 1].x, v[2 * u + 1].y);
+  for (int u = 0; u < 4; ++u)
+    *(float4*)(dst + u * ustep) = make_float4(v[2 * u].x, v[2 * u].y, v[2 * u + 1].x, v[2 * u + 1].y);
 }
 
 // C = f8::seqs(L) columns of length H = 2^L per CTA: DIF, x S (or conj S)
 // on the bottom pass's registers, DIT, in place.
-template <int L, bool CONJ>
+template <int L, bool CONJ, bool PAIRS>
 __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2)
     k_fourier_cols8(float2* __restrict__ buf, const float2* __restrict__ S, const float2* __restrict__ twH, int W) {
   constexpr int C = f8::seqs(L), H = 1 << L, T = H / 8;
@@ -267,13 +301,13 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2)
   const int col = blockIdx.x * C + c;
   const bool ok = col < W;
   const int cc = ok ? col : W - 1;
-  // element (k, col) at buf[k W + col]; 32-bit offsets (H W <= 2^24), so
-  // that no 64-bit address has to live across the transforms
-  int off = t * W + cc;
-  const int step = T * W;
+  // element (k, cc) at off + k kstep; 32-bit offsets (H W <= 2^24), so that
+  // no 64-bit address has to live across the transforms
+  int off = PAIRS ? (cc >> 1) * 2 * H + 2 * t + (cc & 1) : t * W + cc;
+  const int kstep = PAIRS ? 2 * T : T * W;
   float2 v[8];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = buf[off + r * step];
+  for (int r = 0; r < 8; ++r) v[r] = buf[off + r * kstep];
   f8::dif_chain<L, L - 1, C>(v, smem, t, c, twH);
   const float4* s4 = (const float4*)(S + (size_t)cc * H + 8 * t);
 #pragma unroll
@@ -283,11 +317,13 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2)
     v[2 * u] = CONJ ? cmulc(v[2 * u], s0) : cmul(v[2 * u], s0);
     v[2 * u + 1] = CONJ ? cmulc(v[2 * u + 1], s1) : cmul(v[2 * u + 1], s1);
   }
-  f8::dit_chain<L, f8::bottom_hb(L), C>(v, smem, t, c, twH);
+  int t2 = t;
+  asm volatile("" : "+r"(t2));  // recompute the per-pass indices (keeps them out of the registers above)
+  f8::dit_chain<L, f8::bottom_hb(L), C>(v, smem, t2, c, twH);
   if (!ok) return;
   asm volatile("" : "+r"(off));  // recompute the addresses rather than keep the loads' ones live
 #pragma unroll
-  for (int r = 0; r < 8; ++r) buf[off + r * step] = v[r];
+  for (int r = 0; r < 8; ++r) buf[off + r * kstep] = v[r];
 }
 
 template <typename K>
@@ -297,38 +333,52 @@ static cudaError_t set_smem_f(K kern, size_t smem) {
   return cudaSuccess;
 }
 
-template <int L, int MODE>
+template <int L, int MODE, bool PAIRS>
 static cudaError_t launch_frow8(const FourierArgs& a, cudaStream_t s) {
-  constexpr int C = f8::seqs(L);
-  const size_t smem = (size_t)C * f8::padded(1 << L) * sizeof(float2);
-  cudaError_t e = set_smem_f(k_fourier_rows8<L, MODE>, smem);
+  constexpr int C = f8::seqs(L), N = 1 << L;
+  size_t smem = (size_t)C * f8::padded(N) * sizeof(float2);
+  if (MODE == FR_FIN) smem += (size_t)(C + 4) * (N + tv_pad(C)) * sizeof(float);
+  cudaError_t e = set_smem_f(k_fourier_rows8<L, MODE, PAIRS>, smem);
   if (e != cudaSuccess) return e;
-  k_fourier_rows8<L, MODE><<<(a.H + C - 1) / C, f8::threads(L), smem, s>>>(a);
+  k_fourier_rows8<L, MODE, PAIRS><<<(a.H + C - 1) / C, f8::threads(L), smem, s>>>(a);
   count_launch();
   return cudaGetLastError();
 }
 
-template <int L, bool CONJ>
+template <int L, bool CONJ, bool PAIRS>
 static cudaError_t launch_fcol8(float2* buf, const float2* S, const float2* twH, int W, cudaStream_t s) {
   constexpr int C = f8::seqs(L);
   const size_t smem = (size_t)C * f8::padded(1 << L) * sizeof(float2);
-  cudaError_t e = set_smem_f(k_fourier_cols8<L, CONJ>, smem);
+  cudaError_t e = set_smem_f(k_fourier_cols8<L, CONJ, PAIRS>, smem);
   if (e != cudaSuccess) return e;
-  k_fourier_cols8<L, CONJ><<<(W + C - 1) / C, f8::threads(L), smem, s>>>(buf, S, twH, W);
+  k_fourier_cols8<L, CONJ, PAIRS><<<(W + C - 1) / C, f8::threads(L), smem, s>>>(buf, S, twH, W);
   count_launch();
   return cudaGetLastError();
+}
+
+// both sides take the register-resident passes: X and Z in column pairs
+static bool fourier_pairs(int H, int W) { return ilog2(H) >= 6 && ilog2(W) >= 6; }
+
+template <int L, int MODE>
+static cudaError_t launch_frow8p(const FourierArgs& a, cudaStream_t s) {
+  return fourier_pairs(a.H, a.W) ? launch_frow8<L, MODE, true>(a, s) : launch_frow8<L, MODE, false>(a, s);
+}
+template <int L, bool CONJ>
+static cudaError_t launch_fcol8p(float2* buf, const float2* S, const float2* twH, int H, int W, cudaStream_t s) {
+  return fourier_pairs(H, W) ? launch_fcol8<L, CONJ, true>(buf, S, twH, W, s)
+                             : launch_fcol8<L, CONJ, false>(buf, S, twH, W, s);
 }
 
 template <int MODE>
 static cudaError_t launch_frow(const FourierArgs& a, cudaStream_t s) {
   switch (a.logW) {
-    case 6: return launch_frow8<6, MODE>(a, s);
-    case 7: return launch_frow8<7, MODE>(a, s);
-    case 8: return launch_frow8<8, MODE>(a, s);
-    case 9: return launch_frow8<9, MODE>(a, s);
-    case 10: return launch_frow8<10, MODE>(a, s);
-    case 11: return launch_frow8<11, MODE>(a, s);
-    case 12: return launch_frow8<12, MODE>(a, s);
+    case 6: return launch_frow8p<6, MODE>(a, s);
+    case 7: return launch_frow8p<7, MODE>(a, s);
+    case 8: return launch_frow8p<8, MODE>(a, s);
+    case 9: return launch_frow8p<9, MODE>(a, s);
+    case 10: return launch_frow8p<10, MODE>(a, s);
+    case 11: return launch_frow8p<11, MODE>(a, s);
+    case 12: return launch_frow8p<12, MODE>(a, s);
     default: break;
   }
   const size_t smem = (size_t)fft_padded(a.W) * sizeof(float2) + (size_t)(MODE == FR_FIN ? 5 : 1) * a.W * sizeof(float);
@@ -343,13 +393,13 @@ template <bool CONJ>
 static cudaError_t launch_fcol(float2* buf, const float2* S, const float2* twH, int H, int W, cudaStream_t s) {
   const int logH = ilog2(H);
   switch (logH) {
-    case 6: return launch_fcol8<6, CONJ>(buf, S, twH, W, s);
-    case 7: return launch_fcol8<7, CONJ>(buf, S, twH, W, s);
-    case 8: return launch_fcol8<8, CONJ>(buf, S, twH, W, s);
-    case 9: return launch_fcol8<9, CONJ>(buf, S, twH, W, s);
-    case 10: return launch_fcol8<10, CONJ>(buf, S, twH, W, s);
-    case 11: return launch_fcol8<11, CONJ>(buf, S, twH, W, s);
-    case 12: return launch_fcol8<12, CONJ>(buf, S, twH, W, s);
+    case 6: return launch_fcol8p<6, CONJ>(buf, S, twH, H, W, s);
+    case 7: return launch_fcol8p<7, CONJ>(buf, S, twH, H, W, s);
+    case 8: return launch_fcol8p<8, CONJ>(buf, S, twH, H, W, s);
+    case 9: return launch_fcol8p<9, CONJ>(buf, S, twH, H, W, s);
+    case 10: return launch_fcol8p<10, CONJ>(buf, S, twH, H, W, s);
+    case 11: return launch_fcol8p<11, CONJ>(buf, S, twH, H, W, s);
+    case 12: return launch_fcol8p<12, CONJ>(buf, S, twH, H, W, s);
     default: break;
   }
   if (H <= 1024) {
