@@ -192,8 +192,10 @@ __global__ void __launch_bounds__(256, 4) k_fourier_cols(float2* __restrict__ bu
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int tv_pad(int C) { return C >= 32 ? 1 : 32 / C; }
 
+// FR_U and FR_FIN (FR_MID runs in k_fourier_mid8 below)
 template <int L, int MODE, bool PAIRS>
 __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_rows8(FourierArgs a) {
+  static_assert(MODE != FR_MID, "FR_MID runs in k_fourier_mid8");
   constexpr int C = f8::seqs(L), N = 1 << L, T = N / 8;
   constexpr int P = N + tv_pad(C);  // staged u rows (FR_FIN): conflict-free row pitch
   extern __shared__ float2 smem[];
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_row
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = make_float2(ur[t + T * r], 0.f);
   } else {
-    const float2* src = (MODE == FR_MID ? a.X : a.Z) + rbase;
+    const float2* src = a.Z + rbase;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const float4 x = *(const float4*)(src + u * ustep);
@@ -234,16 +236,7 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_row
     f8::dit_chain<L, f8::bottom_hb(L), C>(v, smem, t, q, a.twW);
     // v[r]: element t + T r, natural order
     const RrlParams& p = a.p;
-    if (MODE == FR_MID) {
-      const float* fr = a.f + (size_t)ic * a.ldf;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const float b = v[r].x * a.scale;
-        const float fv = fmaxf(fr[t + T * r], p.floor);
-        const float w = robust_weight_f(b, fv, p);
-        v[r] = make_float2(__fdividef(w * (fv - b), b), w);
-      }
-    } else {
+    {
       cp_async_wait_all();
       __syncthreads();
       // rows ic-2 .. ic+2 of u: staged row rr holds image row
@@ -284,10 +277,70 @@ __global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_row
   asm volatile("" : "+r"(t2));  // recompute the per-pass indices (keeps them out of the registers above)
   f8::dif_chain<L, L - 1, C>(v, smem, t2, q, a.twW);
   if (!ok) return;
-  float2* dst = (MODE == FR_MID ? a.Z : a.X) + rbase;
+  float2* dst = a.X + rbase;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     *(float4*)(dst + u * ustep) = make_float4(v[2 * u].x, v[2 * u].y, v[2 * u + 1].x, v[2 * u + 1].y);
+}
+
+// FR_MID as a persistent kernel: CTA b takes row blocks b, b + gridDim.x, ...
+// While a block is transformed, the next block's row spectra and rows of f
+// are copied into shared memory, each thread copying exactly the elements
+// it will read itself (so no barrier guards the buffer).
+template <int L, bool PAIRS>
+__global__ void __launch_bounds__(f8::threads(L), L >= 12 ? 1 : 2) k_fourier_mid8(FourierArgs a) {
+  constexpr int C = f8::seqs(L), N = 1 << L, T = N / 8, NT = f8::threads(L);
+  extern __shared__ float2 smem[];
+  float4* pfx = (float4*)(smem + C * f8::padded(N));  // [4][NT]: the thread's 8 spectrum elements
+  float* pff = (float*)(pfx + 4 * NT);                 // [8][NT]: the thread's 8 values of f
+  const int tid = threadIdx.x, q = tid % C, t = tid / C;
+  const int nrb = (a.H + C - 1) / C;
+  const size_t ustep = PAIRS ? (size_t)2 * a.H : 2;
+  // float2 offset of elements (ic, 8t), (ic, 8t + 1); + u ustep for 8t + 2u
+  auto rowbase = [&](int ic) -> size_t {
+    return PAIRS ? ((size_t)(4 * t) * a.H + ic) * 2 : (size_t)ic * N + 8 * t;
+  };
+  auto prefetch = [&](int rb) {
+    const int ic = min(rb * C + q, a.H - 1);
+    const float2* src = a.X + rowbase(ic);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cp_async16(pfx + u * NT + tid, src + u * ustep);
+    const float* fr = a.f + (size_t)ic * a.ldf;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) cp_async4(pff + r * NT + tid, fr + t + T * r);
+  };
+  int rb = blockIdx.x;
+  if (rb < nrb) prefetch(rb);
+  const RrlParams& p = a.p;
+  for (; rb < nrb; rb += gridDim.x) {
+    const int i = rb * C + q;
+    cp_async_wait_all();
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 x = pfx[u * NT + tid];
+      v[2 * u] = make_float2(x.x, x.y);
+      v[2 * u + 1] = make_float2(x.z, x.w);
+    }
+    f8::dit_chain<L, f8::bottom_hb(L), C>(v, smem, t, q, a.twW);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const float b = v[r].x * a.scale;
+      const float fv = fmaxf(pff[r * NT + tid], p.floor);
+      const float w = robust_weight_f(b, fv, p);
+      v[r] = make_float2(__fdividef(w * (fv - b), b), w);
+    }
+    if (rb + (int)gridDim.x < nrb) prefetch(rb + gridDim.x);
+    int t2 = t;
+    asm volatile("" : "+r"(t2));  // recompute the per-pass indices
+    f8::dif_chain<L, L - 1, C>(v, smem, t2, q, a.twW);
+    if (i < a.H) {
+      float2* dst = a.Z + rowbase(i);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        *(float4*)(dst + u * ustep) = make_float4(v[2 * u].x, v[2 * u].y, v[2 * u + 1].x, v[2 * u + 1].y);
+    }
+  }
 }
 
 // C = f8::seqs(L) columns of length H = 2^L per CTA: DIF, x S (or conj S)
@@ -345,6 +398,37 @@ static cudaError_t launch_frow8(const FourierArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// grid of a persistent kernel: as many CTAs as fit on the device at once
+// (at most `items`); the occupancy query is made once per kernel
+template <typename K>
+static cudaError_t persistent_grid(K kern, int threads, size_t smem, int items, int* cache, int* grid) {
+  if (*cache == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess)
+      return e;
+    *cache = max(1, sms * per_sm);
+  }
+  *grid = min(items, *cache);
+  return cudaSuccess;
+}
+
+template <int L, bool PAIRS>
+static cudaError_t launch_fmid8(const FourierArgs& a, cudaStream_t s) {
+  constexpr int C = f8::seqs(L), N = 1 << L, NT = f8::threads(L);
+  const size_t smem = (size_t)C * f8::padded(N) * sizeof(float2) + (size_t)NT * (4 * sizeof(float4) + 8 * sizeof(float));
+  static int cache = 0;
+  cudaError_t e = set_smem_f(k_fourier_mid8<L, PAIRS>, smem);
+  int grid = 0;
+  if (e == cudaSuccess) e = persistent_grid(k_fourier_mid8<L, PAIRS>, NT, smem, (a.H + C - 1) / C, &cache, &grid);
+  if (e != cudaSuccess) return e;
+  k_fourier_mid8<L, PAIRS><<<grid, NT, smem, s>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int L, bool CONJ, bool PAIRS>
 static cudaError_t launch_fcol8(float2* buf, const float2* S, const float2* twH, int W, cudaStream_t s) {
   constexpr int C = f8::seqs(L);
@@ -361,7 +445,10 @@ static bool fourier_pairs(int H, int W) { return ilog2(H) >= 6 && ilog2(W) >= 6;
 
 template <int L, int MODE>
 static cudaError_t launch_frow8p(const FourierArgs& a, cudaStream_t s) {
-  return fourier_pairs(a.H, a.W) ? launch_frow8<L, MODE, true>(a, s) : launch_frow8<L, MODE, false>(a, s);
+  if constexpr (MODE == FR_MID)
+    return fourier_pairs(a.H, a.W) ? launch_fmid8<L, true>(a, s) : launch_fmid8<L, false>(a, s);
+  else
+    return fourier_pairs(a.H, a.W) ? launch_frow8<L, MODE, true>(a, s) : launch_frow8<L, MODE, false>(a, s);
 }
 template <int L, bool CONJ>
 static cudaError_t launch_fcol8p(float2* buf, const float2* S, const float2* twH, int H, int W, cudaStream_t s) {
