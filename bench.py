@@ -62,11 +62,12 @@ def parse():
     ap.add_argument("--images", type=int, default=512,
                     help="batch512 only: deblur an evenly spaced subset of this many of the 512 images "
                          "(a smaller case of the same kernels, for profiling)")
-    ap.add_argument("--forms", choices=["auto"] + [f"{d}/{w}" for d in ("dense", "groups")
+    ap.add_argument("--forms", choices=["auto"] + [f"{t}{d}/{w}" for t in ("", "nofft/") for d in ("dense", "groups")
                                                     for w in ("all", "rule", "none")], default="auto",
                     help="batch512 only: tile forms timed (auto: chosen by db_batch_autotune before capture) "
-                         "or fixed as <2D sums>/<one-axis register windows>, e.g. dense/all (for profiling: "
-                         "the autotuner's own runs are then not launched)")
+                         "or fixed as [nofft/]<2D sums>/<one-axis register windows>, e.g. dense/all (FFT tiles "
+                         "by their size rule; nofft/: none) (for profiling: the autotuner's own runs are then "
+                         "not launched)")
     ap.add_argument("--rf", choices=["log1p", "lut"], default="log1p",
                     help="evaluation of r_f: log1p (default) or the lookup table of Sec. 4.1")
     return ap.parse_args()
@@ -487,8 +488,9 @@ def run_batch(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     fixed = None
     if args.forms != "auto":
-        d, w = args.forms.split("/")
-        fixed = {"dense": d == "dense", "windows": w}
+        parts = args.forms.split("/")
+        d, w = parts[-2:]
+        fixed = {"fft": parts[0] != "nofft", "dense": d == "dense", "windows": w}
         set_batch_forms(fixed)
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
@@ -605,13 +607,15 @@ def run_batch(args, world, rank, local):
 
 def set_batch_forms(forms):
     """Process-wide settings under which a batch plan takes the given tile
-    forms ({"dense": bool, "windows": "all" | "rule" | "none"}; None: the
-    defaults)."""
+    forms ({"fft": bool, "dense": bool, "windows": "all" | "rule" | "none"};
+    None: the defaults)."""
     import paper_1212_2245_b300 as db
     if forms is None:
+        db.set_fft_tiles(0)
         db.set_dense_min(0)
         db.set_one_axis_min(0)
         return
+    db.set_fft_tiles(0 if forms.get("fft", True) else 2305)
     db.set_dense_min(50 if forms["dense"] else 101)
     db.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[forms["windows"]])
 

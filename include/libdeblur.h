@@ -208,22 +208,24 @@ void db_batch_destroy(db_batch* b);
 
 /* Choose the batch's tile forms by measurement (the batched counterpart of
  * db_plan_autotune): runs the whole batch `reps` times after one warm-up per
- * candidate, timed with CUDA events on `stream`, for the dense sums on and
- * off (images with dense-eligible 2D PSFs, odd sides 3..25) crossed with the
- * forms of non-box one-axis PSFs (the size rule of db_set_one_axis_min's
- * default, register windows for all, tap groups for all), and keeps the
- * fastest combination for every later db_batch_run.  Classes absent from
- * the batch are not tried.  The runs overwrite the images' outputs;
- * synchronises `stream` (call it before capturing the run in a graph; a
- * graph captured earlier keeps working and picks up the choice).
- * *dense_out (nullable) receives 1 when the dense sums were chosen,
- * *windows_out (nullable) 2 for the size rule, 1 for register windows, 0
- * for tap groups.  The result of each image equals db_deblur's under the
- * corresponding process-wide settings (db_set_dense_min 50 or 101;
- * db_set_one_axis_min 0, 1 or 256).  DB_ERR_ARG for a null batch or
- * reps < 1. */
+ * candidate, timed with CUDA events on `stream`, for the FFT tiles by the
+ * size rule of db_set_fft_tiles or none (2D PSFs), crossed with the dense
+ * sums on and off (images with dense-eligible 2D PSFs, odd sides 3..25) and
+ * with the forms of non-box one-axis PSFs (the size rule of
+ * db_set_one_axis_min's default, register windows for all, tap groups for
+ * all), and keeps the fastest combination for every later db_batch_run.
+ * Classes absent from the batch are not tried.  The runs overwrite the
+ * images' outputs; synchronises `stream` (call it before capturing the run
+ * in a graph; a graph captured earlier keeps working and picks up the
+ * choice).  *dense_out (nullable) receives 1 when the dense sums were
+ * chosen, *windows_out (nullable) 2 for the size rule, 1 for register
+ * windows, 0 for tap groups, *fft_out (nullable) 1 for the FFT tiles.  The
+ * result of each image equals db_deblur's under the corresponding
+ * process-wide settings (db_set_fft_tiles at its value or 2305;
+ * db_set_dense_min 50 or 101; db_set_one_axis_min 0, 1 or 256).
+ * DB_ERR_ARG for a null batch or reps < 1. */
 db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream, int* dense_out,
-                            int* windows_out);
+                            int* windows_out, int* fft_out);
 
 /* db_batch_create + db_batch_run + db_batch_destroy. */
 db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws, size_t ws_bytes,
@@ -432,6 +434,19 @@ db_status db_set_one_axis_min(int min_len);
  * 0 restores the default of 50.  The two forms differ by FP32 rounding
  * only.  DB_ERR_ARG for other values. */
 db_status db_set_dense_min(int percent);
+
+/* FFT tiles for 2D PSFs (sides 2..48; Sec. 4.2 "Fourier transform": the
+ * blur and both correlations as pointwise products of spectra).  The split
+ * schedule (and a batch image) computes them on 64 x 64 windows of u and q
+ * taken with constant continuation, keeping the (65 - kh) x (65 - kw)
+ * outputs whose PSF footprint lies inside the window, so the result is the
+ * same constant-continuation iteration as the direct sums, up to FP32
+ * rounding (FP32 transforms).  Used for a PSF with kh * kw >= min_taps;
+ * the flow schedule falls back to split for such PSFs.  Process-wide;
+ * min_taps >= 1 (above 2304: never), 0 restores the default of 289.  Applies
+ * to runs started, and batches created, after the call.  DB_ERR_ARG for
+ * negative values. */
+db_status db_set_fft_tiles(int min_taps);
 
 /* Evaluation of the information divergence r_f in the robust weight
  * (process-wide setting, all devices):

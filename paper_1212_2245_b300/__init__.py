@@ -391,17 +391,21 @@ class Batch:
         return self.us
 
     def autotune(self, reps: int = 3):
-        """Choose the tile forms by timing whole runs (db_batch_autotune): the
-        dense sums on or off for dense-eligible 2D PSFs, register windows or
-        tap groups for non-box one-axis PSFs.  Overwrites the outputs and
-        synchronises the current stream.  Returns {"dense": bool, "windows": w} with w = "rule"
-        (the size rule of set_one_axis_min(0)), "all" (register windows) or "none" (tap groups)."""
-        d, w = ctypes.c_int(), ctypes.c_int()
+        """Choose the tile forms by timing whole runs (db_batch_autotune): FFT
+        tiles by the size rule of set_fft_tiles or none for 2D PSFs, the dense
+        sums on or off for dense-eligible 2D PSFs, register windows or tap
+        groups for non-box one-axis PSFs.  Overwrites the outputs and
+        synchronises the current stream.  Returns {"fft": bool, "dense": bool,
+        "windows": w} with w = "rule" (the size rule of set_one_axis_min(0)),
+        "all" (register windows) or "none" (tap groups)."""
+        d, w, ft = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self.ws.reset_status()
         _check(_lib.load().db_batch_autotune(self._h, int(reps), self.ws.status.data_ptr(), _stream(),
-                                             ctypes.byref(d), ctypes.byref(w)), "db_batch_autotune")
+                                             ctypes.byref(d), ctypes.byref(w), ctypes.byref(ft)),
+               "db_batch_autotune")
         self.ws.raise_on_flags("db_batch_autotune")
-        return {"dense": bool(d.value), "windows": {0: "none", 1: "all", 2: "rule"}[w.value]}
+        return {"fft": bool(ft.value), "dense": bool(d.value),
+                "windows": {0: "none", 1: "all", 2: "rule"}[w.value]}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -538,6 +542,13 @@ def set_dense_min(percent: int = 0):
     (odd sides 3..25) is summed densely; 101 = never, 0 = the default (50).
     Process-wide; applies to taps prepared after the call."""
     _check(_lib.load().db_set_dense_min(int(percent)), "db_set_dense_min")
+
+
+def set_fft_tiles(min_taps: int = 0):
+    """Smallest kh * kw for which a 2D PSF (sides 2..48) runs the split
+    schedule's blur and correlations as 64 x 64 FFT tiles; 2305 = never,
+    0 = the default (289).  Process-wide; applies to later runs and batches."""
+    _check(_lib.load().db_set_fft_tiles(int(min_taps)), "db_set_fft_tiles")
 
 
 def set_rf_eval(name: str):

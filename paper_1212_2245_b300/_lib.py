@@ -54,7 +54,8 @@ SIGNATURES = {
                                 c_void_p, ctypes.POINTER(c_void_p)]),
     "db_batch_run": (c_int, [c_void_p, c_void_p, c_void_p]),
     "db_batch_destroy": (None, [c_void_p]),
-    "db_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "db_batch_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                  ctypes.POINTER(c_int)]),
     "db_deblur_batch": (c_int, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_void_p, c_size_t, c_void_p,
                                 c_void_p]),
     "db_batch_stream_workspace_bytes": (c_size_t, [ctypes.POINTER(DbImageDesc), c_int, c_int, c_int]),
@@ -84,6 +85,7 @@ SIGNATURES = {
     "db_set_schedule": (c_int, [c_int]),
     "db_set_one_axis_min": (c_int, [c_int]),
     "db_set_dense_min": (c_int, [c_int]),
+    "db_set_fft_tiles": (c_int, [c_int]),
     "db_set_rf_eval": (c_int, [c_int]),
 }
 

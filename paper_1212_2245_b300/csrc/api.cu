@@ -18,6 +18,8 @@ unsigned settings_gen() { return g_settings_gen.load(); }
 static std::atomic<int> g_one_axis_min{0};
 static std::atomic<int> g_dense_min_pct{50};
 int dense_min_pct() { return g_dense_min_pct.load(std::memory_order_relaxed); }
+static std::atomic<int> g_fft_tile_min{kFftTileMinDefault};
+int fft_tile_min() { return g_fft_tile_min.load(std::memory_order_relaxed); }
 int one_axis_min(bool row) {
   const int v = g_one_axis_min.load(std::memory_order_relaxed);
   return v > 0 ? v : row ? 16 : 32;
@@ -126,7 +128,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   if (sched == DB_SCHED_CLUSTER && kh == 1 && axis == 0) axis = 2;
   if (sched == DB_SCHED_CLUSTER && (ckpt || !cluster_fits(H, W, kh, kw, axis))) sched = DB_SCHED_SPLIT;
   // dense-eligible 2D PSFs run the split pair with the dense tile bodies
-  if ((sched == DB_SCHED_FLOW && (ckpt || (axis == 0 && dense_eligible(kh, kw)))) ||
+  if ((sched == DB_SCHED_FLOW && (ckpt || (axis == 0 && (dense_eligible(kh, kw) || fft_tile_form(kh, kw))))) ||
       (sched == DB_SCHED_FUSED && axis == 1))
     sched = DB_SCHED_SPLIT;
   if (sched == DB_SCHED_FUSED) axis = 0;
@@ -627,6 +629,13 @@ db_status db_set_one_axis_min(int min_len) {
 db_status db_set_dense_min(int percent) {
   if (percent < 0 || percent > 101) return DB_ERR_ARG;
   g_dense_min_pct.store(percent == 0 ? 50 : percent);
+  bump_settings();
+  return DB_OK;
+}
+
+db_status db_set_fft_tiles(int min_taps) {
+  if (min_taps < 0) return DB_ERR_ARG;
+  g_fft_tile_min.store(min_taps == 0 ? kFftTileMinDefault : min_taps);
   bump_settings();
   return DB_OK;
 }

@@ -25,6 +25,7 @@
 #include "internal.cuh"
 #include "rrl_box.cuh"
 #include "rrl_dense.cuh"
+#include "rrl_fft_tile.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -41,6 +42,7 @@ struct BatchImg {
   int box;       // 0: tap groups; 1, 2: horizontal, vertical box (sliding-window sums);
                  // 3, 4: other horizontal, vertical one-axis PSF (register windows)
   int kwd;       // dense-eligible 2D PSF: kw (the dense flag then picks the bodies); else 0
+  int fft;       // 1: FFT tiles (rrl_fft_tile.cuh); the tile tables then hold that grid
   RrlParams p;
 };
 
@@ -129,6 +131,19 @@ __device__ __noinline__ void batch_dense(int phase, unsigned char* smem, const B
                                       i0, j0);
 }
 
+// FFT tiles: a q-phase record holds the left tile of a horizontal pair.
+__device__ __noinline__ void batch_fft(int phase, unsigned char* smem, const BatchImg& im, const float* src, int lds,
+                                       float* dst, int ldd, int* status, int i0, int j0) {
+  const int ldp = upitch(im.W);
+  float* qe = reinterpret_cast<float*>(im.q);
+  float* qw = qe + (size_t)im.H * ldp;
+  const float2* spec = fft_tile_spec(im.groups, im.kh, im.kw);
+  if (phase == 0)
+    ftile::q_tile(smem, im.f, im.ldf, src, lds, qe, qw, ldp, im.H, im.W, spec, im.kh, im.kw, im.p, i0, j0);
+  else
+    ftile::update_tile(smem, qe, qw, ldp, src, lds, dst, ldd, im.H, im.W, spec, im.kh, im.kw, im.p, status, i0, j0);
+}
+
 __device__ __forceinline__ void batch_tile(int phase, unsigned char* smem, const BatchImg& im, const float* src,
                                            int lds, float* dst, int ldd, int* status, int i0, int j0) {
   if (im.kwd && __ldg(dense_flag(im.ngroups))) {
@@ -195,21 +210,26 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long 
   return ok != 0;
 }
 
+// tiles_q / tiles_u: the tile tables of the q and update phases (they
+// differ for images with FFT tiles, whose q tiles go in pairs).
 __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict__ imgs,
-                                                   const int4* __restrict__ tiles, int ntiles, int iters,
+                                                   const int4* __restrict__ tiles_q, int ntiles_q,
+                                                   const int4* __restrict__ tiles_u, int ntiles_u, int iters,
                                                    unsigned* bar, int* work, int* status,
                                                    long long spin_limit) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if (tid == 0) {
-    g_queue.imgs = imgs;
-    g_queue.tiles = tiles;
-    g_queue.ntiles = ntiles;
-  }
+  if (tid == 0) g_queue.imgs = imgs;
   for (int k = 0; k < iters; ++k) {
     const bool even = (k & 1) == 0;
     for (int phase = 0; phase < 2; ++phase) {
       int* queue = work + 2 * k + phase;
+      const int4* tiles = phase == 0 ? tiles_q : tiles_u;
+      const int ntiles = phase == 0 ? ntiles_q : ntiles_u;
+      if (tid == 0) {
+        g_queue.tiles = tiles;
+        g_queue.ntiles = ntiles;
+      }
       // the phase's first tile, then each tile prefetches the next one
       if (tid < 32) {
         int t = 0;
@@ -227,7 +247,8 @@ __global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict
         const int lds = even ? im.ldA : im.ldB;
         float* dst = even ? im.B : im.A;
         const int ldd = even ? im.ldB : im.ldA;
-        if (im.box == 1) batch_box<true, true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        if (im.fft) batch_fft(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
+        else if (im.box == 1) batch_box<true, true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else if (im.box == 2) batch_box<false, true>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else if (im.box == 3) batch_box<true, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
         else if (im.box == 4) batch_box<false, false>(phase, smem, im, src, lds, dst, ldd, status, T.y, T.z);
@@ -271,9 +292,10 @@ struct BatchPlan {
   int n = 0, iters = 0;
   WienerBatch* wb = nullptr;
   std::vector<BatchImg> imgs;
-  std::vector<int4> tiles;
+  std::vector<int4> tiles_q, tiles_u;
   BatchImg* d_imgs = nullptr;
-  int4* d_tiles = nullptr;
+  int4* d_tiles_q = nullptr;
+  int4* d_tiles_u = nullptr;
   unsigned* d_bar = nullptr;
   int* d_work = nullptr;
   size_t smem = 0;
@@ -282,6 +304,9 @@ struct BatchPlan {
   // dense-eligible 2D PSF (else 0), the register-window code of a non-box
   // one-axis PSF (3 row, 4 column; else 0) and the code the size rule chose
   std::vector<int> dense_kw, window_box, rule_box;
+  // per image: FFT tiles possible (a 2D PSF of fft_tile_shape), and chosen by
+  // the size rule (fft_tile_form)
+  std::vector<int> fft_ok, fft_rule;
   ~BatchPlan() { if (wb) wiener_batch_delete(wb); }
 };
 
@@ -305,6 +330,56 @@ static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
 
 static size_t count_tiles(int H, int W) {
   return (size_t)((H + kBTH - 1) / kBTH) * ((W + kBTW - 1) / kBTW);
+}
+// Capacity of one tile table for an image: either grid may be chosen later
+// (db_batch_autotune).
+static size_t count_tiles_max(int H, int W, int kh, int kw) {
+  size_t n = count_tiles(H, W);
+  if (fft_tile_shape(kh, kw) && kh > 1 && kw > 1) {
+    const size_t f = (size_t)((H + ftile::tile_oh(kh) - 1) / ftile::tile_oh(kh)) *
+                     ((W + ftile::tile_ow(kw) - 1) / ftile::tile_ow(kw));
+    n = std::max(n, f);
+  }
+  return n;
+}
+
+// Tile tables from the images' current forms: the split grid (kBTH x kBTW)
+// in both phases, or for FFT tiles the (65-kh) x (65-kw) grid, whose q-phase
+// tiles go in horizontal pairs.  Expensive tiles first (the work queue then
+// ends on cheap ones); .w is a cost estimate (tap-group bound, or
+// kFftTileCost for an FFT tile: about the time of a 25 x 25 dense tile's
+// tap sums over 32 x 64 outputs scaled by 8k / 55k cycles).
+constexpr int kFftTileCost = 48;
+static void build_tiles(BatchPlan* P) {
+  P->tiles_q.clear();
+  P->tiles_u.clear();
+  for (int i = 0; i < P->n; ++i) {
+    const BatchImg& bi = P->imgs[i];
+    if (bi.fft) {
+      const int oh = ftile::tile_oh(bi.kh), ow = ftile::tile_ow(bi.kw);
+      for (int i0 = 0; i0 < bi.H; i0 += oh) {
+        for (int j0 = 0; j0 < bi.W; j0 += ow) P->tiles_u.push_back(make_int4(i, i0, j0, kFftTileCost));
+        for (int j0 = 0; j0 < bi.W; j0 += 2 * ow) P->tiles_q.push_back(make_int4(i, i0, j0, kFftTileCost));
+      }
+    } else {
+      for (int i0 = 0; i0 < bi.H; i0 += kBTH)
+        for (int j0 = 0; j0 < bi.W; j0 += kBTW) {
+          P->tiles_q.push_back(make_int4(i, i0, j0, bi.ng_max));
+          P->tiles_u.push_back(make_int4(i, i0, j0, bi.ng_max));
+        }
+    }
+  }
+  auto by_cost = [](const int4& a, const int4& b) { return a.w > b.w; };
+  std::stable_sort(P->tiles_q.begin(), P->tiles_q.end(), by_cost);
+  std::stable_sort(P->tiles_u.begin(), P->tiles_u.end(), by_cost);
+}
+
+static cudaError_t upload_tiles(const BatchPlan* P, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(P->d_tiles_q, P->tiles_q.data(), P->tiles_q.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(P->d_tiles_u, P->tiles_u.data(), P->tiles_u.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                         s);
 }
 
 // Bytes of workspace the whole batch needs; 0 if any descriptor is invalid.
@@ -335,12 +410,12 @@ size_t batch_ws_bytes(const db_image_desc* d, int n, int iters, db_status* why) 
     off = image_regions(off, x.H, x.W, x.psf.kh, x.psf.kw).end;
     if (x.psf.kw > 1 || x.psf.kh == 1) lens[x.W] = true;
     if (x.psf.kh > 1) lens[x.H] = true;
-    ntiles += count_tiles(x.H, x.W);
+    ntiles += count_tiles_max(x.H, x.W, x.psf.kh, x.psf.kw);
     nitems += (size_t)2 * x.H + x.W;  // upper bound on Wiener work items
   }
   for (auto& kv : lens) off += align256(dft_table_elems(kv.first) * sizeof(float4));
   off += align256((size_t)n * sizeof(BatchImg));
-  off += align256(ntiles * sizeof(int4));
+  off += 2 * align256(ntiles * sizeof(int4));          // q and update tile tables
   off += 256;                                         // barrier
   off += align256((size_t)(2 * iters + 2) * sizeof(int));  // work counters
   // batched-Wiener job tables (5 stages x (jobs + 3 item classes) regions):
@@ -387,6 +462,7 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
   }
   // per image: tap groups, Wiener set-up, RRRL descriptor and tiles
   P->imgs.resize(n);
+  size_t ntiles_cap = 0;
   for (int i = 0; i < n; ++i) {
     const db_image_desc& x = d[i];
     const ImgRegions& r = reg[i];
@@ -421,6 +497,9 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.box = axis == 0 ? 0 : (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
     bi.kwd = (axis == 0 && dense_eligible(kh, kw)) ? kw : 0;
     P->dense_kw.push_back(bi.kwd);
+    P->fft_ok.push_back(axis == 0 && fft_tile_shape(kh, kw) ? 1 : 0);
+    P->fft_rule.push_back(P->fft_ok.back() && fft_tile_form(kh, kw) ? 1 : 0);
+    bi.fft = P->fft_rule.back();
     P->window_box.push_back((x.psf.kind != DB_PSF_BOX && (kh == 1 || kw == 1)) ? (kh == 1 ? 3 : 4) : 0);
     P->rule_box.push_back(bi.box);
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
@@ -438,17 +517,17 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
       sm = std::max(sm, std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),
                                  split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max)));
     }
+    if (P->fft_ok.back()) sm = std::max(sm, ftile::smem_update(kh));
     if (sm > P->smem) P->smem = sm;
-    for (int i0 = 0; i0 < x.H; i0 += kBTH)
-      for (int j0 = 0; j0 < x.W; j0 += kBTW) P->tiles.push_back(make_int4(i, i0, j0, bi.ng_max));
+    ntiles_cap += count_tiles_max(x.H, x.W, kh, kw);
   }
-  // expensive tiles first (the work queue then ends on cheap ones)
-  std::stable_sort(P->tiles.begin(), P->tiles.end(),
-                   [](const int4& a, const int4& b) { return a.w > b.w; });
+  build_tiles(P);
   P->d_imgs = (BatchImg*)(base + off);
   off += align256((size_t)n * sizeof(BatchImg));
-  P->d_tiles = (int4*)(base + off);
-  off += align256(P->tiles.size() * sizeof(int4));
+  P->d_tiles_q = (int4*)(base + off);
+  off += align256(ntiles_cap * sizeof(int4));
+  P->d_tiles_u = (int4*)(base + off);
+  off += align256(ntiles_cap * sizeof(int4));
   P->d_bar = (unsigned*)(base + off);
   off += 256;
   P->d_work = (int*)(base + off);
@@ -458,8 +537,7 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
   if (wiener_batch_upload(P->wb, base + off, s) != cudaSuccess) { delete P; return DB_ERR_CUDA; }
   if (cudaMemcpyAsync(P->d_imgs, P->imgs.data(), (size_t)n * sizeof(BatchImg), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
-      cudaMemcpyAsync(P->d_tiles, P->tiles.data(), P->tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess) {
+      upload_tiles(P, s) != cudaSuccess) {
     delete P; return DB_ERR_CUDA;
   }
   // persistent grid: every co-resident CTA.  The kernel's shared-memory
@@ -500,9 +578,9 @@ db_status batch_run(const BatchPlan* P, int* status, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const long long limit = g_spin_limit.load();
-  const int ntiles = (int)P->tiles.size();
-  if (cudaLaunchKernelEx(&cfg, k_rrl_batch, (const BatchImg*)P->d_imgs, (const int4*)P->d_tiles, ntiles,
-                         P->iters, P->d_bar, P->d_work, status, limit) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, k_rrl_batch, (const BatchImg*)P->d_imgs, (const int4*)P->d_tiles_q,
+                         (int)P->tiles_q.size(), (const int4*)P->d_tiles_u, (int)P->tiles_u.size(), P->iters,
+                         P->d_bar, P->d_work, status, limit) != cudaSuccess) {
     (void)cudaGetLastError();
     return DB_ERR_CUDA;
   }
@@ -512,18 +590,21 @@ db_status batch_run(const BatchPlan* P, int* status, cudaStream_t s) {
 
 void batch_destroy(BatchPlan* P) { delete P; }
 
-// Set the tunable forms of every image (dense: dense bodies for the
-// dense-eligible 2D PSFs; windows for the non-box one-axis PSFs: 0 tap
-// groups, 1 register windows, 2 the size rule's choice) and upload the
-// descriptors (synchronises the stream: the host table is reused).
-static db_status batch_set_forms(BatchPlan* P, bool dense, int windows, cudaStream_t s) {
+// Set the tunable forms of every image (fft: FFT tiles by the size rule for
+// 2D PSFs, else none; dense: dense bodies for the dense-eligible 2D PSFs;
+// windows for the non-box one-axis PSFs: 0 tap groups, 1 register windows,
+// 2 the size rule's choice), rebuild the tile tables and upload them with
+// the descriptors (synchronises the stream: the host tables are reused).
+static db_status batch_set_forms(BatchPlan* P, bool fft, bool dense, int windows, cudaStream_t s) {
   for (int i = 0; i < P->n; ++i) {
+    P->imgs[i].fft = fft ? P->fft_rule[i] : 0;
     P->imgs[i].kwd = dense ? P->dense_kw[i] : 0;
     if (P->window_box[i]) P->imgs[i].box = windows == 2 ? P->rule_box[i] : windows == 1 ? P->window_box[i] : 0;
   }
+  build_tiles(P);
   if (cudaMemcpyAsync(P->d_imgs, P->imgs.data(), (size_t)P->n * sizeof(BatchImg), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+      upload_tiles(P, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
     return DB_ERR_CUDA;
   return DB_OK;
 }
@@ -721,30 +802,33 @@ db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_hos
 }
 
 db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream, int* dense_out,
-                            int* windows_out) {
+                            int* windows_out, int* fft_out) {
   BatchPlan* P = (BatchPlan*)b;
   if (!P || reps < 1) return DB_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  bool has_dense = false, has_win = false;
+  bool has_dense = false, has_win = false, has_fft = false;
   for (int i = 0; i < P->n; ++i) {
     has_dense |= P->dense_kw[i] != 0;
     has_win |= P->window_box[i] != 0;
+    has_fft |= P->fft_rule[i] != 0;
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return DB_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DB_ERR_CUDA; }
   float best = -1.f;
-  bool best_d = true;
+  bool best_d = true, best_f = true;
   int best_w = 2;
   db_status st = DB_OK;
   const int wforms[3] = {2, 1, 0};  // the size rule, register windows, tap groups
-  for (int d = 0; d < 2 && st == DB_OK; ++d) {
-    if (d == 1 && !has_dense) break;
+  for (int nf = 0; nf < 4 && st == DB_OK; ++nf) {
+    const int d = nf & 1, fo = nf >> 1;  // fft rule / off, dense on / off
+    if (d == 1 && !has_dense) continue;
+    if (fo == 1 && !has_fft) break;
     for (int iw = 0; iw < 3 && st == DB_OK; ++iw) {
       if (iw > 0 && !has_win) break;
-      const bool dense = d == 0;
+      const bool dense = d == 0, fft = fo == 0;
       const int windows = wforms[iw];
-      if ((st = batch_set_forms(P, dense, windows, s)) != DB_OK) break;
+      if ((st = batch_set_forms(P, fft, dense, windows, s)) != DB_OK) break;
       if ((st = batch_run(P, dev_status, s)) != DB_OK) break;  // warm-up
       if (cudaEventRecord(e0, s) != cudaSuccess) { st = DB_ERR_CUDA; break; }
       for (int k = 0; k < reps && st == DB_OK; ++k) st = batch_run(P, dev_status, s);
@@ -752,15 +836,16 @@ db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream
       float ms = 0.f;
       if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = DB_ERR_CUDA; break; }
-      if (best < 0.f || ms < best) { best = ms; best_d = dense; best_w = windows; }
+      if (best < 0.f || ms < best) { best = ms; best_d = dense; best_w = windows; best_f = fft; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != DB_OK) return st;
-  if ((st = batch_set_forms(P, best_d, best_w, s)) != DB_OK) return st;
+  if ((st = batch_set_forms(P, best_f, best_d, best_w, s)) != DB_OK) return st;
   if (dense_out) *dense_out = best_d ? 1 : 0;
   if (windows_out) *windows_out = best_w;
+  if (fft_out) *fft_out = best_f ? 1 : 0;
   return DB_OK;
 }
 

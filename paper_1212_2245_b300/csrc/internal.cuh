@@ -142,10 +142,30 @@ __host__ __device__ inline int dense_tap_stride(int kw) { return (kw + 3) & ~3; 
 __host__ __device__ inline size_t tap_groups_bytes(int kh, int kw) {
   return ((size_t)max_tap_groups(kh, kw) * sizeof(TapGroup) + 255) & ~size_t(255);
 }
-// Bytes of the tap region of a workspace: the groups and the dense table.
+__host__ __device__ inline size_t dense_table_bytes(int kh, int kw) {
+  return dense_eligible(kh, kw) ? (((size_t)kh * dense_tap_stride(kw) * 4 + 255) & ~size_t(255)) : 0;
+}
+// FFT tiles (rrl_fft_tile.cuh): 2D PSFs with sides 2..kFftMaxSide can run the
+// split schedule's blur and correlations as 64 x 64 circular convolutions.
+// Their tap region ends with the PSF's 64 x 64 spectrum (FP32 complex, in
+// the transform's storage order), written when the taps are prepared.
+constexpr int kFftMaxSide = 48;
+constexpr size_t kFftSpecBytes = (size_t)64 * 64 * 8;
+__host__ __device__ inline bool fft_tile_shape(int kh, int kw) {
+  return kh >= 2 && kw >= 2 && kh <= kFftMaxSide && kw <= kFftMaxSide;
+}
+// Smallest kh * kw for which the split schedule and the batch use the FFT
+// tiles for a PSF of fft_tile_shape (db_set_fft_tiles; above 48 * 48: never).
+int fft_tile_min();
+constexpr int kFftTileMinDefault = 289;
+inline bool fft_tile_form(int kh, int kw) { return fft_tile_shape(kh, kw) && kh * kw >= fft_tile_min(); }
+// Bytes of the tap region of a workspace: the groups, the dense table and
+// the FFT-tile spectrum.
 __host__ __device__ inline size_t tap_region_bytes(int kh, int kw) {
-  return tap_groups_bytes(kh, kw) +
-         (dense_eligible(kh, kw) ? (((size_t)kh * dense_tap_stride(kw) * 4 + 255) & ~size_t(255)) : 0);
+  return tap_groups_bytes(kh, kw) + dense_table_bytes(kh, kw) + (fft_tile_shape(kh, kw) ? kFftSpecBytes : 0);
+}
+__host__ __device__ inline const float2* fft_tile_spec(const TapGroup* groups, int kh, int kw) {
+  return (const float2*)((const char*)groups + tap_groups_bytes(kh, kw) + dense_table_bytes(kh, kw));
 }
 __host__ __device__ inline const float* dense_taps(const TapGroup* groups, int kh, int kw) {
   return (const float*)((const char*)groups + tap_groups_bytes(kh, kw));

@@ -1,0 +1,357 @@
+// FFT tiles: the spatial iteration's blur and correlations for larger 2D
+// PSFs computed as circular convolutions of 64 x 64 windows (Sec. 4.2
+// "Fourier transform": convolution by pointwise products of spectra; the
+// paper's general 2D variant, Sec. 4.3, uses FFT convolution).
+//
+// The result is the constant-continuation sum of Eq. 9, not the periodic
+// one: a window holds u (or q) at clamped image positions, and only the
+// outputs whose whole PSF footprint lies inside the window are kept, where
+// circular and linear convolution coincide.  A tile therefore covers
+// (65 - kh) x (65 - kw) outputs of a 64 x 64 window.
+//
+//  - q phase, two horizontally adjacent tiles per CTA: the complex window
+//    uA + i uB goes through one forward 2D transform, a product with the
+//    PSF's spectrum and one inverse transform; the real part is uA*h, the
+//    imaginary part uB*h (h is real).
+//  - update phase, one tile per CTA: the window e + iW, multiplied by the
+//    conjugate spectrum (correlation with h*), gives Delta (real part) and
+//    B (imaginary part) together.
+//
+// Transforms are FP32, register-resident radix-8 (fft8.cuh): 64 = 8 x 8 per
+// axis, so a 2D transform is four passes of 8-point DFTs, each over 512
+// groups of 8 elements, with a shared-memory exchange between passes.  The
+// forward chain (rows then columns, DIF: natural order in, bit-reversed
+// out), the spectrum product and the first inverse pass run back to back on
+// the same registers; the inverse chain (columns then rows, DIT) returns
+// natural order, so no reordering pass exists.  The PSF spectrum comes out
+// of the same forward chain (k_prepare_fft_spec) in the storage order of the
+// data it multiplies, scaled by 1/4096 for the unnormalised inverse.
+//
+// Shared layout of the 64 x 64 complex window: element (r, c) at
+// r * 68 + c + c / 16.  With the thread-to-group maps below, a bank model of
+// every pass finds each warp access at the minimum of two wavefronts.
+//
+// Every output is a fixed function of its window, independent of the number
+// of threads and of the launch, so the split kernels and the batched kernel
+// give the same bits.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "fft8.cuh"
+#include "internal.cuh"
+#include "rrl_tiles.cuh"
+
+namespace db {
+namespace ftile {
+
+constexpr int kN = 64;              // window side
+constexpr int kRS = 68;             // row stride of the complex window (float2)
+constexpr int kPos = kN * kRS;      // float2 slots of the window
+constexpr int kGroups = 512;        // groups of 8 elements per pass
+constexpr int kUS = 72;             // row stride of the staged u (update phase)
+
+__device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int nth_flat() { return blockDim.x * blockDim.y; }
+
+// tw[k] = exp(-2 pi i k / 64)
+__device__ __forceinline__ void make_twiddles(float2* tw) {
+  const int t = tid_flat();
+  if (t < kN) {
+    float s, c;
+    sincospif(-(float)t / 32.0f, &s, &c);
+    tw[t] = make_float2(c, s);
+  }
+}
+
+// Twiddles w^(j e) of a top-pass group (j < 8) in the output slot order of
+// dif8 (slot s holds DFT index bitrev3(s)), from three table reads.
+__device__ __forceinline__ void group_twiddles(const float2* tw, int j, float2 (&w)[8]) {
+  const float2 w1 = tw[j], w2 = tw[2 * j], w4 = tw[4 * j];
+  const float2 w3 = cmul(w1, w2);
+  w[1] = w4;
+  w[2] = w2;
+  w[3] = cmul(w2, w4);
+  w[4] = w1;
+  w[5] = cmul(w1, w4);
+  w[6] = w3;
+  w[7] = cmul(w3, w4);
+}
+
+// Group maps.  Row passes: top groups (r, j) hold columns j + 8m, bottom
+// groups (r, t) columns 8t + m; column passes: top groups (c, j) rows j + 8m,
+// bottom groups (c, t) rows 8t + m (m = 0..7, the register index).
+__device__ __forceinline__ void row_top_group(int g, int& r, int& j) {
+  j = g & 7;
+  const int rs = (g >> 3) & 3;  // rows r, r+2 share a half-warp
+  r = ((g >> 5) << 2) + ((rs & 1) << 1) + (rs >> 1);
+}
+__device__ __forceinline__ int row_top_base(int r, int j) { return r * kRS + j; }
+__device__ __forceinline__ constexpr int row_top_off(int m) { return 8 * m + (m >> 1); }
+__device__ __forceinline__ int row_bot_base(int g) {
+  const int t = g & 7, r = g >> 3;
+  return r * kRS + 8 * t + (t >> 1);
+}
+__device__ __forceinline__ int col_top_base(int g) {
+  const int c = g & 63, j = g >> 6;
+  return j * kRS + c + (c >> 4);
+}
+__device__ __forceinline__ int col_bot_base(int g) {
+  const int c = g & 63, t = g >> 6;
+  return 8 * t * kRS + c + (c >> 4);
+}
+
+// Forward row top pass: elements from ld(r, c), DIF with twiddles, to A.
+template <class Load>
+__device__ __forceinline__ void rows_top_fwd(float2* A, const float2* tw, Load ld) {
+  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+    int r, j;
+    row_top_group(g, r, j);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = ld(r, j + 8 * m);
+    f8::dif8(v);
+    float2 w[8];
+    group_twiddles(tw, j, w);
+#pragma unroll
+    for (int s = 1; s < 8; ++s) v[s] = cmul(v[s], w[s]);
+    float2* p = A + row_top_base(r, j);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p[row_top_off(m)] = v[m];
+  }
+}
+
+// Inverse row top pass: conjugate twiddles, DIT, natural-order elements to
+// out(r, c, value).
+template <class Out>
+__device__ __forceinline__ void rows_top_inv(const float2* A, const float2* tw, Out out) {
+  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+    int r, j;
+    row_top_group(g, r, j);
+    const float2* p = A + row_top_base(r, j);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = p[row_top_off(m)];
+    float2 w[8];
+    group_twiddles(tw, j, w);
+#pragma unroll
+    for (int s = 1; s < 8; ++s) v[s] = cmulc(v[s], w[s]);
+    f8::dit8_inv(v);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) out(r, j + 8 * m, v[m]);
+  }
+}
+
+// Row bottom pass (no twiddles), forward or inverse, in place.
+template <bool INV>
+__device__ __forceinline__ void rows_bot(float2* A) {
+  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+    float2* p = A + row_bot_base(g);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = p[m];
+    if (INV) f8::dit8_inv(v);
+    else f8::dif8(v);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p[m] = v[m];
+  }
+}
+
+// Column top pass, forward (DIF, then twiddles) or inverse (conjugate
+// twiddles, then DIT), in place.
+template <bool INV>
+__device__ __forceinline__ void cols_top(float2* A, const float2* tw) {
+  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+    float2* p = A + col_top_base(g);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = p[8 * kRS * m];
+    float2 w[8];
+    group_twiddles(tw, g >> 6, w);
+    if (!INV) {
+      f8::dif8(v);
+#pragma unroll
+      for (int s = 1; s < 8; ++s) v[s] = cmul(v[s], w[s]);
+    } else {
+#pragma unroll
+      for (int s = 1; s < 8; ++s) v[s] = cmulc(v[s], w[s]);
+      f8::dit8_inv(v);
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p[8 * kRS * m] = v[m];
+  }
+}
+
+// Column bottom pass: forward DIF, product with the spectrum (conjugated
+// for a correlation), inverse DIT, in place.  The spectrum is stored as
+// spec[m * 512 + g] for register m of group g (coalesced reads).
+template <bool CONJ>
+__device__ __forceinline__ void cols_bot_product(float2* A, const float2* __restrict__ spec) {
+  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+    float2* p = A + col_bot_base(g);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = p[kRS * m];
+    f8::dif8(v);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float2 s = __ldg(spec + m * kGroups + g);
+      v[m] = CONJ ? cmulc(v[m], s) : cmul(v[m], s);
+    }
+    f8::dit8_inv(v);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p[kRS * m] = v[m];
+  }
+}
+
+// out(r, c, y) for y = IDFT(DFT(x) . S) (CONJ: . conj(S)) over the 64 x 64
+// window x(r, c) = ld(r, c), S the prepared spectrum (1/4096 included).
+// tw must be ready and A free on entry (the caller's barrier); the
+// barriers between passes are inside.
+template <bool CONJ, class Load, class Out>
+__device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2* __restrict__ spec, Load ld,
+                                       Out out) {
+  rows_top_fwd(A, tw, ld);
+  __syncthreads();
+  rows_bot<false>(A);
+  __syncthreads();
+  cols_top<false>(A, tw);
+  __syncthreads();
+  cols_bot_product<CONJ>(A, spec);
+  __syncthreads();
+  cols_top<true>(A, tw);
+  __syncthreads();
+  rows_bot<true>(A);
+  __syncthreads();
+  rows_top_inv(A, tw, out);
+}
+
+// Spectrum of the PSF for conv64: the circular kernel k(r, c) = h(a, b) at
+// r = (a - cy) mod 64, c = (b - cx) mod 64 (centre (kh/2, kw/2)), through the
+// forward chain, times 1/4096.  One CTA; A: kPos float2 of shared memory.
+__device__ __forceinline__ void psf_spectrum(float2* A, float2* tw, const float* __restrict__ taps, int kh, int kw,
+                                             float2* __restrict__ spec) {
+  make_twiddles(tw);
+  __syncthreads();
+  const int cy = kh >> 1, cx = kw >> 1;
+  rows_top_fwd(A, tw, [&](int r, int c) {
+    const int a = (r + cy) & (kN - 1), b = (c + cx) & (kN - 1);
+    return make_float2(a < kh && b < kw ? __ldg(taps + a * kw + b) : 0.0f, 0.0f);
+  });
+  __syncthreads();
+  rows_bot<false>(A);
+  __syncthreads();
+  cols_top<false>(A, tw);
+  __syncthreads();
+  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+    const float2* p = A + col_bot_base(g);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = p[kRS * m];
+    f8::dif8(v);
+    constexpr float sc = 1.0f / 4096.0f;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) spec[m * kGroups + g] = make_float2(v[m].x * sc, v[m].y * sc);
+  }
+}
+
+// Outputs of a tile: rows (65 - kh), columns (65 - kw).
+__host__ __device__ inline int tile_oh(int kh) { return kN + 1 - kh; }
+__host__ __device__ inline int tile_ow(int kw) { return kN + 1 - kw; }
+
+// Shared memory of the bodies (bytes): twiddles, window, staged u.
+__host__ __device__ inline size_t smem_q() { return (size_t)(kN + kPos) * sizeof(float2); }
+__host__ __device__ inline size_t smem_update(int kh) {
+  return smem_q() + (size_t)(tile_oh(kh) + 4) * kUS * sizeof(float);
+}
+
+// q = (e, W) on the tiles at (i0, j0) and (i0, j0 + OW) (the second one if it
+// starts inside the image), planar: qe, qw (pitch ldqp).  The u window of a
+// tile starts dy = kh-1-kh/2 rows and dx = kw-1-kw/2 columns before it: the
+// blur b(i, j) = sum h(a, b) u(i - a + kh/2, j - b + kw/2) reaches that far
+// up and left.  smem_raw: smem_q() bytes.
+template <typename Dep = NoDep>
+__device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __restrict__ f, int ldf,
+                                       const float* uin, int ldin, float* qe, float* qw, int ldqp, int H, int W,
+                                       const float2* __restrict__ spec, int kh, int kw, const RrlParams& p, int i0,
+                                       int j0, Dep dep = Dep()) {
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* A = tw + kN;
+  make_twiddles(tw);
+  const int dy = kh - 1 - (kh >> 1), dx = kw - 1 - (kw >> 1);
+  const int OH = tile_oh(kh), OW = tile_ow(kw);
+  const int ys = i0 - dy, xa = j0 - dx, xb = xa + OW;
+  const bool has_b = j0 + OW < W;
+  dep();
+  __syncthreads();  // twiddles
+  conv64<false>(
+      A, tw, spec,
+      [&](int r, int c) {
+        const float* row = uin + (size_t)min(max(ys + r, 0), H - 1) * ldin;
+        const float a = row[min(max(xa + c, 0), W - 1)];
+        const float b = has_b ? row[min(max(xb + c, 0), W - 1)] : 0.0f;
+        return make_float2(a, b);
+      },
+      [&](int r, int c, float2 v) {
+        const int oi = r - dy, oj = c - dx;
+        const int i = i0 + oi;
+        if (oi < 0 || oi >= OH || oj < 0 || oj >= OW || i >= H) return;
+        const int ja = j0 + oj, jb = ja + OW;
+        if (ja < W) {
+          const float2 q = weighted_residual(v.x, fmaxf(__ldg(f + (size_t)i * ldf + ja), p.floor), p);
+          qe[(size_t)i * ldqp + ja] = q.x;
+          qw[(size_t)i * ldqp + ja] = q.y;
+        }
+        if (has_b && jb < W) {
+          const float2 q = weighted_residual(v.y, fmaxf(__ldg(f + (size_t)i * ldf + jb), p.floor), p);
+          qe[(size_t)i * ldqp + jb] = q.x;
+          qw[(size_t)i * ldqp + jb] = q.y;
+        }
+      });
+}
+
+// Delta, B from planar q, the diffusion term and the update on the tile at
+// (i0, j0).  The q window starts kh/2 rows and kw/2 columns before the tile
+// (the correlation reaches that far up and left).  u is staged with two
+// pixels of halo for the diffusion term from the 4-column boundary at or
+// left of j0 - 2.  smem_raw: smem_update(kh) bytes.
+template <typename Dep = NoDep>
+__device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float* qe, const float* qw, int ldqp,
+                                            const float* uin, int ldin, float* __restrict__ uout, int ldout, int H,
+                                            int W, const float2* __restrict__ spec, int kh, int kw,
+                                            const RrlParams& p, int* status, int i0, int j0, Dep dep = Dep()) {
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* A = tw + kN;
+  float* us = reinterpret_cast<float*>(A + kPos);
+  make_twiddles(tw);
+  const int cy = kh >> 1, cx = kw >> 1;
+  const int OH = tile_oh(kh), OW = tile_ow(kw);
+  const int xu = (j0 - 2) & ~3;  // a multiple of 4 at or left of j0 - 2
+  const int ncu = (j0 + OW + 2 - xu + 3) >> 2;
+  stage_tile<float, kUS>(us, uin, ldin, H, W, i0 - 2, OH + 4, xu, ncu, rows_aligned16(uin, ldin));
+  dep();
+  cp_async_wait_all();
+  __syncthreads();  // twiddles, staged u
+  const int ys = i0 - cy, xs = j0 - cx;
+  bool bad = false;
+  conv64<true>(
+      A, tw, spec,
+      [&](int r, int c) {
+        const size_t o = (size_t)min(max(ys + r, 0), H - 1) * ldqp + min(max(xs + c, 0), W - 1);
+        return make_float2(qe[o], qw[o]);
+      },
+      [&](int r, int c, float2 v) {
+        const int oi = r - cy, oj = c - cx;
+        const int i = i0 + oi, j = j0 + oj;
+        if (oi < 0 || oi >= OH || oj < 0 || oj >= OW || i >= H || j >= W) return;
+        float D[1], ctr[1];
+        diffusion_strip<1, kUS>(us + (oi + 2) * kUS + (j - xu), p, D, ctr);
+        const float un = rrl_update(ctr[0], v.x, v.y, D[0], p);
+        bad |= !isfinite(un);
+        uout[(size_t)i * ldout + j] = un;
+      });
+  if (bad && status) atomicOr(status, DB_FLAG_NONFINITE);
+}
+
+}  // namespace ftile
+}  // namespace db

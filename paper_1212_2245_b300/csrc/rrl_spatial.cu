@@ -22,6 +22,7 @@
 #include "internal.cuh"
 #include "rrl_box.cuh"
 #include "rrl_dense.cuh"
+#include "rrl_fft_tile.cuh"
 #include "rrl_tiles.cuh"
 
 namespace db {
@@ -186,11 +187,24 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
   }
 }
 
+// The 64 x 64 spectrum of the FFT tiles (rrl_fft_tile.cuh) for a PSF of
+// fft_tile_shape, one CTA.  Raw taps: k_prepare_taps validates them.
+__global__ void __launch_bounds__(256) k_prepare_fft_spec(const float* __restrict__ taps, int kh, int kw,
+                                                         float2* __restrict__ spec) {
+  __shared__ float2 tw[ftile::kN];
+  __shared__ float2 A[ftile::kPos];
+  ftile::psf_spectrum(A, tw, taps, kh, kw, spec);
+}
+
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s) {
   k_prepare_taps<<<1, 256, 0, s>>>(taps, kh, kw, kind, max_tap_groups(kh, kw), dense_min_pct(), groups, ngroups,
                                    status);
   count_launch();
+  if (fft_tile_shape(kh, kw)) {
+    k_prepare_fft_spec<<<1, 256, 0, s>>>(taps, kh, kw, const_cast<float2*>(fft_tile_spec(groups, kh, kw)));
+    count_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -286,6 +300,33 @@ __global__ void __launch_bounds__((TH / kDR) * (TW / kDC), 6) k_rrl_update_dense
   }
 }
 
+// FFT tiles (rrl_fft_tile.cuh): the q kernel takes two horizontally
+// adjacent tiles per CTA (blockIdx.x pairs), the update kernel one; q is
+// planar as for the dense bodies.
+__global__ void __launch_bounds__(256, 3) k_rrl_q_fft(const float* __restrict__ f, int ldf, const float* uin,
+                                                     int ldin, float2* q, int H, int W,
+                                                     const TapGroup* __restrict__ groups_g, int kh, int kw,
+                                                     RrlParams p, ZStride zs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long z = blockIdx.z;
+  float* qe = reinterpret_cast<float*>(q + z * zs.q);
+  ftile::q_tile(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, qe, qe + (size_t)H * upitch(W), upitch(W), H, W,
+                fft_tile_spec(groups_g, kh, kw), kh, kw, p, blockIdx.y * ftile::tile_oh(kh),
+                2 * blockIdx.x * ftile::tile_ow(kw), PdlDep());
+}
+
+__global__ void __launch_bounds__(256, 3) k_rrl_update_fft(const float2* q, const float* uin, int ldin,
+                                                          float* __restrict__ uout, int ldout, int H, int W,
+                                                          const TapGroup* __restrict__ groups_g, int kh, int kw,
+                                                          RrlParams p, int* status, ZStride zs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long z = blockIdx.z;
+  const float* qe = reinterpret_cast<const float*>(q + z * zs.q);
+  ftile::update_tile(smem_raw, qe, qe + (size_t)H * upitch(W), upitch(W), uin + z * zs.in, ldin, uout + z * zs.out,
+                     ldout, H, W, fft_tile_spec(groups_g, kh, kw), kh, kw, p, status,
+                     blockIdx.y * ftile::tile_oh(kh), blockIdx.x * ftile::tile_ow(kw), PdlDep());
+}
+
 // one-axis PSFs: the same split pair with sliding-window sums (box) or
 // register-window tap sums (rrl_box.cuh)
 // Tiles of TH x 32 outputs (TH = 32, or 16 for images with fewer 32 x 32
@@ -347,6 +388,7 @@ static size_t split_smem_update_single(int kh, int kw, int ng_max) {
   return split_smem_update(kUTH, kUTW, kh, kw, ng_max);
 }
 size_t rrl_split_smem(int kh, int kw) {
+  if (fft_tile_form(kh, kw)) return ftile::smem_update(kh);
   size_t a = split_smem_q_single(kh, kw, max_tap_groups(kh, kw));
   size_t b = split_smem_update_single(kh, kw, max_tap_groups(kh, kw));
   if (dense_eligible(kh, kw)) {
@@ -443,6 +485,41 @@ static cudaError_t launch_split_pair(const IterArgs& a, KQ kq, KU ku, int ng_max
   return cudaSuccess;
 }
 
+static cudaError_t launch_split_fft(const IterArgs& a, cudaStream_t s) {
+  const size_t sq = ftile::smem_q(), su = ftile::smem_update(a.kh);
+  cudaError_t e;
+  if ((e = set_smem(k_rrl_q_fft, sq)) != cudaSuccess) return e;
+  if ((e = set_smem(k_rrl_update_fft, su)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_rrl_q_fft, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_rrl_update_fft, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
+      cudaSuccess)
+    return e;
+  const int tx = (a.W + ftile::tile_ow(a.kw) - 1) / ftile::tile_ow(a.kw);
+  const int ty = (a.H + ftile::tile_oh(a.kh) - 1) / ftile::tile_oh(a.kh);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((tx + 1) / 2, ty, a.nz);
+  cfg.dynamicSmemBytes = sq;
+  if ((e = cudaLaunchKernelEx(&cfg, k_rrl_q_fft, a.f, a.ldf, a.uin, a.ldin, a.q, a.H, a.W, a.groups, a.kh, a.kw,
+                              a.p, a.zs)) != cudaSuccess)
+    return e;
+  count_launch();
+  cfg.gridDim = dim3(tx, ty, a.nz);
+  cfg.dynamicSmemBytes = su;
+  if ((e = cudaLaunchKernelEx(&cfg, k_rrl_update_fft, (const float2*)a.q, a.uin, a.ldin, a.uout, a.ldout, a.H, a.W,
+                              a.groups, a.kh, a.kw, a.p, a.status, a.zs)) != cudaSuccess)
+    return e;
+  count_launch();
+  return cudaSuccess;
+}
+
 // SM count of the current device (per call: devices may differ).
 static int sm_count() {
   int dev = 0, v = 0;
@@ -531,6 +608,7 @@ static cudaError_t dispatch_dense(const IterArgs& a, cudaStream_t s) {
 
 template <bool SPLIT>
 static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
+  if (SPLIT && fft_tile_form(a.kh, a.kw)) return launch_split_fft(a, s);
   if (SPLIT && dense_eligible(a.kh, a.kw)) return dispatch_dense(a, s);
   switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
     case 8: return SPLIT ? launch_split_p<8>(a, s) : launch_fused_p<8>(a, s);

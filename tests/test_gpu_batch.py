@@ -144,14 +144,16 @@ def test_batch_autotune_keeps_the_results_of_the_chosen_forms(lib):
     hs = [cuda(c.h) for c in cases]
     b = lib.Batch(fs, hs, [c.params for c in cases], 4, kinds=[c.psf_kind for c in cases])
     choice = b.autotune(reps=2)
-    assert set(choice) == {"dense", "windows"} and choice["windows"] in ("rule", "all", "none")
+    assert set(choice) == {"fft", "dense", "windows"} and choice["windows"] in ("rule", "all", "none")
     outs = [u.clone() for u in b.run()]
+    lib.set_fft_tiles(0 if choice["fft"] else 2305)
     lib.set_dense_min(50 if choice["dense"] else 101)
     lib.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[choice["windows"]])
     try:
         for c, f, h, u in zip(cases, fs, hs, outs):
             assert torch.equal(u, lib.deblur(f, h, c.params, 4, kind=c.psf_kind)), c.name
     finally:
+        lib.set_fft_tiles(0)
         lib.set_dense_min(0)
         lib.set_one_axis_min(0)
     for c, u in zip(cases[:2] + cases[4:6], outs[:2] + outs[4:6]):

@@ -16,6 +16,14 @@ pytestmark = pytest.mark.gpu
 MAX_ABS, RMS = 1e-3, 1e-4
 
 
+@pytest.fixture(autouse=True)
+def _no_fft_tiles(lib):
+    """These tests cover the direct-sum bodies: FFT tiles off."""
+    lib.set_fft_tiles(2305)
+    yield
+    lib.set_fft_tiles(0)
+
+
 def cuda(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32).cuda()
 
