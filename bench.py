@@ -152,7 +152,7 @@ LINE1024_FLOW_ITER_DRAM_BYTES = (8.489728e6 + 1.274112e6) / 20
 # (dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, 55.88 GB,
 # over its 1.735e9 pixel-iterations; profiles/batch512_launches.md).  Set to None
 # when the kernel changes, until it is captured again.
-BATCH_DRAM_BYTES_PER_PX_ITER = 32.20
+BATCH_DRAM_BYTES_PER_PX_ITER = None
 
 
 def pinned_copy(array):
@@ -351,6 +351,12 @@ def run_ours(args, world, rank, local, workload=None):
         plan = db.Plan(H, W, h, p, iters, kind=case.psf_kind)
         plan_w = db.Plan(H, W, h, p, 0, kind=case.psf_kind)  # Wiener only, to split the step time
         stream.synchronize()
+        # the plan's schedule and tile form by measurement (db_plan_autotune),
+        # unless a schedule was fixed on the command line
+        tuned = None
+        if args.schedule == "auto":
+            sched, form = plan.autotune(f, reps=2)
+            tuned = {"schedule": sched, "form": form}
         # warm-up: at least W steps and at least one second of work (clocks
         # ramp up from idle; the first launches also load the modules)
         t0, n = time.perf_counter(), 0
@@ -445,6 +451,7 @@ def run_ours(args, world, rank, local, workload=None):
                    "parallelism": f"replicas x{world}"},
         "rrrl_only_mpx_iter_s": world * px_iter / (ms_iter / 1e3) / 1e6,
         "wiener_ms": statistics.mean(wiener_ms),
+        "autotuned": tuned,
         "roofline": roof,
         "e2e": {"value": world * px_iter / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": H * W * 4, "d2h_bytes_per_step": H * W * 4, "ms_per_step": e2e_ms},
@@ -490,7 +497,7 @@ def run_batch(args, world, rank, local):
     if args.forms != "auto":
         parts = args.forms.split("/")
         d, w = parts[-2:]
-        fixed = {"fft": parts[0] != "nofft", "dense": d == "dense", "windows": w}
+        fixed = {"fft": -1 if parts[0] != "nofft" else 0, "dense": d == "dense", "windows": w}
         set_batch_forms(fixed)
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
@@ -502,6 +509,7 @@ def run_batch(args, world, rank, local):
         t0 = time.perf_counter()
         tuned = full.autotune(reps=2) if fixed is None else fixed
         tune_s = time.perf_counter() - t0
+        fft_used = tuned.get("fft", -1) != 0  # some 2D PSFs run as FFT tiles
         full.run()
         wien.run()
         n0 = lib.db_launch_count()
@@ -591,7 +599,10 @@ def run_batch(args, world, rank, local):
                                  "k_rrl_batch (persistent: all RRRL iterations of all images in one launch)",
                                  traffic=(BATCH_DRAM_BYTES_PER_PX_ITER * pxi
                                           if BATCH_DRAM_BYTES_PER_PX_ITER and len(all_cases) == 512 else None),
-                                 flops=flops_iter * iters, world=world),
+                                 flops=None if fft_used else flops_iter * iters, world=world,
+                                 **({"alu": {"note": "not reported: the FFT tiles form the 2D tap sums with "
+                                                     "far fewer flops than the direct sums"}}
+                                    if fft_used else {})),
         "e2e": {"value": pxi / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * px, "d2h_bytes_per_step": 4 * px, "ms_per_step": e2e_ms,
                 "path": f"db_batch_stream_run_host (C ABI): {e2e_parts} sub-batches, page-locked host images, "
@@ -607,15 +618,16 @@ def run_batch(args, world, rank, local):
 
 def set_batch_forms(forms):
     """Process-wide settings under which a batch plan takes the given tile
-    forms ({"fft": bool, "dense": bool, "windows": "all" | "rule" | "none"};
-    None: the defaults)."""
+    forms ({"fft": threshold on kh * kw (0: none, -1: the default), "dense":
+    bool, "windows": "all" | "rule" | "none"}; None: the defaults)."""
     import paper_1212_2245_b300 as db
     if forms is None:
         db.set_fft_tiles(0)
         db.set_dense_min(0)
         db.set_one_axis_min(0)
         return
-    db.set_fft_tiles(0 if forms.get("fft", True) else 2305)
+    t = forms.get("fft", -1)
+    db.set_fft_tiles(0 if t == -1 else (t or 2305))
     db.set_dense_min(50 if forms["dense"] else 101)
     db.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[forms["windows"]])
 

@@ -208,22 +208,23 @@ void db_batch_destroy(db_batch* b);
 
 /* Choose the batch's tile forms by measurement (the batched counterpart of
  * db_plan_autotune): runs the whole batch `reps` times after one warm-up per
- * candidate, timed with CUDA events on `stream`, for the FFT tiles by the
- * size rule of db_set_fft_tiles or none (2D PSFs), crossed with the dense
- * sums on and off (images with dense-eligible 2D PSFs, odd sides 3..25) and
- * with the forms of non-box one-axis PSFs (the size rule of
- * db_set_one_axis_min's default, register windows for all, tap groups for
- * all), and keeps the fastest combination for every later db_batch_run.
+ * candidate, timed with CUDA events on `stream`, and keeps the fastest
+ * combination for every later db_batch_run.  A coordinate search from the
+ * process-wide size rules: the form of non-box one-axis PSFs (the size rule
+ * of db_set_one_axis_min's default, register windows for all, tap groups
+ * for all), then the dense sums on and off (dense-eligible 2D PSFs, odd
+ * sides 3..25), then the FFT-tile threshold (FFT tiles for the 2D PSFs with
+ * kh * kw at or above it: each distinct kh * kw of the batch, and none).
  * Classes absent from the batch are not tried.  The runs overwrite the
  * images' outputs; synchronises `stream` (call it before capturing the run
  * in a graph; a graph captured earlier keeps working and picks up the
  * choice).  *dense_out (nullable) receives 1 when the dense sums were
  * chosen, *windows_out (nullable) 2 for the size rule, 1 for register
- * windows, 0 for tap groups, *fft_out (nullable) 1 for the FFT tiles.  The
- * result of each image equals db_deblur's under the corresponding
- * process-wide settings (db_set_fft_tiles at its value or 2305;
- * db_set_dense_min 50 or 101; db_set_one_axis_min 0, 1 or 256).
- * DB_ERR_ARG for a null batch or reps < 1. */
+ * windows, 0 for tap groups, *fft_out (nullable) the FFT-tile threshold (0:
+ * none).  The result of each image equals db_deblur's under the
+ * corresponding process-wide settings (db_set_fft_tiles at that threshold,
+ * 2305 for none; db_set_dense_min 50 or 101; db_set_one_axis_min 0, 1 or
+ * 256).  DB_ERR_ARG for a null batch or reps < 1. */
 db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream, int* dense_out,
                             int* windows_out, int* fft_out);
 
@@ -357,15 +358,17 @@ void db_plan_destroy(db_plan* plan);
 
 /* Choose the plan's kernel schedule by measurement: runs the plan on (f -> u)
  * once per candidate -- the split, flow, fused and (where it applies)
- * cluster schedules, and for a
- * non-box one-axis PSF both the tap-group and the register-window form --
- * `reps` times after one warm-up, timed with CUDA events on `stream`, and
- * keeps the fastest for every later db_plan_run of this plan (instead of the
- * process-wide db_set_schedule / db_set_one_axis_min settings).  Synchronises
- * `stream`; not capturable.  Results of all forms agree to FP32 rounding.
- * *chosen_schedule (DB_SCHED_*) and *chosen_axis (0 tap groups, 2 register
- * windows, -1 not applicable) report the choice (both nullable; -1 for a
- * periodic plan, which has one form).  DB_ERR_ARG for null pointers, f == u
+ * cluster schedules; for a non-box one-axis PSF both the tap-group and the
+ * register-window form; for a 2D PSF with sides 2..48 the direct sums in
+ * every schedule and the FFT tiles (split schedule) -- `reps` times after
+ * one warm-up, timed with CUDA events on `stream`, and keeps the fastest
+ * for every later db_plan_run of this plan (instead of the process-wide
+ * db_set_schedule / db_set_one_axis_min / db_set_fft_tiles settings).
+ * Synchronises `stream`; not capturable.  Results of all forms agree to
+ * FP32 rounding.  *chosen_schedule (DB_SCHED_*) and *chosen_axis (0 direct
+ * sums: tap groups or dense, 2 register windows, 3 FFT tiles, -1 not
+ * applicable) report the choice (both nullable; -1 for a periodic plan,
+ * which has one form).  DB_ERR_ARG for null pointers, f == u
  * or reps < 1; DB_ERR_UNSUPPORTED if no form runs. */
 db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, int* dev_status, void* stream,
                            int* chosen_schedule, int* chosen_axis);
@@ -441,11 +444,15 @@ db_status db_set_dense_min(int percent);
  * taken with constant continuation, keeping the (65 - kh) x (65 - kw)
  * outputs whose PSF footprint lies inside the window, so the result is the
  * same constant-continuation iteration as the direct sums, up to FP32
- * rounding (FP32 transforms).  Used for a PSF with kh * kw >= min_taps;
- * the flow schedule falls back to split for such PSFs.  Process-wide;
- * min_taps >= 1 (above 2304: never), 0 restores the default of 289.  Applies
- * to runs started, and batches created, after the call.  DB_ERR_ARG for
- * negative values. */
+ * rounding (FP32 transforms).  Their cost does not depend on the taps, the
+ * direct sums' grows with the non-zero taps: the FFT tiles are used for a
+ * PSF with kh * kw >= min_taps (the default suits dense PSFs such as
+ * Gaussians; a sparse PSF of large support, such as a thin oblique line,
+ * is often faster with the direct sums: db_plan_autotune measures both).
+ * The flow schedule falls back to split for such PSFs.  Process-wide; min_taps >= 1 (above 2304:
+ * never), 0 restores the default of 225.  Applies to runs started, and
+ * plans and batches created, after the call.  DB_ERR_ARG for negative
+ * values. */
 db_status db_set_fft_tiles(int min_taps);
 
 /* Evaluation of the information divergence r_f in the robust weight

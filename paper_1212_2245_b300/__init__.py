@@ -242,7 +242,7 @@ class Plan:
         """Pick this plan's schedule by timing every form on f (db_plan_autotune;
         synchronises the current stream).  Returns (schedule, one_axis_form):
         schedule one of "split", "flow", "fused" (None for a periodic plan),
-        form "groups", "windows" or None."""
+        form "groups" (direct sums), "windows", "fft" or None."""
         u = torch.empty_like(f)
         cs, ca = ctypes.c_int(-1), ctypes.c_int(-1)
         self.ws.reset_status()
@@ -252,7 +252,7 @@ class Plan:
         self.ws.raise_on_flags("db_plan_autotune")
         names = {_lib.SCHED_SPLIT: "split", _lib.SCHED_FLOW: "flow", _lib.SCHED_FUSED: "fused",
                  _lib.SCHED_CLUSTER: "cluster"}
-        return names.get(cs.value), {0: "groups", 2: "windows"}.get(ca.value)
+        return names.get(cs.value), {0: "groups", 2: "windows", 3: "fft"}.get(ca.value)
 
     def run_host(self, f_host, u_host, check: bool = True, sync: bool = True):
         """The pipeline on an image in host memory (db_plan_run_host): the
@@ -391,20 +391,21 @@ class Batch:
         return self.us
 
     def autotune(self, reps: int = 3):
-        """Choose the tile forms by timing whole runs (db_batch_autotune): FFT
-        tiles by the size rule of set_fft_tiles or none for 2D PSFs, the dense
-        sums on or off for dense-eligible 2D PSFs, register windows or tap
-        groups for non-box one-axis PSFs.  Overwrites the outputs and
-        synchronises the current stream.  Returns {"fft": bool, "dense": bool,
-        "windows": w} with w = "rule" (the size rule of set_one_axis_min(0)),
-        "all" (register windows) or "none" (tap groups)."""
+        """Choose the tile forms by timing whole runs (db_batch_autotune):
+        register windows or tap groups for non-box one-axis PSFs, the dense
+        sums on or off for dense-eligible 2D PSFs, and the FFT-tile threshold
+        on kh * kw for 2D PSFs.  Overwrites the outputs and synchronises the
+        current stream.  Returns {"fft": t, "dense": bool, "windows": w} with t
+        the threshold (0: no FFT tiles; set_fft_tiles(t or 2305) reproduces
+        it), w = "rule" (the size rule of set_one_axis_min(0)), "all"
+        (register windows) or "none" (tap groups)."""
         d, w, ft = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self.ws.reset_status()
         _check(_lib.load().db_batch_autotune(self._h, int(reps), self.ws.status.data_ptr(), _stream(),
                                              ctypes.byref(d), ctypes.byref(w), ctypes.byref(ft)),
                "db_batch_autotune")
         self.ws.raise_on_flags("db_batch_autotune")
-        return {"fft": bool(ft.value), "dense": bool(d.value),
+        return {"fft": int(ft.value), "dense": bool(d.value),
                 "windows": {0: "none", 1: "all", 2: "rule"}[w.value]}
 
     def close(self):
@@ -547,7 +548,8 @@ def set_dense_min(percent: int = 0):
 def set_fft_tiles(min_taps: int = 0):
     """Smallest kh * kw for which a 2D PSF (sides 2..48) runs the split
     schedule's blur and correlations as 64 x 64 FFT tiles; 2305 = never,
-    0 = the default (289).  Process-wide; applies to later runs and batches."""
+    0 = the default (225).  Process-wide; applies to later runs and
+    batches."""
     _check(_lib.load().db_set_fft_tiles(int(min_taps)), "db_set_fft_tiles")
 
 

@@ -116,8 +116,13 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   // 752 / 348 / 425; the fused schedule's halo recompute costs more than q's
   // round trip at every size.
   int sched = sched_in >= 0 ? sched_in : g_schedule.load();
+  // form: axis_mode's one-axis forms; 2D PSFs of fft_tile_shape take the FFT
+  // tiles (3) by the size rule or by a plan's tuned form
   int axis = axis_mode(kind, kh, kw);
-  if (axis_in >= 0 && axis != 1) axis = (axis_in == 2 && (kh == 1 || kw == 1)) ? 2 : 0;
+  if (axis_in >= 0 && axis != 1)
+    axis = (axis_in == 2 && (kh == 1 || kw == 1)) ? 2 : (axis_in == 3 && fft_tile_shape(kh, kw)) ? 3 : 0;
+  else if (axis == 0 && fft_tile_form(kh, kw))
+    axis = 3;
   if (sched == DB_SCHED_AUTO) {
     const size_t px = (size_t)H * W;
     sched = (px >= (size_t)512 * 1024 && px <= (size_t)2 << 20) ? DB_SCHED_FLOW : DB_SCHED_SPLIT;
@@ -128,7 +133,7 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
   if (sched == DB_SCHED_CLUSTER && kh == 1 && axis == 0) axis = 2;
   if (sched == DB_SCHED_CLUSTER && (ckpt || !cluster_fits(H, W, kh, kw, axis))) sched = DB_SCHED_SPLIT;
   // dense-eligible 2D PSFs run the split pair with the dense tile bodies
-  if ((sched == DB_SCHED_FLOW && (ckpt || (axis == 0 && (dense_eligible(kh, kw) || fft_tile_form(kh, kw))))) ||
+  if ((sched == DB_SCHED_FLOW && (ckpt || axis == 3 || (axis == 0 && dense_eligible(kh, kw)))) ||
       (sched == DB_SCHED_FUSED && axis == 1))
     sched = DB_SCHED_SPLIT;
   if (sched == DB_SCHED_FUSED) axis = 0;
@@ -150,8 +155,9 @@ static db_status iterate_spatial(const float* f, float* u, int H, int W, int ld,
       return DB_ERR_CUDA;
     return DB_OK;
   }
-  const size_t smem_need = axis ? rrl_box_smem(kh, kw)
-                               : sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
+  const size_t smem_need = axis == 3 ? rrl_fft_tile_smem(kh)
+                           : axis    ? rrl_box_smem(kh, kw)
+                           : sched == DB_SCHED_SPLIT ? rrl_split_smem(kh, kw) : rrl_spatial_smem(kh, kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const float* src = u;
   int ld_src = ld;
@@ -311,8 +317,11 @@ db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, lon
                           (int*)(base + L.ntaps), dev_status, s) != cudaSuccess)
     return DB_ERR_CUDA;
   if (iters == 0 && !ckpt) return DB_OK;
-  const int axis = axis_mode(psf->kind, psf->kh, psf->kw);
-  const size_t smem_need = axis ? rrl_box_smem(psf->kh, psf->kw) : rrl_split_smem(psf->kh, psf->kw);
+  int axis = axis_mode(psf->kind, psf->kh, psf->kw);
+  if (axis == 0 && fft_tile_form(psf->kh, psf->kw)) axis = 3;
+  const size_t smem_need = axis == 3 ? rrl_fft_tile_smem(psf->kh)
+                           : axis    ? rrl_box_smem(psf->kh, psf->kw)
+                                     : rrl_split_smem(psf->kh, psf->kw);
   if (smem_need > 227 * 1024) return DB_ERR_UNSUPPORTED;
   const RrlParams rp = to_rrl(p);
   float* tmp = (float*)(base + L.utmp);
@@ -368,7 +377,7 @@ struct SinglePlan {
   int ng = 0;       // tap-group count (0: unknown)
   RrlParams rp;     // kernel parameters, r_f evaluation as selected at creation
   int sched = -1;   // tuned schedule (db_plan_autotune; -1: the process-wide setting)
-  int axis = -1;    // tuned one-axis form (0 tap groups, 2 register windows; -1: setting)
+  int axis = -1;    // tuned form (0 direct sums, 2 register windows, 3 FFT tiles; -1: settings)
   // db_plan_run_host: the run captured as a CUDA graph for one set of device
   // buffers, status word, settings generation and tuned form
   cudaStream_t cap_stream = nullptr;
@@ -469,6 +478,9 @@ db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, in
   const bool one_axis = P->kind != DB_PSF_BOX && (P->kh == 1 || P->kw == 1);
   const int scheds[4] = {DB_SCHED_SPLIT, DB_SCHED_FLOW, DB_SCHED_FUSED, DB_SCHED_CLUSTER};
   const int axes[2] = {0, 2};
+  // 2D PSFs of the FFT tiles' shape range: direct sums in every schedule,
+  // and the FFT tiles (split schedule)
+  const bool fft2d = !one_axis && P->kind != DB_PSF_BOX && fft_tile_shape(P->kh, P->kw);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return DB_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DB_ERR_CUDA; }
@@ -493,9 +505,12 @@ db_status db_plan_autotune(db_plan* plan, const float* f, float* u, int reps, in
       if (best < 0.f || ms < best) { best = ms; best_s = P->sched; best_a = P->axis; }
       continue;
     }
-    for (int ia = 0; ia < (one_axis && !fused ? 2 : 1); ++ia) {
+    int forms[2] = {-1, -1}, nf = 1;
+    if (one_axis && !fused) { forms[0] = axes[0]; forms[1] = axes[1]; nf = 2; }
+    else if (fft2d) { forms[0] = 0; if (scheds[is] == DB_SCHED_SPLIT) forms[nf++] = 3; }
+    for (int ia = 0; ia < nf; ++ia) {
       P->sched = scheds[is];
-      P->axis = one_axis ? axes[ia] : -1;
+      P->axis = forms[ia];
       if (db_plan_run(plan, f, u, dev_status, stream) != DB_OK) continue;  // e.g. too large for this form
       if (cudaEventRecord(e0, s) != cudaSuccess) { st = DB_ERR_CUDA; break; }
       db_status r = DB_OK;

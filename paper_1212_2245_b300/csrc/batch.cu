@@ -304,9 +304,10 @@ struct BatchPlan {
   // dense-eligible 2D PSF (else 0), the register-window code of a non-box
   // one-axis PSF (3 row, 4 column; else 0) and the code the size rule chose
   std::vector<int> dense_kw, window_box, rule_box;
-  // per image: FFT tiles possible (a 2D PSF of fft_tile_shape), and chosen by
-  // the size rule (fft_tile_form)
-  std::vector<int> fft_ok, fft_rule;
+  // per image: kh * kw when FFT tiles are possible (a 2D PSF of
+  // fft_tile_shape), else 0; images with fft_taps >= fft_min use them
+  std::vector<int> fft_taps;
+  int fft_min = 0;
   ~BatchPlan() { if (wb) wiener_batch_delete(wb); }
 };
 
@@ -497,9 +498,8 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     bi.box = axis == 0 ? 0 : (axis == 1 ? 0 : 2) + (kh == 1 ? 1 : 2);
     bi.kwd = (axis == 0 && dense_eligible(kh, kw)) ? kw : 0;
     P->dense_kw.push_back(bi.kwd);
-    P->fft_ok.push_back(axis == 0 && fft_tile_shape(kh, kw) ? 1 : 0);
-    P->fft_rule.push_back(P->fft_ok.back() && fft_tile_form(kh, kw) ? 1 : 0);
-    bi.fft = P->fft_rule.back();
+    P->fft_taps.push_back(axis == 0 && fft_tile_shape(kh, kw) ? kh * kw : 0);
+    bi.fft = fft_tile_form(kh, kw) && axis == 0 ? 1 : 0;
     P->window_box.push_back((x.psf.kind != DB_PSF_BOX && (kh == 1 || kw == 1)) ? (kh == 1 ? 3 : 4) : 0);
     P->rule_box.push_back(bi.box);
     bi.p.alpha = x.p.alpha; bi.p.eps_phi = x.p.eps_phi; bi.p.eps_psi = x.p.eps_psi;
@@ -517,7 +517,7 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
       sm = std::max(sm, std::max(split_smem_q(kBTH, kBTW, kh, kw, bi.ng_max),
                                  split_smem_update(kBTH, kBTW, kh, kw, bi.ng_max)));
     }
-    if (P->fft_ok.back()) sm = std::max(sm, ftile::smem_update(kh));
+    if (P->fft_taps.back()) sm = std::max(sm, ftile::smem_update(kh));
     if (sm > P->smem) P->smem = sm;
     ntiles_cap += count_tiles_max(x.H, x.W, kh, kw);
   }
@@ -590,14 +590,16 @@ db_status batch_run(const BatchPlan* P, int* status, cudaStream_t s) {
 
 void batch_destroy(BatchPlan* P) { delete P; }
 
-// Set the tunable forms of every image (fft: FFT tiles by the size rule for
-// 2D PSFs, else none; dense: dense bodies for the dense-eligible 2D PSFs;
-// windows for the non-box one-axis PSFs: 0 tap groups, 1 register windows,
-// 2 the size rule's choice), rebuild the tile tables and upload them with
-// the descriptors (synchronises the stream: the host tables are reused).
-static db_status batch_set_forms(BatchPlan* P, bool fft, bool dense, int windows, cudaStream_t s) {
+// Set the tunable forms of every image (fft_min: FFT tiles for the 2D PSFs
+// of their shape range with kh * kw >= fft_min, none if 0; dense: dense
+// bodies for the dense-eligible 2D PSFs; windows for the non-box one-axis
+// PSFs: 0 tap groups, 1 register windows, 2 the size rule's choice),
+// rebuild the tile tables and upload them with the descriptors
+// (synchronises the stream: the host tables are reused).
+static db_status batch_set_forms(BatchPlan* P, int fft_min, bool dense, int windows, cudaStream_t s) {
+  P->fft_min = fft_min;
   for (int i = 0; i < P->n; ++i) {
-    P->imgs[i].fft = fft ? P->fft_rule[i] : 0;
+    P->imgs[i].fft = fft_min > 0 && P->fft_taps[i] >= fft_min ? 1 : 0;
     P->imgs[i].kwd = dense ? P->dense_kw[i] : 0;
     if (P->window_box[i]) P->imgs[i].box = windows == 2 ? P->rule_box[i] : windows == 1 ? P->window_box[i] : 0;
   }
@@ -806,38 +808,60 @@ db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream
   BatchPlan* P = (BatchPlan*)b;
   if (!P || reps < 1) return DB_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  bool has_dense = false, has_win = false, has_fft = false;
+  bool has_dense = false, has_win = false;
+  std::vector<int> fft_sizes;  // distinct kh * kw of the images that can take FFT tiles
   for (int i = 0; i < P->n; ++i) {
     has_dense |= P->dense_kw[i] != 0;
     has_win |= P->window_box[i] != 0;
-    has_fft |= P->fft_rule[i] != 0;
+    if (P->fft_taps[i]) fft_sizes.push_back(P->fft_taps[i]);
   }
+  std::sort(fft_sizes.begin(), fft_sizes.end());
+  fft_sizes.erase(std::unique(fft_sizes.begin(), fft_sizes.end()), fft_sizes.end());
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return DB_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DB_ERR_CUDA; }
-  float best = -1.f;
-  bool best_d = true, best_f = true;
-  int best_w = 2;
   db_status st = DB_OK;
-  const int wforms[3] = {2, 1, 0};  // the size rule, register windows, tap groups
-  for (int nf = 0; nf < 4 && st == DB_OK; ++nf) {
-    const int d = nf & 1, fo = nf >> 1;  // fft rule / off, dense on / off
-    if (d == 1 && !has_dense) continue;
-    if (fo == 1 && !has_fft) break;
-    for (int iw = 0; iw < 3 && st == DB_OK; ++iw) {
-      if (iw > 0 && !has_win) break;
-      const bool dense = d == 0, fft = fo == 0;
-      const int windows = wforms[iw];
-      if ((st = batch_set_forms(P, fft, dense, windows, s)) != DB_OK) break;
-      if ((st = batch_run(P, dev_status, s)) != DB_OK) break;  // warm-up
-      if (cudaEventRecord(e0, s) != cudaSuccess) { st = DB_ERR_CUDA; break; }
-      for (int k = 0; k < reps && st == DB_OK; ++k) st = batch_run(P, dev_status, s);
-      if (st != DB_OK) break;
-      float ms = 0.f;
-      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = DB_ERR_CUDA; break; }
-      if (best < 0.f || ms < best) { best = ms; best_d = dense; best_w = windows; best_f = fft; }
-    }
+  // time of the whole batch under one combination of forms
+  auto time_forms = [&](int fmin, bool dense, int windows, float* ms) -> db_status {
+    db_status r;
+    if ((r = batch_set_forms(P, fmin, dense, windows, s)) != DB_OK) return r;
+    if ((r = batch_run(P, dev_status, s)) != DB_OK) return r;  // warm-up
+    if (cudaEventRecord(e0, s) != cudaSuccess) return DB_ERR_CUDA;
+    for (int k = 0; k < reps; ++k)
+      if ((r = batch_run(P, dev_status, s)) != DB_OK) return r;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return DB_ERR_CUDA;
+    return DB_OK;
+  };
+  // coordinate search from the size rules: the one-axis form, then the
+  // dense sums, then the FFT-tile threshold (every distinct kh * kw of the
+  // batch's 2D PSFs as a threshold, and none)
+  int best_f = fft_tile_min(), best_w = 2;
+  bool best_d = true;
+  float best = -1.f, ms = 0.f;
+  if ((st = time_forms(best_f, best_d, best_w, &ms)) == DB_OK) best = ms;
+  for (int w : {1, 0}) {
+    if (st != DB_OK || !has_win) break;
+    if ((st = time_forms(best_f, best_d, w, &ms)) == DB_OK && ms < best) { best = ms; best_w = w; }
+  }
+  if (st == DB_OK && has_dense && (st = time_forms(best_f, false, best_w, &ms)) == DB_OK && ms < best) {
+    best = ms;
+    best_d = false;
+  }
+  // thresholds that change the set of FFT images: each distinct size, and
+  // none (a threshold above every size)
+  std::vector<int> cands(fft_sizes);
+  if (!fft_sizes.empty()) cands.push_back(0);
+  auto same_set = [&](int a, int c) {
+    for (int v : fft_sizes)
+      if ((a > 0 && v >= a) != (c > 0 && v >= c)) return false;
+    return true;
+  };
+  for (int c : cands) {
+    if (st != DB_OK) break;
+    if (same_set(c, best_f)) continue;
+    if ((st = time_forms(c, best_d, best_w, &ms)) == DB_OK && ms < best) { best = ms; best_f = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -845,7 +869,7 @@ db_status db_batch_autotune(db_batch* b, int reps, int* dev_status, void* stream
   if ((st = batch_set_forms(P, best_f, best_d, best_w, s)) != DB_OK) return st;
   if (dense_out) *dense_out = best_d ? 1 : 0;
   if (windows_out) *windows_out = best_w;
-  if (fft_out) *fft_out = best_f ? 1 : 0;
+  if (fft_out) *fft_out = best_f;
   return DB_OK;
 }
 

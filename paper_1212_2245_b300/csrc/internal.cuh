@@ -81,7 +81,7 @@ void count_launch(int n = 1);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Bytes k_prepare_taps writes next to the tap groups: the group count (int),
-// at +16 the box weights (e0, w, e1, L), at +32 the taps of a one-axis PSF,
+// at +4 the dense flag, at +16 the box weights (e0, w, e1, L), at +32 the taps of a one-axis PSF,
 // at +1056 the group class starts (kMaxGroupH + 1 ints).
 constexpr size_t kAuxBytes = 1280;
 // Form of the split and flow tiles for a PSF: 0 tap groups, 1 box
@@ -155,10 +155,13 @@ __host__ __device__ inline bool fft_tile_shape(int kh, int kw) {
   return kh >= 2 && kw >= 2 && kh <= kFftMaxSide && kw <= kFftMaxSide;
 }
 // Smallest kh * kw for which the split schedule and the batch use the FFT
-// tiles for a PSF of fft_tile_shape (db_set_fft_tiles; above 48 * 48: never).
+// tiles for a PSF of fft_tile_shape (db_set_fft_tiles; above 48 * 48:
+// never).  Every entry point decides from the shape alone, so that plans,
+// batches and single calls run the same form.
 int fft_tile_min();
-constexpr int kFftTileMinDefault = 289;
-inline bool fft_tile_form(int kh, int kw) { return fft_tile_shape(kh, kw) && kh * kw >= fft_tile_min(); }
+constexpr int kFftTileMinDefault = 225;
+inline bool fft_tile_form(int kh, int kw, int min_taps) { return fft_tile_shape(kh, kw) && kh * kw >= min_taps; }
+inline bool fft_tile_form(int kh, int kw) { return fft_tile_form(kh, kw, fft_tile_min()); }
 // Bytes of the tap region of a workspace: the groups, the dense table and
 // the FFT-tile spectrum.
 __host__ __device__ inline size_t tap_region_bytes(int kh, int kw) {
@@ -177,7 +180,10 @@ __host__ __device__ inline const int* dense_flag(const int* ngroups) { return ng
 cudaError_t launch_prepare_taps(const float* taps, int kh, int kw, int kind, TapGroup* groups,
                                 int* ngroups, int* status, cudaStream_t s);
 size_t rrl_spatial_smem(int kh, int kw);
-size_t rrl_split_smem(int kh, int kw);  // larger of the two split kernels
+size_t rrl_split_smem(int kh, int kw);  // larger of the two split kernels (direct sums)
+size_t rrl_fft_tile_smem(int kh);       // larger of the two FFT-tile split kernels
+// axis: 0 tap groups or dense sums, 1 box sums, 2 register windows (one-axis
+// PSFs), 3 FFT tiles (2D PSFs of fft_tile_shape)
 cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin, float* uout,
                              int ldout, float2* q, int H, int W, const TapGroup* groups,
                              const int* ngroups, int kh, int kw, const RrlParams& p, int* status,

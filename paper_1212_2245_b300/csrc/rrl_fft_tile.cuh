@@ -31,9 +31,10 @@
 // r * 68 + c + c / 16.  With the thread-to-group maps below, a bank model of
 // every pass finds each warp access at the minimum of two wavefronts.
 //
-// Every output is a fixed function of its window, independent of the number
-// of threads and of the launch, so the split kernels and the batched kernel
-// give the same bits.
+// The bodies run with 256 threads (two groups of every pass per thread, so
+// that each thread has two independent chains in flight).  Every output is
+// a fixed function of its window, independent of the launch, so the split
+// kernels and the batched kernel give the same bits.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -50,32 +51,33 @@ constexpr int kRS = 68;             // row stride of the complex window (float2)
 constexpr int kPos = kN * kRS;      // float2 slots of the window
 constexpr int kGroups = 512;        // groups of 8 elements per pass
 constexpr int kUS = 72;             // row stride of the staged u (update phase)
+constexpr int kThreads = 256;       // threads of a CTA running the bodies
+constexpr int kSR = 4;              // rows of an update strip
 
 __device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
-__device__ __forceinline__ int nth_flat() { return blockDim.x * blockDim.y; }
 
-// tw[k] = exp(-2 pi i k / 64)
+// Twiddle table of the top passes: tw[8 j + s] = w^(j bitrev3(s)),
+// w = exp(-2 pi i / 64), the factor of output slot s of group j (slot s of
+// dif8 holds DFT index bitrev3(s)); one CTA-wide table of 64 entries.
 __device__ __forceinline__ void make_twiddles(float2* tw) {
   const int t = tid_flat();
   if (t < kN) {
-    float s, c;
-    sincospif(-(float)t / 32.0f, &s, &c);
-    tw[t] = make_float2(c, s);
+    const int j = t >> 3, sl = t & 7;
+    const int e = ((sl & 1) << 2) | (sl & 2) | (sl >> 2);
+    float sn, cs;
+    sincospif(-(float)(j * e) / 32.0f, &sn, &cs);
+    tw[t] = make_float2(cs, sn);
   }
 }
 
-// Twiddles w^(j e) of a top-pass group (j < 8) in the output slot order of
-// dif8 (slot s holds DFT index bitrev3(s)), from three table reads.
 __device__ __forceinline__ void group_twiddles(const float2* tw, int j, float2 (&w)[8]) {
-  const float2 w1 = tw[j], w2 = tw[2 * j], w4 = tw[4 * j];
-  const float2 w3 = cmul(w1, w2);
-  w[1] = w4;
-  w[2] = w2;
-  w[3] = cmul(w2, w4);
-  w[4] = w1;
-  w[5] = cmul(w1, w4);
-  w[6] = w3;
-  w[7] = cmul(w3, w4);
+  const float4* t4 = reinterpret_cast<const float4*>(tw + 8 * j);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = t4[k];
+    w[2 * k] = make_float2(v.x, v.y);
+    w[2 * k + 1] = make_float2(v.z, v.w);
+  }
 }
 
 // Group maps.  Row passes: top groups (r, j) hold columns j + 8m, bottom
@@ -102,32 +104,42 @@ __device__ __forceinline__ int col_bot_base(int g) {
 }
 
 // Forward row top pass: elements from ld(r, c), DIF with twiddles, to A.
+// Both groups' elements are loaded before either is transformed (sixteen
+// loads in flight per thread).
 template <class Load>
 __device__ __forceinline__ void rows_top_fwd(float2* A, const float2* tw, Load ld) {
-  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
-    int r, j;
-    row_top_group(g, r, j);
-    float2 v[8];
+  const int g0 = tid_flat();
+  int r[2], j[2];
+  row_top_group(g0, r[0], j[0]);
+  row_top_group(g0 + kThreads, r[1], j[1]);
+  float2 v[2][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = ld(r, j + 8 * m);
-    f8::dif8(v);
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[h][m] = ld(r[h], j[h] + 8 * m);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    f8::dif8(v[h]);
     float2 w[8];
-    group_twiddles(tw, j, w);
+    group_twiddles(tw, j[h], w);
 #pragma unroll
-    for (int s = 1; s < 8; ++s) v[s] = cmul(v[s], w[s]);
-    float2* p = A + row_top_base(r, j);
+    for (int s = 1; s < 8; ++s) v[h][s] = cmul(v[h][s], w[s]);
+    float2* p = A + row_top_base(r[h], j[h]);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) p[row_top_off(m)] = v[m];
+    for (int m = 0; m < 8; ++m) p[row_top_off(m)] = v[h][m];
   }
 }
 
-// Inverse row top pass: conjugate twiddles, DIT, natural-order elements to
-// out(r, c, value).
+// Inverse row top pass over the rows r_lo <= r < r_hi: conjugate twiddles,
+// DIT, natural-order elements to out(r, c, value).
 template <class Out>
-__device__ __forceinline__ void rows_top_inv(const float2* A, const float2* tw, Out out) {
-  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+__device__ __forceinline__ void rows_top_inv(const float2* A, const float2* tw, int r_lo, int r_hi, Out out) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int g = tid_flat() + h * kThreads;
     int r, j;
     row_top_group(g, r, j);
+    if (r < r_lo || r >= r_hi) continue;
     const float2* p = A + row_top_base(r, j);
     float2 v[8];
 #pragma unroll
@@ -142,10 +154,14 @@ __device__ __forceinline__ void rows_top_inv(const float2* A, const float2* tw, 
   }
 }
 
-// Row bottom pass (no twiddles), forward or inverse, in place.
+// Row bottom pass (no twiddles), forward or inverse, in place, over the
+// rows r_lo <= r < r_hi.
 template <bool INV>
-__device__ __forceinline__ void rows_bot(float2* A) {
-  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+__device__ __forceinline__ void rows_bot(float2* A, int r_lo = 0, int r_hi = kN) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int g = tid_flat() + h * kThreads;
+    if ((g >> 3) < r_lo || (g >> 3) >= r_hi) continue;
     float2* p = A + row_bot_base(g);
     float2 v[8];
 #pragma unroll
@@ -161,7 +177,9 @@ __device__ __forceinline__ void rows_bot(float2* A) {
 // twiddles, then DIT), in place.
 template <bool INV>
 __device__ __forceinline__ void cols_top(float2* A, const float2* tw) {
-  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int g = tid_flat() + h * kThreads;
     float2* p = A + col_top_base(g);
     float2 v[8];
 #pragma unroll
@@ -187,7 +205,9 @@ __device__ __forceinline__ void cols_top(float2* A, const float2* tw) {
 // spec[m * 512 + g] for register m of group g (coalesced reads).
 template <bool CONJ>
 __device__ __forceinline__ void cols_bot_product(float2* A, const float2* __restrict__ spec) {
-  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int g = tid_flat() + h * kThreads;
     float2* p = A + col_bot_base(g);
     float2 v[8];
 #pragma unroll
@@ -205,12 +225,13 @@ __device__ __forceinline__ void cols_bot_product(float2* A, const float2* __rest
 }
 
 // out(r, c, y) for y = IDFT(DFT(x) . S) (CONJ: . conj(S)) over the 64 x 64
-// window x(r, c) = ld(r, c), S the prepared spectrum (1/4096 included).
+// window x(r, c) = ld(r, c), S the prepared spectrum (1/4096 included), for
+// the rows r_lo <= r < r_hi (the inverse row passes skip the others).
 // tw must be ready and A free on entry (the caller's barrier); the
 // barriers between passes are inside.
 template <bool CONJ, class Load, class Out>
-__device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2* __restrict__ spec, Load ld,
-                                       Out out) {
+__device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2* __restrict__ spec, int r_lo,
+                                       int r_hi, Load ld, Out out) {
   rows_top_fwd(A, tw, ld);
   __syncthreads();
   rows_bot<false>(A);
@@ -221,9 +242,9 @@ __device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2
   __syncthreads();
   cols_top<true>(A, tw);
   __syncthreads();
-  rows_bot<true>(A);
+  rows_bot<true>(A, r_lo, r_hi);
   __syncthreads();
-  rows_top_inv(A, tw, out);
+  rows_top_inv(A, tw, r_lo, r_hi, out);
 }
 
 // Spectrum of the PSF for conv64: the circular kernel k(r, c) = h(a, b) at
@@ -243,7 +264,9 @@ __device__ __forceinline__ void psf_spectrum(float2* A, float2* tw, const float*
   __syncthreads();
   cols_top<false>(A, tw);
   __syncthreads();
-  for (int g = tid_flat(); g < kGroups; g += nth_flat()) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int g = tid_flat() + h * kThreads;
     const float2* p = A + col_bot_base(g);
     float2 v[8];
 #pragma unroll
@@ -260,9 +283,10 @@ __host__ __device__ inline int tile_oh(int kh) { return kN + 1 - kh; }
 __host__ __device__ inline int tile_ow(int kw) { return kN + 1 - kw; }
 
 // Shared memory of the bodies (bytes): twiddles, window, staged u.
+__host__ __device__ inline int staged_u_rows(int kh) { return ((tile_oh(kh) + kSR - 1) / kSR) * kSR + 4; }
 __host__ __device__ inline size_t smem_q() { return (size_t)(kN + kPos) * sizeof(float2); }
 __host__ __device__ inline size_t smem_update(int kh) {
-  return smem_q() + (size_t)(tile_oh(kh) + 4) * kUS * sizeof(float);
+  return smem_q() + (size_t)staged_u_rows(kh) * kUS * sizeof(float);
 }
 
 // q = (e, W) on the tiles at (i0, j0) and (i0, j0 + OW) (the second one if it
@@ -282,20 +306,26 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
   const int OH = tile_oh(kh), OW = tile_ow(kw);
   const int ys = i0 - dy, xa = j0 - dx, xb = xa + OW;
   const bool has_b = j0 + OW < W;
+  // both windows inside the image: no clamping
+  const bool inside = ys >= 0 && ys + kN <= H && xa >= 0 && (has_b ? xb : xa) + kN <= W;
   dep();
   __syncthreads();  // twiddles
   conv64<false>(
-      A, tw, spec,
+      A, tw, spec, dy, dy + OH,
       [&](int r, int c) {
+        if (inside) {
+          const float* row = uin + (size_t)(ys + r) * ldin;
+          return make_float2(row[xa + c], has_b ? row[xb + c] : 0.0f);
+        }
         const float* row = uin + (size_t)min(max(ys + r, 0), H - 1) * ldin;
         const float a = row[min(max(xa + c, 0), W - 1)];
         const float b = has_b ? row[min(max(xb + c, 0), W - 1)] : 0.0f;
         return make_float2(a, b);
       },
       [&](int r, int c, float2 v) {
-        const int oi = r - dy, oj = c - dx;
-        const int i = i0 + oi;
-        if (oi < 0 || oi >= OH || oj < 0 || oj >= OW || i >= H) return;
+        const int oj = c - dx;
+        const int i = i0 + r - dy;
+        if (oj < 0 || oj >= OW || i >= H) return;
         const int ja = j0 + oj, jb = ja + OW;
         if (ja < W) {
           const float2 q = weighted_residual(v.x, fmaxf(__ldg(f + (size_t)i * ldf + ja), p.floor), p);
@@ -312,9 +342,11 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
 
 // Delta, B from planar q, the diffusion term and the update on the tile at
 // (i0, j0).  The q window starts kh/2 rows and kw/2 columns before the tile
-// (the correlation reaches that far up and left).  u is staged with two
-// pixels of halo for the diffusion term from the 4-column boundary at or
-// left of j0 - 2.  smem_raw: smem_update(kh) bytes.
+// (the correlation reaches that far up and left).  The transform leaves
+// (Delta, B) in the window's shared-memory slots; the update then runs in
+// vertical strips of kSR outputs (the diffusion term shares its stencil rows
+// within a strip).  u is staged with two pixels of halo from the 4-column
+// boundary at or left of j0 - 2.  smem_raw: smem_update(kh) bytes.
 template <typename Dep = NoDep>
 __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float* qe, const float* qw, int ldqp,
                                             const float* uin, int ldin, float* __restrict__ uout, int ldout, int H,
@@ -328,28 +360,42 @@ __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float
   const int OH = tile_oh(kh), OW = tile_ow(kw);
   const int xu = (j0 - 2) & ~3;  // a multiple of 4 at or left of j0 - 2
   const int ncu = (j0 + OW + 2 - xu + 3) >> 2;
-  stage_tile<float, kUS>(us, uin, ldin, H, W, i0 - 2, OH + 4, xu, ncu, rows_aligned16(uin, ldin));
+  stage_tile<float, kUS>(us, uin, ldin, H, W, i0 - 2, staged_u_rows(kh), xu, ncu, rows_aligned16(uin, ldin));
   dep();
+  const int ys = i0 - cy, xs = j0 - cx;
+  const bool inside = ys >= 0 && ys + kN <= H && xs >= 0 && xs + kN <= W;
   cp_async_wait_all();
   __syncthreads();  // twiddles, staged u
-  const int ys = i0 - cy, xs = j0 - cx;
-  bool bad = false;
   conv64<true>(
-      A, tw, spec,
+      A, tw, spec, cy, cy + OH,
       [&](int r, int c) {
-        const size_t o = (size_t)min(max(ys + r, 0), H - 1) * ldqp + min(max(xs + c, 0), W - 1);
+        const size_t o = inside ? (size_t)(ys + r) * ldqp + (xs + c)
+                                : (size_t)min(max(ys + r, 0), H - 1) * ldqp + min(max(xs + c, 0), W - 1);
         return make_float2(qe[o], qw[o]);
       },
-      [&](int r, int c, float2 v) {
-        const int oi = r - cy, oj = c - cx;
-        const int i = i0 + oi, j = j0 + oj;
-        if (oi < 0 || oi >= OH || oj < 0 || oj >= OW || i >= H || j >= W) return;
-        float D[1], ctr[1];
-        diffusion_strip<1, kUS>(us + (oi + 2) * kUS + (j - xu), p, D, ctr);
-        const float un = rrl_update(ctr[0], v.x, v.y, D[0], p);
-        bad |= !isfinite(un);
-        uout[(size_t)i * ldout + j] = un;
-      });
+      // each (Delta, B) back into the slot its group read it from
+      [&](int r, int c, float2 v) { A[r * kRS + c + (c >> 4)] = v; });
+  __syncthreads();
+  bool bad = false;
+  const int nsr = (OH + kSR - 1) / kSR;
+  for (int item = tid_flat(); item < nsr * OW; item += kThreads) {
+    const int sr = item / OW, oj = item - sr * OW;
+    const int oi0 = sr * kSR, j = j0 + oj;
+    if (j >= W) continue;
+    float D[kSR], ctr[kSR];
+    diffusion_strip<kSR, kUS>(us + (oi0 + 2) * kUS + (j - xu), p, D, ctr);
+    const int c = cx + oj;
+    const float2* a = A + (cy + oi0) * kRS + c + (c >> 4);
+#pragma unroll
+    for (int t = 0; t < kSR; ++t) {
+      const int i = i0 + oi0 + t;
+      if (oi0 + t >= OH || i >= H) break;
+      const float2 v = a[t * kRS];
+      const float un = rrl_update(ctr[t], v.x, v.y, D[t], p);
+      bad |= !isfinite(un);
+      uout[(size_t)i * ldout + j] = un;
+    }
+  }
   if (bad && status) atomicOr(status, DB_FLAG_NONFINITE);
 }
 

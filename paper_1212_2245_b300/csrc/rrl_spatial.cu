@@ -303,7 +303,7 @@ __global__ void __launch_bounds__((TH / kDR) * (TW / kDC), 6) k_rrl_update_dense
 // FFT tiles (rrl_fft_tile.cuh): the q kernel takes two horizontally
 // adjacent tiles per CTA (blockIdx.x pairs), the update kernel one; q is
 // planar as for the dense bodies.
-__global__ void __launch_bounds__(256, 3) k_rrl_q_fft(const float* __restrict__ f, int ldf, const float* uin,
+__global__ void __launch_bounds__(256, 4) k_rrl_q_fft(const float* __restrict__ f, int ldf, const float* uin,
                                                      int ldin, float2* q, int H, int W,
                                                      const TapGroup* __restrict__ groups_g, int kh, int kw,
                                                      RrlParams p, ZStride zs) {
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256, 3) k_rrl_q_fft(const float* __restrict__ 
                 2 * blockIdx.x * ftile::tile_ow(kw), PdlDep());
 }
 
-__global__ void __launch_bounds__(256, 3) k_rrl_update_fft(const float2* q, const float* uin, int ldin,
+__global__ void __launch_bounds__(256, 4) k_rrl_update_fft(const float2* q, const float* uin, int ldin,
                                                           float* __restrict__ uout, int ldout, int H, int W,
                                                           const TapGroup* __restrict__ groups_g, int kh, int kw,
                                                           RrlParams p, int* status, ZStride zs) {
@@ -387,8 +387,8 @@ static size_t split_smem_q_single(int kh, int kw, int ng_max) {
 static size_t split_smem_update_single(int kh, int kw, int ng_max) {
   return split_smem_update(kUTH, kUTW, kh, kw, ng_max);
 }
+size_t rrl_fft_tile_smem(int kh) { return ftile::smem_update(kh); }
 size_t rrl_split_smem(int kh, int kw) {
-  if (fft_tile_form(kh, kw)) return ftile::smem_update(kh);
   size_t a = split_smem_q_single(kh, kw, max_tap_groups(kh, kw));
   size_t b = split_smem_update_single(kh, kw, max_tap_groups(kh, kw));
   if (dense_eligible(kh, kw)) {
@@ -608,7 +608,6 @@ static cudaError_t dispatch_dense(const IterArgs& a, cudaStream_t s) {
 
 template <bool SPLIT>
 static cudaError_t dispatch(const IterArgs& a, cudaStream_t s) {
-  if (SPLIT && fft_tile_form(a.kh, a.kw)) return launch_split_fft(a, s);
   if (SPLIT && dense_eligible(a.kh, a.kw)) return dispatch_dense(a, s);
   switch (SPLIT ? split_halo_class(a.kw) : halo_class(a.kw)) {
     case 8: return SPLIT ? launch_split_p<8>(a, s) : launch_fused_p<8>(a, s);
@@ -636,6 +635,7 @@ cudaError_t launch_rrl_split(const float* f, int ldf, const float* uin, int ldin
                       nz, {zf, zin, zout, zq}};
   if (axis == 1) return kh == 1 ? launch_split_box<true, true>(a, s) : launch_split_box<false, true>(a, s);
   if (axis == 2) return kh == 1 ? launch_split_box<true, false>(a, s) : launch_split_box<false, false>(a, s);
+  if (axis == 3) return launch_split_fft(a, s);
   return dispatch<true>(a, s);
 }
 

@@ -48,9 +48,9 @@ def test_plan_run_host_equals_device_run(lib):
     plan.close()
 
 
-@pytest.mark.parametrize("form", ["line", "row", "col-box"])
+@pytest.mark.parametrize("form", ["line", "gauss", "row", "col-box"])
 def test_plan_autotune_keeps_a_form_equal_to_the_global_setting(lib, form):
-    """db_plan_autotune times every schedule (and one-axis form) and keeps the
+    """db_plan_autotune times every schedule (and one-axis or FFT-tile form) and keeps the
     fastest for the plan: the tuned plan's result equals, bit for bit, a run
     with that choice set process-wide, and stays within FP32 rounding of the
     untuned plan's."""
@@ -58,6 +58,8 @@ def test_plan_autotune_keeps_a_form_equal_to_the_global_setting(lib, form):
     H, W, kind = 384, 352, "general"
     if form == "line":
         h = synth.line_psf(15, 30.0)
+    elif form == "gauss":
+        h = synth.gaussian_mixture_psf(21, rng)
     elif form == "row":
         h = synth.random_motion_1d(31, rng, "row")
     else:
@@ -71,17 +73,22 @@ def test_plan_autotune_keeps_a_form_equal_to_the_global_setting(lib, form):
     assert sched in ("split", "flow", "fused", "cluster")
     if form == "row" and sched != "cluster":
         assert axis == "groups" if sched == "fused" else axis in ("groups", "windows")
+    elif form in ("line", "gauss"):  # 2D PSFs: direct sums, or FFT tiles (split schedule)
+        assert axis == "groups" or (axis == "fft" and sched == "split")
     else:
         assert axis is None
     tuned = plan.run(f).clone()
     try:
         db.set_schedule(sched)
-        if axis is not None:
+        if form in ("line", "gauss"):
+            db.set_fft_tiles(1 if axis == "fft" else 2305)
+        elif axis is not None:
             db.set_one_axis_min(1 if axis == "windows" else 256)
         assert torch.equal(tuned, db.deblur(f, taps, p, 6, kind=kind))
     finally:
         db.set_schedule("auto")
         db.set_one_axis_min(0)
+        db.set_fft_tiles(0)
     err = (tuned - base).abs().max().item()
     assert err <= 1e-3 * max(1.0, base.abs().max().item()), err
     plan.close()

@@ -146,7 +146,7 @@ def test_batch_autotune_keeps_the_results_of_the_chosen_forms(lib):
     choice = b.autotune(reps=2)
     assert set(choice) == {"fft", "dense", "windows"} and choice["windows"] in ("rule", "all", "none")
     outs = [u.clone() for u in b.run()]
-    lib.set_fft_tiles(0 if choice["fft"] else 2305)
+    lib.set_fft_tiles(choice["fft"] or 2305)
     lib.set_dense_min(50 if choice["dense"] else 101)
     lib.set_one_axis_min({"rule": 0, "all": 1, "none": 256}[choice["windows"]])
     try:
