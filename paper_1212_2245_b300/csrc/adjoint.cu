@@ -1168,7 +1168,7 @@ constexpr int kAdjBlocks = 592;  // 4 x 148 SMs, grid-stride
 
 struct AdjLayout {
   size_t f0, seg, b, q, ab, g, ubar, uacc, abbar, dbar, qbar, bbar, f0bar, a, part, wraw, prow, ppart, psum,
-      spec, unit_taps, unit_spec, tabs, total;
+      spec, unit_taps, unit_spec, tabs, kspec, total;
 };
 
 static AdjLayout adj_layout(int N, int H, int W, int kw, int ntaps, int every) {
@@ -1201,6 +1201,7 @@ static AdjLayout adj_layout(int N, int H, int W, int kw, int ntaps, int every) {
   L.unit_taps = take((size_t)kw * kw * 4);
   L.unit_spec = take((size_t)kw * W * 16);
   L.tabs = take(dft_table_elems(W) * 16);
+  L.kspec = take(wiener_kspec_elems(1, W, 1, kw) * 16);  // the forward Wiener's filter spectrum
   L.total = off;
   return L;
 }
@@ -1386,6 +1387,7 @@ db_status adj_backward(const float* f, int ld, int N, const float* ckpt, int ite
     WL.spec = L.spec;
     WL.work = L.spec;  // not used for a one-row PSF
     WL.tw = L.tabs;
+    WL.kspec = L.kspec;
     // a one-row PSF filters every row on its own: the batch is N*H rows
     ADJ_CHECK(run_wiener(f0, wraw, N * H, W, W, psf->taps, kh, kw, p->K, -FLT_MAX, ws, WL, status, s));
   }

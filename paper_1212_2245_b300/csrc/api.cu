@@ -44,6 +44,7 @@ WsLayout ws_layout(int H, int W, int kh, int kw, int conv, int n, bool iterate_o
   L.work = off;  off += align256(work_elems * sizeof(float4));
   L.s32 = off;   off += (conv == DB_CONV_PERIODIC) ? align256((size_t)H * W * sizeof(float2)) : 0;
   L.tw = off;    off += spatial_only ? 0 : align256((dft_table_elems(W) + dft_table_elems(H)) * sizeof(float4));
+  L.kspec = off; off += spatial_only ? 0 : align256(wiener_kspec_elems(H, W, kh, kw) * sizeof(float4));
   L.flow = off;  off += (conv == DB_CONV_PERIODIC) ? 0 : align256(flow_ws_bytes(H, W));
   L.total = off;
   return L;
@@ -303,7 +304,7 @@ db_status db_deblur_n(const float* f, float* u, int H, int W, int ld, int n, lon
   // images of a contiguous stack of even height go through as one image of
   // n*H rows (the row pairs of the packed transforms stay those of each image)
   WienerState S;
-  if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &S, s) != cudaSuccess) return DB_ERR_CUDA;
+  if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, p->K, ws, L, &S, s) != cudaSuccess) return DB_ERR_CUDA;
   if (psf->kh == 1 && img_stride == (long long)H * ld && H % 2 == 0) {  // same row pairs as one image
     WienerState Sn = S;
     Sn.H = n * H;
@@ -437,11 +438,11 @@ db_status db_plan_create(int H, int W, int ld, const db_psf* psf, const db_param
     // the Wiener filter's own spectrum (1D, or the 2D half spectrum of the
     // real-pair passes) replaces the full one, already rounded for the
     // iterations; the transform tables it rebuilds are the same
-    if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {
+    if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, p->K, ws, L, &P->wst, s) != cudaSuccess) {
       delete P; return DB_ERR_CUDA;
     }
   } else {
-    if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, ws, L, &P->wst, s) != cudaSuccess) {
+    if (wiener_prepare(H, W, psf->taps, psf->kh, psf->kw, p->K, ws, L, &P->wst, s) != cudaSuccess) {
       delete P; return DB_ERR_CUDA;
     }
   }

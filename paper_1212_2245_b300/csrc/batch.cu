@@ -313,7 +313,7 @@ struct BatchPlan {
 
 // Per-image workspace regions, laid out in order.
 struct ImgRegions {
-  size_t groups, ngroups, utmp, q, spec, work, end;
+  size_t groups, ngroups, utmp, q, spec, work, kspec, end;
 };
 
 static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
@@ -325,6 +325,7 @@ static ImgRegions image_regions(size_t off, int H, int W, int kh, int kw) {
   size_t spec = (kh == 1) ? (size_t)W : (kw == 1) ? (size_t)H : (size_t)H * W;
   r.spec = off;    off += align256(spec * sizeof(float4));
   r.work = off;    off += (kh > 1 && kw > 1) ? align256((size_t)H * W * sizeof(float4)) : 0;
+  r.kspec = off;   off += align256(wiener_kspec_elems(H, W, kh, kw) * sizeof(float4));
   r.end = off;
   return r;
 }
@@ -419,10 +420,10 @@ size_t batch_ws_bytes(const db_image_desc* d, int n, int iters, db_status* why) 
   off += 2 * align256(ntiles * sizeof(int4));          // q and update tile tables
   off += 256;                                         // barrier
   off += align256((size_t)(2 * iters + 2) * sizeof(int));  // work counters
-  // batched-Wiener job tables (5 stages x (jobs + 3 item classes) regions):
+  // batched-Wiener job tables (8 stages x (jobs + 3 item classes) regions):
   // at most 3 jobs per image, one item per row
   // (pair) or column group (bounded by nitems), plus alignment slack
-  off += 20 * 256 + (size_t)3 * n * wiener_job_bytes() + nitems * sizeof(int2);
+  off += 32 * 256 + (size_t)3 * n * wiener_job_bytes() + nitems * sizeof(int2);
   return off;
 }
 
@@ -481,6 +482,7 @@ db_status batch_create(const db_image_desc* d, int n, int iters, void* ws, size_
     wi.taps = x.psf.taps; wi.kh = kh; wi.kw = kw; wi.K = x.p.K; wi.floor_ = x.p.pos_floor;
     wi.spec = (float4*)(base + r.spec);
     wi.work = (kh > 1 && kw > 1) ? (float4*)(base + r.work) : nullptr;
+    wi.kspec = wiener_kspec_elems(x.H, x.W, kh, kw) ? (float4*)(base + r.kspec) : nullptr;
     wi.pDW = (kw > 1 || kh == 1) ? &dfts[x.W].first : nullptr;
     wi.pDH = (kh > 1) ? &dfts[x.H].first : nullptr;
     if (wiener_batch_add(P->wb, wi, s) != cudaSuccess) { delete P; return DB_ERR_CUDA; }

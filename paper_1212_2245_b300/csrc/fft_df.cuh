@@ -113,6 +113,7 @@ __host__ __device__ inline int dft_len(const Dft1ff& D) { return (1 << D.logM) *
 struct WienerState {
   int H, W, kh, kw;
   Dft1ff DW, DH;
+  const float4* kspec = nullptr;  // filter spectra of the filtering passes (non-power-of-two axis), or null
 };
 
 __device__ __forceinline__ void seq_item_ff(int it, int nseq, int len, bool seq_fast, int& q, int& k) {

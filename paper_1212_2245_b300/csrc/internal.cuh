@@ -113,6 +113,7 @@ struct WsLayout {
   size_t work;     // float4[work_elems]  (Wiener rows, float-float; Fourier mode: X)
   size_t s32;      // float2[H*W]         (Fourier mode: FP32 PSF spectrum)
   size_t tw;       // float2[dft_table_elems(W) + dft_table_elems(H)]  (transform tables)
+  size_t kspec;    // float4[wiener_kspec_elems]  (Wiener filter spectra, float-float)
   size_t flow;     // flow_ws_bytes(H, W): task counter and per-tile progress counters
   size_t total;
 };
@@ -224,6 +225,11 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 struct Dft1ff;
 int dft_len_n(int N);  // transform length of an axis of N points (Bluestein: 2^a 3^b >= 2N-1)
 size_t dft_table_elems(int N);  // float4 units
+// float4 elements of the filter spectra of a Wiener filter whose filtering
+// pass runs along a non-power-of-two axis (0 otherwise): one length-M
+// spectrum for a one-axis PSF, one per half-spectrum column (W/2 + 1) for a
+// 2D PSF.
+size_t wiener_kspec_elems(int H, int W, int kh, int kw);
 cudaError_t prepare_dft(int N, float4* tab, Dft1ff* ff, Dft1* f32, cudaStream_t s);
 cudaError_t run_psf_spectrum_2d(const float* taps, int kh, int kw, int H, int W, float4* spec,
                                 const Dft1ff& DW, const Dft1ff& DH, cudaStream_t s);
@@ -232,7 +238,7 @@ cudaError_t psf_row_spectrum(const float* taps, int kw, const Dft1ff& D, float4*
 
 // Wiener filter in two parts: set-up (tables, PSF spectrum) and image passes.
 struct WienerState;
-cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, void* ws, const WsLayout& L,
+cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, float K, void* ws, const WsLayout& L,
                            WienerState* st, cudaStream_t s);
 cudaError_t wiener_apply(const float* f, float* u0, int ld, float K, float floor_, void* ws, const WsLayout& L,
                          const WienerState& S, cudaStream_t s);
@@ -246,6 +252,7 @@ struct WienerImage {
   float K, floor_;
   float4* spec;                  // PSF spectrum (1D: length of the axis; 2D: H x W)
   float4* work;                  // 2D only: H x W complex rows
+  float4* kspec;                 // filter spectra (wiener_kspec_elems), or null
   const Dft1ff* pDW;             // transforms (tables already prepared)
   const Dft1ff* pDH;
 };

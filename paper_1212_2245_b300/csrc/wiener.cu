@@ -103,8 +103,9 @@ __global__ void k_chirp(float4* __restrict__ c, float4* __restrict__ b, int N, i
 }
 
 enum RowMode { ROW_PSF = 0, ROW_FWD_REAL = 1, ROW_INV_REAL = 2, ROW_WIENER_1D = 3, ROW_FWD_CPLX = 4,
-               ROW_FWD_R2C = 5, ROW_PSF_R2C = 6, ROW_INV_C2R = 7 };
-enum ColMode { COL_FWD = 0, COL_WIENER = 1, COL_WIENER_1D_REAL = 2 };
+               ROW_FWD_R2C = 5, ROW_PSF_R2C = 6, ROW_INV_C2R = 7, ROW_FILTER_1D = 8, ROW_KSPEC = 9 };
+enum ColMode { COL_FWD = 0, COL_WIENER = 1, COL_WIENER_1D_REAL = 2, COL_FILTER = 3, COL_FILTER_1D_REAL = 4,
+               COL_KSPEC = 5 };
 
 struct FftArgs {
   const float* fin; int ldf;   // real input image
@@ -112,6 +113,8 @@ struct FftArgs {
   float4* cbuf; int ldc;       // complex float-float rows (row pitch ldc elements)
   const float4* spec;          // spectrum (storage order of the transform)
   int ldspec;
+  const float4* kspec;         // filter spectra (the *_FILTER* modes), pitch ldk between columns
+  int ldk;
   const float* taps; int kh, kw;
   Dft1ff D;                    // transform along the kernel's axis
   int nrows;                   // rows (row kernels) or columns (column kernels) of data
@@ -129,6 +132,73 @@ __device__ __forceinline__ float4 wiener_gain(float4 S, float4 X, float K) {
 }
 
 __device__ __forceinline__ float ff_round(float2 v) { return v.x + v.y; }
+
+// ---------------------------------------------------------------------------
+// Filtering passes along a non-power-of-two axis of N points.  The filter
+// Y = IDFT(G . DFT(x)) is the circular convolution of x with the impulse
+// response g' = IDFT(G) (unnormalised, as the inverse sweeps are).  With b
+// the circular sequence of length M >= 2N - 1 that holds g'(d) at d and
+// g'(N - d) at M - d (0 < d < N), zero elsewhere, the zero-padded
+// circular convolution of length M reproduces it exactly at k < N:
+//   (x_pad (*)_M b)(k) = sum_j x_j b((k - j) mod M) = sum_j x_j g'((k - j) mod N),
+// since k - j lies in (-N, N).  Its spectrum FFT_M(b)/M (the filter
+// spectrum) is computed once per image when the filter is prepared, so a
+// pass is two length-M transforms instead of the four of Bluestein's forward
+// and inverse DFTs.
+// ---------------------------------------------------------------------------
+// In place on nseq sequences (element k of sequence q at x[q*ss + k*es],
+// capacity M): g' at k < N becomes the filter spectrum FFT_M(b)/M, in the
+// storage order of fft_fwd_m_ff.  Ends with a barrier.
+__device__ inline void kernel_spectrum_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
+  const int N = D.N, M = dft_len(D), P = M - N;
+  for (int it = threadIdx.x; it < nseq * P; it += blockDim.x) {
+    int q, j;
+    seq_item_ff(it, nseq, P, seq_fast, q, j);
+    float4* base = x + q * ss;
+    const int m = N + j;  // targets m >= N; sources m - M + N < N
+    base[m * es] = (m >= M - N + 1) ? base[(m - M + N) * es] : zzero();
+  }
+  __syncthreads();
+  fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
+  for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    float4* p = x + q * ss + k * es;
+    *p = zscale(*p, D.invM);
+  }
+  __syncthreads();
+}
+
+// The filtering pass on nseq sequences holding x at k < N: zero padding to
+// M, forward sweep, product with the filter spectrum (element m of sequence
+// q at ks[m * ksm + q * ksq], for the first nvalid sequences; the others
+// hold zeros), inverse sweep; the filtered values are at k < N.  Ends with a
+// barrier.
+__device__ inline void filter_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast,
+                                 const float4* __restrict__ ks, int ksm, int ksq, int nvalid) {
+  const int N = D.N, M = dft_len(D), P = M - N;
+  for (int it = threadIdx.x; it < nseq * P; it += blockDim.x) {
+    int q, j;
+    seq_item_ff(it, nseq, P, seq_fast, q, j);
+    x[q * ss + (N + j) * es] = zzero();
+  }
+  __syncthreads();
+  fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
+  for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
+    int q, k;
+    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    if (q >= nvalid) continue;
+    float4* p = x + q * ss + k * es;
+    *p = zmul(*p, __ldg(ks + (size_t)k * ksm + (size_t)q * ksq));
+  }
+  __syncthreads();
+  fft_inv_m_ff(x, D, nseq, es, ss, seq_fast);
+}
+
+// The gain conj(S) / (|S|^2 + K) itself
+__device__ __forceinline__ float4 wiener_gain1(float4 S, float K) {
+  return wiener_gain(S, mkc(make_float2(1.f, 0.f), make_float2(0.f, 0.f)), K);
+}
 
 // Storage position of frequency k in a transformed sequence: bit-reversed
 // for the power-of-two sweeps, natural for Bluestein's form.
@@ -162,7 +232,7 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
       cp_async4(stage + idx, a.fin + (size_t)q * a.ldf + c);
     } else if (MODE == ROW_INV_REAL || MODE == ROW_FWD_CPLX) {
       cp_async16(x + r * M + c, a.cbuf + (size_t)q * a.ldc + c);
-    } else if (MODE == ROW_WIENER_1D || MODE == ROW_FWD_R2C) {
+    } else if (MODE == ROW_WIENER_1D || MODE == ROW_FWD_R2C || MODE == ROW_FILTER_1D) {
       cp_async4(stage + 2 * idx, a.fin + (size_t)(2 * q) * a.ldf + c);
       if (2 * q + 1 < a.img_rows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)(2 * q + 1) * a.ldf + c);
     }
@@ -207,7 +277,9 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
           if (2 * q + 1 < a.img_rows && ta1 < a.kh && tb < a.kw) v.z = __ldg(a.taps + ta1 * a.kw + tb);
         } else if (MODE == ROW_FWD_REAL) {
           v.x = fmaxf(stage[idx], a.floor_);
-        } else {  // ROW_WIENER_1D: sequence q packs image rows 2q and 2q+1
+        } else if (MODE == ROW_KSPEC) {  // the gain; the spectrum is in natural order
+          v = wiener_gain1(__ldg(&a.spec[c]), a.K);
+        } else {  // ROW_WIENER_1D, ROW_FILTER_1D: sequence q packs image rows 2q and 2q+1
           v.x = fmaxf(stage[2 * idx], a.floor_);
           if (2 * q + 1 < a.img_rows) v.z = fmaxf(stage[2 * idx + 1], a.floor_);
         }
@@ -218,6 +290,11 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
   __syncthreads();
   if (MODE == ROW_INV_REAL || MODE == ROW_INV_C2R) {
     dft_inv_ff(x, R, 1, M, a.D, false);
+  } else if (MODE == ROW_FILTER_1D) {
+    filter_ff(x, R, 1, M, a.D, false, a.kspec, 1, 0, R);
+  } else if (MODE == ROW_KSPEC) {
+    dft_inv_ff(x, R, 1, M, a.D, false);
+    kernel_spectrum_ff(x, R, 1, M, a.D, false);
   } else {
     dft_fwd_ff(x, R, 1, M, a.D, false);
     if (MODE == ROW_WIENER_1D) {
@@ -229,7 +306,13 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
       dft_inv_ff(x, R, 1, M, a.D, false);
     }
   }
-  if constexpr (MODE == ROW_FWD_R2C || MODE == ROW_PSF_R2C) {
+  if constexpr (MODE == ROW_KSPEC) {  // all M elements of each filter spectrum
+    for (int idx = threadIdx.x; idx < R * M; idx += blockDim.x) {
+      const int r = idx / M, m = idx - r * M;
+      const int q = q0 + r;
+      if (q < a.nrows) a.cbuf[(size_t)q * a.ldc + m] = x[r * M + m];
+    }
+  } else if constexpr (MODE == ROW_FWD_R2C || MODE == ROW_PSF_R2C) {
     const int Nh = N / 2 + 1;
     for (int idx = threadIdx.x; idx < R * Nh; idx += blockDim.x) {
       const int r = idx / Nh, k = idx - r * Nh;
@@ -288,12 +371,15 @@ __device__ __forceinline__ void cols_body(float4* smem4, const FftArgs& a, int c
   const int N = a.D.N, M = dft_len(a.D);
   float4* x = smem4;
   float* stage = (float*)(x + M * C);  // COL_WIENER_1D_REAL: 2*C real columns
-  const int nseq_total = (MODE == COL_WIENER_1D_REAL) ? (a.nrows + 1) / 2 : a.nrows;
+  constexpr bool REAL1D = MODE == COL_WIENER_1D_REAL || MODE == COL_FILTER_1D_REAL;
+  const int nseq_total = REAL1D ? (a.nrows + 1) / 2 : a.nrows;
   for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
     const int k = idx / C, c = idx - k * C;
     const int q = c0 + c;
     if (q >= nseq_total) continue;
-    if (MODE == COL_WIENER_1D_REAL) {
+    if (MODE == COL_KSPEC) {
+      x[idx] = wiener_gain1(__ldg(&a.spec[(size_t)k * a.ldspec + q]), a.K);
+    } else if (REAL1D) {
       cp_async4(stage + 2 * idx, a.fin + (size_t)k * a.ldf + 2 * q);
       if (2 * q + 1 < a.nrows) cp_async4(stage + 2 * idx + 1, a.fin + (size_t)k * a.ldf + 2 * q + 1);
     } else {
@@ -307,7 +393,7 @@ __device__ __forceinline__ void cols_body(float4* smem4, const FftArgs& a, int c
     const int q = c0 + c;
     if (q >= nseq_total) {
       x[idx] = zzero();
-    } else if (MODE == COL_WIENER_1D_REAL) {
+    } else if (REAL1D) {
       float4 v = zzero();
       v.x = fmaxf(stage[2 * idx], a.floor_);
       if (2 * q + 1 < a.nrows) v.z = fmaxf(stage[2 * idx + 1], a.floor_);
@@ -315,8 +401,22 @@ __device__ __forceinline__ void cols_body(float4* smem4, const FftArgs& a, int c
     }
   }
   __syncthreads();
-  dft_fwd_ff(x, C, C, 1, a.D, true);
-  if (MODE != COL_FWD) {
+  if (MODE == COL_KSPEC) {
+    dft_inv_ff(x, C, C, 1, a.D, true);
+    kernel_spectrum_ff(x, C, C, 1, a.D, true);
+    for (int idx = threadIdx.x; idx < M * C; idx += blockDim.x) {
+      const int m = idx / C, c = idx - m * C;
+      if (c0 + c < nseq_total) a.cbuf[(size_t)m * a.ldc + c0 + c] = x[idx];
+    }
+    return;
+  }
+  if (MODE == COL_FILTER)
+    filter_ff(x, C, C, 1, a.D, true, a.kspec + c0, a.ldk, 1, nseq_total - c0);
+  else if (MODE == COL_FILTER_1D_REAL)
+    filter_ff(x, C, C, 1, a.D, true, a.kspec, 1, 0, C);
+  else
+    dft_fwd_ff(x, C, C, 1, a.D, true);
+  if (MODE == COL_WIENER || MODE == COL_WIENER_1D_REAL) {
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
       const int k = idx / C, c = idx - k * C;
       const int q = c0 + c;
@@ -332,7 +432,7 @@ __device__ __forceinline__ void cols_body(float4* smem4, const FftArgs& a, int c
     const int q = c0 + c;
     if (q >= nseq_total) continue;
     const float4 v = x[idx];
-    if (MODE == COL_WIENER_1D_REAL) {
+    if (REAL1D) {
       a.uout[(size_t)k * a.ldu + 2 * q] = fmaxf(ff_round(ff_mul(re_(v), a.scale)), a.floor_);
       if (2 * q + 1 < a.nrows)
         a.uout[(size_t)k * a.ldu + 2 * q + 1] = fmaxf(ff_round(ff_mul(im_(v), a.scale)), a.floor_);
@@ -392,7 +492,7 @@ static cudaError_t launch_rows(FftArgs a, cudaStream_t s) {
 template <int MODE, int C>
 static cudaError_t launch_cols_c(FftArgs a, int nseq, cudaStream_t s) {
   const int M = dft_len(a.D);
-  const size_t st = (MODE == COL_WIENER_1D_REAL) ? 1 : 0;  // real staging only for packed real columns
+  const size_t st = (MODE == COL_WIENER_1D_REAL || MODE == COL_FILTER_1D_REAL) ? 1 : 0;  // packed real columns
   const size_t smem = (size_t)C * M * sizeof(float4) + st * 2 * C * a.D.N * sizeof(float);
   cudaError_t e = set_dyn_smem(k_fft_cols<MODE, C>, smem);
   if (e != cudaSuccess) return e;
@@ -415,6 +515,26 @@ static cudaError_t launch_cols(FftArgs a, int nseq, cudaStream_t s) {
   if (M <= 2048) return launch_cols_c<MODE, 4>(a, nseq, s);
   return launch_cols_c<MODE, 2>(a, nseq, s);
 }
+
+static int dft_len_host(int N) {
+  int logM, M3;
+  dft_plan(N, &logM, &M3);
+  int M = 1 << logM;
+  while (M3-- > 0) M *= 3;
+  return M;
+}
+
+size_t wiener_kspec_elems(int H, int W, int kh, int kw) {
+  if (kh == 1) return is_pow2(W) ? 0 : (size_t)dft_len_host(W);
+  if (kw == 1) return is_pow2(H) ? 0 : (size_t)dft_len_host(H);
+  return is_pow2(H) ? 0 : (size_t)(W / 2 + 1) * dft_len_host(H);
+}
+
+// Filter spectra of a Wiener filter (kernel_spectrum_ff) from the PSF
+// spectrum `spec` and K: one for a one-axis PSF along the axis of D, one per
+// half-spectrum column (pitch W/2 + 1) for a 2D PSF.  Untimed set-up.
+static cudaError_t prepare_kspec(const float4* spec, int H, int W, int kh, int kw, float K, const Dft1ff& D,
+                                 float4* kspec, cudaStream_t s);
 
 // Fill the tables of a length-N axis in `tab` (dft_table_elems(N) float4s).
 // `ff` receives the float-float descriptor, `f32` (optional) the FP32
@@ -510,6 +630,20 @@ cudaError_t round_spectrum(const float4* in, float2* out, int H, int W, cudaStre
   return cudaGetLastError();
 }
 
+static cudaError_t prepare_kspec(const float4* spec, int H, int W, int kh, int kw, float K, const Dft1ff& D,
+                                 float4* kspec, cudaStream_t s) {
+  FftArgs a = {};
+  a.spec = spec; a.K = K; a.D = D; a.cbuf = kspec;
+  if (kh == 1 || kw == 1) {
+    a.nrows = 1; a.ldc = dft_len(D);
+    return launch_rows<ROW_KSPEC>(a, s);
+  }
+  const int Wh = W / 2 + 1;
+  a.ldspec = Wh; a.nrows = Wh; a.ldc = Wh;
+  (void)H;
+  return launch_cols<COL_KSPEC>(a, Wh, s);
+}
+
 static float2 ff_const(double v) {
   const float hi = (float)v;
   return make_float2(hi, (float)(v - (double)hi));
@@ -517,7 +651,7 @@ static float2 ff_const(double v) {
 
 // Set-up part of the Wiener filter: transform tables and the PSF spectrum
 // (depends on the taps and the image size only).
-cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, void* ws, const WsLayout& L,
+cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, float K, void* ws, const WsLayout& L,
                            WienerState* st, cudaStream_t s) {
   char* base = (char*)ws;
   float4* spec = (float4*)(base + L.spec);
@@ -539,6 +673,13 @@ cudaError_t wiener_prepare(int H, int W, const float* taps, int kh, int kw, void
   } else {
     if ((e = run_psf_spectrum_half(taps, kh, kw, H, W, spec, S.DW, S.DH, s)) != cudaSuccess) return e;
   }
+  // the filtering pass along a non-power-of-two axis as one circular
+  // convolution (its filter spectra depend on K, fixed here)
+  if (wiener_kspec_elems(H, W, kh, kw) > 0) {
+    float4* kspec = (float4*)(base + L.kspec);
+    if ((e = prepare_kspec(spec, H, W, kh, kw, K, kh == 1 ? S.DW : S.DH, kspec, s)) != cudaSuccess) return e;
+    S.kspec = kspec;
+  }
   *st = S;
   return cudaSuccess;
 }
@@ -552,17 +693,18 @@ cudaError_t wiener_apply(const float* f, float* u0, int ld, float K, float floor
   const int H = S.H, W = S.W;
   if (S.kh == 1) {
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = S.DW;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.kspec = S.kspec; b.D = S.DW;
     b.nrows = (H + 1) / 2; b.img_rows = H;
     b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / W);
-    return launch_rows<ROW_WIENER_1D>(b, s);
+    return S.kspec ? launch_rows<ROW_FILTER_1D>(b, s) : launch_rows<ROW_WIENER_1D>(b, s);
   }
   if (S.kw == 1) {
     FftArgs b = {};
-    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.D = S.DH;
+    b.fin = f; b.ldf = ld; b.uout = u0; b.ldu = ld; b.spec = spec; b.kspec = S.kspec; b.D = S.DH;
     b.nrows = W;
     b.K = K; b.floor_ = floor_; b.scale = ff_const(1.0 / H);
-    return launch_cols<COL_WIENER_1D_REAL>(b, (W + 1) / 2, s);
+    return S.kspec ? launch_cols<COL_FILTER_1D_REAL>(b, (W + 1) / 2, s)
+                   : launch_cols<COL_WIENER_1D_REAL>(b, (W + 1) / 2, s);
   }
   // real rows in pairs; only the W/2 + 1 columns of the Hermitian half
   // spectrum go through the column pass
@@ -574,7 +716,9 @@ cudaError_t wiener_apply(const float* f, float* u0, int ld, float K, float floor
   if ((e = launch_rows<ROW_FWD_R2C>(d, s)) != cudaSuccess) return e;
   FftArgs g = {};
   g.cbuf = work; g.ldc = Wh; g.spec = spec; g.ldspec = Wh; g.nrows = Wh; g.D = S.DH; g.K = K;
-  if ((e = launch_cols<COL_WIENER>(g, Wh, s)) != cudaSuccess) return e;
+  g.kspec = S.kspec; g.ldk = Wh;
+  if ((e = S.kspec ? launch_cols<COL_FILTER>(g, Wh, s) : launch_cols<COL_WIENER>(g, Wh, s)) != cudaSuccess)
+    return e;
   FftArgs o = {};
   o.cbuf = work; o.ldc = Wh; o.uout = u0; o.ldu = ld; o.nrows = (H + 1) / 2; o.img_rows = H; o.D = S.DW;
   o.floor_ = floor_; o.scale = ff_const(1.0 / ((double)H * (double)W));
@@ -586,7 +730,7 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
                        cudaStream_t s) {
   (void)status;
   WienerState S;
-  cudaError_t e = wiener_prepare(H, W, taps, kh, kw, ws, L, &S, s);
+  cudaError_t e = wiener_prepare(H, W, taps, kh, kw, K, ws, L, &S, s);
   if (e != cudaSuccess) return e;
   return wiener_apply(f, u0, ld, K, floor_, ws, L, S, s);
 }
@@ -596,7 +740,10 @@ cudaError_t run_wiener(const float* f, float* u0, int H, int W, int ld, const fl
 // transform stage), each CTA working on one row (pair) or column group of
 // one image with that image's own transform lengths.
 // ---------------------------------------------------------------------------
-enum { WB_ROW_1D = 0, WB_ROW_FWD = 1, WB_COL_1D = 2, WB_COL_2D = 3, WB_ROW_INV = 4, WB_STAGES = 5 };
+// The *_F stages are the filtering passes along non-power-of-two axes in
+// their circular-convolution form (filter spectra prepared with the plan).
+enum { WB_ROW_1D = 0, WB_ROW_FWD = 1, WB_COL_1D = 2, WB_COL_2D = 3, WB_ROW_INV = 4, WB_ROW_1D_F = 5,
+       WB_COL_1D_F = 6, WB_COL_2D_F = 7, WB_STAGES = 8 };
 // Column passes: columns per CTA by transform length, in classes launched
 // separately: 2 (the longest transforms: 4 per CTA left one CTA per SM,
 // 36.0 against 30.8 ms for batch512's Wiener), 4 or 8 while C x M <= 4096,
@@ -640,7 +787,9 @@ WienerBatch* wiener_batch_new() { return new WienerBatch(); }
 size_t wiener_job_bytes() { return sizeof(FftArgs); }
 void wiener_batch_delete(WienerBatch* b) { delete b; }
 
-// Precompute the image's PSF spectrum (untimed set-up) and append its jobs.
+// Precompute the image's PSF spectrum and, for a filtering pass along a
+// non-power-of-two axis, its filter spectra (untimed set-up), and append
+// its jobs.
 cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t s) {
   cudaError_t e;
   const int H = im.H, W = im.W;
@@ -648,30 +797,40 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
     FftArgs a = {};
     a.taps = im.taps; a.kh = 1; a.kw = im.kw; a.nrows = 1; a.D = (*im.pDW); a.cbuf = im.spec; a.ldc = W;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+    if (im.kspec && (e = prepare_kspec(im.spec, H, W, 1, im.kw, im.K, *im.pDW, im.kspec, s)) != cudaSuccess)
+      return e;
     FftArgs j = {};
-    j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.D = (*im.pDW);
+    j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.kspec = im.kspec;
+    j.D = (*im.pDW);
     j.nrows = (H + 1) / 2; j.img_rows = H; j.K = im.K; j.floor_ = im.floor_; j.scale = ff_const(1.0 / W);
-    const int id = (int)b->jobs[WB_ROW_1D].size();
-    add_row_items(b, WB_ROW_1D, id, j, W);
-    b->jobs[WB_ROW_1D].push_back(j);
+    const int st = im.kspec ? WB_ROW_1D_F : WB_ROW_1D;
+    const int id = (int)b->jobs[st].size();
+    add_row_items(b, st, id, j, W);
+    b->jobs[st].push_back(j);
     return cudaSuccess;
   }
   if (im.kw == 1) {
     FftArgs a = {};
     a.taps = im.taps; a.kh = 1; a.kw = im.kh; a.nrows = 1; a.D = (*im.pDH); a.cbuf = im.spec; a.ldc = H;
     if ((e = launch_rows<ROW_PSF>(a, s)) != cudaSuccess) return e;
+    if (im.kspec && (e = prepare_kspec(im.spec, H, W, im.kh, 1, im.K, *im.pDH, im.kspec, s)) != cudaSuccess)
+      return e;
     FftArgs j = {};
-    j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.D = (*im.pDH);
+    j.fin = im.f; j.ldf = im.ld; j.uout = im.u0; j.ldu = im.ldu; j.spec = im.spec; j.kspec = im.kspec;
+    j.D = (*im.pDH);
     j.nrows = W; j.K = im.K; j.floor_ = im.floor_; j.scale = ff_const(1.0 / H);
-    const int id = (int)b->jobs[WB_COL_1D].size();
-    b->jobs[WB_COL_1D].push_back(j);
+    const int st = im.kspec ? WB_COL_1D_F : WB_COL_1D;
+    const int id = (int)b->jobs[st].size();
+    b->jobs[st].push_back(j);
     const int nseq = (W + 1) / 2, M = dft_len(*im.pDH), k = col_class(M), C = col_class_c(k);
-    for (int c0 = 0; c0 < nseq; c0 += C) b->items[WB_COL_1D][k].push_back(make_int2(id, c0));
+    for (int c0 = 0; c0 < nseq; c0 += C) b->items[st][k].push_back(make_int2(id, c0));
     const size_t sm = (size_t)C * M * sizeof(float4) + (size_t)2 * C * H * sizeof(float);
-    if (sm > b->smem[WB_COL_1D][k]) b->smem[WB_COL_1D][k] = sm;
+    if (sm > b->smem[st][k]) b->smem[st][k] = sm;
     return cudaSuccess;
   }
   if ((e = run_psf_spectrum_half(im.taps, im.kh, im.kw, H, W, im.spec, (*im.pDW), (*im.pDH), s)) != cudaSuccess)
+    return e;
+  if (im.kspec && (e = prepare_kspec(im.spec, H, W, im.kh, im.kw, im.K, *im.pDH, im.kspec, s)) != cudaSuccess)
     return e;
   const int Wh = W / 2 + 1, Hp = (H + 1) / 2;
   FftArgs d = {};
@@ -679,20 +838,22 @@ cudaError_t wiener_batch_add(WienerBatch* b, const WienerImage& im, cudaStream_t
   d.floor_ = im.floor_;
   FftArgs g = {};
   g.cbuf = im.work; g.ldc = Wh; g.spec = im.spec; g.ldspec = Wh; g.nrows = Wh; g.D = (*im.pDH); g.K = im.K;
+  g.kspec = im.kspec; g.ldk = Wh;
+  const int gst = im.kspec ? WB_COL_2D_F : WB_COL_2D;
   FftArgs o = {};
   o.cbuf = im.work; o.ldc = Wh; o.uout = im.u0; o.ldu = im.ldu; o.nrows = Hp; o.img_rows = H; o.D = (*im.pDW);
   o.floor_ = im.floor_; o.scale = ff_const(1.0 / ((double)H * (double)W));
-  const int i1 = (int)b->jobs[WB_ROW_FWD].size(), i2 = (int)b->jobs[WB_COL_2D].size(),
+  const int i1 = (int)b->jobs[WB_ROW_FWD].size(), i2 = (int)b->jobs[gst].size(),
             i3 = (int)b->jobs[WB_ROW_INV].size();
   add_row_items(b, WB_ROW_FWD, i1, d, W);
   add_row_items(b, WB_ROW_INV, i3, o, W);
   b->jobs[WB_ROW_FWD].push_back(d);
-  b->jobs[WB_COL_2D].push_back(g);
+  b->jobs[gst].push_back(g);
   b->jobs[WB_ROW_INV].push_back(o);
   const int MH = dft_len(*im.pDH), kc = col_class(MH), CC = col_class_c(kc);
-  for (int c0 = 0; c0 < Wh; c0 += CC) b->items[WB_COL_2D][kc].push_back(make_int2(i2, c0));
+  for (int c0 = 0; c0 < Wh; c0 += CC) b->items[gst][kc].push_back(make_int2(i2, c0));
   const size_t smc = (size_t)CC * MH * sizeof(float4);
-  if (smc > b->smem[WB_COL_2D][kc]) b->smem[WB_COL_2D][kc] = smc;
+  if (smc > b->smem[gst][kc]) b->smem[gst][kc] = smc;
   return cudaSuccess;
 }
 
@@ -764,9 +925,12 @@ static cudaError_t launch_cols_batch(const WienerBatch* b, int stage, cudaStream
 cudaError_t wiener_batch_run(const WienerBatch* b, cudaStream_t s) {
   cudaError_t e;
   if ((e = launch_rows_batch<ROW_WIENER_1D>(b, WB_ROW_1D, s)) != cudaSuccess) return e;
+  if ((e = launch_rows_batch<ROW_FILTER_1D>(b, WB_ROW_1D_F, s)) != cudaSuccess) return e;
   if ((e = launch_cols_batch<COL_WIENER_1D_REAL>(b, WB_COL_1D, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_FILTER_1D_REAL>(b, WB_COL_1D_F, s)) != cudaSuccess) return e;
   if ((e = launch_rows_batch<ROW_FWD_R2C>(b, WB_ROW_FWD, s)) != cudaSuccess) return e;
   if ((e = launch_cols_batch<COL_WIENER>(b, WB_COL_2D, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_FILTER>(b, WB_COL_2D_F, s)) != cudaSuccess) return e;
   return launch_rows_batch<ROW_INV_C2R>(b, WB_ROW_INV, s);
 }
 
