@@ -43,6 +43,18 @@ METRIC = "RRRL Mpixel*iter/s"
 UNIT = "Mpx*iter/s"
 
 
+def forms_arg(text):
+    """--forms: "auto" or [fft<T>/|nofft/]<dense|groups>/<all|rule|none>."""
+    if text == "auto":
+        return text
+    parts = text.split("/")
+    ok = (len(parts) in (2, 3) and parts[-2] in ("dense", "groups") and parts[-1] in ("all", "rule", "none")
+          and (len(parts) == 2 or parts[0] == "nofft" or (parts[0].startswith("fft") and parts[0][3:].isdigit())))
+    if not ok:
+        raise argparse.ArgumentTypeError(f"bad --forms value {text!r}")
+    return text
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -62,12 +74,11 @@ def parse():
     ap.add_argument("--images", type=int, default=512,
                     help="batch512 only: deblur an evenly spaced subset of this many of the 512 images "
                          "(a smaller case of the same kernels, for profiling)")
-    ap.add_argument("--forms", choices=["auto"] + [f"{t}{d}/{w}" for t in ("", "nofft/") for d in ("dense", "groups")
-                                                    for w in ("all", "rule", "none")], default="auto",
+    ap.add_argument("--forms", default="auto", type=forms_arg,
                     help="batch512 only: tile forms timed (auto: chosen by db_batch_autotune before capture) "
-                         "or fixed as [nofft/]<2D sums>/<one-axis register windows>, e.g. dense/all (FFT tiles "
-                         "by their size rule; nofft/: none) (for profiling: the autotuner's own runs are then "
-                         "not launched)")
+                         "or fixed as [fft<T>/|nofft/]<2D sums>/<one-axis register windows>, e.g. fft169/dense/all "
+                         "(FFT tiles for 2D PSFs with kh*kw >= T; no prefix: the default threshold; nofft/: none) "
+                         "(for profiling: the autotuner's own runs are then not launched)")
     ap.add_argument("--rf", choices=["log1p", "lut"], default="log1p",
                     help="evaluation of r_f: log1p (default) or the lookup table of Sec. 4.1")
     return ap.parse_args()
@@ -497,7 +508,8 @@ def run_batch(args, world, rank, local):
     if args.forms != "auto":
         parts = args.forms.split("/")
         d, w = parts[-2:]
-        fixed = {"fft": -1 if parts[0] != "nofft" else 0, "dense": d == "dense", "windows": w}
+        fft = -1 if len(parts) == 2 else 0 if parts[0] == "nofft" else int(parts[0][3:])
+        fixed = {"fft": fft, "dense": d == "dense", "windows": w}
         set_batch_forms(fixed)
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()

@@ -53,12 +53,15 @@ constexpr int kGroups = 512;        // groups of 8 elements per pass
 constexpr int kUS = 72;             // row stride of the staged u (update phase)
 constexpr int kThreads = 256;       // threads of a CTA running the bodies
 constexpr int kSR = 4;              // rows of an update strip
+constexpr int kTS = 10;             // row stride of the twiddle table (float2): the 16-byte
+                                    // reads of the eight rows fall on distinct banks
+constexpr int kTwSlots = 8 * kTS;   // float2 slots of the twiddle table
 
 __device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
 
-// Twiddle table of the top passes: tw[8 j + s] = w^(j bitrev3(s)),
+// Twiddle table of the top passes: tw[kTS j + s] = w^(j bitrev3(s)),
 // w = exp(-2 pi i / 64), the factor of output slot s of group j (slot s of
-// dif8 holds DFT index bitrev3(s)); one CTA-wide table of 64 entries.
+// dif8 holds DFT index bitrev3(s)); one CTA-wide table of 8 rows.
 __device__ __forceinline__ void make_twiddles(float2* tw) {
   const int t = tid_flat();
   if (t < kN) {
@@ -66,12 +69,12 @@ __device__ __forceinline__ void make_twiddles(float2* tw) {
     const int e = ((sl & 1) << 2) | (sl & 2) | (sl >> 2);
     float sn, cs;
     sincospif(-(float)(j * e) / 32.0f, &sn, &cs);
-    tw[t] = make_float2(cs, sn);
+    tw[kTS * j + sl] = make_float2(cs, sn);
   }
 }
 
 __device__ __forceinline__ void group_twiddles(const float2* tw, int j, float2 (&w)[8]) {
-  const float4* t4 = reinterpret_cast<const float4*>(tw + 8 * j);
+  const float4* t4 = reinterpret_cast<const float4*>(tw + kTS * j);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const float4 v = t4[k];
@@ -284,7 +287,7 @@ __host__ __device__ inline int tile_ow(int kw) { return kN + 1 - kw; }
 
 // Shared memory of the bodies (bytes): twiddles, window, staged u.
 __host__ __device__ inline int staged_u_rows(int kh) { return ((tile_oh(kh) + kSR - 1) / kSR) * kSR + 4; }
-__host__ __device__ inline size_t smem_q() { return (size_t)(kN + kPos) * sizeof(float2); }
+__host__ __device__ inline size_t smem_q() { return (size_t)(kTwSlots + kPos) * sizeof(float2); }
 __host__ __device__ inline size_t smem_update(int kh) {
   return smem_q() + (size_t)staged_u_rows(kh) * kUS * sizeof(float);
 }
@@ -300,7 +303,7 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
                                        const float2* __restrict__ spec, int kh, int kw, const RrlParams& p, int i0,
                                        int j0, Dep dep = Dep()) {
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* A = tw + kN;
+  float2* A = tw + kTwSlots;
   make_twiddles(tw);
   const int dy = kh - 1 - (kh >> 1), dx = kw - 1 - (kw >> 1);
   const int OH = tile_oh(kh), OW = tile_ow(kw);
@@ -322,22 +325,21 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
         const float b = has_b ? row[min(max(xb + c, 0), W - 1)] : 0.0f;
         return make_float2(a, b);
       },
-      [&](int r, int c, float2 v) {
-        const int oj = c - dx;
-        const int i = i0 + r - dy;
-        if (oj < 0 || oj >= OW || i >= H) return;
-        const int ja = j0 + oj, jb = ja + OW;
-        if (ja < W) {
-          const float2 q = weighted_residual(v.x, fmaxf(__ldg(f + (size_t)i * ldf + ja), p.floor), p);
-          qe[(size_t)i * ldqp + ja] = q.x;
-          qw[(size_t)i * ldqp + ja] = q.y;
-        }
-        if (has_b && jb < W) {
-          const float2 q = weighted_residual(v.y, fmaxf(__ldg(f + (size_t)i * ldf + jb), p.floor), p);
-          qe[(size_t)i * ldqp + jb] = q.x;
-          qw[(size_t)i * ldqp + jb] = q.y;
-        }
-      });
+      // each (bA, bB) back into the slot its group read it from
+      [&](int r, int c, float2 v) { A[r * kRS + c + (c >> 4)] = v; });
+  __syncthreads();
+  // (e, W) over both tiles' outputs as one row of 2 OW columns: consecutive
+  // threads take consecutive image columns
+  const int nr = min(OH, H - i0), nc = min(2 * OW, W - j0);
+  for (int item = tid_flat(); item < nr * nc; item += kThreads) {
+    const int oi = item / nc, oj2 = item - oi * nc;
+    const int second = oj2 >= OW, c = dx + oj2 - (second ? OW : 0);
+    const float2 v = A[(dy + oi) * kRS + c + (c >> 4)];
+    const int i = i0 + oi, j = j0 + oj2;
+    const float2 q = weighted_residual(second ? v.y : v.x, fmaxf(__ldg(f + (size_t)i * ldf + j), p.floor), p);
+    qe[(size_t)i * ldqp + j] = q.x;
+    qw[(size_t)i * ldqp + j] = q.y;
+  }
 }
 
 // Delta, B from planar q, the diffusion term and the update on the tile at
@@ -353,7 +355,7 @@ __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float
                                             int W, const float2* __restrict__ spec, int kh, int kw,
                                             const RrlParams& p, int* status, int i0, int j0, Dep dep = Dep()) {
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* A = tw + kN;
+  float2* A = tw + kTwSlots;
   float* us = reinterpret_cast<float*>(A + kPos);
   make_twiddles(tw);
   const int cy = kh >> 1, cx = kw >> 1;

@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(256) k_prepare_taps(const float* __restrict__ 
 // fft_tile_shape, one CTA.  Raw taps: k_prepare_taps validates them.
 __global__ void __launch_bounds__(256) k_prepare_fft_spec(const float* __restrict__ taps, int kh, int kw,
                                                          float2* __restrict__ spec) {
-  __shared__ float2 tw[ftile::kN];
-  __shared__ float2 A[ftile::kPos];
+  __shared__ __align__(16) float2 tw[ftile::kTwSlots];  // read as float4
+  __shared__ __align__(16) float2 A[ftile::kPos];
   ftile::psf_spectrum(A, tw, taps, kh, kw, spec);
 }
 
