@@ -232,6 +232,17 @@ def case_gauss2048(H: int = 2048, W: int = 2048, iters: int = 30) -> Case:
     return Case("gauss2048", g, f, h, iters, Params(K=0.006, conv="periodic"))
 
 
+def case_gauss3072(H: int = 3072, W: int = 3072, iters: int = 10) -> Case:
+    """3072x3072, 25x25 mixture of 3 Gaussians (the largest PSF of the
+    batch), sigma=2, Wiener K=0.006, 10 RRRL iterations with constant
+    continuation (spatial: the FFT tiles' workload)."""
+    rng = rng_for(5)
+    g = scene(H, W, rng).astype(np.float32)
+    h = gaussian_mixture_psf(25, rng)
+    f = degrade(g, h, 2.0, rng)
+    return Case("gauss3072", g, f, h, iters, Params(K=0.006))
+
+
 def batch_case(index: int, size_cap: int = 1024) -> Case:
     """Image `index` (0..511) of the uneven batch: sides U{128..1024};
     images 0-255 carry axis-aligned 1D motion of length U{5..41} (even
