@@ -176,10 +176,13 @@ db_status db_rrl_backward(const float* f, const float* ckpt, const float* grad_u
  * A plan (db_batch_create) precomputes every transform table, PSF spectrum
  * and tap list and uploads the work tables into the workspace; running it
  * (db_batch_run) enqueues only launches and memsets, so it can be captured
- * in a CUDA graph and replayed.  The run is five batched Wiener launches and
- * one cooperative persistent launch for all RRRL iterations of all images,
- * whose grid barriers wait a bounded time (db_set_spin_limit) and raise
- * DB_FLAG_TIMEOUT instead of hanging.  The plan holds pointers into the
+ * in a CUDA graph and replayed.  The run is the batched Wiener launches (one
+ * per transform stage and column class) and one cooperative persistent
+ * launch for all RRRL iterations of all images.  By default its phases are
+ * separated by grid barriers; db_set_batch_order selects a dependency order
+ * instead (a tile waits only for the previous phase of its own image).
+ * Every wait is bounded (db_set_spin_limit) and raises DB_FLAG_TIMEOUT
+ * instead of hanging.  The plan holds pointers into the
  * workspace and to the images: keep them alive and unchanged in shape while
  * the plan is used; pixel values may change between runs. */
 typedef struct {
@@ -267,9 +270,21 @@ db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_hos
 int db_batch_stream_parts(const db_batch_stream* b);
 void db_batch_stream_destroy(db_batch_stream* b);
 
-/* Clock-cycle budget of every bounded device wait (grid barriers of the
- * batch kernel); default 4e9 (about two seconds). */
+/* Clock-cycle budget of every bounded device wait (the batch kernel's
+ * dependency waits and grid barriers, the flow schedule's tile waits);
+ * default 4e9 (about two seconds). */
 db_status db_set_spin_limit(long long cycles);
+
+/* Order of the batch kernel's tiles (no counterpart in the paper): 0 one
+ * task list over all iterations, each tile waiting only until the previous
+ * phase of its own image is complete (per-image counters), so the phases of
+ * different images overlap; 1 (the default) every phase of every image
+ * before a grid barrier, then the next phase.  Both give the same bits.  On
+ * B300 the barrier form is faster for batches of many small tiles: each
+ * dependency costs a barrier, a release and an acquire per tile.
+ * Process-wide; batches take it when they are created.  DB_ERR_ARG for other
+ * values. */
+db_status db_set_batch_order(int order);
 
 /* Allocation-free RRRL iterations (no counterpart in the paper; an interface
  * convenience).  Some callers cannot allocate device memory at run time:

@@ -503,6 +503,14 @@ def set_spin_limit(cycles: int):
     _check(_lib.load().db_set_spin_limit(int(cycles)), "db_set_spin_limit")
 
 
+def set_batch_order(name: str):
+    """Tile order of batches created after the call: "barrier" (default:
+    phases separated by grid barriers) or "dependency" (each tile waits only
+    for its own image's previous phase).  Both give the same bits."""
+    code = {"dependency": 0, "barrier": 1}[name]
+    _check(_lib.load().db_set_batch_order(code), "db_set_batch_order")
+
+
 def rrl_iterate_noalloc(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, params: Params,
                         iters: int, *, kind: str = "general", status: torch.Tensor | None = None):
     """`iters` RRRL iterations in place on u without any device allocation:

@@ -70,14 +70,16 @@ def test_batch_graph_capture_and_replay(lib):
     b.close()
 
 
-def test_batch_bounded_barrier_reports_timeout(lib):
-    """With a zero wait budget the persistent kernel's grid barriers give up
-    at once: the run returns, the status word carries the time-out flag and
-    the context stays usable."""
+@pytest.mark.parametrize("order", ["dependency", "barrier"])
+def test_batch_bounded_barrier_reports_timeout(lib, order):
+    """With a zero wait budget the persistent kernel's waits (per-image
+    dependency waits, or grid barriers) give up at once: the run returns,
+    the status word carries the time-out flag and the context stays usable."""
     cases = small_batch([20, 280], cap=200)
     fs = [cuda(c.f) for c in cases]
     hs = [cuda(c.h) for c in cases]
     lib.set_spin_limit(0)
+    lib.set_batch_order(order)
     try:
         b = lib.Batch(fs, hs, [c.params for c in cases], 5, kinds=[c.psf_kind for c in cases])
         b.ws.reset_status()
@@ -87,6 +89,7 @@ def test_batch_bounded_barrier_reports_timeout(lib):
         b.close()
     finally:
         lib.set_spin_limit(4_000_000_000)
+        lib.set_batch_order("barrier")
     if flags == 0:
         pytest.skip("every CTA reached each barrier before checking its budget")
     assert flags & 0x4, f"flags 0x{flags:x}"
@@ -161,3 +164,23 @@ def test_batch_autotune_keeps_the_results_of_the_chosen_forms(lib):
         d = (u.double().cpu() - ref).abs()
         assert float(d.max()) <= MAX_ABS and float(d.pow(2).mean().sqrt()) <= RMS, c.name
     b.close()
+
+
+def test_batch_dependency_order_equals_barrier_order(lib):
+    """The dependency-ordered run (each tile waits for its own image's
+    previous phase) and the run with grid barriers between phases give the
+    same bits on a mix of 1D, dense 2D and FFT-tile images."""
+    cases = small_batch([0, 1, 2, 3, 256, 257, 258, 300, 301, 400], cap=320)
+    fs = [cuda(c.f) for c in cases]
+    hs = [cuda(c.h) for c in cases]
+    outs = {}
+    try:
+        for order in ("barrier", "dependency"):
+            lib.set_batch_order(order)
+            b = lib.Batch(fs, hs, [c.params for c in cases], 6, kinds=[c.psf_kind for c in cases])
+            outs[order] = [u.clone() for u in b.run()]
+            b.close()
+    finally:
+        lib.set_batch_order("barrier")
+    for c, a, d in zip(cases, outs["barrier"], outs["dependency"]):
+        assert torch.equal(a, d), c.name
