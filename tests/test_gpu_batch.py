@@ -122,6 +122,31 @@ def test_uneven_batch_512_subset_against_oracle(lib):
     print(f"batch512 subset worst max-abs {worst[0]:.3e} rms {worst[1]:.3e}")
 
 
+def test_uneven_batch_512_all_fft_tiles_against_oracle(lib):
+    """The full batch with FFT tiles for every 2D PSF (the lowest threshold
+    db_batch_autotune can choose: 7x7 up), in one run; 12 of its 2D images,
+    one of each size class and the smallest and largest images, against the
+    oracle."""
+    cases = [synth.batch_case(i) for i in range(512)]
+    fs = [cuda(c.f) for c in cases]
+    lib.set_fft_tiles(1)
+    try:
+        outs = lib.deblur_batch(fs, [cuda(c.h) for c in cases], [c.params for c in cases], 10,
+                                kinds=[c.psf_kind for c in cases])
+    finally:
+        lib.set_fft_tiles(0)
+    by_size = {}
+    for i in range(256, 512):
+        by_size.setdefault(cases[i].h.shape[0], i)
+    px = sorted(range(256, 512), key=lambda i: cases[i].f.size)
+    pick = sorted(set(by_size.values()) | {px[0], px[-1]})
+    for i in pick:
+        _, ref = oracle.wr3l(cases[i].f, cases[i].h, cases[i].params, 10)
+        d = (outs[i].double().cpu() - ref).abs()
+        m, r = float(d.max()), float(d.pow(2).mean().sqrt())
+        assert m <= MAX_ABS and r <= RMS, f"{cases[i].name} {cases[i].f.shape} {cases[i].h.shape}: {m:.3e} {r:.3e}"
+
+
 def test_batch_plans_with_different_shared_memory_coexist(lib):
     """A plan made after another one with smaller tiles (less shared memory
     per CTA) must not stop the earlier plan from launching."""
