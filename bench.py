@@ -160,10 +160,10 @@ LINE1024_FLOW_ITER_DRAM_BYTES = (8.489728e6 + 1.274112e6) / 20
 
 
 # DRAM bytes per pixel and iteration of k_rrl_batch on batch512
-# (dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, 55.88 GB,
-# over its 1.735e9 pixel-iterations; profiles/batch512_launches.md).  Set to None
-# when the kernel changes, until it is captured again.
-BATCH_DRAM_BYTES_PER_PX_ITER = None
+# (dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, 55.93 GB,
+# over its 1.735e9 pixel-iterations, forms fft81/dense/all as the autotuner chose
+# them).  Set to None when the kernel changes, until it is captured again.
+BATCH_DRAM_BYTES_PER_PX_ITER = 32.23
 
 
 def pinned_copy(array):
