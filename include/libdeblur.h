@@ -13,13 +13,21 @@
  *   - Images are float32, row-major, H rows x W columns, with a row pitch of
  *     `ld` elements (ld >= W).  Pixel (i, j) is at ptr[i*ld + j].
  *   - All image, tap, workspace and status pointers are DEVICE pointers owned
- *     by the caller, except the host images of db_plan_run_host.  The library
- *     allocates no device memory (db_host_alloc hands out page-locked host
- *     memory on request; plans and batches keep small host-side records);
- *     scratch space is the caller's workspace `ws` of `ws_bytes` bytes (see
- *     db_workspace_bytes), which must be 256-byte aligned.
+ *     by the caller, except the host images of db_plan_run_host and
+ *     db_batch_stream_run_host.  The library allocates no device memory of
+ *     its own for data: scratch space is the caller's workspace `ws` of
+ *     `ws_bytes` bytes (see db_workspace_bytes), which must be 256-byte
+ *     aligned.  Exceptions: db_host_alloc hands out page-locked host memory
+ *     on request; plans and batches keep small host-side records;
+ *     db_plan_run_host creates a stream of the plan's own and instantiates a
+ *     CUDA graph per set of device buffers (its first call for a buffer set
+ *     must not happen inside a stream capture); db_batch_stream_create
+ *     creates two streams and events; the allocation-free entry point holds
+ *     a fixed array compiled into the library.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
- *     enqueued asynchronously; no entry point synchronises the device.
+ *     enqueued asynchronously.  Run calls never synchronise; the set-up and
+ *     tuning calls that say so (plan and batch creation, the autotuners,
+ *     settings that fill device tables) synchronise their stream.
  *   - Argument errors are returned synchronously as a db_status and nothing is
  *     enqueued.  Errors found on the device (invalid taps, non-finite values,
  *     a bounded wait that ran out) are OR-ed as DB_FLAG_* bits into the int32
