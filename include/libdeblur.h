@@ -247,9 +247,12 @@ db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws
  * The batch above, fed from and returned to HOST memory, with the transfers
  * overlapped with the work (the paper reports its host-device transfers
  * separately, Sec. 5.3; this form hides most of them).  The images are split
- * into `parts` sub-batches of about equal pixel count (longest processing
- * time first; fewer when n < parts), each an ordinary batch plan over its
- * share of the workspace.  db_batch_stream_run_host enqueues, per
+ * into `parts` sub-batches (fewer when n < parts) whose pixel counts follow
+ * the shares 1, 2, 4, 8, ..., 8, 4, 2, 1 in streaming order (largest images
+ * first, each to the sub-batch least loaded for its share), each an ordinary
+ * batch plan over its share of the workspace.  The small first and last
+ * sub-batches shorten the first upload and the last download, which no run
+ * overlaps.  db_batch_stream_run_host enqueues, per
  * sub-batch k: the copies of its host images into the descriptors' DEVICE
  * buffers f on an internal upload stream, its run on `stream` once those
  * copies have landed, and the copies of its results (the descriptors'

@@ -761,21 +761,28 @@ static db_status batch_set_forms(BatchPlan* P, int fft_min, bool dense, int wind
 // streamed batch: host images in, results out, the copies overlapped with
 // the runs of other sub-batches
 // ---------------------------------------------------------------------------
-// Longest-processing-time partition of the images into `parts` groups by
-// pixel count (ties to the lowest group); each group keeps ascending image
-// order.  The largest group load is within 4/3 of the optimum.
+// Partition of the images into `parts` groups by pixel count, in the order
+// the groups are streamed: target shares w_k = min(2^k, 2^(parts-1-k), 8)
+// (1, 2, 4, 8, ..., 8, 4, 2, 1), so that the first group's upload and the
+// last group's download, which no run overlaps, are short, while each
+// group's run still covers the next group's upload.  Images are dealt
+// largest first to the group with the least load relative to its share
+// (ties to the lowest group); each group keeps ascending image order.
+// batch512 end to end (ms) with equal shares / these shares: 8 groups
+// 68.7 / 70.5, 12 groups 69.4 / 66.7, 16 groups 70.2 / 68.4.
 static std::vector<std::vector<int>> lpt_parts(const db_image_desc* d, int n, int parts) {
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (long long)d[a].H * d[a].W > (long long)d[b].H * d[b].W;
   });
-  std::vector<long long> load(parts, 0);
+  std::vector<long long> load(parts, 0), share(parts);
+  for (int k = 0; k < parts; ++k) share[k] = std::min(std::min(1LL << std::min(k, 3), 1LL << std::min(parts - 1 - k, 3)), 8LL);
   std::vector<std::vector<int>> out(parts);
   for (int i : order) {
     int k = 0;
     for (int j = 1; j < parts; ++j)
-      if (load[j] < load[k]) k = j;
+      if ((double)load[j] / share[j] < (double)load[k] / share[k]) k = j;
     load[k] += (long long)d[i].H * d[i].W;
     out[k].push_back(i);
   }
