@@ -12,7 +12,7 @@
 // Knuth's two-sum, multiplication the FMA-based exact product (Dekker/Knuth
 // error-free transformations), each followed by a renormalising fast
 // two-sum.  The sweep structure (DIF forward to bit-reversed order, DIT
-// inverse back, radix-2^2 butterflies, Bluestein for other lengths) is the
+// inverse back, radix-4 butterflies, Bluestein for other lengths) is the
 // same as in fft.cuh.  Twiddle and chirp tables are float-float too and are
 // read from global memory (they stay in L1/L2).
 #pragma once
@@ -172,13 +172,16 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
       float4* p = x + q * ss + ((u << logN) + blk * len + j) * es;
       const int sm = m * es;
       const float4 x0 = p[0], x1 = p[sm], x2 = p[2 * sm], x3 = p[3 * sm];
-      const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
-      const float4 y0 = zadd(x0, x2), y2 = zmul(zsub(x0, x2), w1);
-      const float4 y1 = zadd(x1, x3), y3 = zmul_mi(zmul(zsub(x1, x3), w1));
-      p[0] = zadd(y0, y1);
-      p[sm] = zmul(zsub(y0, y1), w2);
-      p[2 * sm] = zadd(y2, y3);
-      p[3 * sm] = zmul(zsub(y2, y3), w2);
+      // the two radix-2 stages as one radix-4 butterfly: the 4-point DFT
+      // Y of (x0..x3), slots in bit-reversed order, Y_s times w^(s j)
+      // (three products instead of the four of two separate stages)
+      const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep), w3 = __ldg(tw + 3 * j * tstep);
+      const float4 t0 = zadd(x0, x2), t1 = zsub(x0, x2);
+      const float4 t2 = zadd(x1, x3), t3 = zmul_mi(zsub(x1, x3));
+      p[0] = zadd(t0, t2);
+      p[sm] = zmul(zsub(t0, t2), w2);
+      p[2 * sm] = zmul(zadd(t1, t3), w1);
+      p[3 * sm] = zmul(zsub(t1, t3), w3);
     }
     __syncthreads();
     logLen -= 2;
@@ -239,15 +242,16 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
       float4* p = x + q * ss + ((u << logN) + blk * len + j) * es;
       const int sm = m * es;
       const float4 z0 = p[0], z1 = p[sm], z2 = p[2 * sm], z3 = p[3 * sm];
-      const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep);
-      const float4 t1 = zmulc(z1, w2), t3 = zmulc(z3, w2);
-      const float4 y0 = zadd(z0, t1), y1 = zsub(z0, t1);
-      const float4 y2 = zadd(z2, t3), y3 = zsub(z2, t3);
-      const float4 u2 = zmulc(y2, w1), u3 = zmul_pi(zmulc(y3, w1));
-      p[0] = zadd(y0, u2);
-      p[2 * sm] = zsub(y0, u2);
-      p[sm] = zadd(y1, u3);
-      p[3 * sm] = zsub(y1, u3);
+      // inverse of the radix-4 butterfly of fft_dif_ff: conjugate twiddles
+      // (three products), then the 4-point inverse DFT
+      const float4 w1 = __ldg(tw + j * tstep), w2 = __ldg(tw + 2 * j * tstep), w3 = __ldg(tw + 3 * j * tstep);
+      const float4 Y2 = zmulc(z1, w2), Y1 = zmulc(z2, w1), Y3 = zmulc(z3, w3);
+      const float4 t0 = zadd(z0, Y2), t2 = zsub(z0, Y2);
+      const float4 t1 = zadd(Y1, Y3), t3 = zmul_pi(zsub(Y1, Y3));
+      p[0] = zadd(t0, t1);
+      p[2 * sm] = zsub(t0, t1);
+      p[sm] = zadd(t2, t3);
+      p[3 * sm] = zsub(t2, t3);
     }
     __syncthreads();
   }
