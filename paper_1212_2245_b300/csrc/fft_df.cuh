@@ -87,6 +87,8 @@ __device__ __forceinline__ float4 zmul_pi(float4 a) { return make_float4(-a.z, -
 __device__ __forceinline__ float4 zconj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
 __device__ __forceinline__ float4 zscale(float4 a, float2 s) { return mkc(ff_mul(re_(a), s), ff_mul(im_(a), s)); }
 __device__ __forceinline__ float4 zzero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// a / 2: exact on both words (no renormalisation needed)
+__device__ __forceinline__ float4 zhalf(float4 a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
 
 // A 1D DFT of length N in float-float.  A power of two N is transformed
 // directly (M = N); any other N by Bluestein's chirp-z form as a circular
@@ -270,7 +272,7 @@ __device__ __forceinline__ float2 ff_sqrt3_half() { return make_float2(0x1.bb67a
 // Ends with a barrier.
 __device__ inline void fft3_dif_ff(float4* x, const Dft1ff& D, int nseq, int es, int ss, bool seq_fast) {
   const int M = dft_len(D), nt = M / 3;  // triples per sequence and stage
-  const float2 s3 = ff_sqrt3_half(), half = make_float2(0.5f, 0.f);
+  const float2 s3 = ff_sqrt3_half();
   int len = M;
   for (int st = 0; st < D.M3; ++st, len /= 3) {
     const int m = len / 3, tstep = M / len;
@@ -282,7 +284,7 @@ __device__ inline void fft3_dif_ff(float4* x, const Dft1ff& D, int nseq, int es,
       const int sm = m * es;
       const float4 x0 = p[0], x1 = p[sm], x2 = p[2 * sm];
       const float4 t1 = zadd(x1, x2);
-      const float4 t2 = zsub(x0, zscale(t1, half));
+      const float4 t2 = zsub(x0, zhalf(t1));
       const float4 d = zsub(x1, x2);
       const float4 t3 = zmul_mi(zscale(d, s3));  // -i sqrt(3)/2 (x1 - x2)
       p[0] = zadd(x0, t1);
@@ -298,7 +300,7 @@ __device__ inline void fft3_dif_ff(float4* x, const Dft1ff& D, int nseq, int es,
 // w = exp(+2 pi i / 3).  Ends with a barrier.
 __device__ inline void fft3_dit_inv_ff(float4* x, const Dft1ff& D, int nseq, int es, int ss, bool seq_fast) {
   const int M = dft_len(D), nt = M / 3;
-  const float2 s3 = ff_sqrt3_half(), half = make_float2(0.5f, 0.f);
+  const float2 s3 = ff_sqrt3_half();
   int len = 3 << D.logM;
   for (int st = 0; st < D.M3; ++st, len *= 3) {
     const int m = len / 3, tstep = M / len;
@@ -312,7 +314,7 @@ __device__ inline void fft3_dit_inv_ff(float4* x, const Dft1ff& D, int nseq, int
       const float4 z1 = zmulc(p[sm], __ldg(D.tw + j * tstep));
       const float4 z2 = zmulc(p[2 * sm], __ldg(D.tw + 2 * j * tstep));
       const float4 t1 = zadd(z1, z2);
-      const float4 t2 = zsub(z0, zscale(t1, half));
+      const float4 t2 = zsub(z0, zhalf(t1));
       const float4 t3 = zmul_pi(zscale(zsub(z1, z2), s3));  // +i sqrt(3)/2 (z1 - z2)
       p[0] = zadd(z0, t1);
       p[sm] = zadd(t2, t3);

@@ -212,9 +212,8 @@ __device__ __forceinline__ int spec_pos(const Dft1ff& D, int k) {
 // Hermitian, X(N-k) = conj X(k), so columns k = 0..N/2 hold all of it.
 // From Z = X1 + i X2:  X1 = (Z(k) + conj Z(N-k))/2,  X2 = -i (Z(k) - conj Z(N-k))/2.
 __device__ __forceinline__ void unpack_pair(float4 Zk, float4 Zm, float4& X1, float4& X2) {
-  const float2 h = make_float2(0.5f, 0.f);
-  X1 = mkc(ff_mul(ff_add(re_(Zk), re_(Zm)), h), ff_mul(ff_sub(im_(Zk), im_(Zm)), h));
-  X2 = mkc(ff_mul(ff_add(im_(Zk), im_(Zm)), h), ff_mul(ff_sub(re_(Zm), re_(Zk)), h));
+  X1 = zhalf(mkc(ff_add(re_(Zk), re_(Zm)), ff_sub(im_(Zk), im_(Zm))));
+  X2 = zhalf(mkc(ff_add(im_(Zk), im_(Zm)), ff_sub(re_(Zm), re_(Zk))));
 }
 
 // Row transforms: a CTA owns R consecutive sequences (capacity M each)
