@@ -215,7 +215,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long 
 
 // tiles_q / tiles_u: the tile tables of the q and update phases (they
 // differ for images with FFT tiles, whose q tiles go in pairs).
-__global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict__ imgs,
+__global__ void __launch_bounds__(256, 4) k_rrl_batch(const BatchImg* __restrict__ imgs,
                                                    const int4* __restrict__ tiles_q, int ntiles_q,
                                                    const int4* __restrict__ tiles_u, int ntiles_u, int iters,
                                                    unsigned* bar, int* work, int* status,
