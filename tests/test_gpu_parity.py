@@ -53,6 +53,30 @@ def test_full_pipeline_configs(lib, maker, sched):
     print(f"{case.name} [{sched}] WR3L max-abs {m:.3e} rms {r:.3e}")
     ud = lib.deblur(f, h, case.params, case.iters, kind=case.psf_kind)
     assert torch.equal(ud, u)
+    # the same schedule with direct sums only (line1024's 17 x 27 PSF takes the
+    # FFT tiles by the size rule, so the flow kernel and the tap groups run here)
+    lib.set_fft_tiles(2305)
+    try:
+        u2 = lib.rrl_iterate(f, u0.clone(), h, case.params, case.iters, kind=case.psf_kind)
+    finally:
+        lib.set_fft_tiles(0)
+    m, r = assert_close(u2, u_ref, f"{case.name} WR3L direct sums")
+    print(f"{case.name} [{sched}, direct sums] WR3L max-abs {m:.3e} rms {r:.3e}")
+
+
+@pytest.mark.parametrize("maker", [synth.case_box256, synth.case_line1024])
+def test_full_pipeline_tuned_plan(lib, maker):
+    """The configuration the bench times: a plan whose schedule and tile
+    form db_plan_autotune chose, at full size, against the oracle."""
+    case = maker()
+    f, h = cuda(case.f), cuda(case.h)
+    _, u_ref = oracle_pipeline(case)
+    plan = lib.Plan(*case.f.shape, h, case.params, case.iters, kind=case.psf_kind)
+    sched, form = plan.autotune(f, reps=2)
+    u = plan.run(f)
+    m, r = assert_close(u, u_ref, f"{case.name} tuned plan ({sched}, {form})")
+    print(f"{case.name} tuned plan [{sched}, {form}] WR3L max-abs {m:.3e} rms {r:.3e}")
+    plan.close()
 
 
 def test_full_pipeline_fourier_gauss2048(lib):
@@ -286,6 +310,7 @@ def test_flow_equals_split_bitwise(lib, H, W, psf, kind):
     p = Params()
     f, u0 = _iterate_case(H, W, h, 7, p, seed=11)
     out = {}
+    lib.set_fft_tiles(2305)  # direct sums: the flow kernel runs them (FFT tiles run split)
     try:
         for knob in (1, 256):  # one-axis PSFs: register windows, then tap groups
             lib.set_one_axis_min(knob)
@@ -295,6 +320,7 @@ def test_flow_equals_split_bitwise(lib, H, W, psf, kind):
     finally:
         lib.set_schedule("auto")
         lib.set_one_axis_min(0)
+        lib.set_fft_tiles(0)
     for knob in (1, 256):
         assert torch.equal(out["split", knob], out["flow", knob])
 
