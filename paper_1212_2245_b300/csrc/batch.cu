@@ -7,12 +7,13 @@
 // for every image, the batched-Wiener job tables, a table of RRRL tiles over
 // all images (sorted by cost), all uploaded into the caller's workspace.
 // Run (capturable: stream-ordered launches and memsets only):
-//   1. five batched Wiener launches (one per transform stage);
+//   1. the batched Wiener launches (one per transform stage and column class);
 //   2. one cooperative persistent launch that performs every RRRL iteration
 //      of every image: per iteration a q-phase and an update-phase over all
 //      tiles, tiles taken from an atomic work queue, phases separated by a
-//      grid barrier whose wait is bounded (on time-out it raises
-//      DB_FLAG_TIMEOUT and the kernel returns).
+//      grid barrier (or, in the dependency order, per-image counters) whose
+//      wait is bounded (on time-out it raises DB_FLAG_TIMEOUT and the kernel
+//      returns).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -215,7 +216,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long 
 
 // tiles_q / tiles_u: the tile tables of the q and update phases (they
 // differ for images with FFT tiles, whose q tiles go in pairs).
-__global__ void __launch_bounds__(256, 4) k_rrl_batch(const BatchImg* __restrict__ imgs,
+__global__ void __launch_bounds__(256, 3) k_rrl_batch(const BatchImg* __restrict__ imgs,
                                                    const int4* __restrict__ tiles_q, int ntiles_q,
                                                    const int4* __restrict__ tiles_u, int ntiles_u, int iters,
                                                    unsigned* bar, int* work, int* status,
