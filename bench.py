@@ -566,16 +566,16 @@ def run_batch(args, world, rank, local):
     ms_w = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     ms_rrl = ms - ms_w
     # end to end through the C ABI (db_batch_stream_run_host): page-locked
-    # host images in, results out, every step; 12 sub-batches (shares 1, 2,
-    # 4, 8, ..., 8, 4, 2, 1) whose copies overlap the other sub-batches' runs.  Each step starts after the
-    # previous one has fully finished (the call's stream waits for its
-    # downloads).
+    # host images in, results out, every step; 6 sub-batches (pixel shares
+    # 1, 4, 16, 16, 4, 1) whose copies overlap the other sub-batches' runs.
+    # Each step starts after the previous one has fully finished (the call's
+    # stream waits for its downloads).
     f_host = [pinned_copy(c.f) for c in cases]
     u_host = [torch.empty(c.f.shape, dtype=torch.float32).pin_memory() for c in cases]
     # the sub-batch plans take the tuned forms through the process-wide settings
     set_batch_forms(tuned)
     with torch.cuda.stream(stream):
-        bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=12, device=dev)
+        bs = db.BatchStream([c.f.shape for c in cases], hs, ps, iters, kinds=kinds, parts=6, device=dev)
         bs.run(f_host, u_host)
     set_batch_forms(None)
     for a, b_ in zip(u_host, full.us):

@@ -248,11 +248,14 @@ db_status db_deblur_batch(const db_image_desc* descs, int n, int iters, void* ws
  * overlapped with the work (the paper reports its host-device transfers
  * separately, Sec. 5.3; this form hides most of them).  The images are split
  * into `parts` sub-batches (fewer when n < parts) whose pixel counts follow
- * the shares 1, 2, 4, 8, ..., 8, 4, 2, 1 in streaming order (largest images
+ * the shares 1, 4, 16, ..., 16, 4, 1 in streaming order (largest images
  * first, each to the sub-batch least loaded for its share), each an ordinary
  * batch plan over its share of the workspace.  The small first and last
  * sub-batches shorten the first upload and the last download, which no run
- * overlaps.  db_batch_stream_run_host enqueues, per
+ * overlaps; each run hides the next sub-batch's upload while runs take at
+ * least four times as long as the uploads of the same pixels, and each
+ * further sub-batch adds some run time (5 to 7 suit a 0.7 GB batch of 512
+ * images).  db_batch_stream_run_host enqueues, per
  * sub-batch k: the copies of its host images into the descriptors' DEVICE
  * buffers f on an internal upload stream, its run on `stream` once those
  * copies have landed, and the copies of its results (the descriptors'

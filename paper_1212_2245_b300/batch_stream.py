@@ -2,7 +2,7 @@
 
 A thin binding of the library's streamed batch (db_batch_stream_*): the
 images are split into `parts` sub-batches whose pixel counts ramp up from
-the first and down to the last (shares 1, 2, 4, 8, ..., 8, 4, 2, 1); for
+the first and down to the last (shares 1, 4, 16, ..., 16, 4, 1); for
 each sub-batch the library copies its host images in on an upload stream,
 runs it on the caller's stream once they have landed, and copies its
 results out on a download stream, so the transfers of the other sub-batches

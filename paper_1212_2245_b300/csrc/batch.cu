@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -763,22 +764,24 @@ static db_status batch_set_forms(BatchPlan* P, int fft_min, bool dense, int wind
 // the runs of other sub-batches
 // ---------------------------------------------------------------------------
 // Partition of the images into `parts` groups by pixel count, in the order
-// the groups are streamed: target shares w_k = min(2^k, 2^(parts-1-k), 8)
-// (1, 2, 4, 8, ..., 8, 4, 2, 1), so that the first group's upload and the
-// last group's download, which no run overlaps, are short, while each
-// group's run still covers the next group's upload.  Images are dealt
-// largest first to the group with the least load relative to its share
-// (ties to the lowest group); each group keeps ascending image order.
-// batch512 end to end (ms) with equal shares / these shares: 8 groups
-// 68.7 / 70.5, 12 groups 69.4 / 66.7, 16 groups 70.2 / 68.4.
+// the groups are streamed: target shares w_k = 4^min(k, parts-1-k)
+// (1, 4, 16, ..., 16, 4, 1).  The first group's upload and the last group's
+// download, which no run overlaps, are then short, and each group's run
+// still covers the next group's upload while a run takes at least four times
+// as long as the upload of the same pixels (batch512: 56 ms of runs, 14 ms of
+// uploads).  Every further group costs about 0.5 ms of run time (its own
+// Wiener launches, grid barriers and tails).  Images are dealt largest first
+// to the group with the least load relative to its share (ties to the lowest
+// group); each group keeps ascending image order.
 static std::vector<std::vector<int>> lpt_parts(const db_image_desc* d, int n, int parts) {
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (long long)d[a].H * d[a].W > (long long)d[b].H * d[b].W;
   });
-  std::vector<long long> load(parts, 0), share(parts);
-  for (int k = 0; k < parts; ++k) share[k] = std::min(std::min(1LL << std::min(k, 3), 1LL << std::min(parts - 1 - k, 3)), 8LL);
+  std::vector<long long> load(parts, 0);
+  std::vector<double> share(parts);
+  for (int k = 0; k < parts; ++k) share[k] = std::ldexp(1.0, 2 * std::min(std::min(k, parts - 1 - k), 24));
   std::vector<std::vector<int>> out(parts);
   for (int i : order) {
     int k = 0;
@@ -914,6 +917,15 @@ db_status db_batch_stream_create(const db_image_desc* descs, int n, int iters, i
   return DB_OK;
 }
 
+// Copy one image between a packed host buffer and a device buffer of row
+// stride ld (one linear copy when the rows are packed on both sides).
+static cudaError_t copy_image(void* dst, size_t dst_ld, const void* src, size_t src_ld, int H, int W,
+                              cudaMemcpyKind kind, cudaStream_t s) {
+  const size_t row = (size_t)W * sizeof(float);
+  if (dst_ld == row && src_ld == row) return cudaMemcpyAsync(dst, src, row * (size_t)H, kind, s);
+  return cudaMemcpy2DAsync(dst, dst_ld, src, src_ld, row, (size_t)H, kind, s);
+}
+
 db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_host, float* const* u_host,
                                    int* dev_status, void* stream) {
   BatchStream* B = (BatchStream*)b;
@@ -926,31 +938,33 @@ db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_hos
   if (cudaEventRecord(B->start, s) != cudaSuccess || cudaStreamWaitEvent(B->up, B->start, 0) != cudaSuccess)
     return DB_ERR_CUDA;
   const size_t np = B->plans.size();
-  for (size_t k = 0; k < np; ++k) {
+  auto upload = [&](size_t k) -> db_status {
     for (int i : B->idx[k]) {
       const db_image_desc& x = B->descs[i];
-      const size_t row = (size_t)x.W * sizeof(float);
-      if (cudaMemcpy2DAsync((void*)x.f, (size_t)x.ld * sizeof(float), f_host[i], row, row, x.H,
-                            cudaMemcpyHostToDevice, B->up) != cudaSuccess)
+      if (copy_image((void*)x.f, (size_t)x.ld * sizeof(float), f_host[i], (size_t)x.W * sizeof(float), x.H, x.W,
+                     cudaMemcpyHostToDevice, B->up) != cudaSuccess)
         return DB_ERR_CUDA;
     }
-    if (cudaEventRecord(B->ev_up[k], B->up) != cudaSuccess) return DB_ERR_CUDA;
-  }
-  for (size_t k = 0; k < np; ++k) {
+    return cudaEventRecord(B->ev_up[k], B->up) == cudaSuccess ? DB_OK : DB_ERR_CUDA;
+  };
+  // sub-batch k+1's copies are enqueued before sub-batch k's run, so that the
+  // first run does not wait for the host to enqueue every upload
+  db_status st = upload(0);
+  for (size_t k = 0; k < np && st == DB_OK; ++k) {
+    if (k + 1 < np && (st = upload(k + 1)) != DB_OK) break;
     if (cudaStreamWaitEvent(s, B->ev_up[k], 0) != cudaSuccess) return DB_ERR_CUDA;
-    const db_status st = batch_run(B->plans[k], dev_status, s);
-    if (st != DB_OK) return st;
+    if ((st = batch_run(B->plans[k], dev_status, s)) != DB_OK) break;
     if (cudaEventRecord(B->ev_done[k], s) != cudaSuccess || cudaStreamWaitEvent(B->down, B->ev_done[k], 0) != cudaSuccess)
       return DB_ERR_CUDA;
     for (int i : B->idx[k]) {
       const db_image_desc& x = B->descs[i];
-      const size_t row = (size_t)x.W * sizeof(float);
-      if (cudaMemcpy2DAsync(u_host[i], row, x.u, (size_t)x.ld * sizeof(float), row, x.H, cudaMemcpyDeviceToHost,
-                            B->down) != cudaSuccess)
+      if (copy_image(u_host[i], (size_t)x.W * sizeof(float), x.u, (size_t)x.ld * sizeof(float), x.H, x.W,
+                     cudaMemcpyDeviceToHost, B->down) != cudaSuccess)
         return DB_ERR_CUDA;
     }
     if (cudaEventRecord(B->ev_down[k], B->down) != cudaSuccess) return DB_ERR_CUDA;
   }
+  if (st != DB_OK) return st;
   // `stream` completes only after every result has reached the host
   for (size_t k = 0; k < np; ++k)
     if (cudaStreamWaitEvent(s, B->ev_down[k], 0) != cudaSuccess) return DB_ERR_CUDA;
