@@ -581,7 +581,7 @@ db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, fl
   if (!P || !f_host || !u_host || !f_dev || !u_dev || f_dev == u_dev) return DB_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t row = (size_t)P->W * sizeof(float), pitch = (size_t)P->ld * sizeof(float);
-  if (cudaMemcpy2DAsync(f_dev, pitch, f_host, row, row, P->H, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (copy_image_async(f_dev, pitch, f_host, row, P->H, P->W, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return DB_ERR_CUDA;
   if (plan_graph(P, plan, f_dev, u_dev, dev_status)) {
     if (cudaGraphLaunch(P->gexec, s) != cudaSuccess) return DB_ERR_CUDA;
@@ -589,7 +589,7 @@ db_status db_plan_run_host(db_plan* plan, const float* f_host, float* u_host, fl
     const db_status st = db_plan_run(plan, f_dev, u_dev, dev_status, stream);
     if (st != DB_OK) return st;
   }
-  if (cudaMemcpy2DAsync(u_host, row, u_dev, pitch, row, P->H, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (copy_image_async(u_host, row, u_dev, pitch, P->H, P->W, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return DB_ERR_CUDA;
   return DB_OK;
 }

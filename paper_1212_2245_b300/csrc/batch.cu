@@ -917,15 +917,6 @@ db_status db_batch_stream_create(const db_image_desc* descs, int n, int iters, i
   return DB_OK;
 }
 
-// Copy one image between a packed host buffer and a device buffer of row
-// stride ld (one linear copy when the rows are packed on both sides).
-static cudaError_t copy_image(void* dst, size_t dst_ld, const void* src, size_t src_ld, int H, int W,
-                              cudaMemcpyKind kind, cudaStream_t s) {
-  const size_t row = (size_t)W * sizeof(float);
-  if (dst_ld == row && src_ld == row) return cudaMemcpyAsync(dst, src, row * (size_t)H, kind, s);
-  return cudaMemcpy2DAsync(dst, dst_ld, src, src_ld, row, (size_t)H, kind, s);
-}
-
 db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_host, float* const* u_host,
                                    int* dev_status, void* stream) {
   BatchStream* B = (BatchStream*)b;
@@ -941,8 +932,8 @@ db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_hos
   auto upload = [&](size_t k) -> db_status {
     for (int i : B->idx[k]) {
       const db_image_desc& x = B->descs[i];
-      if (copy_image((void*)x.f, (size_t)x.ld * sizeof(float), f_host[i], (size_t)x.W * sizeof(float), x.H, x.W,
-                     cudaMemcpyHostToDevice, B->up) != cudaSuccess)
+      if (copy_image_async((void*)x.f, (size_t)x.ld * sizeof(float), f_host[i], (size_t)x.W * sizeof(float), x.H,
+                           x.W, cudaMemcpyHostToDevice, B->up) != cudaSuccess)
         return DB_ERR_CUDA;
     }
     return cudaEventRecord(B->ev_up[k], B->up) == cudaSuccess ? DB_OK : DB_ERR_CUDA;
@@ -958,8 +949,8 @@ db_status db_batch_stream_run_host(db_batch_stream* b, const float* const* f_hos
       return DB_ERR_CUDA;
     for (int i : B->idx[k]) {
       const db_image_desc& x = B->descs[i];
-      if (copy_image(u_host[i], (size_t)x.W * sizeof(float), x.u, (size_t)x.ld * sizeof(float), x.H, x.W,
-                     cudaMemcpyDeviceToHost, B->down) != cudaSuccess)
+      if (copy_image_async(u_host[i], (size_t)x.W * sizeof(float), x.u, (size_t)x.ld * sizeof(float), x.H, x.W,
+                           cudaMemcpyDeviceToHost, B->down) != cudaSuccess)
         return DB_ERR_CUDA;
     }
     if (cudaEventRecord(B->ev_down[k], B->down) != cudaSuccess) return DB_ERR_CUDA;
