@@ -232,11 +232,14 @@ __device__ __forceinline__ void cols_bot_product(float2* A, const float2* __rest
 // the rows r_lo <= r < r_hi (the inverse row passes skip the others).
 // tw must be ready and A free on entry (the caller's barrier); the
 // barriers between passes are inside.
+// The two row passes of a row exchange data within one warp (both group
+// maps give warp w the rows 4w..4w+3 and 32+4w..32+4w+3), so a warp barrier
+// separates them; the column passes span four warps and take CTA barriers.
 template <bool CONJ, class Load, class Out>
 __device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2* __restrict__ spec, int r_lo,
                                        int r_hi, Load ld, Out out) {
   rows_top_fwd(A, tw, ld);
-  __syncthreads();
+  __syncwarp();
   rows_bot<false>(A);
   __syncthreads();
   cols_top<false>(A, tw);
@@ -246,7 +249,7 @@ __device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2
   cols_top<true>(A, tw);
   __syncthreads();
   rows_bot<true>(A, r_lo, r_hi);
-  __syncthreads();
+  __syncwarp();
   rows_top_inv(A, tw, r_lo, r_hi, out);
 }
 
@@ -262,7 +265,7 @@ __device__ __forceinline__ void psf_spectrum(float2* A, float2* tw, const float*
     const int a = (r + cy) & (kN - 1), b = (c + cx) & (kN - 1);
     return make_float2(a < kh && b < kw ? __ldg(taps + a * kw + b) : 0.0f, 0.0f);
   });
-  __syncthreads();
+  __syncwarp();
   rows_bot<false>(A);
   __syncthreads();
   cols_top<false>(A, tw);
