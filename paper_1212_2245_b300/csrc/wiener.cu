@@ -351,14 +351,30 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs a, int R) {
   rows_body<MODE>(smem4, a, blockIdx.x * R, R);
 }
 
-// Batched form: CTA b transforms sequence items[b].y of job items[b].x.
+// Batched forms.  The batch's stages are launched back to back with
+// programmatic dependent launch (wiener_batch_run): a stage's CTAs may start
+// while the previous stage's last CTAs still run.  A stage that reads what an
+// earlier stage of the run wrote (the 2D column passes read the forward row
+// pass, the inverse row pass reads the column passes) waits for its
+// predecessor first; the others work on images no earlier stage of the run
+// touches and wait for their predecessor only before they exit.  Either way a
+// stage completes after its predecessor, so each wait covers every earlier
+// stage.  Job and item tables are written at plan time, before the run.
+__device__ __host__ constexpr bool wb_reads_earlier_stage(int mode) {
+  return mode == COL_WIENER || mode == COL_FILTER || mode == ROW_INV_C2R;
+}
+
+// CTA b transforms sequence items[b].y of job items[b].x.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_fft_rows_batch(const FftArgs* __restrict__ jobs,
                                                         const int2* __restrict__ items) {
   extern __shared__ float4 smem4[];
+  pdl_trigger();
   const int2 it = items[blockIdx.x];
   const FftArgs a = jobs[it.x];
+  if (wb_reads_earlier_stage(MODE)) pdl_wait();
   rows_body<MODE>(smem4, a, it.y, a.seqs_per_cta);
+  if (!wb_reads_earlier_stage(MODE)) pdl_wait();
 }
 
 // Column transforms: a CTA owns C adjacent sequences laid out across a row
@@ -451,9 +467,12 @@ template <int MODE, int C>
 __global__ void __launch_bounds__(256) k_fft_cols_batch(const FftArgs* __restrict__ jobs,
                                                         const int2* __restrict__ items) {
   extern __shared__ float4 smem4[];
+  pdl_trigger();
   const int2 it = items[blockIdx.x];
   const FftArgs a = jobs[it.x];
+  if (wb_reads_earlier_stage(MODE)) pdl_wait();
   cols_body<MODE, C>(smem4, a, it.y);
+  if (!wb_reads_earlier_stage(MODE)) pdl_wait();
 }
 
 static constexpr size_t kSmemLimit = 227 * 1024;
@@ -890,47 +909,73 @@ cudaError_t wiener_batch_upload(WienerBatch* b, void* dst, cudaStream_t s) {
   return cudaSuccess;
 }
 
-template <int MODE>
-static cudaError_t launch_rows_batch(const WienerBatch* b, int stage, cudaStream_t s) {
-  if (b->items[stage][0].empty()) return cudaSuccess;
-  cudaError_t e = set_dyn_smem(k_fft_rows_batch<MODE>, b->smem[stage][0]);
+// Launch a batched stage kernel; `pdl`: programmatic dependent launch on the
+// previous launch of the run (every launch of the run but its first).
+template <typename Kern>
+static cudaError_t launch_wb(Kern kern, unsigned grid, size_t smem, bool pdl, const WienerBatch* b, int stage,
+                             int cls, cudaStream_t s) {
+  cudaError_t e = set_dyn_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  k_fft_rows_batch<MODE><<<(unsigned)b->items[stage][0].size(), 256, b->smem[stage][0], s>>>(
-      b->d_jobs[stage], b->d_items[stage][0]);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if ((e = cudaLaunchKernelEx(&cfg, kern, (const FftArgs*)b->d_jobs[stage], (const int2*)b->d_items[stage][cls])) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return e;
+  }
   count_launch();
-  return cudaGetLastError();
+  return cudaSuccess;
+}
+
+template <int MODE>
+static cudaError_t launch_rows_batch(const WienerBatch* b, int stage, bool& pdl, cudaStream_t s) {
+  if (b->items[stage][0].empty()) return cudaSuccess;
+  const cudaError_t e = launch_wb(k_fft_rows_batch<MODE>, (unsigned)b->items[stage][0].size(), b->smem[stage][0],
+                                  pdl, b, stage, 0, s);
+  pdl = true;
+  return e;
 }
 
 template <int MODE, int K>
-static cudaError_t launch_cols_batch_c(const WienerBatch* b, int stage, cudaStream_t s) {
+static cudaError_t launch_cols_batch_c(const WienerBatch* b, int stage, bool& pdl, cudaStream_t s) {
   if (b->items[stage][K].empty()) return cudaSuccess;
-  auto kern = k_fft_cols_batch<MODE, col_class_c(K)>;
-  cudaError_t e = set_dyn_smem(kern, b->smem[stage][K]);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)b->items[stage][K].size(), 256, b->smem[stage][K], s>>>(b->d_jobs[stage], b->d_items[stage][K]);
-  count_launch();
-  return cudaGetLastError();
+  const cudaError_t e = launch_wb(k_fft_cols_batch<MODE, col_class_c(K)>, (unsigned)b->items[stage][K].size(),
+                                  b->smem[stage][K], pdl, b, stage, K, s);
+  pdl = true;
+  return e;
 }
 
 template <int MODE>
-static cudaError_t launch_cols_batch(const WienerBatch* b, int stage, cudaStream_t s) {
+static cudaError_t launch_cols_batch(const WienerBatch* b, int stage, bool& pdl, cudaStream_t s) {
   static_assert(kColClasses == 3, "one launch per column class");
   cudaError_t e;
-  if ((e = launch_cols_batch_c<MODE, 0>(b, stage, s)) != cudaSuccess) return e;
-  if ((e = launch_cols_batch_c<MODE, 1>(b, stage, s)) != cudaSuccess) return e;
-  return launch_cols_batch_c<MODE, 2>(b, stage, s);
+  if ((e = launch_cols_batch_c<MODE, 0>(b, stage, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch_c<MODE, 1>(b, stage, pdl, s)) != cudaSuccess) return e;
+  return launch_cols_batch_c<MODE, 2>(b, stage, pdl, s);
 }
 
+// The stages in launch order.  The run's first launch depends on everything
+// before it in the stream in full; each later one is a programmatic
+// dependent of the launch before it (see k_fft_rows_batch).
 cudaError_t wiener_batch_run(const WienerBatch* b, cudaStream_t s) {
   cudaError_t e;
-  if ((e = launch_rows_batch<ROW_WIENER_1D>(b, WB_ROW_1D, s)) != cudaSuccess) return e;
-  if ((e = launch_rows_batch<ROW_FILTER_1D>(b, WB_ROW_1D_F, s)) != cudaSuccess) return e;
-  if ((e = launch_cols_batch<COL_WIENER_1D_REAL>(b, WB_COL_1D, s)) != cudaSuccess) return e;
-  if ((e = launch_cols_batch<COL_FILTER_1D_REAL>(b, WB_COL_1D_F, s)) != cudaSuccess) return e;
-  if ((e = launch_rows_batch<ROW_FWD_R2C>(b, WB_ROW_FWD, s)) != cudaSuccess) return e;
-  if ((e = launch_cols_batch<COL_WIENER>(b, WB_COL_2D, s)) != cudaSuccess) return e;
-  if ((e = launch_cols_batch<COL_FILTER>(b, WB_COL_2D_F, s)) != cudaSuccess) return e;
-  return launch_rows_batch<ROW_INV_C2R>(b, WB_ROW_INV, s);
+  bool pdl = false;
+  if ((e = launch_rows_batch<ROW_WIENER_1D>(b, WB_ROW_1D, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_rows_batch<ROW_FILTER_1D>(b, WB_ROW_1D_F, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_WIENER_1D_REAL>(b, WB_COL_1D, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_FILTER_1D_REAL>(b, WB_COL_1D_F, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_rows_batch<ROW_FWD_R2C>(b, WB_ROW_FWD, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_WIENER>(b, WB_COL_2D, pdl, s)) != cudaSuccess) return e;
+  if ((e = launch_cols_batch<COL_FILTER>(b, WB_COL_2D_F, pdl, s)) != cudaSuccess) return e;
+  return launch_rows_batch<ROW_INV_C2R>(b, WB_ROW_INV, pdl, s);
 }
 
 }  // namespace db
