@@ -300,6 +300,17 @@ db_status db_set_spin_limit(long long cycles);
  * values. */
 db_status db_set_batch_order(int order);
 
+/* TMA staging (no counterpart in the paper): 1 (the default) lets the
+ * q phase of FFT tiles fetch each tile pair's 64 x 136 window of u with one
+ * tensor copy (cp.async.bulk.tensor) into shared memory, where the elements
+ * outside the image then take their clamped neighbours' values; 0 loads the
+ * windows element by element with clamped indices.  Both load the same
+ * values and give the same bits.  The copy needs u 16-byte aligned with a
+ * row stride (and image stride) that is a multiple of 4 floats; other
+ * buffers take the element-wise loads.  Process-wide; plans and batches take
+ * it when their runs are enqueued or created.  DB_ERR_ARG for other values. */
+db_status db_set_tma(int on);
+
 /* Allocation-free RRRL iterations (no counterpart in the paper; an interface
  * convenience).  Some callers cannot allocate device memory at run time:
  * a deblurring step embedded in a fixed-latency frame loop (an inspection

@@ -18,7 +18,8 @@ from .params import Params
 
 __all__ = ["Params", "DeblurError", "Workspace", "workspace_bytes", "wiener", "rrl_iterate",
            "deblur", "Plan", "Batch", "deblur_batch", "rrl_backward", "DeblurFn", "rrl_iterate_noalloc", "HostBuffer", "set_schedule", "set_one_axis_min", "set_spin_limit",
-           "set_rf_eval", "set_dense_min", "version", "FrameStream", "BatchStream", "deblur_n", "workspace_bytes_n"]
+           "set_rf_eval", "set_dense_min", "set_fft_tiles", "set_batch_order", "set_tma", "version", "FrameStream",
+           "BatchStream", "deblur_n", "workspace_bytes_n"]
 
 
 class DeblurError(RuntimeError):
@@ -509,6 +510,13 @@ def set_batch_order(name: str):
     for its own image's previous phase).  Both give the same bits."""
     code = {"dependency": 0, "barrier": 1}[name]
     _check(_lib.load().db_set_batch_order(code), "db_set_batch_order")
+
+
+def set_tma(on: bool):
+    """Stage the FFT tiles' q-phase windows by TMA tensor copies (True, the
+    default) or by element-wise clamped loads (False).  Both give the same
+    bits."""
+    _check(_lib.load().db_set_tma(1 if on else 0), "db_set_tma")
 
 
 def rrl_iterate_noalloc(f: torch.Tensor, u: torch.Tensor, taps: torch.Tensor, params: Params,

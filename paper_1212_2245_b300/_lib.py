@@ -67,6 +67,7 @@ SIGNATURES = {
     "db_batch_stream_destroy": (None, [c_void_p]),
     "db_set_spin_limit": (c_int, [ctypes.c_longlong]),
     "db_set_batch_order": (c_int, [c_int]),
+    "db_set_tma": (c_int, [c_int]),
     "db_backward_workspace_bytes": (c_size_t, [c_int, c_int, c_int, P_PSF, c_int]),
     "db_rrl_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, P_PSF, P_PAR, c_int, c_int,
                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),

@@ -42,6 +42,7 @@
 #include "fft8.cuh"
 #include "internal.cuh"
 #include "rrl_tiles.cuh"
+#include "tma.cuh"
 
 namespace db {
 namespace ftile {
@@ -108,8 +109,9 @@ __device__ __forceinline__ int col_bot_base(int g) {
 
 // Forward row top pass: elements from ld(r, c), DIF with twiddles, to A.
 // Both groups' elements are loaded before either is transformed (sixteen
-// loads in flight per thread).
-template <class Load>
+// loads in flight per thread).  SYNC: ld reads shared memory that A
+// overlays, so every thread's loads finish (CTA barrier) before any writes.
+template <bool SYNC = false, class Load>
 __device__ __forceinline__ void rows_top_fwd(float2* A, const float2* tw, Load ld) {
   const int g0 = tid_flat();
   int r[2], j[2];
@@ -120,6 +122,7 @@ __device__ __forceinline__ void rows_top_fwd(float2* A, const float2* tw, Load l
   for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[h][m] = ld(r[h], j[h] + 8 * m);
+  if (SYNC) __syncthreads();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     f8::dif8(v[h]);
@@ -235,10 +238,10 @@ __device__ __forceinline__ void cols_bot_product(float2* A, const float2* __rest
 // The two row passes of a row exchange data within one warp (both group
 // maps give warp w the rows 4w..4w+3 and 32+4w..32+4w+3), so a warp barrier
 // separates them; the column passes span four warps and take CTA barriers.
-template <bool CONJ, class Load, class Out>
+template <bool CONJ, bool SYNC_LOAD = false, class Load, class Out>
 __device__ __forceinline__ void conv64(float2* A, const float2* tw, const float2* __restrict__ spec, int r_lo,
                                        int r_hi, Load ld, Out out) {
-  rows_top_fwd(A, tw, ld);
+  rows_top_fwd<SYNC_LOAD>(A, tw, ld);
   __syncwarp();
   rows_bot<false>(A);
   __syncthreads();
@@ -295,16 +298,35 @@ __host__ __device__ inline size_t smem_update(int kh) {
   return smem_q() + (size_t)staged_u_rows(kh) * kUS * sizeof(float);
 }
 
+// TMA staging of the q phase's u window (tma.cuh): both tiles' windows,
+// columns xa .. xb + 63, as one box of kN rows x kBoxW columns whose x starts
+// at xa rounded down to a multiple of 4.  The box overlays the transform
+// buffer A exactly (kBoxW floats = kRS float2 per row): its row stride of
+// 136 floats puts the four rows a warp's first pass reads on distinct banks.
+constexpr int kBoxW = 2 * kRS;
+static_assert(kBoxW % 4 == 0 && kBoxW >= 3 + 2 * kN + 2 && kN * kBoxW * 4 == kPos * 8, "box over A");
+struct WinTma {
+  const CUtensorMap* map;   // 3D map (W, H, images) of u with kBoxW x kN x 1 boxes
+  int z;                    // the image's index in the map
+  unsigned long long* bar;  // the CTA's mbarrier (count 1)
+  unsigned parity;          // parity of the barrier phase this copy completes
+  long long limit;          // bound of the wait (clock cycles)
+  int* status;              // DB_FLAG_TIMEOUT if the wait runs out
+};
+
 // q = (e, W) on the tiles at (i0, j0) and (i0, j0 + OW) (the second one if it
 // starts inside the image), planar: qe, qw (pitch ldqp).  The u window of a
 // tile starts dy = kh-1-kh/2 rows and dx = kw-1-kw/2 columns before it: the
 // blur b(i, j) = sum h(a, b) u(i - a + kh/2, j - b + kw/2) reaches that far
-// up and left.  smem_raw: smem_q() bytes.
+// up and left.  smem_raw: smem_q() bytes.  With `tma` (and A 128-byte
+// aligned) the windows arrive by one TMA copy; elements outside the image
+// then take their clamped neighbours' values in shared memory, so that both
+// ways load the same values and give the same bits.
 template <typename Dep = NoDep>
 __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __restrict__ f, int ldf,
                                        const float* uin, int ldin, float* qe, float* qw, int ldqp, int H, int W,
                                        const float2* __restrict__ spec, int kh, int kw, const RrlParams& p, int i0,
-                                       int j0, Dep dep = Dep()) {
+                                       int j0, Dep dep = Dep(), const WinTma* tma = nullptr) {
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* A = tw + kTwSlots;
   make_twiddles(tw);
@@ -315,33 +337,82 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
   // both windows inside the image: no clamping
   const bool inside = ys >= 0 && ys + kN <= H && xa >= 0 && (has_b ? xb : xa) + kN <= W;
   dep();
-  __syncthreads();  // twiddles
-  conv64<false>(
-      A, tw, spec, dy, dy + OH,
-      [&](int r, int c) {
-        if (inside) {
-          const float* row = uin + (size_t)(ys + r) * ldin;
-          return make_float2(row[xa + c], has_b ? row[xb + c] : 0.0f);
-        }
-        const float* row = uin + (size_t)min(max(ys + r, 0), H - 1) * ldin;
-        const float a = row[min(max(xa + c, 0), W - 1)];
-        const float b = has_b ? row[min(max(xb + c, 0), W - 1)] : 0.0f;
-        return make_float2(a, b);
-      },
-      // each (bA, bB) back into the slot its group read it from
-      [&](int r, int c, float2 v) { A[r * kRS + c + (c >> 4)] = v; });
+  float* box = reinterpret_cast<float*>(A);
+  const int x0 = xa & ~3, e = xa - x0;  // x0: a multiple of 4 at or left of xa
+  const bool staged = tma != nullptr && (smem_u32(box) & 127u) == 0;
+  if (staged) {
+    if (tid_flat() == 0) {
+      fence_proxy_async_smem();  // the CTA's earlier uses of A (barrier before the tile) come first
+      mbar_arrive_expect_tx(tma->bar, kN * kBoxW * (unsigned)sizeof(float));
+      tma_load_3d(box, tma->map, x0, ys, tma->z, tma->bar);
+    }
+    const bool late = !mbar_wait_bounded(tma->bar, tma->parity, tma->limit);
+    if (__syncthreads_or(late)) {  // also publishes the twiddles
+      if (tid_flat() == 0 && tma->status) atomicOr(tma->status, DB_FLAG_TIMEOUT);
+      (void)mbar_wait_bounded(tma->bar, tma->parity, tma->limit);  // the copy in flight, bounded again
+      return;
+    }
+    if (!inside) {  // constant continuation: outside elements copy their clamped neighbours
+      for (int k = tid_flat(); k < kN * kBoxW; k += kThreads) {
+        const int t = k / kBoxW, c = k - t * kBoxW;
+        const int ty = min(max(ys + t, 0), H - 1) - ys, tx = min(max(x0 + c, 0), W - 1) - x0;
+        if (ty != t || tx != c) box[k] = box[ty * kBoxW + tx];
+      }
+      __syncthreads();
+    }
+    conv64<false, true>(
+        A, tw, spec, dy, dy + OH,
+        [&](int r, int c) {
+          const float* row = box + r * kBoxW + e + c;
+          return make_float2(row[0], has_b ? row[OW] : 0.0f);
+        },
+        [&](int r, int c, float2 v) { A[r * kRS + c + (c >> 4)] = v; });
+  } else {
+    __syncthreads();  // twiddles
+    conv64<false>(
+        A, tw, spec, dy, dy + OH,
+        [&](int r, int c) {
+          if (inside) {
+            const float* row = uin + (size_t)(ys + r) * ldin;
+            return make_float2(row[xa + c], has_b ? row[xb + c] : 0.0f);
+          }
+          const float* row = uin + (size_t)min(max(ys + r, 0), H - 1) * ldin;
+          const float a = row[min(max(xa + c, 0), W - 1)];
+          const float b = has_b ? row[min(max(xb + c, 0), W - 1)] : 0.0f;
+          return make_float2(a, b);
+        },
+        // each (bA, bB) back into the slot its group read it from
+        [&](int r, int c, float2 v) { A[r * kRS + c + (c >> 4)] = v; });
+  }
   __syncthreads();
   // (e, W) over both tiles' outputs as one row of 2 OW columns: consecutive
-  // threads take consecutive image columns
-  const int nr = min(OH, H - i0), nc = min(2 * OW, W - j0);
-  for (int item = tid_flat(); item < nr * nc; item += kThreads) {
-    const int oi = item / nc, oj2 = item - oi * nc;
-    const int second = oj2 >= OW, c = dx + oj2 - (second ? OW : 0);
-    const float2 v = A[(dy + oi) * kRS + c + (c >> 4)];
-    const int i = i0 + oi, j = j0 + oj2;
-    const float2 q = weighted_residual(second ? v.y : v.x, fmaxf(__ldg(f + (size_t)i * ldf + j), p.floor), p);
-    qe[(size_t)i * ldqp + j] = q.x;
-    qw[(size_t)i * ldqp + j] = q.y;
+  // threads take consecutive image columns.  A thread's items go in groups of
+  // kQB whose f loads are issued together.
+  constexpr int kQB = 4;
+  const int nr = min(OH, H - i0), nc = min(2 * OW, W - j0), n = nr * nc;
+  for (int base = tid_flat(); base < n; base += kQB * kThreads) {
+    float fv[kQB];
+#pragma unroll
+    for (int k = 0; k < kQB; ++k) {
+      const int item = base + k * kThreads;
+      fv[k] = 0.f;
+      if (item < n) {
+        const int oi = item / nc;
+        fv[k] = __ldg(f + (size_t)(i0 + oi) * ldf + j0 + (item - oi * nc));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kQB; ++k) {
+      const int item = base + k * kThreads;
+      if (item >= n) break;
+      const int oi = item / nc, oj2 = item - oi * nc;
+      const int second = oj2 >= OW, c = dx + oj2 - (second ? OW : 0);
+      const float2 v = A[(dy + oi) * kRS + c + (c >> 4)];
+      const int i = i0 + oi, j = j0 + oj2;
+      const float2 q = weighted_residual(second ? v.y : v.x, fmaxf(fv[k], p.floor), p);
+      qe[(size_t)i * ldqp + j] = q.x;
+      qw[(size_t)i * ldqp + j] = q.y;
+    }
   }
 }
 

@@ -19,6 +19,8 @@
 // exactly, which gives the zero-flux diffusion term.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "internal.cuh"
 #include "rrl_box.cuh"
 #include "rrl_dense.cuh"
@@ -303,16 +305,26 @@ __global__ void __launch_bounds__((TH / kDR) * (TW / kDC), 6) k_rrl_update_dense
 // FFT tiles (rrl_fft_tile.cuh): the q kernel takes two horizontally
 // adjacent tiles per CTA (blockIdx.x pairs), the update kernel one; q is
 // planar as for the dense bodies.
+// umap (use_tma): the 3D tensor map of uin's images for the TMA-staged
+// windows (encode_window_map; kBoxW x kN boxes).
 __global__ void __launch_bounds__(256, 4) k_rrl_q_fft(const float* __restrict__ f, int ldf, const float* uin,
                                                      int ldin, float2* q, int H, int W,
                                                      const TapGroup* __restrict__ groups_g, int kh, int kw,
-                                                     RrlParams p, ZStride zs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                     RrlParams p, ZStride zs,
+                                                     const __grid_constant__ CUtensorMap umap, int use_tma,
+                                                     int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ unsigned long long bar;
+  if (use_tma) {
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+  }
   const long long z = blockIdx.z;
   float* qe = reinterpret_cast<float*>(q + z * zs.q);
+  const ftile::WinTma tma = {&umap, (int)blockIdx.z, &bar, 0u, kTmaWaitLimit, status};
   ftile::q_tile(smem_raw, f + z * zs.f, ldf, uin + z * zs.in, ldin, qe, qe + (size_t)H * upitch(W), upitch(W), H, W,
                 fft_tile_spec(groups_g, kh, kw), kh, kw, p, blockIdx.y * ftile::tile_oh(kh),
-                2 * blockIdx.x * ftile::tile_ow(kw), PdlDep());
+                2 * blockIdx.x * ftile::tile_ow(kw), PdlDep(), use_tma ? &tma : nullptr);
 }
 
 __global__ void __launch_bounds__(256, 4) k_rrl_update_fft(const float2* q, const float* uin, int ldin,
@@ -507,8 +519,12 @@ static cudaError_t launch_split_fft(const IterArgs& a, cudaStream_t s) {
   cfg.numAttrs = 1;
   cfg.gridDim = dim3((tx + 1) / 2, ty, a.nz);
   cfg.dynamicSmemBytes = sq;
+  CUtensorMap umap;
+  const int use_tma = tma_enabled() &&
+                      encode_window_map(&umap, a.uin, a.W, a.H, a.ldin, a.nz, a.zs.in, ftile::kBoxW, ftile::kN);
+  if (!use_tma) memset(&umap, 0, sizeof(umap));
   if ((e = cudaLaunchKernelEx(&cfg, k_rrl_q_fft, a.f, a.ldf, a.uin, a.ldin, a.q, a.H, a.W, a.groups, a.kh, a.kw,
-                              a.p, a.zs)) != cudaSuccess)
+                              a.p, a.zs, umap, use_tma, a.status)) != cudaSuccess)
     return e;
   count_launch();
   cfg.gridDim = dim3(tx, ty, a.nz);

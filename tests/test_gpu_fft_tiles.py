@@ -160,3 +160,47 @@ def test_fft_tiles_checkpoints(lib, fft_all):
     b = lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 6, ckpt=ck, ckpt_every=2)
     assert torch.equal(a, b)
     assert torch.equal(ck[0], cuda(u0))
+
+
+@pytest.mark.parametrize("H,W,kh,kw", [
+    (77, 132, 9, 9),      # ragged rows, TMA windows over every edge
+    (36, 40, 15, 15),     # image smaller than a window: clamped on all four sides
+    (97, 200, 48, 2),     # the largest height
+    (68, 128, 2, 48),     # the largest width: the box's widest reach (130 of 136 columns)
+    (300, 516, 25, 24),   # many interior tiles, even width of the PSF
+    (77, 131, 9, 9),      # row stride not a multiple of 4: element-wise loads on the caller's buffer
+])
+def test_fft_tiles_tma_equals_elementwise(lib, fft_all, H, W, kh, kw):
+    """The q phase's windows staged by one TMA tensor copy (with the
+    constant continuation applied in shared memory) give the bits of the
+    element-wise clamped loads."""
+    rng = np.random.default_rng(kh * 7 + kw)
+    h = _psf(kh, kw, rng)
+    p = Params()
+    f, u0 = _case(H, W, h, H + 3 * W)
+    outs = []
+    try:
+        for on in (True, False):
+            lib.set_tma(on)
+            outs.append(lib.rrl_iterate(cuda(f), cuda(u0), cuda(h), p, 3))
+    finally:
+        lib.set_tma(True)
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_fft_tiles_tma_n_images(lib, fft_all):
+    """db_deblur_n over three images: one 3D tensor map (image index as the
+    third coordinate) gives each image's element-wise bits."""
+    rng = np.random.default_rng(14)
+    h = _psf(13, 17, rng)
+    H, W, n = 90, 116, 3
+    fs = np.stack([_case(H, W, h, 60 + k)[0] for k in range(n)])
+    p = Params(K=0.006)
+    outs = []
+    try:
+        for on in (True, False):
+            lib.set_tma(on)
+            outs.append(lib.deblur_n(cuda(fs), cuda(h), p, 4))
+    finally:
+        lib.set_tma(True)
+    assert torch.equal(outs[0], outs[1])
