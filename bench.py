@@ -156,7 +156,7 @@ class ClockSampler:
 # (flow) schedule: one ncu capture of the persistent launch (20 iterations,
 # dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # capture), divided by the iteration count.
-LINE1024_FLOW_ITER_DRAM_BYTES = (8.489728e6 + 1.274112e6) / 20
+LINE1024_FLOW_ITER_DRAM_BYTES = (8.488448e6 + 1.435136e6) / 20
 
 
 # DRAM bytes per pixel and iteration of k_rrl_batch on batch512
@@ -239,11 +239,21 @@ def _spatial_model(case, ms_iter, schedule="auto"):
                         traffic=traffic, flops=flops_per_px_iter(case.h, case.psf_kind) * H * W)
 
 
+# DRAM bytes of one periodic iteration on the gauss2048 workload: one ncu
+# capture of its four launches (dram__bytes_read.sum + dram__bytes_write.sum,
+# caches flushed between passes).  Set to None when the kernels change, until
+# they are captured again.
+GAUSS2048_ITER_DRAM_BYTES = (67.135488 + 1.007360 + 50.380032 + 4.249856 + 67.135232 + 1.110784
+                             + 50.377984 + 11.309056) * 1e6
+
+
 def _fourier_model(case, ms_iter, schedule="auto"):
     """One periodic RRRL iteration: 68 algorithmic B/px (four passes)."""
     H, W = case.f.shape
+    traffic = GAUSS2048_ITER_DRAM_BYTES if case.name == "gauss2048" and (H, W) == (2048, 2048) else None
     return hbm_roofline(ALGO_BYTES["fourier"], H * W, ms_iter,
-                        "one Fourier RRRL iteration (k_fourier_cols x2 + k_fourier_rows x2)")
+                        "one Fourier RRRL iteration (k_fourier_cols8 x2, k_fourier_mid8, k_fourier_rows8; "
+                        "k_fourier_cols / k_fourier_rows for sides below 64)", traffic=traffic)
 
 
 def _make(name):
