@@ -392,20 +392,19 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
   const int nr = min(OH, H - i0), nc = min(2 * OW, W - j0), n = nr * nc;
   for (int base = tid_flat(); base < n; base += kQB * kThreads) {
     float fv[kQB];
+    int ois[kQB], ojs[kQB];
 #pragma unroll
     for (int k = 0; k < kQB; ++k) {
       const int item = base + k * kThreads;
       fv[k] = 0.f;
-      if (item < n) {
-        const int oi = item / nc;
-        fv[k] = __ldg(f + (size_t)(i0 + oi) * ldf + j0 + (item - oi * nc));
-      }
+      ois[k] = item / nc;
+      ojs[k] = item - ois[k] * nc;
+      if (item < n) fv[k] = __ldg(f + (size_t)(i0 + ois[k]) * ldf + j0 + ojs[k]);
     }
 #pragma unroll
     for (int k = 0; k < kQB; ++k) {
-      const int item = base + k * kThreads;
-      if (item >= n) break;
-      const int oi = item / nc, oj2 = item - oi * nc;
+      if (base + k * kThreads >= n) break;
+      const int oi = ois[k], oj2 = ojs[k];
       const int second = oj2 >= OW, c = dx + oj2 - (second ? OW : 0);
       const float2 v = A[(dy + oi) * kRS + c + (c >> 4)];
       const int i = i0 + oi, j = j0 + oj2;
