@@ -390,6 +390,9 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
   // kQB whose f loads are issued together.
   constexpr int kQB = 4;
   const int nr = min(OH, H - i0), nc = min(2 * OW, W - j0), n = nr * nc;
+  // item = oi nc + oj2, advanced by kThreads = dq nc + dr without a division
+  const int dq = kThreads / nc, dr = kThreads - dq * nc;
+  int oi_n = tid_flat() / nc, oj_n = tid_flat() - oi_n * nc;
   for (int base = tid_flat(); base < n; base += kQB * kThreads) {
     float fv[kQB];
     int ois[kQB], ojs[kQB];
@@ -397,9 +400,12 @@ __device__ __forceinline__ void q_tile(unsigned char* smem_raw, const float* __r
     for (int k = 0; k < kQB; ++k) {
       const int item = base + k * kThreads;
       fv[k] = 0.f;
-      ois[k] = item / nc;
-      ojs[k] = item - ois[k] * nc;
-      if (item < n) fv[k] = __ldg(f + (size_t)(i0 + ois[k]) * ldf + j0 + ojs[k]);
+      ois[k] = oi_n;
+      ojs[k] = oj_n;
+      if (item < n) fv[k] = __ldg(f + (size_t)(i0 + oi_n) * ldf + j0 + oj_n);
+      oi_n += dq;
+      oj_n += dr;
+      if (oj_n >= nc) { oj_n -= nc; ++oi_n; }
     }
 #pragma unroll
     for (int k = 0; k < kQB; ++k) {
@@ -453,8 +459,11 @@ __device__ __forceinline__ void update_tile(unsigned char* smem_raw, const float
   __syncthreads();
   bool bad = false;
   const int nsr = (OH + kSR - 1) / kSR;
-  for (int item = tid_flat(); item < nsr * OW; item += kThreads) {
-    const int sr = item / OW, oj = item - sr * OW;
+  // item = sr OW + oj, advanced by kThreads = dq OW + dr without a division
+  const int dq = kThreads / OW, dr = kThreads - dq * OW;
+  int sr = tid_flat() / OW, oj = tid_flat() - sr * OW;
+  for (int item = tid_flat(); item < nsr * OW; item += kThreads, sr += dq, oj += dr) {
+    if (oj >= OW) { oj -= OW; ++sr; }
     const int oi0 = sr * kSR, j = j0 + oj;
     if (j >= W) continue;
     float D[kSR], ctr[kSR];
