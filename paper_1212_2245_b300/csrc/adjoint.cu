@@ -702,16 +702,42 @@ __device__ __forceinline__ void run_window(const T* x, F f) {
   }
 }
 
+// (row, column) of a loop index over rows of n columns that starts at
+// `start` and advances by `stride`, kept without a division per step.
+struct RowCol {
+  int r, c, dr, dc, n;
+  __device__ __forceinline__ RowCol(int start, int stride, int n_) : n(n_) {
+    r = start / n;
+    c = start - r * n;
+    dr = stride / n;
+    dc = stride - dr * n;
+  }
+  __device__ __forceinline__ void next() {
+    r += dr;
+    c += dc;
+    if (c >= n) { c -= n; ++r; }
+  }
+};
+
+// Row within its image of row r of the block starting at stacked row R0
+// (ib = R0 mod H).
+__device__ __forceinline__ int image_row(int ib, int r, int H) {
+  int i = ib + r;
+  while (i >= H) i -= H;
+  return i;
+}
+
 // Row-block loop: the CTA takes kAdjRowBlock rows at a time (grid-stride).
 #define ADJ_ROW_BLOCKS(rows)                                                                       \
   for (int R0 = blockIdx.x * kAdjRowBlock; R0 < (rows); R0 += gridDim.x * kAdjRowBlock)
+// Pixel loop over nr rows of W: row rc_.r, column rc_.c.
 #define ADJ_ROW_ITEMS(nr, W)                                                                       \
-  for (int it = threadIdx.x; it < (nr) * (W); it += blockDim.x)
-// Run loop: run `it` of row r starts at column j0 and holds n outputs.
+  for (RowCol rc_(threadIdx.x, blockDim.x, (W)); rc_.r < (nr); rc_.next())
+// Run loop: run rc_.c of row r starts at column j0 and holds n outputs.
 #define ADJ_ROW_RUNS(nr, nrun, W)                                                                  \
-  for (int it = threadIdx.x; it < (nr) * (nrun); it += blockDim.x)
+  for (RowCol rc_(threadIdx.x, blockDim.x, (nrun)); rc_.r < (nr); rc_.next())
 #define ADJ_RUN_DECOMPOSE(nrun, W)                                                                 \
-  const int r = it / (nrun), j0 = (it - r * (nrun)) * RUN, n = min(RUN, (W) - j0);
+  const int r = rc_.r, j0 = rc_.c * RUN, n = min(RUN, (W) - j0);
 
 // Forward recompute of one iteration for one-row PSFs, fused: b = C u and
 // q = (W f/b, W) into a shared row, then A, B = C' q and g from it.
@@ -733,7 +759,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
   const bool vec = (W & 3) == 0 && al16(u) && al16(f0) && al16(b_out) && al16(q_out) && al16(ab_out) && al16(g_out);
   load_row_taps<KWB>(taps, im);
   ADJ_ROW_BLOCKS(rows) {
-    const int nr = min(kAdjRowBlock, rows - R0);
+    const int nr = min(kAdjRowBlock, rows - R0), ib = R0 % H;
     __syncthreads();
     stage_rows<RUN, float, true>(su, u, R0, nr, W, shu);
     __syncthreads();
@@ -787,8 +813,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
           B[s] = fmaf(w, win[s].y, B[s]);
         }
       });
-      const int Rr = R0 + r, img = Rr / H, i = Rr - img * H;
-      const float* ip = u + (size_t)img * H * W + j0;
+      const int Rr = R0 + r, i = image_row(ib, r, H);
+      const float* ip = u + (size_t)(Rr - i) * W + j0;
       const float* ur = su + r * P;
       float up[RUN], dn[RUN];
       run_load(up, ip + (size_t)clampi(i - 1, H) * W, n, full);
@@ -819,7 +845,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_fwd_rows(const float* __res
 // transposes, summed per tap) in part[G + t G ...].  The diffusion adjoint
 // (k_adj_rev_diff) follows: it needs Dbar of the neighbouring rows.
 template <int KWB>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
+__global__ void __launch_bounds__(kAdjThreads, KWB <= 24 ? 3 : 2) k_adj_rev_rows(
     const float* __restrict__ Ubar_next, const float* __restrict__ u, const float2* __restrict__ ab,
     const float* __restrict__ g, const float2* __restrict__ q, const float* __restrict__ b,
     const float* __restrict__ f0, AdjImage im, float* __restrict__ Uacc, float* __restrict__ Dbar,
@@ -851,10 +877,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rev_rows(
       sb[r * P + pidx<RUN>(kAdjRowPad + shp + jj)] = 0.f;
     }
     // U = U' num/den, Abar, Bbar, Dbar
+    const int ib = R0 % H;
     ADJ_ROW_ITEMS(nr, W) {
-      const int r = it / W, j = it - r * W;
-      const int R = R0 + r, n = R / H, i = R - n * H;
-      const size_t o = (size_t)n * H * W, idx = (size_t)R0 * W + it;
+      const int r = rc_.r, j = rc_.c;
+      const int R = R0 + r, i = image_row(ib, r, H);
+      const size_t o = (size_t)(R - i) * W, idx = (size_t)R * W + j;
       const float D = diffusion_at(u + o, g + o, i, j, H, W);
       const float2 v = ab[idx];
       const float Dp = fmaxf(D, 0.f), Dm = fminf(D, 0.f);
