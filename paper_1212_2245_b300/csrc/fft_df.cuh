@@ -118,9 +118,30 @@ struct WienerState {
   const float4* kspec = nullptr;  // filter spectra of the filtering passes (non-power-of-two axis), or null
 };
 
-__device__ __forceinline__ void seq_item_ff(int it, int nseq, int len, bool seq_fast, int& q, int& k) {
-  if (seq_fast) { q = it % nseq; k = it / nseq; } else { q = it / len; k = it - q * len; }
+// Quotient and remainder of 0 <= n < 2^24 by a divisor 1 <= d < 2^24 fixed
+// for a loop, through a float reciprocal formed once: the product n (1/d)
+// is within one of n / d, and one step on the remainder makes it exact.
+struct DivBy {
+  float r;
+  int d;
+};
+__device__ __forceinline__ DivBy div_by(int d) { return DivBy{__frcp_rn((float)d), d}; }
+__device__ __forceinline__ int div_q(int n, const DivBy& v, int& rem) {
+  int q = __float2int_rz((float)n * v.r);
+  rem = n - q * v.d;
+  if (rem < 0) { --q; rem += v.d; }
+  else if (rem >= v.d) { ++q; rem -= v.d; }
+  return q;
 }
+
+// Item `it` of nseq sequences of len items: sequence q, item k (seq_fast:
+// consecutive items in consecutive sequences).  dv = div_by(seq_fast ? nseq
+// : len).
+__device__ __forceinline__ void seq_item_ff(int it, const DivBy& dv, bool seq_fast, int& q, int& k) {
+  if (seq_fast) k = div_q(it, dv, q);
+  else q = div_q(it, dv, k);
+}
+__device__ __forceinline__ DivBy seq_div(int nseq, int len, bool seq_fast) { return div_by(seq_fast ? nseq : len); }
 // The same with shifts: nseq = 2^lns sequences of 2^lnb items each.
 __device__ __forceinline__ void split_item_ff(int it, int lns, int lnb, bool seq_fast, int& q, int& b) {
   if (seq_fast) { q = it & ((1 << lns) - 1); b = it >> lns; }
@@ -129,12 +150,13 @@ __device__ __forceinline__ void split_item_ff(int it, int lns, int lnb, bool seq
 
 // Item `it` of nseq (a power of two, 2^lns) sequences x nsub contiguous
 // sub-blocks x 2^lnb items: sequence q, sub-block u, item b.
-__device__ __forceinline__ void sub_item_ff(int it, int lns, int nsub, int lnb, bool seq_fast, int& q, int& u,
-                                            int& b) {
+// dv = div_by(nsub << lnb) (used when nsub > 1 and not seq_fast).
+__device__ __forceinline__ void sub_item_ff(int it, int lns, int nsub, int lnb, bool seq_fast, const DivBy& dv,
+                                            int& q, int& u, int& b) {
   int r;
   if (seq_fast) { q = it & ((1 << lns) - 1); r = it >> lns; }
   else if (nsub == 1) { q = it >> lnb; r = it - (q << lnb); }
-  else { q = it / (nsub << lnb); r = it - q * (nsub << lnb); }
+  else q = div_q(it, dv, r);
   u = r >> lnb;
   b = r & ((1 << lnb) - 1);
 }
@@ -145,6 +167,7 @@ __device__ __forceinline__ void sub_item_ff(int it, int lns, int nsub, int lnb, 
 __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss, const float4* __restrict__ tw,
                                   bool seq_fast, int nsub = 1, int twmul = 1) {
   const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
+  const DivBy dv2 = div_by(logN >= 2 ? nsub << (logN - 2) : 1), dv1 = div_by(logN >= 1 ? nsub << (logN - 1) : 1);
   const int nb = N >> 2;
   int logLen = logN;
   while (logLen >= 2) {
@@ -153,7 +176,7 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
     if (m == 1) {  // blocks of 4: every twiddle is 1
       for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
         int q, u, b;
-        sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
+        sub_item_ff(it, lns, nsub, logN - 2, seq_fast, dv2, q, u, b);
         float4* p = x + q * ss + ((u << logN) + b * 4) * es;
         const float4 x0 = p[0], x1 = p[es], x2 = p[2 * es], x3 = p[3 * es];
         const float4 y0 = zadd(x0, x2), y2 = zsub(x0, x2);
@@ -169,7 +192,7 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
     }
     for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
       int q, u, b;
-      sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
+      sub_item_ff(it, lns, nsub, logN - 2, seq_fast, dv2, q, u, b);
       const int blk = b >> logm, j = b & (m - 1);
       float4* p = x + q * ss + ((u << logN) + blk * len + j) * es;
       const int sm = m * es;
@@ -191,7 +214,7 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
   if (logLen == 1) {
     for (int it = threadIdx.x; it < nseq * nsub * (N >> 1); it += blockDim.x) {
       int q, u, b;
-      sub_item_ff(it, lns, nsub, logN - 1, seq_fast, q, u, b);
+      sub_item_ff(it, lns, nsub, logN - 1, seq_fast, dv1, q, u, b);
       float4* p = x + q * ss + ((u << logN) + 2 * b) * es;
       const float4 a = p[0], c = p[es];
       p[0] = zadd(a, c);
@@ -205,12 +228,13 @@ __device__ inline void fft_dif_ff(float4* x, int logN, int nseq, int es, int ss,
 __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int ss,
                                       const float4* __restrict__ tw, bool seq_fast, int nsub = 1, int twmul = 1) {
   const int N = 1 << logN, lns = 31 - __clz(nseq);  // nseq: a power of two
+  const DivBy dv2 = div_by(logN >= 2 ? nsub << (logN - 2) : 1), dv1 = div_by(logN >= 1 ? nsub << (logN - 1) : 1);
   const int nb = N >> 2;
   int logLen = (logN & 1) ? 1 : 0;
   if (logLen == 1) {
     for (int it = threadIdx.x; it < nseq * nsub * (N >> 1); it += blockDim.x) {
       int q, u, b;
-      sub_item_ff(it, lns, nsub, logN - 1, seq_fast, q, u, b);
+      sub_item_ff(it, lns, nsub, logN - 1, seq_fast, dv1, q, u, b);
       float4* p = x + q * ss + ((u << logN) + 2 * b) * es;
       const float4 a = p[0], c = p[es];
       p[0] = zadd(a, c);
@@ -224,7 +248,7 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
     if (m == 1) {  // blocks of 4: every twiddle is 1
       for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
         int q, u, b;
-        sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
+        sub_item_ff(it, lns, nsub, logN - 2, seq_fast, dv2, q, u, b);
         float4* p = x + q * ss + ((u << logN) + b * 4) * es;
         const float4 z0 = p[0], z1 = p[es], z2 = p[2 * es], z3 = p[3 * es];
         const float4 y0 = zadd(z0, z1), y1 = zsub(z0, z1);
@@ -239,7 +263,7 @@ __device__ inline void fft_dit_inv_ff(float4* x, int logN, int nseq, int es, int
     }
     for (int it = threadIdx.x; it < nseq * nsub * nb; it += blockDim.x) {
       int q, u, b;
-      sub_item_ff(it, lns, nsub, logN - 2, seq_fast, q, u, b);
+      sub_item_ff(it, lns, nsub, logN - 2, seq_fast, dv2, q, u, b);
       const int blk = b >> logm, j = b & (m - 1);
       float4* p = x + q * ss + ((u << logN) + blk * len + j) * es;
       const int sm = m * es;
@@ -276,10 +300,11 @@ __device__ inline void fft3_dif_ff(float4* x, const Dft1ff& D, int nseq, int es,
   int len = M;
   for (int st = 0; st < D.M3; ++st, len /= 3) {
     const int m = len / 3, tstep = M / len;
+    const DivBy dvs = seq_div(nseq, nt, seq_fast), dvm = div_by(m);
     for (int it = threadIdx.x; it < nseq * nt; it += blockDim.x) {
-      int q, b;
-      seq_item_ff(it, nseq, nt, seq_fast, q, b);
-      const int blk = b / m, j = b - blk * m;
+      int q, b, j;
+      seq_item_ff(it, dvs, seq_fast, q, b);
+      const int blk = div_q(b, dvm, j);
       float4* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
       const float4 x0 = p[0], x1 = p[sm], x2 = p[2 * sm];
@@ -304,10 +329,11 @@ __device__ inline void fft3_dit_inv_ff(float4* x, const Dft1ff& D, int nseq, int
   int len = 3 << D.logM;
   for (int st = 0; st < D.M3; ++st, len *= 3) {
     const int m = len / 3, tstep = M / len;
+    const DivBy dvs = seq_div(nseq, nt, seq_fast), dvm = div_by(m);
     for (int it = threadIdx.x; it < nseq * nt; it += blockDim.x) {
-      int q, b;
-      seq_item_ff(it, nseq, nt, seq_fast, q, b);
-      const int blk = b / m, j = b - blk * m;
+      int q, b, j;
+      seq_item_ff(it, dvs, seq_fast, q, b);
+      const int blk = div_q(b, dvm, j);
       float4* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
       const float4 z0 = p[0];
@@ -343,25 +369,28 @@ __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft
     return;
   }
   const int N = D.N, M = dft_len(D);
+  const DivBy dv1_ = seq_div(nseq, M, seq_fast);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    seq_item_ff(it, dv1_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = (k < N) ? zmulc(*p, __ldg(D.c + k)) : zzero();
   }
   __syncthreads();
   fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
+  const DivBy dv2_ = seq_div(nseq, M, seq_fast);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    seq_item_ff(it, dv2_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zmul(*p, __ldg(D.Bf + k));
   }
   __syncthreads();
   fft_inv_m_ff(x, D, nseq, es, ss, seq_fast);
+  const DivBy dv3_ = seq_div(nseq, N, seq_fast);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, N, seq_fast, q, k);
+    seq_item_ff(it, dv3_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zscale(zmulc(*p, __ldg(D.c + k)), D.invM);
   }
@@ -375,17 +404,19 @@ __device__ inline void dft_inv_ff(float4* x, int nseq, int es, int ss, const Dft
     return;
   }
   const int N = D.N;
+  const DivBy dv4_ = seq_div(nseq, N, seq_fast);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, N, seq_fast, q, k);
+    seq_item_ff(it, dv4_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zconj(*p);
   }
   __syncthreads();
   dft_fwd_ff(x, nseq, es, ss, D, seq_fast);
+  const DivBy dv5_ = seq_div(nseq, N, seq_fast);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, N, seq_fast, q, k);
+    seq_item_ff(it, dv5_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zconj(*p);
   }

@@ -151,18 +151,20 @@ __device__ __forceinline__ float ff_round(float2 v) { return v.x + v.y; }
 // storage order of fft_fwd_m_ff.  Ends with a barrier.
 __device__ inline void kernel_spectrum_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
   const int N = D.N, M = dft_len(D), P = M - N;
+  const DivBy dv1_ = seq_div(nseq, P, seq_fast);
   for (int it = threadIdx.x; it < nseq * P; it += blockDim.x) {
     int q, j;
-    seq_item_ff(it, nseq, P, seq_fast, q, j);
+    seq_item_ff(it, dv1_, seq_fast, q, j);
     float4* base = x + q * ss;
     const int m = N + j;  // targets m >= N; sources m - M + N < N
     base[m * es] = (m >= M - N + 1) ? base[(m - M + N) * es] : zzero();
   }
   __syncthreads();
   fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
+  const DivBy dv2_ = seq_div(nseq, M, seq_fast);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    seq_item_ff(it, dv2_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zscale(*p, D.invM);
   }
@@ -177,16 +179,18 @@ __device__ inline void kernel_spectrum_ff(float4* x, int nseq, int es, int ss, c
 __device__ inline void filter_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast,
                                  const float4* __restrict__ ks, int ksm, int ksq, int nvalid) {
   const int N = D.N, M = dft_len(D), P = M - N;
+  const DivBy dv3_ = seq_div(nseq, P, seq_fast);
   for (int it = threadIdx.x; it < nseq * P; it += blockDim.x) {
     int q, j;
-    seq_item_ff(it, nseq, P, seq_fast, q, j);
+    seq_item_ff(it, dv3_, seq_fast, q, j);
     x[q * ss + (N + j) * es] = zzero();
   }
   __syncthreads();
   fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
+  const DivBy dv4_ = seq_div(nseq, M, seq_fast);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, nseq, M, seq_fast, q, k);
+    seq_item_ff(it, dv4_, seq_fast, q, k);
     if (q >= nvalid) continue;
     float4* p = x + q * ss + k * es;
     *p = zmul(*p, __ldg(ks + (size_t)k * ksm + (size_t)q * ksq));
@@ -221,10 +225,12 @@ __device__ __forceinline__ void unpack_pair(float4 Zk, float4 Zm, float4& X1, fl
 template <int MODE>
 __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q0, int R) {
   const int N = a.D.N, M = dft_len(a.D);
+  const DivBy dN = div_by(N), dM = div_by(M), dNh = div_by(N / 2 + 1);
   float4* x = smem4;
   float* stage = (float*)(x + R * M);  // real rows (x2 for row pairs)
   for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-    const int r = idx / N, c = idx - r * N;
+    int c;
+    const int r = div_q(idx, dN, c);
     const int q = q0 + r;
     if (q >= a.nrows) continue;
     if (MODE == ROW_FWD_REAL) {
@@ -243,7 +249,8 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
     // Z = Y1 + i Y2, placed in transform order
     const int Nh = N / 2 + 1;
     for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-      const int r = idx / N, k = idx - r * N;
+      int k;
+      const int r = div_q(idx, dN, k);
       const int q = q0 + r;
       float4 Z = zzero();
       if (q < a.nrows) {
@@ -258,7 +265,8 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
     }
   } else if (MODE != ROW_INV_REAL && MODE != ROW_FWD_CPLX) {
     for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-      const int r = idx / N, c = idx - r * N;
+    int c;
+    const int r = div_q(idx, dN, c);
       const int q = q0 + r;
       float4 v = zzero();
       if (q < a.nrows) {
@@ -298,7 +306,8 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
     dft_fwd_ff(x, R, 1, M, a.D, false);
     if (MODE == ROW_WIENER_1D) {
       for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-        const int r = idx / N, c = idx - r * N;
+    int c;
+    const int r = div_q(idx, dN, c);
         x[r * M + c] = wiener_gain(__ldg(&a.spec[c]), x[r * M + c], a.K);
       }
       __syncthreads();
@@ -307,14 +316,16 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
   }
   if constexpr (MODE == ROW_KSPEC) {  // all M elements of each filter spectrum
     for (int idx = threadIdx.x; idx < R * M; idx += blockDim.x) {
-      const int r = idx / M, m = idx - r * M;
+      int m;
+      const int r = div_q(idx, dM, m);
       const int q = q0 + r;
       if (q < a.nrows) a.cbuf[(size_t)q * a.ldc + m] = x[r * M + m];
     }
   } else if constexpr (MODE == ROW_FWD_R2C || MODE == ROW_PSF_R2C) {
     const int Nh = N / 2 + 1;
     for (int idx = threadIdx.x; idx < R * Nh; idx += blockDim.x) {
-      const int r = idx / Nh, k = idx - r * Nh;
+      int k;
+      const int r = div_q(idx, dNh, k);
       const int q = q0 + r;
       if (q >= a.nrows) continue;
       float4 X1, X2;
@@ -324,7 +335,8 @@ __device__ __forceinline__ void rows_body(float4* smem4, const FftArgs& a, int q
     }
   } else {
     for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
-      const int r = idx / N, c = idx - r * N;
+    int c;
+    const int r = div_q(idx, dN, c);
       const int q = q0 + r;
       if (q >= a.nrows) continue;
       const float4 v = x[r * M + c];
