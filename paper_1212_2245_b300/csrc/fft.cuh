@@ -270,76 +270,4 @@ __device__ inline void fft_dit_inv_blk(float2* x, int logN, int nseq, int es, in
   }
 }
 
-// Thread -> (sequence q, element k) mapping shared by the routines below.
-__device__ __forceinline__ void seq_item(int it, int nseq, int len, bool seq_fast, int& q, int& k) {
-  if (seq_fast) { q = it % nseq; k = it / nseq; } else { q = it / len; k = it - q * len; }
-}
-
-// Forward DFT of `nseq` sequences (capacity 2^D.logM each, data in the first
-// D.N elements, element k of sequence q at x[q*ss + k*es]).  Power-of-two N:
-// the DIF sweep, output bit-reversed.  Otherwise Bluestein: premultiply by
-// conj(c), circular convolution with the chirp via the power-of-two sweeps
-// and the precomputed chirp spectrum, post-multiply by conj(c) and 1/M;
-// output in natural order in the first N elements.  Ends with __syncthreads().
-__device__ inline void dft_fwd(float2* x, int nseq, int es, int ss, const Dft1& D, const float2* tw,
-                               bool seq_fast) {
-  if (D.c == nullptr) {
-    fft_dif(x, D.logM, nseq, es, ss, tw, 0, seq_fast);
-    return;
-  }
-  const int N = D.N, M = 1 << D.logM;
-  for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
-    int q, k;
-    seq_item(it, nseq, M, seq_fast, q, k);
-    float2* p = x + q * ss + k * es;
-    *p = (k < N) ? cmulc(*p, __ldg(D.c + k)) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_dif(x, D.logM, nseq, es, ss, tw, 0, seq_fast);
-  for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
-    int q, k;
-    seq_item(it, nseq, M, seq_fast, q, k);
-    float2* p = x + q * ss + k * es;
-    *p = cmul(*p, __ldg(D.Bf + k));
-  }
-  __syncthreads();
-  fft_dit_inv(x, D.logM, nseq, es, ss, tw, 0, seq_fast);
-  const float invM = 1.0f / (float)M;
-  for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
-    int q, k;
-    seq_item(it, nseq, N, seq_fast, q, k);
-    float2* p = x + q * ss + k * es;
-    const float2 v = cmulc(*p, __ldg(D.c + k));
-    *p = make_float2(v.x * invM, v.y * invM);
-  }
-  __syncthreads();
-}
-
-// Inverse DFT, unnormalised (N times the inverse), taking the storage order
-// dft_fwd produces back to natural order.  Bluestein: conj(DFT(conj(.))).
-// Ends with __syncthreads().
-__device__ inline void dft_inv(float2* x, int nseq, int es, int ss, const Dft1& D, const float2* tw,
-                               bool seq_fast) {
-  if (D.c == nullptr) {
-    fft_dit_inv(x, D.logM, nseq, es, ss, tw, 0, seq_fast);
-    return;
-  }
-  const int N = D.N;
-  for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
-    int q, k;
-    seq_item(it, nseq, N, seq_fast, q, k);
-    float2* p = x + q * ss + k * es;
-    p->y = -p->y;
-  }
-  __syncthreads();
-  dft_fwd(x, nseq, es, ss, D, tw, seq_fast);
-  for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
-    int q, k;
-    seq_item(it, nseq, N, seq_fast, q, k);
-    float2* p = x + q * ss + k * es;
-    p->y = -p->y;
-  }
-  __syncthreads();
-}
-
 }  // namespace db

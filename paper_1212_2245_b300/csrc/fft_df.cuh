@@ -361,8 +361,12 @@ __device__ inline void fft_inv_m_ff(float4* x, const Dft1ff& D, int nseq, int es
   if (D.M3 > 0) fft3_dit_inv_ff(x, D, nseq, es, ss, seq_fast);
 }
 
-// Forward DFT (power of two: DIF, bit-reversed; else Bluestein, natural).
-// Same contract as dft_fwd.  Ends with a barrier.
+// Forward DFT of nseq sequences (capacity dft_len(D) each, data in the first
+// D.N elements, element k of sequence q at x[q*ss + k*es]).  Power-of-two N:
+// the DIF sweep, output bit-reversed.  Otherwise Bluestein: premultiply by
+// conj(c), circular convolution with the chirp through the length-M sweeps
+// and the chirp's precomputed spectrum, post-multiply by conj(c) and 1/M;
+// output in natural order in the first N elements.  Ends with a barrier.
 __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
   if (D.c == nullptr) {
     fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
@@ -397,7 +401,9 @@ __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft
   __syncthreads();
 }
 
-// Inverse DFT (unnormalised), see dft_inv.  Ends with a barrier.
+// Inverse DFT, unnormalised (N times the inverse), taking the storage order
+// dft_fwd_ff produces back to natural order; Bluestein as conj(DFT(conj(.))).
+// Ends with a barrier.
 __device__ inline void dft_inv_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
   if (D.c == nullptr) {
     fft_inv_m_ff(x, D, nseq, es, ss, seq_fast);
