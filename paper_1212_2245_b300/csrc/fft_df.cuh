@@ -135,13 +135,12 @@ __device__ __forceinline__ int div_q(int n, const DivBy& v, int& rem) {
 }
 
 // Item `it` of nseq sequences of len items: sequence q, item k (seq_fast:
-// consecutive items in consecutive sequences).  dv = div_by(seq_fast ? nseq
-// : len).
-__device__ __forceinline__ void seq_item_ff(int it, const DivBy& dv, bool seq_fast, int& q, int& k) {
-  if (seq_fast) k = div_q(it, dv, q);
+// consecutive items in consecutive sequences; the column kernels' nseq is a
+// compile-time power of two there).  dv = div_by(len).
+__device__ __forceinline__ void seq_item_ff(int it, int nseq, const DivBy& dv, bool seq_fast, int& q, int& k) {
+  if (seq_fast) { q = it % nseq; k = it / nseq; }
   else q = div_q(it, dv, k);
 }
-__device__ __forceinline__ DivBy seq_div(int nseq, int len, bool seq_fast) { return div_by(seq_fast ? nseq : len); }
 // The same with shifts: nseq = 2^lns sequences of 2^lnb items each.
 __device__ __forceinline__ void split_item_ff(int it, int lns, int lnb, bool seq_fast, int& q, int& b) {
   if (seq_fast) { q = it & ((1 << lns) - 1); b = it >> lns; }
@@ -300,10 +299,10 @@ __device__ inline void fft3_dif_ff(float4* x, const Dft1ff& D, int nseq, int es,
   int len = M;
   for (int st = 0; st < D.M3; ++st, len /= 3) {
     const int m = len / 3, tstep = M / len;
-    const DivBy dvs = seq_div(nseq, nt, seq_fast), dvm = div_by(m);
+    const DivBy dvs = div_by(nt), dvm = div_by(m);
     for (int it = threadIdx.x; it < nseq * nt; it += blockDim.x) {
       int q, b, j;
-      seq_item_ff(it, dvs, seq_fast, q, b);
+      seq_item_ff(it, nseq, dvs, seq_fast, q, b);
       const int blk = div_q(b, dvm, j);
       float4* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
@@ -329,10 +328,10 @@ __device__ inline void fft3_dit_inv_ff(float4* x, const Dft1ff& D, int nseq, int
   int len = 3 << D.logM;
   for (int st = 0; st < D.M3; ++st, len *= 3) {
     const int m = len / 3, tstep = M / len;
-    const DivBy dvs = seq_div(nseq, nt, seq_fast), dvm = div_by(m);
+    const DivBy dvs = div_by(nt), dvm = div_by(m);
     for (int it = threadIdx.x; it < nseq * nt; it += blockDim.x) {
       int q, b, j;
-      seq_item_ff(it, dvs, seq_fast, q, b);
+      seq_item_ff(it, nseq, dvs, seq_fast, q, b);
       const int blk = div_q(b, dvm, j);
       float4* p = x + q * ss + (blk * len + j) * es;
       const int sm = m * es;
@@ -373,28 +372,28 @@ __device__ inline void dft_fwd_ff(float4* x, int nseq, int es, int ss, const Dft
     return;
   }
   const int N = D.N, M = dft_len(D);
-  const DivBy dv1_ = seq_div(nseq, M, seq_fast);
+  const DivBy dv1_ = div_by(M);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv1_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv1_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = (k < N) ? zmulc(*p, __ldg(D.c + k)) : zzero();
   }
   __syncthreads();
   fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
-  const DivBy dv2_ = seq_div(nseq, M, seq_fast);
+  const DivBy dv2_ = div_by(M);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv2_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv2_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zmul(*p, __ldg(D.Bf + k));
   }
   __syncthreads();
   fft_inv_m_ff(x, D, nseq, es, ss, seq_fast);
-  const DivBy dv3_ = seq_div(nseq, N, seq_fast);
+  const DivBy dv3_ = div_by(N);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv3_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv3_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zscale(zmulc(*p, __ldg(D.c + k)), D.invM);
   }
@@ -410,19 +409,19 @@ __device__ inline void dft_inv_ff(float4* x, int nseq, int es, int ss, const Dft
     return;
   }
   const int N = D.N;
-  const DivBy dv4_ = seq_div(nseq, N, seq_fast);
+  const DivBy dv4_ = div_by(N);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv4_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv4_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zconj(*p);
   }
   __syncthreads();
   dft_fwd_ff(x, nseq, es, ss, D, seq_fast);
-  const DivBy dv5_ = seq_div(nseq, N, seq_fast);
+  const DivBy dv5_ = div_by(N);
   for (int it = threadIdx.x; it < nseq * N; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv5_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv5_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zconj(*p);
   }

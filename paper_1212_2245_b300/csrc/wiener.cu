@@ -151,20 +151,20 @@ __device__ __forceinline__ float ff_round(float2 v) { return v.x + v.y; }
 // storage order of fft_fwd_m_ff.  Ends with a barrier.
 __device__ inline void kernel_spectrum_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast) {
   const int N = D.N, M = dft_len(D), P = M - N;
-  const DivBy dv1_ = seq_div(nseq, P, seq_fast);
+  const DivBy dv1_ = div_by(P);
   for (int it = threadIdx.x; it < nseq * P; it += blockDim.x) {
     int q, j;
-    seq_item_ff(it, dv1_, seq_fast, q, j);
+    seq_item_ff(it, nseq, dv1_, seq_fast, q, j);
     float4* base = x + q * ss;
     const int m = N + j;  // targets m >= N; sources m - M + N < N
     base[m * es] = (m >= M - N + 1) ? base[(m - M + N) * es] : zzero();
   }
   __syncthreads();
   fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
-  const DivBy dv2_ = seq_div(nseq, M, seq_fast);
+  const DivBy dv2_ = div_by(M);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv2_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv2_, seq_fast, q, k);
     float4* p = x + q * ss + k * es;
     *p = zscale(*p, D.invM);
   }
@@ -179,18 +179,18 @@ __device__ inline void kernel_spectrum_ff(float4* x, int nseq, int es, int ss, c
 __device__ inline void filter_ff(float4* x, int nseq, int es, int ss, const Dft1ff& D, bool seq_fast,
                                  const float4* __restrict__ ks, int ksm, int ksq, int nvalid) {
   const int N = D.N, M = dft_len(D), P = M - N;
-  const DivBy dv3_ = seq_div(nseq, P, seq_fast);
+  const DivBy dv3_ = div_by(P);
   for (int it = threadIdx.x; it < nseq * P; it += blockDim.x) {
     int q, j;
-    seq_item_ff(it, dv3_, seq_fast, q, j);
+    seq_item_ff(it, nseq, dv3_, seq_fast, q, j);
     x[q * ss + (N + j) * es] = zzero();
   }
   __syncthreads();
   fft_fwd_m_ff(x, D, nseq, es, ss, seq_fast);
-  const DivBy dv4_ = seq_div(nseq, M, seq_fast);
+  const DivBy dv4_ = div_by(M);
   for (int it = threadIdx.x; it < nseq * M; it += blockDim.x) {
     int q, k;
-    seq_item_ff(it, dv4_, seq_fast, q, k);
+    seq_item_ff(it, nseq, dv4_, seq_fast, q, k);
     if (q >= nvalid) continue;
     float4* p = x + q * ss + k * es;
     *p = zmul(*p, __ldg(ks + (size_t)k * ksm + (size_t)q * ksq));
