@@ -121,6 +121,8 @@ struct WienerState {
 // Quotient and remainder of 0 <= n < 2^24 by a divisor 1 <= d < 2^24 fixed
 // for a loop, through a float reciprocal formed once: the product n (1/d)
 // is within one of n / d, and one step on the remainder makes it exact.
+// Here n counts the items of one CTA's sequences, which live in its shared
+// memory (at most 227 KB / 16 B per float-float element), so n < 2^24.
 struct DivBy {
   float r;
   int d;
