@@ -94,6 +94,16 @@ def test_process_wide_knobs_validate_their_arguments(lib):
         assert lib.db_set_one_axis_min(bad) == 1
     for good in (1, 16, 256, 0):
         assert lib.db_set_one_axis_min(good) == 0
+    for bad in (-1, 102):
+        assert lib.db_set_dense_min(bad) == 1
+    assert lib.db_set_dense_min(0) == 0
+    assert lib.db_set_fft_tiles(-1) == 1
+    assert lib.db_set_fft_tiles(0) == 0
+    for bad in (-1, 2):
+        assert lib.db_set_batch_order(bad) == 1
+        assert lib.db_set_tma(bad) == 1
+    assert lib.db_set_batch_order(1) == 0
+    assert lib.db_set_tma(1) == 0
 
 
 def test_host_path_arguments_are_checked_before_any_cuda_call(lib):
